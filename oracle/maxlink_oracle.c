@@ -1,0 +1,665 @@
+/*
+ * FP64 CPU oracle for the self-consistent Yee / molecular-ensemble time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously-correct
+ * restatement of the method of arXiv 2512.06173 (MaxwellLink), written from the
+ * paper's equations.  Only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it.  It shares no code, header, table or helper with the
+ * CUDA library: every quantity here is recomputed from its definition.
+ *
+ * Units: c = eps0 = mu0 = hbar = 1, cell edge 1 (Appendix A), dt = Courant number.
+ * Staggering (Yee 1966, cited in Sec. II.A.1): E at integer steps, H at half steps;
+ *   Ex(i,j,k) at (i+1/2, j, k)     Hx(i,j,k) at (i, j+1/2, k+1/2)
+ *   Ey(i,j,k) at (i, j+1/2, k)     Hy(i,j,k) at (i+1/2, j, k+1/2)
+ *   Ez(i,j,k) at (i, j, k+1/2)     Hz(i,j,k) at (i+1/2, j+1/2, k)
+ * Arrays are (nz, ny, nx) row-major, x fastest.  Outside the grid a non-periodic
+ * axis reads 0 (a PEC wall at index n); tangential E on the wall at index 0 is held
+ * at 0.  Periodic axes wrap.
+ *
+ * One step n -> n+1 (Eq. Maxwell, Eq. E_regu, Eq. von-Neumann-tls, Eq.
+ * dipole_derivative, Eq. J_mol, Eq. Polarization_mol):
+ *   1. every molecule gathers Etilde_m = gamma_m * sum_cells E^n kappa_m   (Eq. E_regu_Emi)
+ *   2. rho_m^n -> rho_m^{n+1} under H0 - Etilde_m . mu (held over the step), with
+ *      the optional Lindblad terms                                          (Eq. von-Neumann-tls)
+ *   3. mudot_m = (Tr rho^{n+1} mu - Tr rho^n mu) / dt                       (Eq. dipole_derivative)
+ *   4. H^{n+1/2} = H^{n-1/2} - dt curl E^n  (CPML)                           (Eq. Maxwell b)
+ *   5. J^{n+1/2} = sum_m gamma_m mudot_m kappa_m + sources; Drude J_D^{n+1/2}
+ *   6. E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J - J_D)                     (Eq. Maxwell a)
+ *   7. DFT accumulators (E at t=(n+1)dt, H at t=(n+1/2)dt), molecular energy.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define MAXLEV 8
+
+typedef struct {
+    int n;
+    double pos[3], sigma, gamma, decay, dephase;
+    int kind, nsub;
+    cplx H0[MAXLEV * MAXLEV], mu[3][MAXLEV * MAXLEV], rho[MAXLEV * MAXLEV];
+    double Et[3], mudot[3], energy_sum;
+} omol;
+
+typedef struct {
+    int axis, index, comp;
+    double amp, omega, width, t0;
+} osrc;
+
+typedef struct {
+    int axis, index, nfreq;
+    double *omega;
+    /* accumulators over the plane (two tangential E, two tangential H), per freq */
+    cplx *E1, *E2, *H1, *H2;
+} oplane;
+
+typedef struct {
+    int nx, ny, nz;
+    double dt;
+    int periodic[3];
+    int pml[6];
+    double pml_m, sigma_max, kappa_max, alpha_max;
+    double *E[3], *H[3];
+    double *psi[12];   /* CPML memory variables, full grid (0 outside the layers) */
+    double *eps;       /* relative permittivity (eps_inf in Drude cells) */
+    double *wp, *dg;   /* Drude plasma frequency and damping per cell */
+    double *JD[3];     /* Drude polarisation current at n-1/2 */
+    double *J[3];      /* scratch: molecular + source current at n+1/2 */
+    /* CPML coefficients per axis: integer positions (E update) and half positions (H update) */
+    double *bE[3], *cE[3], *kE[3], *bH[3], *cH[3], *kH[3];
+    int nmol, capmol;
+    omol *mol;
+    int nsrc;
+    osrc src[16];
+    int nplane;
+    oplane plane[16];
+    long step;
+    double absorbed;
+} osim;
+
+static long nn(const osim *s) { return (long)s->nx * s->ny * s->nz; }
+static int dimn(const osim *s, int a) { return a == 0 ? s->nx : (a == 1 ? s->ny : s->nz); }
+
+/* flat index of a cell after applying the boundary rule; -1 if outside a wall */
+static long cell(const osim *s, int i, int j, int k) {
+    int c[3] = {i, j, k};
+    for (int a = 0; a < 3; a++) {
+        int n = dimn(s, a);
+        if (c[a] < 0 || c[a] >= n) {
+            if (!s->periodic[a]) return -1;
+            c[a] = ((c[a] % n) + n) % n;
+        }
+    }
+    return ((long)c[2] * s->ny + c[1]) * s->nx + c[0];
+}
+
+static double at(const osim *s, const double *f, int i, int j, int k) {
+    long c = cell(s, i, j, k);
+    return c < 0 ? 0.0 : f[c];
+}
+
+/* Roden-Gedney CPML profile (Taflove & Hagness, cited as the PML reference) at
+ * position x along axis a.  Depth u in [0,1] grows towards the outer wall. */
+static void pml_coeff(const osim *s, int a, double x, double *b, double *c, double *ik) {
+    int n = dimn(s, a);
+    int dl = s->pml[2 * a], dh = s->pml[2 * a + 1];
+    double u = 0.0;
+    if (dl > 0 && x < dl) u = (dl - x) / dl;
+    else if (dh > 0 && x > n - dh) u = (x - (n - dh)) / dh;
+    if (u <= 0.0) { *b = 0.0; *c = 0.0; *ik = 1.0; return; }
+    double sig = s->sigma_max * pow(u, s->pml_m);
+    double kap = 1.0 + (s->kappa_max - 1.0) * pow(u, s->pml_m);
+    double alp = s->alpha_max * (1.0 - u);
+    *b = exp(-(sig / kap + alp) * s->dt);
+    *c = sig > 0.0 ? sig / (sig * kap + kap * kap * alp) * (*b - 1.0) : 0.0;
+    *ik = 1.0 / kap;
+}
+
+osim *orc_create(int nx, int ny, int nz, double dt, const int *periodic, const int *pml,
+                 double pml_m, double sigma_max, double kappa_max, double alpha_max,
+                 const double *eps, const double *wp, const double *dg) {
+    osim *s = (osim *)calloc(1, sizeof(osim));
+    s->nx = nx; s->ny = ny; s->nz = nz; s->dt = dt;
+    for (int a = 0; a < 3; a++) s->periodic[a] = periodic[a];
+    for (int f = 0; f < 6; f++) s->pml[f] = pml[f];
+    s->pml_m = pml_m; s->sigma_max = sigma_max; s->kappa_max = kappa_max; s->alpha_max = alpha_max;
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) {
+        s->E[a] = calloc(N, sizeof(double));
+        s->H[a] = calloc(N, sizeof(double));
+        s->JD[a] = calloc(N, sizeof(double));
+        s->J[a] = calloc(N, sizeof(double));
+    }
+    for (int p = 0; p < 12; p++) s->psi[p] = calloc(N, sizeof(double));
+    s->eps = malloc(N * sizeof(double));
+    s->wp = calloc(N, sizeof(double));
+    s->dg = calloc(N, sizeof(double));
+    for (long c = 0; c < N; c++) {
+        s->eps[c] = eps ? eps[c] : 1.0;
+        if (wp) s->wp[c] = wp[c];
+        if (dg) s->dg[c] = dg[c];
+    }
+    for (int a = 0; a < 3; a++) {
+        int n = dimn(s, a);
+        s->bE[a] = malloc(n * sizeof(double)); s->cE[a] = malloc(n * sizeof(double));
+        s->kE[a] = malloc(n * sizeof(double)); s->bH[a] = malloc(n * sizeof(double));
+        s->cH[a] = malloc(n * sizeof(double)); s->kH[a] = malloc(n * sizeof(double));
+        for (int i = 0; i < n; i++) {
+            pml_coeff(s, a, (double)i, &s->bE[a][i], &s->cE[a][i], &s->kE[a][i]);
+            pml_coeff(s, a, i + 0.5, &s->bH[a][i], &s->cH[a][i], &s->kH[a][i]);
+        }
+    }
+    return s;
+}
+
+void orc_destroy(osim *s) {
+    if (!s) return;
+    for (int a = 0; a < 3; a++) {
+        free(s->E[a]); free(s->H[a]); free(s->JD[a]); free(s->J[a]);
+        free(s->bE[a]); free(s->cE[a]); free(s->kE[a]);
+        free(s->bH[a]); free(s->cH[a]); free(s->kH[a]);
+    }
+    for (int p = 0; p < 12; p++) free(s->psi[p]);
+    free(s->eps); free(s->wp); free(s->dg);
+    free(s->mol);
+    for (int p = 0; p < s->nplane; p++) {
+        free(s->plane[p].omega); free(s->plane[p].E1); free(s->plane[p].E2);
+        free(s->plane[p].H1); free(s->plane[p].H2);
+    }
+    free(s);
+}
+
+/* ------------------------------------------------------------------ molecules */
+
+int orc_add_molecule(osim *s, int n, const double *pos, double sigma, double gamma,
+                     double decay, double dephase, int kind, int nsub,
+                     const double *H0_ri, const double *mu_ri, const double *rho_ri) {
+    if (n < 2 || n > MAXLEV) return -1;
+    if (s->nmol == s->capmol) {
+        s->capmol = s->capmol ? 2 * s->capmol : 16;
+        s->mol = realloc(s->mol, s->capmol * sizeof(omol));
+    }
+    omol *m = &s->mol[s->nmol];
+    memset(m, 0, sizeof(*m));
+    m->n = n; m->sigma = sigma; m->gamma = gamma; m->decay = decay; m->dephase = dephase;
+    m->kind = kind; m->nsub = nsub < 1 ? 1 : nsub;
+    for (int a = 0; a < 3; a++) m->pos[a] = pos[a];
+    for (int e = 0; e < n * n; e++) {
+        m->H0[e] = H0_ri[2 * e] + I * H0_ri[2 * e + 1];
+        m->rho[e] = rho_ri[2 * e] + I * rho_ri[2 * e + 1];
+        for (int a = 0; a < 3; a++)
+            m->mu[a][e] = mu_ri[2 * (a * n * n + e)] + I * mu_ri[2 * (a * n * n + e) + 1];
+    }
+    return s->nmol++;
+}
+
+/* Gaussian kernel (Eq. Polarization_mol with the Gaussian choice of Sec. II.A.1):
+ * along axis a the window is the 2R+2 indices starting at floor(pos)-R, R=ceil(3 sigma);
+ * sample positions are i (stag=0) or i+1/2 (stag=1); the 1D weights are normalised
+ * to sum 1 over the window, so the 3D sum of kappa times the cell volume is 1. */
+static int window(const omol *m, int a, int stag, int *i0, double *w) {
+    int R = (int)ceil(3.0 * m->sigma);
+    int W = 2 * R + 2;
+    *i0 = (int)floor(m->pos[a]) - R;
+    double sum = 0.0;
+    for (int t = 0; t < W; t++) {
+        double x = (*i0 + t) + 0.5 * stag;
+        double d = x - m->pos[a];
+        w[t] = exp(-d * d / (2.0 * m->sigma * m->sigma));
+        sum += w[t];
+    }
+    for (int t = 0; t < W; t++) w[t] /= sum;
+    return W;
+}
+
+/* Etilde_m^c = gamma_m * sum over the window of E^c(cell) kappa^c(cell)   (Eq. E_regu_Emi) */
+static int gather(const osim *s, const omol *m, double *out) {
+    for (int c = 0; c < 3; c++) {
+        int i0[3], W[3];
+        double w[3][32];
+        for (int a = 0; a < 3; a++) W[a] = window(m, a, a == c ? 1 : 0, &i0[a], w[a]);
+        double acc = 0.0;
+        for (int tk = 0; tk < W[2]; tk++)
+            for (int tj = 0; tj < W[1]; tj++)
+                for (int ti = 0; ti < W[0]; ti++) {
+                    long cc = cell(s, i0[0] + ti, i0[1] + tj, i0[2] + tk);
+                    if (cc < 0) return -1;
+                    acc += w[0][ti] * w[1][tj] * w[2][tk] * s->E[c][cc];
+                }
+        out[c] = m->gamma * acc;
+    }
+    return 0;
+}
+
+/* J^c(cell) += gamma_m * mudot_m^c * kappa^c(cell)   (Eq. J_mol with Eq. Polarization_mol) */
+static int scatter(osim *s, const omol *m) {
+    for (int c = 0; c < 3; c++) {
+        int i0[3], W[3];
+        double w[3][32];
+        for (int a = 0; a < 3; a++) W[a] = window(m, a, a == c ? 1 : 0, &i0[a], w[a]);
+        double amp = m->gamma * m->mudot[c];
+        for (int tk = 0; tk < W[2]; tk++)
+            for (int tj = 0; tj < W[1]; tj++)
+                for (int ti = 0; ti < W[0]; ti++) {
+                    long cc = cell(s, i0[0] + ti, i0[1] + tj, i0[2] + tk);
+                    if (cc < 0) return -1;
+                    s->J[c][cc] += amp * w[0][ti] * w[1][tj] * w[2][tk];
+                }
+    }
+    return 0;
+}
+
+static void matmul(int n, const cplx *A, const cplx *B, cplx *C) {
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            cplx acc = 0;
+            for (int l = 0; l < n; l++) acc += A[i * n + l] * B[l * n + j];
+            C[i * n + j] = acc;
+        }
+}
+
+static void dagger(int n, const cplx *A, cplx *B) {
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) B[j * n + i] = conj(A[i * n + j]);
+}
+
+/* Right-hand side of Eq. von-Neumann-tls in GKSL form:
+ *   drho/dt = -i [H, rho] + sum_k ( L_k rho L_k^+ - 1/2 {L_k^+ L_k, rho} )
+ * with ladder decay L_k = sqrt(decay) |k-1><k| (k = 1..n-1) and pure dephasing
+ * L_k = sqrt(dephase) |k><k| (k = 0..n-1).  The operators are built as matrices and
+ * multiplied out literally. */
+static void lindblad_rhs(const omol *m, const cplx *H, const cplx *rho, cplx *out) {
+    int n = m->n;
+    cplx A[MAXLEV * MAXLEV], B[MAXLEV * MAXLEV], L[MAXLEV * MAXLEV], Ld[MAXLEV * MAXLEV];
+    cplx LdL[MAXLEV * MAXLEV], T1[MAXLEV * MAXLEV], T2[MAXLEV * MAXLEV];
+    matmul(n, H, rho, A);
+    matmul(n, rho, H, B);
+    for (int e = 0; e < n * n; e++) out[e] = -I * (A[e] - B[e]);
+    for (int pass = 0; pass < 2; pass++) {
+        double rate = pass == 0 ? m->decay : m->dephase;
+        if (rate == 0.0) continue;
+        for (int k = (pass == 0 ? 1 : 0); k < n; k++) {
+            memset(L, 0, sizeof(L));
+            if (pass == 0) L[(k - 1) * n + k] = sqrt(rate);
+            else L[k * n + k] = sqrt(rate);
+            dagger(n, L, Ld);
+            matmul(n, Ld, L, LdL);
+            matmul(n, L, rho, T1);
+            matmul(n, T1, Ld, T2);          /* L rho L^+ */
+            matmul(n, LdL, rho, A);
+            matmul(n, rho, LdL, B);
+            for (int e = 0; e < n * n; e++) out[e] += T2[e] - 0.5 * (A[e] + B[e]);
+        }
+    }
+}
+
+static void effective_h(const omol *m, const double *Et, cplx *H) {
+    int n = m->n;
+    for (int e = 0; e < n * n; e++)
+        H[e] = m->H0[e] - (Et[0] * m->mu[0][e] + Et[1] * m->mu[1][e] + Et[2] * m->mu[2][e]);
+}
+
+/* exp(-i H dt) for a 2x2 Hermitian H:
+ *   e^{-i tr dt/2} [cos(W dt) I - i sin(W dt)/W (H - tr/2 I)],  W = sqrt(((a-d)/2)^2 + |b|^2) */
+static void unitary2(const cplx *H, double dt, cplx *U) {
+    double a = creal(H[0]), d = creal(H[3]);
+    cplx b = H[1];
+    double h = 0.5 * (a + d), z = 0.5 * (a - d);
+    double W = sqrt(z * z + creal(b * conj(b)));
+    double cw = cos(W * dt);
+    double sw = W > 0 ? sin(W * dt) / W : dt;
+    cplx ph = cexp(-I * h * dt);
+    U[0] = ph * (cw - I * sw * z);
+    U[1] = ph * (-I * sw * b);
+    U[2] = ph * (-I * sw * conj(b));
+    U[3] = ph * (cw + I * sw * z);
+}
+
+static void mu_expect(const omol *m, const cplx *rho, double *out) {
+    int n = m->n;
+    for (int a = 0; a < 3; a++) {
+        cplx acc = 0;
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) acc += rho[i * n + j] * m->mu[a][j * n + i];
+        out[a] = creal(acc);
+    }
+}
+
+/* Advance one molecule over dt under the held field Et; sets mudot (Eq. dipole_derivative). */
+static void molecule_advance(omol *m, const double *Et, double dt) {
+    int n = m->n;
+    cplx H[MAXLEV * MAXLEV];
+    double mu0[3], mu1[3];
+    for (int a = 0; a < 3; a++) m->Et[a] = Et[a];
+    mu_expect(m, m->rho, mu0);
+    effective_h(m, Et, H);
+    if (m->kind == 0) {
+        cplx U[4], Ud[4], T[4];
+        unitary2(H, dt, U);
+        dagger(2, U, Ud);
+        matmul(2, U, m->rho, T);
+        matmul(2, T, Ud, m->rho);
+    } else {
+        double h = dt / m->nsub;
+        cplx k1[MAXLEV * MAXLEV], k2[MAXLEV * MAXLEV], k3[MAXLEV * MAXLEV], k4[MAXLEV * MAXLEV];
+        cplx tmp[MAXLEV * MAXLEV];
+        for (int sstep = 0; sstep < m->nsub; sstep++) {
+            lindblad_rhs(m, H, m->rho, k1);
+            for (int e = 0; e < n * n; e++) tmp[e] = m->rho[e] + 0.5 * h * k1[e];
+            lindblad_rhs(m, H, tmp, k2);
+            for (int e = 0; e < n * n; e++) tmp[e] = m->rho[e] + 0.5 * h * k2[e];
+            lindblad_rhs(m, H, tmp, k3);
+            for (int e = 0; e < n * n; e++) tmp[e] = m->rho[e] + h * k3[e];
+            lindblad_rhs(m, H, tmp, k4);
+            for (int e = 0; e < n * n; e++)
+                m->rho[e] += h / 6.0 * (k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + k4[e]);
+        }
+    }
+    mu_expect(m, m->rho, mu1);
+    for (int a = 0; a < 3; a++) m->mudot[a] = (mu1[a] - mu0[a]) / dt;
+}
+
+/* ------------------------------------------------------------------ field step */
+
+static double src_value(const osrc *q, double t) {
+    double u = (t - q->t0) / q->width;
+    return q->amp * exp(-0.5 * u * u) * cos(q->omega * (t - q->t0));
+}
+
+static int pec_forced(const osim *s, int comp, int i, int j, int k) {
+    /* tangential E on the wall at index 0 of a non-periodic axis */
+    int idx[3] = {i, j, k};
+    for (int a = 0; a < 3; a++)
+        if (a != comp && !s->periodic[a] && idx[a] == 0) return 1;
+    return 0;
+}
+
+int orc_step(osim *s, long nsteps) {
+    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    const double dt = s->dt;
+    long N = nn(s);
+    for (long it = 0; it < nsteps; it++) {
+        /* 1-3: molecules */
+        for (int q = 0; q < s->nmol; q++) {
+            double Et[3];
+            if (gather(s, &s->mol[q], Et)) return -1;
+            molecule_advance(&s->mol[q], Et, dt);
+        }
+        /* 4: H^{n+1/2} with CPML */
+        double **E = s->E, **H = s->H, **P = s->psi;
+        #pragma omp parallel for schedule(static)
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    long c = ((long)k * ny + j) * nx + i;
+                    double ex = E[0][c], ey = E[1][c], ez = E[2][c];
+                    double dEz_dy = at(s, E[2], i, j + 1, k) - ez;
+                    double dEy_dz = at(s, E[1], i, j, k + 1) - ey;
+                    double dEx_dz = at(s, E[0], i, j, k + 1) - ex;
+                    double dEz_dx = at(s, E[2], i + 1, j, k) - ez;
+                    double dEy_dx = at(s, E[1], i + 1, j, k) - ey;
+                    double dEx_dy = at(s, E[0], i, j + 1, k) - ex;
+                    P[0][c] = s->bH[1][j] * P[0][c] + s->cH[1][j] * dEz_dy;
+                    P[1][c] = s->bH[2][k] * P[1][c] + s->cH[2][k] * dEy_dz;
+                    P[2][c] = s->bH[2][k] * P[2][c] + s->cH[2][k] * dEx_dz;
+                    P[3][c] = s->bH[0][i] * P[3][c] + s->cH[0][i] * dEz_dx;
+                    P[4][c] = s->bH[0][i] * P[4][c] + s->cH[0][i] * dEy_dx;
+                    P[5][c] = s->bH[1][j] * P[5][c] + s->cH[1][j] * dEx_dy;
+                    double cx = (s->kH[1][j] * dEz_dy + P[0][c]) - (s->kH[2][k] * dEy_dz + P[1][c]);
+                    double cy = (s->kH[2][k] * dEx_dz + P[2][c]) - (s->kH[0][i] * dEz_dx + P[3][c]);
+                    double cz = (s->kH[0][i] * dEy_dx + P[4][c]) - (s->kH[1][j] * dEx_dy + P[5][c]);
+                    H[0][c] -= dt * cx;
+                    H[1][c] -= dt * cy;
+                    H[2][c] -= dt * cz;
+                }
+        /* 5: currents at n+1/2 */
+        for (int a = 0; a < 3; a++) memset(s->J[a], 0, N * sizeof(double));
+        for (int q = 0; q < s->nmol; q++)
+            if (scatter(s, &s->mol[q])) return -1;
+        double th = (s->step + 0.5) * dt;
+        for (int q = 0; q < s->nsrc; q++) {
+            const osrc *src = &s->src[q];
+            double v = src_value(src, th);
+            for (int k = 0; k < nz; k++)
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        int idx[3] = {i, j, k};
+                        if (idx[src->axis] != src->index) continue;
+                        s->J[src->comp][((long)k * ny + j) * nx + i] += v;
+                    }
+        }
+        /* 6: E^{n+1} (Drude current from E^n first) */
+        double absorbed = 0.0;
+        #pragma omp parallel for schedule(static) reduction(+:absorbed)
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    long c = ((long)k * ny + j) * nx + i;
+                    double hx = H[0][c], hy = H[1][c], hz = H[2][c];
+                    double dHz_dy = hz - at(s, H[2], i, j - 1, k);
+                    double dHy_dz = hy - at(s, H[1], i, j, k - 1);
+                    double dHx_dz = hx - at(s, H[0], i, j, k - 1);
+                    double dHz_dx = hz - at(s, H[2], i - 1, j, k);
+                    double dHy_dx = hy - at(s, H[1], i - 1, j, k);
+                    double dHx_dy = hx - at(s, H[0], i, j - 1, k);
+                    P[6][c] = s->bE[1][j] * P[6][c] + s->cE[1][j] * dHz_dy;
+                    P[7][c] = s->bE[2][k] * P[7][c] + s->cE[2][k] * dHy_dz;
+                    P[8][c] = s->bE[2][k] * P[8][c] + s->cE[2][k] * dHx_dz;
+                    P[9][c] = s->bE[0][i] * P[9][c] + s->cE[0][i] * dHz_dx;
+                    P[10][c] = s->bE[0][i] * P[10][c] + s->cE[0][i] * dHy_dx;
+                    P[11][c] = s->bE[1][j] * P[11][c] + s->cE[1][j] * dHx_dy;
+                    double curl[3];
+                    curl[0] = (s->kE[1][j] * dHz_dy + P[6][c]) - (s->kE[2][k] * dHy_dz + P[7][c]);
+                    curl[1] = (s->kE[2][k] * dHx_dz + P[8][c]) - (s->kE[0][i] * dHz_dx + P[9][c]);
+                    curl[2] = (s->kE[0][i] * dHy_dx + P[10][c]) - (s->kE[1][j] * dHx_dy + P[11][c]);
+                    for (int a = 0; a < 3; a++) {
+                        double jd = 0.0;
+                        if (s->wp[c] != 0.0) {
+                            /* Drude ADE: dJ/dt + g J = wp^2 E, centred at n */
+                            double g2 = 0.5 * s->dg[c] * dt;
+                            jd = ((1.0 - g2) * s->JD[a][c] + dt * s->wp[c] * s->wp[c] * E[a][c]) / (1.0 + g2);
+                        }
+                        double e_old = E[a][c];
+                        double e_new = pec_forced(s, a, i, j, k)
+                                           ? 0.0
+                                           : e_old + dt / s->eps[c] * (curl[a] - s->J[a][c] - jd);
+                        if (s->wp[c] != 0.0) {
+                            absorbed += jd * 0.5 * (e_old + e_new) * dt;
+                            s->JD[a][c] = jd;
+                        }
+                        E[a][c] = e_new;
+                    }
+                }
+        s->absorbed += absorbed;
+        /* 7: DFT accumulators and molecular energy */
+        double tE = (s->step + 1) * dt;
+        for (int p = 0; p < s->nplane; p++) {
+            oplane *pl = &s->plane[p];
+            int a = pl->axis, b = (a + 1) % 3, c2 = (a + 2) % 3;
+            int nb = dimn(s, b), nc = dimn(s, c2);
+            for (int f = 0; f < pl->nfreq; f++) {
+                cplx pe = cexp(I * pl->omega[f] * tE) * dt;
+                cplx ph = cexp(I * pl->omega[f] * th) * dt;
+                for (int v = 0; v < nc; v++)
+                    for (int u = 0; u < nb; u++) {
+                        int idx[3], idm[3];
+                        idx[a] = pl->index; idx[b] = u; idx[c2] = v;
+                        idm[a] = pl->index - 1; idm[b] = u; idm[c2] = v;
+                        long o = ((long)f * nc + v) * nb + u;
+                        pl->E1[o] += pe * at(s, E[b], idx[0], idx[1], idx[2]);
+                        pl->E2[o] += pe * at(s, E[c2], idx[0], idx[1], idx[2]);
+                        pl->H1[o] += ph * 0.5 * (at(s, H[b], idx[0], idx[1], idx[2]) +
+                                                 at(s, H[b], idm[0], idm[1], idm[2]));
+                        pl->H2[o] += ph * 0.5 * (at(s, H[c2], idx[0], idx[1], idx[2]) +
+                                                 at(s, H[c2], idm[0], idm[1], idm[2]));
+                    }
+            }
+        }
+        for (int q = 0; q < s->nmol; q++) {
+            omol *m = &s->mol[q];
+            cplx acc = 0;
+            for (int i = 0; i < m->n; i++)
+                for (int j = 0; j < m->n; j++) acc += m->rho[i * m->n + j] * m->H0[j * m->n + i];
+            m->energy_sum += creal(acc);
+        }
+        s->step++;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ sources, planes */
+
+int orc_add_source(osim *s, int axis, int index, int comp, double amp, double omega,
+                   double width, double t0) {
+    if (s->nsrc >= 16) return -1;
+    osrc *q = &s->src[s->nsrc];
+    q->axis = axis; q->index = index; q->comp = comp;
+    q->amp = amp; q->omega = omega; q->width = width; q->t0 = t0;
+    return s->nsrc++;
+}
+
+int orc_add_plane(osim *s, int axis, int index, int nfreq, const double *omega) {
+    if (s->nplane >= 16) return -1;
+    oplane *p = &s->plane[s->nplane];
+    p->axis = axis; p->index = index; p->nfreq = nfreq;
+    p->omega = malloc(nfreq * sizeof(double));
+    memcpy(p->omega, omega, nfreq * sizeof(double));
+    int b = (axis + 1) % 3, c = (axis + 2) % 3;
+    long cnt = (long)nfreq * dimn(s, b) * dimn(s, c);
+    p->E1 = calloc(cnt, sizeof(cplx)); p->E2 = calloc(cnt, sizeof(cplx));
+    p->H1 = calloc(cnt, sizeof(cplx)); p->H2 = calloc(cnt, sizeof(cplx));
+    return s->nplane++;
+}
+
+/* Net flux Re sum over the plane of (Etilde x Htilde*) . n per frequency, with
+ * (a,b,c) cyclic: S_a = E_b H_c^* - E_c H_b^*; H is the mean of the two half cells
+ * on either side of the plane. */
+int orc_flux(const osim *s, int p, double *out) {
+    if (p < 0 || p >= s->nplane) return -1;
+    const oplane *pl = &s->plane[p];
+    int b = (pl->axis + 1) % 3, c = (pl->axis + 2) % 3;
+    long cnt = (long)dimn(s, b) * dimn(s, c);
+    for (int f = 0; f < pl->nfreq; f++) {
+        double acc = 0.0;
+        for (long o = 0; o < cnt; o++) {
+            long q = (long)f * cnt + o;
+            acc += creal(pl->E1[q] * conj(pl->H2[q]) - pl->E2[q] * conj(pl->H1[q]));
+        }
+        out[f] = acc;
+    }
+    return 0;
+}
+
+/* raw plane accumulators, interleaved re/im: order E1, E2, H1, H2, each (nfreq, nc, nb) */
+int orc_plane_data(const osim *s, int p, double *out) {
+    if (p < 0 || p >= s->nplane) return -1;
+    const oplane *pl = &s->plane[p];
+    int b = (pl->axis + 1) % 3, c = (pl->axis + 2) % 3;
+    long cnt = (long)pl->nfreq * dimn(s, b) * dimn(s, c);
+    const cplx *arr[4] = {pl->E1, pl->E2, pl->H1, pl->H2};
+    for (int q = 0; q < 4; q++)
+        for (long o = 0; o < cnt; o++) {
+            out[2 * (q * cnt + o)] = creal(arr[q][o]);
+            out[2 * (q * cnt + o) + 1] = cimag(arr[q][o]);
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ accessors */
+
+void orc_get_fields(const osim *s, double *out) {   /* 6 x N: Ex Ey Ez Hx Hy Hz */
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) {
+        memcpy(out + a * N, s->E[a], N * sizeof(double));
+        memcpy(out + (3 + a) * N, s->H[a], N * sizeof(double));
+    }
+}
+
+void orc_set_fields(osim *s, const double *in) {
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) {
+        memcpy(s->E[a], in + a * N, N * sizeof(double));
+        memcpy(s->H[a], in + (3 + a) * N, N * sizeof(double));
+    }
+}
+
+void orc_get_drude(const osim *s, double *out) {
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) memcpy(out + a * N, s->JD[a], N * sizeof(double));
+}
+
+void orc_get_psi(const osim *s, double *out) {
+    long N = nn(s);
+    for (int p = 0; p < 12; p++) memcpy(out + p * N, s->psi[p], N * sizeof(double));
+}
+
+int orc_nmol(const osim *s) { return s->nmol; }
+long orc_step_count(const osim *s) { return s->step; }
+double orc_absorbed(const osim *s) { return s->absorbed; }
+
+/* per molecule: Et[3], mudot[3], energy_sum */
+int orc_get_mol(const osim *s, int q, double *Et, double *mudot, double *energy_sum) {
+    if (q < 0 || q >= s->nmol) return -1;
+    for (int a = 0; a < 3; a++) { Et[a] = s->mol[q].Et[a]; mudot[a] = s->mol[q].mudot[a]; }
+    *energy_sum = s->mol[q].energy_sum;
+    return 0;
+}
+
+int orc_get_rho(const osim *s, int q, double *rho_ri) {
+    if (q < 0 || q >= s->nmol) return -1;
+    const omol *m = &s->mol[q];
+    for (int e = 0; e < m->n * m->n; e++) {
+        rho_ri[2 * e] = creal(m->rho[e]);
+        rho_ri[2 * e + 1] = cimag(m->rho[e]);
+    }
+    return m->n;
+}
+
+int orc_set_rho(osim *s, int q, const double *rho_ri) {
+    if (q < 0 || q >= s->nmol) return -1;
+    omol *m = &s->mol[q];
+    for (int e = 0; e < m->n * m->n; e++) m->rho[e] = rho_ri[2 * e] + I * rho_ri[2 * e + 1];
+    return 0;
+}
+
+/* Field-free pieces for unit tests: gather at the current fields; advance one
+ * molecule under a prescribed field (classical-path mode, Eq. E_analytical). */
+int orc_gather(const osim *s, int q, double *out) {
+    if (q < 0 || q >= s->nmol) return -1;
+    return gather(s, &s->mol[q], out);
+}
+
+int orc_molecule_step(osim *s, int q, const double *Et, double dt, double *mudot) {
+    if (q < 0 || q >= s->nmol) return -1;
+    molecule_advance(&s->mol[q], Et, dt);
+    for (int a = 0; a < 3; a++) mudot[a] = s->mol[q].mudot[a];
+    return 0;
+}
+
+int orc_lindblad_rhs(const osim *s, int q, const double *Et, const double *rho_ri, double *out_ri) {
+    if (q < 0 || q >= s->nmol) return -1;
+    const omol *m = &s->mol[q];
+    cplx H[MAXLEV * MAXLEV], r[MAXLEV * MAXLEV], o[MAXLEV * MAXLEV];
+    for (int e = 0; e < m->n * m->n; e++) r[e] = rho_ri[2 * e] + I * rho_ri[2 * e + 1];
+    effective_h(m, Et, H);
+    lindblad_rhs(m, H, r, o);
+    for (int e = 0; e < m->n * m->n; e++) { out_ri[2 * e] = creal(o[e]); out_ri[2 * e + 1] = cimag(o[e]); }
+    return 0;
+}
+
+/* the dense molecular current of the last step (for the gather/scatter duality test) */
+void orc_get_current(const osim *s, double *out) {
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) memcpy(out + a * N, s->J[a], N * sizeof(double));
+}
+
+/* CPML coefficient tables: 6 x n (bE cE kE bH cH kH) along axis a */
+void orc_pml_tables(const osim *s, int a, double *out) {
+    int n = dimn(s, a);
+    double *src[6] = {s->bE[a], s->cE[a], s->kE[a], s->bH[a], s->cH[a], s->kH[a]};
+    for (int q = 0; q < 6; q++) memcpy(out + (long)q * n, src[q], n * sizeof(double));
+}

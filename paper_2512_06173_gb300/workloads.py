@@ -1,0 +1,357 @@
+"""Seeded synthetic inputs for the coupled Yee/molecule step.
+
+This module only *describes* problems: grid sizes, boundary layers, material maps,
+sources, molecule tables and flux planes, drawn from numpy PCG64 generators with
+fixed seeds.  It holds none of the method's arithmetic (no field update, no kernel
+weights, no propagator); both the CUDA library binding and the FP64 oracle consume
+the same `Problem` objects and each converts them on its own.
+
+Units are grid units with c = eps0 = mu0 = hbar = 1 and a cell edge of 1 (the MEEP
+convention the paper adopts in Appendix A), so the time step equals the Courant
+number.
+
+Workload shapes follow the paper's examples (Sec. IV and Appendix B):
+superradiant emitter ensembles (Sec. IV.A), a Bragg resonator with a vibrational
+ensemble (Sec. IV.C) and a metal nanostructure with a molecular shell (Sec. IV.D).
+The paper's own inputs (MEEP geometries, water and HCN data) are not available, so
+these synthetic problems stand in for them.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# Propagator kinds for molecules.
+KIND_EXACT2 = 0  # two-level, no dissipation: exact exponential of the held 2x2 Hamiltonian
+KIND_RK4 = 1     # any level count 2..8, optional Lindblad terms: classic RK4 substeps
+
+MAX_LEVELS = 8
+
+
+@dataclass
+class Source:
+    """Soft current sheet on the plane index `index` normal to `axis`,
+    polarised along `comp`, time profile amp*exp(-((t-t0)/width)^2/2)*cos(omega*(t-t0))."""
+    axis: int
+    index: int
+    comp: int
+    amp: float
+    omega: float
+    width: float
+    t0: float
+
+
+@dataclass
+class FluxPlane:
+    axis: int
+    index: int
+    omegas: np.ndarray  # float64 (nfreq,)
+
+
+@dataclass
+class Material:
+    eps_inf: float = 1.0
+    wp: float = 0.0      # Drude plasma frequency (0: no Drude term)
+    gamma: float = 0.0   # Drude damping
+
+
+@dataclass
+class Molecules:
+    """Packed molecule table.  Matrices of molecule m live at pool[off[m] : off[m]+n*n]
+    (row-major n x n, complex128)."""
+    nlev: np.ndarray      # int32 (M,)
+    off: np.ndarray       # int64 (M,)
+    pos: np.ndarray       # float64 (M,3), grid units, cell (i,j,k) spans [i,i+1) x ...
+    sigma: np.ndarray     # float64 (M,) Gaussian width in cells
+    gamma: np.ndarray     # float64 (M,) coupling rescale (Eq. Polarization_mol)
+    decay: np.ndarray     # float64 (M,) ladder decay rate (Lindblad, k -> k-1)
+    dephase: np.ndarray   # float64 (M,) pure dephasing rate of every coherence
+    kind: np.ndarray      # int32 (M,) KIND_EXACT2 | KIND_RK4
+    nsub: np.ndarray      # int32 (M,) RK4 substeps per field step
+    H0: np.ndarray        # complex128 pool
+    mu: np.ndarray        # complex128 (3, pool) dipole operators x, y, z
+    rho0: np.ndarray      # complex128 pool, initial density matrices
+
+    @property
+    def count(self) -> int:
+        return int(self.nlev.shape[0])
+
+    def matrix(self, pool: np.ndarray, m: int) -> np.ndarray:
+        n = int(self.nlev[m])
+        o = int(self.off[m])
+        return pool[o:o + n * n].reshape(n, n)
+
+    def subset(self, idx: Sequence[int]) -> "Molecules":
+        idx = np.asarray(idx, dtype=np.int64)
+        nl = self.nlev[idx]
+        sizes = nl.astype(np.int64) ** 2
+        off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        total = int(sizes.sum())
+        H0 = np.zeros(total, np.complex128)
+        mu = np.zeros((3, total), np.complex128)
+        rho = np.zeros(total, np.complex128)
+        for new, old in enumerate(idx):
+            s = int(sizes[new])
+            o, oo = int(off[new]), int(self.off[old])
+            H0[o:o + s] = self.H0[oo:oo + s]
+            mu[:, o:o + s] = self.mu[:, oo:oo + s]
+            rho[o:o + s] = self.rho0[oo:oo + s]
+        return Molecules(nl.copy(), off, self.pos[idx].copy(), self.sigma[idx].copy(),
+                         self.gamma[idx].copy(), self.decay[idx].copy(),
+                         self.dephase[idx].copy(), self.kind[idx].copy(),
+                         self.nsub[idx].copy(), H0, mu, rho)
+
+
+def empty_molecules() -> Molecules:
+    z = np.zeros(0)
+    return Molecules(np.zeros(0, np.int32), np.zeros(0, np.int64), np.zeros((0, 3)), z.copy(),
+                     z.copy(), z.copy(), z.copy(), np.zeros(0, np.int32), np.zeros(0, np.int32),
+                     np.zeros(0, np.complex128), np.zeros((3, 0), np.complex128),
+                     np.zeros(0, np.complex128))
+
+
+def pack_molecules(mats: List[dict]) -> Molecules:
+    """Pack a list of per-molecule dicts with keys n, pos, sigma, gamma, H0 (n x n),
+    mu (3, n, n), rho (n x n) and optional decay, dephase, kind, nsub."""
+    M = len(mats)
+    nlev = np.array([d["n"] for d in mats], np.int32)
+    sizes = nlev.astype(np.int64) ** 2
+    off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64) if M else np.zeros(0, np.int64)
+    total = int(sizes.sum())
+    H0 = np.zeros(total, np.complex128)
+    mu = np.zeros((3, total), np.complex128)
+    rho = np.zeros(total, np.complex128)
+    for m, d in enumerate(mats):
+        o, s = int(off[m]), int(sizes[m])
+        H0[o:o + s] = np.asarray(d["H0"], np.complex128).ravel()
+        mu[:, o:o + s] = np.asarray(d["mu"], np.complex128).reshape(3, s)
+        rho[o:o + s] = np.asarray(d["rho"], np.complex128).ravel()
+    decay = np.array([d.get("decay", 0.0) for d in mats], np.float64)
+    deph = np.array([d.get("dephase", 0.0) for d in mats], np.float64)
+    kind = np.array([d.get("kind", KIND_EXACT2 if (d["n"] == 2 and d.get("decay", 0.0) == 0.0
+                                                   and d.get("dephase", 0.0) == 0.0) else KIND_RK4)
+                     for d in mats], np.int32)
+    nsub = np.array([d.get("nsub", 1) for d in mats], np.int32)
+    pos = np.array([d["pos"] for d in mats], np.float64).reshape(M, 3)
+    sigma = np.array([d["sigma"] for d in mats], np.float64)
+    gamma = np.array([d.get("gamma", 1.0) for d in mats], np.float64)
+    return Molecules(nlev, off, pos, sigma, gamma, decay, deph, kind, nsub, H0, mu, rho)
+
+
+def tls(pos, omega0, mu12, axis=2, sigma=1.5, gamma=1.0, cg=1.0, ce=0.0, dephase=0.0,
+        decay=0.0, kind=None, nsub=1) -> dict:
+    """Two-level emitter: H0 = diag(0, omega0), mu = mu12 * e_axis * sigma_x (Eq. von-Neumann-tls)."""
+    H0 = np.diag([0.0, omega0]).astype(np.complex128)
+    mu = np.zeros((3, 2, 2), np.complex128)
+    mu[axis] = mu12 * np.array([[0, 1], [1, 0]])
+    c = np.array([cg, ce], np.complex128)
+    rho = np.outer(c, c.conj())
+    d = dict(n=2, pos=pos, sigma=sigma, gamma=gamma, H0=H0, mu=mu, rho=rho,
+             dephase=dephase, decay=decay, nsub=nsub)
+    if kind is not None:
+        d["kind"] = kind
+    return d
+
+
+@dataclass
+class Problem:
+    nx: int
+    ny: int
+    nz: int
+    courant: float = 0.5
+    periodic: Tuple[bool, bool, bool] = (False, False, False)
+    pml: Tuple[int, int, int, int, int, int] = (0, 0, 0, 0, 0, 0)
+    pml_m: float = 3.0
+    pml_sigma_max: float = 3.2        # 0.8 (m+1) / (eta dx) with eta = dx = 1
+    pml_kappa_max: float = 1.0
+    pml_alpha_max: float = 0.05
+    mat: Optional[np.ndarray] = None  # uint8 (nz, ny, nx) material index
+    materials: List[Material] = field(default_factory=lambda: [Material()])
+    design_box: Optional[Tuple[int, int, int, int, int, int]] = None  # x0,y0,z0,sx,sy,sz
+    design_eps: Optional[np.ndarray] = None  # float64 (sz, sy, sx) relative permittivity
+    sources: List[Source] = field(default_factory=list)
+    molecules: Molecules = field(default_factory=empty_molecules)
+    planes: List[FluxPlane] = field(default_factory=list)
+    name: str = "custom"
+
+    @property
+    def dt(self) -> float:
+        return float(self.courant)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+# ----------------------------------------------------------------------------------
+# Workloads shaped like the paper's examples.
+# ----------------------------------------------------------------------------------
+
+def plain_single_emitter(dtype_note: str = "") -> Problem:
+    """40^3 cells, Courant 0.5, vacuum, 8-cell CPML on all faces, one two-level
+    emitter at the grid centre (omega0 = 0.25, mu12 = 0.1 along z, sigma = 2 cells),
+    initial amplitudes (sqrt(0.9), sqrt(0.1)), no Lindblad terms."""
+    n = 40
+    mol = pack_molecules([tls((n / 2, n / 2, n / 2), 0.25, 0.1, axis=2, sigma=2.0,
+                              cg=np.sqrt(0.9), ce=np.sqrt(0.1))])
+    return Problem(n, n, n, 0.5, pml=(8,) * 6, molecules=mol, name="plain-40^3-1tls")
+
+
+def superradiant_slab(n: int = 256, nmol: int = 10000, slab: int = 32, pml: int = 10,
+                      nfreq: int = 8, seed: int = 2) -> Problem:
+    """Vacuum cube with `nmol` two-level emitters (omega0 = 0.25, mu12 = 0.02 along z,
+    sigma = 1.5 cells) at seeded uniform positions in a `slab`-cell-thick central slab,
+    all excited with a seeded random coherence of 1e-3 and pure dephasing 1e-5; flux
+    planes on both sides at `nfreq` frequencies in [0.20, 0.30].  Stand-in for the
+    superradiance example of Sec. IV.A at 3D scale."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = pml + 2, n - pml - 2
+    zc = n // 2
+    xs = rng.uniform(lo, hi, size=nmol)
+    ys = rng.uniform(lo, hi, size=nmol)
+    zs = rng.uniform(zc - slab // 2, zc + slab // 2, size=nmol)
+    phi = rng.uniform(0.0, 2 * np.pi, size=nmol)
+    mats = []
+    for m in range(nmol):
+        cg = 1e-3 * np.exp(1j * phi[m])
+        ce = np.sqrt(1.0 - 1e-6)
+        mats.append(tls((xs[m], ys[m], zs[m]), 0.25, 0.02, axis=2, sigma=1.5,
+                        cg=cg, ce=ce, dephase=1e-5))
+    om = np.linspace(0.20, 0.30, nfreq)
+    planes = [FluxPlane(2, pml + 4, om.copy()), FluxPlane(2, n - pml - 4, om.copy())]
+    return Problem(n, n, n, 0.5, pml=(pml,) * 6, molecules=pack_molecules(mats),
+                   planes=planes, name=f"superradiant-slab-{n}^3-{nmol}tls")
+
+
+def random_hermitian(rng, n, std):
+    a = rng.normal(0, std, (n, n)) + 1j * rng.normal(0, std, (n, n))
+    return (a + a.conj().T) / 2
+
+
+def bragg_ensemble(nx=512, ny=512, nz=384, nmol=100000, pml=10, slab=32, seed=3,
+                   layers=12, nfreq=8) -> Problem:
+    """Bragg-mirror stack along z (alternating eps 2.25 / 1.0 quarter-wave layers at
+    omega = 0.25, 4 and 6 cells) split around a central slab holding `nmol` multilevel
+    systems with level count uniform in 2..8, Hermitian z-dipoles with N(0, 0.01)
+    entries, harmonic ladders with spacing 0.2 +- 5 % and log-uniform decay rates in
+    [1e-6, 1e-4]; z-polarised Gaussian pulse sheet source.  Stand-in for the Bragg
+    resonator of Sec. IV.C."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mat = np.zeros((nz, ny, nx), np.uint8)
+    zc = nz // 2
+    half = layers // 2
+    # stack above and below the slab: (4 cells eps 2.25, 6 cells eps 1) x half
+    z = zc + slab // 2
+    for _ in range(half):
+        mat[z:z + 4] = 1
+        z += 10
+    z = zc - slab // 2
+    for _ in range(half):
+        mat[z - 4:z] = 1
+        z -= 10
+    mats = []
+    nl = rng.integers(2, 9, size=nmol)
+    px = rng.uniform(pml + 2, nx - pml - 2, size=nmol)
+    py = rng.uniform(pml + 2, ny - pml - 2, size=nmol)
+    pz = rng.uniform(zc - slab // 2, zc + slab // 2, size=nmol)
+    rates = np.exp(rng.uniform(np.log(1e-6), np.log(1e-4), size=nmol))
+    for m in range(nmol):
+        n = int(nl[m])
+        steps = 0.2 * (1 + rng.uniform(-0.05, 0.05, size=n - 1))
+        E = np.concatenate([[0.0], np.cumsum(steps)])
+        mu = np.zeros((3, n, n), np.complex128)
+        mu[2] = random_hermitian(rng, n, 0.01)
+        rho = np.zeros((n, n), np.complex128)
+        rho[0, 0] = 1.0
+        mats.append(dict(n=n, pos=(px[m], py[m], pz[m]), sigma=1.5, gamma=1.0,
+                         H0=np.diag(E).astype(np.complex128), mu=mu, rho=rho,
+                         decay=float(rates[m]), kind=KIND_RK4, nsub=1))
+    src = [Source(axis=2, index=pml + 2, comp=0, amp=1.0, omega=0.25, width=20.0, t0=100.0)]
+    om = np.linspace(0.20, 0.30, nfreq)
+    planes = [FluxPlane(2, pml + 6, om.copy()), FluxPlane(2, nz - pml - 4, om.copy())]
+    return Problem(nx, ny, nz, 0.5, periodic=(False, False, False), pml=(pml,) * 6, mat=mat,
+                   materials=[Material(1.0), Material(2.25)], sources=src,
+                   molecules=pack_molecules(mats), planes=planes,
+                   name=f"bragg-{nx}x{ny}x{nz}-{nmol}ml")
+
+
+def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4,
+                  multilevel: bool = True, eps_map: bool = True, drude: bool = False,
+                  source: bool = True, planes: bool = True, periodic=(False, False, False)) -> Problem:
+    """Small ragged problem for parity tests: every feature at once on a grid the
+    oracle finishes in well under a second per hundred steps."""
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    nx, ny, nz = shape
+    pmls = tuple(0 if periodic[a // 2] else pml for a in range(6))
+    mat = None
+    materials = [Material(1.0)]
+    design_box = None
+    design_eps = None
+    if eps_map:
+        mat = np.zeros((nz, ny, nx), np.uint8)
+        materials.append(Material(2.25))
+        mat[nz // 2 + 3:nz // 2 + 6] = 1
+        sx, sy, sz = max(2, nx // 4), max(2, ny // 4), max(2, nz // 5)
+        design_box = (nx // 2 - sx // 2, ny // 2 - sy // 2, 2 + pml, sx, sy, sz)
+        design_eps = 1.0 + rng.uniform(0, 1.5, size=(sz, sy, sx))
+    if drude:
+        if mat is None:
+            mat = np.zeros((nz, ny, nx), np.uint8)
+        materials.append(Material(1.0, wp=1.0, gamma=0.05))
+        zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        r = min(nx, ny, nz) / 6
+        inside = (xx + 0.5 - nx / 2) ** 2 + (yy + 0.5 - ny / 2) ** 2 + (zz + 0.5 - nz / 2) ** 2 < r * r
+        mat[inside] = len(materials) - 1
+    mats = []
+    for m in range(nmol):
+        sigma = float(rng.choice([1.0, 1.5]))
+        R = int(np.ceil(3 * sigma))
+        p = []
+        for a, n in enumerate(shape):
+            if periodic[a]:
+                p.append(rng.uniform(0, n))
+            else:
+                p.append(rng.uniform(R + 1, n - R - 2))
+        if multilevel and m % 2 == 1:
+            n = int(rng.integers(3, 9))
+            steps = 0.2 * (1 + rng.uniform(-0.05, 0.05, size=n - 1))
+            E = np.concatenate([[0.0], np.cumsum(steps)])
+            mu = np.stack([random_hermitian(rng, n, 0.3) for _ in range(3)])
+            c = rng.normal(size=n) + 1j * rng.normal(size=n)
+            c /= np.linalg.norm(c)
+            mats.append(dict(n=n, pos=tuple(p), sigma=sigma, gamma=float(rng.uniform(0.5, 1.5)),
+                             H0=np.diag(E).astype(np.complex128), mu=mu,
+                             rho=np.outer(c, c.conj()), decay=float(rng.uniform(0, 1e-2)),
+                             dephase=float(rng.uniform(0, 1e-2)), kind=KIND_RK4,
+                             nsub=int(rng.integers(1, 3))))
+        else:
+            ce = np.sqrt(rng.uniform(0.05, 0.95))
+            cg = np.sqrt(1 - ce ** 2) * np.exp(1j * rng.uniform(0, 2 * np.pi))
+            mats.append(tls(tuple(p), 0.25, float(rng.uniform(0.2, 1.0)), axis=int(rng.integers(0, 3)),
+                            sigma=sigma, gamma=float(rng.uniform(0.5, 1.5)), cg=cg, ce=ce))
+    srcs = []
+    if source:
+        srcs.append(Source(axis=2, index=pmls[4] + 2 if not periodic[2] else 1, comp=0, amp=0.5,
+                           omega=0.3, width=6.0, t0=18.0))
+    pl = []
+    if planes:
+        om = np.linspace(0.2, 0.35, 3)
+        pl.append(FluxPlane(2, nz - pmls[5] - 2, om.copy()))
+        pl.append(FluxPlane(0, pmls[0] + 2, om.copy()))
+        pl.append(FluxPlane(1, ny // 2, om.copy()))
+    return Problem(nx, ny, nz, 0.5, periodic=tuple(periodic), pml=pmls, mat=mat,
+                   materials=materials, design_box=design_box, design_eps=design_eps,
+                   sources=srcs, molecules=pack_molecules(mats) if mats else empty_molecules(),
+                   planes=pl, name=f"small-{nx}x{ny}x{nz}-s{seed}")
+
+
+def random_fields(prob: Problem, seed: int, scale: float = 1.0):
+    """Seeded random initial E and H (6 arrays of shape (nz, ny, nx), float64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [scale * rng.standard_normal((prob.nz, prob.ny, prob.nx)) for _ in range(6)]

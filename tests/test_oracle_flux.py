@@ -1,0 +1,93 @@
+"""Pins of the oracle's DFT flux planes and Drude medium.
+
+  * DFT accumulators of a travelling Yee eigenmode equal the closed-form sums of the
+    analytic field (E sampled at t = (n+1) dt, H at (n+1/2) dt, weight dt), and the
+    flux assembled from them equals the closed form and is positive along +k.
+  * A current sheet in a box periodic in x, y: equal flux through two planes on the
+    same side, equal and opposite flux on the two sides.
+  * Drude ADE: a spatially uniform field in a Drude medium oscillates as the damped
+    plasma oscillation E(t) = E0 e^{-g t/2}(cos w't + g/(2w') sin w't), w'^2 = wp^2/eps - g^2/4.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_06173_gb300.workloads import FluxPlane, Material, Problem, Source
+
+from test_oracle_yee import eigenmode
+
+
+def test_dft_accumulators_of_eigenmode(oracle_mod):
+    shape = (16, 6, 5)  # nz, ny, nx
+    dt = 0.5
+    om = np.array([0.31, 0.5, 0.77])
+    prob = Problem(5, 6, 16, dt, periodic=(True, True, True), planes=[FluxPlane(2, 7, om)])
+    sim = oracle_mod.OracleSim(prob)
+    e_dir = np.array([0.0, 1.0, 0.0])
+    f0, w = eigenmode(shape, (0, 0, 1), dt, 0.0, e_dir)
+    sim.set_fields(f0)
+    N = 137
+    sim.step(N)
+    E1, E2, H1, H2 = sim.plane_data(0)
+    wantE = [np.zeros((3, 6, 5), complex) for _ in range(2)]
+    wantH = [np.zeros((3, 6, 5), complex) for _ in range(2)]
+    for n in range(N):
+        fe, _ = eigenmode(shape, (0, 0, 1), dt, (n + 1) * dt, e_dir)
+        # fields at t_E=(n+1)dt; H returned at t_E - dt/2 = (n+1/2) dt
+        for fi in range(3):
+            pe = np.exp(1j * om[fi] * (n + 1) * dt) * dt
+            ph = np.exp(1j * om[fi] * (n + 0.5) * dt) * dt
+            wantE[0][fi] += pe * fe[0][7]
+            wantE[1][fi] += pe * fe[1][7]
+            wantH[0][fi] += ph * 0.5 * (fe[3][7] + fe[3][6])
+            wantH[1][fi] += ph * 0.5 * (fe[4][7] + fe[4][6])
+    for got, want in zip([E1, E2, H1, H2], wantE + wantH):
+        assert np.abs(got - want).max() < 1e-11
+    flux = sim.flux(0)
+    want_flux = np.array([np.real(wantE[0][f] * np.conj(wantH[1][f]) - wantE[1][f] * np.conj(wantH[0][f])).sum()
+                          for f in range(3)])
+    assert np.allclose(flux, want_flux, rtol=1e-11, atol=1e-12)
+    # a +z wave carries positive flux at its own frequency
+    p2 = Problem(5, 6, 16, dt, periodic=(True, True, True), planes=[FluxPlane(2, 7, np.array([w]))])
+    s2 = oracle_mod.OracleSim(p2)
+    s2.set_fields(f0)
+    s2.step(400)
+    assert s2.flux(0)[0] > 0
+
+
+def test_sheet_source_flux_balance(oracle_mod):
+    om = np.array([0.2, 0.3, 0.4])
+    nz = 96
+    planes = [FluxPlane(2, 60, om), FluxPlane(2, 75, om), FluxPlane(2, 30, om)]
+    prob = Problem(4, 4, nz, 0.5, periodic=(True, True, False), pml=(0, 0, 0, 0, 12, 12),
+                   sources=[Source(2, 48, 0, 1.0, 0.3, 6.0, 30.0)], planes=planes)
+    sim = oracle_mod.OracleSim(prob)
+    sim.step(900)
+    f1, f2, f3 = sim.flux(0), sim.flux(1), sim.flux(2)
+    assert np.all(f1 > 0) and np.all(f3 < 0)
+    assert np.allclose(f1, f2, rtol=2e-3)
+    assert np.allclose(f1, -f3, rtol=2e-3)
+
+
+def test_drude_plasma_oscillation(oracle_mod):
+    wp, g, einf, dt = 1.0, 0.05, 1.0, 0.002
+    prob = Problem(3, 3, 3, dt, periodic=(True, True, True), mat=np.zeros((3, 3, 3), np.uint8),
+                   materials=[Material(einf, wp, g)])
+    sim = oracle_mod.OracleSim(prob)
+    E0 = 0.7
+    sim.set_fields([np.full((3, 3, 3), E0), np.zeros((3, 3, 3)), np.zeros((3, 3, 3))] +
+                   [np.zeros((3, 3, 3))] * 3)
+    ws = np.sqrt(wp ** 2 / einf - g ** 2 / 4)
+    maxerr = 0.0
+    for n in range(1, 15001):
+        sim.step(1)
+        t = n * dt
+        want = E0 * np.exp(-g * t / 2) * (np.cos(ws * t) + g / (2 * ws) * np.sin(ws * t))
+        maxerr = max(maxerr, abs(sim.fields()[0][1, 1, 1] - want))
+    # the half-step Drude current starts at 0 instead of J(-dt/2): O(wp dt / 2) amplitude
+    # error; the frequency error is O((wp dt)^2)
+    assert maxerr < 2e-3 * E0
+    # energy bookkeeping: the accumulated work sum J_D . (E^n + E^{n+1})/2 dt on the
+    # Drude current plus the field energy stays at the initial field energy
+    Ef = sim.fields()[0]
+    tot = 0.5 * einf * (Ef ** 2).sum() + sim.absorbed()
+    assert abs(tot - 0.5 * einf * E0 ** 2 * 27) < 2e-3 * 0.5 * E0 ** 2 * 27

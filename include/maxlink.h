@@ -1,0 +1,193 @@
+/*
+ * maxlink.h - C ABI of the GB300-native coupled Yee FDTD / molecular-ensemble step.
+ *
+ * Method: arXiv 2512.06173 (MaxwellLink), Sec. II.A.1 and II.B.1.  One time step
+ * advances a 3D Yee grid (Eq. Maxwell with the constitutive relation Eq. Dromega)
+ * with CPML absorbing layers, lets every molecule gather its regularised field
+ * (Eq. E_regu_Emi), advance its density matrix (Eq. von-Neumann-tls, optional
+ * Lindblad terms) and scatter its current gamma * d<mu>/dt * kappa (Eq. J_mol,
+ * Eq. Polarization_mol) into the E update.  All of the step runs in CUDA kernels
+ * for sm_103a; there is no CPU fallback.
+ *
+ * Conventions (all entry points):
+ *   - Units c = eps0 = mu0 = hbar = 1, cell edge 1 (Appendix A), dt = Courant number.
+ *   - Staggering: Ex(i,j,k) at (i+1/2,j,k), Ey at (i,j+1/2,k), Ez at (i,j,k+1/2),
+ *     Hx at (i,j+1/2,k+1/2), Hy at (i+1/2,j,k+1/2), Hz at (i+1/2,j+1/2,k);
+ *     E lives at integer steps, H at half steps.
+ *   - Host arrays over the grid are (nz, ny, nx) row-major, x fastest.
+ *   - Non-periodic axes end in PEC walls at index 0 and n (behind the CPML, if any).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that only enqueue work return before it finishes; device-side
+ *     failures are latched in a status word read by ml_sync_status.
+ *   - Every call returns an ml_status; ml_last_error() gives a message for the
+ *     last failure on the calling thread.  No exception crosses the ABI.
+ *   - The library copies every input; the caller keeps ownership of its buffers.
+ *     Device memory of a grid is owned by the library until ml_grid_destroy.
+ */
+#ifndef MAXLINK_H
+#define MAXLINK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ML_OK = 0,
+    ML_ERR_INVALID_ARG = 1, /* bad size, index, pointer or combination of options */
+    ML_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    ML_ERR_OOM = 3,         /* device allocation failed */
+    ML_ERR_STATE = 4,       /* call not valid in the object's current state */
+    ML_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    ML_ERR_NUMERIC = 6      /* a NaN or Inf reached a molecule's field or current */
+} ml_status;
+
+typedef enum { ML_F32 = 0, ML_F64 = 1 } ml_precision;
+
+typedef struct ml_grid ml_grid;
+
+/* Material of a cell: eps_inf plus an optional Drude term (Sec. II.A.1 mentions
+ * Drude/Lorentz dielectric functions): dJ/dt + gamma J = wp^2 E.  wp = 0: none. */
+typedef struct {
+    double eps_inf, wp, gamma;
+} ml_material;
+
+/* Soft current-sheet source on the plane `index` normal to `axis`, polarised along
+ * `comp` (comp != axis): J_comp(t) = amp exp(-((t-t0)/width)^2/2) cos(omega (t-t0)),
+ * evaluated at t = (n+1/2) dt (the Gaussian-pulse plane wave of Appendix B). */
+typedef struct {
+    int axis, index, comp;
+    double amp, omega, width, t0;
+} ml_source;
+
+#define ML_MAX_SOURCES 4
+#define ML_MAX_MATERIALS 64
+#define ML_MAX_LEVELS 8
+#define ML_MAX_FREQS 64
+
+typedef struct {
+    int nx, ny, nz;             /* cells, each >= 1 */
+    double courant;             /* dt; stable for courant <= 1/sqrt(3) in 3D */
+    int precision;              /* ML_F32 or ML_F64: field and molecule arithmetic */
+    int periodic[3];            /* 1 = periodic axis (no CPML allowed on it) */
+    int pml[6];                 /* CPML cells on faces x-,x+,y-,y+,z-,z+ */
+    double pml_m;               /* grading exponent (3) */
+    double pml_sigma_max;       /* sigma at the outer wall (0.8 (m+1) = 3.2) */
+    double pml_kappa_max;       /* kappa at the outer wall (>= 1) */
+    double pml_alpha_max;       /* alpha at the inner edge, decreasing linearly (0.05) */
+    const uint8_t *mat;         /* host (nz,ny,nx) material index, or NULL = material 0 */
+    int n_materials;            /* 1..ML_MAX_MATERIALS */
+    const ml_material *materials;
+    int design_box[6];          /* x0,y0,z0,sx,sy,sz of a continuous-eps region (sx=0: none) */
+    const double *design_eps;   /* host (sz,sy,sx) relative permittivity, no Drude inside */
+    int n_sources;              /* 0..ML_MAX_SOURCES */
+    const ml_source *sources;
+} ml_grid_desc;
+
+/* Molecule table (Sec. II.B.1).  Matrices are n x n row-major complex numbers
+ * stored as interleaved (re, im) doubles in shared pools; molecule m's matrices
+ * start at complex element off[m].  H0 and the three dipole operators must be
+ * Hermitian; rho a density matrix. */
+typedef struct {
+    int count;
+    const int32_t *nlev;        /* 2..ML_MAX_LEVELS */
+    const int64_t *off;         /* offset into the pools, complex elements */
+    const double *pos;          /* (count,3) centre in grid units */
+    const double *sigma;        /* Gaussian width in cells; ceil(3 sigma) <= 7 */
+    const double *gamma;        /* coupling rescale of Eq. Polarization_mol */
+    const double *decay;        /* ladder decay rate: L_k = sqrt(decay)|k-1><k| */
+    const double *dephase;      /* pure dephasing:    L_k = sqrt(dephase)|k><k|  */
+    const int32_t *kind;        /* 0: exact 2x2 unitary (n=2, no Lindblad); 1: RK4 */
+    const int32_t *nsub;        /* RK4 substeps per field step (>= 1) */
+    const double *H0;           /* pool, interleaved complex */
+    const double *mu;           /* 3 pools back to back (x, y, z), each `pool` complex */
+    const double *rho;          /* pool, initial density matrices */
+    int64_t pool;               /* complex elements in each pool */
+} ml_molecule_desc;
+
+/* what to read with ml_get_molecules (all as double) */
+enum {
+    ML_MOL_RHO = 0,     /* pool of interleaved complex rho (2*pool doubles) */
+    ML_MOL_EFIELD = 1,  /* (count,3) regularised field of the last step (Eq. E_regu_Em) */
+    ML_MOL_MUDOT = 2,   /* (count,3) d<mu>/dt of the last step (Eq. dipole_derivative) */
+    ML_MOL_ENERGY = 3,  /* (count) sum over steps of Tr(rho H0) (time average = / steps) */
+    ML_MOL_POP = 4      /* (count, ML_MAX_LEVELS) diagonal of rho, zero-padded */
+};
+
+/* component mask bits for ml_get_fields / ml_set_fields (order of the copies) */
+enum { ML_EX = 1, ML_EY = 2, ML_EZ = 4, ML_HX = 8, ML_HY = 16, ML_HZ = 32, ML_ALL = 63 };
+
+/* Message of the last failure on this thread ("" if none).  Never NULL. */
+const char *ml_last_error(void);
+
+/* Version string of the library build. */
+const char *ml_version(void);
+
+/* Create a grid (Eq. Maxwell on a Yee lattice, Eq. Dromega per cell), zero fields.
+ * Copies the descriptor's arrays.  *out receives the handle. */
+ml_status ml_grid_create(const ml_grid_desc *desc, void *stream, ml_grid **out);
+
+/* Free all device memory of the grid.  Synchronises the device. */
+ml_status ml_grid_destroy(ml_grid *g);
+
+/* Append molecules (Eq. Polarization_mol: centre, Gaussian width, coupling, and the
+ * Sec. II.B.1 model: H0, dipole operators, Lindblad rates, initial rho).  Their
+ * kernel windows must lie inside the grid on non-periodic axes.  Builds the kernel
+ * weights and the cell-binned molecule lists.  *first_id (may be NULL) receives the
+ * index of the first appended molecule. */
+ml_status ml_add_molecules(ml_grid *g, const ml_molecule_desc *m, void *stream, int *first_id);
+
+/* Add a DFT flux plane: E-plane `index` normal to `axis`, nfreq frequencies.  The
+ * accumulators integrate E(t=(n+1)dt) and H(t=(n+1/2)dt) with weight e^{i w t} dt
+ * from the next step on.  *id receives the plane index. */
+ml_status ml_add_flux_plane(ml_grid *g, int axis, int index, int nfreq, const double *omega, int *id);
+
+/* Enqueue nsteps coupled time steps on `stream`. */
+ml_status ml_step(ml_grid *g, int64_t nsteps, void *stream);
+
+/* Copy the selected components (mask of ML_EX..ML_HZ, in that order) to dst:
+ * each nz*ny*nx elements of the grid's precision.  dst is device memory if
+ * dst_on_device, else host memory (the call then synchronises `stream`). */
+ml_status ml_get_fields(ml_grid *g, unsigned mask, void *dst, int dst_on_device, void *stream);
+
+/* Overwrite the selected components from src (same layout as ml_get_fields).
+ * Tangential E on PEC walls is kept at zero by every later step. */
+ml_status ml_set_fields(ml_grid *g, unsigned mask, const void *src, int src_on_device, void *stream);
+
+/* Read molecular state `what` (ML_MOL_*) as doubles into dst (device or host). */
+ml_status ml_get_molecules(ml_grid *g, int what, double *dst, int dst_on_device, void *stream);
+
+/* Net flux through plane `id` per frequency: Re sum over the plane of
+ * (E~ x H~*) . n (Sec. IV.C, IV.D spectra), H~ averaged over the two half cells
+ * around the plane.  out: host, nfreq doubles.  Synchronises `stream`. */
+ml_status ml_flux(ml_grid *g, int id, double *out, void *stream);
+
+/* Raw DFT accumulators of plane `id` (E_b, E_c, H_b, H_c with (a,b,c) cyclic, each
+ * (nfreq, n_c, n_b) complex) as interleaved doubles into host `out`. */
+ml_status ml_flux_data(ml_grid *g, int id, double *out, void *stream);
+
+/* Energy absorbed by Drude cells so far: sum J_D . (E^n + E^{n+1})/2 dt.  Host out. */
+ml_status ml_absorbed(ml_grid *g, double *out, void *stream);
+
+/* Synchronise `stream` and return the latched device status (then clear it). */
+ml_status ml_sync_status(ml_grid *g, void *stream);
+
+/* Steps taken so far. */
+int64_t ml_step_count(const ml_grid *g);
+
+/* Number of molecules. */
+int ml_molecule_count(const ml_grid *g);
+
+/* Checkpoint the full state (fields, CPML memory, Drude currents, molecules, DFT
+ * accumulators, step count) into host_buf.  With host_buf == NULL only *bytes is
+ * set to the size needed.  ml_restore takes a buffer written by ml_checkpoint of a
+ * grid created with the same descriptor, molecules and planes. */
+ml_status ml_checkpoint(ml_grid *g, void *host_buf, size_t *bytes, void *stream);
+ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAXLINK_H */

@@ -1,0 +1,890 @@
+// Host side of libmaxlink: the C ABI of include/maxlink.h.
+//
+// Owns the device state of a grid, validates arguments, lays out the padded
+// fields, builds the CPML and material coefficient tables, bins molecules into
+// per-tile lists, and enqueues the per-step kernels:
+//   K2 molecules (gather E^n, rho step, mudot)  ->  K1 fused field pass (H, E)
+//   ->  K4 plane sampling (every step) / fold (every DFT_KMAX steps).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "maxlink.h"
+#include "ml_internal.cuh"
+
+using namespace ml;
+
+namespace {
+
+thread_local std::string g_err;
+
+ml_status fail(ml_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ML_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+struct Plane {
+    int axis, index, nfreq, nb, nc;
+    std::vector<double> omega;
+    double *d_omega = nullptr;
+    void *d_buf = nullptr;
+    double2 *d_acc = nullptr;
+};
+
+}  // namespace
+
+struct ml_grid {
+    int prec = 0;
+    size_t esz = 4;
+    int nx = 0, ny = 0, nz = 0;
+    double dt = 0.5;
+    int per[3] = {0, 0, 0};
+    int pml[6] = {0, 0, 0, 0, 0, 0};
+    double pml_m = 3, smax = 3.2, kmax = 1, amax = 0.05;
+    int ntx = 0, nty = 0, nchunk = 0, cz = 0, nblocks = 0;
+    int px = 0, py = 0;
+    long long plane = 0;
+    size_t vol = 0;  // padded elements per array
+    void *F[2][6] = {};
+    int cur = 0;
+    void *cpml[3] = {};
+    void *psiH[2][3][2] = {};
+    void *psiE[3][2] = {};
+    size_t psi_n[3] = {0, 0, 0};
+    uint8_t *mat = nullptr;
+    void *mat_cb = nullptr, *mat_dk = nullptr, *mat_db = nullptr;
+    int dbox[6] = {0, 0, 0, 0, 0, 0};
+    void *dcb = nullptr;
+    int jbox[6] = {0, 0, 0, 0, 0, 0};
+    void *JD[3] = {};
+    double *absorbed_part = nullptr;
+    double *d_scalar = nullptr;
+    std::vector<SrcDev> src;
+    // molecules: host mirror of the static description
+    int nmol = 0;
+    long long pool = 0;
+    std::vector<int> nlev, kind, nsub, cmask, win, wf, wraw;
+    std::vector<long long> off;
+    std::vector<double> pos, sigma, gamma, decay, deph, H0, mu, rho0;
+    // molecules: device
+    int *d_nlev = nullptr, *d_kind = nullptr, *d_nsub = nullptr, *d_cmask = nullptr, *d_win = nullptr,
+        *d_wf = nullptr, *d_wraw = nullptr;
+    long long *d_off = nullptr;
+    double *d_pos = nullptr, *d_sigma = nullptr, *d_energy = nullptr, *d_export = nullptr;
+    void *d_gamma = nullptr, *d_decay = nullptr, *d_deph = nullptr, *d_H0 = nullptr, *d_mu = nullptr,
+         *d_rho = nullptr, *d_w = nullptr, *d_Et = nullptr, *d_mudot = nullptr, *d_c = nullptr;
+    int *d_tile_off = nullptr;
+    int4 *d_tile_ent = nullptr;
+    long long n_ent = 0;
+    std::vector<Plane> planes;
+    int nsamp = 0;
+    long long samp_step0 = 0;
+    void *scratch = nullptr;
+    int *d_status = nullptr;
+    long long step = 0;
+    std::vector<void *> allocs;       // grid lifetime
+    std::vector<void *> mol_allocs;   // rebuilt when molecules are added
+};
+
+namespace {
+
+ml_status dalloc(std::vector<void *> &list, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return ML_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(ML_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    e = cudaMemset(*p, 0, bytes);
+    if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    list.push_back(*p);
+    return ML_OK;
+}
+
+#define AL(list, ptr, bytes)                                                \
+    do {                                                                    \
+        ml_status s_ = dalloc(list, (void **)&(ptr), (bytes));              \
+        if (s_ != ML_OK) return s_;                                         \
+    } while (0)
+
+template <typename T>
+ml_status upload_as(std::vector<void *> &list, void **dst, const std::vector<double> &v) {
+    std::vector<T> t(v.begin(), v.end());
+    AL(list, *dst, t.size() * sizeof(T));
+    if (!t.empty()) CK(cudaMemcpy(*dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ML_OK;
+}
+
+ml_status upload_reals(ml_grid *g, std::vector<void *> &list, void **dst, const std::vector<double> &v) {
+    return g->prec ? upload_as<double>(list, dst, v) : upload_as<float>(list, dst, v);
+}
+
+template <typename V>
+ml_status upload_raw(std::vector<void *> &list, V **dst, const std::vector<V> &v) {
+    AL(list, *dst, v.size() * sizeof(V));
+    if (!v.empty()) CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return ML_OK;
+}
+
+int dim(const ml_grid *g, int a) { return a == 0 ? g->nx : (a == 1 ? g->ny : g->nz); }
+
+// Roden-Gedney CPML coefficients (Taflove & Hagness Ch. 7) at position x along axis a.
+void cpml_coeff(const ml_grid *g, int a, double x, double &b, double &c, double &ik) {
+    int n = dim(g, a), dl = g->pml[2 * a], dh = g->pml[2 * a + 1];
+    double u = 0.0;
+    if (dl > 0 && x < dl) u = (dl - x) / dl;
+    else if (dh > 0 && x > n - dh) u = (x - (n - dh)) / dh;
+    if (u <= 0.0) { b = 0.0; c = 0.0; ik = 1.0; return; }
+    double sg = g->smax * std::pow(u, g->pml_m);
+    double kp = 1.0 + (g->kmax - 1.0) * std::pow(u, g->pml_m);
+    double al = g->amax * (1.0 - u);
+    b = std::exp(-(sg / kp + al) * g->dt);
+    c = sg > 0 ? sg / (sg * kp + kp * kp * al) * (b - 1.0) : 0.0;
+    ik = 1.0 / kp;
+}
+
+}  // namespace
+
+// Definitions below take C linkage from their declarations in maxlink.h.
+
+const char *ml_last_error(void) { return g_err.c_str(); }
+
+const char *ml_version(void) { return "maxlink-gb300 0.1 (sm_103a)"; }
+
+ml_status ml_grid_destroy(ml_grid *g) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    cudaDeviceSynchronize();
+    for (void *p : g->mol_allocs) cudaFree(p);
+    for (void *p : g->allocs) cudaFree(p);
+    delete g;
+    return ML_OK;
+}
+
+ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
+    (void)stream;
+    if (!d || !out) return fail(ML_ERR_INVALID_ARG, "null descriptor or output");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(ML_ERR_INVALID_ARG, "grid dimensions must be >= 1");
+    if ((long long)d->nx * d->ny * d->nz > (1ll << 34)) return fail(ML_ERR_INVALID_ARG, "grid too large");
+    if (!(d->courant > 0.0 && d->courant <= 1.0)) return fail(ML_ERR_INVALID_ARG, "courant must be in (0, 1]");
+    if (d->precision != ML_F32 && d->precision != ML_F64) return fail(ML_ERR_INVALID_ARG, "precision must be ML_F32 or ML_F64");
+    const int dims[3] = {d->nx, d->ny, d->nz};
+    for (int a = 0; a < 3; a++) {
+        if (d->periodic[a] && (d->pml[2 * a] || d->pml[2 * a + 1]))
+            return fail(ML_ERR_INVALID_ARG, "CPML on a periodic axis");
+        if (d->pml[2 * a] < 0 || d->pml[2 * a + 1] < 0 || d->pml[2 * a] + d->pml[2 * a + 1] > dims[a])
+            return fail(ML_ERR_INVALID_ARG, "CPML thickness out of range");
+    }
+    if (d->n_materials < 1 || d->n_materials > ML_MAX_MATERIALS || !d->materials)
+        return fail(ML_ERR_INVALID_ARG, "need 1..64 materials");
+    for (int q = 0; q < d->n_materials; q++)
+        if (!(d->materials[q].eps_inf > 0.0) || d->materials[q].wp < 0.0 || d->materials[q].gamma < 0.0)
+            return fail(ML_ERR_INVALID_ARG, "material needs eps_inf > 0, wp >= 0, gamma >= 0");
+    if (d->n_sources < 0 || d->n_sources > ML_MAX_SOURCES || (d->n_sources && !d->sources))
+        return fail(ML_ERR_INVALID_ARG, "0..4 sources");
+    for (int q = 0; q < d->n_sources; q++) {
+        const ml_source &s = d->sources[q];
+        if (s.axis < 0 || s.axis > 2 || s.comp < 0 || s.comp > 2 || s.comp == s.axis || s.index < 0 ||
+            s.index >= dims[s.axis] || !(s.width > 0))
+            return fail(ML_ERR_INVALID_ARG, "bad source");
+    }
+    const long long N = (long long)d->nx * d->ny * d->nz;
+    if (d->mat)
+        for (long long c = 0; c < N; c++)
+            if (d->mat[c] >= d->n_materials) return fail(ML_ERR_INVALID_ARG, "material index out of range");
+    if (d->design_box[3] > 0) {
+        for (int a = 0; a < 3; a++)
+            if (d->design_box[a] < 0 || d->design_box[3 + a] < 1 || d->design_box[a] + d->design_box[3 + a] > dims[a])
+                return fail(ML_ERR_INVALID_ARG, "design box outside the grid");
+        if (!d->design_eps) return fail(ML_ERR_INVALID_ARG, "design box without eps values");
+    }
+
+    ml_grid *g = new ml_grid();
+    auto bail = [&](ml_status s) {
+        for (void *p : g->allocs) cudaFree(p);
+        delete g;
+        return s;
+    };
+    g->prec = d->precision;
+    g->esz = g->prec ? 8 : 4;
+    g->nx = d->nx; g->ny = d->ny; g->nz = d->nz;
+    g->dt = d->courant;
+    for (int a = 0; a < 3; a++) g->per[a] = d->periodic[a] ? 1 : 0;
+    for (int f = 0; f < 6; f++) g->pml[f] = d->pml[f];
+    g->pml_m = d->pml_m; g->smax = d->pml_sigma_max; g->kmax = d->pml_kappa_max; g->amax = d->pml_alpha_max;
+    // tiling and padded layout
+    g->ntx = (g->nx + TX - 1) / TX;
+    g->nty = (g->ny + TY - 1) / TY;
+    int tiles = g->ntx * g->nty;
+    int target = 8 * 152;
+    int nch = std::max(1, std::min((target + tiles - 1) / tiles, (g->nz + 3) / 4));
+    g->cz = (g->nz + nch - 1) / nch;
+    g->nchunk = (g->nz + g->cz - 1) / g->cz;
+    g->nblocks = tiles * g->nchunk;
+    g->px = XO + g->ntx * TX + 4;
+    g->py = g->nty * TY + 2;
+    g->plane = (long long)g->px * g->py;
+    g->vol = (size_t)g->plane * (g->nz + 2);
+    ml_status st;
+#define GA(ptr, bytes)                                                  \
+    do {                                                                \
+        st = dalloc(g->allocs, (void **)&(ptr), (bytes));               \
+        if (st != ML_OK) return bail(st);                               \
+    } while (0)
+#define GC(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            fail(ML_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return bail(ML_ERR_CUDA);                                   \
+        }                                                               \
+    } while (0)
+    for (int l = 0; l < 2; l++)
+        for (int c = 0; c < 6; c++) GA(g->F[l][c], g->vol * g->esz);
+    GA(g->scratch, (size_t)N * 8);
+    // CPML tables and memory slabs
+    for (int a = 0; a < 3; a++) {
+        int n = dims[a];
+        std::vector<double> tab(6 * (size_t)n);
+        for (int i = 0; i < n; i++) {
+            cpml_coeff(g, a, (double)i, tab[i], tab[n + i], tab[2 * n + i]);
+            cpml_coeff(g, a, i + 0.5, tab[3 * n + i], tab[4 * n + i], tab[5 * n + i]);
+        }
+        st = upload_reals(g, g->allocs, &g->cpml[a], tab);
+        if (st != ML_OK) return bail(st);
+        int th = g->pml[2 * a] + g->pml[2 * a + 1];
+        if (th) {
+            size_t cnt = (size_t)N / n * th;
+            g->psi_n[a] = cnt;
+            for (int q = 0; q < 2; q++) {
+                GA(g->psiH[0][a][q], cnt * g->esz);
+                GA(g->psiH[1][a][q], cnt * g->esz);
+                GA(g->psiE[a][q], cnt * g->esz);
+            }
+        }
+    }
+    // materials
+    std::vector<double> cb(ML_MAX_MATERIALS, g->dt), dk(ML_MAX_MATERIALS, 0.0), db(ML_MAX_MATERIALS, 0.0);
+    bool any_drude = false;
+    for (int q = 0; q < d->n_materials; q++) {
+        const ml_material &m = d->materials[q];
+        cb[q] = g->dt / m.eps_inf;
+        if (m.wp > 0) {
+            double g2 = 0.5 * m.gamma * g->dt;
+            dk[q] = (1.0 - g2) / (1.0 + g2);
+            db[q] = m.wp * m.wp * g->dt / (1.0 + g2);
+            any_drude = true;
+        }
+    }
+    st = upload_reals(g, g->allocs, &g->mat_cb, cb);
+    if (st != ML_OK) return bail(st);
+    st = upload_reals(g, g->allocs, &g->mat_dk, dk);
+    if (st != ML_OK) return bail(st);
+    st = upload_reals(g, g->allocs, &g->mat_db, db);
+    if (st != ML_OK) return bail(st);
+    if (d->mat) {
+        GA(g->mat, (size_t)N);
+        GC(cudaMemcpy(g->mat, d->mat, (size_t)N, cudaMemcpyHostToDevice));
+    }
+    if (d->design_box[3] > 0) {
+        for (int q = 0; q < 6; q++) g->dbox[q] = d->design_box[q];
+        size_t cnt = (size_t)g->dbox[3] * g->dbox[4] * g->dbox[5];
+        std::vector<double> v(cnt);
+        for (size_t q = 0; q < cnt; q++) {
+            if (!(d->design_eps[q] > 0.0)) return bail(fail(ML_ERR_INVALID_ARG, "design eps must be > 0"));
+            v[q] = g->dt / d->design_eps[q];
+        }
+        st = upload_reals(g, g->allocs, &g->dcb, v);
+        if (st != ML_OK) return bail(st);
+    }
+    // Drude box: bounding box of cells whose material has a Drude term
+    int lo[3] = {g->nx, g->ny, g->nz}, hi[3] = {-1, -1, -1};
+    if (any_drude) {
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    int q = d->mat ? d->mat[((long long)k * g->ny + j) * g->nx + i] : 0;
+                    if (d->materials[q].wp > 0) {
+                        int idx[3] = {i, j, k};
+                        for (int a = 0; a < 3; a++) { lo[a] = std::min(lo[a], idx[a]); hi[a] = std::max(hi[a], idx[a]); }
+                    }
+                }
+    }
+    if (hi[0] >= 0) {
+        for (int a = 0; a < 3; a++) { g->jbox[a] = lo[a]; g->jbox[3 + a] = hi[a] - lo[a] + 1; }
+        size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
+        for (int c = 0; c < 3; c++) GA(g->JD[c], cnt * g->esz);
+    }
+    GA(g->absorbed_part, (size_t)g->nblocks * sizeof(double));
+    GA(g->d_scalar, 64 * sizeof(double));
+    GA(g->d_status, sizeof(int));
+    for (int q = 0; q < d->n_sources; q++) {
+        const ml_source &s = d->sources[q];
+        g->src.push_back(SrcDev{s.axis, s.index, s.comp, s.amp, s.omega, s.width, s.t0});
+    }
+    GC(cudaDeviceSynchronize());
+    *out = g;
+    return ML_OK;
+#undef GA
+#undef GC
+}
+
+// ------------------------------------------------------------------ molecules
+
+namespace {
+
+ml_status rebuild_molecules(ml_grid *g) {
+    for (void *p : g->mol_allocs) cudaFree(p);
+    g->mol_allocs.clear();
+    auto &L = g->mol_allocs;
+    const int M = g->nmol;
+    ml_status st;
+#define CKS(x)                     \
+    do {                           \
+        st = (x);                  \
+        if (st != ML_OK) return st; \
+    } while (0)
+    CKS(upload_raw(L, &g->d_nlev, g->nlev));
+    CKS(upload_raw(L, &g->d_kind, g->kind));
+    CKS(upload_raw(L, &g->d_nsub, g->nsub));
+    CKS(upload_raw(L, &g->d_cmask, g->cmask));
+    CKS(upload_raw(L, &g->d_win, g->win));
+    CKS(upload_raw(L, &g->d_wf, g->wf));
+    CKS(upload_raw(L, &g->d_wraw, g->wraw));
+    CKS(upload_raw(L, &g->d_off, g->off));
+    CKS(upload_raw(L, &g->d_pos, g->pos));
+    CKS(upload_raw(L, &g->d_sigma, g->sigma));
+    CKS(upload_reals(g, L, &g->d_gamma, g->gamma));
+    CKS(upload_reals(g, L, &g->d_decay, g->decay));
+    CKS(upload_reals(g, L, &g->d_deph, g->deph));
+    CKS(upload_reals(g, L, &g->d_H0, g->H0));
+    CKS(upload_reals(g, L, &g->d_mu, g->mu));
+    CKS(upload_reals(g, L, &g->d_rho, g->rho0));
+    AL(L, g->d_w, (size_t)M * NW * g->esz);
+    AL(L, g->d_Et, (size_t)M * 3 * g->esz);
+    AL(L, g->d_mudot, (size_t)M * 3 * g->esz);
+    AL(L, g->d_c, (size_t)M * 3 * g->esz);
+    AL(L, g->d_energy, (size_t)M * sizeof(double));
+    AL(L, g->d_export, std::max<size_t>((size_t)std::max<long long>(2 * g->pool, (long long)M * MAXLEV), 1) * sizeof(double));
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    cudaError_t e = g->prec ? launch_weights<double>(M, g->d_pos, g->d_sigma, g->d_win, g->d_wf, g->d_wraw, dims,
+                                                     g->per, (double *)g->d_w, 0)
+                            : launch_weights<float>(M, g->d_pos, g->d_sigma, g->d_win, g->d_wf, g->d_wraw, dims,
+                                                    g->per, (float *)g->d_w, 0);
+    if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("weights kernel: ") + cudaGetErrorString(e));
+    // tile-binned lists: entries (m, xs - x0, ys - y0, zs) for every (tile, chunk) that
+    // the (folded) window touches, sorted by (zs, m) inside each list
+    const int ntiles = g->nblocks;
+    std::vector<std::vector<int4>> lists(ntiles);
+    for (int m = 0; m < M; m++) {
+        std::vector<std::pair<int, int>> ax[3];  // (block coordinate, local start)
+        for (int a = 0; a < 3; a++) {
+            const int n = dims[a];
+            const int Wf = (g->wf[m] >> (8 * a)) & 0xff;
+            const int start = g->win[3 * m + a];
+            int copies[2] = {start, start - n};
+            int ncopy = g->per[a] ? 2 : 1;
+            const int T_ = a == 0 ? TX : (a == 1 ? TY : g->cz);
+            const int nblk = a == 0 ? g->ntx : (a == 1 ? g->nty : g->nchunk);
+            for (int q = 0; q < ncopy; q++) {
+                int c0 = std::max(copies[q], 0), c1 = std::min(copies[q] + Wf, n);
+                if (c0 >= c1) continue;
+                for (int b = c0 / T_; b <= (c1 - 1) / T_ && b < nblk; b++) {
+                    int base = a == 2 ? 0 : b * T_;
+                    ax[a].push_back({b, copies[q] - base});
+                }
+            }
+        }
+        for (auto &z : ax[2])
+            for (auto &y : ax[1])
+                for (auto &x : ax[0]) {
+                    int tile = (z.first * g->nty + y.first) * g->ntx + x.first;
+                    lists[tile].push_back(make_int4(m, x.second, y.second, z.second));
+                }
+    }
+    std::vector<int> toff(ntiles + 1, 0);
+    std::vector<int4> ent;
+    for (int t = 0; t < ntiles; t++) {
+        auto &l = lists[t];
+        std::stable_sort(l.begin(), l.end(), [](const int4 &a, const int4 &b) {
+            return a.w != b.w ? a.w < b.w : a.x < b.x;
+        });
+        toff[t] = (int)ent.size();
+        ent.insert(ent.end(), l.begin(), l.end());
+    }
+    toff[ntiles] = (int)ent.size();
+    g->n_ent = (long long)ent.size();
+    CKS(upload_raw(L, &g->d_tile_off, toff));
+    if (!ent.empty()) CKS(upload_raw(L, &g->d_tile_ent, ent));
+    else g->d_tile_ent = nullptr;
+    CK(cudaDeviceSynchronize());
+    return ML_OK;
+#undef CKS
+}
+
+}  // namespace
+
+ml_status ml_add_molecules(ml_grid *g, const ml_molecule_desc *md, void *stream, int *first_id) {
+    (void)stream;
+    if (!g || !md) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (md->count < 0) return fail(ML_ERR_INVALID_ARG, "negative count");
+    if (md->count == 0) {
+        if (first_id) *first_id = g->nmol;
+        return ML_OK;
+    }
+    if (!md->nlev || !md->off || !md->pos || !md->sigma || !md->gamma || !md->decay || !md->dephase ||
+        !md->kind || !md->nsub || !md->H0 || !md->mu || !md->rho)
+        return fail(ML_ERR_INVALID_ARG, "null molecule array");
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    // keep the evolving state of molecules added earlier
+    if (g->nmol > 0 && g->step > 0) {
+        std::vector<double> buf(2 * g->pool);
+        ml_status s = ml_get_molecules(g, ML_MOL_RHO, buf.data(), 0, nullptr);
+        if (s != ML_OK) return s;
+        g->rho0 = buf;
+    }
+    const long long base = g->pool;
+    for (int m = 0; m < md->count; m++) {
+        int n = md->nlev[m];
+        if (n < 2 || n > ML_MAX_LEVELS) return fail(ML_ERR_INVALID_ARG, "nlev must be 2..8");
+        if (md->off[m] < 0 || md->off[m] + (long long)n * n > md->pool) return fail(ML_ERR_INVALID_ARG, "pool offset out of range");
+        if (md->kind[m] != 0 && md->kind[m] != 1) return fail(ML_ERR_INVALID_ARG, "kind must be 0 or 1");
+        if (md->kind[m] == 0 && (n != 2 || md->decay[m] != 0.0 || md->dephase[m] != 0.0))
+            return fail(ML_ERR_INVALID_ARG, "kind 0 needs two levels and no Lindblad terms");
+        if (md->nsub[m] < 1) return fail(ML_ERR_INVALID_ARG, "nsub must be >= 1");
+        if (!(md->sigma[m] > 0.0) || std::ceil(3.0 * md->sigma[m]) > 7.0)
+            return fail(ML_ERR_INVALID_ARG, "sigma must be in (0, 7/3]");
+        if (md->decay[m] < 0.0 || md->dephase[m] < 0.0) return fail(ML_ERR_INVALID_ARG, "negative rate");
+        int R = (int)std::ceil(3.0 * md->sigma[m]);
+        int W = 2 * R + 2;
+        int wfp = 0;
+        int wstart[3];
+        for (int a = 0; a < 3; a++) {
+            double p = md->pos[3 * m + a];
+            if (!std::isfinite(p)) return fail(ML_ERR_INVALID_ARG, "non-finite position");
+            long long s = (long long)std::floor(p) - R;
+            int n_ = dims[a];
+            int Wf;
+            if (g->per[a]) {
+                long long sc = ((s % n_) + n_) % n_;
+                wstart[a] = (int)sc;
+                Wf = std::min(W, n_);
+            } else {
+                if (s < 0 || s + W > n_)
+                    return fail(ML_ERR_INVALID_ARG, "molecule " + std::to_string(m) + ": kernel window crosses a wall");
+                wstart[a] = (int)s;
+                Wf = W;
+            }
+            wfp |= Wf << (8 * a);
+        }
+        int cm = 0;
+        for (int c = 0; c < 3; c++)
+            for (int e = 0; e < n * n; e++) {
+                const double *z = md->mu + 2 * (c * md->pool + md->off[m] + e);
+                if (z[0] != 0.0 || z[1] != 0.0) cm |= 1 << c;
+            }
+        g->nlev.push_back(n);
+        g->off.push_back(g->pool);
+        g->kind.push_back(md->kind[m]);
+        g->nsub.push_back(md->nsub[m]);
+        g->cmask.push_back(cm);
+        for (int a = 0; a < 3; a++) {
+            g->win.push_back(wstart[a]);
+            g->wraw.push_back(W);
+            g->pos.push_back(md->pos[3 * m + a]);
+        }
+        g->wf.push_back(wfp);
+        g->sigma.push_back(md->sigma[m]);
+        g->gamma.push_back(md->gamma[m]);
+        g->decay.push_back(md->decay[m]);
+        g->deph.push_back(md->dephase[m]);
+        g->pool += (long long)n * n;
+    }
+    // pools (append)
+    std::vector<double> mu_new(2 * 3 * (size_t)g->pool, 0.0);
+    for (int c = 0; c < 3; c++) {
+        long long oldp = base;
+        for (long long e = 0; e < oldp; e++) {
+            mu_new[2 * (c * g->pool + e)] = g->mu.empty() ? 0.0 : g->mu[2 * (c * oldp + e)];
+            mu_new[2 * (c * g->pool + e) + 1] = g->mu.empty() ? 0.0 : g->mu[2 * (c * oldp + e) + 1];
+        }
+    }
+    long long w = base;
+    for (int m = 0; m < md->count; m++) {
+        int nn = md->nlev[m] * md->nlev[m];
+        for (int e = 0; e < nn; e++) {
+            long long src = md->off[m] + e;
+            g->H0.push_back(md->H0[2 * src]);
+            g->H0.push_back(md->H0[2 * src + 1]);
+            g->rho0.push_back(md->rho[2 * src]);
+            g->rho0.push_back(md->rho[2 * src + 1]);
+            for (int c = 0; c < 3; c++) {
+                mu_new[2 * (c * g->pool + w + e)] = md->mu[2 * (c * md->pool + src)];
+                mu_new[2 * (c * g->pool + w + e) + 1] = md->mu[2 * (c * md->pool + src) + 1];
+            }
+        }
+        w += nn;
+    }
+    g->mu.swap(mu_new);
+    std::vector<double> energy_keep;
+    if (g->nmol > 0 && g->d_energy) {
+        energy_keep.resize(g->nmol);
+        CK(cudaMemcpy(energy_keep.data(), g->d_energy, g->nmol * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    int first = g->nmol;
+    g->nmol += md->count;
+    ml_status s = rebuild_molecules(g);
+    if (s != ML_OK) return s;
+    if (!energy_keep.empty())
+        CK(cudaMemcpy(g->d_energy, energy_keep.data(), energy_keep.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (first_id) *first_id = first;
+    return ML_OK;
+}
+
+ml_status ml_add_flux_plane(ml_grid *g, int axis, int index, int nfreq, const double *omega, int *id) {
+    if (!g || !omega) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (axis < 0 || axis > 2) return fail(ML_ERR_INVALID_ARG, "axis must be 0..2");
+    if (index < 0 || index >= dim(g, axis)) return fail(ML_ERR_INVALID_ARG, "plane index out of range");
+    if (nfreq < 1 || nfreq > ML_MAX_FREQS) return fail(ML_ERR_INVALID_ARG, "nfreq must be 1..64");
+    if (g->nsamp != 0) return fail(ML_ERR_STATE, "planes must be added between folds (before stepping)");
+    Plane p;
+    p.axis = axis;
+    p.index = index;
+    p.nfreq = nfreq;
+    p.nb = dim(g, (axis + 1) % 3);
+    p.nc = dim(g, (axis + 2) % 3);
+    p.omega.assign(omega, omega + nfreq);
+    ml_status st = upload_raw(g->allocs, &p.d_omega, p.omega);
+    if (st != ML_OK) return st;
+    size_t ncell = (size_t)p.nb * p.nc;
+    AL(g->allocs, p.d_buf, (size_t)DFT_KMAX * 4 * ncell * g->esz);
+    AL(g->allocs, p.d_acc, 4 * (size_t)nfreq * ncell * sizeof(double2));
+    g->planes.push_back(p);
+    if (id) *id = (int)g->planes.size() - 1;
+    return ML_OK;
+}
+
+// ------------------------------------------------------------------ stepping
+
+namespace {
+
+template <typename T>
+ml_status fold_planes(ml_grid *g, cudaStream_t s) {
+    if (g->nsamp == 0) return ML_OK;
+    for (auto &p : g->planes)
+        CK(launch_dft_fold<T>((const T *)p.d_buf, g->nsamp, p.nb * p.nc, p.nfreq, p.d_omega, g->samp_step0, g->dt,
+                              p.d_acc, s));
+    g->nsamp = 0;
+    return ML_OK;
+}
+
+template <typename T>
+ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
+    for (long long it = 0; it < nsteps; it++) {
+        const int cur = g->cur, nxt = cur ^ 1;
+        if (g->nmol > 0) {
+            MolArgs<T> m{};
+            m.nmol = g->nmol;
+            m.dt = (T)g->dt;
+            m.nx = g->nx; m.ny = g->ny; m.nz = g->nz; m.px = g->px; m.plane = g->plane;
+            for (int a = 0; a < 3; a++) { m.per[a] = g->per[a]; m.E[a] = (const T *)g->F[cur][a]; }
+            m.nlev = g->d_nlev; m.off = g->d_off; m.kind = g->d_kind; m.nsub = g->d_nsub; m.cmask = g->d_cmask;
+            m.gamma = (const T *)g->d_gamma; m.decay = (const T *)g->d_decay; m.dephase = (const T *)g->d_deph;
+            m.H0 = (const cx<T> *)g->d_H0; m.mu = (const cx<T> *)g->d_mu; m.pool = g->pool;
+            m.rho = (cx<T> *)g->d_rho;
+            m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
+            m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
+            m.energy = g->d_energy; m.status = g->d_status;
+            CK(launch_molecules<T>(m, s));
+        }
+        YeeArgs<T> y{};
+        y.nx = g->nx; y.ny = g->ny; y.nz = g->nz; y.px = g->px; y.py = g->py; y.plane = g->plane;
+        for (int a = 0; a < 3; a++) y.per[a] = g->per[a];
+        for (int f = 0; f < 6; f++) y.pml[f] = g->pml[f];
+        y.ntx = g->ntx; y.nty = g->nty; y.nchunk = g->nchunk; y.cz = g->cz;
+        y.dt = (T)g->dt;
+        for (int c = 0; c < 3; c++) {
+            y.Eo[c] = (const T *)g->F[cur][c];
+            y.Ho[c] = (const T *)g->F[cur][3 + c];
+            y.En[c] = (T *)g->F[nxt][c];
+            y.Hn[c] = (T *)g->F[nxt][3 + c];
+        }
+        for (int a = 0; a < 3; a++) {
+            y.cpml[a] = (const T *)g->cpml[a];
+            for (int q = 0; q < 2; q++) {
+                y.psiHo[a][q] = (const T *)g->psiH[cur][a][q];
+                y.psiHn[a][q] = (T *)g->psiH[nxt][a][q];
+                y.psiE[a][q] = (T *)g->psiE[a][q];
+            }
+        }
+        y.mat = g->mat;
+        y.mat_cb = (const T *)g->mat_cb; y.mat_dk = (const T *)g->mat_dk; y.mat_db = (const T *)g->mat_db;
+        for (int q = 0; q < 6; q++) { y.dbox[q] = g->dbox[q]; y.jbox[q] = g->jbox[q]; }
+        y.dcb = (const T *)g->dcb;
+        for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
+        y.absorbed_part = g->absorbed_part;
+        if (g->nmol > 0 && g->n_ent > 0) {
+            y.tile_off = g->d_tile_off; y.tile_ent = g->d_tile_ent; y.mol_wf = g->d_wf;
+            y.mol_c = (const T *)g->d_c; y.mol_w = (const T *)g->d_w;
+        }
+        y.nsrc = (int)g->src.size();
+        for (int q = 0; q < y.nsrc; q++) y.src[q] = g->src[q];
+        y.step = g->step;
+        CK(launch_yee<T>(y, g->nblocks, s));
+        if (!g->planes.empty()) {
+            if (g->nsamp == 0) g->samp_step0 = g->step;
+            for (auto &p : g->planes) {
+                PlaneArgs<T> pa{};
+                pa.axis = p.axis; pa.index = p.index; pa.nb = p.nb; pa.nc = p.nc;
+                pa.px = g->px; pa.plane = g->plane;
+                for (int c = 0; c < 3; c++) { pa.E[c] = (const T *)g->F[nxt][c]; pa.H[c] = (const T *)g->F[nxt][3 + c]; }
+                pa.buf = (T *)p.d_buf;
+                pa.slot = g->nsamp;
+                CK(launch_dft_sample<T>(pa, s));
+            }
+            g->nsamp++;
+            if (g->nsamp == DFT_KMAX) {
+                ml_status st = fold_planes<T>(g, s);
+                if (st != ML_OK) return st;
+            }
+        }
+        g->cur = nxt;
+        g->step++;
+    }
+    return ML_OK;
+}
+
+}  // namespace
+
+ml_status ml_step(ml_grid *g, int64_t nsteps, void *stream) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    if (nsteps < 0) return fail(ML_ERR_INVALID_ARG, "negative step count");
+    cudaStream_t s = (cudaStream_t)stream;
+    return g->prec ? step_impl<double>(g, nsteps, s) : step_impl<float>(g, nsteps, s);
+}
+
+// ------------------------------------------------------------------ state access
+
+namespace {
+const unsigned kMaskBits[6] = {ML_EX, ML_EY, ML_EZ, ML_HX, ML_HY, ML_HZ};
+}
+
+ml_status ml_get_fields(ml_grid *g, unsigned mask, void *dst, int dst_on_device, void *stream) {
+    if (!g || !dst) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (mask == 0 || (mask & ~63u)) return fail(ML_ERR_INVALID_ARG, "bad component mask");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)g->nx * g->ny * g->nz;
+    char *out = (char *)dst;
+    for (int c = 0; c < 6; c++) {
+        if (!(mask & kMaskBits[c])) continue;
+        void *tgt = dst_on_device ? (void *)out : g->scratch;
+        cudaError_t e = g->prec ? launch_pack_fields<double>((const double *)g->F[g->cur][c], (double *)tgt, g->nx, g->ny,
+                                                             g->nz, g->px, g->plane, 0, s)
+                                : launch_pack_fields<float>((const float *)g->F[g->cur][c], (float *)tgt, g->nx, g->ny,
+                                                            g->nz, g->px, g->plane, 0, s);
+        CK(e);
+        if (!dst_on_device) CK(cudaMemcpyAsync(out, g->scratch, N * g->esz, cudaMemcpyDeviceToHost, s));
+        out += N * g->esz;
+    }
+    if (!dst_on_device) CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+ml_status ml_set_fields(ml_grid *g, unsigned mask, const void *src, int src_on_device, void *stream) {
+    if (!g || !src) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (mask == 0 || (mask & ~63u)) return fail(ML_ERR_INVALID_ARG, "bad component mask");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)g->nx * g->ny * g->nz;
+    const char *in = (const char *)src;
+    for (int c = 0; c < 6; c++) {
+        if (!(mask & kMaskBits[c])) continue;
+        const void *from = in;
+        if (!src_on_device) {
+            CK(cudaMemcpyAsync(g->scratch, in, N * g->esz, cudaMemcpyHostToDevice, s));
+            from = g->scratch;
+        }
+        cudaError_t e = g->prec ? launch_pack_fields<double>((const double *)from, (double *)g->F[g->cur][c], g->nx,
+                                                             g->ny, g->nz, g->px, g->plane, 1, s)
+                                : launch_pack_fields<float>((const float *)from, (float *)g->F[g->cur][c], g->nx,
+                                                            g->ny, g->nz, g->px, g->plane, 1, s);
+        CK(e);
+        e = g->prec ? launch_refresh_ghosts<double>((double *)g->F[g->cur][c], g->nx, g->ny, g->nz, g->px, g->plane,
+                                                    g->per, s)
+                    : launch_refresh_ghosts<float>((float *)g->F[g->cur][c], g->nx, g->ny, g->nz, g->px, g->plane,
+                                                   g->per, s);
+        CK(e);
+        in += N * g->esz;
+        if (!src_on_device) CK(cudaStreamSynchronize(s));  // scratch is reused
+    }
+    return ML_OK;
+}
+
+ml_status ml_get_molecules(ml_grid *g, int what, double *dst, int dst_on_device, void *stream) {
+    if (!g || !dst) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (what < 0 || what > 4) return fail(ML_ERR_INVALID_ARG, "unknown molecule quantity");
+    if (g->nmol == 0) return ML_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t n = what == 0 ? 2 * (size_t)g->pool
+                         : (what == 3 ? (size_t)g->nmol : (what == 4 ? (size_t)g->nmol * MAXLEV : 3 * (size_t)g->nmol));
+    double *tgt = dst_on_device ? dst : g->d_export;
+    cudaError_t e = g->prec ? launch_mol_export<double>(what, g->nmol, g->d_nlev, g->d_off, (const cx<double> *)g->d_rho,
+                                                        (const double *)g->d_Et, (const double *)g->d_mudot, g->d_energy,
+                                                        g->pool, tgt, s)
+                            : launch_mol_export<float>(what, g->nmol, g->d_nlev, g->d_off, (const cx<float> *)g->d_rho,
+                                                       (const float *)g->d_Et, (const float *)g->d_mudot, g->d_energy,
+                                                       g->pool, tgt, s);
+    CK(e);
+    if (!dst_on_device) {
+        CK(cudaMemcpyAsync(dst, g->d_export, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return ML_OK;
+}
+
+ml_status ml_flux(ml_grid *g, int id, double *out, void *stream) {
+    if (!g || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (id < 0 || id >= (int)g->planes.size()) return fail(ML_ERR_INVALID_ARG, "no such plane");
+    cudaStream_t s = (cudaStream_t)stream;
+    ml_status st = g->prec ? fold_planes<double>(g, s) : fold_planes<float>(g, s);
+    if (st != ML_OK) return st;
+    Plane &p = g->planes[id];
+    CK(launch_flux_reduce(p.d_acc, p.nb * p.nc, p.nfreq, g->d_scalar, s));
+    CK(cudaMemcpyAsync(out, g->d_scalar, p.nfreq * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+ml_status ml_flux_data(ml_grid *g, int id, double *out, void *stream) {
+    if (!g || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (id < 0 || id >= (int)g->planes.size()) return fail(ML_ERR_INVALID_ARG, "no such plane");
+    cudaStream_t s = (cudaStream_t)stream;
+    ml_status st = g->prec ? fold_planes<double>(g, s) : fold_planes<float>(g, s);
+    if (st != ML_OK) return st;
+    Plane &p = g->planes[id];
+    CK(cudaMemcpyAsync(out, p.d_acc, 4 * (size_t)p.nfreq * p.nb * p.nc * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+ml_status ml_absorbed(ml_grid *g, double *out, void *stream) {
+    if (!g || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_sum_doubles(g->absorbed_part, g->nblocks, g->d_scalar, s));
+    CK(cudaMemcpyAsync(out, g->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+ml_status ml_sync_status(ml_grid *g, void *stream) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    int st = 0;
+    CK(cudaMemcpy(&st, g->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(g->d_status, 0, sizeof(int)));
+    if (st == ML_ERR_NUMERIC) return fail(ML_ERR_NUMERIC, "non-finite molecular field or current");
+    if (st == ML_ERR_TIMEOUT) return fail(ML_ERR_TIMEOUT, "device wait timed out");
+    if (st != 0) return fail((ml_status)st, "device status " + std::to_string(st));
+    return ML_OK;
+}
+
+int64_t ml_step_count(const ml_grid *g) { return g ? g->step : -1; }
+int ml_molecule_count(const ml_grid *g) { return g ? g->nmol : -1; }
+
+// ------------------------------------------------------------------ checkpoint
+
+namespace {
+struct Blob {
+    void *p;
+    size_t bytes;
+};
+
+std::vector<Blob> state_blobs(ml_grid *g) {
+    std::vector<Blob> b;
+    for (int c = 0; c < 6; c++) b.push_back({g->F[g->cur][c], g->vol * g->esz});
+    for (int a = 0; a < 3; a++)
+        for (int q = 0; q < 2; q++)
+            if (g->psi_n[a]) {
+                b.push_back({g->psiH[g->cur][a][q], g->psi_n[a] * g->esz});
+                b.push_back({g->psiE[a][q], g->psi_n[a] * g->esz});
+            }
+    if (g->JD[0]) {
+        size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
+        for (int c = 0; c < 3; c++) b.push_back({g->JD[c], cnt * g->esz});
+    }
+    b.push_back({g->absorbed_part, (size_t)g->nblocks * sizeof(double)});
+    if (g->nmol) {
+        b.push_back({g->d_rho, 2 * (size_t)g->pool * g->esz});
+        b.push_back({g->d_energy, (size_t)g->nmol * sizeof(double)});
+        b.push_back({g->d_Et, 3 * (size_t)g->nmol * g->esz});
+        b.push_back({g->d_mudot, 3 * (size_t)g->nmol * g->esz});
+        b.push_back({g->d_c, 3 * (size_t)g->nmol * g->esz});
+    }
+    for (auto &p : g->planes) {
+        size_t ncell = (size_t)p.nb * p.nc;
+        b.push_back({p.d_acc, 4 * (size_t)p.nfreq * ncell * sizeof(double2)});
+        b.push_back({p.d_buf, (size_t)DFT_KMAX * 4 * ncell * g->esz});
+    }
+    return b;
+}
+const uint64_t kMagic = 0x4d4c434b50543031ull;  // "MLCKPT01"
+}  // namespace
+
+ml_status ml_checkpoint(ml_grid *g, void *host_buf, size_t *bytes, void *stream) {
+    if (!g || !bytes) return fail(ML_ERR_INVALID_ARG, "null argument");
+    auto blobs = state_blobs(g);
+    size_t need = 4 * sizeof(uint64_t);
+    for (auto &b : blobs) need += b.bytes;
+    if (!host_buf) {
+        *bytes = need;
+        return ML_OK;
+    }
+    if (*bytes < need) return fail(ML_ERR_INVALID_ARG, "checkpoint buffer too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t *hdr = (uint64_t *)host_buf;
+    hdr[0] = kMagic;
+    hdr[1] = (uint64_t)g->step;
+    hdr[2] = (uint64_t)g->nsamp;
+    hdr[3] = (uint64_t)g->samp_step0;
+    char *o = (char *)host_buf + 4 * sizeof(uint64_t);
+    for (auto &b : blobs) {
+        CK(cudaMemcpyAsync(o, b.p, b.bytes, cudaMemcpyDeviceToHost, s));
+        o += b.bytes;
+    }
+    CK(cudaStreamSynchronize(s));
+    *bytes = need;
+    return ML_OK;
+}
+
+ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *stream) {
+    if (!g || !host_buf) return fail(ML_ERR_INVALID_ARG, "null argument");
+    auto blobs = state_blobs(g);
+    size_t need = 4 * sizeof(uint64_t);
+    for (auto &b : blobs) need += b.bytes;
+    const uint64_t *hdr = (const uint64_t *)host_buf;
+    if (bytes != need || hdr[0] != kMagic) return fail(ML_ERR_INVALID_ARG, "checkpoint does not match this grid");
+    cudaStream_t s = (cudaStream_t)stream;
+    const char *o = (const char *)host_buf + 4 * sizeof(uint64_t);
+    for (auto &b : blobs) {
+        CK(cudaMemcpyAsync(b.p, o, b.bytes, cudaMemcpyHostToDevice, s));
+        o += b.bytes;
+    }
+    CK(cudaStreamSynchronize(s));
+    g->step = (long long)hdr[1];
+    g->nsamp = (int)hdr[2];
+    g->samp_step0 = (long long)hdr[3];
+    return ML_OK;
+}

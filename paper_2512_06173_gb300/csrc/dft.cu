@@ -1,0 +1,124 @@
+// K4: DFT flux planes.  The transmitted-flux spectra of Sec. IV.C/IV.D are
+// Re sum_plane (E~ x H~*) . n with E~(w) = sum_n E^{n+1} e^{i w (n+1) dt} dt and
+// H~(w) = sum_n H^{n+1/2} e^{i w (n+1/2) dt} dt.  Instead of touching FP64
+// accumulators of every frequency each step (a read-modify-write of 16 B x 4
+// components x nfreq per plane cell per step), each step only copies the four
+// tangential plane components into a K-deep FP32/FP64 sample ring; every K steps
+// the fold kernel adds the K samples, with phases computed in FP64 from the
+// absolute step index, into FP64 accumulators.  Same sums, regrouped.
+#include "ml_internal.cuh"
+
+namespace ml {
+
+constexpr int DFT_K = DFT_KMAX;
+
+template <typename T>
+__global__ void dft_sample_kernel(const PlaneArgs<T> a) {
+    const int ncell = a.nb * a.nc;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncell) return;
+    const int u = t % a.nb, v = t / a.nb;
+    const int b = (a.axis + 1) % 3, c = (a.axis + 2) % 3;
+    int idx[3], idm[3];
+    idx[a.axis] = a.index; idx[b] = u; idx[c] = v;
+    idm[a.axis] = a.index - 1; idm[b] = u; idm[c] = v;
+    const long long g = (long long)(idx[2] + 1) * a.plane + (long long)(idx[1] + 1) * a.px + (idx[0] + XO);
+    const long long gm = (long long)(idm[2] + 1) * a.plane + (long long)(idm[1] + 1) * a.px + (idm[0] + XO);
+    T *out = a.buf + (long long)a.slot * 4 * ncell;
+    out[t] = a.E[b][g];
+    out[ncell + t] = a.E[c][g];
+    out[2 * ncell + t] = T(0.5) * (a.H[b][g] + a.H[b][gm]);
+    out[3 * ncell + t] = T(0.5) * (a.H[c][g] + a.H[c][gm]);
+}
+
+template <typename T>
+cudaError_t launch_dft_sample(const PlaneArgs<T> &a, cudaStream_t s) {
+    int n = a.nb * a.nc;
+    dft_sample_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// acc: [4][nfreq][ncell] double2.  step0: step index n of the first sample (it holds
+// E at (n+1) dt and H at (n+1/2) dt).
+template <typename T>
+__global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
+                                double dt, double2 *acc) {
+    __shared__ double2 phE[DFT_K * ML_MAX_FREQS_DEV];
+    __shared__ double2 phH[DFT_K * ML_MAX_FREQS_DEV];
+    for (int q = threadIdx.x; q < nsamp * nfreq; q += blockDim.x) {
+        int s = q / nfreq, f = q % nfreq;
+        double tE = (double)(step0 + s + 1) * dt, tH = ((double)(step0 + s) + 0.5) * dt;
+        double sn, cs;
+        sincos(omega[f] * tE, &sn, &cs);
+        phE[q] = make_double2(cs * dt, sn * dt);
+        sincos(omega[f] * tH, &sn, &cs);
+        phH[q] = make_double2(cs * dt, sn * dt);
+    }
+    __syncthreads();
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 4ll * ncell) return;
+    const int comp = (int)(t / ncell), cell = (int)(t % ncell);
+    const double2 *ph = comp < 2 ? phE : phH;
+    double v[DFT_K];
+    for (int s = 0; s < nsamp; s++) v[s] = (double)buf[((long long)s * 4 + comp) * ncell + cell];
+    for (int f = 0; f < nfreq; f++) {
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < nsamp; s++) {
+            double2 p = ph[s * nfreq + f];
+            re += v[s] * p.x;
+            im += v[s] * p.y;
+        }
+        double2 *o = acc + ((long long)comp * nfreq + f) * ncell + cell;
+        double2 x = *o;
+        x.x += re;
+        x.y += im;
+        *o = x;
+    }
+}
+
+template <typename T>
+cudaError_t launch_dft_fold(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
+                            double dt, double2 *acc, cudaStream_t s) {
+    if (nsamp == 0) return cudaSuccess;
+    long long n = 4ll * ncell;
+    int blocks = (int)((n + 255) / 256);
+    dft_fold_kernel<T><<<blocks, 256, 0, s>>>(buf, nsamp, ncell, nfreq, omega, step0, dt, acc);
+    return cudaGetLastError();
+}
+
+// out[f] = sum_cells Re(E_b conj(H_c) - E_c conj(H_b)), one block per frequency,
+// fixed-order tree reduction.
+__global__ void flux_reduce_kernel(const double2 *acc, int ncell, int nfreq, double *out) {
+    __shared__ double red[256];
+    const int f = blockIdx.x;
+    const double2 *E1 = acc + (0ll * nfreq + f) * ncell;
+    const double2 *E2 = acc + (1ll * nfreq + f) * ncell;
+    const double2 *H1 = acc + (2ll * nfreq + f) * ncell;
+    const double2 *H2 = acc + (3ll * nfreq + f) * ncell;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        double2 e1 = E1[c], e2 = E2[c], h1 = H1[c], h2 = H2[c];
+        s += (e1.x * h2.x + e1.y * h2.y) - (e2.x * h1.x + e2.y * h1.y);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[f] = red[0];
+}
+
+cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *out, cudaStream_t s) {
+    flux_reduce_kernel<<<nfreq, 256, 0, s>>>(acc, ncell, nfreq, out);
+    return cudaGetLastError();
+}
+
+#define ML_INST(T)                                                                          \
+    template cudaError_t launch_dft_sample<T>(const PlaneArgs<T> &, cudaStream_t);          \
+    template cudaError_t launch_dft_fold<T>(const T *, int, int, int, const double *, long long, double, \
+                                            double2 *, cudaStream_t);
+ML_INST(float)
+ML_INST(double)
+
+}  // namespace ml

@@ -1,0 +1,149 @@
+// Internal declarations of libmaxlink (not part of the ABI).
+//
+// Device layout of a grid (HBM):
+//   * six field arrays per time level, E and H double-buffered (ping-pong), each
+//     padded with one ghost layer on every side: element (i,j,k), i in [-1, nx],
+//     lives at (k+1)*plane + (j+1)*px + (i+XO).  Rows start 16 bytes aligned
+//     (XO = 4 elements).  Ghosts of non-periodic axes stay 0 (PEC wall); ghosts of
+//     periodic axes are written by the owner of the mirrored cell in the same pass.
+//   * CPML memory variables only inside the layers: per axis a slab of
+//     (pml_lo + pml_hi) cells along a, two H-side components (double-buffered,
+//     because neighbouring tiles recompute halo H from them) and two E-side
+//     components (updated in place by the owning cell).
+//   * per-cell uint8 material index, a continuous-eps design box, a Drude box.
+//   * molecule tables (SoA), per-molecule separable kernel weights, and the
+//     tile-binned molecule lists that make the current scatter deterministic.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ml {
+
+constexpr int TX = 32;      // tile width in x (one warp)
+constexpr int TY = 8;       // tile rows in y
+constexpr int XO = 4;       // x offset of the interior in a padded row
+constexpr int WMAX = 16;    // max kernel window per axis (2 ceil(3 sigma) + 2)
+constexpr int NW = 6 * WMAX;  // weights per molecule: [axis][stagger][WMAX]
+constexpr int MAXLEV = 8;
+constexpr int MAXSRC = 4;
+#define ML_MAX_FREQS_DEV 64
+constexpr int DFT_KMAX = 16;  // samples buffered per plane before a fold
+
+struct SrcDev {
+    int axis, index, comp;
+    double amp, omega, width, t0;
+};
+
+template <typename T>
+struct cx {
+    T re, im;
+};
+
+// ------------------------------------------------------------------ field pass
+template <typename T>
+struct YeeArgs {
+    int nx, ny, nz, px, py;
+    long long plane;
+    int per[3];
+    int pml[6];
+    int ntx, nty, nchunk, cz;
+    T dt;
+    const T *Eo[3];
+    const T *Ho[3];
+    T *En[3];
+    T *Hn[3];
+    // CPML coefficients per axis: 6 rows of n (bE cE kE bH cH kH)
+    const T *cpml[3];
+    // CPML memory: per axis, H side [2] old/new, E side [2] in place
+    const T *psiHo[3][2];
+    T *psiHn[3][2];
+    T *psiE[3][2];
+    // materials
+    const uint8_t *mat;   // (nz,ny,nx) or null
+    const T *mat_cb;      // dt / eps_inf per material
+    const T *mat_dk;      // Drude recursion factor per material
+    const T *mat_db;      // Drude drive factor per material (0 = none)
+    int dbox[6];
+    const T *dcb;         // dt / eps per design-box cell
+    int jbox[6];
+    T *JD[3];             // Drude current over the Drude box
+    double *absorbed_part;  // one accumulator per block
+    // molecules
+    const int *tile_off;    // CSR over (chunk, tile y, tile x)
+    const int4 *tile_ent;   // (molecule, xs - x0, ys - y0, zs absolute)
+    const int *mol_wf;      // packed window lengths x | y<<8 | z<<16
+    const T *mol_c;         // (M,3) gamma * mudot
+    const T *mol_w;         // (M, NW) weights
+    int nsrc;
+    SrcDev src[MAXSRC];
+    long long step;
+};
+
+// ------------------------------------------------------------------ molecules
+template <typename T>
+struct MolArgs {
+    int nmol;
+    T dt;
+    int nx, ny, nz, px;
+    long long plane;
+    int per[3];
+    const T *E[3];
+    const int *nlev;
+    const long long *off;
+    const int *kind;
+    const int *nsub;
+    const int *cmask;      // bit c set: dipole has a nonzero component along c
+    const T *gamma;
+    const T *decay;
+    const T *dephase;
+    const cx<T> *H0;
+    const cx<T> *mu;       // 3 pools back to back
+    long long pool;
+    cx<T> *rho;
+    const int *win;        // (M,3) window starts
+    const int *wf;         // packed window lengths
+    const T *w;            // (M, NW)
+    T *Et;
+    T *mudot;
+    T *c;
+    double *energy;
+    int *status;
+};
+
+// ------------------------------------------------------------------ DFT planes
+template <typename T>
+struct PlaneArgs {
+    int axis, index, nb, nc;   // (a,b,c) cyclic; sample grid nb x nc (b fastest)
+    int px;
+    long long plane;
+    int per_a, n_a;
+    const T *E[3];
+    const T *H[3];
+    T *buf;                    // [K][4][nc*nb]
+    int slot;
+};
+
+// launchers (explicit instantiations for float and double live in the .cu files)
+template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, int nblocks, cudaStream_t s);
+template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,
+                                                 const int *win, const int *wf, const int *wraw,
+                                                 const int *dims, const int *per, T *w, cudaStream_t s);
+template <typename T> cudaError_t launch_dft_sample(const PlaneArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_dft_fold(const T *buf, int nsamp, int ncell, int nfreq,
+                                                  const double *omega, long long step0, double dt,
+                                                  double2 *acc, cudaStream_t s);
+cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *out, cudaStream_t s);
+template <typename T> cudaError_t launch_pack_fields(const T *src, T *dst, int nx, int ny, int nz, int px,
+                                                     long long plane, int to_padded, cudaStream_t s);
+template <typename T> cudaError_t launch_refresh_ghosts(T *f, int nx, int ny, int nz, int px, long long plane,
+                                                        const int *per, cudaStream_t s);
+template <typename T> cudaError_t launch_zero_pec(T *const *E, int nx, int ny, int nz, int px, long long plane,
+                                                  const int *per, cudaStream_t s);
+template <typename T> cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long long *off,
+                                                    const cx<T> *rho, const T *Et, const T *mudot,
+                                                    const double *energy, long long pool, double *dst,
+                                                    cudaStream_t s);
+cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream_t s);
+
+}  // namespace ml

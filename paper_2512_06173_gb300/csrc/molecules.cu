@@ -1,0 +1,348 @@
+// K2: one warp per molecule, once per time step.
+//   1. regularised field Etilde_m^c = gamma_m sum_window E^c kappa_m^c
+//      (Eq. E_regu_Emi), lanes striding over the (folded) kernel window, combined
+//      by a fixed xor-shuffle tree (deterministic);
+//   2. density-matrix step under H0 - Etilde . mu held over dt (Eq.
+//      von-Neumann-tls): closed-form 2x2 exponential, or classic RK4 substeps of
+//      the GKSL equation with ladder decay and pure dephasing written element-wise;
+//   3. mudot = (Tr rho' mu - Tr rho mu) / dt (Eq. dipole_derivative) and the
+//      current amplitude gamma * mudot consumed by the field pass (Eq. J_mol);
+//   4. FP64 running sum of Tr(rho H0) for the time-averaged molecular energy.
+// K3 (setup): separable, normalised 1D Gaussian weights per molecule, axis and
+// staggering, folded onto one period on periodic axes.
+#include "ml_internal.cuh"
+
+namespace ml {
+
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.re * s, a.im * s}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cconj(cx<T> a) { return {a.re, -a.im}; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long fidx(int px, long long plane, int i, int j, int k) {
+    return (long long)(k + 1) * plane + (long long)(j + 1) * px + (i + XO);
+}
+
+constexpr int MOL_WARPS = 4;
+
+template <typename T>
+struct MolShared {
+    T w[MOL_WARPS][NW];
+    cx<T> H[MOL_WARPS][MAXLEV * MAXLEV];
+    cx<T> S[MOL_WARPS][2][MAXLEV * MAXLEV];
+};
+
+// GKSL right-hand side for element (j,l) of rho given in S (n x n), H in Hs.
+template <typename T>
+__device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, const cx<T> *Hs, T decay, T deph) {
+    cx<T> acc = {T(0), T(0)};
+    for (int p = 0; p < n; p++) {
+        cx<T> a = cmul(Hs[j * n + p], S[p * n + l]);
+        cx<T> b = cmul(S[j * n + p], Hs[p * n + l]);
+        acc.re += a.re - b.re;
+        acc.im += a.im - b.im;
+    }
+    // -i * acc
+    cx<T> out = {acc.im, -acc.re};
+    const cx<T> r = S[j * n + l];
+    if (decay != T(0)) {
+        T f = T(0.5) * decay * (T(j >= 1) + T(l >= 1));
+        out.re -= f * r.re;
+        out.im -= f * r.im;
+        if (j == l && j + 1 < n) out.re += decay * S[(j + 1) * n + (j + 1)].re;
+    }
+    if (deph != T(0) && j != l) {
+        out.re -= deph * r.re;
+        out.im -= deph * r.im;
+    }
+    return out;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<T> a) {
+    __shared__ MolShared<T> sh;
+    const int lane = threadIdx.x & 31;
+    const int wl = threadIdx.x >> 5;
+    const int m = blockIdx.x * MOL_WARPS + wl;
+    if (m >= a.nmol) return;  // whole warp leaves together
+
+    // ---- 1. gather
+    for (int q = lane; q < NW; q += 32) sh.w[wl][q] = a.w[(long long)m * NW + q];
+    __syncwarp();
+    const int wfp = a.wf[m];
+    const int Wx = wfp & 0xff, Wy = (wfp >> 8) & 0xff, Wz = (wfp >> 16) & 0xff;
+    const int xs = a.win[3 * m], ys = a.win[3 * m + 1], zs = a.win[3 * m + 2];
+    const int cm = a.cmask[m];
+    const T *w = sh.w[wl];
+    T g[3] = {T(0), T(0), T(0)};
+    const int total = Wx * Wy * Wz;
+    for (int t = lane; t < total; t += 32) {
+        const int dx = t % Wx;
+        const int r = t / Wx;
+        const int dy = r % Wy;
+        const int dz = r / Wy;
+        int x = xs + dx, y = ys + dy, z = zs + dz;
+        if (x >= a.nx) x -= a.nx;
+        if (y >= a.ny) y -= a.ny;
+        if (z >= a.nz) z -= a.nz;
+        const long long f = fidx(a.px, a.plane, x, y, z);
+        if (cm & 1) g[0] += a.E[0][f] * (w[WMAX + dx] * w[2 * WMAX + dy] * w[4 * WMAX + dz]);
+        if (cm & 2) g[1] += a.E[1][f] * (w[dx] * w[3 * WMAX + dy] * w[4 * WMAX + dz]);
+        if (cm & 4) g[2] += a.E[2][f] * (w[dx] * w[2 * WMAX + dy] * w[5 * WMAX + dz]);
+    }
+    const T gam = a.gamma[m];
+    T Et[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) Et[c] = gam * warp_sum(g[c]);
+
+    // ---- 2. density-matrix step
+    const int n = a.nlev[m];
+    const int nn = n * n;
+    const long long o = a.off[m];
+    cx<T> *Hs = sh.H[wl];
+    for (int e = lane; e < nn; e += 32) {
+        cx<T> h = a.H0[o + e];
+        for (int c = 0; c < 3; c++) {
+            cx<T> mu = a.mu[c * a.pool + o + e];
+            h.re -= Et[c] * mu.re;
+            h.im -= Et[c] * mu.im;
+        }
+        Hs[e] = h;
+    }
+    // <mu> before
+    T mu0[3] = {T(0), T(0), T(0)};
+    cx<T> r0[2];
+    for (int q = 0; q < 2; q++) {
+        int e = lane + 32 * q;
+        r0[q] = e < nn ? a.rho[o + e] : cx<T>{T(0), T(0)};
+        if (e < nn) {
+            int jj = e / n, ll = e % n;
+            for (int c = 0; c < 3; c++) {
+                cx<T> mu = a.mu[c * a.pool + o + ll * n + jj];
+                mu0[c] += r0[q].re * mu.re - r0[q].im * mu.im;
+            }
+        }
+    }
+    for (int c = 0; c < 3; c++) mu0[c] = warp_sum(mu0[c]);
+    __syncwarp();
+    cx<T> r1[2] = {r0[0], r0[1]};
+    if (a.kind[m] == 0) {
+        // exact exponential of a 2x2 Hermitian H held over dt
+        if (lane == 0) {
+            const T dt = a.dt;
+            T ha = Hs[0].re, hd = Hs[3].re;
+            cx<T> b = Hs[1];
+            T hbar = T(0.5) * (ha + hd), z = T(0.5) * (ha - hd);
+            T W = sqrt(z * z + b.re * b.re + b.im * b.im);
+            T cw = cos(W * dt);
+            T sw = W > T(0) ? sin(W * dt) / W : dt;
+            (void)hbar;  // global phase cancels in U rho U^+
+            cx<T> U[4];
+            U[0] = {cw, -sw * z};
+            U[1] = {sw * b.im, -sw * b.re};       // -i sw b
+            U[2] = {-sw * b.im, -sw * b.re};      // -i sw conj(b)
+            U[3] = {cw, sw * z};
+            cx<T> R[4];
+            for (int e = 0; e < 4; e++) R[e] = a.rho[o + e];
+            cx<T> TT[4], out[4];
+            for (int p = 0; p < 2; p++)
+                for (int q = 0; q < 2; q++)
+                    TT[p * 2 + q] = cadd(cmul(U[p * 2 + 0], R[0 * 2 + q]), cmul(U[p * 2 + 1], R[1 * 2 + q]));
+            for (int p = 0; p < 2; p++)
+                for (int q = 0; q < 2; q++)
+                    out[p * 2 + q] = cadd(cmul(TT[p * 2 + 0], cconj(U[q * 2 + 0])), cmul(TT[p * 2 + 1], cconj(U[q * 2 + 1])));
+            for (int e = 0; e < 4; e++) sh.S[wl][0][e] = out[e];
+        }
+        __syncwarp();
+        for (int q = 0; q < 2; q++) {
+            int e = lane + 32 * q;
+            if (e < nn) r1[q] = sh.S[wl][0][e];
+        }
+    } else {
+        const int ns = a.nsub[m];
+        const T h = a.dt / T(ns);
+        const T decay = a.decay[m], deph = a.dephase[m];
+        for (int sstep = 0; sstep < ns; sstep++) {
+            cx<T> base[2] = {r1[0], r1[1]};
+            cx<T> acc[2] = {{T(0), T(0)}, {T(0), T(0)}};
+            for (int q = 0; q < 2; q++) {
+                int e = lane + 32 * q;
+                if (e < nn) sh.S[wl][0][e] = base[q];
+            }
+            __syncwarp();
+            int sb = 0;
+#pragma unroll 1
+            for (int st = 0; st < 4; st++) {
+                const T wgt = (st == 0 || st == 3) ? T(1) : T(2);
+                const T cn = (st < 2) ? T(0.5) : T(1);
+                cx<T> f[2];
+                for (int q = 0; q < 2; q++) {
+                    int e = lane + 32 * q;
+                    if (e < nn) {
+                        f[q] = rhs_elem(n, e / n, e % n, sh.S[wl][sb], Hs, decay, deph);
+                        acc[q].re += wgt * f[q].re;
+                        acc[q].im += wgt * f[q].im;
+                    }
+                }
+                if (st < 3) {
+                    for (int q = 0; q < 2; q++) {
+                        int e = lane + 32 * q;
+                        if (e < nn) sh.S[wl][sb ^ 1][e] = {base[q].re + cn * h * f[q].re, base[q].im + cn * h * f[q].im};
+                    }
+                    sb ^= 1;
+                    __syncwarp();
+                }
+            }
+            for (int q = 0; q < 2; q++) {
+                r1[q].re = base[q].re + h / T(6) * acc[q].re;
+                r1[q].im = base[q].im + h / T(6) * acc[q].im;
+            }
+            __syncwarp();
+        }
+    }
+    // ---- 3. <mu> after, mudot, energy
+    T mu1[3] = {T(0), T(0), T(0)};
+    T en = T(0);
+    for (int q = 0; q < 2; q++) {
+        int e = lane + 32 * q;
+        if (e < nn) {
+            a.rho[o + e] = r1[q];
+            int jj = e / n, ll = e % n;
+            for (int c = 0; c < 3; c++) {
+                cx<T> mu = a.mu[c * a.pool + o + ll * n + jj];
+                mu1[c] += r1[q].re * mu.re - r1[q].im * mu.im;
+            }
+            cx<T> h0 = a.H0[o + ll * n + jj];
+            en += r1[q].re * h0.re - r1[q].im * h0.im;
+        }
+    }
+    en = warp_sum(en);
+    for (int c = 0; c < 3; c++) mu1[c] = warp_sum(mu1[c]);
+    if (lane == 0) {
+        bool bad = false;
+        for (int c = 0; c < 3; c++) {
+            T md = (mu1[c] - mu0[c]) / a.dt;
+            a.Et[3 * m + c] = Et[c];
+            a.mudot[3 * m + c] = md;
+            a.c[3 * m + c] = gam * md;
+            if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
+        }
+        a.energy[m] += (double)en;
+        if (bad) atomicCAS(a.status, 0, 6);
+    }
+}
+
+template <typename T>
+cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s) {
+    if (a.nmol == 0) return cudaSuccess;
+    int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
+    molecule_kernel<T><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// K3: weights.  One thread per (molecule, axis, stagger).  The raw window has
+// wraw = 2R+2 entries starting at the (unwrapped) index s = floor(pos) - R; the
+// entries are normalised to sum 1 and, on a periodic axis, folded onto the
+// Wf = min(wraw, n) cells starting at the canonical start win.
+template <typename T>
+__global__ void weights_kernel(int nmol, const double *pos, const double *sigma, const int *win, const int *wf,
+                               const int *wraw, int nx, int ny, int nz, int p0, int p1, int p2, T *w) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nmol * 6) return;
+    const int m = t / 6, ax = (t % 6) / 2, st = t % 2;
+    const int n = ax == 0 ? nx : (ax == 1 ? ny : nz);
+    const int per = ax == 0 ? p0 : (ax == 1 ? p1 : p2);
+    const double p = pos[3 * m + ax], sg = sigma[m];
+    const int W = wraw[3 * m + ax];
+    const int R = (W - 2) / 2;
+    const int s = (int)floor(p) - R;
+    double v[32];
+    double sum = 0.0;
+    for (int q = 0; q < W; q++) {
+        double x = (double)(s + q) + 0.5 * st - p;
+        v[q] = exp(-x * x / (2.0 * sg * sg));
+        sum += v[q];
+    }
+    double f[WMAX];
+    for (int q = 0; q < WMAX; q++) f[q] = 0.0;
+    const int Wf = (wf[m] >> (8 * ax)) & 0xff;
+    const int start = win[3 * m + ax];
+    for (int q = 0; q < W; q++) {
+        int c = s + q;
+        int d;
+        if (per) {
+            int cc = ((c % n) + n) % n;
+            d = cc - start;
+            if (d < 0) d += n;
+        } else {
+            d = c - start;
+        }
+        if (d >= 0 && d < Wf) f[d] += v[q] / sum;
+    }
+    T *out = w + (long long)m * NW + (2 * ax + st) * WMAX;
+    for (int q = 0; q < WMAX; q++) out[q] = (T)f[q];
+}
+
+template <typename T>
+cudaError_t launch_weights(int nmol, const double *pos, const double *sigma, const int *win, const int *wf,
+                           const int *wraw, const int *dims, const int *per, T *w, cudaStream_t s) {
+    if (nmol == 0) return cudaSuccess;
+    int threads = 128, blocks = (nmol * 6 + threads - 1) / threads;
+    weights_kernel<T><<<blocks, threads, 0, s>>>(nmol, pos, sigma, win, wf, wraw, dims[0], dims[1], dims[2], per[0],
+                                                  per[1], per[2], w);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void mol_export_kernel(int what, int nmol, const int *nlev, const long long *off, const cx<T> *rho,
+                                  const T *Et, const T *mudot, const double *energy, long long pool, double *dst) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (what == 0) {
+        if (t < pool) { dst[2 * t] = (double)rho[t].re; dst[2 * t + 1] = (double)rho[t].im; }
+    } else if (what == 1 || what == 2) {
+        if (t < 3ll * nmol) dst[t] = (double)(what == 1 ? Et[t] : mudot[t]);
+    } else if (what == 3) {
+        if (t < nmol) dst[t] = energy[t];
+    } else if (what == 4) {
+        if (t < (long long)nmol * MAXLEV) {
+            int m = (int)(t / MAXLEV), l = (int)(t % MAXLEV);
+            int n = nlev[m];
+            dst[t] = l < n ? (double)rho[off[m] + l * n + l].re : 0.0;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long long *off, const cx<T> *rho,
+                              const T *Et, const T *mudot, const double *energy, long long pool, double *dst,
+                              cudaStream_t s) {
+    long long n = what == 0 ? pool : (what == 3 ? nmol : (what == 4 ? (long long)nmol * MAXLEV : 3ll * nmol));
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)((n + 255) / 256);
+    mol_export_kernel<T><<<blocks, 256, 0, s>>>(what, nmol, nlev, off, rho, Et, mudot, energy, pool, dst);
+    return cudaGetLastError();
+}
+
+#define ML_INST(T)                                                                                              \
+    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t);                                 \
+    template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \
+                                           const int *, const int *, const int *, T *, cudaStream_t);           \
+    template cudaError_t launch_mol_export<T>(int, int, const int *, const long long *, const cx<T> *, const T *, \
+                                              const T *, const double *, long long, double *, cudaStream_t);
+ML_INST(float)
+ML_INST(double)
+
+}  // namespace ml

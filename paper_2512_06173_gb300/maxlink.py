@@ -1,0 +1,376 @@
+"""ctypes binding of libmaxlink (include/maxlink.h), argument marshalling only.
+
+Every entry point of the C ABI is exposed under its own name (`ml_grid_create`,
+`ml_add_molecules`, `ml_step`, `ml_get_fields`, `ml_flux`, ...).  `Grid` wraps a
+handle built from a `workloads.Problem`.  All computation happens in the CUDA
+library; if it cannot be loaded this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional
+
+import numpy as np
+
+from . import build as _build
+
+ML_OK, ML_ERR_INVALID_ARG, ML_ERR_CUDA, ML_ERR_OOM, ML_ERR_STATE, ML_ERR_TIMEOUT, ML_ERR_NUMERIC = range(7)
+ML_F32, ML_F64 = 0, 1
+ML_MOL_RHO, ML_MOL_EFIELD, ML_MOL_MUDOT, ML_MOL_ENERGY, ML_MOL_POP = range(5)
+ML_EX, ML_EY, ML_EZ, ML_HX, ML_HY, ML_HZ, ML_ALL = 1, 2, 4, 8, 16, 32, 63
+ML_MAX_LEVELS = 8
+
+EXPORTED = ["ml_last_error", "ml_version", "ml_grid_create", "ml_grid_destroy", "ml_add_molecules",
+            "ml_add_flux_plane", "ml_step", "ml_get_fields", "ml_set_fields", "ml_get_molecules", "ml_flux",
+            "ml_flux_data", "ml_absorbed", "ml_sync_status", "ml_step_count", "ml_molecule_count",
+            "ml_checkpoint", "ml_restore"]
+
+
+class ml_material(C.Structure):
+    _fields_ = [("eps_inf", C.c_double), ("wp", C.c_double), ("gamma", C.c_double)]
+
+
+class ml_source(C.Structure):
+    _fields_ = [("axis", C.c_int), ("index", C.c_int), ("comp", C.c_int), ("amp", C.c_double),
+                ("omega", C.c_double), ("width", C.c_double), ("t0", C.c_double)]
+
+
+class ml_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("courant", C.c_double),
+                ("precision", C.c_int), ("periodic", C.c_int * 3), ("pml", C.c_int * 6),
+                ("pml_m", C.c_double), ("pml_sigma_max", C.c_double), ("pml_kappa_max", C.c_double),
+                ("pml_alpha_max", C.c_double), ("mat", C.c_void_p), ("n_materials", C.c_int),
+                ("materials", C.POINTER(ml_material)), ("design_box", C.c_int * 6),
+                ("design_eps", C.c_void_p), ("n_sources", C.c_int), ("sources", C.POINTER(ml_source))]
+
+
+class ml_molecule_desc(C.Structure):
+    _fields_ = [("count", C.c_int), ("nlev", C.c_void_p), ("off", C.c_void_p), ("pos", C.c_void_p),
+                ("sigma", C.c_void_p), ("gamma", C.c_void_p), ("decay", C.c_void_p), ("dephase", C.c_void_p),
+                ("kind", C.c_void_p), ("nsub", C.c_void_p), ("H0", C.c_void_p), ("mu", C.c_void_p),
+                ("rho", C.c_void_p), ("pool", C.c_int64)]
+
+
+_lib = None
+
+
+class MaxlinkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"maxlink status {status}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmaxlink.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        try:
+            path = _build.build()
+        except Exception as e:  # no toolkit: only an existing library can be used
+            if not os.path.exists(path):
+                raise RuntimeError(f"libmaxlink is not built and cannot be built: {e}") from e
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmaxlink not found at {path}")
+    L = C.CDLL(path)
+    P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "ml_last_error": (C.c_char_p, []),
+        "ml_version": (C.c_char_p, []),
+        "ml_grid_create": (I, [C.POINTER(ml_grid_desc), P, C.POINTER(P)]),
+        "ml_grid_destroy": (I, [P]),
+        "ml_add_molecules": (I, [P, C.POINTER(ml_molecule_desc), P, C.POINTER(I)]),
+        "ml_add_flux_plane": (I, [P, I, I, I, P, C.POINTER(I)]),
+        "ml_step": (I, [P, I64, P]),
+        "ml_get_fields": (I, [P, C.c_uint, P, I, P]),
+        "ml_set_fields": (I, [P, C.c_uint, P, I, P]),
+        "ml_get_molecules": (I, [P, I, P, I, P]),
+        "ml_flux": (I, [P, I, P, P]),
+        "ml_flux_data": (I, [P, I, P, P]),
+        "ml_absorbed": (I, [P, P, P]),
+        "ml_sync_status": (I, [P, P]),
+        "ml_step_count": (I64, [P]),
+        "ml_molecule_count": (I, [P]),
+        "ml_checkpoint": (I, [P, P, C.POINTER(C.c_size_t), P]),
+        "ml_restore": (I, [P, P, C.c_size_t, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != ML_OK:
+        msg = load().ml_last_error().decode()
+        raise MaxlinkError(status, msg)
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- C-ABI names
+
+def ml_version() -> str:
+    return load().ml_version().decode()
+
+
+def ml_last_error() -> str:
+    return load().ml_last_error().decode()
+
+
+def ml_grid_create(desc: ml_grid_desc, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().ml_grid_create(C.byref(desc), C.c_void_p(stream), C.byref(h)))
+    return h.value
+
+
+def ml_grid_destroy(h: int):
+    _check(load().ml_grid_destroy(C.c_void_p(h)))
+
+
+def ml_add_molecules(h: int, desc: ml_molecule_desc, stream: int = 0) -> int:
+    first = C.c_int()
+    _check(load().ml_add_molecules(C.c_void_p(h), C.byref(desc), C.c_void_p(stream), C.byref(first)))
+    return first.value
+
+
+def ml_add_flux_plane(h: int, axis: int, index: int, omegas) -> int:
+    om = np.ascontiguousarray(omegas, np.float64)
+    pid = C.c_int()
+    _check(load().ml_add_flux_plane(C.c_void_p(h), axis, index, len(om), C.c_void_p(_ptr(om)), C.byref(pid)))
+    return pid.value
+
+
+def ml_step(h: int, nsteps: int, stream: int = 0):
+    _check(load().ml_step(C.c_void_p(h), int(nsteps), C.c_void_p(stream)))
+
+
+def ml_get_fields(h: int, mask: int, dst_ptr: int, on_device: bool, stream: int = 0):
+    _check(load().ml_get_fields(C.c_void_p(h), mask, C.c_void_p(dst_ptr), int(on_device), C.c_void_p(stream)))
+
+
+def ml_set_fields(h: int, mask: int, src_ptr: int, on_device: bool, stream: int = 0):
+    _check(load().ml_set_fields(C.c_void_p(h), mask, C.c_void_p(src_ptr), int(on_device), C.c_void_p(stream)))
+
+
+def ml_get_molecules(h: int, what: int, dst_ptr: int, on_device: bool, stream: int = 0):
+    _check(load().ml_get_molecules(C.c_void_p(h), what, C.c_void_p(dst_ptr), int(on_device), C.c_void_p(stream)))
+
+
+def ml_flux(h: int, plane: int, nfreq: int, stream: int = 0) -> np.ndarray:
+    out = np.zeros(nfreq)
+    _check(load().ml_flux(C.c_void_p(h), plane, C.c_void_p(_ptr(out)), C.c_void_p(stream)))
+    return out
+
+
+def ml_flux_data(h: int, plane: int, count: int, stream: int = 0) -> np.ndarray:
+    out = np.zeros(2 * count)
+    _check(load().ml_flux_data(C.c_void_p(h), plane, C.c_void_p(_ptr(out)), C.c_void_p(stream)))
+    return out.view(np.complex128)
+
+
+def ml_absorbed(h: int, stream: int = 0) -> float:
+    out = np.zeros(1)
+    _check(load().ml_absorbed(C.c_void_p(h), C.c_void_p(_ptr(out)), C.c_void_p(stream)))
+    return float(out[0])
+
+
+def ml_sync_status(h: int, stream: int = 0):
+    _check(load().ml_sync_status(C.c_void_p(h), C.c_void_p(stream)))
+
+
+def ml_step_count(h: int) -> int:
+    return int(load().ml_step_count(C.c_void_p(h)))
+
+
+def ml_molecule_count(h: int) -> int:
+    return int(load().ml_molecule_count(C.c_void_p(h)))
+
+
+def ml_checkpoint(h: int, stream: int = 0) -> bytes:
+    n = C.c_size_t(0)
+    _check(load().ml_checkpoint(C.c_void_p(h), None, C.byref(n), C.c_void_p(stream)))
+    buf = C.create_string_buffer(n.value)
+    _check(load().ml_checkpoint(C.c_void_p(h), buf, C.byref(n), C.c_void_p(stream)))
+    return buf.raw
+
+
+def ml_restore(h: int, blob: bytes, stream: int = 0):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().ml_restore(C.c_void_p(h), buf, len(blob), C.c_void_p(stream)))
+
+
+# ---------------------------------------------------------------- Problem wrapper
+
+def grid_desc(prob, precision: int = ML_F32):
+    """Marshal a workloads.Problem into ml_grid_desc (plus the arrays it points to)."""
+    keep = []
+    d = ml_grid_desc()
+    d.nx, d.ny, d.nz = prob.nx, prob.ny, prob.nz
+    d.courant = prob.courant
+    d.precision = precision
+    for a in range(3):
+        d.periodic[a] = 1 if prob.periodic[a] else 0
+    for f in range(6):
+        d.pml[f] = prob.pml[f]
+    d.pml_m, d.pml_sigma_max = prob.pml_m, prob.pml_sigma_max
+    d.pml_kappa_max, d.pml_alpha_max = prob.pml_kappa_max, prob.pml_alpha_max
+    if prob.mat is not None:
+        m = np.ascontiguousarray(prob.mat, np.uint8)
+        keep.append(m)
+        d.mat = _ptr(m)
+    mats = (ml_material * len(prob.materials))(*[ml_material(x.eps_inf, x.wp, x.gamma) for x in prob.materials])
+    keep.append(mats)
+    d.n_materials = len(prob.materials)
+    d.materials = mats
+    if prob.design_box is not None:
+        for q in range(6):
+            d.design_box[q] = prob.design_box[q]
+        de = np.ascontiguousarray(prob.design_eps, np.float64)
+        keep.append(de)
+        d.design_eps = _ptr(de)
+    if prob.sources:
+        srcs = (ml_source * len(prob.sources))(*[ml_source(s.axis, s.index, s.comp, s.amp, s.omega, s.width, s.t0)
+                                                 for s in prob.sources])
+        keep.append(srcs)
+        d.n_sources = len(prob.sources)
+        d.sources = srcs
+    return d, keep
+
+
+def molecule_desc(mol):
+    keep = []
+
+    def arr(x, dt):
+        a = np.ascontiguousarray(x, dt)
+        keep.append(a)
+        return _ptr(a)
+
+    d = ml_molecule_desc()
+    d.count = mol.count
+    d.nlev = arr(mol.nlev, np.int32)
+    d.off = arr(mol.off, np.int64)
+    d.pos = arr(mol.pos, np.float64)
+    d.sigma = arr(mol.sigma, np.float64)
+    d.gamma = arr(mol.gamma, np.float64)
+    d.decay = arr(mol.decay, np.float64)
+    d.dephase = arr(mol.dephase, np.float64)
+    d.kind = arr(mol.kind, np.int32)
+    d.nsub = arr(mol.nsub, np.int32)
+    d.H0 = arr(np.ascontiguousarray(mol.H0, np.complex128).view(np.float64), np.float64)
+    d.mu = arr(np.ascontiguousarray(mol.mu, np.complex128).view(np.float64), np.float64)
+    d.rho = arr(np.ascontiguousarray(mol.rho0, np.complex128).view(np.float64), np.float64)
+    d.pool = int(mol.H0.shape[0])
+    return d, keep
+
+
+class Grid:
+    """A grid handle built from a Problem (fields, molecules, flux planes)."""
+
+    def __init__(self, prob, precision: int = ML_F32, stream: int = 0, molecules: bool = True):
+        self.prob = prob
+        self.precision = precision
+        self.dtype = np.float64 if precision == ML_F64 else np.float32
+        self.stream = stream
+        d, keep = grid_desc(prob, precision)
+        self.h = ml_grid_create(d, stream)
+        try:
+            self.planes = []
+            for p in prob.planes:
+                self.planes.append(ml_add_flux_plane(self.h, p.axis, p.index, p.omegas))
+            if molecules and prob.molecules.count:
+                md, keep2 = molecule_desc(prob.molecules)
+                ml_add_molecules(self.h, md, stream)
+        except Exception:
+            ml_grid_destroy(self.h)
+            self.h = None
+            raise
+
+    def close(self):
+        if getattr(self, "h", None):
+            ml_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.prob.nz, self.prob.ny, self.prob.nx)
+
+    def step(self, n: int = 1):
+        ml_step(self.h, n, self.stream)
+
+    def sync(self):
+        ml_sync_status(self.h, self.stream)
+
+    @property
+    def nstep(self) -> int:
+        return ml_step_count(self.h)
+
+    def fields(self, mask: int = ML_ALL) -> List[np.ndarray]:
+        ncomp = bin(mask).count("1")
+        out = np.zeros((ncomp,) + self.shape, self.dtype)
+        ml_get_fields(self.h, mask, _ptr(out), False, self.stream)
+        return [out[q] for q in range(ncomp)]
+
+    def set_fields(self, f: List[np.ndarray], mask: int = ML_ALL):
+        buf = np.ascontiguousarray(np.stack([np.asarray(x, self.dtype) for x in f]))
+        ml_set_fields(self.h, mask, _ptr(buf), False, self.stream)
+
+    def molecules(self, what: int) -> np.ndarray:
+        M = self.prob.molecules.count
+        if what == ML_MOL_RHO:
+            out = np.zeros(2 * int(self.prob.molecules.H0.shape[0]))
+            ml_get_molecules(self.h, what, _ptr(out), False, self.stream)
+            return out.view(np.complex128)
+        n = {ML_MOL_EFIELD: 3 * M, ML_MOL_MUDOT: 3 * M, ML_MOL_ENERGY: M, ML_MOL_POP: ML_MAX_LEVELS * M}[what]
+        out = np.zeros(n)
+        ml_get_molecules(self.h, what, _ptr(out), False, self.stream)
+        if what in (ML_MOL_EFIELD, ML_MOL_MUDOT):
+            return out.reshape(M, 3)
+        if what == ML_MOL_POP:
+            return out.reshape(M, ML_MAX_LEVELS)
+        return out
+
+    def rho(self, m: int) -> np.ndarray:
+        pool = self.molecules(ML_MOL_RHO)
+        mol = self.prob.molecules
+        n = int(mol.nlev[m])
+        o = int(mol.off[m])
+        return pool[o:o + n * n].reshape(n, n)
+
+    def flux(self, p: int) -> np.ndarray:
+        return ml_flux(self.h, self.planes[p], len(self.prob.planes[p].omegas), self.stream)
+
+    def plane_data(self, p: int):
+        pl = self.prob.planes[p]
+        dims = [self.prob.nx, self.prob.ny, self.prob.nz]
+        nb, nc = dims[(pl.axis + 1) % 3], dims[(pl.axis + 2) % 3]
+        nf = len(pl.omegas)
+        z = ml_flux_data(self.h, self.planes[p], 4 * nf * nb * nc, self.stream)
+        cnt = nf * nb * nc
+        return [z[q * cnt:(q + 1) * cnt].reshape(nf, nc, nb) for q in range(4)]
+
+    def absorbed(self) -> float:
+        return ml_absorbed(self.h, self.stream)
+
+    def checkpoint(self) -> bytes:
+        return ml_checkpoint(self.h, self.stream)
+
+    def restore(self, blob: bytes):
+        ml_restore(self.h, blob, self.stream)

@@ -1,0 +1,174 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs, element by element.
+
+Tolerances: FP64 GPU runs agree with the oracle to round-off (relative L2 <= 1e-10;
+the summation order of the molecular current and the kernel sums differ); FP32
+runs agree within relative L2 <= 1e-4 for fields and populations.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_06173_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ml():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2512_06173_gb300 import maxlink
+    maxlink.load()
+    return maxlink
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def run_pair(ml, oracle_mod, prob, steps, precision, fields=None, molecules=True):
+    g = ml.Grid(prob, precision, molecules=molecules)
+    o = oracle_mod.OracleSim(prob, molecules=molecules)
+    if fields is not None:
+        g.set_fields(fields)
+        o.set_fields(fields)
+    g.step(steps)
+    o.step(steps)
+    g.sync()
+    return g, o
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+@pytest.mark.parametrize("shape", [(37, 21, 19), (64, 16, 9), (5, 3, 40)])
+def test_vacuum_cpml_fields(ml, oracle_mod, precision, tol, shape):
+    nx, ny, nz = shape
+    pml = tuple(min(4, n // 3) for n in (nx, nx, ny, ny, nz, nz))
+    prob = W.Problem(nx, ny, nz, 0.5, pml=pml)
+    f = W.random_fields(prob, 5)
+    g, o = run_pair(ml, oracle_mod, prob, 30, precision, fields=f)
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+@pytest.mark.parametrize("per", [(True, True, True), (True, False, True), (False, True, False)])
+def test_periodic_and_walls(ml, oracle_mod, precision, tol, per):
+    nx, ny, nz = 33, 10, 12
+    pml = tuple(0 if per[a // 2] else 3 for a in range(6))
+    prob = W.Problem(nx, ny, nz, 0.5, periodic=per, pml=pml)
+    f = W.random_fields(prob, 8)
+    g, o = run_pair(ml, oracle_mod, prob, 25, precision, fields=f)
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_thin_periodic_layer(ml, oracle_mod, precision, tol):
+    """nz = 1 periodic: the 2D limit used by the paper's superradiance example."""
+    mols = W.pack_molecules([W.tls((20.3, 17.8, 0.4), 0.25, 0.5, sigma=1.0, cg=np.sqrt(0.99), ce=0.1),
+                             W.tls((11.0, 25.5, 0.9), 0.3, 0.4, sigma=1.5, cg=np.sqrt(0.5), ce=np.sqrt(0.5))])
+    prob = W.Problem(40, 36, 1, 0.5, periodic=(False, False, True), pml=(6, 6, 6, 6, 0, 0), molecules=mols)
+    g, o = run_pair(ml, oracle_mod, prob, 120, precision)
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+    for m in range(2):
+        assert np.abs(g.rho(m) - o.rho(m)).max() < tol * 10
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_coupled_all_features(ml, oracle_mod, precision, tol, seed):
+    """eps map + design box + source sheet + flux planes + two-level and multilevel
+    Lindblad molecules on a ragged grid."""
+    prob = W.small_coupled(seed=seed, shape=(37 + seed, 22, 29))
+    g, o = run_pair(ml, oracle_mod, prob, 60, precision)
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+    for m in range(prob.molecules.count):
+        assert np.abs(g.rho(m) - o.rho(m)).max() < 10 * tol
+    pops = g.molecules(ml.ML_MOL_POP)
+    for m in range(prob.molecules.count):
+        n = int(prob.molecules.nlev[m])
+        assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+    md = g.molecules(ml.ML_MOL_MUDOT)
+    for m in range(prob.molecules.count):
+        _, omd, _ = o.mol_state(m)
+        assert np.abs(md[m] - omd).max() <= 10 * tol * max(1.0, np.abs(omd).max())
+    for p in range(len(prob.planes)):
+        fg, fo = g.flux(p), o.flux(p)
+        assert rel(fg, fo) < (1e-9 if precision == 1 else 1e-3)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_drude_sphere(ml, oracle_mod, precision, tol):
+    prob = W.small_coupled(seed=4, shape=(30, 30, 30), drude=True, eps_map=False, nmol=4, planes=False)
+    g, o = run_pair(ml, oracle_mod, prob, 80, precision)
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+    ab_g, ab_o = g.absorbed(), o.absorbed()
+    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_plain_single_emitter_trajectory(ml, oracle_mod, precision, tol):
+    """40^3 cells, one emitter at the centre, 1000 steps; excited population every
+    step and Ez along the centre line."""
+    prob = W.plain_single_emitter()
+    g = ml.Grid(prob, precision)
+    o = oracle_mod.OracleSim(prob)
+    pe_g, pe_o = [], []
+    for _ in range(1000):
+        g.step(1)
+        o.step(1)
+        pe_g.append(g.molecules(ml.ML_MOL_POP)[0, 1])
+        pe_o.append(o.rho(0)[1, 1].real)
+    assert rel(pe_g, pe_o) < tol
+    ez_g = g.fields(ml.ML_EZ)[0][:, 20, 20]
+    ez_o = o.fields()[2][:, 20, 20]
+    assert rel(ez_g, ez_o) < (tol if precision == 1 else 1e-3)
+
+
+def test_checkpoint_roundtrip(ml):
+    prob = W.small_coupled(seed=5, shape=(24, 20, 22))
+    g = ml.Grid(prob, 0)
+    g.step(17)
+    blob = g.checkpoint()
+    g.step(23)
+    a = g.fields()
+    ra = g.molecules(ml.ML_MOL_RHO)
+    fa = g.flux(0)
+    g.restore(blob)
+    assert g.nstep == 17
+    g.step(23)
+    b = g.fields()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.array_equal(ra, g.molecules(ml.ML_MOL_RHO))
+    assert np.array_equal(fa, g.flux(0))
+
+
+def test_deterministic_repeat(ml):
+    prob = W.small_coupled(seed=6, shape=(40, 24, 30))
+    outs = []
+    for _ in range(2):
+        g = ml.Grid(prob, 0)
+        g.step(40)
+        outs.append((g.fields(), g.molecules(ml.ML_MOL_RHO)))
+    for x, y in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_window_crossing_wall_rejected(ml):
+    mols = W.pack_molecules([W.tls((1.5, 8.0, 8.0), 0.25, 0.1, sigma=1.5)])
+    prob = W.Problem(16, 16, 16, 0.5, molecules=mols)
+    with pytest.raises(ml.MaxlinkError) as e:
+        ml.Grid(prob, 0)
+    assert e.value.status == ml.ML_ERR_INVALID_ARG

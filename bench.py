@@ -1,0 +1,336 @@
+"""Benchmark of the coupled Yee / molecular-ensemble step on GB300.
+
+Workload (one step = the whole hot path: molecule gather + density-matrix step +
+current scatter + fused H/E pass with CPML + DFT flux planes): the superradiant
+slab, a 256^3 vacuum grid with 10-cell CPML on every face, 10,000 two-level
+emitters (omega0 = 0.25, mu12 = 0.02 along z, sigma = 1.5 cells, pure dephasing
+1e-5) at seeded positions in a 32-cell central slab, all excited with a seeded
+1e-3 coherence, and two 8-frequency flux planes.  FP32 fields and molecules,
+FP64 DFT and energy accumulators.  Synthetic, seeded inputs.
+
+  python bench.py [--gpus N --steps K --warmup W]      our CUDA path (C ABI)
+  python bench.py --impl reference ...                  the FP64 CPU oracle
+
+Under torchrun each rank advances an independent replica (seed offset by rank);
+there is no data-path collective.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled Yee Gcell-updates/s"
+UNIT = "Gcell-updates/s"
+WORKLOAD = ("superradiant slab: 256^3 vacuum, 10-cell CPML all faces, 10000 two-level emitters "
+            "(w0=0.25, mu12=0.02 z, sigma=1.5, dephasing 1e-5) in a 32-cell central slab, "
+            "2 flux planes x 8 frequencies")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def field_pass_bytes(prob, esz: int) -> float:
+    """Algorithmic bytes of one launch of the fused field pass: E and H read and
+    written once (12 esz per cell), four CPML memory variables read and written per
+    cell and layer axis (8 esz), 1 B material index per cell if present, esz per
+    design-box cell, 6 esz per Drude cell.  Halo re-reads are not credited."""
+    import numpy as np
+    N = prob.cells
+    b = 12 * esz * N
+    dims = (prob.nx, prob.ny, prob.nz)
+    for a in range(3):
+        th = prob.pml[2 * a] + prob.pml[2 * a + 1]
+        b += 8 * esz * th * (N // dims[a])
+    if prob.mat is not None:
+        b += N
+        drude = [q for q, m in enumerate(prob.materials) if m.wp > 0]
+        if drude:
+            b += 6 * esz * int(np.isin(prob.mat, drude).sum())
+    if prob.design_box is not None:
+        x0, y0, z0, sx, sy, sz = prob.design_box
+        b += esz * sx * sy * sz
+    return float(b)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        loaded = [r for r in rows if r[9].isdigit() and int(r[9]) > 50] or rows
+        sm = [float(r[1]) for r in loaded if r[1].replace(".", "").isdigit()]
+        reasons = sorted({names[q] for r in loaded for q in range(4) if r[5 + q].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, x: float) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(world, x: float) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_run(prob, budget_s: float, max_steps: int, warm: int = 1):
+    """Time the FP64 oracle as it stands on this host's cores on the same workload."""
+    import oracle
+    sim = oracle.OracleSim(prob)
+    t0 = time.perf_counter()
+    sim.step(warm)
+    t_one = (time.perf_counter() - t0) / max(warm, 1)
+    n = max(2, min(max_steps, int(budget_s / max(t_one, 1e-6))))
+    t0 = time.perf_counter()
+    sim.step(n)
+    dt = time.perf_counter() - t0
+    return n, dt, oracle.threads()
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle, rank 0 only, bounded sample."""
+    if rank != 0:
+        return
+    from paper_2512_06173_gb300 import workloads
+    prob = workloads.superradiant_slab(n=args.edge, nmol=args.nmol, seed=2)
+    n, dt, cores = cpu_oracle_run(prob, budget_s=45.0, max_steps=args.steps, warm=max(1, min(args.warmup, 1)))
+    value = prob.cells * n / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": n, "warmup": 1, "ms_per_step": dt / n * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": prob.cells, "molecules": prob.molecules.count},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} full steps of the 256^3 workload with all 10000 emitters"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for the CUDA path")
+    torch.cuda.set_device(local)
+    prob = workloads.superradiant_slab(n=args.edge, nmol=args.nmol, seed=2 + rank)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    esz = 4
+    K, W = args.steps, args.warmup
+    # ---- device-resident timed region
+    g.step(W)
+    g.sync()
+    maxlink.ml_set_timing(g.h, True)
+    maxlink.ml_timing(g.h)  # clear
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    sampler = ClockSampler(gpu_index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    launches0 = maxlink.ml_launch_count(g.h)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(K)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    launches = maxlink.ml_launch_count(g.h) - launches0
+    ms = e0.elapsed_time(e1)
+    kms, kcnt = maxlink.ml_timing(g.h)
+    maxlink.ml_set_timing(g.h, False)
+    g.sync()
+    ms_max = allreduce_max(world, ms)
+    cells_total = allreduce_sum(world, float(prob.cells) * K)
+    value = cells_total / (ms_max / 1e3) / 1e9
+    mol_steps = allreduce_sum(world, float(prob.molecules.count) * K) / (ms_max / 1e3)
+    hbm, peak_kind = peaks()
+    k1_ms = kms[1] / max(kcnt[1], 1)
+    alg = field_pass_bytes(prob, esz)
+    achieved = alg / (k1_ms / 1e3) / 1e9
+    pe_last = g.molecules(maxlink.ML_MOL_POP)[:, 1]
+    flux = [g.flux(p) for p in range(len(prob.planes))]
+    # ---- end to end through the C ABI with host buffers
+    N = prob.cells
+    if args.no_e2e:
+        g.close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": K, "profiling_run": True}))
+        return
+    g2 = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    host_fields = torch.zeros((6, N), dtype=torch.float32, pin_memory=True)
+    host_pop = torch.zeros((prob.molecules.count * maxlink.ML_MAX_LEVELS,), dtype=torch.float64, pin_memory=True)
+    g2.step(W)
+    g2.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    maxlink.ml_set_fields(g2.h, maxlink.ML_ALL, host_fields.data_ptr(), False, sh)
+    for _ in range(K):
+        maxlink.ml_step(g2.h, 1, sh)
+        maxlink.ml_get_molecules(g2.h, maxlink.ML_MOL_POP, host_pop.data_ptr(), False, sh)
+    fl = [g2.flux(p) for p in range(len(prob.planes))]
+    stream.synchronize()
+    e2e_s = allreduce_max(world, time.perf_counter() - t0)
+    g2.sync()
+    e2e = cells_total / e2e_s / 1e9
+    h2d = 6 * N * esz / K
+    d2h = prob.molecules.count * maxlink.ML_MAX_LEVELS * 8 + sum(8 * len(p.omegas) for p in prob.planes) / K
+    g2.close()
+    # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, cores = cpu_oracle_run(prob, budget_s=args.cpu_budget, max_steps=50)
+        cpu = {"value": prob.cells * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} full steps of the same 256^3 workload (all 10000 emitters), FP64"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": prob.cells, "molecules": prob.molecules.count,
+                       "grid": [prob.nx, prob.ny, prob.nz], "l2": "inputs larger than L2 (fields 805 MB per level)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "yee_kernel (fused H/E + CPML + current scatter)",
+                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "alg_bytes_per_launch": alg,
+                         "avg_launch_ms": k1_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "molecule_steps_per_s": mol_steps,
+            "kernel_ms_per_step": {"molecules": kms[0] / K, "field_pass": kms[1] / K,
+                                   "plane_sample": kms[2] / K, "plane_fold": kms[3] / K},
+            "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
+                      "e2e_flux_plane0_f0": float(fl[0][0])},
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--edge", type=int, default=256, help="grid edge (profiling runs use a smaller cube)")
+    ap.add_argument("--nmol", type=int, default=10000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -88,6 +88,8 @@ def _load():
     L.orc_lindblad_rhs.restype = C.c_int
     L.orc_lindblad_rhs.argtypes = [P, C.c_int, dp, dp, dp]
     L.orc_pml_tables.argtypes = [P, C.c_int, dp]
+    L.orc_threads.restype = C.c_int
+    L.orc_threads.argtypes = []
     _lib = L
     return L
 
@@ -95,6 +97,10 @@ def _load():
 def _ri(z: np.ndarray) -> np.ndarray:
     z = np.ascontiguousarray(z, dtype=np.complex128)
     return np.ascontiguousarray(z.view(np.float64).ravel())
+
+
+def threads() -> int:
+    return int(_load().orc_threads())
 
 
 class OracleSim:

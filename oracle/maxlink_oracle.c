@@ -32,6 +32,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -598,6 +601,15 @@ void orc_get_psi(const osim *s, double *out) {
 }
 
 int orc_nmol(const osim *s) { return s->nmol; }
+
+/* threads the field loops run on (OpenMP), for reporting the CPU baseline */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 long orc_step_count(const osim *s) { return s->step; }
 double orc_absorbed(const osim *s) { return s->absorbed; }
 

@@ -92,6 +92,12 @@ struct ml_grid {
     void *scratch = nullptr;
     int *d_status = nullptr;
     long long step = 0;
+    // tracing: CUDA events around each launch of ml_step, per kernel class
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    struct Timed { cudaEvent_t a, b; int kind; };
+    std::vector<Timed> timed;
+    long long launches = 0;
     std::vector<void *> allocs;       // grid lifetime
     std::vector<void *> mol_allocs;   // rebuilt when molecules are added
 };
@@ -166,6 +172,8 @@ const char *ml_version(void) { return "maxlink-gb300 0.1 (sm_103a)"; }
 ml_status ml_grid_destroy(ml_grid *g) {
     if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
     cudaDeviceSynchronize();
+    for (auto &x : g->timed) { g->ev_free.push_back(x.a); g->ev_free.push_back(x.b); }
+    for (cudaEvent_t e : g->ev_free) cudaEventDestroy(e);
     for (void *p : g->mol_allocs) cudaFree(p);
     for (void *p : g->allocs) cudaFree(p);
     delete g;
@@ -580,12 +588,47 @@ ml_status ml_add_flux_plane(ml_grid *g, int axis, int index, int nfreq, const do
 
 namespace {
 
+cudaEvent_t take_event(ml_grid *g) {
+    if (!g->ev_free.empty()) {
+        cudaEvent_t e = g->ev_free.back();
+        g->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one kernel launch with events when tracing is on; count every launch.
+struct LaunchScope {
+    ml_grid *g;
+    cudaStream_t s;
+    int kind;
+    cudaEvent_t a = nullptr;
+    LaunchScope(ml_grid *g_, cudaStream_t s_, int kind_) : g(g_), s(s_), kind(kind_) {
+        g->launches++;
+        if (g->timing) {
+            a = take_event(g);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~LaunchScope() {
+        if (a) {
+            cudaEvent_t b = take_event(g);
+            cudaEventRecord(b, s);
+            g->timed.push_back({a, b, kind});
+        }
+    }
+};
+
 template <typename T>
 ml_status fold_planes(ml_grid *g, cudaStream_t s) {
     if (g->nsamp == 0) return ML_OK;
-    for (auto &p : g->planes)
+    for (auto &p : g->planes) {
+        LaunchScope ls(g, s, 3);
         CK(launch_dft_fold<T>((const T *)p.d_buf, g->nsamp, p.nb * p.nc, p.nfreq, p.d_omega, g->samp_step0, g->dt,
                               p.d_acc, s));
+    }
     g->nsamp = 0;
     return ML_OK;
 }
@@ -607,6 +650,7 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
             m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
             m.energy = g->d_energy; m.status = g->d_status;
+            LaunchScope ls(g, s, 0);
             CK(launch_molecules<T>(m, s));
         }
         YeeArgs<T> y{};
@@ -642,7 +686,10 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
         y.nsrc = (int)g->src.size();
         for (int q = 0; q < y.nsrc; q++) y.src[q] = g->src[q];
         y.step = g->step;
-        CK(launch_yee<T>(y, g->nblocks, s));
+        {
+            LaunchScope ls(g, s, 1);
+            CK(launch_yee<T>(y, g->nblocks, s));
+        }
         if (!g->planes.empty()) {
             if (g->nsamp == 0) g->samp_step0 = g->step;
             for (auto &p : g->planes) {
@@ -652,6 +699,7 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
                 for (int c = 0; c < 3; c++) { pa.E[c] = (const T *)g->F[nxt][c]; pa.H[c] = (const T *)g->F[nxt][3 + c]; }
                 pa.buf = (T *)p.d_buf;
                 pa.slot = g->nsamp;
+                LaunchScope ls(g, s, 2);
                 CK(launch_dft_sample<T>(pa, s));
             }
             g->nsamp++;
@@ -802,6 +850,34 @@ ml_status ml_sync_status(ml_grid *g, void *stream) {
 }
 
 int64_t ml_step_count(const ml_grid *g) { return g ? g->step : -1; }
+int64_t ml_launch_count(const ml_grid *g) { return g ? g->launches : -1; }
+
+ml_status ml_set_timing(ml_grid *g, int enable) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    g->timing = enable != 0;
+    return ML_OK;
+}
+
+ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    double t[4] = {0, 0, 0, 0};
+    int64_t c[4] = {0, 0, 0, 0};
+    for (auto &x : g->timed) {
+        CK(cudaEventSynchronize(x.b));
+        float f = 0.f;
+        CK(cudaEventElapsedTime(&f, x.a, x.b));
+        t[x.kind] += f;
+        c[x.kind]++;
+        g->ev_free.push_back(x.a);
+        g->ev_free.push_back(x.b);
+    }
+    g->timed.clear();
+    for (int q = 0; q < 4; q++) {
+        if (ms) ms[q] = t[q];
+        if (counts) counts[q] = c[q];
+    }
+    return ML_OK;
+}
 int ml_molecule_count(const ml_grid *g) { return g ? g->nmol : -1; }
 
 // ------------------------------------------------------------------ checkpoint

@@ -24,7 +24,7 @@ ML_MAX_LEVELS = 8
 EXPORTED = ["ml_last_error", "ml_version", "ml_grid_create", "ml_grid_destroy", "ml_add_molecules",
             "ml_add_flux_plane", "ml_step", "ml_get_fields", "ml_set_fields", "ml_get_molecules", "ml_flux",
             "ml_flux_data", "ml_absorbed", "ml_sync_status", "ml_step_count", "ml_molecule_count",
-            "ml_checkpoint", "ml_restore"]
+            "ml_checkpoint", "ml_restore", "ml_set_timing", "ml_timing", "ml_launch_count"]
 
 
 class ml_material(C.Structure):
@@ -100,6 +100,9 @@ def load(build_if_missing: bool = True):
         "ml_molecule_count": (I, [P]),
         "ml_checkpoint": (I, [P, P, C.POINTER(C.c_size_t), P]),
         "ml_restore": (I, [P, P, C.c_size_t, P]),
+        "ml_set_timing": (I, [P, I]),
+        "ml_timing": (I, [P, P, P]),
+        "ml_launch_count": (I64, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -209,6 +212,22 @@ def ml_checkpoint(h: int, stream: int = 0) -> bytes:
 def ml_restore(h: int, blob: bytes, stream: int = 0):
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().ml_restore(C.c_void_p(h), buf, len(blob), C.c_void_p(stream)))
+
+
+def ml_set_timing(h: int, enable: bool):
+    _check(load().ml_set_timing(C.c_void_p(h), int(enable)))
+
+
+def ml_timing(h: int):
+    """(ms[4], counts[4]) per kernel class: molecules, field pass, plane sample, plane fold."""
+    ms = np.zeros(4)
+    cnt = np.zeros(4, np.int64)
+    _check(load().ml_timing(C.c_void_p(h), C.c_void_p(_ptr(ms)), C.c_void_p(_ptr(cnt))))
+    return ms, cnt
+
+
+def ml_launch_count(h: int) -> int:
+    return int(load().ml_launch_count(C.c_void_p(h)))
 
 
 # ---------------------------------------------------------------- Problem wrapper

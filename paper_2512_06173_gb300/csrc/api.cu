@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -52,6 +53,8 @@ struct ml_grid {
     int pml[6] = {0, 0, 0, 0, 0, 0};
     double pml_m = 3, smax = 3.2, kmax = 1, amax = 0.05;
     int ntx = 0, nty = 0, nchunk = 0, cz = 0, nblocks = 0;
+    std::vector<int> zcut;  // chunk boundaries along z
+    int *d_zcut = nullptr;
     int px = 0, py = 0;
     long long plane = 0;
     size_t vol = 0;  // padded elements per array
@@ -85,6 +88,8 @@ struct ml_grid {
          *d_rho = nullptr, *d_w = nullptr, *d_Et = nullptr, *d_mudot = nullptr, *d_c = nullptr;
     int *d_tile_off = nullptr;
     int4 *d_tile_ent = nullptr;
+    int2 *d_plane_rng = nullptr;
+    TmapSet tm[2];
     long long n_ent = 0;
     std::vector<Plane> planes;
     int nsamp = 0;
@@ -145,6 +150,32 @@ ml_status upload_raw(std::vector<void *> &list, V **dst, const std::vector<V> &v
 }
 
 int dim(const ml_grid *g, int a) { return a == 0 ? g->nx : (a == 1 ? g->ny : g->nz); }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// TMA descriptor of one padded field array: 3D (px, py, nz+2), box BOXW x BOXH x 1.
+ml_status make_tmap(const ml_grid *g, void *base, CUtensorMap *out) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+            return fail(ML_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        fn = (EncodeTiledFn)p;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)g->px, (cuuint64_t)g->py, (cuuint64_t)(g->nz + 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)g->px * g->esz, (cuuint64_t)g->plane * g->esz};
+    cuuint32_t box[3] = {(cuuint32_t)BOXW, (cuuint32_t)BOXH, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(out, g->prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ML_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return ML_OK;
+}
 
 // Roden-Gedney CPML coefficients (Taflove & Hagness Ch. 7) at position x along axis a.
 void cpml_coeff(const ml_grid *g, int a, double x, double &b, double &c, double &ik) {
@@ -236,12 +267,36 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     g->ntx = (g->nx + TX - 1) / TX;
     g->nty = (g->ny + TY - 1) / TY;
     int tiles = g->ntx * g->nty;
-    int target = 8 * 152;
-    int nch = std::max(1, std::min((target + tiles - 1) / tiles, (g->nz + 3) / 4));
-    g->cz = (g->nz + nch - 1) / nch;
-    g->nchunk = (g->nz + g->cz - 1) / g->cz;
+    // z chunks: the z CPML layers get chunks of their own so that interior chunks
+    // take the lean path of the field pass; the interior is split evenly so that
+    // the grid has about 8 blocks per SM
+    {
+        const int target = 8 * 152;
+        const int want = std::max(1, std::min((target + tiles - 1) / tiles, (g->nz + 3) / 4));
+        const int zl = g->pml[4], zh = g->pml[5];
+        std::vector<std::pair<int, int>> seg;
+        if (zl > 0) seg.push_back({0, zl});
+        if (g->nz - zh > zl) seg.push_back({zl, g->nz - zh});
+        if (zh > 0) seg.push_back({g->nz - zh, g->nz});
+        int len = std::min(16, std::max(4, (g->nz + want - 1) / want));
+        // tuning knob: target planes per chunk (shorter chunks shrink the last
+        // wave of blocks, longer ones amortise the chunk's extra boundary plane)
+        if (const char *ev = std::getenv("ML_ZCHUNK")) {
+            const int v = std::atoi(ev);
+            if (v >= 2) len = v;
+        }
+        g->zcut.assign(1, 0);
+        for (auto &sg : seg) {
+            const int n = sg.second - sg.first;
+            const int pieces = std::max(1, (n + len - 1) / len);
+            for (int q = 1; q <= pieces; q++) g->zcut.push_back(sg.first + (int)((long long)n * q / pieces));
+        }
+        g->nchunk = (int)g->zcut.size() - 1;
+        g->cz = 0;
+        for (int c = 0; c < g->nchunk; c++) g->cz = std::max(g->cz, g->zcut[c + 1] - g->zcut[c]);
+    }
     g->nblocks = tiles * g->nchunk;
-    g->px = XO + g->ntx * TX + 4;
+    g->px = XO + g->ntx * TX + 32;
     g->py = g->nty * TY + 2;
     g->plane = (long long)g->px * g->py;
     g->vol = (size_t)g->plane * (g->nz + 2);
@@ -335,7 +390,16 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
         for (int c = 0; c < 3; c++) GA(g->JD[c], cnt * g->esz);
     }
+    for (int l = 0; l < 2; l++)
+        for (int c = 0; c < 3; c++) {
+            st = make_tmap(g, g->F[l][c], &g->tm[l].E[c]);
+            if (st != ML_OK) return bail(st);
+            st = make_tmap(g, g->F[l][3 + c], &g->tm[l].H[c]);
+            if (st != ML_OK) return bail(st);
+        }
     GA(g->absorbed_part, (size_t)g->nblocks * sizeof(double));
+    GA(g->d_zcut, g->zcut.size() * sizeof(int));
+    GC(cudaMemcpy(g->d_zcut, g->zcut.data(), g->zcut.size() * sizeof(int), cudaMemcpyHostToDevice));
     GA(g->d_scalar, 64 * sizeof(double));
     GA(g->d_status, sizeof(int));
     for (int q = 0; q < d->n_sources; q++) {
@@ -404,14 +468,16 @@ ml_status rebuild_molecules(ml_grid *g) {
             const int start = g->win[3 * m + a];
             int copies[2] = {start, start - n};
             int ncopy = g->per[a] ? 2 : 1;
-            const int T_ = a == 0 ? TX : (a == 1 ? TY : g->cz);
-            const int nblk = a == 0 ? g->ntx : (a == 1 ? g->nty : g->nchunk);
+            const int T_ = a == 0 ? TX : TY;
+            const int nblk = a == 0 ? g->ntx : g->nty;
             for (int q = 0; q < ncopy; q++) {
                 int c0 = std::max(copies[q], 0), c1 = std::min(copies[q] + Wf, n);
                 if (c0 >= c1) continue;
-                for (int b = c0 / T_; b <= (c1 - 1) / T_ && b < nblk; b++) {
-                    int base = a == 2 ? 0 : b * T_;
-                    ax[a].push_back({b, copies[q] - base});
+                if (a < 2) {
+                    for (int b = c0 / T_; b <= (c1 - 1) / T_ && b < nblk; b++) ax[a].push_back({b, copies[q] - b * T_});
+                } else {
+                    for (int b = 0; b < g->nchunk; b++)
+                        if (g->zcut[b] < c1 && g->zcut[b + 1] > c0) ax[a].push_back({b, copies[q]});
                 }
             }
         }
@@ -434,6 +500,20 @@ ml_status rebuild_molecules(ml_grid *g) {
     }
     toff[ntiles] = (int)ent.size();
     g->n_ent = (long long)ent.size();
+    // per (block, plane of its chunk): entries whose window may cover the plane,
+    // i.e. zs in (k - WMAX, k] -- a contiguous range of the zs-sorted list
+    std::vector<int2> rng((size_t)ntiles * g->cz);
+    for (int t = 0; t < ntiles; t++) {
+        const int bz = t / (g->ntx * g->nty);
+        const int4 *b0 = ent.data() + toff[t], *b1 = ent.data() + toff[t + 1];
+        for (int p = 0; p < g->cz; p++) {
+            const int k = g->zcut[bz] + p;
+            const int4 *lo = std::lower_bound(b0, b1, k - WMAX + 1, [](const int4 &e, int v) { return e.w < v; });
+            const int4 *hi = std::upper_bound(b0, b1, k, [](int v, const int4 &e) { return v < e.w; });
+            rng[(size_t)t * g->cz + p] = make_int2((int)(lo - ent.data()), (int)(hi - ent.data()));
+        }
+    }
+    CKS(upload_raw(L, &g->d_plane_rng, rng));
     CKS(upload_raw(L, &g->d_tile_off, toff));
     if (!ent.empty()) CKS(upload_raw(L, &g->d_tile_ent, ent));
     else g->d_tile_ent = nullptr;
@@ -567,6 +647,7 @@ ml_status ml_add_flux_plane(ml_grid *g, int axis, int index, int nfreq, const do
     if (index < 0 || index >= dim(g, axis)) return fail(ML_ERR_INVALID_ARG, "plane index out of range");
     if (nfreq < 1 || nfreq > ML_MAX_FREQS) return fail(ML_ERR_INVALID_ARG, "nfreq must be 1..64");
     if (g->nsamp != 0) return fail(ML_ERR_STATE, "planes must be added between folds (before stepping)");
+    if ((int)g->planes.size() >= MAXPLANES) return fail(ML_ERR_INVALID_ARG, "at most 8 flux planes");
     Plane p;
     p.axis = axis;
     p.index = index;
@@ -657,7 +738,7 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
         y.nx = g->nx; y.ny = g->ny; y.nz = g->nz; y.px = g->px; y.py = g->py; y.plane = g->plane;
         for (int a = 0; a < 3; a++) y.per[a] = g->per[a];
         for (int f = 0; f < 6; f++) y.pml[f] = g->pml[f];
-        y.ntx = g->ntx; y.nty = g->nty; y.nchunk = g->nchunk; y.cz = g->cz;
+        y.ntx = g->ntx; y.nty = g->nty; y.nchunk = g->nchunk; y.cz = g->cz; y.zcut = g->d_zcut;
         y.dt = (T)g->dt;
         for (int c = 0; c < 3; c++) {
             y.Eo[c] = (const T *)g->F[cur][c];
@@ -679,29 +760,30 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
         y.dcb = (const T *)g->dcb;
         for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
         y.absorbed_part = g->absorbed_part;
+        y.status = g->d_status;
         if (g->nmol > 0 && g->n_ent > 0) {
             y.tile_off = g->d_tile_off; y.tile_ent = g->d_tile_ent; y.mol_wf = g->d_wf;
+            y.plane_rng = g->d_plane_rng;
             y.mol_c = (const T *)g->d_c; y.mol_w = (const T *)g->d_w;
         }
         y.nsrc = (int)g->src.size();
         for (int q = 0; q < y.nsrc; q++) y.src[q] = g->src[q];
         y.step = g->step;
+        if (!g->planes.empty() && g->nsamp == 0) g->samp_step0 = g->step;
+        y.nplanes = (int)g->planes.size();
+        for (int p = 0; p < y.nplanes; p++) {
+            const Plane &pl = g->planes[p];
+            y.planes[p].axis = pl.axis;
+            y.planes[p].index = pl.index;
+            y.planes[p].nb = pl.nb;
+            y.planes[p].nc = pl.nc;
+            y.planes[p].buf = (T *)pl.d_buf + (size_t)g->nsamp * 4 * pl.nb * pl.nc;
+        }
         {
             LaunchScope ls(g, s, 1);
-            CK(launch_yee<T>(y, g->nblocks, s));
+            CK(launch_yee<T>(y, g->tm[cur], g->nblocks, s));
         }
         if (!g->planes.empty()) {
-            if (g->nsamp == 0) g->samp_step0 = g->step;
-            for (auto &p : g->planes) {
-                PlaneArgs<T> pa{};
-                pa.axis = p.axis; pa.index = p.index; pa.nb = p.nb; pa.nc = p.nc;
-                pa.px = g->px; pa.plane = g->plane;
-                for (int c = 0; c < 3; c++) { pa.E[c] = (const T *)g->F[nxt][c]; pa.H[c] = (const T *)g->F[nxt][3 + c]; }
-                pa.buf = (T *)p.d_buf;
-                pa.slot = g->nsamp;
-                LaunchScope ls(g, s, 2);
-                CK(launch_dft_sample<T>(pa, s));
-            }
             g->nsamp++;
             if (g->nsamp == DFT_KMAX) {
                 ml_status st = fold_planes<T>(g, s);

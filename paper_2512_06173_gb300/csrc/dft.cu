@@ -39,39 +39,48 @@ cudaError_t launch_dft_sample(const PlaneArgs<T> &a, cudaStream_t s) {
 }
 
 // acc: [4][nfreq][ncell] double2.  step0: step index n of the first sample (it holds
-// E at (n+1) dt and H at (n+1/2) dt).
+// E at (n+1) dt and H at (n+1/2) dt).  Sample s lies s*dt after the first, so
+//   sum_s v_s e^{i w t_s} dt = e^{i w t_0} dt * sum_s v_s e^{i w s dt}:
+// the inner K-term sum runs in the field precision T with phases rounded from FP64,
+// the product with e^{i w t_0} dt and the running sum are FP64.
 template <typename T>
 __global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
                                 double dt, double2 *acc) {
-    __shared__ double2 phE[DFT_K * ML_MAX_FREQS_DEV];
-    __shared__ double2 phH[DFT_K * ML_MAX_FREQS_DEV];
+    __shared__ T phr[DFT_K * ML_MAX_FREQS_DEV];
+    __shared__ T phi[DFT_K * ML_MAX_FREQS_DEV];
+    __shared__ double2 p0[2 * ML_MAX_FREQS_DEV];
     for (int q = threadIdx.x; q < nsamp * nfreq; q += blockDim.x) {
-        int s = q / nfreq, f = q % nfreq;
-        double tE = (double)(step0 + s + 1) * dt, tH = ((double)(step0 + s) + 0.5) * dt;
+        const int s = q / nfreq, f = q % nfreq;
         double sn, cs;
-        sincos(omega[f] * tE, &sn, &cs);
-        phE[q] = make_double2(cs * dt, sn * dt);
-        sincos(omega[f] * tH, &sn, &cs);
-        phH[q] = make_double2(cs * dt, sn * dt);
+        sincos(omega[f] * (double)s * dt, &sn, &cs);
+        phr[q] = (T)cs;
+        phi[q] = (T)sn;
+    }
+    for (int f = threadIdx.x; f < nfreq; f += blockDim.x) {
+        double sn, cs;
+        sincos(omega[f] * (double)(step0 + 1) * dt, &sn, &cs);
+        p0[f] = make_double2(cs * dt, sn * dt);
+        sincos(omega[f] * ((double)step0 + 0.5) * dt, &sn, &cs);
+        p0[ML_MAX_FREQS_DEV + f] = make_double2(cs * dt, sn * dt);
     }
     __syncthreads();
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= 4ll * ncell) return;
     const int comp = (int)(t / ncell), cell = (int)(t % ncell);
-    const double2 *ph = comp < 2 ? phE : phH;
-    double v[DFT_K];
-    for (int s = 0; s < nsamp; s++) v[s] = (double)buf[((long long)s * 4 + comp) * ncell + cell];
+    const double2 *ph0 = comp < 2 ? p0 : p0 + ML_MAX_FREQS_DEV;
+    T v[DFT_K];
+    for (int s = 0; s < nsamp; s++) v[s] = buf[((long long)s * 4 + comp) * ncell + cell];
     for (int f = 0; f < nfreq; f++) {
-        double re = 0.0, im = 0.0;
+        T re = T(0), im = T(0);
         for (int s = 0; s < nsamp; s++) {
-            double2 p = ph[s * nfreq + f];
-            re += v[s] * p.x;
-            im += v[s] * p.y;
+            re += v[s] * phr[s * nfreq + f];
+            im += v[s] * phi[s * nfreq + f];
         }
+        const double2 e0 = ph0[f];
         double2 *o = acc + ((long long)comp * nfreq + f) * ncell + cell;
         double2 x = *o;
-        x.x += re;
-        x.y += im;
+        x.x += (double)re * e0.x - (double)im * e0.y;
+        x.y += (double)re * e0.y + (double)im * e0.x;
         *o = x;
     }
 }

@@ -3,8 +3,10 @@
 // Device layout of a grid (HBM):
 //   * six field arrays per time level, E and H double-buffered (ping-pong), each
 //     padded with one ghost layer on every side: element (i,j,k), i in [-1, nx],
-//     lives at (k+1)*plane + (j+1)*px + (i+XO).  Rows start 16 bytes aligned
-//     (XO = 4 elements).  Ghosts of non-periodic axes stay 0 (PEC wall); ghosts of
+//     lives at (k+1)*plane + (j+1)*px + (i+XO).  Interior rows start 128-byte
+//     aligned (XO = 32 elements, px a multiple of 32), so every warp-wide row
+//     access covers whole cache lines and no partially written sector is left for
+//     another block to complete.  Ghosts of non-periodic axes stay 0 (PEC wall); ghosts of
 //     periodic axes are written by the owner of the mirrored cell in the same pass.
 //   * CPML memory variables only inside the layers: per axis a slab of
 //     (pml_lo + pml_hi) cells along a, two H-side components (double-buffered,
@@ -14,6 +16,7 @@
 //   * molecule tables (SoA), per-molecule separable kernel weights, and the
 //     tile-binned molecule lists that make the current scatter deterministic.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,11 +24,15 @@ namespace ml {
 
 constexpr int TX = 32;      // tile width in x (one warp)
 constexpr int TY = 8;       // tile rows in y
-constexpr int XO = 4;       // x offset of the interior in a padded row
+constexpr int RY = 1;       // rows per thread (threads per block: TX x TY/RY)
+constexpr int NTY = TY / RY;
+constexpr int NTHREADS = TX * NTY;
+constexpr int XO = 32;      // x offset of the interior in a padded row (rows start 128-byte aligned)
 constexpr int WMAX = 16;    // max kernel window per axis (2 ceil(3 sigma) + 2)
 constexpr int NW = 6 * WMAX;  // weights per molecule: [axis][stagger][WMAX]
 constexpr int MAXLEV = 8;
 constexpr int MAXSRC = 4;
+constexpr int MAXPLANES = 8;
 #define ML_MAX_FREQS_DEV 64
 constexpr int DFT_KMAX = 16;  // samples buffered per plane before a fold
 
@@ -40,13 +47,23 @@ struct cx {
 };
 
 // ------------------------------------------------------------------ field pass
+// A DFT flux plane sampled by the field pass: the two tangential E and the two
+// tangential H (averaged over the half cells on both sides) of every plane cell
+// are written to buf[4][nc*nb] (the current ring slot).
+template <typename T>
+struct PlaneDev {
+    int axis, index, nb, nc;
+    T *buf;
+};
+
 template <typename T>
 struct YeeArgs {
     int nx, ny, nz, px, py;
     long long plane;
     int per[3];
     int pml[6];
-    int ntx, nty, nchunk, cz;
+    int ntx, nty, nchunk, cz;   // cz: longest chunk (row stride of plane_rng)
+    const int *zcut;            // chunk c covers planes [zcut[c], zcut[c+1])
     T dt;
     const T *Eo[3];
     const T *Ho[3];
@@ -71,13 +88,34 @@ struct YeeArgs {
     // molecules
     const int *tile_off;    // CSR over (chunk, tile y, tile x)
     const int4 *tile_ent;   // (molecule, xs - x0, ys - y0, zs absolute)
+    const int2 *plane_rng;  // per (block, plane of the chunk): candidate entries [x, y)
     const int *mol_wf;      // packed window lengths x | y<<8 | z<<16
     const T *mol_c;         // (M,3) gamma * mudot
     const T *mol_w;         // (M, NW) weights
     int nsrc;
     SrcDev src[MAXSRC];
+    int nplanes;
+    PlaneDev<T> planes[MAXPLANES];
     long long step;
+    int *status;
 };
+
+// TMA descriptors of the six arrays of the time level the field pass reads.
+struct TmapSet {
+    CUtensorMap E[3];
+    CUtensorMap H[3];
+};
+
+constexpr int BOXW = TX + 8;   // TMA box: x0-4 .. x0+TX+3 (16-byte aligned start)
+constexpr int BOXX = XO - 4;   // padded x index of the box start minus x0
+constexpr int BOXH = TY + 2;   // rows y0-1 .. y0+TY
+constexpr int ACT_CAP = NTHREADS;
+template <typename T> constexpr int yee_stages() { return sizeof(T) == 4 ? 4 : 3; }
+template <typename T> constexpr int box_pad() { return (int)(((BOXW * BOXH * sizeof(T) + 127) / 128) * 128 / sizeof(T)); }
+template <typename T> constexpr size_t yee_smem_bytes() {
+    return 128 + (size_t)yee_stages<T>() * 6 * box_pad<T>() * sizeof(T) + 3 * (TY + 1) * (TX + 1) * sizeof(T) +
+           (size_t)ACT_CAP * (16 + 4 * sizeof(T)) + 64;
+}
 
 // ------------------------------------------------------------------ molecules
 template <typename T>
@@ -124,7 +162,7 @@ struct PlaneArgs {
 };
 
 // launchers (explicit instantiations for float and double live in the .cu files)
-template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, int nblocks, cudaStream_t s);
+template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,
                                                  const int *win, const int *wf, const int *wraw,

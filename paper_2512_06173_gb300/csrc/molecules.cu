@@ -88,20 +88,25 @@ __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<
     const int cm = a.cmask[m];
     const T *w = sh.w[wl];
     T g[3] = {T(0), T(0), T(0)};
-    const int total = Wx * Wy * Wz;
-    for (int t = lane; t < total; t += 32) {
-        const int dx = t % Wx;
-        const int r = t / Wx;
-        const int dy = r % Wy;
-        const int dz = r / Wy;
-        int x = xs + dx, y = ys + dy, z = zs + dz;
+    // lanes: dx = lane & 15, two rows (dy, dy+1) per pass; no integer division
+    const int dx = lane & 15, ly = lane >> 4;
+    if (dx < Wx) {
+        int x = xs + dx;
         if (x >= a.nx) x -= a.nx;
-        if (y >= a.ny) y -= a.ny;
-        if (z >= a.nz) z -= a.nz;
-        const long long f = fidx(a.px, a.plane, x, y, z);
-        if (cm & 1) g[0] += a.E[0][f] * (w[WMAX + dx] * w[2 * WMAX + dy] * w[4 * WMAX + dz]);
-        if (cm & 2) g[1] += a.E[1][f] * (w[dx] * w[3 * WMAX + dy] * w[4 * WMAX + dz]);
-        if (cm & 4) g[2] += a.E[2][f] * (w[dx] * w[2 * WMAX + dy] * w[5 * WMAX + dz]);
+        const T wxh = w[WMAX + dx], wxi = w[dx];
+        for (int dz = 0; dz < Wz; dz++) {
+            int z = zs + dz;
+            if (z >= a.nz) z -= a.nz;
+            const T wzi = w[4 * WMAX + dz], wzh = w[5 * WMAX + dz];
+            for (int dy = ly; dy < Wy; dy += 2) {
+                int y = ys + dy;
+                if (y >= a.ny) y -= a.ny;
+                const long long f = fidx(a.px, a.plane, x, y, z);
+                if (cm & 1) g[0] += a.E[0][f] * (wxh * w[2 * WMAX + dy] * wzi);
+                if (cm & 2) g[1] += a.E[1][f] * (wxi * w[3 * WMAX + dy] * wzi);
+                if (cm & 4) g[2] += a.E[2][f] * (wxi * w[2 * WMAX + dy] * wzh);
+            }
+        }
     }
     const T gam = a.gamma[m];
     T Et[3];

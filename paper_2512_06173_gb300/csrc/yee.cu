@@ -18,6 +18,7 @@
 // of plane k with its low halo lives in shared memory for the E update, the own
 // column's H^{n+1/2}(k-1) in registers.
 #include "ml_internal.cuh"
+#include "tma.cuh"
 
 namespace ml {
 
@@ -43,74 +44,57 @@ __device__ __forceinline__ int slab(int p, int n, int lo, int hi) {
 template <typename T>
 __device__ __forceinline__ void store_img(const YeeArgs<T> &a, T *f, int i, int j, int k, T v) {
     f[gi(a, i, j, k)] = v;
-    bool bx = a.per[0] && (i == 0 || i == a.nx - 1);
-    bool by = a.per[1] && (j == 0 || j == a.ny - 1);
-    bool bz = a.per[2] && (k == 0 || k == a.nz - 1);
+    const bool bx = a.per[0] && (i == 0 || i == a.nx - 1);
+    const bool by = a.per[1] && (j == 0 || j == a.ny - 1);
+    const bool bz = a.per[2] && (k == 0 || k == a.nz - 1);
     if (!(bx | by | bz)) return;
-    int xs[3], ys[3], zs[3];
-    int nxs = 1, nys = 1, nzs = 1;
-    xs[0] = i; ys[0] = j; zs[0] = k;
-    if (bx) { if (i == 0) xs[nxs++] = a.nx; if (i == a.nx - 1) xs[nxs++] = -1; }
-    if (by) { if (j == 0) ys[nys++] = a.ny; if (j == a.ny - 1) ys[nys++] = -1; }
-    if (bz) { if (k == 0) zs[nzs++] = a.nz; if (k == a.nz - 1) zs[nzs++] = -1; }
-    for (int c = 0; c < nzs; c++)
-        for (int b = 0; b < nys; b++)
-            for (int q = 0; q < nxs; q++)
-                if (q | b | c) f[gi(a, xs[q], ys[b], zs[c])] = v;
+    // candidate coordinates per axis: the cell itself, its image at n (if at 0),
+    // its image at -1 (if at n-1); a value of INT_MIN marks "no such image"
+    const int NONE = -0x40000000;
+    for (int c = 0; c < 3; c++) {
+        const int kk = c == 0 ? k : (c == 1 ? (bz && k == 0 ? a.nz : NONE) : (bz && k == a.nz - 1 ? -1 : NONE));
+        if (kk == NONE) continue;
+        for (int b = 0; b < 3; b++) {
+            const int jj = b == 0 ? j : (b == 1 ? (by && j == 0 ? a.ny : NONE) : (by && j == a.ny - 1 ? -1 : NONE));
+            if (jj == NONE) continue;
+            for (int q = 0; q < 3; q++) {
+                const int ii = q == 0 ? i : (q == 1 ? (bx && i == 0 ? a.nx : NONE) : (bx && i == a.nx - 1 ? -1 : NONE));
+                if (ii == NONE || (q | b | c) == 0) continue;
+                f[gi(a, ii, jj, kk)] = v;
+            }
+        }
+    }
 }
 
-// H^{n+1/2} at (i,j,k) from E^n values around it (Eq. Maxwell b) with CPML.
-// hx,hy,hz: in = H^{n-1/2}, out = H^{n+1/2}.  `own`: write CPML memory.
+// Curl differences of E^n around H cell o (Eq. Maxwell b): Ek / Ek1 point at Ex of the
+// staged planes k / k+1 (components BP apart), o = row * BOXW + col.
+// d = {dEz/dy, dEy/dz, dEx/dz, dEz/dx, dEy/dx, dEx/dy}.
+template <typename T, int BP>
+__device__ __forceinline__ void e_diffs(const T *Ek, const T *Ek1, int o, T (&d)[6]) {
+    const T ex = Ek[o], ey = Ek[BP + o], ez = Ek[2 * BP + o];
+    d[0] = Ek[2 * BP + o + BOXW] - ez;
+    d[1] = Ek1[BP + o] - ey;
+    d[2] = Ek1[o] - ex;
+    d[3] = Ek[2 * BP + o + 1] - ez;
+    d[4] = Ek[BP + o + 1] - ey;
+    d[5] = Ek[o + BOXW] - ex;
+}
+
 template <typename T>
-__device__ __forceinline__ void h_cell(const YeeArgs<T> &a, int i, int j, int k, bool own, T ex, T ey, T ez,
-                                       T ex_y1, T ex_z1, T ey_x1, T ey_z1, T ez_x1, T ez_y1, T &hx, T &hy,
-                                       T &hz) {
-    T dEz_dy = ez_y1 - ez, dEy_dz = ey_z1 - ey;
-    T dEx_dz = ex_z1 - ex, dEz_dx = ez_x1 - ez;
-    T dEy_dx = ey_x1 - ey, dEx_dy = ex_y1 - ex;
-    const int ci = canon(i, a.nx, a.per[0]), cj = canon(j, a.ny, a.per[1]), ck = canon(k, a.nz, a.per[2]);
-    if (a.pml[0] | a.pml[1]) {
-        int s = slab(ci, a.nx, a.pml[0], a.pml[1]);
-        if (s >= 0) {
-            const T *cf = a.cpml[0];
-            T b = cf[3 * a.nx + ci], c = cf[4 * a.nx + ci], kk = cf[5 * a.nx + ci];
-            long long q = ((long long)ck * a.ny + cj) * (a.pml[0] + a.pml[1]) + s;
-            T p0 = b * a.psiHo[0][0][q] + c * dEz_dx;
-            T p1 = b * a.psiHo[0][1][q] + c * dEy_dx;
-            if (own) { a.psiHn[0][0][q] = p0; a.psiHn[0][1][q] = p1; }
-            dEz_dx = kk * dEz_dx + p0;
-            dEy_dx = kk * dEy_dx + p1;
-        }
-    }
-    if (a.pml[2] | a.pml[3]) {
-        int s = slab(cj, a.ny, a.pml[2], a.pml[3]);
-        if (s >= 0) {
-            const T *cf = a.cpml[1];
-            T b = cf[3 * a.ny + cj], c = cf[4 * a.ny + cj], kk = cf[5 * a.ny + cj];
-            long long q = ((long long)ck * (a.pml[2] + a.pml[3]) + s) * a.nx + ci;
-            T p0 = b * a.psiHo[1][0][q] + c * dEz_dy;
-            T p1 = b * a.psiHo[1][1][q] + c * dEx_dy;
-            if (own) { a.psiHn[1][0][q] = p0; a.psiHn[1][1][q] = p1; }
-            dEz_dy = kk * dEz_dy + p0;
-            dEx_dy = kk * dEx_dy + p1;
-        }
-    }
-    if (a.pml[4] | a.pml[5]) {
-        int s = slab(ck, a.nz, a.pml[4], a.pml[5]);
-        if (s >= 0) {
-            const T *cf = a.cpml[2];
-            T b = cf[3 * a.nz + ck], c = cf[4 * a.nz + ck], kk = cf[5 * a.nz + ck];
-            long long q = ((long long)s * a.ny + cj) * a.nx + ci;
-            T p0 = b * a.psiHo[2][0][q] + c * dEy_dz;
-            T p1 = b * a.psiHo[2][1][q] + c * dEx_dz;
-            if (own) { a.psiHn[2][0][q] = p0; a.psiHn[2][1][q] = p1; }
-            dEy_dz = kk * dEy_dz + p0;
-            dEx_dz = kk * dEx_dz + p1;
-        }
-    }
-    hx -= a.dt * (dEz_dy - dEy_dz);
-    hy -= a.dt * (dEx_dz - dEz_dx);
-    hz -= a.dt * (dEy_dx - dEx_dy);
+__device__ __forceinline__ void h_finish(T dt, const T (&d)[6], T &hx, T &hy, T &hz) {
+    hx -= dt * (d[0] - d[1]);
+    hy -= dt * (d[2] - d[3]);
+    hz -= dt * (d[4] - d[5]);
+}
+
+// CPML recursive convolution (Roden-Gedney, Taflove & Hagness Ch. 7) on one pair of
+// curl terms whose derivative crosses a layer: psi' = b psi + c d, d' = kinv d + psi'.
+template <typename T>
+__device__ __forceinline__ void cpml_pair(T b, T c, T kinv, T &d0, T &d1, T &p0, T &p1) {
+    p0 = b * p0 + c * d0;
+    p1 = b * p1 + c * d1;
+    d0 = kinv * d0 + p0;
+    d1 = kinv * d1 + p1;
 }
 
 template <typename T>
@@ -119,246 +103,497 @@ __device__ __forceinline__ T src_value(const SrcDev &q, double t) {
     return (T)(q.amp * exp(-0.5 * u * u) * cos(q.omega * (t - q.t0)));
 }
 
+// A molecule active on the current plane: packed window starts relative to the
+// tile, packed window lengths, index, and gamma*mudot times its z weight.
 template <typename T>
-__global__ void __launch_bounds__(TX *TY) yee_kernel(const YeeArgs<T> a) {
-    __shared__ T sE[2][3][TY + 2][TX + 2];
-    __shared__ T sH[3][TY + 1][TX + 1];
+struct ActMol {
+    int xy;   // (xs & 0xffff) | (ys << 16), signed 16-bit halves
+    int wf;   // Wx | Wy << 8 (0: inactive)
+    int m;
+    int pad;
+    T f[4];
+};
+
+constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before giving up
+
+// Body of the field pass for one block.  GEN = false is the interior form: the
+// caller guarantees the tile and its halo touch no CPML layer, wall, periodic
+// image, material/source cell, molecule window or flux plane, so none of those
+// paths is compiled in.
+template <typename T, bool GEN>
+__device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &maps) {
+    constexpr int S = yee_stages<T>();
+    constexpr int BP = box_pad<T>();
+    constexpr int SW = 6 * BP;  // elements per stage
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+    T *stages = reinterpret_cast<T *>(smem_raw + 128);
+    T *sHp = stages + S * SW;
+    T(*sH)[TY + 1][TX + 1] = reinterpret_cast<T(*)[TY + 1][TX + 1]>(sHp);
+    ActMol<T> *act = reinterpret_cast<ActMol<T> *>(
+        (reinterpret_cast<uintptr_t>(sHp + 3 * (TY + 1) * (TX + 1)) + 15) & ~(uintptr_t)15);
     __shared__ T s_src[MAXSRC];
-    __shared__ int s_lo, s_hi;
-    __shared__ double s_red[TX * TY / 32];
+    __shared__ double s_red[NTHREADS / 32];
+    __shared__ T sCx[6][BOXW];  // CPML coefficients at x = x0-4+col (bE cE kE bH cH kH)
+    __shared__ T sCy[6][BOXH];  // at y = y0-1+row
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int tile = blockIdx.x;
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY;
-    const int k0 = bz * a.cz;
-    const int k1 = min(k0 + a.cz, a.nz);
-    const int i = x0 + tx, j = y0 + ty;
-    const bool inb = (i < a.nx) && (j < a.ny);
+    const int k0 = a.zcut[bz];
+    const int k1 = a.zcut[bz + 1];
+    const int i = x0 + tx;
+    const int jb = y0 + ty * RY;  // first own row; own rows jb .. jb+RY-1
+    const int q0 = k0 - 1;        // first plane of the ring
+    const int qlast = k1;         // last plane needed (z+1 neighbour of the last own plane)
+    constexpr uint32_t STAGE_BYTES = 6u * BOXW * BOXH * sizeof(T);
 
-    if (tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
-    const int mbeg = a.tile_off ? a.tile_off[tile] : 0;
-    const int mend = a.tile_off ? a.tile_off[tile + 1] : 0;
+    // block-uniform features: CPML layers this tile (with its halo) can touch,
+    // periodic ghost images to write, per-cell material work, molecular current
+    const bool fx = GEN && (a.pml[0] | a.pml[1]) && (x0 - 1 < a.pml[0] || x0 + TX > a.nx - a.pml[1]);
+    const bool fy = GEN && (a.pml[2] | a.pml[3]) && (y0 - 1 < a.pml[2] || y0 + TY > a.ny - a.pml[3]);
+    const bool zl = GEN && (a.pml[4] | a.pml[5]) != 0;
+    const bool img = GEN && ((a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
+                             (a.per[2] && (k0 == 0 || k1 == a.nz)));
+    const bool walls = GEN && ((!a.per[0] && x0 == 0) || (!a.per[1] && y0 == 0) || (!a.per[2] && k0 == 0));
+    const bool general = GEN && (a.mat != nullptr || a.dcb != nullptr || a.JD[0] != nullptr || a.nsrc > 0);
+    const bool has_mol = GEN && a.plane_rng != nullptr && a.tile_off[tile + 1] > a.tile_off[tile];
+    const T cb0 = a.mat_cb[0];
+    const int col = tx + 4;
+    const int ob = (ty * RY + 1) * BOXW + col;       // first own cell inside a staged box
+    const int gb = (jb + 1) * a.px + (i + XO);       // first own cell inside a padded plane
+    const int dxt = a.pml[0] + a.pml[1], dyt = a.pml[2] + a.pml[3];
+    const bool xin = i < a.nx;
+    // CPML slab coordinates of the own cells
+    const int ic = canon(i, a.nx, a.per[0]);
+    const int sxo = fx ? slab(ic, a.nx, a.pml[0], a.pml[1]) : -1;
+    int syo[RY];
+#pragma unroll
+    for (int r = 0; r < RY; r++) syo[r] = fy ? slab(canon(jb + r, a.ny, a.per[1]), a.ny, a.pml[2], a.pml[3]) : -1;
+    // halo cells: row y0-1 (x0..x0+TX-1) and column x0-1 (y0-1..y0+TY-1)
+    const bool halo = tid < TX + TY + 1;
+    const int hxs = tid < TX ? tid + 1 : 0, hys = tid < TX ? 0 : tid - TX;
+    const int hic = canon(x0 - 1 + hxs, a.nx, a.per[0]), hjc = canon(y0 - 1 + hys, a.ny, a.per[1]);
+    const int sxh = fx ? slab(hic, a.nx, a.pml[0], a.pml[1]) : -1;
+    const int syh = fy ? slab(hjc, a.ny, a.pml[2], a.pml[3]) : -1;
+    const int oh = hys * BOXW + hxs + 3;
+
+    if (GEN && tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
+    if (fx)
+        for (int t = tid; t < 6 * BOXW; t += NTHREADS) {
+            const int r = t / BOXW, cc = t % BOXW;
+            sCx[r][cc] = a.cpml[0][r * a.nx + canon(x0 - 4 + cc, a.nx, a.per[0])];
+        }
+    if (fy)
+        for (int t = tid; t < 6 * BOXH; t += NTHREADS) {
+            const int r = t / BOXH, rr = t % BOXH;
+            sCy[r][rr] = a.cpml[1][r * a.ny + canon(y0 - 1 + rr, a.ny, a.per[1])];
+        }
     if (tid == 0) {
-        int lo = mbeg;
-        while (lo < mend && a.tile_ent[lo].w <= k0 - WMAX) lo++;
-        s_lo = lo;
-        s_hi = lo;
+        for (int s = 0; s < S; s++) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        for (int c = 0; c < 3; c++) { prefetch_tmap(&maps.E[c]); prefetch_tmap(&maps.H[c]); }
     }
+    __syncthreads();
+    // producer: one thread issues the six tiled loads of plane q into its stage
+    auto issue = [&](int q) {
+        const int s = (q - q0) % S;
+        T *st = stages + s * SW;
+        mbar_expect_tx(&bars[s], STAGE_BYTES);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            tma_load_3d(st + c * BP, &maps.E[c], x0 + BOXX, y0, q + 1, &bars[s]);
+            tma_load_3d(st + (3 + c) * BP, &maps.H[c], x0 + BOXX, y0, q + 1, &bars[s]);
+        }
+    };
+    int issued = q0 - 1;
+    if (tid == 0)
+        for (int q = q0; q <= qlast && q < q0 + S; q++) { issue(q); issued = q; }
+    bool ok = true;
+    auto wait_stage = [&](int s, uint32_t par) {
+        if (ok && !mbar_wait_bounded(&bars[s], par, WAIT_LIMIT)) ok = false;
+    };
+    auto zslab = [&](int kc) { return zl ? slab(kc, a.nz, a.pml[4], a.pml[5]) : -1; };
+    // H-side CPML for a cell at canonical (xc, yc, kc) with slab coords sx, sy, sz;
+    // coefficient column cx (sCx) and row ry (sCy); psi read from the old level and,
+    // for an own cell, written to the new one.
+    auto h_pml = [&](T (&d)[6], int xc, int yc, int kc, int sx, int sy, int sz, int cx, int ry, bool own) {
+        if (sx >= 0) {
+            const long long q = ((long long)kc * a.ny + yc) * dxt + sx;
+            T p0 = a.psiHo[0][0][q], p1 = a.psiHo[0][1][q];
+            cpml_pair(sCx[3][cx], sCx[4][cx], sCx[5][cx], d[3], d[4], p0, p1);
+            if (own) { a.psiHn[0][0][q] = p0; a.psiHn[0][1][q] = p1; }
+        }
+        if (sy >= 0) {
+            const long long q = ((long long)kc * dyt + sy) * a.nx + xc;
+            T p0 = a.psiHo[1][0][q], p1 = a.psiHo[1][1][q];
+            cpml_pair(sCy[3][ry], sCy[4][ry], sCy[5][ry], d[0], d[5], p0, p1);
+            if (own) { a.psiHn[1][0][q] = p0; a.psiHn[1][1][q] = p1; }
+        }
+        if (sz >= 0) {
+            const long long q = ((long long)sz * a.ny + yc) * a.nx + xc;
+            const T *cf = a.cpml[2];
+            T p0 = a.psiHo[2][0][q], p1 = a.psiHo[2][1][q];
+            cpml_pair(cf[3 * a.nz + kc], cf[4 * a.nz + kc], cf[5 * a.nz + kc], d[1], d[2], p0, p1);
+            if (own) { a.psiHn[2][0][q] = p0; a.psiHn[2][1][q] = p1; }
+        }
+    };
 
     // ---- prologue: H^{n+1/2}(k0-1) of the own column (z-1 neighbour of plane k0)
-    T hpx, hpy, hpz;
+    wait_stage(0, 0);
+    wait_stage(1 % S, S == 1 ? 1u : 0u);
+    T hpx[RY], hpy[RY];
     {
-        const int km = k0 - 1;
-        T ex = a.Eo[0][gi(a, i, j, km)], ey = a.Eo[1][gi(a, i, j, km)], ez = a.Eo[2][gi(a, i, j, km)];
-        hpx = a.Ho[0][gi(a, i, j, km)];
-        hpy = a.Ho[1][gi(a, i, j, km)];
-        hpz = a.Ho[2][gi(a, i, j, km)];
-        h_cell(a, i, j, km, false, ex, ey, ez, a.Eo[0][gi(a, i, j + 1, km)], a.Eo[0][gi(a, i, j, k0)],
-               a.Eo[1][gi(a, i + 1, j, km)], a.Eo[1][gi(a, i, j, k0)], a.Eo[2][gi(a, i + 1, j, km)],
-               a.Eo[2][gi(a, i, j + 1, km)], hpx, hpy, hpz);
-    }
-    // ---- stage E^n(k0) with halo
-    constexpr int RW = TX + 2, RH = TY + 2, RN = RW * RH;
-    for (int r = tid; r < RN; r += TX * TY) {
-        int hx = r % RW, hy = r / RW;
-        long long g = gi(a, x0 - 1 + hx, y0 - 1 + hy, k0);
-        sE[0][0][hy][hx] = a.Eo[0][g];
-        sE[0][1][hy][hx] = a.Eo[1][g];
-        sE[0][2][hy][hx] = a.Eo[2][g];
-    }
-    double absorbed = 0.0;
-    int cur = 0;
-    for (int k = k0; k < k1; k++) {
-        const int nxt = cur ^ 1;
-        for (int r = tid; r < RN; r += TX * TY) {
-            int hx = r % RW, hy = r / RW;
-            long long g = gi(a, x0 - 1 + hx, y0 - 1 + hy, k + 1);
-            sE[nxt][0][hy][hx] = a.Eo[0][g];
-            sE[nxt][1][hy][hx] = a.Eo[1][g];
-            sE[nxt][2][hy][hx] = a.Eo[2][g];
-        }
-        if (tid == 0) {
-            int lo = s_lo, hi = s_hi;
-            while (lo < mend && a.tile_ent[lo].w <= k - WMAX) lo++;
-            if (hi < lo) hi = lo;
-            while (hi < mend && a.tile_ent[hi].w <= k) hi++;
-            s_lo = lo;
-            s_hi = hi;
-        }
-        __syncthreads();
-        // ---- H^{n+1/2}(k): own cell
-        T hx, hy, hz;
-        {
-            const int sx = tx + 1, sy = ty + 1;
-            long long g = gi(a, i, j, k);
-            hx = a.Ho[0][g];
-            hy = a.Ho[1][g];
-            hz = a.Ho[2][g];
-            h_cell(a, i, j, k, inb, sE[cur][0][sy][sx], sE[cur][1][sy][sx], sE[cur][2][sy][sx],
-                   sE[cur][0][sy + 1][sx], sE[nxt][0][sy][sx], sE[cur][1][sy][sx + 1], sE[nxt][1][sy][sx],
-                   sE[cur][2][sy][sx + 1], sE[cur][2][sy + 1][sx], hx, hy, hz);
-            sH[0][sy][sx] = hx;
-            sH[1][sy][sx] = hy;
-            sH[2][sy][sx] = hz;
-            if (inb) {
-                store_img(a, a.Hn[0], i, j, k, hx);
-                store_img(a, a.Hn[1], i, j, k, hy);
-                store_img(a, a.Hn[2], i, j, k, hz);
-            }
-        }
-        // ---- H^{n+1/2}(k): low halo row (y0-1) and column (x0-1), recomputed
-        if (tid < TX + TY + 1) {
-            int hxs, hys;
-            if (tid < TX) { hxs = tid + 1; hys = 0; }
-            else { hxs = 0; hys = tid - TX; }
-            const int ii = x0 - 1 + hxs, jj = y0 - 1 + hys;
-            long long g = gi(a, ii, jj, k);
-            T qx = a.Ho[0][g], qy = a.Ho[1][g], qz = a.Ho[2][g];
-            h_cell(a, ii, jj, k, false, sE[cur][0][hys][hxs], sE[cur][1][hys][hxs], sE[cur][2][hys][hxs],
-                   sE[cur][0][hys + 1][hxs], sE[nxt][0][hys][hxs], sE[cur][1][hys][hxs + 1],
-                   sE[nxt][1][hys][hxs], sE[cur][2][hys][hxs + 1], sE[cur][2][hys + 1][hxs], qx, qy, qz);
-            sH[0][hys][hxs] = qx;
-            sH[1][hys][hxs] = qy;
-            sH[2][hys][hxs] = qz;
-        }
-        __syncthreads();
-        // ---- E^{n+1}(k): own cell
-        if (inb) {
-            const int sx = tx + 1, sy = ty + 1;
-            T dHz_dy = hz - sH[2][sy - 1][sx];
-            T dHy_dz = hy - hpy;
-            T dHx_dz = hx - hpx;
-            T dHz_dx = hz - sH[2][sy][sx - 1];
-            T dHy_dx = hy - sH[1][sy][sx - 1];
-            T dHx_dy = hx - sH[0][sy - 1][sx];
-            if (a.pml[0] | a.pml[1]) {
-                int s = slab(i, a.nx, a.pml[0], a.pml[1]);
-                if (s >= 0) {
-                    const T *cf = a.cpml[0];
-                    T b = cf[i], c = cf[a.nx + i], kk = cf[2 * a.nx + i];
-                    long long q = ((long long)k * a.ny + j) * (a.pml[0] + a.pml[1]) + s;
-                    T p0 = b * a.psiE[0][0][q] + c * dHz_dx;
-                    T p1 = b * a.psiE[0][1][q] + c * dHy_dx;
-                    a.psiE[0][0][q] = p0;
-                    a.psiE[0][1][q] = p1;
-                    dHz_dx = kk * dHz_dx + p0;
-                    dHy_dx = kk * dHy_dx + p1;
-                }
-            }
-            if (a.pml[2] | a.pml[3]) {
-                int s = slab(j, a.ny, a.pml[2], a.pml[3]);
-                if (s >= 0) {
-                    const T *cf = a.cpml[1];
-                    T b = cf[j], c = cf[a.ny + j], kk = cf[2 * a.ny + j];
-                    long long q = ((long long)k * (a.pml[2] + a.pml[3]) + s) * a.nx + i;
-                    T p0 = b * a.psiE[1][0][q] + c * dHz_dy;
-                    T p1 = b * a.psiE[1][1][q] + c * dHx_dy;
-                    a.psiE[1][0][q] = p0;
-                    a.psiE[1][1][q] = p1;
-                    dHz_dy = kk * dHz_dy + p0;
-                    dHx_dy = kk * dHx_dy + p1;
-                }
-            }
-            if (a.pml[4] | a.pml[5]) {
-                int s = slab(k, a.nz, a.pml[4], a.pml[5]);
-                if (s >= 0) {
-                    const T *cf = a.cpml[2];
-                    T b = cf[k], c = cf[a.nz + k], kk = cf[2 * a.nz + k];
-                    long long q = ((long long)s * a.ny + j) * a.nx + i;
-                    T p0 = b * a.psiE[2][0][q] + c * dHy_dz;
-                    T p1 = b * a.psiE[2][1][q] + c * dHx_dz;
-                    a.psiE[2][0][q] = p0;
-                    a.psiE[2][1][q] = p1;
-                    dHy_dz = kk * dHy_dz + p0;
-                    dHx_dz = kk * dHx_dz + p1;
-                }
-            }
-            T curl[3];
-            curl[0] = dHz_dy - dHy_dz;
-            curl[1] = dHx_dz - dHz_dx;
-            curl[2] = dHy_dx - dHx_dy;
-            // molecular current (fixed order of the tile list)
-            T J[3] = {T(0), T(0), T(0)};
-            for (int e = s_lo; e < s_hi; e++) {
-                const int4 ent = a.tile_ent[e];
-                const int wf = a.mol_wf[ent.x];
-                const int dz = k - ent.w;
-                const int dx = tx - ent.y;
-                const int dy = ty - ent.z;
-                if ((unsigned)dz < (unsigned)((wf >> 16) & 0xff) && (unsigned)dx < (unsigned)(wf & 0xff) &&
-                    (unsigned)dy < (unsigned)((wf >> 8) & 0xff)) {
-                    const T *w = a.mol_w + (long long)ent.x * NW;
-                    const T *c = a.mol_c + 3ll * ent.x;
-                    const T xi = w[dx], xh = w[WMAX + dx];
-                    const T yi = w[2 * WMAX + dy], yh = w[3 * WMAX + dy];
-                    const T zi = w[4 * WMAX + dz], zh = w[5 * WMAX + dz];
-                    J[0] += c[0] * (xh * yi * zi);
-                    J[1] += c[1] * (xi * yh * zi);
-                    J[2] += c[2] * (xi * yi * zh);
-                }
-            }
-            for (int q = 0; q < a.nsrc; q++) {
-                const int idx3[3] = {i, j, k};
-                if (idx3[a.src[q].axis] == a.src[q].index) J[a.src[q].comp] += s_src[q];
-            }
-            // coefficient dt/eps
-            T cb = a.mat ? a.mat_cb[a.mat[((long long)k * a.ny + j) * a.nx + i]] : a.mat_cb[0];
-            int midx = a.mat ? a.mat[((long long)k * a.ny + j) * a.nx + i] : 0;
-            if (a.dcb && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] &&
-                j < a.dbox[1] + a.dbox[4] && k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5])
-                cb = a.dcb[((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0])];
-            bool drude = false;
-            long long jq = 0;
-            if (a.JD[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] &&
-                j < a.jbox[1] + a.jbox[4] && k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx] != T(0)) {
-                drude = true;
-                jq = ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
-            }
-            const int sx2 = tx + 1, sy2 = ty + 1;
-            const int idx3[3] = {i, j, k};
-            const long long g = gi(a, i, j, k);
+        const T *Ek = stages, *Ek1 = stages + SW;
+        const int kc = canon(q0, a.nz, a.per[2]);
+        const int sz = zslab(kc);
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const T eo = sE[cur][c][sy2][sx2];
-                T jd = T(0);
-                if (drude) {
-                    jd = a.mat_dk[midx] * a.JD[c][jq] + a.mat_db[midx] * eo;
-                    a.JD[c][jq] = jd;
-                }
-                bool forced = false;
+        for (int r = 0; r < RY; r++) {
+            const int o = ob + r * BOXW;
+            T d[6];
+            e_diffs<T, BP>(Ek, Ek1, o, d);
+            if (sxo >= 0 || syo[r] >= 0 || sz >= 0)
+                h_pml(d, ic, canon(jb + r, a.ny, a.per[1]), kc, sxo, syo[r], sz, col, ty * RY + r + 1, false);
+            T hz = Ek[5 * BP + o];
+            hpx[r] = Ek[3 * BP + o];
+            hpy[r] = Ek[4 * BP + o];
+            h_finish(a.dt, d, hpx[r], hpy[r], hz);
+        }
+    }
+    if (__syncthreads_or(!ok)) goto drain;
+    if (tid == 0 && q0 + S <= qlast) {
+        fence_proxy_async();
+        issue(q0 + S);
+        issued = q0 + S;
+    }
+    {
+        double absorbed = 0.0;
+        int sc = 1 % S;               // stage of plane k (= k0 = q0 + 1)
+        int sn = 2 % S;               // stage of plane k + 1
+        uint32_t pn = S > 2 ? 0u : 1u;  // parity of the fill of stage sn that holds plane k + 1
+        for (int k = k0; k < k1; k++) {
+            const int sz = zslab(k);
+            wait_stage(sn, pn);
+            const T *Ek = stages + sc * SW, *Ek1 = stages + sn * SW, *Hk = Ek + 3 * BP;
+            const long long pb = (long long)(k + 1) * a.plane;
+            // ---- H^{n+1/2}(k): own cells
+            T hx[RY], hy[RY], hz[RY];
 #pragma unroll
-                for (int b = 0; b < 3; b++)
-                    if (b != c && !a.per[b] && idx3[b] == 0) forced = true;
-                T en = forced ? T(0) : eo + cb * (curl[c] - J[c] - jd);
-                if (drude) absorbed += (double)jd * 0.5 * ((double)eo + (double)en) * (double)a.dt;
-                store_img(a, a.En[c], i, j, k, en);
+            for (int r = 0; r < RY; r++) {
+                const int o = ob + r * BOXW;
+                const int j = jb + r;
+                const bool own = xin && j < a.ny;
+                hx[r] = Hk[o];
+                hy[r] = Hk[BP + o];
+                hz[r] = Hk[2 * BP + o];
+                T d[6];
+                e_diffs<T, BP>(Ek, Ek1, o, d);
+                if (own && (sxo >= 0 || syo[r] >= 0 || sz >= 0))
+                    h_pml(d, i, j, k, sxo, syo[r], sz, col, ty * RY + r + 1, true);
+                h_finish(a.dt, d, hx[r], hy[r], hz[r]);
+                const int sr = ty * RY + r + 1;
+                sH[0][sr][tx + 1] = hx[r];
+                sH[1][sr][tx + 1] = hy[r];
+                sH[2][sr][tx + 1] = hz[r];
+                if (own) {
+                    if (img) {
+                        store_img(a, a.Hn[0], i, j, k, hx[r]);
+                        store_img(a, a.Hn[1], i, j, k, hy[r]);
+                        store_img(a, a.Hn[2], i, j, k, hz[r]);
+                    } else {
+                        const long long g = pb + gb + r * a.px;
+                        a.Hn[0][g] = hx[r];
+                        a.Hn[1][g] = hy[r];
+                        a.Hn[2][g] = hz[r];
+                    }
+                }
             }
-            (void)g;
+            // ---- H^{n+1/2}(k): low halo row (y0-1) and column (x0-1), recomputed
+            if (halo) {
+                T qx = Hk[oh], qy = Hk[BP + oh], qz = Hk[2 * BP + oh];
+                T d[6];
+                e_diffs<T, BP>(Ek, Ek1, oh, d);
+                if (sxh >= 0 || syh >= 0 || sz >= 0) h_pml(d, hic, hjc, k, sxh, syh, sz, hxs + 3, hys, false);
+                h_finish(a.dt, d, qx, qy, qz);
+                sH[0][hys][hxs] = qx;
+                sH[1][hys][hxs] = qy;
+                sH[2][hys][hxs] = qz;
+            }
+            // ---- molecular current of plane k, staged in batches of ACT_CAP
+            T J0[RY], J1[RY], J2[RY];
+#pragma unroll
+            for (int r = 0; r < RY; r++) J0[r] = J1[r] = J2[r] = T(0);
+            int nact = 0, lo = 0;
+            if (has_mol) {
+                const int2 rng = a.plane_rng[(long long)blockIdx.x * a.cz + (k - k0)];
+                lo = rng.x;
+                nact = rng.y - rng.x;
+            }
+            for (int base = 0;; base += ACT_CAP) {
+                const int nb = min(ACT_CAP, nact - base);
+                if (tid < nb) {
+                    const int4 ent = a.tile_ent[lo + base + tid];
+                    const int wf = a.mol_wf[ent.x];
+                    const int dz = k - ent.w;
+                    ActMol<T> am;
+                    am.xy = (ent.y & 0xffff) | (ent.z << 16);
+                    am.m = ent.x;
+                    am.pad = 0;
+                    if (dz >= 0 && dz < ((wf >> 16) & 0xff)) {
+                        const T *w = a.mol_w + (long long)ent.x * NW;
+                        const T *c = a.mol_c + 3ll * ent.x;
+                        const T zi = w[4 * WMAX + dz], zh = w[5 * WMAX + dz];
+                        am.wf = wf & 0xffff;
+                        am.f[0] = c[0] * zi;
+                        am.f[1] = c[1] * zi;
+                        am.f[2] = c[2] * zh;
+                    } else {
+                        am.wf = 0;
+                        am.f[0] = am.f[1] = am.f[2] = T(0);
+                    }
+                    am.f[3] = T(0);
+                    act[tid] = am;
+                }
+                __syncthreads();  // also publishes sH of this plane
+                if (xin) {
+                    for (int e = 0; e < nb; e++) {
+                        const int4 h = *reinterpret_cast<const int4 *>(&act[e]);
+                        const int xs = (int)(short)(h.x & 0xffff), ys = h.x >> 16;
+                        const int dx = tx - xs;
+                        if ((unsigned)dx >= (unsigned)(h.y & 0xff)) continue;
+                        const int wy = (h.y >> 8) & 0xff;
+                        const T *w = a.mol_w + (long long)h.z * NW;
+                        const T f0 = act[e].f[0], f1 = act[e].f[1], f2 = act[e].f[2];
+                        const T xi = w[dx];
+                        const bool lat = f0 != T(0) || f1 != T(0);
+                        const T xh = lat ? w[WMAX + dx] : T(0);
+#pragma unroll
+                        for (int r = 0; r < RY; r++) {
+                            const int dy = ty * RY + r - ys;
+                            if ((unsigned)dy < (unsigned)wy) {
+                                const T yi = w[2 * WMAX + dy];
+                                J2[r] += f2 * (xi * yi);
+                                if (lat) {
+                                    const T yh = w[3 * WMAX + dy];
+                                    J0[r] += f0 * (xh * yi);
+                                    J1[r] += f1 * (xi * yh);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (base + ACT_CAP >= nact) break;
+                __syncthreads();  // before the next batch overwrites act[]
+            }
+            // ---- E^{n+1}(k): own cells
+#pragma unroll
+            for (int r = 0; r < RY; r++) {
+                const int j = jb + r;
+                if (!(xin && j < a.ny)) continue;
+                const int sr = ty * RY + r + 1;
+                const int o = ob + r * BOXW;
+                T dHz_dy = hz[r] - sH[2][sr - 1][tx + 1];
+                T dHy_dz = hy[r] - hpy[r];
+                T dHx_dz = hx[r] - hpx[r];
+                T dHz_dx = hz[r] - sH[2][sr][tx];
+                T dHy_dx = hy[r] - sH[1][sr][tx];
+                T dHx_dy = hx[r] - sH[0][sr - 1][tx + 1];
+                if (sxo >= 0 || syo[r] >= 0 || sz >= 0) {
+                    if (sxo >= 0) {
+                        const long long q = ((long long)k * a.ny + j) * dxt + sxo;
+                        T p0 = a.psiE[0][0][q], p1 = a.psiE[0][1][q];
+                        cpml_pair(sCx[0][col], sCx[1][col], sCx[2][col], dHz_dx, dHy_dx, p0, p1);
+                        a.psiE[0][0][q] = p0;
+                        a.psiE[0][1][q] = p1;
+                    }
+                    if (syo[r] >= 0) {
+                        const long long q = ((long long)k * dyt + syo[r]) * a.nx + i;
+                        T p0 = a.psiE[1][0][q], p1 = a.psiE[1][1][q];
+                        cpml_pair(sCy[0][sr], sCy[1][sr], sCy[2][sr], dHz_dy, dHx_dy, p0, p1);
+                        a.psiE[1][0][q] = p0;
+                        a.psiE[1][1][q] = p1;
+                    }
+                    if (sz >= 0) {
+                        const long long q = ((long long)sz * a.ny + j) * a.nx + i;
+                        const T *cf = a.cpml[2];
+                        T p0 = a.psiE[2][0][q], p1 = a.psiE[2][1][q];
+                        cpml_pair(cf[k], cf[a.nz + k], cf[2 * a.nz + k], dHy_dz, dHx_dz, p0, p1);
+                        a.psiE[2][0][q] = p0;
+                        a.psiE[2][1][q] = p1;
+                    }
+                }
+                const T curl0 = dHz_dy - dHy_dz;
+                const T curl1 = dHx_dz - dHz_dx;
+                const T curl2 = dHy_dx - dHx_dy;
+                const T eo0 = Ek[o], eo1 = Ek[BP + o], eo2 = Ek[2 * BP + o];
+                T j0 = J0[r], j1 = J1[r], j2 = J2[r];
+                T en0, en1, en2;
+                if (!general) {
+                    en0 = eo0 + cb0 * (curl0 - j0);
+                    en1 = eo1 + cb0 * (curl1 - j1);
+                    en2 = eo2 + cb0 * (curl2 - j2);
+                } else {
+                    for (int q = 0; q < a.nsrc; q++) {
+                        const int ax = a.src[q].axis;
+                        const int pos = ax == 0 ? i : (ax == 1 ? j : k);
+                        if (pos == a.src[q].index) {
+                            const int cmp = a.src[q].comp;
+                            if (cmp == 0) j0 += s_src[q];
+                            else if (cmp == 1) j1 += s_src[q];
+                            else j2 += s_src[q];
+                        }
+                    }
+                    // coefficient dt/eps (material table or design box)
+                    const int midx = a.mat ? a.mat[((long long)k * a.ny + j) * a.nx + i] : 0;
+                    T cb = a.mat_cb[midx];
+                    if (a.dcb && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] &&
+                        j < a.dbox[1] + a.dbox[4] && k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5])
+                        cb = a.dcb[((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0])];
+                    const bool drude = a.JD[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] &&
+                                       j < a.jbox[1] + a.jbox[4] && k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] &&
+                                       a.mat_db[midx] != T(0);
+                    T jd0 = T(0), jd1 = T(0), jd2 = T(0);
+                    if (drude) {
+                        const long long jq =
+                            ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
+                        const T dk = a.mat_dk[midx], db = a.mat_db[midx];
+                        jd0 = dk * a.JD[0][jq] + db * eo0;
+                        jd1 = dk * a.JD[1][jq] + db * eo1;
+                        jd2 = dk * a.JD[2][jq] + db * eo2;
+                        a.JD[0][jq] = jd0;
+                        a.JD[1][jq] = jd1;
+                        a.JD[2][jq] = jd2;
+                    }
+                    en0 = eo0 + cb * (curl0 - j0 - jd0);
+                    en1 = eo1 + cb * (curl1 - j1 - jd1);
+                    en2 = eo2 + cb * (curl2 - j2 - jd2);
+                    if (drude)
+                        absorbed += 0.5 * (double)a.dt *
+                                    ((double)jd0 * ((double)eo0 + (double)en0) + (double)jd1 * ((double)eo1 + (double)en1) +
+                                     (double)jd2 * ((double)eo2 + (double)en2));
+                }
+                if (walls) {
+                    // tangential E on an index-0 wall stays 0 (PEC)
+                    const bool wx = !a.per[0] && i == 0, wy = !a.per[1] && j == 0, wz = !a.per[2] && k == 0;
+                    if (wy || wz) en0 = T(0);
+                    if (wx || wz) en1 = T(0);
+                    if (wx || wy) en2 = T(0);
+                }
+                if (img) {
+                    store_img(a, a.En[0], i, j, k, en0);
+                    store_img(a, a.En[1], i, j, k, en1);
+                    store_img(a, a.En[2], i, j, k, en2);
+                } else {
+                    const long long g = pb + gb + r * a.px;
+                    a.En[0][g] = en0;
+                    a.En[1][g] = en1;
+                    a.En[2][g] = en2;
+                }
+                // ---- DFT flux planes through this cell: E^{n+1} and the mean of H^{n+1/2}
+                // on both sides of the plane, written to the current sample slot
+                for (int p = 0; p < (GEN ? a.nplanes : 0); p++) {
+                    const PlaneDev<T> &pl = a.planes[p];
+                    const int ax = pl.axis;
+                    if ((ax == 0 ? i : (ax == 1 ? j : k)) != pl.index) continue;
+                    const bool zero_m = pl.index == 0 && !a.per[ax];  // H(-1) is the wall ghost (0)
+                    T eb, ec, hb, hc, hbm, hcm;
+                    int u, v;
+                    if (ax == 2) {
+                        eb = en0; ec = en1; hb = hx[r]; hc = hy[r]; hbm = hpx[r]; hcm = hpy[r]; u = i; v = j;
+                    } else if (ax == 0) {
+                        eb = en1; ec = en2; hb = hy[r]; hc = hz[r]; hbm = sH[1][sr][tx]; hcm = sH[2][sr][tx]; u = j; v = k;
+                    } else {
+                        eb = en2; ec = en0; hb = hz[r]; hc = hx[r]; hbm = sH[2][sr - 1][tx + 1]; hcm = sH[0][sr - 1][tx + 1]; u = k; v = i;
+                    }
+                    if (zero_m) { hbm = T(0); hcm = T(0); }
+                    const long long ncell = (long long)pl.nb * pl.nc, t = (long long)v * pl.nb + u;
+                    pl.buf[t] = eb;
+                    pl.buf[ncell + t] = ec;
+                    pl.buf[2 * ncell + t] = T(0.5) * (hb + hbm);
+                    pl.buf[3 * ncell + t] = T(0.5) * (hc + hcm);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RY; r++) {
+                hpx[r] = hx[r];
+                hpy[r] = hy[r];
+            }
+            if (__syncthreads_or(!ok)) goto drain;
+            // the stage of plane k is free: refill it with plane k + S
+            if (tid == 0 && k + S <= qlast) {
+                fence_proxy_async();
+                issue(k + S);
+                issued = k + S;
+            }
+            sc = sn;
+            if (++sn == S) { sn = 0; pn ^= 1u; }
         }
-        hpx = hx;
-        hpy = hy;
-        hpz = hz;
-        cur = nxt;
-        __syncthreads();
+        if (GEN && a.JD[0]) {
+            // fixed-order block reduction into this block's accumulator
+            for (int q = 16; q > 0; q >>= 1) absorbed += __shfl_xor_sync(0xffffffffu, absorbed, q);
+            if (tx == 0) s_red[ty] = absorbed;
+            __syncthreads();
+            if (tid == 0) {
+                double s = 0.0;
+                for (int q = 0; q < NTHREADS / 32; q++) s += s_red[q];
+                a.absorbed_part[blockIdx.x] += s;
+            }
+        }
+        return;
     }
-    if (a.JD[0]) {
-        // fixed-order block reduction into this block's accumulator
-        for (int o = 16; o > 0; o >>= 1) absorbed += __shfl_xor_sync(0xffffffffu, absorbed, o);
-        if (tx == 0) s_red[ty] = absorbed;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int q = 0; q < TX * TY / 32; q++) s += s_red[q];
-            a.absorbed_part[blockIdx.x] += s;
+drain:
+    // a plane never arrived: report, then wait (bounded) for the copies this block
+    // issued so that none lands in shared memory after the block has exited
+    if (tid == 0) {
+        atomicCAS(a.status, 0, 5);
+        for (int q = q0; q <= issued; q++) {
+            const int s = (q - q0) % S;
+            mbar_wait_bounded(&bars[s], (uint32_t)((q - q0) / S) & 1u, WAIT_LIMIT);
         }
     }
+    __syncthreads();
+}
+
+// True when the block's tile (with its one-cell halo) needs none of the optional
+// paths of the field pass.
+template <typename T>
+__device__ __forceinline__ bool interior_block(const YeeArgs<T> &a) {
+    const int tile = blockIdx.x;
+    const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
+    const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
+    if (a.mat || a.dcb || a.JD[0] || a.nsrc) return false;
+    if (x0 == 0 || y0 == 0 || k0 == 0 || x0 + TX >= a.nx || y0 + TY >= a.ny || k1 >= a.nz) return false;
+    if ((a.pml[0] && x0 - 1 < a.pml[0]) || (a.pml[1] && x0 + TX > a.nx - a.pml[1])) return false;
+    if ((a.pml[2] && y0 - 1 < a.pml[2]) || (a.pml[3] && y0 + TY > a.ny - a.pml[3])) return false;
+    if ((a.pml[4] && k0 - 1 < a.pml[4]) || (a.pml[5] && k1 > a.nz - a.pml[5])) return false;
+    if (a.plane_rng && a.tile_off[tile + 1] > a.tile_off[tile]) return false;
+    for (int p = 0; p < a.nplanes; p++) {
+        const int ax = a.planes[p].axis, idx = a.planes[p].index;
+        const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
+        if (idx >= lo && idx < hi) return false;
+    }
+    return true;
 }
 
 template <typename T>
-cudaError_t launch_yee(const YeeArgs<T> &a, int nblocks, cudaStream_t s) {
-    yee_kernel<T><<<nblocks, dim3(TX, TY), 0, s>>>(a);
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_kernel(const YeeArgs<T> a,
+                                                                           const __grid_constant__ TmapSet maps) {
+    if (interior_block(a)) yee_body<T, false>(a, maps);
+    else yee_body<T, true>(a, maps);
+}
+
+template <typename T>
+cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s) {
+    static bool configured = false;
+    const size_t smem = yee_smem_bytes<T>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(yee_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    yee_kernel<T><<<nblocks, dim3(TX, NTY), smem, s>>>(a, maps);
     return cudaGetLastError();
 }
 
@@ -461,7 +696,7 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
 }
 
 #define ML_INST(T)                                                                                            \
-    template cudaError_t launch_yee<T>(const YeeArgs<T> &, int, cudaStream_t);                               \
+    template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t);                               \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \
     template cudaError_t launch_zero_pec<T>(T *const *, int, int, int, int, long long, const int *, cudaStream_t);

@@ -86,11 +86,13 @@ struct ml_grid {
     double *d_pos = nullptr, *d_sigma = nullptr, *d_energy = nullptr, *d_export = nullptr;
     void *d_gamma = nullptr, *d_decay = nullptr, *d_deph = nullptr, *d_H0 = nullptr, *d_mu = nullptr,
          *d_rho = nullptr, *d_w = nullptr, *d_Et = nullptr, *d_mudot = nullptr, *d_c = nullptr;
-    int *d_tile_off = nullptr;
-    int4 *d_tile_ent = nullptr;
-    int2 *d_plane_rng = nullptr;
+    // molecular current box and the entry lists of its blocks
+    int jb0[3] = {0, 0, 0}, jbn[3] = {0, 0, 0};
+    int jnbx = 0, jnby = 0, jnb = 0, gcmask = 0;
+    int *d_joff = nullptr;
+    int4 *d_jent = nullptr;
+    void *d_J[3] = {};
     TmapSet tm[2];
-    long long n_ent = 0;
     std::vector<Plane> planes;
     int nsamp = 0;
     long long samp_step0 = 0;
@@ -100,7 +102,7 @@ struct ml_grid {
     // tracing: CUDA events around each launch of ml_step, per kernel class
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
-    struct Timed { cudaEvent_t a, b; int kind; };
+    struct Timed { cudaEvent_t a, b; int kind; };  // kind: 0 molecules 1 field 2 sample 3 fold 4 current
     std::vector<Timed> timed;
     long long launches = 0;
     std::vector<void *> allocs;       // grid lifetime
@@ -456,67 +458,68 @@ ml_status rebuild_molecules(ml_grid *g) {
                             : launch_weights<float>(M, g->d_pos, g->d_sigma, g->d_win, g->d_wf, g->d_wraw, dims,
                                                     g->per, (float *)g->d_w, 0);
     if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("weights kernel: ") + cudaGetErrorString(e));
-    // tile-binned lists: entries (m, xs - x0, ys - y0, zs) for every (tile, chunk) that
-    // the (folded) window touches, sorted by (zs, m) inside each list
-    const int ntiles = g->nblocks;
-    std::vector<std::vector<int4>> lists(ntiles);
+    // box of the molecular current: bounding box of the (folded) kernel windows;
+    // an axis on which some window wraps around a periodic boundary is taken whole
+    g->gcmask = 0;
+    for (int m = 0; m < M; m++) g->gcmask |= g->cmask[m];
+    for (int a = 0; a < 3; a++) {
+        const int n = dims[a];
+        int lo = n, hi = 0;
+        bool whole = false;
+        for (int m = 0; m < M; m++) {
+            const int Wf = (g->wf[m] >> (8 * a)) & 0xff;
+            const int st0 = g->win[3 * m + a];
+            if (st0 + Wf > n) whole = true;
+            lo = std::min(lo, st0);
+            hi = std::max(hi, st0 + Wf);
+        }
+        if (whole || M == 0) { lo = 0; hi = n; }
+        g->jb0[a] = lo;
+        g->jbn[a] = std::max(0, hi - lo);
+    }
+    g->jnbx = (g->jbn[0] + JX - 1) / JX;
+    g->jnby = (g->jbn[1] + JY - 1) / JY;
+    const int jnbz = (g->jbn[2] + JZ - 1) / JZ;
+    g->jnb = g->jnbx * g->jnby * jnbz;
+    // entries (m, window start relative to the block origin) of every block a window
+    // touches, in molecule order
+    std::vector<std::vector<int4>> lists(g->jnb);
     for (int m = 0; m < M; m++) {
         std::vector<std::pair<int, int>> ax[3];  // (block coordinate, local start)
         for (int a = 0; a < 3; a++) {
             const int n = dims[a];
             const int Wf = (g->wf[m] >> (8 * a)) & 0xff;
-            const int start = g->win[3 * m + a];
-            int copies[2] = {start, start - n};
-            int ncopy = g->per[a] ? 2 : 1;
-            const int T_ = a == 0 ? TX : TY;
-            const int nblk = a == 0 ? g->ntx : g->nty;
+            const int st0 = g->win[3 * m + a];
+            const int T_ = a == 0 ? JX : (a == 1 ? JY : JZ);
+            const int nbk = a == 0 ? g->jnbx : (a == 1 ? g->jnby : jnbz);
+            int copies[2] = {st0, st0 - n};
+            const int ncopy = g->per[a] ? 2 : 1;
             for (int q = 0; q < ncopy; q++) {
-                int c0 = std::max(copies[q], 0), c1 = std::min(copies[q] + Wf, n);
+                const int s0 = copies[q] - g->jb0[a];
+                const int c0 = std::max(s0, 0), c1 = std::min(s0 + Wf, g->jbn[a]);
                 if (c0 >= c1) continue;
-                if (a < 2) {
-                    for (int b = c0 / T_; b <= (c1 - 1) / T_ && b < nblk; b++) ax[a].push_back({b, copies[q] - b * T_});
-                } else {
-                    for (int b = 0; b < g->nchunk; b++)
-                        if (g->zcut[b] < c1 && g->zcut[b + 1] > c0) ax[a].push_back({b, copies[q]});
-                }
+                for (int b = c0 / T_; b <= (c1 - 1) / T_ && b < nbk; b++) ax[a].push_back({b, s0 - b * T_});
             }
         }
         for (auto &z : ax[2])
             for (auto &y : ax[1])
-                for (auto &x : ax[0]) {
-                    int tile = (z.first * g->nty + y.first) * g->ntx + x.first;
-                    lists[tile].push_back(make_int4(m, x.second, y.second, z.second));
-                }
+                for (auto &x : ax[0])
+                    lists[(z.first * g->jnby + y.first) * g->jnbx + x.first].push_back(make_int4(m, x.second, y.second, z.second));
     }
-    std::vector<int> toff(ntiles + 1, 0);
-    std::vector<int4> ent;
-    for (int t = 0; t < ntiles; t++) {
-        auto &l = lists[t];
-        std::stable_sort(l.begin(), l.end(), [](const int4 &a, const int4 &b) {
-            return a.w != b.w ? a.w < b.w : a.x < b.x;
-        });
-        toff[t] = (int)ent.size();
-        ent.insert(ent.end(), l.begin(), l.end());
+    std::vector<int> joff(g->jnb + 1, 0);
+    std::vector<int4> jent;
+    for (int b = 0; b < g->jnb; b++) {
+        joff[b] = (int)jent.size();
+        jent.insert(jent.end(), lists[b].begin(), lists[b].end());
     }
-    toff[ntiles] = (int)ent.size();
-    g->n_ent = (long long)ent.size();
-    // per (block, plane of its chunk): entries whose window may cover the plane,
-    // i.e. zs in (k - WMAX, k] -- a contiguous range of the zs-sorted list
-    std::vector<int2> rng((size_t)ntiles * g->cz);
-    for (int t = 0; t < ntiles; t++) {
-        const int bz = t / (g->ntx * g->nty);
-        const int4 *b0 = ent.data() + toff[t], *b1 = ent.data() + toff[t + 1];
-        for (int p = 0; p < g->cz; p++) {
-            const int k = g->zcut[bz] + p;
-            const int4 *lo = std::lower_bound(b0, b1, k - WMAX + 1, [](const int4 &e, int v) { return e.w < v; });
-            const int4 *hi = std::upper_bound(b0, b1, k, [](int v, const int4 &e) { return v < e.w; });
-            rng[(size_t)t * g->cz + p] = make_int2((int)(lo - ent.data()), (int)(hi - ent.data()));
-        }
+    joff[g->jnb] = (int)jent.size();
+    CKS(upload_raw(L, &g->d_joff, joff));
+    if (!jent.empty()) CKS(upload_raw(L, &g->d_jent, jent));
+    const size_t jvol = (size_t)g->jbn[0] * g->jbn[1] * g->jbn[2];
+    for (int c = 0; c < 3; c++) {
+        g->d_J[c] = nullptr;
+        if ((g->gcmask >> c) & 1) AL(L, g->d_J[c], jvol * g->esz);
     }
-    CKS(upload_raw(L, &g->d_plane_rng, rng));
-    CKS(upload_raw(L, &g->d_tile_off, toff));
-    if (!ent.empty()) CKS(upload_raw(L, &g->d_tile_ent, ent));
-    else g->d_tile_ent = nullptr;
     CK(cudaDeviceSynchronize());
     return ML_OK;
 #undef CKS
@@ -731,8 +734,18 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
             m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
             m.energy = g->d_energy; m.status = g->d_status;
-            LaunchScope ls(g, s, 0);
-            CK(launch_molecules<T>(m, s));
+            {
+                LaunchScope ls(g, s, 0);
+                CK(launch_molecules<T>(m, s));
+            }
+            CurArgs<T> ca{};
+            ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
+            for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
+            ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf;
+            ca.w = (const T *)g->d_w; ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
+            for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
+            LaunchScope ls(g, s, 4);
+            CK(launch_current<T>(ca, s));
         }
         YeeArgs<T> y{};
         y.nx = g->nx; y.ny = g->ny; y.nz = g->nz; y.px = g->px; y.py = g->py; y.plane = g->plane;
@@ -761,11 +774,12 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
         for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
         y.absorbed_part = g->absorbed_part;
         y.status = g->d_status;
-        if (g->nmol > 0 && g->n_ent > 0) {
-            y.tile_off = g->d_tile_off; y.tile_ent = g->d_tile_ent; y.mol_wf = g->d_wf;
-            y.plane_rng = g->d_plane_rng;
-            y.mol_c = (const T *)g->d_c; y.mol_w = (const T *)g->d_w;
-        }
+        if (g->nmol > 0)
+            for (int a = 0; a < 3; a++) {
+                y.jb0[a] = g->jb0[a];
+                y.jbn[a] = g->jbn[a];
+                y.Jb[a] = (const T *)g->d_J[a];
+            }
         y.nsrc = (int)g->src.size();
         for (int q = 0; q < y.nsrc; q++) y.src[q] = g->src[q];
         y.step = g->step;
@@ -942,8 +956,8 @@ ml_status ml_set_timing(ml_grid *g, int enable) {
 
 ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts) {
     if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
-    double t[4] = {0, 0, 0, 0};
-    int64_t c[4] = {0, 0, 0, 0};
+    double t[5] = {0, 0, 0, 0, 0};
+    int64_t c[5] = {0, 0, 0, 0, 0};
     for (auto &x : g->timed) {
         CK(cudaEventSynchronize(x.b));
         float f = 0.f;
@@ -954,7 +968,7 @@ ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts) {
         g->ev_free.push_back(x.b);
     }
     g->timed.clear();
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < 5; q++) {
         if (ms) ms[q] = t[q];
         if (counts) counts[q] = c[q];
     }

@@ -85,13 +85,9 @@ struct YeeArgs {
     int jbox[6];
     T *JD[3];             // Drude current over the Drude box
     double *absorbed_part;  // one accumulator per block
-    // molecules
-    const int *tile_off;    // CSR over (chunk, tile y, tile x)
-    const int4 *tile_ent;   // (molecule, xs - x0, ys - y0, zs absolute)
-    const int2 *plane_rng;  // per (block, plane of the chunk): candidate entries [x, y)
-    const int *mol_wf;      // packed window lengths x | y<<8 | z<<16
-    const T *mol_c;         // (M,3) gamma * mudot
-    const T *mol_w;         // (M, NW) weights
+    // molecular current on its box (written by the current kernel this step)
+    int jb0[3], jbn[3];     // box origin and extent in cells
+    const T *Jb[3];         // per component, null if no molecule has a dipole along it
     int nsrc;
     SrcDev src[MAXSRC];
     int nplanes;
@@ -109,13 +105,27 @@ struct TmapSet {
 constexpr int BOXW = TX + 8;   // TMA box: x0-4 .. x0+TX+3 (16-byte aligned start)
 constexpr int BOXX = XO - 4;   // padded x index of the box start minus x0
 constexpr int BOXH = TY + 2;   // rows y0-1 .. y0+TY
-constexpr int ACT_CAP = NTHREADS;
 template <typename T> constexpr int yee_stages() { return sizeof(T) == 4 ? 4 : 3; }
 template <typename T> constexpr int box_pad() { return (int)(((BOXW * BOXH * sizeof(T) + 127) / 128) * 128 / sizeof(T)); }
 template <typename T> constexpr size_t yee_smem_bytes() {
-    return 128 + (size_t)yee_stages<T>() * 6 * box_pad<T>() * sizeof(T) + 3 * (TY + 1) * (TX + 1) * sizeof(T) +
-           (size_t)ACT_CAP * (16 + 4 * sizeof(T)) + 64;
+    return 128 + (size_t)yee_stages<T>() * 6 * box_pad<T>() * sizeof(T) + 3 * (TY + 1) * (TX + 1) * sizeof(T) + 64;
 }
+
+// ------------------------------------------------------------------ current
+constexpr int JX = 32, JY = 8, JZ = 8;  // cells per block of the current kernel
+
+template <typename T>
+struct CurArgs {
+    int nblocks, nbx, nby;
+    int bn[3];           // box extent in cells
+    const int *off;      // CSR: entries of block b are ent[off[b] .. off[b+1])
+    const int4 *ent;     // (molecule, window start - block origin along x, y, z)
+    const int *wf;       // packed folded window lengths
+    const T *w;          // (M, NW) kernel weights
+    const T *c;          // (M, 3) gamma * mudot of this step
+    int cmask;           // components with a dipole
+    T *J[3];             // box arrays (nz, ny, nx of the box)
+};
 
 // ------------------------------------------------------------------ molecules
 template <typename T>
@@ -164,6 +174,7 @@ struct PlaneArgs {
 // launchers (explicit instantiations for float and double live in the .cu files)
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,
                                                  const int *win, const int *wf, const int *wraw,
                                                  const int *dims, const int *per, T *w, cudaStream_t s);

@@ -103,17 +103,6 @@ __device__ __forceinline__ T src_value(const SrcDev &q, double t) {
     return (T)(q.amp * exp(-0.5 * u * u) * cos(q.omega * (t - q.t0)));
 }
 
-// A molecule active on the current plane: packed window starts relative to the
-// tile, packed window lengths, index, and gamma*mudot times its z weight.
-template <typename T>
-struct ActMol {
-    int xy;   // (xs & 0xffff) | (ys << 16), signed 16-bit halves
-    int wf;   // Wx | Wy << 8 (0: inactive)
-    int m;
-    int pad;
-    T f[4];
-};
-
 constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before giving up
 
 // Body of the field pass for one block.  GEN = false is the interior form: the
@@ -130,8 +119,6 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
     T *stages = reinterpret_cast<T *>(smem_raw + 128);
     T *sHp = stages + S * SW;
     T(*sH)[TY + 1][TX + 1] = reinterpret_cast<T(*)[TY + 1][TX + 1]>(sHp);
-    ActMol<T> *act = reinterpret_cast<ActMol<T> *>(
-        (reinterpret_cast<uintptr_t>(sHp + 3 * (TY + 1) * (TX + 1)) + 15) & ~(uintptr_t)15);
     __shared__ T s_src[MAXSRC];
     __shared__ double s_red[NTHREADS / 32];
     __shared__ T sCx[6][BOXW];  // CPML coefficients at x = x0-4+col (bE cE kE bH cH kH)
@@ -159,7 +146,10 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
                              (a.per[2] && (k0 == 0 || k1 == a.nz)));
     const bool walls = GEN && ((!a.per[0] && x0 == 0) || (!a.per[1] && y0 == 0) || (!a.per[2] && k0 == 0));
     const bool general = GEN && (a.mat != nullptr || a.dcb != nullptr || a.JD[0] != nullptr || a.nsrc > 0);
-    const bool has_mol = GEN && a.plane_rng != nullptr && a.tile_off[tile + 1] > a.tile_off[tile];
+    // does the tile's column meet the box of the molecular current?
+    const bool has_mol = GEN && (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
+                         x0 + TX > a.jb0[0] && y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] &&
+                         k0 < a.jb0[2] + a.jbn[2] && k1 > a.jb0[2];
     const T cb0 = a.mat_cb[0];
     const int col = tx + 4;
     const int ob = (ty * RY + 1) * BOXW + col;       // first own cell inside a staged box
@@ -278,6 +268,25 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
             wait_stage(sn, pn);
             const T *Ek = stages + sc * SW, *Ek1 = stages + sn * SW, *Hk = Ek + 3 * BP;
             const long long pb = (long long)(k + 1) * a.plane;
+            // molecular current J^{n+1/2} of the own cells (box written by the current kernel)
+            T J0[RY], J1[RY], J2[RY];
+#pragma unroll
+            for (int r = 0; r < RY; r++) J0[r] = J1[r] = J2[r] = T(0);
+            if (has_mol) {
+                const int kr = k - a.jb0[2], xr = i - a.jb0[0];
+                if ((unsigned)kr < (unsigned)a.jbn[2] && (unsigned)xr < (unsigned)a.jbn[0]) {
+#pragma unroll
+                    for (int r = 0; r < RY; r++) {
+                        const int yr = jb + r - a.jb0[1];
+                        if ((unsigned)yr < (unsigned)a.jbn[1]) {
+                            const long long q = ((long long)kr * a.jbn[1] + yr) * a.jbn[0] + xr;
+                            if (a.Jb[0]) J0[r] = a.Jb[0][q];
+                            if (a.Jb[1]) J1[r] = a.Jb[1][q];
+                            if (a.Jb[2]) J2[r] = a.Jb[2][q];
+                        }
+                    }
+                }
+            }
             // ---- H^{n+1/2}(k): own cells
             T hx[RY], hy[RY], hz[RY];
 #pragma unroll
@@ -321,72 +330,7 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
                 sH[1][hys][hxs] = qy;
                 sH[2][hys][hxs] = qz;
             }
-            // ---- molecular current of plane k, staged in batches of ACT_CAP
-            T J0[RY], J1[RY], J2[RY];
-#pragma unroll
-            for (int r = 0; r < RY; r++) J0[r] = J1[r] = J2[r] = T(0);
-            int nact = 0, lo = 0;
-            if (has_mol) {
-                const int2 rng = a.plane_rng[(long long)blockIdx.x * a.cz + (k - k0)];
-                lo = rng.x;
-                nact = rng.y - rng.x;
-            }
-            for (int base = 0;; base += ACT_CAP) {
-                const int nb = min(ACT_CAP, nact - base);
-                if (tid < nb) {
-                    const int4 ent = a.tile_ent[lo + base + tid];
-                    const int wf = a.mol_wf[ent.x];
-                    const int dz = k - ent.w;
-                    ActMol<T> am;
-                    am.xy = (ent.y & 0xffff) | (ent.z << 16);
-                    am.m = ent.x;
-                    am.pad = 0;
-                    if (dz >= 0 && dz < ((wf >> 16) & 0xff)) {
-                        const T *w = a.mol_w + (long long)ent.x * NW;
-                        const T *c = a.mol_c + 3ll * ent.x;
-                        const T zi = w[4 * WMAX + dz], zh = w[5 * WMAX + dz];
-                        am.wf = wf & 0xffff;
-                        am.f[0] = c[0] * zi;
-                        am.f[1] = c[1] * zi;
-                        am.f[2] = c[2] * zh;
-                    } else {
-                        am.wf = 0;
-                        am.f[0] = am.f[1] = am.f[2] = T(0);
-                    }
-                    am.f[3] = T(0);
-                    act[tid] = am;
-                }
-                __syncthreads();  // also publishes sH of this plane
-                if (xin) {
-                    for (int e = 0; e < nb; e++) {
-                        const int4 h = *reinterpret_cast<const int4 *>(&act[e]);
-                        const int xs = (int)(short)(h.x & 0xffff), ys = h.x >> 16;
-                        const int dx = tx - xs;
-                        if ((unsigned)dx >= (unsigned)(h.y & 0xff)) continue;
-                        const int wy = (h.y >> 8) & 0xff;
-                        const T *w = a.mol_w + (long long)h.z * NW;
-                        const T f0 = act[e].f[0], f1 = act[e].f[1], f2 = act[e].f[2];
-                        const T xi = w[dx];
-                        const bool lat = f0 != T(0) || f1 != T(0);
-                        const T xh = lat ? w[WMAX + dx] : T(0);
-#pragma unroll
-                        for (int r = 0; r < RY; r++) {
-                            const int dy = ty * RY + r - ys;
-                            if ((unsigned)dy < (unsigned)wy) {
-                                const T yi = w[2 * WMAX + dy];
-                                J2[r] += f2 * (xi * yi);
-                                if (lat) {
-                                    const T yh = w[3 * WMAX + dy];
-                                    J0[r] += f0 * (xh * yi);
-                                    J1[r] += f1 * (xi * yh);
-                                }
-                            }
-                        }
-                    }
-                }
-                if (base + ACT_CAP >= nact) break;
-                __syncthreads();  // before the next batch overwrites act[]
-            }
+            __syncthreads();  // publishes sH of this plane
             // ---- E^{n+1}(k): own cells
 #pragma unroll
             for (int r = 0; r < RY; r++) {
@@ -568,7 +512,9 @@ __device__ __forceinline__ bool interior_block(const YeeArgs<T> &a) {
     if ((a.pml[0] && x0 - 1 < a.pml[0]) || (a.pml[1] && x0 + TX > a.nx - a.pml[1])) return false;
     if ((a.pml[2] && y0 - 1 < a.pml[2]) || (a.pml[3] && y0 + TY > a.ny - a.pml[3])) return false;
     if ((a.pml[4] && k0 - 1 < a.pml[4]) || (a.pml[5] && k1 > a.nz - a.pml[5])) return false;
-    if (a.plane_rng && a.tile_off[tile + 1] > a.tile_off[tile]) return false;
+    if ((a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] && x0 + TX > a.jb0[0] &&
+        y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] && k0 < a.jb0[2] + a.jbn[2] && k1 > a.jb0[2])
+        return false;
     for (int p = 0; p < a.nplanes; p++) {
         const int ax = a.planes[p].axis, idx = a.planes[p].index;
         const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);

@@ -219,9 +219,10 @@ def ml_set_timing(h: int, enable: bool):
 
 
 def ml_timing(h: int):
-    """(ms[4], counts[4]) per kernel class: molecules, field pass, plane sample, plane fold."""
-    ms = np.zeros(4)
-    cnt = np.zeros(4, np.int64)
+    """(ms[5], counts[5]) per kernel class: molecules, field pass, plane sample, plane fold,
+    molecular current."""
+    ms = np.zeros(5)
+    cnt = np.zeros(5, np.int64)
     _check(load().ml_timing(C.c_void_p(h), C.c_void_p(_ptr(ms)), C.c_void_p(_ptr(cnt))))
     return ms, cnt
 

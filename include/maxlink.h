@@ -183,9 +183,9 @@ int ml_molecule_count(const ml_grid *g);
 /* Per-kernel timing (tracing).  With ml_set_timing(g, 1) every kernel that
  * ml_step enqueues is bracketed by CUDA events recorded on the launching stream.
  * ml_timing synchronises those events and writes, for the kernel classes
- * {molecules, field pass, plane sampling, plane fold, molecular current}, the
- * summed milliseconds into ms[0..4] and the launch counts into counts[0..4], then
- * clears the record.
+ * {molecules, field pass, plane sampling, plane fold, molecular current, gather},
+ * the summed milliseconds into ms[0..5] and the launch counts into counts[0..5],
+ * then clears the record.
  * Either output pointer may be NULL. */
 ml_status ml_set_timing(ml_grid *g, int enable);
 ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts);

@@ -91,6 +91,16 @@ struct ml_grid {
     int jnbx = 0, jnby = 0, jnb = 0, gcmask = 0;
     int *d_joff = nullptr;
     int4 *d_jent = nullptr;
+    int *d_moff = nullptr, *d_mlist = nullptr;  // molecule -> its entries
+    // field-pass blocks split by whether they touch the current box: the others
+    // run while the gather -> molecules -> current chain runs on the side stream
+    int *d_blA = nullptr, *d_blB = nullptr;
+    int nblA = 0, nblB = 0;
+    cudaStream_t side = nullptr;
+    bool overlap = false;  // tuning (ML_OVERLAP=1): run the molecule chain beside the clear field blocks
+    cudaEvent_t ev_join = nullptr, ev_box = nullptr;
+    void *d_part = nullptr;                     // gather partials (entries, 3)
+    void *d_rec = nullptr;                      // static weight records (entries, REC)
     void *d_J[3] = {};
     TmapSet tm[2];
     std::vector<Plane> planes;
@@ -102,7 +112,7 @@ struct ml_grid {
     // tracing: CUDA events around each launch of ml_step, per kernel class
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
-    struct Timed { cudaEvent_t a, b; int kind; };  // kind: 0 molecules 1 field 2 sample 3 fold 4 current
+    struct Timed { cudaEvent_t a, b; int kind; };  // kind: 0 molecules 1 field 2 sample 3 fold 4 current 5 gather
     std::vector<Timed> timed;
     long long launches = 0;
     std::vector<void *> allocs;       // grid lifetime
@@ -207,6 +217,9 @@ ml_status ml_grid_destroy(ml_grid *g) {
     cudaDeviceSynchronize();
     for (auto &x : g->timed) { g->ev_free.push_back(x.a); g->ev_free.push_back(x.b); }
     for (cudaEvent_t e : g->ev_free) cudaEventDestroy(e);
+    if (g->side) cudaStreamDestroy(g->side);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->ev_box) cudaEventDestroy(g->ev_box);
     for (void *p : g->mol_allocs) cudaFree(p);
     for (void *p : g->allocs) cudaFree(p);
     delete g;
@@ -515,6 +528,50 @@ ml_status rebuild_molecules(ml_grid *g) {
     joff[g->jnb] = (int)jent.size();
     CKS(upload_raw(L, &g->d_joff, joff));
     if (!jent.empty()) CKS(upload_raw(L, &g->d_jent, jent));
+    // molecule -> entries (ascending entry index)
+    std::vector<int> moff(M + 1, 0), mlist(jent.size());
+    for (const int4 &e : jent) moff[e.x + 1]++;
+    for (int m = 0; m < M; m++) moff[m + 1] += moff[m];
+    {
+        std::vector<int> fill(moff.begin(), moff.end() - 1);
+        for (int e = 0; e < (int)jent.size(); e++) mlist[fill[jent[e].x]++] = e;
+    }
+    CKS(upload_raw(L, &g->d_moff, moff));
+    if (!mlist.empty()) CKS(upload_raw(L, &g->d_mlist, mlist));
+    AL(L, g->d_part, std::max<size_t>(jent.size(), 1) * 3 * g->esz);
+    AL(L, g->d_rec, std::max<size_t>(jent.size(), 1) * REC * g->esz);
+    {
+        cudaError_t e = g->prec ? launch_records<double>((int)jent.size(), g->d_jent, g->d_wf, (const double *)g->d_w,
+                                                         (double *)g->d_rec, 0)
+                                : launch_records<float>((int)jent.size(), g->d_jent, g->d_wf, (const float *)g->d_w,
+                                                        (float *)g->d_rec, 0);
+        if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("records kernel: ") + cudaGetErrorString(e));
+    }
+    // field-pass blocks whose tile (with halo) meets the current box
+    {
+        std::vector<int> A, B;
+        for (int t = 0; t < g->nblocks; t++) {
+            const int bx = t % g->ntx, by = (t / g->ntx) % g->nty, bz = t / (g->ntx * g->nty);
+            const int x0 = bx * TX, y0 = by * TY, k0 = g->zcut[bz], k1 = g->zcut[bz + 1];
+            const bool hit = g->gcmask && x0 - 1 < g->jb0[0] + g->jbn[0] && x0 + TX > g->jb0[0] &&
+                             y0 - 1 < g->jb0[1] + g->jbn[1] && y0 + TY > g->jb0[1] && k0 - 1 < g->jb0[2] + g->jbn[2] &&
+                             k1 > g->jb0[2];
+            (hit ? B : A).push_back(t);
+        }
+        g->nblA = (int)A.size();
+        g->nblB = (int)B.size();
+        if (!A.empty()) CKS(upload_raw(L, &g->d_blA, A));
+        if (!B.empty()) CKS(upload_raw(L, &g->d_blB, B));
+    }
+    if (const char *ev = std::getenv("ML_OVERLAP")) g->overlap = std::atoi(ev) != 0;
+    if (!g->side) {
+        // highest priority: the chain's short kernels take SMs as field-pass blocks retire
+        int lowest = 0, highest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lowest, &highest));
+        CK(cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, highest));
+        CK(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&g->ev_box, cudaEventDisableTiming));
+    }
     const size_t jvol = (size_t)g->jbn[0] * g->jbn[1] * g->jbn[2];
     for (int c = 0; c < 3; c++) {
         g->d_J[c] = nullptr;
@@ -721,6 +778,14 @@ template <typename T>
 ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
     for (long long it = 0; it < nsteps; it++) {
         const int cur = g->cur, nxt = cur ^ 1;
+        // the molecule chain (gather -> molecules -> current) runs on the side stream,
+        // forked from everything enqueued on s so far
+        const bool chain = g->nmol > 0 && g->overlap;
+        cudaStream_t cs = chain ? g->side : s;
+        if (chain) {
+            CK(cudaEventRecord(g->ev_box, s));
+            CK(cudaStreamWaitEvent(g->side, g->ev_box, 0));
+        }
         if (g->nmol > 0) {
             MolArgs<T> m{};
             m.nmol = g->nmol;
@@ -731,21 +796,34 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             m.gamma = (const T *)g->d_gamma; m.decay = (const T *)g->d_decay; m.dephase = (const T *)g->d_deph;
             m.H0 = (const cx<T> *)g->d_H0; m.mu = (const cx<T> *)g->d_mu; m.pool = g->pool;
             m.rho = (cx<T> *)g->d_rho;
-            m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
+            m.moff = g->d_moff; m.mlist = g->d_mlist; m.part = (const T *)g->d_part;
             m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
             m.energy = g->d_energy; m.status = g->d_status;
             {
-                LaunchScope ls(g, s, 0);
-                CK(launch_molecules<T>(m, s));
+                GathArgs<T> ga{};
+                ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
+                for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = (const T *)g->F[cur][q]; }
+                ga.px = g->px; ga.plane = g->plane;
+                ga.off = g->d_joff; ga.ent = g->d_jent; ga.rec = (const T *)g->d_rec; ga.cmask = g->d_cmask;
+                ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
+                LaunchScope ls(g, cs, 5);
+                CK(launch_gather<T>(ga, cs));
+            }
+            {
+                LaunchScope ls(g, cs, 0);
+                CK(launch_molecules<T>(m, cs));
             }
             CurArgs<T> ca{};
             ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
             for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
-            ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf;
-            ca.w = (const T *)g->d_w; ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
+            ca.off = g->d_joff; ca.ent = g->d_jent; ca.rec = (const T *)g->d_rec;
+            ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
             for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
-            LaunchScope ls(g, s, 4);
-            CK(launch_current<T>(ca, s));
+            {
+                LaunchScope ls(g, cs, 4);
+                CK(launch_current<T>(ca, cs));
+            }
+            CK(cudaEventRecord(g->ev_join, cs));
         }
         YeeArgs<T> y{};
         y.nx = g->nx; y.ny = g->ny; y.nz = g->nz; y.px = g->px; y.py = g->py; y.plane = g->plane;
@@ -793,7 +871,20 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             y.planes[p].nc = pl.nc;
             y.planes[p].buf = (T *)pl.d_buf + (size_t)g->nsamp * 4 * pl.nb * pl.nc;
         }
-        {
+        if (chain) {
+            // blocks clear of the current box overlap the chain; the others wait for J
+            if (g->nblA > 0) {
+                y.blist = g->d_blA;
+                LaunchScope ls(g, s, 1);
+                CK(launch_yee<T>(y, g->tm[cur], g->nblA, s));
+            }
+            CK(cudaStreamWaitEvent(s, g->ev_join, 0));
+            if (g->nblB > 0) {
+                y.blist = g->d_blB;
+                LaunchScope ls(g, s, 1);
+                CK(launch_yee<T>(y, g->tm[cur], g->nblB, s));
+            }
+        } else {
             LaunchScope ls(g, s, 1);
             CK(launch_yee<T>(y, g->tm[cur], g->nblocks, s));
         }
@@ -956,8 +1047,8 @@ ml_status ml_set_timing(ml_grid *g, int enable) {
 
 ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts) {
     if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
-    double t[5] = {0, 0, 0, 0, 0};
-    int64_t c[5] = {0, 0, 0, 0, 0};
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    int64_t c[6] = {0, 0, 0, 0, 0, 0};
     for (auto &x : g->timed) {
         CK(cudaEventSynchronize(x.b));
         float f = 0.f;
@@ -968,7 +1059,7 @@ ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts) {
         g->ev_free.push_back(x.b);
     }
     g->timed.clear();
-    for (int q = 0; q < 5; q++) {
+    for (int q = 0; q < 6; q++) {
         if (ms) ms[q] = t[q];
         if (counts) counts[q] = c[q];
     }

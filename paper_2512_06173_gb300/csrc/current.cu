@@ -17,53 +17,70 @@
 namespace ml {
 
 
+// Static records (setup): thread per (entry, slot).
+template <typename T>
+__global__ void records_kernel(int nent, const int4 *ent, const int *wf, const T *w, T *rec) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nent * REC) return;
+    const int e = (int)(t / REC), q = (int)(t % REC);
+    const int4 en = ent[e];
+    const int f = wf[en.x];
+    int axis, stag, d;
+    if (q < 2 * JX) { axis = 0; stag = q / JX; d = q % JX - en.y; }
+    else if (q < 2 * JX + 2 * JY) { axis = 1; stag = (q - 2 * JX) / JY; d = (q - 2 * JX) % JY - en.z; }
+    else { axis = 2; stag = (q - 2 * JX - 2 * JY) / JZ; d = (q - 2 * JX - 2 * JY) % JZ - en.w; }
+    const int W = (f >> (8 * axis)) & 0xff;
+    rec[(long long)e * REC + q] = ((unsigned)d < (unsigned)W) ? w[(long long)en.x * NW + (2 * axis + stag) * WMAX + d] : T(0);
+}
+
+template <typename T>
+cudaError_t launch_records(int nent, const int4 *ent, const int *wf, const T *w, T *rec, cudaStream_t s) {
+    if (nent == 0) return cudaSuccess;
+    const long long n = (long long)nent * REC;
+    records_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nent, ent, wf, w, rec);
+    return cudaGetLastError();
+}
+
+// Record slot offsets of component c (half-integer along c, integer elsewhere).
+__device__ __forceinline__ void rec_slots(int c, int &bx, int &ay, int &cz) {
+    bx = c == 0 ? JX : 0;
+    ay = 2 * JX + (c == 1 ? JY : 0);
+    cz = 2 * JX + 2 * JY + (c == 2 ? JZ : 0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) {
-    constexpr int JEB = sizeof(T) == 4 ? 64 : 32;  // entries staged per batch
-    __shared__ T sB[JEB][JX];
+    constexpr int JEB = sizeof(T) == 4 ? 32 : 16;  // entries staged per batch
+    __shared__ __align__(16) T sR[JEB][REC];
     __shared__ __align__(16) T sG[JEB][JY][JZ];
-    __shared__ int4 sE[JEB];
+    __shared__ T sC[JEB];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * JX + tx;
     const int blk = blockIdx.x;
-    const int bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
     const int beg = a.off[blk], end = a.off[blk + 1];
-    // box-relative cell of this thread's column
+    if (beg == end) return;  // no window here: J stays 0 (the box is zeroed at setup)
+    const int bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
     const int xr = bx * JX + tx, yr = by * JY + ty, zr0 = bz * JZ;
     for (int c = 0; c < 3; c++) {
         if (!((a.cmask >> c) & 1)) continue;
-        // staggering of component c: half-integer along c, integer elsewhere
-        const int sxo = (c == 0 ? WMAX : 0), syo = 2 * WMAX + (c == 1 ? WMAX : 0), szo = 4 * WMAX + (c == 2 ? WMAX : 0);
+        int sbx, say, scz;
+        rec_slots(c, sbx, say, scz);
         T acc[JZ];
 #pragma unroll
         for (int q = 0; q < JZ; q++) acc[q] = T(0);
         for (int base = beg; base < end; base += JEB) {
             const int nb = min(JEB, end - base);
             __syncthreads();  // previous batch fully consumed
-            if (tid < nb) sE[tid] = a.ent[base + tid];
+            for (int t = tid; t < nb * REC; t += JX * JY) sR[t / REC][t % REC] = a.rec[(long long)base * REC + t];
+            if (tid < nb) sC[tid] = a.c[3ll * a.ent[base + tid].x + c];
             __syncthreads();
-            // Bx: entry e per thread row group, column tx
-            for (int e = ty; e < nb; e += JY) {
-                const int4 en = sE[e];
-                const int wf = a.wf[en.x];
-                const int dx = tx - en.y;
-                sB[e][tx] = ((unsigned)dx < (unsigned)(wf & 0xff)) ? a.w[(long long)en.x * NW + sxo + dx] : T(0);
-            }
-            // G: entries x (JY x JZ) values
+            // G_e(y, k) = gamma mudot_e^c Ay_e(y) Cz_e(k)
             for (int t = tid; t < nb * JY * JZ; t += JX * JY) {
                 const int e = t / (JY * JZ), r = t % (JY * JZ), yy = r / JZ, zz = r % JZ;
-                const int4 en = sE[e];
-                const int wf = a.wf[en.x];
-                const int dy = yy - en.z, dz = zz - en.w;
-                T g = T(0);
-                if ((unsigned)dy < (unsigned)((wf >> 8) & 0xff) && (unsigned)dz < (unsigned)((wf >> 16) & 0xff)) {
-                    const T *w = a.w + (long long)en.x * NW;
-                    g = a.c[3ll * en.x + c] * w[syo + dy] * w[szo + dz];
-                }
-                sG[e][yy][zz] = g;
+                sG[e][yy][zz] = sC[e] * sR[e][say + yy] * sR[e][scz + zz];
             }
             __syncthreads();
             for (int e = 0; e < nb; e++) {
-                const T b = sB[e][tx];
+                const T b = sR[e][sbx + tx];
 #pragma unroll
                 for (int q = 0; q < JZ; q++) acc[q] += b * sG[e][ty][q];
             }
@@ -79,6 +96,74 @@ __global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) {
     }
 }
 
+// Gather (Eq. E_regu_Emi), the transpose of the current kernel over the same
+// blocks, entry lists and records: the block stages E^n of its JX x JY x JZ cells
+// (coalesced), then one warp per entry forms, lane x,
+//     T(x) = sum_k Cz_e(k) sum_y Ay_e(y) E(x, y, k)
+// and reduces sum_x Bx_e(x) T(x) with a fixed xor-shuffle tree.  The partial of
+// entry e and component c goes to part[e][c]; nothing is accumulated across
+// blocks here, so the result does not depend on scheduling.
+template <typename T>
+__global__ void __launch_bounds__(JX *JY) gather_kernel(const GathArgs<T> a) {
+    constexpr int JEB = sizeof(T) == 4 ? 32 : 16;
+    __shared__ __align__(16) T sE[JZ][JY][JX];
+    __shared__ __align__(16) T sR[JEB][REC];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * JX + tx;
+    const int blk = blockIdx.x;
+    const int beg = a.off[blk], end = a.off[blk + 1];
+    if (beg == end) return;
+    const int bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+    const int xr = bx * JX + tx, yr0 = by * JY, zr0 = bz * JZ;
+    for (int c = 0; c < 3; c++) {
+        if (!((a.gcmask >> c) & 1)) continue;
+        int sbx, say, scz;
+        rec_slots(c, sbx, say, scz);
+        __syncthreads();  // sE of the previous component consumed
+        for (int q = ty; q < JY * JZ; q += JY) {
+            const int yy = q % JY, zz = q / JY;
+            const int yr = yr0 + yy, zr = zr0 + zz;
+            T v = T(0);
+            if (xr < a.bn[0] && yr < a.bn[1] && zr < a.bn[2]) {
+                const long long g = (long long)(a.b0[2] + zr + 1) * a.plane + (long long)(a.b0[1] + yr + 1) * a.px +
+                                    (a.b0[0] + xr + XO);
+                v = a.E[c][g];
+            }
+            sE[zz][yy][tx] = v;
+        }
+        for (int base = beg; base < end; base += JEB) {
+            const int nb = min(JEB, end - base);
+            __syncthreads();  // previous batch consumed (and sE written)
+            for (int t = tid; t < nb * REC; t += JX * JY) sR[t / REC][t % REC] = a.rec[(long long)base * REC + t];
+            __syncthreads();
+            for (int e = ty; e < nb; e += JY) {
+                const int m = a.ent[base + e].x;
+                T v = T(0);
+                if ((a.cmask[m] >> c) & 1) {
+                    T t = T(0);
+#pragma unroll
+                    for (int zz = 0; zz < JZ; zz++) {
+                        T u = T(0);
+#pragma unroll
+                        for (int yy = 0; yy < JY; yy++) u += sR[e][say + yy] * sE[zz][yy][tx];
+                        t += sR[e][scz + zz] * u;
+                    }
+                    v = sR[e][sbx + tx] * t;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (tx == 0) a.part[3ll * (base + e) + c] = v;
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s) {
+    if (a.nblocks == 0) return cudaSuccess;
+    gather_kernel<T><<<a.nblocks, dim3(JX, JY), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s) {
     if (a.nblocks == 0) return cudaSuccess;
@@ -86,7 +171,11 @@ cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template cudaError_t launch_current<float>(const CurArgs<float> &, cudaStream_t);
-template cudaError_t launch_current<double>(const CurArgs<double> &, cudaStream_t);
+#define ML_INST(T)                                                                                 \
+    template cudaError_t launch_current<T>(const CurArgs<T> &, cudaStream_t);                      \
+    template cudaError_t launch_gather<T>(const GathArgs<T> &, cudaStream_t);                      \
+    template cudaError_t launch_records<T>(int, const int4 *, const int *, const T *, T *, cudaStream_t);
+ML_INST(float)
+ML_INST(double)
 
 }  // namespace ml

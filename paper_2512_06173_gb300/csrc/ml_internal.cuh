@@ -62,7 +62,8 @@ struct YeeArgs {
     long long plane;
     int per[3];
     int pml[6];
-    int ntx, nty, nchunk, cz;   // cz: longest chunk (row stride of plane_rng)
+    int ntx, nty, nchunk, cz;   // cz: longest chunk
+    const int *blist;           // blocks of this launch (tile indices), or null for all
     const int *zcut;            // chunk c covers planes [zcut[c], zcut[c+1])
     T dt;
     const T *Eo[3];
@@ -113,6 +114,11 @@ template <typename T> constexpr size_t yee_smem_bytes() {
 
 // ------------------------------------------------------------------ current
 constexpr int JX = 32, JY = 8, JZ = 8;  // cells per block of the current kernel
+// Static record of one (block, molecule window) entry: the molecule's 1D kernel
+// weights at the block's own cells, zero outside the window:
+//   [0,32) Bx integer-x  [32,64) Bx half-x  [64,72) Ay integer-y  [72,80) Ay half-y
+//   [80,88) Cz integer-z  [88,96) Cz half-z
+constexpr int REC = 2 * JX + 2 * JY + 2 * JZ;
 
 template <typename T>
 struct CurArgs {
@@ -120,11 +126,29 @@ struct CurArgs {
     int bn[3];           // box extent in cells
     const int *off;      // CSR: entries of block b are ent[off[b] .. off[b+1])
     const int4 *ent;     // (molecule, window start - block origin along x, y, z)
-    const int *wf;       // packed folded window lengths
-    const T *w;          // (M, NW) kernel weights
+    const T *rec;        // (entries, REC) static weight records
     const T *c;          // (M, 3) gamma * mudot of this step
     int cmask;           // components with a dipole
     T *J[3];             // box arrays (nz, ny, nx of the box)
+};
+
+// Gather partials: for every (box block, entry) the field sum of the entry's kernel
+// window inside the block, per component; the molecule kernel adds a molecule's
+// partials in list order.
+template <typename T>
+struct GathArgs {
+    int nblocks, nbx, nby;
+    int bn[3];           // box extent in cells
+    int b0[3];           // box origin in grid cells
+    int px;              // padded field layout
+    long long plane;
+    const int *off;
+    const int4 *ent;
+    const T *rec;        // (entries, REC) static weight records
+    const int *cmask;    // per molecule
+    int gcmask;          // components staged
+    const T *E[3];       // E^n (padded)
+    T *part;             // (entries, 3)
 };
 
 // ------------------------------------------------------------------ molecules
@@ -148,9 +172,9 @@ struct MolArgs {
     const cx<T> *mu;       // 3 pools back to back
     long long pool;
     cx<T> *rho;
-    const int *win;        // (M,3) window starts
-    const int *wf;         // packed window lengths
-    const T *w;            // (M, NW)
+    const int *moff;       // CSR over molecules: partial-sum entries of molecule m
+    const int *mlist;      //   are mlist[moff[m] .. moff[m+1]]
+    const T *part;         // (entries, 3) gather partials of this step
     T *Et;
     T *mudot;
     T *c;
@@ -175,6 +199,9 @@ struct PlaneArgs {
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_records(int nent, const int4 *ent, const int *wf, const T *w, T *rec,
+                                                 cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,
                                                  const int *win, const int *wf, const int *wraw,
                                                  const int *dims, const int *per, T *w, cudaStream_t s);

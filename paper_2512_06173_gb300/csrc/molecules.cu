@@ -1,7 +1,7 @@
 // K2: one warp per molecule, once per time step.
 //   1. regularised field Etilde_m^c = gamma_m sum_window E^c kappa_m^c
-//      (Eq. E_regu_Emi), lanes striding over the (folded) kernel window, combined
-//      by a fixed xor-shuffle tree (deterministic);
+//      (Eq. E_regu_Emi): the sum of the molecule's gather partials (one per box
+//      block its window touches, written by the gather kernel), in list order;
 //   2. density-matrix step under H0 - Etilde . mu held over dt (Eq.
 //      von-Neumann-tls): closed-form 2x2 exponential, or classic RK4 substeps of
 //      the GKSL equation with ladder decay and pure dephasing written element-wise;
@@ -40,7 +40,6 @@ constexpr int MOL_WARPS = 4;
 
 template <typename T>
 struct MolShared {
-    T w[MOL_WARPS][NW];
     cx<T> H[MOL_WARPS][MAXLEV * MAXLEV];
     cx<T> S[MOL_WARPS][2][MAXLEV * MAXLEV];
 };
@@ -79,114 +78,107 @@ __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<
     const int m = blockIdx.x * MOL_WARPS + wl;
     if (m >= a.nmol) return;  // whole warp leaves together
 
-    // ---- 1. gather
-    for (int q = lane; q < NW; q += 32) sh.w[wl][q] = a.w[(long long)m * NW + q];
-    __syncwarp();
-    const int wfp = a.wf[m];
-    const int Wx = wfp & 0xff, Wy = (wfp >> 8) & 0xff, Wz = (wfp >> 16) & 0xff;
-    const int xs = a.win[3 * m], ys = a.win[3 * m + 1], zs = a.win[3 * m + 2];
+    // ---- 0. every load of this molecule's data, issued before any is used
+    const int n = a.nlev[m];
+    const int nn = n * n;
+    const long long o = a.off[m];
     const int cm = a.cmask[m];
-    const T *w = sh.w[wl];
-    T g[3] = {T(0), T(0), T(0)};
-    // lanes: dx = lane & 15, two rows (dy, dy+1) per pass; no integer division
-    const int dx = lane & 15, ly = lane >> 4;
-    if (dx < Wx) {
-        int x = xs + dx;
-        if (x >= a.nx) x -= a.nx;
-        const T wxh = w[WMAX + dx], wxi = w[dx];
-        for (int dz = 0; dz < Wz; dz++) {
-            int z = zs + dz;
-            if (z >= a.nz) z -= a.nz;
-            const T wzi = w[4 * WMAX + dz], wzh = w[5 * WMAX + dz];
-            for (int dy = ly; dy < Wy; dy += 2) {
-                int y = ys + dy;
-                if (y >= a.ny) y -= a.ny;
-                const long long f = fidx(a.px, a.plane, x, y, z);
-                if (cm & 1) g[0] += a.E[0][f] * (wxh * w[2 * WMAX + dy] * wzi);
-                if (cm & 2) g[1] += a.E[1][f] * (wxi * w[3 * WMAX + dy] * wzi);
-                if (cm & 4) g[2] += a.E[2][f] * (wxi * w[2 * WMAX + dy] * wzh);
-            }
-        }
-    }
+    const int kind = a.kind[m];
     const T gam = a.gamma[m];
+    // lane owns density-matrix elements e = lane and e = lane + 32 (row-major n x n)
+    cx<T> r0[2], h0[2], mu[3][2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int e = lane + 32 * q;
+        const bool in = e < nn;
+        r0[q] = in ? a.rho[o + e] : cx<T>{T(0), T(0)};
+        h0[q] = in ? a.H0[o + e] : cx<T>{T(0), T(0)};
+#pragma unroll
+        for (int c = 0; c < 3; c++) mu[c][q] = (in && ((cm >> c) & 1)) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
+    }
+    __syncwarp();
+
+    // ---- 1. regularised field: this molecule's gather partials, added lane-strided
+    // in list order and combined by a fixed xor tree
+    T g[3] = {T(0), T(0), T(0)};
+    for (int t = a.moff[m] + lane; t < a.moff[m + 1]; t += 32) {
+        const T *pp = a.part + 3ll * a.mlist[t];
+        g[0] += pp[0];
+        g[1] += pp[1];
+        g[2] += pp[2];
+    }
     T Et[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) Et[c] = gam * warp_sum(g[c]);
 
-    // ---- 2. density-matrix step
-    const int n = a.nlev[m];
-    const int nn = n * n;
-    const long long o = a.off[m];
+    // ---- 2. H = H0 - Etilde . mu and <mu> before the step.  For Hermitian
+    // operators Re Tr(rho A) = sum_jl Re(rho_jl conj(A_jl)): own elements only.
     cx<T> *Hs = sh.H[wl];
-    for (int e = lane; e < nn; e += 32) {
-        cx<T> h = a.H0[o + e];
-        for (int c = 0; c < 3; c++) {
-            cx<T> mu = a.mu[c * a.pool + o + e];
-            h.re -= Et[c] * mu.re;
-            h.im -= Et[c] * mu.im;
-        }
-        Hs[e] = h;
-    }
-    // <mu> before
     T mu0[3] = {T(0), T(0), T(0)};
-    cx<T> r0[2];
+#pragma unroll
     for (int q = 0; q < 2; q++) {
-        int e = lane + 32 * q;
-        r0[q] = e < nn ? a.rho[o + e] : cx<T>{T(0), T(0)};
+        const int e = lane + 32 * q;
         if (e < nn) {
-            int jj = e / n, ll = e % n;
+            cx<T> h = h0[q];
+#pragma unroll
             for (int c = 0; c < 3; c++) {
-                cx<T> mu = a.mu[c * a.pool + o + ll * n + jj];
-                mu0[c] += r0[q].re * mu.re - r0[q].im * mu.im;
+                h.re -= Et[c] * mu[c][q].re;
+                h.im -= Et[c] * mu[c][q].im;
+                mu0[c] += r0[q].re * mu[c][q].re + r0[q].im * mu[c][q].im;
             }
+            Hs[e] = h;
         }
     }
+#pragma unroll
     for (int c = 0; c < 3; c++) mu0[c] = warp_sum(mu0[c]);
     __syncwarp();
+
+    // ---- 3. density-matrix step over dt with the field held
     cx<T> r1[2] = {r0[0], r0[1]};
-    if (a.kind[m] == 0) {
-        // exact exponential of a 2x2 Hermitian H held over dt
+    if (kind == 0) {
+        // exact exponential of a 2x2 Hermitian H:
+        // U = e^{-i hbar dt}[cos(W dt) - i sin(W dt)/W (H - hbar)], the phase cancels in U rho U^+
+        // gather rho (elements 0..3 live on lanes 0..3) into shared memory first
+        if (lane < 4) sh.S[wl][0][lane] = r0[0];
+        __syncwarp();
         if (lane == 0) {
             const T dt = a.dt;
-            T ha = Hs[0].re, hd = Hs[3].re;
-            cx<T> b = Hs[1];
-            T hbar = T(0.5) * (ha + hd), z = T(0.5) * (ha - hd);
-            T W = sqrt(z * z + b.re * b.re + b.im * b.im);
-            T cw = cos(W * dt);
-            T sw = W > T(0) ? sin(W * dt) / W : dt;
-            (void)hbar;  // global phase cancels in U rho U^+
+            const T ha = Hs[0].re, hd = Hs[3].re;
+            const cx<T> b = Hs[1];
+            const T z = T(0.5) * (ha - hd);
+            const T W = sqrt(z * z + b.re * b.re + b.im * b.im);
+            const T cw = cos(W * dt);
+            const T sw = W > T(0) ? sin(W * dt) / W : dt;
             cx<T> U[4];
             U[0] = {cw, -sw * z};
-            U[1] = {sw * b.im, -sw * b.re};       // -i sw b
-            U[2] = {-sw * b.im, -sw * b.re};      // -i sw conj(b)
+            U[1] = {sw * b.im, -sw * b.re};   // -i sw b
+            U[2] = {-sw * b.im, -sw * b.re};  // -i sw conj(b)
             U[3] = {cw, sw * z};
             cx<T> R[4];
-            for (int e = 0; e < 4; e++) R[e] = a.rho[o + e];
+            for (int e = 0; e < 4; e++) R[e] = sh.S[wl][0][e];
             cx<T> TT[4], out[4];
             for (int p = 0; p < 2; p++)
                 for (int q = 0; q < 2; q++)
                     TT[p * 2 + q] = cadd(cmul(U[p * 2 + 0], R[0 * 2 + q]), cmul(U[p * 2 + 1], R[1 * 2 + q]));
             for (int p = 0; p < 2; p++)
                 for (int q = 0; q < 2; q++)
-                    out[p * 2 + q] = cadd(cmul(TT[p * 2 + 0], cconj(U[q * 2 + 0])), cmul(TT[p * 2 + 1], cconj(U[q * 2 + 1])));
-            for (int e = 0; e < 4; e++) sh.S[wl][0][e] = out[e];
+                    out[p * 2 + q] =
+                        cadd(cmul(TT[p * 2 + 0], cconj(U[q * 2 + 0])), cmul(TT[p * 2 + 1], cconj(U[q * 2 + 1])));
+            for (int e = 0; e < 4; e++) sh.S[wl][1][e] = out[e];
         }
         __syncwarp();
-        for (int q = 0; q < 2; q++) {
-            int e = lane + 32 * q;
-            if (e < nn) r1[q] = sh.S[wl][0][e];
-        }
+        if (lane < 4) r1[0] = sh.S[wl][1][lane];
     } else {
         const int ns = a.nsub[m];
         const T h = a.dt / T(ns);
         const T decay = a.decay[m], deph = a.dephase[m];
+        const int e0 = lane, e1 = lane + 32;
+        const int j0 = e0 / n, l0 = e0 - j0 * n, j1 = e1 / n, l1 = e1 - j1 * n;
         for (int sstep = 0; sstep < ns; sstep++) {
             cx<T> base[2] = {r1[0], r1[1]};
             cx<T> acc[2] = {{T(0), T(0)}, {T(0), T(0)}};
-            for (int q = 0; q < 2; q++) {
-                int e = lane + 32 * q;
-                if (e < nn) sh.S[wl][0][e] = base[q];
-            }
+            if (e0 < nn) sh.S[wl][0][e0] = base[0];
+            if (e1 < nn) sh.S[wl][0][e1] = base[1];
             __syncwarp();
             int sb = 0;
 #pragma unroll 1
@@ -194,19 +186,19 @@ __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<
                 const T wgt = (st == 0 || st == 3) ? T(1) : T(2);
                 const T cn = (st < 2) ? T(0.5) : T(1);
                 cx<T> f[2];
-                for (int q = 0; q < 2; q++) {
-                    int e = lane + 32 * q;
-                    if (e < nn) {
-                        f[q] = rhs_elem(n, e / n, e % n, sh.S[wl][sb], Hs, decay, deph);
-                        acc[q].re += wgt * f[q].re;
-                        acc[q].im += wgt * f[q].im;
-                    }
+                if (e0 < nn) {
+                    f[0] = rhs_elem(n, j0, l0, sh.S[wl][sb], Hs, decay, deph);
+                    acc[0].re += wgt * f[0].re;
+                    acc[0].im += wgt * f[0].im;
+                }
+                if (e1 < nn) {
+                    f[1] = rhs_elem(n, j1, l1, sh.S[wl][sb], Hs, decay, deph);
+                    acc[1].re += wgt * f[1].re;
+                    acc[1].im += wgt * f[1].im;
                 }
                 if (st < 3) {
-                    for (int q = 0; q < 2; q++) {
-                        int e = lane + 32 * q;
-                        if (e < nn) sh.S[wl][sb ^ 1][e] = {base[q].re + cn * h * f[q].re, base[q].im + cn * h * f[q].im};
-                    }
+                    if (e0 < nn) sh.S[wl][sb ^ 1][e0] = {base[0].re + cn * h * f[0].re, base[0].im + cn * h * f[0].im};
+                    if (e1 < nn) sh.S[wl][sb ^ 1][e1] = {base[1].re + cn * h * f[1].re, base[1].im + cn * h * f[1].im};
                     sb ^= 1;
                     __syncwarp();
                 }
@@ -218,28 +210,26 @@ __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<
             __syncwarp();
         }
     }
-    // ---- 3. <mu> after, mudot, energy
+    // ---- 4. <mu> after, mudot, current amplitude, energy
     T mu1[3] = {T(0), T(0), T(0)};
     T en = T(0);
+#pragma unroll
     for (int q = 0; q < 2; q++) {
-        int e = lane + 32 * q;
+        const int e = lane + 32 * q;
         if (e < nn) {
             a.rho[o + e] = r1[q];
-            int jj = e / n, ll = e % n;
-            for (int c = 0; c < 3; c++) {
-                cx<T> mu = a.mu[c * a.pool + o + ll * n + jj];
-                mu1[c] += r1[q].re * mu.re - r1[q].im * mu.im;
-            }
-            cx<T> h0 = a.H0[o + ll * n + jj];
-            en += r1[q].re * h0.re - r1[q].im * h0.im;
+#pragma unroll
+            for (int c = 0; c < 3; c++) mu1[c] += r1[q].re * mu[c][q].re + r1[q].im * mu[c][q].im;
+            en += r1[q].re * h0[q].re + r1[q].im * h0[q].im;
         }
     }
     en = warp_sum(en);
+#pragma unroll
     for (int c = 0; c < 3; c++) mu1[c] = warp_sum(mu1[c]);
     if (lane == 0) {
         bool bad = false;
         for (int c = 0; c < 3; c++) {
-            T md = (mu1[c] - mu0[c]) / a.dt;
+            const T md = (mu1[c] - mu0[c]) / a.dt;
             a.Et[3 * m + c] = Et[c];
             a.mudot[3 * m + c] = md;
             a.c[3 * m + c] = gam * md;

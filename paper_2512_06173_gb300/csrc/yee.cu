@@ -126,7 +126,7 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
-    const int tile = blockIdx.x;
+    const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY;
     const int k0 = a.zcut[bz];
@@ -206,28 +206,28 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
         if (ok && !mbar_wait_bounded(&bars[s], par, WAIT_LIMIT)) ok = false;
     };
     auto zslab = [&](int kc) { return zl ? slab(kc, a.nz, a.pml[4], a.pml[5]) : -1; };
-    // H-side CPML for a cell at canonical (xc, yc, kc) with slab coords sx, sy, sz;
-    // coefficient column cx (sCx) and row ry (sCy); psi read from the old level and,
-    // for an own cell, written to the new one.
-    auto h_pml = [&](T (&d)[6], int xc, int yc, int kc, int sx, int sy, int sz, int cx, int ry, bool own) {
+    // H-side CPML memory of a cell at canonical (xc, yc, kc) with slab coordinates
+    // sx, sy, sz: old values (p = {x0, x1, y0, y1, z0, z1}) loaded ahead of use
+    auto h_pml_load = [&](T (&p)[6], int xc, int yc, int kc, int sx, int sy, int sz) {
+        if (sx >= 0) { const long long q = ((long long)kc * a.ny + yc) * dxt + sx; p[0] = a.psiHo[0][0][q]; p[1] = a.psiHo[0][1][q]; }
+        if (sy >= 0) { const long long q = ((long long)kc * dyt + sy) * a.nx + xc; p[2] = a.psiHo[1][0][q]; p[3] = a.psiHo[1][1][q]; }
+        if (sz >= 0) { const long long q = ((long long)sz * a.ny + yc) * a.nx + xc; p[4] = a.psiHo[2][0][q]; p[5] = a.psiHo[2][1][q]; }
+    };
+    // apply the recursion (coefficient column cx of sCx, row ry of sCy) and, for an
+    // own cell, store the new memory in the other time level
+    auto h_pml = [&](T (&d)[6], T (&p)[6], int xc, int yc, int kc, int sx, int sy, int sz, int cx, int ry, bool own) {
         if (sx >= 0) {
-            const long long q = ((long long)kc * a.ny + yc) * dxt + sx;
-            T p0 = a.psiHo[0][0][q], p1 = a.psiHo[0][1][q];
-            cpml_pair(sCx[3][cx], sCx[4][cx], sCx[5][cx], d[3], d[4], p0, p1);
-            if (own) { a.psiHn[0][0][q] = p0; a.psiHn[0][1][q] = p1; }
+            cpml_pair(sCx[3][cx], sCx[4][cx], sCx[5][cx], d[3], d[4], p[0], p[1]);
+            if (own) { const long long q = ((long long)kc * a.ny + yc) * dxt + sx; a.psiHn[0][0][q] = p[0]; a.psiHn[0][1][q] = p[1]; }
         }
         if (sy >= 0) {
-            const long long q = ((long long)kc * dyt + sy) * a.nx + xc;
-            T p0 = a.psiHo[1][0][q], p1 = a.psiHo[1][1][q];
-            cpml_pair(sCy[3][ry], sCy[4][ry], sCy[5][ry], d[0], d[5], p0, p1);
-            if (own) { a.psiHn[1][0][q] = p0; a.psiHn[1][1][q] = p1; }
+            cpml_pair(sCy[3][ry], sCy[4][ry], sCy[5][ry], d[0], d[5], p[2], p[3]);
+            if (own) { const long long q = ((long long)kc * dyt + sy) * a.nx + xc; a.psiHn[1][0][q] = p[2]; a.psiHn[1][1][q] = p[3]; }
         }
         if (sz >= 0) {
-            const long long q = ((long long)sz * a.ny + yc) * a.nx + xc;
             const T *cf = a.cpml[2];
-            T p0 = a.psiHo[2][0][q], p1 = a.psiHo[2][1][q];
-            cpml_pair(cf[3 * a.nz + kc], cf[4 * a.nz + kc], cf[5 * a.nz + kc], d[1], d[2], p0, p1);
-            if (own) { a.psiHn[2][0][q] = p0; a.psiHn[2][1][q] = p1; }
+            cpml_pair(cf[3 * a.nz + kc], cf[4 * a.nz + kc], cf[5 * a.nz + kc], d[1], d[2], p[4], p[5]);
+            if (own) { const long long q = ((long long)sz * a.ny + yc) * a.nx + xc; a.psiHn[2][0][q] = p[4]; a.psiHn[2][1][q] = p[5]; }
         }
     };
 
@@ -244,8 +244,12 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
             const int o = ob + r * BOXW;
             T d[6];
             e_diffs<T, BP>(Ek, Ek1, o, d);
-            if (sxo >= 0 || syo[r] >= 0 || sz >= 0)
-                h_pml(d, ic, canon(jb + r, a.ny, a.per[1]), kc, sxo, syo[r], sz, col, ty * RY + r + 1, false);
+            if (sxo >= 0 || syo[r] >= 0 || sz >= 0) {
+                const int jc_ = canon(jb + r, a.ny, a.per[1]);
+                T p[6];
+                h_pml_load(p, ic, jc_, kc, sxo, syo[r], sz);
+                h_pml(d, p, ic, jc_, kc, sxo, syo[r], sz, col, ty * RY + r + 1, false);
+            }
             T hz = Ek[5 * BP + o];
             hpx[r] = Ek[3 * BP + o];
             hpy[r] = Ek[4 * BP + o];
@@ -265,6 +269,23 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
         uint32_t pn = S > 2 ? 0u : 1u;  // parity of the fill of stage sn that holds plane k + 1
         for (int k = k0; k < k1; k++) {
             const int sz = zslab(k);
+            // CPML memory of this plane, loaded before the plane wait so that its
+            // latency overlaps the wait and the H phase (own H side, own E side, halo H side)
+            T ph[RY][6], pe[RY][6], phh[6];
+            bool pown[RY];
+#pragma unroll
+            for (int r = 0; r < RY; r++) {
+                const int j = jb + r;
+                pown[r] = xin && j < a.ny && (sxo >= 0 || syo[r] >= 0 || sz >= 0);
+                if (pown[r]) {
+                    h_pml_load(ph[r], i, j, k, sxo, syo[r], sz);
+                    if (sxo >= 0) { const long long q = ((long long)k * a.ny + j) * dxt + sxo; pe[r][0] = a.psiE[0][0][q]; pe[r][1] = a.psiE[0][1][q]; }
+                    if (syo[r] >= 0) { const long long q = ((long long)k * dyt + syo[r]) * a.nx + i; pe[r][2] = a.psiE[1][0][q]; pe[r][3] = a.psiE[1][1][q]; }
+                    if (sz >= 0) { const long long q = ((long long)sz * a.ny + j) * a.nx + i; pe[r][4] = a.psiE[2][0][q]; pe[r][5] = a.psiE[2][1][q]; }
+                }
+            }
+            const bool phalo = halo && (sxh >= 0 || syh >= 0 || sz >= 0);
+            if (phalo) h_pml_load(phh, hic, hjc, k, sxh, syh, sz);
             wait_stage(sn, pn);
             const T *Ek = stages + sc * SW, *Ek1 = stages + sn * SW, *Hk = Ek + 3 * BP;
             const long long pb = (long long)(k + 1) * a.plane;
@@ -299,8 +320,7 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
                 hz[r] = Hk[2 * BP + o];
                 T d[6];
                 e_diffs<T, BP>(Ek, Ek1, o, d);
-                if (own && (sxo >= 0 || syo[r] >= 0 || sz >= 0))
-                    h_pml(d, i, j, k, sxo, syo[r], sz, col, ty * RY + r + 1, true);
+                if (pown[r]) h_pml(d, ph[r], i, j, k, sxo, syo[r], sz, col, ty * RY + r + 1, true);
                 h_finish(a.dt, d, hx[r], hy[r], hz[r]);
                 const int sr = ty * RY + r + 1;
                 sH[0][sr][tx + 1] = hx[r];
@@ -324,7 +344,7 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
                 T qx = Hk[oh], qy = Hk[BP + oh], qz = Hk[2 * BP + oh];
                 T d[6];
                 e_diffs<T, BP>(Ek, Ek1, oh, d);
-                if (sxh >= 0 || syh >= 0 || sz >= 0) h_pml(d, hic, hjc, k, sxh, syh, sz, hxs + 3, hys, false);
+                if (phalo) h_pml(d, phh, hic, hjc, k, sxh, syh, sz, hxs + 3, hys, false);
                 h_finish(a.dt, d, qx, qy, qz);
                 sH[0][hys][hxs] = qx;
                 sH[1][hys][hxs] = qy;
@@ -344,28 +364,25 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
                 T dHz_dx = hz[r] - sH[2][sr][tx];
                 T dHy_dx = hy[r] - sH[1][sr][tx];
                 T dHx_dy = hx[r] - sH[0][sr - 1][tx + 1];
-                if (sxo >= 0 || syo[r] >= 0 || sz >= 0) {
+                if (pown[r]) {
                     if (sxo >= 0) {
                         const long long q = ((long long)k * a.ny + j) * dxt + sxo;
-                        T p0 = a.psiE[0][0][q], p1 = a.psiE[0][1][q];
-                        cpml_pair(sCx[0][col], sCx[1][col], sCx[2][col], dHz_dx, dHy_dx, p0, p1);
-                        a.psiE[0][0][q] = p0;
-                        a.psiE[0][1][q] = p1;
+                        cpml_pair(sCx[0][col], sCx[1][col], sCx[2][col], dHz_dx, dHy_dx, pe[r][0], pe[r][1]);
+                        a.psiE[0][0][q] = pe[r][0];
+                        a.psiE[0][1][q] = pe[r][1];
                     }
                     if (syo[r] >= 0) {
                         const long long q = ((long long)k * dyt + syo[r]) * a.nx + i;
-                        T p0 = a.psiE[1][0][q], p1 = a.psiE[1][1][q];
-                        cpml_pair(sCy[0][sr], sCy[1][sr], sCy[2][sr], dHz_dy, dHx_dy, p0, p1);
-                        a.psiE[1][0][q] = p0;
-                        a.psiE[1][1][q] = p1;
+                        cpml_pair(sCy[0][sr], sCy[1][sr], sCy[2][sr], dHz_dy, dHx_dy, pe[r][2], pe[r][3]);
+                        a.psiE[1][0][q] = pe[r][2];
+                        a.psiE[1][1][q] = pe[r][3];
                     }
                     if (sz >= 0) {
                         const long long q = ((long long)sz * a.ny + j) * a.nx + i;
                         const T *cf = a.cpml[2];
-                        T p0 = a.psiE[2][0][q], p1 = a.psiE[2][1][q];
-                        cpml_pair(cf[k], cf[a.nz + k], cf[2 * a.nz + k], dHy_dz, dHx_dz, p0, p1);
-                        a.psiE[2][0][q] = p0;
-                        a.psiE[2][1][q] = p1;
+                        cpml_pair(cf[k], cf[a.nz + k], cf[2 * a.nz + k], dHy_dz, dHx_dz, pe[r][4], pe[r][5]);
+                        a.psiE[2][0][q] = pe[r][4];
+                        a.psiE[2][1][q] = pe[r][5];
                     }
                 }
                 const T curl0 = dHz_dy - dHy_dz;
@@ -482,7 +499,7 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
             if (tid == 0) {
                 double s = 0.0;
                 for (int q = 0; q < NTHREADS / 32; q++) s += s_red[q];
-                a.absorbed_part[blockIdx.x] += s;
+                a.absorbed_part[tile] += s;
             }
         }
         return;
@@ -504,7 +521,7 @@ drain:
 // paths of the field pass.
 template <typename T>
 __device__ __forceinline__ bool interior_block(const YeeArgs<T> &a) {
-    const int tile = blockIdx.x;
+    const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
     if (a.mat || a.dcb || a.JD[0] || a.nsrc) return false;

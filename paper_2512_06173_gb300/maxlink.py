@@ -219,10 +219,10 @@ def ml_set_timing(h: int, enable: bool):
 
 
 def ml_timing(h: int):
-    """(ms[5], counts[5]) per kernel class: molecules, field pass, plane sample, plane fold,
-    molecular current."""
-    ms = np.zeros(5)
-    cnt = np.zeros(5, np.int64)
+    """(ms[6], counts[6]) per kernel class: molecules, field pass, plane sample, plane fold,
+    molecular current, gather."""
+    ms = np.zeros(6)
+    cnt = np.zeros(6, np.int64)
     _check(load().ml_timing(C.c_void_p(h), C.c_void_p(_ptr(ms)), C.c_void_p(_ptr(cnt))))
     return ms, cnt
 

@@ -241,3 +241,19 @@ def test_dipole_derivative_identity(oracle_mod):
         mid = (rho + rm) / 2
         errs.append(abs(md - (-2 * w0 * mu12 * mid[0, 1].imag)))
     assert errs[1] < errs[0] / 3.5
+
+
+def test_energy_sum_free_precession(oracle_mod):
+    """The per-molecule energy accumulator sums Tr(rho^{n+1} H0) over steps; for an
+    uncoupled emitter Tr(rho H0) = w0 rho_11 stays constant, so after N steps the sum
+    is N w0 rho_11 (and the multilevel ladder gives sum_k E_k rho_kk)."""
+    w0 = 0.31
+    d = tls((3.3, 3.7, 3.1), w0, 0.0, cg=np.sqrt(0.6), ce=np.sqrt(0.4) * np.exp(0.2j))
+    rho = np.diag([0.5, 0.3, 0.2]).astype(complex)
+    d3 = dict(n=3, pos=(4.2, 3.1, 2.9), sigma=1.0, gamma=1.0, H0=np.diag([0.0, 0.2, 0.45]).astype(complex),
+              mu=np.zeros((3, 3, 3)), rho=rho, kind=KIND_RK4, nsub=1)
+    prob = Problem(8, 8, 8, 0.5, periodic=(True, True, True), molecules=pack_molecules([d, d3]))
+    s = oracle_mod.OracleSim(prob)
+    s.step(37)
+    assert abs(s.mol_state(0)[2] - 37 * w0 * 0.4) < 1e-12
+    assert abs(s.mol_state(1)[2] - 37 * (0.2 * 0.3 + 0.45 * 0.2)) < 1e-12

@@ -200,6 +200,46 @@ int64_t ml_launch_count(const ml_grid *g);
 ml_status ml_checkpoint(ml_grid *g, void *host_buf, size_t *bytes, void *stream);
 ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *stream);
 
+/* ---- Allocation-free gather (the paper has no counterpart) --------------------
+ *
+ * ml_gather_static computes the regularised field of Eq. E_regu_Emi,
+ *     out[m][c] = gamma_m * sum over cells of E_c * kappa_m^c,
+ * for nmol molecules from an FP32 field that the caller owns, with the same
+ * separable, normalised Gaussian weights as a grid's step.  It exists for callers
+ * that cannot let a library allocate device memory: programs whose GPU memory is
+ * reserved up front by their own allocator or a fixed budget, and loops where a
+ * cudaMalloc, which may synchronise the device, is not acceptable.  It needs no
+ * grid handle and allocates nothing; its only scratch is a fixed device array in
+ * the library, ML_STATIC_GATHER_MAX_MOLECULES x 16 planes x 3 floats (3 MiB),
+ * present on every GPU the library is loaded on, and nothing in it has to start
+ * at zero (each call writes every scratch element it reads).
+ *
+ * Arguments (all device memory unless said otherwise):
+ *   E          3 components Ex, Ey, Ez, each nz*ny*nx floats, (nz, ny, nx) row-major:
+ *              the layout ml_get_fields writes for mask ML_EX|ML_EY|ML_EZ.
+ *   nx,ny,nz   grid dimensions (>= 1).
+ *   periodic   HOST int[3]; nonzero = periodic axis (indices wrap), else cells
+ *              outside the grid are left out of the sum.
+ *   nmol       0..ML_STATIC_GATHER_MAX_MOLECULES; larger counts are rejected with
+ *              ML_ERR_INVALID_ARG before anything is enqueued.
+ *   pos        (nmol, 3) doubles, centre in cell units; sigma, gamma: nmol doubles.
+ *              A molecule with sigma outside (0, 7/3] or |pos| >= 1e9 gets NaN.
+ *   out        (nmol, 3) floats, written by the call.
+ *   stream     cudaStream_t as void*; the call enqueues two kernels and returns.
+ * The caller keeps ownership of every buffer and must keep them alive until the
+ * stream reaches the call.
+ *
+ * The first call on each device does a one-time set-up (it looks up the device
+ * address of the scratch array with the device current); make that first call
+ * before any stream capture.  All calls on a device share the one scratch array,
+ * so calls that overlap on the GPU (on different streams, or from several host
+ * threads) race and give wrong results: order them on one stream or synchronise
+ * between them. */
+#define ML_STATIC_GATHER_MAX_MOLECULES 16384
+ml_status ml_gather_static(const float *E, int nx, int ny, int nz, const int *periodic, int nmol,
+                           const double *pos, const double *sigma, const double *gamma, float *out,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace ml {
+
+// Message returned by ml_last_error on the calling thread.
+void set_last_error(const std::string &msg);
 
 constexpr int TX = 32;      // tile width in x (one warp)
 constexpr int TY = 8;       // tile rows in y

@@ -1,0 +1,172 @@
+// ml_gather_static: regularised molecular fields from a caller-owned field, for
+// callers that cannot allocate device memory.
+//
+// Some applications cannot let a library call cudaMalloc: their device memory is
+// reserved up front by their own allocator (a framework's caching pool, a fixed
+// budget on a shared GPU), or the call sits on a latency-critical path where an
+// allocation, which may synchronise the device, is not acceptable.  This entry
+// point needs no grid handle and allocates nothing: its only scratch is the
+// file-scope device array below, of a fixed maximum size, held by every GPU that
+// loads the library until the process exits.
+//
+// Two kernels: for each molecule and each plane of its kernel window, one warp
+// writes the plane's weighted field sums into the scratch array (every slot the
+// second kernel reads is written by the first, so nothing needs clearing); one warp
+// per molecule then adds the planes in a fixed order and applies the coupling.
+// Calls share the scratch: calls that overlap on the GPU (for example on two
+// streams) race, so issue them one after another.
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "maxlink.h"
+#include "ml_internal.cuh"
+
+namespace {
+
+constexpr int SG_PLANES = ml::WMAX;  // window planes per molecule (2 ceil(3 sigma) + 2 <= 16)
+
+static __device__ __align__(256) float g_sg_scratch[ML_STATIC_GATHER_MAX_MOLECULES * SG_PLANES * 3];
+
+struct SgArgs {
+    const float *E;   // 3 x (nz, ny, nx)
+    int nx, ny, nz, px, py, pz;  // dims and periodic flags
+    int nmol;
+    const double *pos, *sigma, *gamma;
+    float *scratch;   // device address of g_sg_scratch
+    float *out;
+};
+
+// normalised Gaussian weight of index t in the window starting at s along an axis,
+// sample position (s + t) + stag/2, molecule centre p
+__device__ __forceinline__ double sg_w(int t, int W, int s, int stag, double p, double sg) {
+    double sum = 0.0, v = 0.0;
+    for (int q = 0; q < W; q++) {
+        const double d = (double)(s + q) + 0.5 * stag - p;
+        const double g = exp(-d * d / (2.0 * sg * sg));
+        sum += g;
+        if (q == t) v = g;
+    }
+    return v / sum;
+}
+
+__device__ __forceinline__ int sg_wrap(int c, int n, int per, bool &ok) {
+    if (c >= 0 && c < n) return c;
+    if (!per) { ok = false; return 0; }
+    return ((c % n) + n) % n;
+}
+
+// Molecules whose width or position the entry point cannot take get NaN outputs.
+__device__ __forceinline__ bool sg_valid(const SgArgs &a, int m) {
+    const double sg = a.sigma[m];
+    bool ok = sg > 0.0 && ceil(3.0 * sg) <= 7.0;
+    for (int ax = 0; ax < 3; ax++) ok = ok && fabs(a.pos[3 * m + ax]) < 1.0e9;
+    return ok;
+}
+
+// grid: (molecules, SG_PLANES), 32 threads.  Lane = (dx in 0..15, row parity).
+__global__ void sg_partial_kernel(const SgArgs a) {
+    const int m = blockIdx.x, dz = blockIdx.y, lane = threadIdx.x;
+    if (m >= a.nmol) return;
+    float part[3] = {0.f, 0.f, 0.f};
+    if (sg_valid(a, m)) {
+        const double sg = a.sigma[m];
+        const int R = (int)ceil(3.0 * sg), W = 2 * R + 2;
+        int s[3];
+        double p[3];
+        for (int ax = 0; ax < 3; ax++) {
+            p[ax] = a.pos[3 * m + ax];
+            s[ax] = (int)floor(p[ax]) - R;
+        }
+        const int dx = lane & 15, ly = lane >> 4;
+        bool okz = dz < W;
+        const int z = sg_wrap(s[2] + dz, a.nz, a.pz, okz);
+        bool okx = dx < W;
+        const int x = sg_wrap(s[0] + dx, a.nx, a.px, okx);
+        if (okz && okx) {
+            // component c is sampled half a cell along c (Yee staggering)
+            const double wx[2] = {sg_w(dx, W, s[0], 0, p[0], sg), sg_w(dx, W, s[0], 1, p[0], sg)};
+            const double wz[2] = {sg_w(dz, W, s[2], 0, p[2], sg), sg_w(dz, W, s[2], 1, p[2], sg)};
+            const long long N = (long long)a.nx * a.ny * a.nz;
+            for (int dy = ly; dy < W; dy += 2) {
+                bool oky = true;
+                const int y = sg_wrap(s[1] + dy, a.ny, a.py, oky);
+                if (!oky) continue;
+                const double wy0 = sg_w(dy, W, s[1], 0, p[1], sg), wy1 = sg_w(dy, W, s[1], 1, p[1], sg);
+                const long long f = ((long long)z * a.ny + y) * a.nx + x;
+                part[0] += a.E[f] * (float)(wx[1] * wy0 * wz[0]);
+                part[1] += a.E[N + f] * (float)(wx[0] * wy1 * wz[0]);
+                part[2] += a.E[2 * N + f] * (float)(wx[0] * wy0 * wz[1]);
+            }
+        }
+    }
+    for (int c = 0; c < 3; c++) {
+        float v = part[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.scratch[((long long)m * SG_PLANES + dz) * 3 + c] = v;
+    }
+}
+
+// one warp per molecule: the SG_PLANES plane sums added by a fixed xor tree
+__global__ void sg_reduce_kernel(const SgArgs a) {
+    const int m = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (m >= a.nmol) return;
+    const bool ok = sg_valid(a, m);
+    for (int c = 0; c < 3; c++) {
+        float v = lane < SG_PLANES ? a.scratch[((long long)m * SG_PLANES + lane) * 3 + c] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.out[3 * m + c] = ok ? (float)a.gamma[m] * v : __int_as_float(0x7fc00000);
+    }
+}
+
+std::mutex g_mu;
+float *g_ptr[256] = {};  // device address of g_sg_scratch, per device ordinal
+
+ml_status sg_fail(ml_status s, const std::string &msg) {
+    ml::set_last_error(msg);
+    return s;
+}
+
+}  // namespace
+
+ml_status ml_gather_static(const float *E, int nx, int ny, int nz, const int *periodic, int nmol, const double *pos,
+                           const double *sigma, const double *gamma, float *out, void *stream) {
+    if (nmol < 0 || nmol > ML_STATIC_GATHER_MAX_MOLECULES)
+        return sg_fail(ML_ERR_INVALID_ARG, "nmol must be 0.." + std::to_string(ML_STATIC_GATHER_MAX_MOLECULES) +
+                                               " (the fixed scratch holds that many molecules)");
+    if (nx < 1 || ny < 1 || nz < 1 || !periodic) return sg_fail(ML_ERR_INVALID_ARG, "bad grid dimensions");
+    if (nmol == 0) return ML_OK;
+    if (!E || !pos || !sigma || !gamma || !out) return sg_fail(ML_ERR_INVALID_ARG, "null pointer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) return sg_fail(ML_ERR_CUDA, "cudaGetDevice failed");
+    float *scratch = nullptr;
+    {
+        // set-up on the first call for this device (the device is current here)
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_sg_scratch);
+            if (e != cudaSuccess || !p)
+                return sg_fail(ML_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_ptr[dev] = static_cast<float *>(p);
+        }
+        scratch = g_ptr[dev];
+    }
+    SgArgs a;
+    a.E = E;
+    a.nx = nx; a.ny = ny; a.nz = nz;
+    a.px = periodic[0] ? 1 : 0; a.py = periodic[1] ? 1 : 0; a.pz = periodic[2] ? 1 : 0;
+    a.nmol = nmol;
+    a.pos = pos; a.sigma = sigma; a.gamma = gamma;
+    a.scratch = scratch;
+    a.out = out;
+    cudaStream_t s = (cudaStream_t)stream;
+    sg_partial_kernel<<<dim3(nmol, SG_PLANES), 32, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return sg_fail(ML_ERR_CUDA, std::string("partial kernel: ") + cudaGetErrorString(e));
+    sg_reduce_kernel<<<(nmol + 3) / 4, 128, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return sg_fail(ML_ERR_CUDA, std::string("reduce kernel: ") + cudaGetErrorString(e));
+    return ML_OK;
+}

@@ -20,6 +20,7 @@ ML_F32, ML_F64 = 0, 1
 ML_MOL_RHO, ML_MOL_EFIELD, ML_MOL_MUDOT, ML_MOL_ENERGY, ML_MOL_POP = range(5)
 ML_EX, ML_EY, ML_EZ, ML_HX, ML_HY, ML_HZ, ML_ALL = 1, 2, 4, 8, 16, 32, 63
 ML_MAX_LEVELS = 8
+ML_STATIC_GATHER_MAX_MOLECULES = 16384
 
 EXPORTED = ["ml_last_error", "ml_version", "ml_grid_create", "ml_grid_destroy", "ml_add_molecules",
             "ml_add_flux_plane", "ml_step", "ml_get_fields", "ml_set_fields", "ml_get_molecules", "ml_flux",
@@ -103,6 +104,7 @@ def load(build_if_missing: bool = True):
         "ml_set_timing": (I, [P, I]),
         "ml_timing": (I, [P, P, P]),
         "ml_launch_count": (I64, [P]),
+        "ml_gather_static": (I, [P, I, I, I, P, I, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -229,6 +231,17 @@ def ml_timing(h: int):
 
 def ml_launch_count(h: int) -> int:
     return int(load().ml_launch_count(C.c_void_p(h)))
+
+
+def ml_gather_static(E_ptr: int, nx: int, ny: int, nz: int, periodic, nmol: int, pos_ptr: int,
+                     sigma_ptr: int, gamma_ptr: int, out_ptr: int, stream: int = 0):
+    """Allocation-free regularised field from a caller-owned FP32 field (device
+    pointers; see the header).  Allocates nothing here either: the periodic flags
+    travel as a ctypes array on the host."""
+    per = (C.c_int * 3)(*[1 if p else 0 for p in periodic])
+    _check(load().ml_gather_static(C.c_void_p(E_ptr), nx, ny, nz, per, nmol, C.c_void_p(pos_ptr),
+                                   C.c_void_p(sigma_ptr), C.c_void_p(gamma_ptr), C.c_void_p(out_ptr),
+                                   C.c_void_p(stream)))
 
 
 # ---------------------------------------------------------------- Problem wrapper

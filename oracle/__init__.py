@@ -7,7 +7,8 @@ shares no code with the CUDA library.
 
 Functions without an independent pin are marked "parity unpinned" in their
 docstring (none at present: every piece is pinned by a test under `tests/`,
-see `tests/test_oracle_*.py`).
+see `tests/test_oracle_*.py`; the discrete adjoint by a dot-product identity and
+central differences in `tests/test_oracle_adjoint.py`).
 """
 from __future__ import annotations
 
@@ -88,6 +89,16 @@ def _load():
     L.orc_lindblad_rhs.restype = C.c_int
     L.orc_lindblad_rhs.argtypes = [P, C.c_int, dp, dp, dp]
     L.orc_pml_tables.argtypes = [P, C.c_int, dp]
+    L.orc_set_psi.argtypes = [P, dp]
+    L.orc_set_drude.argtypes = [P, dp]
+    L.orc_adj_reset.argtypes = [P]
+    L.orc_adj_get.argtypes = [P, dp]
+    L.orc_adj_set.argtypes = [P, dp]
+    L.orc_adj_field.argtypes = [P]
+    L.orc_mol_vjp.restype = C.c_int
+    L.orc_mol_vjp.argtypes = [P, C.c_int, dp, dp, dp, dp, dp, dp]
+    L.orc_adjoint_run.restype = C.c_int
+    L.orc_adjoint_run.argtypes = [P, C.c_long, C.c_int, C.c_int, dp, dp, dp]
     L.orc_threads.restype = C.c_int
     L.orc_threads.argtypes = []
     _lib = L
@@ -263,3 +274,52 @@ class OracleSim:
         out = np.zeros(6 * n)
         self.L.orc_pml_tables(self.h, axis, out)
         return out.reshape(6, n)
+
+    # -- discrete adjoint (reverse mode of `step`) ---------------------------------
+    def set_psi(self, psi: List[np.ndarray]):
+        self.L.orc_set_psi(self.h, np.ascontiguousarray(np.concatenate([np.ravel(x) for x in psi]), np.float64))
+
+    def set_drude_current(self, jd: List[np.ndarray]):
+        self.L.orc_set_drude(self.h, np.ascontiguousarray(np.concatenate([np.ravel(x) for x in jd]), np.float64))
+
+    def adj_reset(self):
+        self.L.orc_adj_reset(self.h)
+
+    def adj_state(self) -> np.ndarray:
+        """Adjoint field state as (21, nz, ny, nx): Eb[3], Hb[3], psi_b[12], JD_b[3]."""
+        N = int(np.prod(self.shape))
+        out = np.zeros(21 * N)
+        self.L.orc_adj_get(self.h, out)
+        return out.reshape((21,) + self.shape)
+
+    def set_adj_state(self, st: np.ndarray):
+        self.L.orc_adj_set(self.h, np.ascontiguousarray(st, np.float64).ravel())
+
+    def adj_field_step(self):
+        """Transpose of the field part of one step (CPML H and E updates, Drude)."""
+        self.L.orc_adj_field(self.h)
+
+    def mol_vjp(self, m: int, Et, rho: np.ndarray, X: np.ndarray, mdb):
+        """Adjoints of (rho, Et) of one exact two-level step from those of (rho', mudot)."""
+        n = rho.shape[0]
+        rb = np.zeros(2 * n * n)
+        Etb = np.zeros(3)
+        if self.L.orc_mol_vjp(self.h, m, np.ascontiguousarray(Et, np.float64), _ri(rho), _ri(X),
+                              np.ascontiguousarray(mdb, np.float64), rb, Etb) != 0:
+            raise ValueError("bad molecule index")
+        return rb.view(np.complex128).reshape(n, n), Etb
+
+    def adjoint_run(self, nsteps: int, plane: int, freq: int):
+        """Run nsteps from the present state; return the flux of `plane` at frequency
+        index `freq` over those steps and its gradients with respect to the
+        permittivity of every cell (nz, ny, nx) and the coupling of every molecule."""
+        N = int(np.prod(self.shape))
+        ge = np.zeros(N)
+        gg = np.zeros(max(self.nmol, 1))
+        obj = np.zeros(1)
+        rc = self.L.orc_adjoint_run(self.h, int(nsteps), int(plane), int(freq), ge, gg, obj)
+        if rc == -2:
+            raise ValueError("the adjoint takes exact two-level molecules only")
+        if rc != 0:
+            raise ValueError(f"adjoint run failed ({rc})")
+        return float(obj[0]), ge.reshape(self.shape), gg[:self.nmol]

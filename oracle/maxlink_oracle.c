@@ -82,6 +82,7 @@ typedef struct {
     oplane plane[16];
     long step;
     double absorbed;
+    struct oadj *adj;  /* adjoint state (orc_adj_*), allocated on first use */
 } osim;
 
 static long nn(const osim *s) { return (long)s->nx * s->ny * s->nz; }
@@ -159,6 +160,8 @@ osim *orc_create(int nx, int ny, int nz, double dt, const int *periodic, const i
     return s;
 }
 
+static void adj_free(osim *s);
+
 void orc_destroy(osim *s) {
     if (!s) return;
     for (int a = 0; a < 3; a++) {
@@ -169,6 +172,7 @@ void orc_destroy(osim *s) {
     for (int p = 0; p < 12; p++) free(s->psi[p]);
     free(s->eps); free(s->wp); free(s->dg);
     free(s->mol);
+    adj_free(s);
     for (int p = 0; p < s->nplane; p++) {
         free(s->plane[p].omega); free(s->plane[p].E1); free(s->plane[p].E2);
         free(s->plane[p].H1); free(s->plane[p].H2);
@@ -674,4 +678,463 @@ void orc_pml_tables(const osim *s, int a, double *out) {
     int n = dimn(s, a);
     double *src[6] = {s->bE[a], s->cE[a], s->kE[a], s->bH[a], s->cH[a], s->kH[a]};
     for (int q = 0; q < 6; q++) memcpy(out + (long)q * n, src[q], n * sizeof(double));
+}
+
+/* ------------------------------------------------------------------ state setters */
+
+void orc_set_psi(osim *s, const double *in) {
+    long N = nn(s);
+    for (int p = 0; p < 12; p++) memcpy(s->psi[p], in + p * N, N * sizeof(double));
+}
+
+void orc_set_drude(osim *s, const double *in) {
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) memcpy(s->JD[a], in + a * N, N * sizeof(double));
+}
+
+/* ================================================================== adjoint
+ *
+ * Discrete adjoint (reverse mode) of orc_step, for gradients of a DFT-flux value
+ * (the Sec. IV spectra) with respect to the permittivity of every cell and the
+ * coupling gamma of every molecule.  Each forward statement
+ *     y = f(x1, x2, ...)
+ * is undone in reverse order by adding (df/dxi)^T ybar to xbar_i; nothing is
+ * reorganised, so the code below can be read against orc_step line by line.
+ * Complex matrices are real vectors under <X, Y> = Re sum conj(X_ij) Y_ij.
+ * Molecules: the exact two-level propagator (kind 0) only.
+ */
+
+
+struct oadj {
+    double *Eb[3], *Hb[3], *Pb[12], *JDb[3];  /* adjoints of E, H, psi, J_D */
+    double *Jb[3];     /* adjoint of the molecular + source current of the step */
+    double *Eb_in[3];  /* scratch: adjoint of E^n while a step is reversed */
+    cplx *rhob;        /* nmol x MAXLEV^2: adjoint of each density matrix */
+};
+
+static void adj_free(osim *s) {
+    struct oadj *A = s->adj;
+    if (!A) return;
+    for (int a = 0; a < 3; a++) {
+        free(A->Eb[a]); free(A->Hb[a]); free(A->JDb[a]); free(A->Jb[a]); free(A->Eb_in[a]);
+    }
+    for (int p = 0; p < 12; p++) free(A->Pb[p]);
+    free(A->rhob);
+    free(A);
+    s->adj = NULL;
+}
+
+/* Allocate the adjoint state, all zero. */
+void orc_adj_reset(osim *s) {
+    adj_free(s);
+    long N = nn(s);
+    struct oadj *A = calloc(1, sizeof(*A));
+    for (int a = 0; a < 3; a++) {
+        A->Eb[a] = calloc(N, sizeof(double)); A->Hb[a] = calloc(N, sizeof(double));
+        A->JDb[a] = calloc(N, sizeof(double)); A->Jb[a] = calloc(N, sizeof(double));
+        A->Eb_in[a] = calloc(N, sizeof(double));
+    }
+    for (int p = 0; p < 12; p++) A->Pb[p] = calloc(N, sizeof(double));
+    A->rhob = calloc((size_t)(s->nmol > 0 ? s->nmol : 1) * MAXLEV * MAXLEV, sizeof(cplx));
+    s->adj = A;
+}
+
+/* adjoint field state as 21 x N doubles: Eb[3], Hb[3], Pb[12], JDb[3] */
+void orc_adj_get(const osim *s, double *out) {
+    const struct oadj *A = s->adj;
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) {
+        memcpy(out + a * N, A->Eb[a], N * sizeof(double));
+        memcpy(out + (3 + a) * N, A->Hb[a], N * sizeof(double));
+        memcpy(out + (18 + a) * N, A->JDb[a], N * sizeof(double));
+    }
+    for (int p = 0; p < 12; p++) memcpy(out + (6 + p) * N, A->Pb[p], N * sizeof(double));
+}
+
+void orc_adj_set(osim *s, const double *in) {
+    struct oadj *A = s->adj;
+    long N = nn(s);
+    for (int a = 0; a < 3; a++) {
+        memcpy(A->Eb[a], in + a * N, N * sizeof(double));
+        memcpy(A->Hb[a], in + (3 + a) * N, N * sizeof(double));
+        memcpy(A->JDb[a], in + (18 + a) * N, N * sizeof(double));
+    }
+    for (int p = 0; p < 12; p++) memcpy(A->Pb[p], in + (6 + p) * N, N * sizeof(double));
+}
+
+/* f(i,j,k) += v if the cell exists (the transpose of reading it through at()) */
+static void adj_add(const osim *s, double *f, int i, int j, int k, double v) {
+    long c = cell(s, i, j, k);
+    if (c >= 0) f[c] += v;
+}
+
+/* Reverse of steps 4-6 of orc_step (CPML H update, currents, E update with Drude).
+ * On entry the state holds the adjoints of the step's outputs (E^{n+1}, H^{n+1/2},
+ * psi after the step, J_D^{n+1/2}); on exit those of its inputs (E^n, H^{n-1/2},
+ * psi before, J_D^{n-1/2}).  Jb receives the adjoint of the current J^{n+1/2}.
+ * With grad_eps, adds d(objective)/d eps of every cell, which needs E^n (En) and
+ * E^{n+1} (En1): dE^{n+1}/d eps = -(E^{n+1} - E^n) / eps in a cell that is not held
+ * at zero. */
+static void adj_field_step(osim *s, const double *En, const double *En1, double *grad_eps) {
+    struct oadj *A = s->adj;
+    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    const double dt = s->dt;
+    const long N = nn(s);
+    double **Eb = A->Eb, **Hb = A->Hb, **Pb = A->Pb;
+    for (int a = 0; a < 3; a++) {
+        memset(A->Eb_in[a], 0, N * sizeof(double));
+        memset(A->Jb[a], 0, N * sizeof(double));
+    }
+    /* ---- step 6 reversed (E update), cell by cell */
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long c = ((long)k * ny + j) * nx + i;
+                double curlb[3] = {0.0, 0.0, 0.0};
+                for (int a = 0; a < 3; a++) {
+                    double eb = Eb[a][c];
+                    double jdb = 0.0;
+                    if (!pec_forced(s, a, i, j, k)) {
+                        /* e_new = e_old + dt/eps (curl - J - jd) */
+                        double g = dt / s->eps[c];
+                        A->Eb_in[a][c] += eb;
+                        curlb[a] = g * eb;
+                        A->Jb[a][c] = -g * eb;
+                        jdb = -g * eb;
+                        if (grad_eps) grad_eps[c] += eb * (-(En1[a * N + c] - En[a * N + c]) / s->eps[c]);
+                    }
+                    if (s->wp[c] != 0.0) {
+                        /* JD = jd; jd = ((1 - g2) JD_old + dt wp^2 E^n) / (1 + g2) */
+                        jdb += A->JDb[a][c];
+                        double g2 = 0.5 * s->dg[c] * dt;
+                        A->JDb[a][c] = jdb * (1.0 - g2) / (1.0 + g2);
+                        A->Eb_in[a][c] += jdb * dt * s->wp[c] * s->wp[c] / (1.0 + g2);
+                    }
+                }
+                /* curl[0] = (kE_y dHz_dy + P6) - (kE_z dHy_dz + P7), P6 = bE_y P6 + cE_y dHz_dy, ... */
+                double t6 = Pb[6][c] + curlb[0], t7 = Pb[7][c] - curlb[0];
+                double t8 = Pb[8][c] + curlb[1], t9 = Pb[9][c] - curlb[1];
+                double t10 = Pb[10][c] + curlb[2], t11 = Pb[11][c] - curlb[2];
+                double dHz_dy = s->kE[1][j] * curlb[0] + s->cE[1][j] * t6;
+                double dHy_dz = -s->kE[2][k] * curlb[0] + s->cE[2][k] * t7;
+                double dHx_dz = s->kE[2][k] * curlb[1] + s->cE[2][k] * t8;
+                double dHz_dx = -s->kE[0][i] * curlb[1] + s->cE[0][i] * t9;
+                double dHy_dx = s->kE[0][i] * curlb[2] + s->cE[0][i] * t10;
+                double dHx_dy = -s->kE[1][j] * curlb[2] + s->cE[1][j] * t11;
+                Pb[6][c] = s->bE[1][j] * t6;
+                Pb[7][c] = s->bE[2][k] * t7;
+                Pb[8][c] = s->bE[2][k] * t8;
+                Pb[9][c] = s->bE[0][i] * t9;
+                Pb[10][c] = s->bE[0][i] * t10;
+                Pb[11][c] = s->bE[1][j] * t11;
+                /* dHz_dy = hz - H_z(i, j-1, k), ... */
+                Hb[2][c] += dHz_dy; adj_add(s, Hb[2], i, j - 1, k, -dHz_dy);
+                Hb[1][c] += dHy_dz; adj_add(s, Hb[1], i, j, k - 1, -dHy_dz);
+                Hb[0][c] += dHx_dz; adj_add(s, Hb[0], i, j, k - 1, -dHx_dz);
+                Hb[2][c] += dHz_dx; adj_add(s, Hb[2], i - 1, j, k, -dHz_dx);
+                Hb[1][c] += dHy_dx; adj_add(s, Hb[1], i - 1, j, k, -dHy_dx);
+                Hb[0][c] += dHx_dy; adj_add(s, Hb[0], i, j - 1, k, -dHx_dy);
+            }
+    /* ---- step 5: J^{n+1/2} depends on the molecules (reversed by the caller) and on
+     * the sources (no parameter) */
+    /* ---- step 4 reversed (H update): H_new = H_old - dt c, c from the CPML curl of E^n */
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long c = ((long)k * ny + j) * nx + i;
+                double cxb = -dt * Hb[0][c], cyb = -dt * Hb[1][c], czb = -dt * Hb[2][c];
+                double t0 = Pb[0][c] + cxb, t1 = Pb[1][c] - cxb;
+                double t2 = Pb[2][c] + cyb, t3 = Pb[3][c] - cyb;
+                double t4 = Pb[4][c] + czb, t5 = Pb[5][c] - czb;
+                double dEz_dy = s->kH[1][j] * cxb + s->cH[1][j] * t0;
+                double dEy_dz = -s->kH[2][k] * cxb + s->cH[2][k] * t1;
+                double dEx_dz = s->kH[2][k] * cyb + s->cH[2][k] * t2;
+                double dEz_dx = -s->kH[0][i] * cyb + s->cH[0][i] * t3;
+                double dEy_dx = s->kH[0][i] * czb + s->cH[0][i] * t4;
+                double dEx_dy = -s->kH[1][j] * czb + s->cH[1][j] * t5;
+                Pb[0][c] = s->bH[1][j] * t0;
+                Pb[1][c] = s->bH[2][k] * t1;
+                Pb[2][c] = s->bH[2][k] * t2;
+                Pb[3][c] = s->bH[0][i] * t3;
+                Pb[4][c] = s->bH[0][i] * t4;
+                Pb[5][c] = s->bH[1][j] * t5;
+                /* dEz_dy = E_z(i, j+1, k) - ez, ... */
+                adj_add(s, A->Eb_in[2], i, j + 1, k, dEz_dy); A->Eb_in[2][c] -= dEz_dy;
+                adj_add(s, A->Eb_in[1], i, j, k + 1, dEy_dz); A->Eb_in[1][c] -= dEy_dz;
+                adj_add(s, A->Eb_in[0], i, j, k + 1, dEx_dz); A->Eb_in[0][c] -= dEx_dz;
+                adj_add(s, A->Eb_in[2], i + 1, j, k, dEz_dx); A->Eb_in[2][c] -= dEz_dx;
+                adj_add(s, A->Eb_in[1], i + 1, j, k, dEy_dx); A->Eb_in[1][c] -= dEy_dx;
+                adj_add(s, A->Eb_in[0], i, j + 1, k, dEx_dy); A->Eb_in[0][c] -= dEx_dy;
+            }
+    for (int a = 0; a < 3; a++) {
+        double *t = A->Eb[a];
+        A->Eb[a] = A->Eb_in[a];
+        A->Eb_in[a] = t;
+    }
+}
+
+/* Field part of one reversed step on the adjoint state (no molecules, no gradient). */
+void orc_adj_field(osim *s) { adj_field_step(s, NULL, NULL, NULL); }
+
+/* ---- molecules */
+
+/* sum over the window of F^c kappa^c per component (the gather without gamma) */
+static int kappa_sum(const osim *s, const omol *m, double *const F[3], double *out) {
+    for (int c = 0; c < 3; c++) {
+        int i0[3], W[3];
+        double w[3][32];
+        for (int a = 0; a < 3; a++) W[a] = window(m, a, a == c ? 1 : 0, &i0[a], w[a]);
+        double acc = 0.0;
+        for (int tk = 0; tk < W[2]; tk++)
+            for (int tj = 0; tj < W[1]; tj++)
+                for (int ti = 0; ti < W[0]; ti++) {
+                    long cc = cell(s, i0[0] + ti, i0[1] + tj, i0[2] + tk);
+                    if (cc < 0) return -1;
+                    acc += w[0][ti] * w[1][tj] * w[2][tk] * F[c][cc];
+                }
+        out[c] = acc;
+    }
+    return 0;
+}
+
+/* F^c(cell) += amp[c] kappa^c(cell) over the window (the transpose of kappa_sum) */
+static int kappa_add(const osim *s, const omol *m, double *F[3], const double *amp) {
+    for (int c = 0; c < 3; c++) {
+        int i0[3], W[3];
+        double w[3][32];
+        for (int a = 0; a < 3; a++) W[a] = window(m, a, a == c ? 1 : 0, &i0[a], w[a]);
+        for (int tk = 0; tk < W[2]; tk++)
+            for (int tj = 0; tj < W[1]; tj++)
+                for (int ti = 0; ti < W[0]; ti++) {
+                    long cc = cell(s, i0[0] + ti, i0[1] + tj, i0[2] + tk);
+                    if (cc < 0) return -1;
+                    F[c][cc] += amp[c] * w[0][ti] * w[1][tj] * w[2][tk];
+                }
+    }
+    return 0;
+}
+
+/* exp(A) of a complex n x n matrix (n <= 16): scaling and squaring of the Taylor
+ * series (Moler & Van Loan, "Nineteen dubious ways", method 3). */
+static void expm(int n, const cplx *A, cplx *out) {
+    double nrm = 0.0;
+    for (int i = 0; i < n; i++) {
+        double r = 0.0;
+        for (int j = 0; j < n; j++) r += cabs(A[i * n + j]);
+        if (r > nrm) nrm = r;
+    }
+    int sq = 0;
+    while (nrm > 0.125) { nrm *= 0.5; sq++; }
+    double sc = ldexp(1.0, -sq);
+    cplx X[256], term[256], tmp[256];
+    for (int e = 0; e < n * n; e++) {
+        X[e] = A[e] * sc;
+        out[e] = (e / n == e % n) ? 1.0 : 0.0;
+        term[e] = out[e];
+    }
+    for (int q = 1; q <= 24; q++) {
+        matmul(n, term, X, tmp);
+        for (int e = 0; e < n * n; e++) {
+            term[e] = tmp[e] / q;
+            out[e] += term[e];
+        }
+    }
+    for (int r = 0; r < sq; r++) {
+        matmul(n, out, out, tmp);
+        memcpy(out, tmp, (size_t)n * n * sizeof(cplx));
+    }
+}
+
+/* Frechet derivative of exp at X in direction Ed: the upper-right block of
+ * exp([[X, Ed], [0, X]]) (Van Loan 1978; Higham, Functions of Matrices, Thm 3.6). */
+static void expm_frechet(int n, const cplx *X, const cplx *Ed, cplx *L) {
+    int m2 = 2 * n;
+    cplx B[256], EB[256];
+    for (int e = 0; e < m2 * m2; e++) B[e] = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            B[i * m2 + j] = X[i * n + j];
+            B[i * m2 + n + j] = Ed[i * n + j];
+            B[(n + i) * m2 + n + j] = X[i * n + j];
+        }
+    expm(m2, B, EB);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) L[i * n + j] = EB[i * m2 + n + j];
+}
+
+static double rdot(int n, const cplx *X, const cplx *Y) {
+    double acc = 0.0;
+    for (int e = 0; e < n * n; e++) acc += creal(conj(X[e]) * Y[e]);
+    return acc;
+}
+
+/* Vector-Jacobian product of one exact two-level step (rho, Et) -> (rho', mudot)
+ * with rho' = U rho U^+, U = exp(-i dt (H0 - Et . mu)), mudot = (<mu>(rho') - <mu>(rho))/dt:
+ * given the adjoints X of rho' and mdb of mudot, returns those of rho (rhob) and Et (Etb). */
+static void mol_vjp_core(const omol *m, const double *Et, const cplx *rho, const cplx *X, const double *mdb,
+                         double dt, cplx *rhob, double *Etb) {
+    const int n = m->n;
+    cplx Xt[MAXLEV * MAXLEV], H[MAXLEV * MAXLEV], A[MAXLEV * MAXLEV], U[MAXLEV * MAXLEV];
+    cplx Ud[MAXLEV * MAXLEV], T1[MAXLEV * MAXLEV], T2[MAXLEV * MAXLEV];
+    /* <mu_a>(r) = Re sum_ij r_ij mu_a,ji: its gradient is conj(mu_a,ji) at (i, j) */
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            cplx g = 0.0;
+            for (int a = 0; a < 3; a++) g += mdb[a] / dt * conj(m->mu[a][j * n + i]);
+            Xt[i * n + j] = X[i * n + j] + g;   /* total adjoint of rho' */
+            rhob[i * n + j] = -g;
+        }
+    effective_h(m, Et, H);
+    for (int e = 0; e < n * n; e++) A[e] = -I * dt * H[e];
+    expm(n, A, U);
+    dagger(n, U, Ud);
+    /* rho' = U rho U^+  ->  rhob += U^+ Xt U */
+    matmul(n, Ud, Xt, T1);
+    matmul(n, T1, U, T2);
+    for (int e = 0; e < n * n; e++) rhob[e] += T2[e];
+    /* dU/dEt_a = L_exp(A, i dt mu_a) (dA/dEt_a = -i dt dH/dEt_a = i dt mu_a) */
+    for (int a = 0; a < 3; a++) {
+        cplx Ed[MAXLEV * MAXLEV], dU[MAXLEV * MAXLEV], dUd[MAXLEV * MAXLEV], P1[MAXLEV * MAXLEV], P2[MAXLEV * MAXLEV];
+        for (int e = 0; e < n * n; e++) Ed[e] = I * dt * m->mu[a][e];
+        expm_frechet(n, A, Ed, dU);
+        dagger(n, dU, dUd);
+        matmul(n, dU, rho, T1);
+        matmul(n, T1, Ud, P1);     /* dU rho U^+ */
+        matmul(n, U, rho, T1);
+        matmul(n, T1, dUd, P2);    /* U rho dU^+ */
+        for (int e = 0; e < n * n; e++) P1[e] += P2[e];
+        Etb[a] = rdot(n, Xt, P1);
+    }
+}
+
+/* The same product for molecule q at the given point (for tests): rho, X as
+ * interleaved re/im n x n, mdb[3]; writes rhob (re/im) and Etb[3]. */
+int orc_mol_vjp(const osim *s, int q, const double *Et, const double *rho_ri, const double *X_ri,
+                const double *mdb, double *rhob_ri, double *Etb) {
+    if (q < 0 || q >= s->nmol) return -1;
+    const omol *m = &s->mol[q];
+    int n = m->n;
+    cplx rho[MAXLEV * MAXLEV], X[MAXLEV * MAXLEV], rb[MAXLEV * MAXLEV];
+    for (int e = 0; e < n * n; e++) {
+        rho[e] = rho_ri[2 * e] + I * rho_ri[2 * e + 1];
+        X[e] = X_ri[2 * e] + I * X_ri[2 * e + 1];
+    }
+    mol_vjp_core(m, Et, rho, X, mdb, s->dt, rb, Etb);
+    for (int e = 0; e < n * n; e++) { rhob_ri[2 * e] = creal(rb[e]); rhob_ri[2 * e + 1] = cimag(rb[e]); }
+    return 0;
+}
+
+/* Reverse of steps 1-3 (and the molecular part of step 5) for molecule q at the
+ * step that started from E^n (En), rho^n (rho_n), with the field Et_n and mudot md_n
+ * it produced.  Uses Jb from adj_field_step and the adjoint of rho^{n+1} held in the
+ * state; leaves the adjoint of rho^n there and adds gamma Etb kappa into the adjoint
+ * of E^n. */
+static int adj_molecule(osim *s, int q, const double *En, const cplx *rho_n, const double *Et_n,
+                        const double *md_n, double *grad_gamma) {
+    struct oadj *A = s->adj;
+    const omol *m = &s->mol[q];
+    const long N = nn(s);
+    cplx *X = A->rhob + (long)q * MAXLEV * MAXLEV;
+    /* step 5: J += gamma mudot kappa */
+    double gJ[3], mdb[3];
+    if (kappa_sum(s, m, A->Jb, gJ)) return -1;
+    for (int a = 0; a < 3; a++) {
+        mdb[a] = m->gamma * gJ[a];
+        grad_gamma[q] += md_n[a] * gJ[a];
+    }
+    /* steps 2-3 */
+    cplx rb[MAXLEV * MAXLEV];
+    double Etb[3];
+    mol_vjp_core(m, Et_n, rho_n, X, mdb, s->dt, rb, Etb);
+    memcpy(X, rb, (size_t)m->n * m->n * sizeof(cplx));
+    /* step 1: Et = gamma * sum E^n kappa */
+    double *Fn[3] = {(double *)En, (double *)En + N, (double *)En + 2 * N};
+    double G[3], amp[3];
+    if (kappa_sum(s, m, Fn, G)) return -1;
+    for (int a = 0; a < 3; a++) {
+        grad_gamma[q] += Etb[a] * G[a];
+        amp[a] = m->gamma * Etb[a];
+    }
+    return kappa_add(s, m, A->Eb, amp);
+}
+
+/* Objective and gradients of one run of nsteps steps from the present state.
+ * Objective: the flux of plane p at frequency index f (orc_flux), counting the
+ * steps of this run only (the plane's sums restart).  grad_eps (N doubles) and
+ * grad_gamma (nmol doubles) receive d(objective)/d eps per cell and d/d gamma per
+ * molecule.  The forward fields of every step are kept (memory 3 N (nsteps + 1)
+ * doubles).  Returns -2 if a molecule is not an exact two-level one. */
+int orc_adjoint_run(osim *s, long nsteps, int p, int f, double *grad_eps, double *grad_gamma, double *obj) {
+    if (p < 0 || p >= s->nplane || f < 0 || f >= s->plane[p].nfreq || nsteps < 1) return -1;
+    for (int q = 0; q < s->nmol; q++)
+        if (s->mol[q].kind != 0) return -2;
+    const long N = nn(s);
+    const int M = s->nmol;
+    const double dt = s->dt;
+    oplane *pl = &s->plane[p];
+    const int a = pl->axis, b = (a + 1) % 3, c2 = (a + 2) % 3;
+    const int nb = dimn(s, b), nc = dimn(s, c2);
+    const long cnt = (long)nb * nc;
+    memset(pl->E1, 0, pl->nfreq * cnt * sizeof(cplx));
+    memset(pl->E2, 0, pl->nfreq * cnt * sizeof(cplx));
+    memset(pl->H1, 0, pl->nfreq * cnt * sizeof(cplx));
+    memset(pl->H2, 0, pl->nfreq * cnt * sizeof(cplx));
+    const long n0 = s->step;
+    double *Eh = malloc((size_t)(nsteps + 1) * 3 * N * sizeof(double));
+    cplx *rh = malloc((size_t)(M > 0 ? M : 1) * nsteps * MAXLEV * MAXLEV * sizeof(cplx));
+    double *eth = malloc((size_t)(M > 0 ? M : 1) * nsteps * 3 * sizeof(double));
+    double *mdh = malloc((size_t)(M > 0 ? M : 1) * nsteps * 3 * sizeof(double));
+    if (!Eh || !rh || !eth || !mdh) { free(Eh); free(rh); free(eth); free(mdh); return -3; }
+    for (int q = 0; q < 3; q++) memcpy(Eh + q * N, s->E[q], N * sizeof(double));
+    int rc = 0;
+    for (long n = 0; n < nsteps && rc == 0; n++) {
+        for (int q = 0; q < M; q++)
+            memcpy(rh + ((long)n * M + q) * MAXLEV * MAXLEV, s->mol[q].rho, MAXLEV * MAXLEV * sizeof(cplx));
+        rc = orc_step(s, 1);
+        for (int q = 0; q < M; q++)
+            for (int c = 0; c < 3; c++) {
+                eth[((long)n * M + q) * 3 + c] = s->mol[q].Et[c];
+                mdh[((long)n * M + q) * 3 + c] = s->mol[q].mudot[c];
+            }
+        for (int q = 0; q < 3; q++) memcpy(Eh + ((n + 1) * 3 + q) * N, s->E[q], N * sizeof(double));
+    }
+    if (rc == 0) {
+        double *fl = malloc(pl->nfreq * sizeof(double));
+        orc_flux(s, p, fl);
+        *obj = fl[f];
+        free(fl);
+        orc_adj_reset(s);
+        struct oadj *A = s->adj;
+        memset(grad_eps, 0, N * sizeof(double));
+        if (M > 0) memset(grad_gamma, 0, M * sizeof(double));
+        const double w = pl->omega[f];
+        const cplx *E1 = pl->E1 + f * cnt, *E2 = pl->E2 + f * cnt, *H1 = pl->H1 + f * cnt, *H2 = pl->H2 + f * cnt;
+        for (long n = nsteps - 1; n >= 0 && rc == 0; n--) {
+            /* step 7 reversed: E1 += pe E_b, E2 += pe E_c at the plane, H1/H2 += ph * mean of
+             * H_b/H_c over the plane and the layer below; J = Re sum (E1 H2* - E2 H1*) */
+            const double S = (double)(n0 + n);
+            const cplx pe = cexp(I * w * (S + 1.0) * dt) * dt;
+            const cplx ph = cexp(I * w * (S + 0.5) * dt) * dt;
+            for (int v = 0; v < nc; v++)
+                for (int u = 0; u < nb; u++) {
+                    int idx[3], idm[3];
+                    idx[a] = pl->index; idx[b] = u; idx[c2] = v;
+                    idm[a] = pl->index - 1; idm[b] = u; idm[c2] = v;
+                    long o = (long)v * nb + u;
+                    adj_add(s, A->Eb[b], idx[0], idx[1], idx[2], creal(pe * conj(H2[o])));
+                    adj_add(s, A->Eb[c2], idx[0], idx[1], idx[2], -creal(pe * conj(H1[o])));
+                    double hb = -0.5 * creal(E2[o] * conj(ph)), hc = 0.5 * creal(E1[o] * conj(ph));
+                    adj_add(s, A->Hb[b], idx[0], idx[1], idx[2], hb);
+                    adj_add(s, A->Hb[b], idm[0], idm[1], idm[2], hb);
+                    adj_add(s, A->Hb[c2], idx[0], idx[1], idx[2], hc);
+                    adj_add(s, A->Hb[c2], idm[0], idm[1], idm[2], hc);
+                }
+            adj_field_step(s, Eh + n * 3 * N, Eh + (n + 1) * 3 * N, grad_eps);
+            for (int q = 0; q < M && rc == 0; q++)
+                rc = adj_molecule(s, q, Eh + n * 3 * N, rh + ((long)n * M + q) * MAXLEV * MAXLEV,
+                                  eth + ((long)n * M + q) * 3, mdh + ((long)n * M + q) * 3, grad_gamma);
+        }
+    }
+    free(Eh); free(rh); free(eth); free(mdh);
+    return rc;
 }

@@ -1,0 +1,141 @@
+"""Pins of the oracle's discrete adjoint (gradients of a DFT flux with respect to
+per-cell permittivity and per-molecule coupling) against facts that do not come
+from the adjoint code itself:
+
+* dot-product identity <L x, y> = <x, L^T y> for the linear field step (CPML on
+  some axes, periodic and wall axes, material table, Drude cells): any dropped
+  term, wrong sign or transposed index in the reversed step breaks it;
+* the vector-Jacobian product of one exact two-level step against central
+  differences of the forward molecule step (which the molecule tests pin to
+  closed forms);
+* the full gradient against central differences of the forward flux
+  (Sec. IV spectra) for a coupled problem with CPML, a design box, a source and
+  molecules.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_06173_gb300 import workloads as W
+
+
+def _dot_case(oracle_mod, prob, seed):
+    rng = np.random.default_rng(seed)
+    o = oracle_mod.OracleSim(prob)
+    sh = o.shape
+    x = [rng.standard_normal(sh) for _ in range(6)]
+    psi = [rng.standard_normal(sh) for _ in range(12)]
+    jd = [rng.standard_normal(sh) for _ in range(3)]
+    o.set_fields(x)
+    o.set_psi(psi)
+    o.set_drude_current(jd)
+    o.step(1)
+    Lx = np.concatenate([np.ravel(f) for f in o.fields() + o.psi() + o.drude_current()])
+    y = rng.standard_normal((21,) + sh)
+    o.adj_reset()
+    o.set_adj_state(y)
+    o.adj_field_step()
+    LTy = o.adj_state().ravel()
+    xv = np.concatenate([np.ravel(f) for f in x + psi + jd])
+    a, b = Lx @ y.ravel(), xv @ LTy
+    return abs(a - b) / abs(a)
+
+
+def test_field_step_dot_product_cpml_periodic(oracle_mod):
+    prob = W.Problem(13, 11, 12, 0.5, periodic=(False, True, False), pml=(3, 4, 0, 0, 2, 3))
+    assert _dot_case(oracle_mod, prob, 0) < 1e-12
+
+
+def test_field_step_dot_product_materials_drude_walls(oracle_mod):
+    mat = np.zeros((12, 11, 13), np.uint8)
+    mat[4:8, 3:7, 5:9] = 1
+    mat[0:3, :, :] = 2
+    prob = W.Problem(13, 11, 12, 0.5, periodic=(False, False, True), pml=(3, 2, 2, 3, 0, 0), mat=mat,
+                     materials=[W.Material(), W.Material(eps_inf=1.5, wp=0.8, gamma=0.1),
+                                W.Material(eps_inf=2.25)])
+    assert _dot_case(oracle_mod, prob, 1) < 1e-12
+
+
+def test_molecule_vjp_matches_central_differences(oracle_mod):
+    rng = np.random.default_rng(3)
+    mu = np.array([[[0, .3], [.3, 0]], [[0, -.2j], [.2j, 0]], [[0.1, 0.5], [0.5, -0.1]]])
+    rho = np.array([[0.6, 0.3 + 0.1j], [0.3 - 0.1j, 0.4]])
+    mol = W.pack_molecules([dict(n=2, pos=[6.3, 5.1, 6.7], sigma=1.0, gamma=0.7, H0=np.diag([0.0, 0.25]),
+                                 mu=mu, rho=rho)])
+    o = oracle_mod.OracleSim(W.Problem(13, 11, 12, 0.5, molecules=mol))
+    Et = rng.standard_normal(3)
+    X = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    X = X + X.conj().T
+    mdb = rng.standard_normal(3)
+    rb, Etb = o.mol_vjp(0, Et, rho, X, mdb)
+
+    def F(E, r):
+        o.set_rho(0, r)
+        md = o.molecule_step(0, E)
+        return np.sum((X.conj() * o.rho(0)).real) + md @ mdb
+
+    h = 1e-6
+    fd = np.array([(F(Et + h * e, rho) - F(Et - h * e, rho)) / (2 * h) for e in np.eye(3)])
+    np.testing.assert_allclose(Etb, fd, rtol=0, atol=1e-8)
+    for d in [np.array([[1, 0], [0, 0]]), np.array([[0, 1], [1, 0]]), np.array([[0, 1j], [-1j, 0]])]:
+        fdr = (F(Et, rho + h * d) - F(Et, rho - h * d)) / (2 * h)
+        assert abs(fdr - np.sum((rb.conj() * d).real)) < 1e-8
+
+
+def _coupled(seed, drude=False):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = 14, 12, 20
+    mats = [W.tls([rng.uniform(5, 9), rng.uniform(5, 7), rng.uniform(11, 13)], 0.3, 0.8, axis=q % 3,
+                  sigma=0.8, gamma=rng.uniform(0.5, 1.5), cg=np.sqrt(0.7), ce=np.sqrt(0.3)) for q in range(3)]
+    mol = W.pack_molecules(mats)
+    deps = 1.0 + rng.uniform(0, 1.5, (4, 5, 6))
+    kw = {}
+    if drude:
+        m = np.zeros((nz, ny, nx), np.uint8)
+        m[14:17, 2:6, 8:12] = 1
+        kw = dict(mat=m, materials=[W.Material(), W.Material(eps_inf=1.2, wp=0.9, gamma=0.05)])
+    return W.Problem(nx, ny, nz, 0.5, periodic=(False, True, False), pml=(3, 3, 0, 0, 3, 3),
+                     design_box=(0 if drude else 4, 3, 6, 6, 5, 4), design_eps=deps,
+                     sources=[W.Source(2, 4, 0, 1.0, 0.3, 6.0, 18.0)],
+                     planes=[W.FluxPlane(2, 15, np.array([0.25, 0.3]))], molecules=mol, **kw)
+
+
+@pytest.mark.parametrize("drude", [False, True])
+def test_gradient_matches_central_differences(oracle_mod, drude):
+    prob = _coupled(5, drude)
+    NS = 80
+
+    def J(p):
+        o = oracle_mod.OracleSim(p)
+        o.step(NS)
+        return o.flux(0)[1]
+
+    o = oracle_mod.OracleSim(prob)
+    obj, ge, gg = o.adjoint_run(NS, 0, 1)
+    assert obj == J(prob)
+    x0, y0, z0 = prob.design_box[:3]
+    h = 1e-4
+    for (k, j, i) in [(6, 3, x0), (8, 5, x0 + 3), (9, 7, x0 + 5), (7, 4, x0 + 1)]:
+        d2 = prob.design_eps.copy()
+        d2[k - z0, j - y0, i - x0] += h
+        d1 = prob.design_eps.copy()
+        d1[k - z0, j - y0, i - x0] -= h
+        fd = (J(prob.replace(design_eps=d2)) - J(prob.replace(design_eps=d1))) / (2 * h)
+        assert abs(ge[k, j, i] - fd) <= 1e-6 * abs(fd)
+    mol = prob.molecules
+    for m in range(mol.count):
+        g2, g1 = mol.gamma.copy(), mol.gamma.copy()
+        g2[m] += h
+        g1[m] -= h
+        fd = (J(prob.replace(molecules=W.Molecules(mol.nlev, mol.off, mol.pos, mol.sigma, g2, mol.decay,
+                                                    mol.dephase, mol.kind, mol.nsub, mol.H0, mol.mu, mol.rho0)))
+              - J(prob.replace(molecules=W.Molecules(mol.nlev, mol.off, mol.pos, mol.sigma, g1, mol.decay,
+                                                      mol.dephase, mol.kind, mol.nsub, mol.H0, mol.mu,
+                                                      mol.rho0)))) / (2 * h)
+        assert abs(gg[m] - fd) <= 1e-6 * abs(fd)
+
+
+def test_adjoint_takes_two_level_exact_molecules_only(oracle_mod):
+    mol = W.pack_molecules([W.tls([6.0, 5.0, 10.0], 0.3, 0.5, decay=0.01)])
+    prob = W.Problem(12, 10, 20, 0.5, molecules=mol, planes=[W.FluxPlane(2, 15, np.array([0.3]))])
+    with pytest.raises(ValueError):
+        oracle_mod.OracleSim(prob).adjoint_run(5, 0, 0)

@@ -207,6 +207,51 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def measure_adjoint(args, stream):
+    """Forward and adjoint wall time of the inverse-design workload (192^3 vacuum with
+    CPML, 96^3 design box, 2000 emitters, 3000 steps, checkpoints every 100 steps).
+    `reverse_ms` is the adjoint call minus a plain forward run of the same steps: the
+    checkpointed recompute plus the reversed steps."""
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    prob = workloads.adjoint_design()
+    sh = stream.cuda_stream
+    g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    S, K = args.adj_steps, 100
+    try:
+        state0 = g.checkpoint()
+        nb = 96 ** 3
+        ge = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        gg = torch.zeros(prob.molecules.count, dtype=torch.float64, device="cuda")
+        # warm-up of both paths (module load, first allocations)
+        g.step(20)
+        g.sync()
+        g.restore(state0)
+        maxlink.ml_adjoint_run(g.h, 40, 20, 0, 0, ge.data_ptr(), gg.data_ptr(), True, sh)
+        g.restore(state0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(S)
+        g.sync()
+        fwd = time.perf_counter() - t0
+        fwd_flux = float(g.flux(0)[0])
+        g.restore(state0)
+        torch.cuda.synchronize()
+        l0 = maxlink.ml_launch_count(g.h)
+        t0 = time.perf_counter()
+        obj = maxlink.ml_adjoint_run(g.h, S, K, 0, 0, ge.data_ptr(), gg.data_ptr(), True, sh)
+        adj = time.perf_counter() - t0
+        launches = maxlink.ml_launch_count(g.h) - l0
+        return {"workload": prob.name, "steps": S, "ckpt_every": K, "dtype": "f32 fields, f64 gradient sums",
+                "forward_ms": fwd * 1e3, "adjoint_call_ms": adj * 1e3, "reverse_ms": (adj - fwd) * 1e3,
+                "ratio_reverse_to_forward": (adj - fwd) / fwd, "gpu_launches": int(launches),
+                "objective": obj, "forward_flux_check": fwd_flux,
+                "grad_eps_l2": float(torch.linalg.norm(ge)), "grad_gamma_l2": float(torch.linalg.norm(gg))}
+    finally:
+        g.close()
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -293,6 +338,7 @@ def run_ours(args, world, rank, local):
     h2d = 6 * N * esz / K
     d2h = prob.molecules.count * maxlink.ML_MAX_LEVELS * 8 + sum(8 * len(p.omegas) for p in prob.planes) / K
     g2.close()
+    adjoint = measure_adjoint(args, stream) if (world == 1 and not args.no_adjoint) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -317,6 +363,7 @@ def run_ours(args, world, rank, local):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "molecule_steps_per_s": mol_steps,
+            "adjoint": adjoint,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
                                    "field_pass": kms[1] / K, "plane_fold": kms[3] / K},
             "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
@@ -337,6 +384,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--edge", type=int, default=256, help="grid edge (profiling runs use a smaller cube)")
     ap.add_argument("--nmol", type=int, default=10000)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--adj-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

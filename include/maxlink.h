@@ -200,6 +200,32 @@ int64_t ml_launch_count(const ml_grid *g);
 ml_status ml_checkpoint(ml_grid *g, void *host_buf, size_t *bytes, void *stream);
 ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *stream);
 
+/* Discrete adjoint of nsteps coupled steps, for gradients of a transmitted flux
+ * (the Sec. IV spectra as objective; the paper does not differentiate its solver).
+ * From the grid's present state the call runs nsteps steps (the grid ends exactly
+ * as after ml_step(g, nsteps)), with the DFT sums of plane `plane_id` restarted at
+ * the first of them, and returns
+ *   *objective  = that plane's net flux (as ml_flux) at frequency index `freq`,
+ *   grad_eps    = d objective / d eps for each design-box cell, (sz, sy, sx) doubles
+ *                 (NULL to skip; requires a design box),
+ *   grad_gamma  = d objective / d gamma_m for each molecule, nmol doubles (NULL to skip).
+ * Gradient buffers are device memory if on_device, else host memory.  The reverse
+ * sweep is the exact transpose of the discrete step (CPML, Drude, PEC walls,
+ * periodic axes, molecule gather/step/scatter); the field history is rebuilt from
+ * full-state device checkpoints taken every ckpt_every steps, each segment
+ * recomputed once (device memory ~ nsteps/ckpt_every checkpoints plus ckpt_every
+ * design-box E records).  Molecules must be exact two-level ones (kind 0) with
+ * gamma != 0.  Allocates its work memory for the call and frees it; synchronises
+ * `stream`. */
+ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_id, int freq, double *objective,
+                         double *grad_eps, double *grad_gamma, int on_device, void *stream);
+
+/* Replace the design-box permittivities ((sz, sy, sx) doubles, each > 0) or the
+ * couplings gamma_m (nmol doubles) of the molecules; device memory if on_device.
+ * Synchronise `stream`; later steps use the new values. */
+ml_status ml_set_design_eps(ml_grid *g, const double *eps, int on_device, void *stream);
+ml_status ml_set_couplings(ml_grid *g, const double *gamma, int on_device, void *stream);
+
 /* ---- Allocation-free gather (the paper has no counterpart) --------------------
  *
  * ml_gather_static computes the regularised field of Eq. E_regu_Emi,

@@ -1,0 +1,871 @@
+// Discrete adjoint of the coupled step: gradients of a DFT flux (the Sec. IV
+// spectra) with respect to the permittivity of every design-box cell and the
+// coupling gamma_m of every molecule, with checkpoint-and-recompute of the field
+// history.
+//
+// Adjoint variables, in the padded layout of the fields:
+//   U    = Ebar / eps  (adjoint of E divided by the cell's relative permittivity),
+//   Hbar               (adjoint of H),
+// and, per CPML slab and layer pair, one adjoint memory for each convolution of
+// the E update (phi) and of the H update (chi).  For a convolution that enters a
+// curl component with sign s, the forward pair  psi' = b psi + c d,  term = s (kinv d
+// + psi')  has the transpose  w = kinv u + c (m + u),  dbar = s w,  m' = b (m + u),
+// with u the adjoint of the curl component and m the memory (kept multiplied by s,
+// so that every pair uses the same update).  Outside a layer w = u.
+//
+// Reversing the step that took E^n to E^{n+1} keeps the forward launch order:
+//   gather of U^{n+1} over the molecule windows (the forward gather kernel),
+//   molecule kernel: adjoint of rho and of the regularised field (Eq. E_regu_Emi,
+//     Eq. von-Neumann-tls, Eq. dipole_derivative reversed),
+//   current kernel with amplitudes -gamma Etbar / dt (the forward kernel),
+//   pass A: Hbar^{n+1/2} += transpose of the E update applied to u = dt U^{n+1},
+//           + d objective / d H^{n+1/2}; permittivity gradient,
+//   pass B: U^n = U^{n+1} + (dt/eps)/dt (transpose of the H update applied to
+//           v = -dt Hbar, Drude, d objective / d E^n) - (dt/eps) J,
+// with tangential U on the index-0 PEC walls held at zero.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "grid.cuh"
+
+namespace ml {
+
+template <typename T>
+struct AdjFieldArgs {
+    int nx, ny, nz, px;
+    long long plane;
+    int per[3], pml[6];
+    T dt;
+    T *U[3];
+    T *Hb[3];
+    const T *cpml[3];
+    const T *phi_in[3][2];
+    T *phi_out[3][2];
+    const T *chi_in[3][2];
+    T *chi_out[3][2];
+    const uint8_t *mat;
+    const T *mat_cb, *mat_dk, *mat_db;
+    int dbox[6];
+    const T *dcb;
+    int jbox[6];
+    T *JDb[3];
+    int jb0[3], jbn[3];
+    const T *Jb[3];
+    double *geps;           // design-box gradient (pass A), or null
+    const T *Eprev, *Enext;  // design-box E^n and E^{n+1} (3 x nbox each)
+    long long nbox;
+    int pax, pidx, pnb;      // objective plane: axis, index, cells along b
+    const double2 *acc[4];   // its sums E_b, E_c, H_b, H_c at the chosen frequency
+    double omega, tH, tE;    // sample times reversed by pass A (H) and pass B (E)
+    int injectE;
+};
+
+__device__ __forceinline__ int adj_slab(int p, int n, int lo, int hi) {
+    if (p < lo) return p;
+    if (p >= n - hi) return p - (n - hi) + lo;
+    return -1;
+}
+
+template <typename T>
+__device__ __forceinline__ long long adj_gidx(const AdjFieldArgs<T> &a, int i, int j, int k) {
+    return (long long)(k + 1) * a.plane + (long long)(j + 1) * a.px + (i + XO);
+}
+
+// index of cell (i,j,k) in the slab storage of axis ax (slab coordinate s)
+template <typename T>
+__device__ __forceinline__ long long adj_midx(const AdjFieldArgs<T> &a, int ax, int s, int i, int j, int k) {
+    if (ax == 0) return ((long long)k * a.ny + j) * (a.pml[0] + a.pml[1]) + s;
+    if (ax == 1) return ((long long)k * (a.pml[2] + a.pml[3]) + s) * a.nx + i;
+    return ((long long)s * a.ny + j) * a.nx + i;
+}
+
+// Weighted adjoint of one curl term at cell (i,j,k) whose derivative runs along ax
+// (pair q of that axis).  side 0: E-update terms (bE cE kE, memory phi); side 1:
+// H-update terms (bH cH kH, memory chi).
+template <typename T>
+__device__ __forceinline__ T wterm(const AdjFieldArgs<T> &a, int side, int ax, int q, int i, int j, int k, T u) {
+    const int p = ax == 0 ? i : (ax == 1 ? j : k);
+    const int n = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
+    const int s = adj_slab(p, n, a.pml[2 * ax], a.pml[2 * ax + 1]);
+    if (s < 0) return u;
+    const T *cf = a.cpml[ax];
+    const T c = cf[(side * 3 + 1) * n + p], kinv = cf[(side * 3 + 2) * n + p];
+    const long long m = adj_midx(a, ax, s, i, j, k);
+    const T mem = side == 0 ? a.phi_in[ax][q][m] : a.chi_in[ax][q][m];
+    return kinv * u + c * (mem + u);
+}
+
+template <typename T>
+__device__ __forceinline__ void mstore(const AdjFieldArgs<T> &a, int side, int ax, int q, int i, int j, int k, T u) {
+    const int p = ax == 0 ? i : (ax == 1 ? j : k);
+    const int n = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
+    const int s = adj_slab(p, n, a.pml[2 * ax], a.pml[2 * ax + 1]);
+    if (s < 0) return;
+    const T b = a.cpml[ax][(side * 3) * n + p];
+    const long long m = adj_midx(a, ax, s, i, j, k);
+    if (side == 0) a.phi_out[ax][q][m] = b * (a.phi_in[ax][q][m] + u);
+    else a.chi_out[ax][q][m] = b * (a.chi_in[ax][q][m] + u);
+}
+
+// dt/eps of the cell and its material index
+template <typename T>
+__device__ __forceinline__ T adj_cb(const AdjFieldArgs<T> &a, int i, int j, int k, int &midx) {
+    midx = a.mat ? a.mat[((long long)k * a.ny + j) * a.nx + i] : 0;
+    T cb = a.mat_cb[midx];
+    if (a.dcb && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] && j < a.dbox[1] + a.dbox[4] &&
+        k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5])
+        cb = a.dcb[((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0])];
+    return cb;
+}
+
+// components held at zero by an index-0 PEC wall (bit c)
+template <typename T>
+__device__ __forceinline__ int adj_forced(const AdjFieldArgs<T> &a, int i, int j, int k) {
+    const bool wx = !a.per[0] && i == 0, wy = !a.per[1] && j == 0, wz = !a.per[2] && k == 0;
+    return ((wy || wz) ? 1 : 0) | ((wx || wz) ? 2 : 0) | ((wx || wy) ? 4 : 0);
+}
+
+// d objective / d E at a plane cell for sample time t: (E_b, E_c) parts
+__device__ __forceinline__ void obj_dE(const double2 *const acc[4], long long o, double omega, double t, double dt,
+                                       double &db, double &dc) {
+    double sn, cs;
+    sincos(omega * t, &sn, &cs);
+    const double pr = cs * dt, pi = sn * dt;
+    const double2 h1 = acc[2][o], h2 = acc[3][o];
+    db = pr * h2.x + pi * h2.y;       // Re(pe conj(H_c))
+    dc = -(pr * h1.x + pi * h1.y);    // -Re(pe conj(H_b))
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) adj_passA_kernel(const AdjFieldArgs<T> a) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= a.nx || j >= a.ny) return;
+    const long long g = adj_gidx(a, i, j, k);
+    const T u0 = a.dt * a.U[0][g], u1 = a.dt * a.U[1][g], u2 = a.dt * a.U[2][g];
+    int xp = i + 1, yp = j + 1, zp = k + 1;
+    bool vx = true, vy = true, vz = true;
+    if (xp == a.nx) { if (a.per[0]) xp = 0; else vx = false; }
+    if (yp == a.ny) { if (a.per[1]) yp = 0; else vy = false; }
+    if (zp == a.nz) { if (a.per[2]) zp = 0; else vz = false; }
+    // pairs: x (q0: comp 1, q1: comp 2), y (q0: comp 0, q1: comp 2), z (q0: comp 0, q1: comp 1)
+    const T w1z = wterm(a, 0, 2, 1, i, j, k, u1), w0z = wterm(a, 0, 2, 0, i, j, k, u0);
+    const T w2y = wterm(a, 0, 1, 1, i, j, k, u2), w0y = wterm(a, 0, 1, 0, i, j, k, u0);
+    const T w2x = wterm(a, 0, 0, 1, i, j, k, u2), w1x = wterm(a, 0, 0, 0, i, j, k, u1);
+    T w1zp = T(0), w0zp = T(0), w2yp = T(0), w0yp = T(0), w2xp = T(0), w1xp = T(0);
+    if (vz) {
+        const long long q = adj_gidx(a, i, j, zp);
+        w1zp = wterm(a, 0, 2, 1, i, j, zp, a.dt * a.U[1][q]);
+        w0zp = wterm(a, 0, 2, 0, i, j, zp, a.dt * a.U[0][q]);
+    }
+    if (vy) {
+        const long long q = adj_gidx(a, i, yp, k);
+        w2yp = wterm(a, 0, 1, 1, i, yp, k, a.dt * a.U[2][q]);
+        w0yp = wterm(a, 0, 1, 0, i, yp, k, a.dt * a.U[0][q]);
+    }
+    if (vx) {
+        const long long q = adj_gidx(a, xp, j, k);
+        w2xp = wterm(a, 0, 0, 1, xp, j, k, a.dt * a.U[2][q]);
+        w1xp = wterm(a, 0, 0, 0, xp, j, k, a.dt * a.U[1][q]);
+    }
+    // E update: curl0 = dHz/dy - dHy/dz, curl1 = dHx/dz - dHz/dx, curl2 = dHy/dx - dHx/dy
+    // with backward differences of H; their transposes are forward differences.
+    T hx = a.Hb[0][g] + (w1z - w1zp) - (w2y - w2yp);
+    T hy = a.Hb[1][g] + (w2x - w2xp) - (w0z - w0zp);
+    T hz = a.Hb[2][g] + (w0y - w0yp) - (w1x - w1xp);
+    mstore(a, 0, 2, 1, i, j, k, u1);
+    mstore(a, 0, 2, 0, i, j, k, u0);
+    mstore(a, 0, 1, 1, i, j, k, u2);
+    mstore(a, 0, 1, 0, i, j, k, u0);
+    mstore(a, 0, 0, 1, i, j, k, u2);
+    mstore(a, 0, 0, 0, i, j, k, u1);
+    // d objective / d H^{n+1/2}: the plane's H sums take the mean of the cells at the
+    // plane index and the one below it
+    if (a.acc[0]) {
+        const int ax = a.pax, b = (ax + 1) % 3, c = (ax + 2) % 3;
+        const int pc[3] = {i, j, k};
+        const int nax = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
+        int im = a.pidx - 1;
+        bool hasm = true;
+        if (im < 0) {
+            if (a.per[ax]) im += nax;
+            else hasm = false;
+        }
+        const int mult = (pc[ax] == a.pidx ? 1 : 0) + ((hasm && pc[ax] == im) ? 1 : 0);
+        if (mult) {
+            const long long o = (long long)pc[c] * a.pnb + pc[b];
+            const double2 e1 = a.acc[0][o], e2 = a.acc[1][o];
+            double sn, cs;
+            sincos(a.omega * a.tH, &sn, &cs);
+            const double pr = cs * (double)a.dt, pi = sn * (double)a.dt;
+            const T db = (T)(mult * -0.5 * (e2.x * pr + e2.y * pi));  // -1/2 Re(E_c conj(ph))
+            const T dc = (T)(mult * 0.5 * (e1.x * pr + e1.y * pi));   //  1/2 Re(E_b conj(ph))
+            T *hp[3] = {&hx, &hy, &hz};
+            *hp[b] += db;
+            *hp[c] += dc;
+        }
+    }
+    a.Hb[0][g] = hx;
+    a.Hb[1][g] = hy;
+    a.Hb[2][g] = hz;
+    // d/d eps of E^{n+1} = E^n + dt/eps (...) is -(E^{n+1} - E^n)/eps; with U = Ebar/eps
+    if (a.geps && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] && j < a.dbox[1] + a.dbox[4] &&
+        k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5]) {
+        const long long q = ((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0]);
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            s += (double)a.U[c][g] * ((double)a.Enext[c * a.nbox + q] - (double)a.Eprev[c * a.nbox + q]);
+        a.geps[q] -= s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) adj_passB_kernel(const AdjFieldArgs<T> a) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= a.nx || j >= a.ny) return;
+    const long long g = adj_gidx(a, i, j, k);
+    const T dt = a.dt;
+    const T v0 = -dt * a.Hb[0][g], v1 = -dt * a.Hb[1][g], v2 = -dt * a.Hb[2][g];
+    int xm = i - 1, ym = j - 1, zm = k - 1;
+    bool vx = true, vy = true, vz = true;
+    if (xm < 0) { if (a.per[0]) xm = a.nx - 1; else vx = false; }
+    if (ym < 0) { if (a.per[1]) ym = a.ny - 1; else vy = false; }
+    if (zm < 0) { if (a.per[2]) zm = a.nz - 1; else vz = false; }
+    const T w1z = wterm(a, 1, 2, 1, i, j, k, v1), w0z = wterm(a, 1, 2, 0, i, j, k, v0);
+    const T w2y = wterm(a, 1, 1, 1, i, j, k, v2), w0y = wterm(a, 1, 1, 0, i, j, k, v0);
+    const T w2x = wterm(a, 1, 0, 1, i, j, k, v2), w1x = wterm(a, 1, 0, 0, i, j, k, v1);
+    T w1zm = T(0), w0zm = T(0), w2ym = T(0), w0ym = T(0), w2xm = T(0), w1xm = T(0);
+    if (vz) {
+        const long long q = adj_gidx(a, i, j, zm);
+        w1zm = wterm(a, 1, 2, 1, i, j, zm, -dt * a.Hb[1][q]);
+        w0zm = wterm(a, 1, 2, 0, i, j, zm, -dt * a.Hb[0][q]);
+    }
+    if (vy) {
+        const long long q = adj_gidx(a, i, ym, k);
+        w2ym = wterm(a, 1, 1, 1, i, ym, k, -dt * a.Hb[2][q]);
+        w0ym = wterm(a, 1, 1, 0, i, ym, k, -dt * a.Hb[0][q]);
+    }
+    if (vx) {
+        const long long q = adj_gidx(a, xm, j, k);
+        w2xm = wterm(a, 1, 0, 1, xm, j, k, -dt * a.Hb[2][q]);
+        w1xm = wterm(a, 1, 0, 0, xm, j, k, -dt * a.Hb[1][q]);
+    }
+    // H update: cx = dEz/dy - dEy/dz, cy = dEx/dz - dEz/dx, cz = dEy/dx - dEx/dy with
+    // forward differences of E; their transposes are backward differences.
+    T d[3];
+    d[0] = (w1zm - w1z) - (w2ym - w2y);
+    d[1] = (w0z - w0zm) + (w2xm - w2x);
+    d[2] = (w0ym - w0y) - (w1xm - w1x);
+    mstore(a, 1, 2, 1, i, j, k, v1);
+    mstore(a, 1, 2, 0, i, j, k, v0);
+    mstore(a, 1, 1, 1, i, j, k, v2);
+    mstore(a, 1, 1, 0, i, j, k, v0);
+    mstore(a, 1, 0, 1, i, j, k, v2);
+    mstore(a, 1, 0, 0, i, j, k, v1);
+    T Uo[3] = {a.U[0][g], a.U[1][g], a.U[2][g]};
+    int midx;
+    const T cb = adj_cb(a, i, j, k, midx);
+    // Drude: J_D = dk J_D + db E^n, used in the E update as -dt/eps J_D
+    if (a.JDb[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] && j < a.jbox[1] + a.jbox[4] &&
+        k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx] != T(0)) {
+        const long long jq = ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
+        const T dk = a.mat_dk[midx], db = a.mat_db[midx];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const T t = a.JDb[c][jq] - dt * Uo[c];
+            a.JDb[c][jq] = dk * t;
+            d[c] += db * t;
+        }
+    }
+    // d objective / d E^n (sampled by the step before this one)
+    if (a.injectE && a.acc[0]) {
+        const int ax = a.pax, b = (ax + 1) % 3, c = (ax + 2) % 3;
+        const int pc[3] = {i, j, k};
+        if (pc[ax] == a.pidx) {
+            double db, dc;
+            obj_dE(a.acc, (long long)pc[c] * a.pnb + pc[b], a.omega, a.tE, (double)a.dt, db, dc);
+            d[b] += (T)db;
+            d[c] += (T)dc;
+        }
+    }
+    T J[3] = {T(0), T(0), T(0)};
+    if (a.Jb[0] || a.Jb[1] || a.Jb[2]) {
+        const int xr = i - a.jb0[0], yr = j - a.jb0[1], kr = k - a.jb0[2];
+        if ((unsigned)xr < (unsigned)a.jbn[0] && (unsigned)yr < (unsigned)a.jbn[1] && (unsigned)kr < (unsigned)a.jbn[2]) {
+            const long long q = ((long long)kr * a.jbn[1] + yr) * a.jbn[0] + xr;
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                if (a.Jb[c]) J[c] = a.Jb[c][q];
+        }
+    }
+    const int forced = adj_forced(a, i, j, k);
+    const T inv = cb / dt;  // 1/eps
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const T un = Uo[c] + inv * d[c] - cb * J[c];
+        a.U[c][g] = ((forced >> c) & 1) ? T(0) : un;
+    }
+}
+
+// d objective / d E^N of the last sample, added to U before the reverse sweep.
+template <typename T>
+__global__ void adj_inject_kernel(const AdjFieldArgs<T> a, int nc) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)a.pnb * nc) return;
+    const int u = (int)(t % a.pnb), v = (int)(t / a.pnb);
+    const int ax = a.pax, b = (ax + 1) % 3, c = (ax + 2) % 3;
+    int pc[3];
+    pc[ax] = a.pidx;
+    pc[b] = u;
+    pc[c] = v;
+    double db, dc;
+    obj_dE(a.acc, t, a.omega, a.tE, (double)a.dt, db, dc);
+    int midx;
+    const T inv = adj_cb(a, pc[0], pc[1], pc[2], midx) / a.dt;
+    const int forced = adj_forced(a, pc[0], pc[1], pc[2]);
+    const long long g = adj_gidx(a, pc[0], pc[1], pc[2]);
+    if (!((forced >> b) & 1)) a.U[b][g] += inv * (T)db;
+    if (!((forced >> c) & 1)) a.U[c][g] += inv * (T)dc;
+}
+
+template <typename T>
+struct AdjMolArgs {
+    int nmol;
+    T dt;
+    const int *cmask;
+    const long long *off;
+    const T *gamma;
+    const cx<T> *H0, *mu;
+    long long pool;
+    const int *moff, *mlist;
+    const T *part;
+    const cx<T> *rho_n;       // rho^n (pool)
+    const T *Et_n, *md_n;     // field and mudot of the forward step (3 per molecule)
+    cx<T> *rhob;              // adjoint of rho (pool): rho^{n+1} in, rho^n out
+    T *cadj;                  // current amplitudes for the adjoint scatter
+    double *ggam;             // d objective / d gamma (accumulated)
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> acmul(cx<T> a, cx<T> b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+template <typename T>
+__device__ __forceinline__ cx<T> aconj(cx<T> a) { return {a.re, -a.im}; }
+
+// C = A B, 2x2 row-major
+template <typename T>
+__device__ __forceinline__ void mm2(const cx<T> *A, const cx<T> *B, cx<T> *C) {
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            cx<T> x = acmul(A[2 * p], B[q]), y = acmul(A[2 * p + 1], B[2 + q]);
+            C[2 * p + q] = {x.re + y.re, x.im + y.im};
+        }
+}
+template <typename T>
+__device__ __forceinline__ void dag2(const cx<T> *A, cx<T> *B) {
+    B[0] = aconj(A[0]);
+    B[1] = aconj(A[2]);
+    B[2] = aconj(A[1]);
+    B[3] = aconj(A[3]);
+}
+
+// One thread per exact two-level molecule.  Forward: rho' = U rho U^+ with
+// U = cos(W dt) - i sin(W dt)/W Z, Z = H - tr(H)/2, W^2 = z^2 + |b|^2 (the global
+// phase cancels), H = H0 - Et . mu; mudot = (<mu>' - <mu>)/dt; the current scatter
+// uses gamma mudot and the gather gamma sum E kappa.  Reversed here with the chain
+// rule through that closed form.
+template <typename T>
+__global__ void adj_mol_kernel(const AdjMolArgs<T> a) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.nmol) return;
+    const int cmk = a.cmask[m];
+    const long long o = a.off[m];
+    const T gam = a.gamma[m], dt = a.dt;
+    // sum of the adjoint field over the window: G_c = sum kappa U^{n+1}
+    T G[3] = {T(0), T(0), T(0)};
+    for (int t = a.moff[m]; t < a.moff[m + 1]; t++) {
+        const T *pp = a.part + 3ll * a.mlist[t];
+        G[0] += pp[0];
+        G[1] += pp[1];
+        G[2] += pp[2];
+    }
+    cx<T> mu[3][4], rho[4], R[4], H[4];
+    T Et[3], md[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const bool on = (cmk >> c) & 1;
+        if (!on) G[c] = T(0);
+        Et[c] = a.Et_n[3 * m + c];
+        md[c] = a.md_n[3 * m + c];
+#pragma unroll
+        for (int e = 0; e < 4; e++) mu[c][e] = on ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
+    }
+    // J = sum gamma mudot kappa enters E^{n+1} as -dt/eps J, so Jbar = -dt U^{n+1} and
+    // mudotbar_c = gamma sum Jbar kappa = -gamma dt G_c; d/dgamma from the scatter:
+    double gg = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) gg += (double)md[c] * (double)(-dt * G[c]);
+    // total adjoint of rho': incoming + gradient of mudot (grad <mu_c> = mu_c)
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        rho[e] = a.rho_n[o + e];
+        cx<T> r = a.rhob[o + e];
+        cx<T> h = a.H0[o + e];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const T f = -gam * G[c];  // mudotbar_c / dt
+            r.re += f * mu[c][e].re;
+            r.im += f * mu[c][e].im;
+            h.re -= Et[c] * mu[c][e].re;
+            h.im -= Et[c] * mu[c][e].im;
+        }
+        R[e] = r;
+        H[e] = h;
+    }
+    const T z = T(0.5) * (H[0].re - H[3].re);
+    const cx<T> b = H[1];
+    const T W = sqrt(z * z + b.re * b.re + b.im * b.im);
+    const T x = W * dt;
+    const T cw = cos(x);
+    const T sw = W > T(0) ? sin(x) / W : dt;
+    cx<T> U[4] = {{cw, -sw * z}, {sw * b.im, -sw * b.re}, {-sw * b.im, -sw * b.re}, {cw, sw * z}};
+    cx<T> Ud[4], T1[4], T2[4];
+    dag2(U, Ud);
+    // rhobar^n = U^+ R U - grad of <mu>(rho^n) term
+    mm2(Ud, R, T1);
+    mm2(T1, U, T2);
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        cx<T> r = T2[e];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const T f = -gam * G[c];
+            r.re -= f * mu[c][e].re;
+            r.im -= f * mu[c][e].im;
+        }
+        a.rhob[o + e] = r;
+    }
+    // d(sin(x)/W)/dW / W: (dt cos x - sin x / W) / W^2, series near W = 0
+    const T small = sizeof(T) == 4 ? T(2e-2) : T(1e-3);
+    const T fs = x < small ? dt * dt * dt * (T(-1) / T(3) + x * x / T(30)) : (dt * cw - sw) / (W * W);
+    cx<T> rUd[4];
+    mm2(rho, Ud, rUd);  // rho U^+
+    double Etb[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        Etb[c] = 0.0;
+        if (!((cmk >> c) & 1)) continue;
+        // dH/dEt_c = -mu_c: dz = -(mu00 - mu11)/2, db = -mu01
+        const T dz = -T(0.5) * (mu[c][0].re - mu[c][3].re);
+        const cx<T> dbb = {-mu[c][1].re, -mu[c][1].im};
+        const T q = z * dz + b.re * dbb.re + b.im * dbb.im;  // W dW
+        const T dcw = -sw * dt * q;
+        const T dsw = fs * q;
+        // dU = dcw - i (dsw Z + sw dZ), Z = [[z, b], [conj b, -z]]
+        const cx<T> Z[4] = {{z, T(0)}, b, aconj(b), {-z, T(0)}};
+        const cx<T> dZ[4] = {{dz, T(0)}, dbb, aconj(dbb), {-dz, T(0)}};
+        cx<T> dU[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const T mr = dsw * Z[e].re + sw * dZ[e].re, mi = dsw * Z[e].im + sw * dZ[e].im;
+            dU[e] = {mi, -mr};  // -i (mr + i mi)
+            if (e == 0 || e == 3) dU[e].re += dcw;
+        }
+        // P = dU rho U^+ + U rho dU^+ = X + X^+ with X = dU rho U^+
+        cx<T> X[4];
+        mm2(dU, rUd, X);
+        double s = 0.0;
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int qq = 0; qq < 2; qq++) {
+                const cx<T> xv = X[2 * p + qq], xt = aconj(X[2 * qq + p]);
+                const cx<T> r = R[2 * p + qq];
+                s += (double)r.re * ((double)xv.re + (double)xt.re) + (double)r.im * ((double)xv.im + (double)xt.im);
+            }
+        Etb[c] = s;
+    }
+    // Et = gamma sum E^n kappa: d/dgamma = Etbar . Et / gamma; scatter amplitude
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        gg += Etb[c] * (double)Et[c] / (double)gam;
+        a.cadj[3 * m + c] = (T)(-(double)gam * Etb[c] / (double)dt);
+    }
+    a.ggam[m] += gg;
+}
+
+// Copy what the reverse sweep needs from one forward step: the design-box E (3 x
+// nbox), rho (pool) and, if rec_mol, the step's field and mudot (3 per molecule).
+template <typename T>
+__global__ void adj_record_kernel(const T *E0, const T *E1, const T *E2, int px, long long plane, int bx0, int by0,
+                                  int bz0, int bsx, int bsy, long long nbox, T *recE, const cx<T> *rho, long long pool,
+                                  cx<T> *recRho, const T *Et, const T *md, int nmol3, T *recEt, T *recMd) {
+    const long long total = 3 * nbox + pool + nmol3;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < 3 * nbox) {
+            const int c = (int)(t / nbox);
+            const long long q = t % nbox;
+            const int i = (int)(q % bsx), j = (int)((q / bsx) % bsy), k = (int)(q / ((long long)bsx * bsy));
+            const T *E = c == 0 ? E0 : (c == 1 ? E1 : E2);
+            recE[t] = E[(long long)(bz0 + k + 1) * plane + (long long)(by0 + j + 1) * px + (bx0 + i + XO)];
+        } else if (t < 3 * nbox + pool) {
+            recRho[t - 3 * nbox] = rho[t - 3 * nbox];
+        } else if (recEt) {
+            const long long q = t - 3 * nbox - pool;
+            recEt[q] = Et[q];
+            recMd[q] = md[q];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host driver
+
+namespace {
+
+struct DevList {
+    std::vector<void *> p;
+    ~DevList() {
+        for (void *q : p) cudaFree(q);
+    }
+};
+
+ml_status adj_alloc(DevList &L, void **out, size_t bytes) {
+    *out = nullptr;
+    if (bytes == 0) return ML_OK;
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        cudaGetLastError();
+        return fail(ML_ERR_OOM, "adjoint: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    L.p.push_back(*out);
+    return ML_OK;
+}
+
+#define AA(ptr, bytes)                                             \
+    do {                                                           \
+        ml_status s_ = adj_alloc(L, (void **)&(ptr), (bytes));     \
+        if (s_ != ML_OK) return s_;                                \
+    } while (0)
+
+struct Snap {
+    long long step;
+    int nsamp;
+    long long samp_step0;
+};
+
+ml_status snapshot(ml_grid *g, char *dst, Snap &sn, cudaStream_t s) {
+    for (auto &b : state_blobs(g)) {
+        CK(cudaMemcpyAsync(dst, b.p, b.bytes, cudaMemcpyDeviceToDevice, s));
+        dst += b.bytes;
+    }
+    sn = {g->step, g->nsamp, g->samp_step0};
+    return ML_OK;
+}
+
+ml_status restore(ml_grid *g, const char *src, const Snap &sn, cudaStream_t s) {
+    for (auto &b : state_blobs(g)) {
+        CK(cudaMemcpyAsync(b.p, src, b.bytes, cudaMemcpyDeviceToDevice, s));
+        src += b.bytes;
+    }
+    g->step = sn.step;
+    g->nsamp = sn.nsamp;
+    g->samp_step0 = sn.samp_step0;
+    return ML_OK;
+}
+
+template <typename T>
+ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *obj, double *grad_eps,
+                       double *grad_gamma, int on_device, cudaStream_t s) {
+    DevList L;
+    const Plane &pl = g->planes[pid];
+    const long long ncell = (long long)pl.nb * pl.nc;
+    const int M = g->nmol;
+    const long long nbox = g->dcb ? (long long)g->dbox[3] * g->dbox[4] * g->dbox[5] : 0;
+    // the objective counts the steps of this run only
+    CK(cudaGetLastError());
+    {
+        ml_status st = fold_planes<T>(g, s);
+        if (st != ML_OK) return st;
+    }
+    CK(cudaMemsetAsync(pl.d_acc, 0, 4 * (size_t)pl.nfreq * ncell * sizeof(double2), s));
+    const long long n0 = g->step;
+    // ---- forward sweep with a full-state checkpoint at the start of every segment
+    size_t sbytes = 0;
+    for (auto &b : state_blobs(g)) sbytes += b.bytes;
+    const long long nseg = (N + K - 1) / K;
+    char *ck = nullptr;
+    AA(ck, sbytes * (size_t)(nseg + 1));
+    std::vector<Snap> snaps(nseg + 1);
+    for (long long sg = 0; sg < nseg; sg++) {
+        ml_status st = snapshot(g, ck + sbytes * sg, snaps[sg], s);
+        if (st != ML_OK) return st;
+        st = step_impl<T>(g, std::min<long long>(K, N - sg * K), s);
+        if (st != ML_OK) return st;
+    }
+    {
+        ml_status st = fold_planes<T>(g, s);
+        if (st != ML_OK) return st;
+        st = snapshot(g, ck + sbytes * nseg, snaps[nseg], s);
+        if (st != ML_OK) return st;
+    }
+    CK(launch_flux_reduce(pl.d_acc, (int)ncell, pl.nfreq, g->d_scalar, s));
+    // the chosen frequency's sums, kept aside: the recompute below refills the plane
+    double2 *objacc = nullptr;
+    AA(objacc, 4 * (size_t)ncell * sizeof(double2));
+    for (int q = 0; q < 4; q++)
+        CK(cudaMemcpyAsync(objacc + q * ncell, pl.d_acc + ((long long)q * pl.nfreq + f) * ncell,
+                           ncell * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    double objv = 0.0;
+    CK(cudaMemcpyAsync(&objv, g->d_scalar + f, sizeof(double), cudaMemcpyDeviceToHost, s));
+    // ---- adjoint state
+    const size_t esz = sizeof(T);
+    T *U[3], *Hb[3];
+    for (int c = 0; c < 3; c++) {
+        AA(U[c], g->vol * esz);
+        AA(Hb[c], g->vol * esz);
+        CK(cudaMemsetAsync(U[c], 0, g->vol * esz, s));
+        CK(cudaMemsetAsync(Hb[c], 0, g->vol * esz, s));
+    }
+    T *phi[2][3][2] = {}, *chi[2][3][2] = {};
+    for (int a = 0; a < 3; a++)
+        if (g->psi_n[a])
+            for (int q = 0; q < 2; q++)
+                for (int l = 0; l < 2; l++) {
+                    AA(phi[l][a][q], g->psi_n[a] * esz);
+                    AA(chi[l][a][q], g->psi_n[a] * esz);
+                    CK(cudaMemsetAsync(phi[l][a][q], 0, g->psi_n[a] * esz, s));
+                    CK(cudaMemsetAsync(chi[l][a][q], 0, g->psi_n[a] * esz, s));
+                }
+    T *JDb[3] = {};
+    if (g->JD[0]) {
+        const size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
+        for (int c = 0; c < 3; c++) {
+            AA(JDb[c], cnt * esz);
+            CK(cudaMemsetAsync(JDb[c], 0, cnt * esz, s));
+        }
+    }
+    double *geps = nullptr, *ggam = nullptr;
+    if (nbox) {
+        AA(geps, nbox * sizeof(double));
+        CK(cudaMemsetAsync(geps, 0, nbox * sizeof(double), s));
+    }
+    cx<T> *rhob = nullptr;
+    T *cadj = nullptr;
+    if (M) {
+        AA(ggam, M * sizeof(double));
+        CK(cudaMemsetAsync(ggam, 0, M * sizeof(double), s));
+        AA(rhob, (size_t)g->pool * sizeof(cx<T>));
+        CK(cudaMemsetAsync(rhob, 0, (size_t)g->pool * sizeof(cx<T>), s));
+        AA(cadj, 3 * (size_t)M * esz);
+    }
+    // per-segment records: slot t holds E^n (design box) and rho^n of step n = seg0 + t,
+    // and (t >= 1) the field and mudot of step n - 1
+    const size_t slotE = 3 * (size_t)nbox, slotR = (size_t)g->pool, slotM = 3 * (size_t)M;
+    T *recE = nullptr, *recEt = nullptr, *recMd = nullptr;
+    cx<T> *recR = nullptr;
+    AA(recE, (size_t)(K + 1) * slotE * esz);
+    if (M) {
+        AA(recR, (size_t)(K + 1) * slotR * sizeof(cx<T>));
+        AA(recEt, (size_t)(K + 1) * slotM * esz);
+        AA(recMd, (size_t)(K + 1) * slotM * esz);
+    }
+    // ---- field-pass arguments shared by every reversed step
+    AdjFieldArgs<T> fa{};
+    fa.nx = g->nx; fa.ny = g->ny; fa.nz = g->nz; fa.px = g->px; fa.plane = g->plane;
+    for (int a = 0; a < 3; a++) fa.per[a] = g->per[a];
+    for (int q = 0; q < 6; q++) fa.pml[q] = g->pml[q];
+    fa.dt = (T)g->dt;
+    for (int c = 0; c < 3; c++) { fa.U[c] = U[c]; fa.Hb[c] = Hb[c]; fa.cpml[c] = (const T *)g->cpml[c]; fa.JDb[c] = JDb[c]; }
+    fa.mat = g->mat;
+    fa.mat_cb = (const T *)g->mat_cb; fa.mat_dk = (const T *)g->mat_dk; fa.mat_db = (const T *)g->mat_db;
+    for (int q = 0; q < 6; q++) { fa.dbox[q] = g->dbox[q]; fa.jbox[q] = g->jbox[q]; }
+    fa.dcb = (const T *)g->dcb;
+    if (M)
+        for (int a = 0; a < 3; a++) {
+            fa.jb0[a] = g->jb0[a];
+            fa.jbn[a] = g->jbn[a];
+            fa.Jb[a] = (const T *)g->d_J[a];
+        }
+    fa.geps = geps;
+    fa.nbox = nbox;
+    fa.pax = pl.axis; fa.pidx = pl.index; fa.pnb = pl.nb;
+    for (int q = 0; q < 4; q++) fa.acc[q] = objacc + q * ncell;
+    fa.omega = pl.omega[f];
+    const dim3 fgrid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), fblock(32, 8);
+    // d objective / d E^N
+    fa.tE = (double)(n0 + N) * g->dt;
+    adj_inject_kernel<T><<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(fa, pl.nc);
+    CK(cudaGetLastError());
+    g->launches++;
+    int ping = 0;
+    for (long long sg = nseg - 1; sg >= 0; sg--) {
+        const long long seg0 = sg * K, len = std::min<long long>(K, N - seg0);
+        ml_status st = restore(g, ck + sbytes * sg, snaps[sg], s);
+        if (st != ML_OK) return st;
+        auto record = [&](long long slot, bool mol) -> ml_status {
+            const int cur = g->cur;
+            const long long total = 3 * nbox + (M ? g->pool : 0) + (mol && M ? 3 * M : 0);
+            if (total == 0) return ML_OK;
+            const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 4096);
+            adj_record_kernel<T><<<blocks, 256, 0, s>>>(
+                (const T *)g->F[cur][0], (const T *)g->F[cur][1], (const T *)g->F[cur][2], g->px, g->plane, g->dbox[0],
+                g->dbox[1], g->dbox[2], g->dbox[3] ? g->dbox[3] : 1, g->dbox[4] ? g->dbox[4] : 1, nbox,
+                recE + slot * slotE, M ? (const cx<T> *)g->d_rho : nullptr, M ? g->pool : 0,
+                recR ? recR + slot * slotR : nullptr, (const T *)g->d_Et, (const T *)g->d_mudot,
+                (mol && M) ? 3 * M : 0, (mol && M) ? recEt + slot * slotM : nullptr,
+                (mol && M) ? recMd + slot * slotM : nullptr);
+            CK(cudaGetLastError());
+            g->launches++;
+            return ML_OK;
+        };
+        st = record(0, false);
+        if (st != ML_OK) return st;
+        for (long long t = 0; t < len; t++) {
+            st = step_impl<T>(g, 1, s);
+            if (st != ML_OK) return st;
+            st = record(t + 1, true);
+            if (st != ML_OK) return st;
+        }
+        for (long long t = len - 1; t >= 0; t--) {
+            const long long n = seg0 + t;
+            if (M) {
+                GathArgs<T> ga{};
+                ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
+                for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = U[q]; }
+                ga.px = g->px; ga.plane = g->plane;
+                ga.off = g->d_joff; ga.ent = g->d_jent; ga.rec = (const T *)g->d_rec; ga.cmask = g->d_cmask;
+                ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
+                CK(launch_gather<T>(ga, s));
+                g->launches++;
+                AdjMolArgs<T> ma{};
+                ma.nmol = M; ma.dt = (T)g->dt; ma.cmask = g->d_cmask; ma.off = g->d_off;
+                ma.gamma = (const T *)g->d_gamma; ma.H0 = (const cx<T> *)g->d_H0; ma.mu = (const cx<T> *)g->d_mu;
+                ma.pool = g->pool; ma.moff = g->d_moff; ma.mlist = g->d_mlist; ma.part = (const T *)g->d_part;
+                ma.rho_n = recR + t * slotR; ma.Et_n = recEt + (t + 1) * slotM; ma.md_n = recMd + (t + 1) * slotM;
+                ma.rhob = rhob; ma.cadj = cadj; ma.ggam = ggam;
+                adj_mol_kernel<T><<<(M + 127) / 128, 128, 0, s>>>(ma);
+                CK(cudaGetLastError());
+                g->launches++;
+                CurArgs<T> ca{};
+                ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
+                for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
+                ca.off = g->d_joff; ca.ent = g->d_jent; ca.rec = (const T *)g->d_rec;
+                ca.c = cadj; ca.cmask = g->gcmask;
+                for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
+                CK(launch_current<T>(ca, s));
+                g->launches++;
+            }
+            for (int a = 0; a < 3; a++)
+                for (int q = 0; q < 2; q++) {
+                    fa.phi_in[a][q] = phi[ping][a][q];
+                    fa.phi_out[a][q] = phi[ping ^ 1][a][q];
+                    fa.chi_in[a][q] = chi[ping][a][q];
+                    fa.chi_out[a][q] = chi[ping ^ 1][a][q];
+                }
+            fa.Eprev = recE + t * slotE;
+            fa.Enext = recE + (t + 1) * slotE;
+            fa.tH = ((double)(n0 + n) + 0.5) * g->dt;
+            fa.tE = (double)(n0 + n) * g->dt;
+            fa.injectE = n >= 1;
+            adj_passA_kernel<T><<<fgrid, fblock, 0, s>>>(fa);
+            CK(cudaGetLastError());
+            adj_passB_kernel<T><<<fgrid, fblock, 0, s>>>(fa);
+            CK(cudaGetLastError());
+            g->launches += 2;
+            ping ^= 1;
+        }
+    }
+    // ---- results, and the forward end state back in place
+    if (grad_eps && nbox)
+        CK(cudaMemcpyAsync(grad_eps, geps, nbox * sizeof(double),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (grad_gamma && M)
+        CK(cudaMemcpyAsync(grad_gamma, ggam, M * sizeof(double),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    {
+        ml_status st = restore(g, ck + sbytes * nseg, snaps[nseg], s);
+        if (st != ML_OK) return st;
+    }
+    CK(cudaStreamSynchronize(s));
+    if (obj) *obj = objv;
+    return ML_OK;
+}
+
+}  // namespace
+}  // namespace ml
+
+using namespace ml;
+
+ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_id, int freq, double *objective,
+                         double *grad_eps, double *grad_gamma, int on_device, void *stream) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    if (nsteps < 1 || ckpt_every < 1) return fail(ML_ERR_INVALID_ARG, "nsteps and ckpt_every must be >= 1");
+    if (plane_id < 0 || plane_id >= (int)g->planes.size()) return fail(ML_ERR_INVALID_ARG, "no such plane");
+    if (freq < 0 || freq >= g->planes[plane_id].nfreq) return fail(ML_ERR_INVALID_ARG, "no such frequency");
+    if (grad_eps && !g->dcb) return fail(ML_ERR_INVALID_ARG, "grad_eps needs a design box");
+    for (int m = 0; m < g->nmol; m++) {
+        if (g->kind[m] != 0)
+            return fail(ML_ERR_INVALID_ARG, "the adjoint takes exact two-level molecules (kind 0) only");
+        if (g->gamma[m] == 0.0) return fail(ML_ERR_INVALID_ARG, "the adjoint needs gamma != 0 for every molecule");
+    }
+    const int K = (int)std::min<int64_t>(ckpt_every, nsteps);
+    cudaStream_t s = (cudaStream_t)stream;
+    return g->prec ? adjoint_impl<double>(g, nsteps, K, plane_id, freq, objective, grad_eps, grad_gamma, on_device, s)
+                   : adjoint_impl<float>(g, nsteps, K, plane_id, freq, objective, grad_eps, grad_gamma, on_device, s);
+}
+
+// Parameters of the objective: the design-box permittivity and the couplings.
+ml_status ml_set_design_eps(ml_grid *g, const double *eps, int on_device, void *stream) {
+    if (!g || !eps) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (!g->dcb) return fail(ML_ERR_INVALID_ARG, "the grid has no design box");
+    const size_t n = (size_t)g->dbox[3] * g->dbox[4] * g->dbox[5];
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> v(n);
+    if (on_device) {
+        CK(cudaMemcpyAsync(v.data(), eps, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        std::copy(eps, eps + n, v.begin());
+    }
+    for (size_t q = 0; q < n; q++) {
+        if (!(v[q] > 0.0)) return fail(ML_ERR_INVALID_ARG, "design eps must be > 0");
+        v[q] = g->dt / v[q];
+    }
+    CK(cudaStreamSynchronize(s));
+    if (g->prec) {
+        CK(cudaMemcpy(g->dcb, v.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        CK(cudaMemcpy(g->dcb, f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return ML_OK;
+}
+
+ml_status ml_set_couplings(ml_grid *g, const double *gamma, int on_device, void *stream) {
+    if (!g || !gamma) return fail(ML_ERR_INVALID_ARG, "null argument");
+    const size_t n = (size_t)g->nmol;
+    if (n == 0) return ML_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> v(n);
+    if (on_device) {
+        CK(cudaMemcpyAsync(v.data(), gamma, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        std::copy(gamma, gamma + n, v.begin());
+    }
+    for (size_t q = 0; q < n; q++)
+        if (!std::isfinite(v[q])) return fail(ML_ERR_INVALID_ARG, "non-finite coupling");
+    CK(cudaStreamSynchronize(s));
+    if (g->prec) {
+        CK(cudaMemcpy(g->d_gamma, v.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        CK(cudaMemcpy(g->d_gamma, f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    g->gamma = v;
+    return ML_OK;
+}

@@ -105,6 +105,9 @@ def load(build_if_missing: bool = True):
         "ml_timing": (I, [P, P, P]),
         "ml_launch_count": (I64, [P]),
         "ml_gather_static": (I, [P, I, I, I, P, I, P, P, P, P, P]),
+        "ml_adjoint_run": (I, [P, I64, I, I, I, P, P, P, I, P]),
+        "ml_set_design_eps": (I, [P, P, I, P]),
+        "ml_set_couplings": (I, [P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -231,6 +234,25 @@ def ml_timing(h: int):
 
 def ml_launch_count(h: int) -> int:
     return int(load().ml_launch_count(C.c_void_p(h)))
+
+
+def ml_adjoint_run(h: int, nsteps: int, ckpt_every: int, plane: int, freq: int, grad_eps_ptr: int = 0,
+                   grad_gamma_ptr: int = 0, on_device: bool = False, stream: int = 0) -> float:
+    """Objective (flux of `plane` at frequency index `freq` over nsteps steps) and its
+    gradients written to the given buffers (0 = skip)."""
+    obj = C.c_double(0.0)
+    _check(load().ml_adjoint_run(C.c_void_p(h), int(nsteps), int(ckpt_every), int(plane), int(freq),
+                                 C.byref(obj), C.c_void_p(grad_eps_ptr or None), C.c_void_p(grad_gamma_ptr or None),
+                                 1 if on_device else 0, C.c_void_p(stream)))
+    return float(obj.value)
+
+
+def ml_set_design_eps(h: int, eps_ptr: int, on_device: bool = False, stream: int = 0):
+    _check(load().ml_set_design_eps(C.c_void_p(h), C.c_void_p(eps_ptr), 1 if on_device else 0, C.c_void_p(stream)))
+
+
+def ml_set_couplings(h: int, gamma_ptr: int, on_device: bool = False, stream: int = 0):
+    _check(load().ml_set_couplings(C.c_void_p(h), C.c_void_p(gamma_ptr), 1 if on_device else 0, C.c_void_p(stream)))
 
 
 def ml_gather_static(E_ptr: int, nx: int, ny: int, nz: int, periodic, nmol: int, pos_ptr: int,
@@ -401,6 +423,26 @@ class Grid:
 
     def absorbed(self) -> float:
         return ml_absorbed(self.h, self.stream)
+
+    def adjoint(self, nsteps: int, plane: int, freq: int, ckpt_every: int = 100):
+        """Flux of `plane` at frequency index `freq` over the next nsteps steps and its
+        gradients: (objective, d/d design eps (sz, sy, sx) or None, d/d gamma (nmol))."""
+        ge = None
+        if self.prob.design_box is not None:
+            sx, sy, sz = self.prob.design_box[3:]
+            ge = np.zeros((sz, sy, sx))
+        gg = np.zeros(max(self.prob.molecules.count, 1))
+        obj = ml_adjoint_run(self.h, nsteps, ckpt_every, plane, freq, _ptr(ge) if ge is not None else 0,
+                             _ptr(gg), False, self.stream)
+        return obj, ge, gg[:self.prob.molecules.count]
+
+    def set_design_eps(self, eps: np.ndarray):
+        e = np.ascontiguousarray(eps, np.float64)
+        ml_set_design_eps(self.h, _ptr(e), False, self.stream)
+
+    def set_couplings(self, gamma: np.ndarray):
+        gm = np.ascontiguousarray(gamma, np.float64)
+        ml_set_couplings(self.h, _ptr(gm), False, self.stream)
 
     def checkpoint(self) -> bytes:
         return ml_checkpoint(self.h, self.stream)

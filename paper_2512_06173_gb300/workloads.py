@@ -281,6 +281,35 @@ def bragg_ensemble(nx=512, ny=512, nz=384, nmol=100000, pml=10, slab=32, seed=3,
                    name=f"bragg-{nx}x{ny}x{nz}-{nmol}ml")
 
 
+def adjoint_design(n: int = 192, design: int = 96, nmol: int = 2000, pml: int = 10, sigma: float = 1.5,
+                   gamma: float = 0.02, seed: int = 4, omega: float = 0.25, width: float = 20.0,
+                   mol_x: Optional[Tuple[float, float]] = None) -> Problem:
+    """Inverse-design problem for the adjoint: vacuum cube with CPML on every face, a
+    centred design box of `design`^3 cells with eps = 1 + U(0, 1.5), `nmol` two-level
+    emitters (omega0 = `omega`, mu12 = 1 along z, coupling `gamma`, ground state) in a
+    slab in front of the box, a z-polarised Gaussian-pulse current sheet (carrier
+    `omega`, width `width`, peak at 5 widths) on the plane x = pml + 2 and one flux
+    plane near the far x face.  The pulse travels along x, so its field and the
+    dipoles are both along z."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x0 = (n - design) // 2
+    deps = 1.0 + rng.uniform(0.0, 1.5, (design, design, design))
+    R = int(np.ceil(3 * sigma))
+    if mol_x is None:
+        mol_x = (max(R + 1.0, x0 - 12.0), max(R + 2.0, x0 - 4.0))
+    lo, hi = pml + R + 1.0, n - pml - R - 2.0
+    xs = rng.uniform(mol_x[0], mol_x[1], size=nmol)
+    ys = rng.uniform(lo, hi, size=nmol)
+    zs = rng.uniform(lo, hi, size=nmol)
+    mats = [tls((xs[m], ys[m], zs[m]), omega, 1.0, axis=2, sigma=sigma, gamma=gamma, cg=1.0, ce=0.0)
+            for m in range(nmol)]
+    src = [Source(axis=0, index=pml + 2, comp=2, amp=1.0, omega=omega, width=width, t0=5.0 * width)]
+    planes = [FluxPlane(0, n - pml - 4, np.array([omega]))]
+    return Problem(n, n, n, 0.5, pml=(pml,) * 6, design_box=(x0, x0, x0, design, design, design),
+                   design_eps=deps, sources=src, molecules=pack_molecules(mats), planes=planes,
+                   name=f"adjoint-design-{n}^3-box{design}^3-{nmol}tls")
+
+
 def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4,
                   multilevel: bool = True, eps_map: bool = True, drude: bool = False,
                   source: bool = True, planes: bool = True, periodic=(False, False, False)) -> Problem:

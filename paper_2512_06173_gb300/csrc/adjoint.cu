@@ -52,12 +52,15 @@ struct AdjFieldArgs {
     T *JDb[3];
     int jb0[3], jbn[3];
     const T *Jb[3];
-    double *geps;           // design-box gradient (pass A), or null
+    T *gseg;                 // design-box gradient of the current segment (pass A), or null
     const T *Eprev, *Enext;  // design-box E^n and E^{n+1} (3 x nbox each)
     long long nbox;
     int pax, pidx, pnb;      // objective plane: axis, index, cells along b
-    const double2 *acc[4];   // its sums E_b, E_c, H_b, H_c at the chosen frequency
-    double omega, tH, tE;    // sample times reversed by pass A (H) and pass B (E)
+    int pim, hasm;           // index of the layer below the plane (wrapped), and whether it exists
+    // d objective / d (E_b, E_c, H_b, H_c) at plane cell o for a sample at time t is
+    // cos(w t) tab[q][o].re + sin(w t) tab[q][o].im (table built once per run)
+    const cx<T> *tab;        // 4 x ncell, or null
+    T csH, snH, csE, snE;    // cos, sin of w t for the H sample (pass A) and E sample (pass B)
     int injectE;
 };
 
@@ -126,185 +129,299 @@ __device__ __forceinline__ int adj_forced(const AdjFieldArgs<T> &a, int i, int j
     return ((wy || wz) ? 1 : 0) | ((wx || wz) ? 2 : 0) | ((wx || wy) ? 4 : 0);
 }
 
-// d objective / d E at a plane cell for sample time t: (E_b, E_c) parts
-__device__ __forceinline__ void obj_dE(const double2 *const acc[4], long long o, double omega, double t, double dt,
-                                       double &db, double &dc) {
-    double sn, cs;
-    sincos(omega * t, &sn, &cs);
-    const double pr = cs * dt, pi = sn * dt;
-    const double2 h1 = acc[2][o], h2 = acc[3][o];
-    db = pr * h2.x + pi * h2.y;       // Re(pe conj(H_c))
-    dc = -(pr * h1.x + pi * h1.y);    // -Re(pe conj(H_b))
+// cos(w t) re + sin(w t) im of one table entry
+template <typename T>
+__device__ __forceinline__ T adj_phase(cx<T> e, T cs, T sn) { return cs * e.re + sn * e.im; }
+
+constexpr int AZC = 8;  // z planes per thread column in the adjoint passes
+
+// CPML coefficients (b, c, kinv) of one side (0: E update, 1: H update) at index p of axis ax
+template <typename T>
+__device__ __forceinline__ void adj_coef(const AdjFieldArgs<T> &a, int side, int ax, int n, int p, T &b, T &c, T &k) {
+    const T *cf = a.cpml[ax];
+    b = cf[(side * 3) * n + p];
+    c = cf[(side * 3 + 1) * n + p];
+    k = cf[(side * 3 + 2) * n + p];
 }
 
+// Pass A: Hbar^{n+1/2} += transpose of the E update applied to u = dt U^{n+1} (with the
+// E-side CPML memories phi), + d objective / d H^{n+1/2}; d objective / d eps.  One
+// thread per (x, y) column marching AZC planes up in z; U of the column's next plane
+// is carried to the following iteration.
 template <typename T>
-__global__ void __launch_bounds__(256) adj_passA_kernel(const AdjFieldArgs<T> a) {
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) adj_passA_kernel(const AdjFieldArgs<T> a) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int k0 = blockIdx.z * AZC, k1 = min(k0 + AZC, a.nz);
     if (i >= a.nx || j >= a.ny) return;
-    const long long g = adj_gidx(a, i, j, k);
-    const T u0 = a.dt * a.U[0][g], u1 = a.dt * a.U[1][g], u2 = a.dt * a.U[2][g];
-    int xp = i + 1, yp = j + 1, zp = k + 1;
-    bool vx = true, vy = true, vz = true;
+    const T dt = a.dt;
+    int xp = i + 1, yp = j + 1;
+    bool vx = true, vy = true;
     if (xp == a.nx) { if (a.per[0]) xp = 0; else vx = false; }
     if (yp == a.ny) { if (a.per[1]) yp = 0; else vy = false; }
-    if (zp == a.nz) { if (a.per[2]) zp = 0; else vz = false; }
-    // pairs: x (q0: comp 1, q1: comp 2), y (q0: comp 0, q1: comp 2), z (q0: comp 0, q1: comp 1)
-    const T w1z = wterm(a, 0, 2, 1, i, j, k, u1), w0z = wterm(a, 0, 2, 0, i, j, k, u0);
-    const T w2y = wterm(a, 0, 1, 1, i, j, k, u2), w0y = wterm(a, 0, 1, 0, i, j, k, u0);
-    const T w2x = wterm(a, 0, 0, 1, i, j, k, u2), w1x = wterm(a, 0, 0, 0, i, j, k, u1);
-    T w1zp = T(0), w0zp = T(0), w2yp = T(0), w0yp = T(0), w2xp = T(0), w1xp = T(0);
-    if (vz) {
-        const long long q = adj_gidx(a, i, j, zp);
-        w1zp = wterm(a, 0, 2, 1, i, j, zp, a.dt * a.U[1][q]);
-        w0zp = wterm(a, 0, 2, 0, i, j, zp, a.dt * a.U[0][q]);
-    }
-    if (vy) {
-        const long long q = adj_gidx(a, i, yp, k);
-        w2yp = wterm(a, 0, 1, 1, i, yp, k, a.dt * a.U[2][q]);
-        w0yp = wterm(a, 0, 1, 0, i, yp, k, a.dt * a.U[0][q]);
-    }
-    if (vx) {
-        const long long q = adj_gidx(a, xp, j, k);
-        w2xp = wterm(a, 0, 0, 1, xp, j, k, a.dt * a.U[2][q]);
-        w1xp = wterm(a, 0, 0, 0, xp, j, k, a.dt * a.U[1][q]);
-    }
-    // E update: curl0 = dHz/dy - dHy/dz, curl1 = dHx/dz - dHz/dx, curl2 = dHy/dx - dHx/dy
-    // with backward differences of H; their transposes are forward differences.
-    T hx = a.Hb[0][g] + (w1z - w1zp) - (w2y - w2yp);
-    T hy = a.Hb[1][g] + (w2x - w2xp) - (w0z - w0zp);
-    T hz = a.Hb[2][g] + (w0y - w0yp) - (w1x - w1xp);
-    mstore(a, 0, 2, 1, i, j, k, u1);
-    mstore(a, 0, 2, 0, i, j, k, u0);
-    mstore(a, 0, 1, 1, i, j, k, u2);
-    mstore(a, 0, 1, 0, i, j, k, u0);
-    mstore(a, 0, 0, 1, i, j, k, u2);
-    mstore(a, 0, 0, 0, i, j, k, u1);
-    // d objective / d H^{n+1/2}: the plane's H sums take the mean of the cells at the
-    // plane index and the one below it
-    if (a.acc[0]) {
-        const int ax = a.pax, b = (ax + 1) % 3, c = (ax + 2) % 3;
-        const int pc[3] = {i, j, k};
-        const int nax = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
-        int im = a.pidx - 1;
-        bool hasm = true;
-        if (im < 0) {
-            if (a.per[ax]) im += nax;
-            else hasm = false;
+    const int dxt = a.pml[0] + a.pml[1], dyt = a.pml[2] + a.pml[3];
+    const int sx = adj_slab(i, a.nx, a.pml[0], a.pml[1]), sxp = vx ? adj_slab(xp, a.nx, a.pml[0], a.pml[1]) : -1;
+    const int sy = adj_slab(j, a.ny, a.pml[2], a.pml[3]), syp = vy ? adj_slab(yp, a.ny, a.pml[2], a.pml[3]) : -1;
+    T bx = 0, cx = 0, kx = 1, bxp = 0, cxp = 0, kxp = 1, by = 0, cy = 0, ky = 1, byp = 0, cyp = 0, kyp = 1;
+    if (sx >= 0) adj_coef(a, 0, 0, a.nx, i, bx, cx, kx);
+    if (sxp >= 0) adj_coef(a, 0, 0, a.nx, xp, bxp, cxp, kxp);
+    if (sy >= 0) adj_coef(a, 0, 1, a.ny, j, by, cy, ky);
+    if (syp >= 0) adj_coef(a, 0, 1, a.ny, yp, byp, cyp, kyp);
+    const long long ro = (long long)(j + 1) * a.px + i + XO;
+    const long long rx = (long long)(j + 1) * a.px + xp + XO;
+    const long long ry = (long long)(yp + 1) * a.px + i + XO;
+    const T *U0 = a.U[0], *U1 = a.U[1], *U2 = a.U[2];
+    const bool inbx = a.gseg && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] && j < a.dbox[1] + a.dbox[4];
+    long long pk = (long long)(k0 + 1) * a.plane;
+    T c0 = U0[pk + ro], c1 = U1[pk + ro], c2 = U2[pk + ro];
+    for (int k = k0; k < k1; k++, pk += a.plane) {
+        int zp = k + 1;
+        bool vz = true;
+        if (zp == a.nz) { if (a.per[2]) zp = 0; else vz = false; }
+        T n0 = T(0), n1 = T(0), n2 = T(0);
+        if (vz) {
+            const long long pz = (long long)(zp + 1) * a.plane + ro;
+            n0 = U0[pz];
+            n1 = U1[pz];
+            n2 = U2[pz];
         }
-        const int mult = (pc[ax] == a.pidx ? 1 : 0) + ((hasm && pc[ax] == im) ? 1 : 0);
-        if (mult) {
-            const long long o = (long long)pc[c] * a.pnb + pc[b];
-            const double2 e1 = a.acc[0][o], e2 = a.acc[1][o];
-            double sn, cs;
-            sincos(a.omega * a.tH, &sn, &cs);
-            const double pr = cs * (double)a.dt, pi = sn * (double)a.dt;
-            const T db = (T)(mult * -0.5 * (e2.x * pr + e2.y * pi));  // -1/2 Re(E_c conj(ph))
-            const T dc = (T)(mult * 0.5 * (e1.x * pr + e1.y * pi));   //  1/2 Re(E_b conj(ph))
-            T *hp[3] = {&hx, &hy, &hz};
-            *hp[b] += db;
-            *hp[c] += dc;
+        T w1xp = T(0), w2xp = T(0), w0yp = T(0), w2yp = T(0);
+        if (vx) { w1xp = dt * U1[pk + rx]; w2xp = dt * U2[pk + rx]; }
+        if (vy) { w0yp = dt * U0[pk + ry]; w2yp = dt * U2[pk + ry]; }
+        const T u0 = dt * c0, u1 = dt * c1, u2 = dt * c2;
+        T w1x = u1, w2x = u2, w0y = u0, w2y = u2, w0z = u0, w1z = u1;
+        T w0zp = dt * n0, w1zp = dt * n1;
+        // CPML: pairs x (comp 1, comp 2), y (comp 0, comp 2), z (comp 0, comp 1)
+        if (sx >= 0) {
+            const long long q = ((long long)k * a.ny + j) * dxt + sx;
+            const T p0 = a.phi_in[0][0][q], p1 = a.phi_in[0][1][q];
+            w1x = kx * u1 + cx * (p0 + u1);
+            w2x = kx * u2 + cx * (p1 + u2);
+            a.phi_out[0][0][q] = bx * (p0 + u1);
+            a.phi_out[0][1][q] = bx * (p1 + u2);
         }
-    }
-    a.Hb[0][g] = hx;
-    a.Hb[1][g] = hy;
-    a.Hb[2][g] = hz;
-    // d/d eps of E^{n+1} = E^n + dt/eps (...) is -(E^{n+1} - E^n)/eps; with U = Ebar/eps
-    if (a.geps && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] && j < a.dbox[1] + a.dbox[4] &&
-        k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5]) {
-        const long long q = ((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0]);
-        double s = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-            s += (double)a.U[c][g] * ((double)a.Enext[c * a.nbox + q] - (double)a.Eprev[c * a.nbox + q]);
-        a.geps[q] -= s;
+        if (sxp >= 0) {
+            const long long q = ((long long)k * a.ny + j) * dxt + sxp;
+            w1xp = kxp * w1xp + cxp * (a.phi_in[0][0][q] + w1xp);
+            w2xp = kxp * w2xp + cxp * (a.phi_in[0][1][q] + w2xp);
+        }
+        if (sy >= 0) {
+            const long long q = ((long long)k * dyt + sy) * a.nx + i;
+            const T p0 = a.phi_in[1][0][q], p1 = a.phi_in[1][1][q];
+            w0y = ky * u0 + cy * (p0 + u0);
+            w2y = ky * u2 + cy * (p1 + u2);
+            a.phi_out[1][0][q] = by * (p0 + u0);
+            a.phi_out[1][1][q] = by * (p1 + u2);
+        }
+        if (syp >= 0) {
+            const long long q = ((long long)k * dyt + syp) * a.nx + i;
+            w0yp = kyp * w0yp + cyp * (a.phi_in[1][0][q] + w0yp);
+            w2yp = kyp * w2yp + cyp * (a.phi_in[1][1][q] + w2yp);
+        }
+        if (a.pml[4] | a.pml[5]) {
+            const int sz = adj_slab(k, a.nz, a.pml[4], a.pml[5]);
+            if (sz >= 0) {
+                T bz, cz, kz;
+                adj_coef(a, 0, 2, a.nz, k, bz, cz, kz);
+                const long long q = ((long long)sz * a.ny + j) * a.nx + i;
+                const T p0 = a.phi_in[2][0][q], p1 = a.phi_in[2][1][q];
+                w0z = kz * u0 + cz * (p0 + u0);
+                w1z = kz * u1 + cz * (p1 + u1);
+                a.phi_out[2][0][q] = bz * (p0 + u0);
+                a.phi_out[2][1][q] = bz * (p1 + u1);
+            }
+            const int szp = vz ? adj_slab(zp, a.nz, a.pml[4], a.pml[5]) : -1;
+            if (szp >= 0) {
+                T bz, cz, kz;
+                adj_coef(a, 0, 2, a.nz, zp, bz, cz, kz);
+                const long long q = ((long long)szp * a.ny + j) * a.nx + i;
+                w0zp = kz * w0zp + cz * (a.phi_in[2][0][q] + w0zp);
+                w1zp = kz * w1zp + cz * (a.phi_in[2][1][q] + w1zp);
+            }
+        }
+        // E update: curl0 = dHz/dy - dHy/dz, curl1 = dHx/dz - dHz/dx, curl2 = dHy/dx - dHx/dy
+        // with backward differences of H; their transposes are forward differences.
+        const long long g = pk + ro;
+        T hx = a.Hb[0][g] + (w1z - w1zp) - (w2y - w2yp);
+        T hy = a.Hb[1][g] + (w2x - w2xp) - (w0z - w0zp);
+        T hz = a.Hb[2][g] + (w0y - w0yp) - (w1x - w1xp);
+        // d objective / d H^{n+1/2}: the plane's H sums take the mean of the cells at the
+        // plane index and the one below it
+        if (a.tab) {
+            const int pc = a.pax == 0 ? i : (a.pax == 1 ? j : k);
+            const int mult = (pc == a.pidx ? 1 : 0) + ((a.hasm && pc == a.pim) ? 1 : 0);
+            if (mult) {
+                const int u = a.pax == 0 ? j : (a.pax == 1 ? k : i);
+                const int v = a.pax == 0 ? k : (a.pax == 1 ? i : j);
+                const long long o = (long long)v * a.pnb + u;
+                const long long nc = (long long)a.pnb * (a.pax == 0 ? a.nz : (a.pax == 1 ? a.nx : a.ny));
+                const T db = T(mult) * adj_phase(a.tab[2 * nc + o], a.csH, a.snH);
+                const T dc = T(mult) * adj_phase(a.tab[3 * nc + o], a.csH, a.snH);
+                if (a.pax == 0) { hy += db; hz += dc; }
+                else if (a.pax == 1) { hz += db; hx += dc; }
+                else { hx += db; hy += dc; }
+            }
+        }
+        a.Hb[0][g] = hx;
+        a.Hb[1][g] = hy;
+        a.Hb[2][g] = hz;
+        // d/d eps of E^{n+1} = E^n + dt/eps (...) is -(E^{n+1} - E^n)/eps; with U = Ebar/eps
+        if (inbx && k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5]) {
+            const long long q = ((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0]);
+            a.gseg[q] -= c0 * (a.Enext[q] - a.Eprev[q]) + c1 * (a.Enext[a.nbox + q] - a.Eprev[a.nbox + q]) +
+                         c2 * (a.Enext[2 * a.nbox + q] - a.Eprev[2 * a.nbox + q]);
+        }
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
     }
 }
 
+// Pass B: U^n = U^{n+1} + (1/eps)(transpose of the H update applied to v = -dt Hbar,
+// with the H-side memories chi; Drude; d objective / d E^n) - (dt/eps) J, tangential
+// U on index-0 walls held at 0.  Column march as in pass A; the z-pair terms of the
+// plane below are carried.
 template <typename T>
-__global__ void __launch_bounds__(256) adj_passB_kernel(const AdjFieldArgs<T> a) {
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) adj_passB_kernel(const AdjFieldArgs<T> a) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int k0 = blockIdx.z * AZC, k1 = min(k0 + AZC, a.nz);
     if (i >= a.nx || j >= a.ny) return;
-    const long long g = adj_gidx(a, i, j, k);
     const T dt = a.dt;
-    const T v0 = -dt * a.Hb[0][g], v1 = -dt * a.Hb[1][g], v2 = -dt * a.Hb[2][g];
-    int xm = i - 1, ym = j - 1, zm = k - 1;
-    bool vx = true, vy = true, vz = true;
+    int xm = i - 1, ym = j - 1;
+    bool vx = true, vy = true;
     if (xm < 0) { if (a.per[0]) xm = a.nx - 1; else vx = false; }
     if (ym < 0) { if (a.per[1]) ym = a.ny - 1; else vy = false; }
-    if (zm < 0) { if (a.per[2]) zm = a.nz - 1; else vz = false; }
-    const T w1z = wterm(a, 1, 2, 1, i, j, k, v1), w0z = wterm(a, 1, 2, 0, i, j, k, v0);
-    const T w2y = wterm(a, 1, 1, 1, i, j, k, v2), w0y = wterm(a, 1, 1, 0, i, j, k, v0);
-    const T w2x = wterm(a, 1, 0, 1, i, j, k, v2), w1x = wterm(a, 1, 0, 0, i, j, k, v1);
-    T w1zm = T(0), w0zm = T(0), w2ym = T(0), w0ym = T(0), w2xm = T(0), w1xm = T(0);
-    if (vz) {
-        const long long q = adj_gidx(a, i, j, zm);
-        w1zm = wterm(a, 1, 2, 1, i, j, zm, -dt * a.Hb[1][q]);
-        w0zm = wterm(a, 1, 2, 0, i, j, zm, -dt * a.Hb[0][q]);
-    }
-    if (vy) {
-        const long long q = adj_gidx(a, i, ym, k);
-        w2ym = wterm(a, 1, 1, 1, i, ym, k, -dt * a.Hb[2][q]);
-        w0ym = wterm(a, 1, 1, 0, i, ym, k, -dt * a.Hb[0][q]);
-    }
-    if (vx) {
-        const long long q = adj_gidx(a, xm, j, k);
-        w2xm = wterm(a, 1, 0, 1, xm, j, k, -dt * a.Hb[2][q]);
-        w1xm = wterm(a, 1, 0, 0, xm, j, k, -dt * a.Hb[1][q]);
-    }
-    // H update: cx = dEz/dy - dEy/dz, cy = dEx/dz - dEz/dx, cz = dEy/dx - dEx/dy with
-    // forward differences of E; their transposes are backward differences.
-    T d[3];
-    d[0] = (w1zm - w1z) - (w2ym - w2y);
-    d[1] = (w0z - w0zm) + (w2xm - w2x);
-    d[2] = (w0ym - w0y) - (w1xm - w1x);
-    mstore(a, 1, 2, 1, i, j, k, v1);
-    mstore(a, 1, 2, 0, i, j, k, v0);
-    mstore(a, 1, 1, 1, i, j, k, v2);
-    mstore(a, 1, 1, 0, i, j, k, v0);
-    mstore(a, 1, 0, 1, i, j, k, v2);
-    mstore(a, 1, 0, 0, i, j, k, v1);
-    T Uo[3] = {a.U[0][g], a.U[1][g], a.U[2][g]};
-    int midx;
-    const T cb = adj_cb(a, i, j, k, midx);
-    // Drude: J_D = dk J_D + db E^n, used in the E update as -dt/eps J_D
-    if (a.JDb[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] && j < a.jbox[1] + a.jbox[4] &&
-        k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx] != T(0)) {
-        const long long jq = ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
-        const T dk = a.mat_dk[midx], db = a.mat_db[midx];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const T t = a.JDb[c][jq] - dt * Uo[c];
-            a.JDb[c][jq] = dk * t;
-            d[c] += db * t;
+    const int dxt = a.pml[0] + a.pml[1], dyt = a.pml[2] + a.pml[3];
+    const int sx = adj_slab(i, a.nx, a.pml[0], a.pml[1]), sxm = vx ? adj_slab(xm, a.nx, a.pml[0], a.pml[1]) : -1;
+    const int sy = adj_slab(j, a.ny, a.pml[2], a.pml[3]), sym = vy ? adj_slab(ym, a.ny, a.pml[2], a.pml[3]) : -1;
+    T bx = 0, cx = 0, kx = 1, bxm = 0, cxm = 0, kxm = 1, by = 0, cy = 0, ky = 1, bym = 0, cym = 0, kym = 1;
+    if (sx >= 0) adj_coef(a, 1, 0, a.nx, i, bx, cx, kx);
+    if (sxm >= 0) adj_coef(a, 1, 0, a.nx, xm, bxm, cxm, kxm);
+    if (sy >= 0) adj_coef(a, 1, 1, a.ny, j, by, cy, ky);
+    if (sym >= 0) adj_coef(a, 1, 1, a.ny, ym, bym, cym, kym);
+    const long long ro = (long long)(j + 1) * a.px + i + XO;
+    const long long rx = (long long)(j + 1) * a.px + xm + XO;
+    const long long ry = (long long)(ym + 1) * a.px + i + XO;
+    const T *H0 = a.Hb[0], *H1 = a.Hb[1], *H2 = a.Hb[2];
+    const bool zl = (a.pml[4] | a.pml[5]) != 0;
+    // z-pair terms (comp 0, comp 1) of the cell below the first plane
+    T w0zm = T(0), w1zm = T(0);
+    {
+        int zm = k0 - 1;
+        bool vz = true;
+        if (zm < 0) { if (a.per[2]) zm = a.nz - 1; else vz = false; }
+        if (vz) {
+            const long long q = (long long)(zm + 1) * a.plane + ro;
+            w0zm = -dt * H0[q];
+            w1zm = -dt * H1[q];
+            const int szm = zl ? adj_slab(zm, a.nz, a.pml[4], a.pml[5]) : -1;
+            if (szm >= 0) {
+                T bz, cz, kz;
+                adj_coef(a, 1, 2, a.nz, zm, bz, cz, kz);
+                const long long m = ((long long)szm * a.ny + j) * a.nx + i;
+                w0zm = kz * w0zm + cz * (a.chi_in[2][0][m] + w0zm);
+                w1zm = kz * w1zm + cz * (a.chi_in[2][1][m] + w1zm);
+            }
         }
     }
-    // d objective / d E^n (sampled by the step before this one)
-    if (a.injectE && a.acc[0]) {
-        const int ax = a.pax, b = (ax + 1) % 3, c = (ax + 2) % 3;
-        const int pc[3] = {i, j, k};
-        if (pc[ax] == a.pidx) {
-            double db, dc;
-            obj_dE(a.acc, (long long)pc[c] * a.pnb + pc[b], a.omega, a.tE, (double)a.dt, db, dc);
-            d[b] += (T)db;
-            d[c] += (T)dc;
+    const int forced_xy = (!a.per[0] && i == 0 ? 1 : 0) | (!a.per[1] && j == 0 ? 2 : 0);
+    long long pk = (long long)(k0 + 1) * a.plane;
+    for (int k = k0; k < k1; k++, pk += a.plane) {
+        const long long g = pk + ro;
+        const T v0 = -dt * H0[g], v1 = -dt * H1[g], v2 = -dt * H2[g];
+        T w1xm = T(0), w2xm = T(0), w0ym = T(0), w2ym = T(0);
+        if (vx) { w1xm = -dt * H1[pk + rx]; w2xm = -dt * H2[pk + rx]; }
+        if (vy) { w0ym = -dt * H0[pk + ry]; w2ym = -dt * H2[pk + ry]; }
+        T w1x = v1, w2x = v2, w0y = v0, w2y = v2, w0z = v0, w1z = v1;
+        if (sx >= 0) {
+            const long long q = ((long long)k * a.ny + j) * dxt + sx;
+            const T p0 = a.chi_in[0][0][q], p1 = a.chi_in[0][1][q];
+            w1x = kx * v1 + cx * (p0 + v1);
+            w2x = kx * v2 + cx * (p1 + v2);
+            a.chi_out[0][0][q] = bx * (p0 + v1);
+            a.chi_out[0][1][q] = bx * (p1 + v2);
         }
-    }
-    T J[3] = {T(0), T(0), T(0)};
-    if (a.Jb[0] || a.Jb[1] || a.Jb[2]) {
-        const int xr = i - a.jb0[0], yr = j - a.jb0[1], kr = k - a.jb0[2];
-        if ((unsigned)xr < (unsigned)a.jbn[0] && (unsigned)yr < (unsigned)a.jbn[1] && (unsigned)kr < (unsigned)a.jbn[2]) {
-            const long long q = ((long long)kr * a.jbn[1] + yr) * a.jbn[0] + xr;
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                if (a.Jb[c]) J[c] = a.Jb[c][q];
+        if (sxm >= 0) {
+            const long long q = ((long long)k * a.ny + j) * dxt + sxm;
+            w1xm = kxm * w1xm + cxm * (a.chi_in[0][0][q] + w1xm);
+            w2xm = kxm * w2xm + cxm * (a.chi_in[0][1][q] + w2xm);
         }
-    }
-    const int forced = adj_forced(a, i, j, k);
-    const T inv = cb / dt;  // 1/eps
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const T un = Uo[c] + inv * d[c] - cb * J[c];
-        a.U[c][g] = ((forced >> c) & 1) ? T(0) : un;
+        if (sy >= 0) {
+            const long long q = ((long long)k * dyt + sy) * a.nx + i;
+            const T p0 = a.chi_in[1][0][q], p1 = a.chi_in[1][1][q];
+            w0y = ky * v0 + cy * (p0 + v0);
+            w2y = ky * v2 + cy * (p1 + v2);
+            a.chi_out[1][0][q] = by * (p0 + v0);
+            a.chi_out[1][1][q] = by * (p1 + v2);
+        }
+        if (sym >= 0) {
+            const long long q = ((long long)k * dyt + sym) * a.nx + i;
+            w0ym = kym * w0ym + cym * (a.chi_in[1][0][q] + w0ym);
+            w2ym = kym * w2ym + cym * (a.chi_in[1][1][q] + w2ym);
+        }
+        if (zl) {
+            const int sz = adj_slab(k, a.nz, a.pml[4], a.pml[5]);
+            if (sz >= 0) {
+                T bz, cz, kz;
+                adj_coef(a, 1, 2, a.nz, k, bz, cz, kz);
+                const long long q = ((long long)sz * a.ny + j) * a.nx + i;
+                const T p0 = a.chi_in[2][0][q], p1 = a.chi_in[2][1][q];
+                w0z = kz * v0 + cz * (p0 + v0);
+                w1z = kz * v1 + cz * (p1 + v1);
+                a.chi_out[2][0][q] = bz * (p0 + v0);
+                a.chi_out[2][1][q] = bz * (p1 + v1);
+            }
+        }
+        // H update: cx = dEz/dy - dEy/dz, cy = dEx/dz - dEz/dx, cz = dEy/dx - dEx/dy with
+        // forward differences of E; their transposes are backward differences.
+        T d0 = (w1zm - w1z) - (w2ym - w2y);
+        T d1 = (w0z - w0zm) + (w2xm - w2x);
+        T d2 = (w0ym - w0y) - (w1xm - w1x);
+        w0zm = w0z;
+        w1zm = w1z;
+        const T o0 = a.U[0][g], o1 = a.U[1][g], o2 = a.U[2][g];
+        int midx;
+        const T cb = adj_cb(a, i, j, k, midx);
+        // Drude: J_D = dk J_D + db E^n, used in the E update as -dt/eps J_D
+        if (a.JDb[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] && j < a.jbox[1] + a.jbox[4] &&
+            k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx] != T(0)) {
+            const long long jq = ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
+            const T dk = a.mat_dk[midx], db = a.mat_db[midx];
+            const T t0 = a.JDb[0][jq] - dt * o0, t1 = a.JDb[1][jq] - dt * o1, t2 = a.JDb[2][jq] - dt * o2;
+            a.JDb[0][jq] = dk * t0;
+            a.JDb[1][jq] = dk * t1;
+            a.JDb[2][jq] = dk * t2;
+            d0 += db * t0;
+            d1 += db * t1;
+            d2 += db * t2;
+        }
+        // d objective / d E^n (sampled by the step before this one)
+        if (a.injectE && a.tab && (a.pax == 0 ? i : (a.pax == 1 ? j : k)) == a.pidx) {
+            const int u = a.pax == 0 ? j : (a.pax == 1 ? k : i);
+            const int v = a.pax == 0 ? k : (a.pax == 1 ? i : j);
+            const long long o = (long long)v * a.pnb + u;
+            const long long nc = (long long)a.pnb * (a.pax == 0 ? a.nz : (a.pax == 1 ? a.nx : a.ny));
+            const T db = adj_phase(a.tab[o], a.csE, a.snE), dc = adj_phase(a.tab[nc + o], a.csE, a.snE);
+            if (a.pax == 0) { d1 += db; d2 += dc; }
+            else if (a.pax == 1) { d2 += db; d0 += dc; }
+            else { d0 += db; d1 += dc; }
+        }
+        T J0 = T(0), J1 = T(0), J2 = T(0);
+        if (a.Jb[0] || a.Jb[1] || a.Jb[2]) {
+            const int xr = i - a.jb0[0], yr = j - a.jb0[1], kr = k - a.jb0[2];
+            if ((unsigned)xr < (unsigned)a.jbn[0] && (unsigned)yr < (unsigned)a.jbn[1] &&
+                (unsigned)kr < (unsigned)a.jbn[2]) {
+                const long long q = ((long long)kr * a.jbn[1] + yr) * a.jbn[0] + xr;
+                if (a.Jb[0]) J0 = a.Jb[0][q];
+                if (a.Jb[1]) J1 = a.Jb[1][q];
+                if (a.Jb[2]) J2 = a.Jb[2][q];
+            }
+        }
+        const T inv = cb / dt;  // 1/eps
+        const bool wz = !a.per[2] && k == 0;
+        const bool f0 = (forced_xy & 2) || wz, f1 = (forced_xy & 1) || wz, f2 = forced_xy != 0;
+        a.U[0][g] = f0 ? T(0) : o0 + inv * d0 - cb * J0;
+        a.U[1][g] = f1 ? T(0) : o1 + inv * d1 - cb * J1;
+        a.U[2][g] = f2 ? T(0) : o2 + inv * d2 - cb * J2;
     }
 }
 
@@ -319,14 +436,41 @@ __global__ void adj_inject_kernel(const AdjFieldArgs<T> a, int nc) {
     pc[ax] = a.pidx;
     pc[b] = u;
     pc[c] = v;
-    double db, dc;
-    obj_dE(a.acc, t, a.omega, a.tE, (double)a.dt, db, dc);
+    const long long ncell = (long long)a.pnb * nc;
+    const T db = adj_phase(a.tab[t], a.csE, a.snE), dc = adj_phase(a.tab[ncell + t], a.csE, a.snE);
     int midx;
     const T inv = adj_cb(a, pc[0], pc[1], pc[2], midx) / a.dt;
     const int forced = adj_forced(a, pc[0], pc[1], pc[2]);
     const long long g = adj_gidx(a, pc[0], pc[1], pc[2]);
-    if (!((forced >> b) & 1)) a.U[b][g] += inv * (T)db;
-    if (!((forced >> c) & 1)) a.U[c][g] += inv * (T)dc;
+    if (!((forced >> b) & 1)) a.U[b][g] += inv * db;
+    if (!((forced >> c) & 1)) a.U[c][g] += inv * dc;
+}
+
+// Objective J = Re sum_o (E_b,o conj(H_c,o) - E_c,o conj(H_b,o)) with the sums
+// E = sum_n e^{i w t_E} dt E^{n+1}, H = sum_n e^{i w t_H} dt (mean of H^{n+1/2} over the
+// plane and the layer below).  Its derivative with respect to one sample is
+// Re(e^{i w t} c) for a fixed complex c per cell and component:
+//   E_b: dt conj(H_c)   E_c: -dt conj(H_b)   H_b (each of the two cells): -dt E_c / 2
+//   H_c: dt E_b / 2,
+// stored as (Re c, -Im c) so that Re(e^{i w t} c) = cos(w t) re + sin(w t) im.
+template <typename T>
+__global__ void adj_table_kernel(const double2 *acc, long long ncell, double dt, cx<T> *tab) {
+    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (o >= ncell) return;
+    const double2 e1 = acc[o], e2 = acc[ncell + o], h1 = acc[2 * ncell + o], h2 = acc[3 * ncell + o];
+    tab[o] = {(T)(dt * h2.x), (T)(dt * h2.y)};
+    tab[ncell + o] = {(T)(-dt * h1.x), (T)(-dt * h1.y)};
+    tab[2 * ncell + o] = {(T)(-0.5 * dt * e2.x), (T)(-0.5 * dt * e2.y)};
+    tab[3 * ncell + o] = {(T)(0.5 * dt * e1.x), (T)(0.5 * dt * e1.y)};
+}
+
+// FP64 total of the design-box gradient += the segment's sum; the segment sum restarts.
+template <typename T>
+__global__ void adj_fold_kernel(T *gseg, double *geps, long long n) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    geps[q] += (double)gseg[q];
+    gseg[q] = T(0);
 }
 
 template <typename T>
@@ -649,9 +793,12 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
         }
     }
     double *geps = nullptr, *ggam = nullptr;
+    T *gseg = nullptr;
     if (nbox) {
         AA(geps, nbox * sizeof(double));
         CK(cudaMemsetAsync(geps, 0, nbox * sizeof(double), s));
+        AA(gseg, nbox * esz);
+        CK(cudaMemsetAsync(gseg, 0, nbox * esz, s));
     }
     cx<T> *rhob = nullptr;
     T *cadj = nullptr;
@@ -690,14 +837,32 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
             fa.jbn[a] = g->jbn[a];
             fa.Jb[a] = (const T *)g->d_J[a];
         }
-    fa.geps = geps;
+    fa.gseg = gseg;
     fa.nbox = nbox;
     fa.pax = pl.axis; fa.pidx = pl.index; fa.pnb = pl.nb;
-    for (int q = 0; q < 4; q++) fa.acc[q] = objacc + q * ncell;
-    fa.omega = pl.omega[f];
-    const dim3 fgrid((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz), fblock(32, 8);
+    {
+        const int nax = pl.axis == 0 ? g->nx : (pl.axis == 1 ? g->ny : g->nz);
+        fa.pim = pl.index - 1;
+        fa.hasm = 1;
+        if (fa.pim < 0) {
+            if (g->per[pl.axis]) fa.pim += nax;
+            else fa.hasm = 0;
+        }
+    }
+    cx<T> *tab = nullptr;
+    AA(tab, 4 * (size_t)ncell * sizeof(cx<T>));
+    adj_table_kernel<T><<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(objacc, ncell, g->dt, tab);
+    CK(cudaGetLastError());
+    g->launches++;
+    fa.tab = tab;
+    const double omega = pl.omega[f];
+    auto phase = [&](double t, T &cs, T &sn) {
+        cs = (T)std::cos(omega * t);
+        sn = (T)std::sin(omega * t);
+    };
+    const dim3 fgrid((g->nx + 31) / 32, (g->ny + 7) / 8, (g->nz + AZC - 1) / AZC), fblock(32, 8);
     // d objective / d E^N
-    fa.tE = (double)(n0 + N) * g->dt;
+    phase((double)(n0 + N) * g->dt, fa.csE, fa.snE);
     adj_inject_kernel<T><<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(fa, pl.nc);
     CK(cudaGetLastError());
     g->launches++;
@@ -768,8 +933,8 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 }
             fa.Eprev = recE + t * slotE;
             fa.Enext = recE + (t + 1) * slotE;
-            fa.tH = ((double)(n0 + n) + 0.5) * g->dt;
-            fa.tE = (double)(n0 + n) * g->dt;
+            phase(((double)(n0 + n) + 0.5) * g->dt, fa.csH, fa.snH);
+            phase((double)(n0 + n) * g->dt, fa.csE, fa.snE);
             fa.injectE = n >= 1;
             adj_passA_kernel<T><<<fgrid, fblock, 0, s>>>(fa);
             CK(cudaGetLastError());
@@ -777,6 +942,11 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
             CK(cudaGetLastError());
             g->launches += 2;
             ping ^= 1;
+        }
+        if (nbox) {
+            adj_fold_kernel<T><<<(unsigned)((nbox + 255) / 256), 256, 0, s>>>(gseg, geps, nbox);
+            CK(cudaGetLastError());
+            g->launches++;
         }
     }
     // ---- results, and the forward end state back in place

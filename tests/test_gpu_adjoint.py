@@ -2,7 +2,8 @@
 seeded problems: objective, d/d eps over the design box and d/d gamma per
 molecule.  FP64 runs agree to round-off; FP32 runs within 1e-3 relative L2
 (gradients) and 1e-4 (objective).  Also: the result does not depend on the
-checkpoint interval, the grid ends in the state a plain run reaches, and
+checkpoint interval (up to the round-off of the per-segment gradient sums), the
+grid ends in the state a plain run reaches, and
 unsupported inputs are refused.
 """
 import numpy as np
@@ -93,7 +94,8 @@ def test_checkpoint_interval_and_end_state(ml):
         finally:
             g.close()
     (o1, e1, m1, f1, n1), (o2, e2, m2, f2, n2) = res
-    assert o1 == o2 and np.array_equal(e1, e2) and np.array_equal(m1, m2)
+    # the permittivity gradient is folded into FP64 once per segment: round-off only
+    assert o1 == o2 and np.array_equal(m1, m2) and rel(e1, e2) < 1e-12
     g = ml.Grid(prob, 1)
     try:
         g.step(45)

@@ -252,6 +252,57 @@ def measure_adjoint(args, stream):
         g.close()
 
 
+def measure_batch(args, stream):
+    """64 plasmonic realisations of uneven size (edges 64..160, 200-5000 emitters each):
+    K steps as one batch (one launch per kernel class per step, graph-replayed, field-pass
+    grid from the autotuner) against the same K steps with ml_step on each grid in turn
+    (the plain one-instance-per-launch method).  Both start from the same state; the
+    per-instance absorbed energies must agree exactly."""
+    import numpy as np
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    probs = workloads.plasmonic_batch(count=args.batch_count)
+    sh = stream.cuda_stream
+    K = args.batch_steps
+    cells = sum(p.cells for p in probs)
+    plain = [maxlink.Grid(p, maxlink.ML_F32, stream=sh) for p in probs]
+    grids = [maxlink.Grid(p, maxlink.ML_F32, stream=sh) for p in probs]
+    b = maxlink.Batch(grids, stream=sh)
+    try:
+        for g in plain:
+            g.step(32)
+        b.step(32)
+        choice, tune_ms = b.autotune(64)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for g in plain:
+            g.step(K)
+        e1.record(stream)
+        l0 = b.launches
+        b.step(K)
+        e2.record(stream)
+        stream.synchronize()
+        plain_ms, batch_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        launches = b.launches - l0
+        ab_p = np.array([g.absorbed() for g in plain])
+        ab_b = np.array([g.absorbed() for g in grids])
+        return {"workload": f"{len(probs)} plasmonic realisations, edges {{64,96,128,160}}, Drude sphere r=edge/6, "
+                            f"200-5000 emitters in a shell, z-polarised pulse", "instances": len(probs),
+                "cells": cells, "molecules": int(sum(p.molecules.count for p in probs)), "steps": K,
+                "dtype": "f32", "plain_ms": plain_ms, "batched_ms": batch_ms,
+                "plain_gcells": cells * K / plain_ms / 1e6, "batched_gcells": cells * K / batch_ms / 1e6,
+                "speedup": plain_ms / batch_ms, "blocks_per_sm": choice, "autotune_trial_ms": tune_ms,
+                "batched_launches": int(launches),
+                "absorbed_max_abs_diff": float(np.max(np.abs(ab_p - ab_b))),
+                "absorbed_sum": float(ab_b.sum())}
+    finally:
+        b.close()
+        for g in plain + grids:
+            g.close()
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -339,6 +390,7 @@ def run_ours(args, world, rank, local):
     d2h = prob.molecules.count * maxlink.ML_MAX_LEVELS * 8 + sum(8 * len(p.omegas) for p in prob.planes) / K
     g2.close()
     adjoint = measure_adjoint(args, stream) if (world == 1 and not args.no_adjoint) else None
+    batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -364,6 +416,7 @@ def run_ours(args, world, rank, local):
             "clocks": clocks,
             "molecule_steps_per_s": mol_steps,
             "adjoint": adjoint,
+            "batch": batch,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
                                    "field_pass": kms[1] / K, "plane_fold": kms[3] / K},
             "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
@@ -386,6 +439,9 @@ def main():
     ap.add_argument("--nmol", type=int, default=10000)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--adj-steps", type=int, default=3000)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
+    ap.add_argument("--batch-steps", type=int, default=3000)
+    ap.add_argument("--batch-count", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

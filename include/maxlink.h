@@ -226,6 +226,38 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
 ml_status ml_set_design_eps(ml_grid *g, const double *eps, int on_device, void *stream);
 ml_status ml_set_couplings(ml_grid *g, const double *gamma, int on_device, void *stream);
 
+/* ---- Batches of independent grids (many realisations of uneven sizes) ----------
+ * A batch advances several grids of the same precision and time step together:
+ * each step is one launch per kernel class over every instance's blocks (gather,
+ * molecules, current, one persistent field pass, and a DFT fold every 16 steps),
+ * and runs of 32 steps are replayed from a CUDA graph captured on first use.
+ * Results are identical to stepping each grid with ml_step.  The grids keep their
+ * own state and API (fields, flux, absorbed energy, checkpoints); while a batch
+ * exists, structural changes to a member (molecules, planes) are picked up at the
+ * next ml_batch_step.  Destroying a batch leaves the grids intact. */
+typedef struct ml_batch ml_batch;
+
+/* n grids (distinct, same precision and Courant number); *out receives the handle. */
+ml_status ml_batch_create(ml_grid *const *grids, int n, ml_batch **out);
+
+/* Enqueue nsteps steps of every grid in the batch on `stream`. */
+ml_status ml_batch_step(ml_batch *b, int64_t nsteps, void *stream);
+
+/* Field-pass grid: blocks_per_sm blocks per SM looping over the tiles (1..occupancy),
+ * or 0 for one block per tile; use_graph = 0 launches every step directly. */
+ml_status ml_batch_set_tuning(ml_batch *b, int blocks_per_sm, int use_graph);
+
+/* Time trial_steps steps for each field-pass grid shape, restore every grid after
+ * each trial, keep the fastest.  *blocks_per_sm and *ms (either may be NULL) receive
+ * the choice and its time.  Synchronises `stream`. */
+ml_status ml_batch_autotune(ml_batch *b, int trial_steps, void *stream, int *blocks_per_sm, double *ms);
+
+/* Kernels (and graph launches) this batch has enqueued. */
+int64_t ml_batch_launch_count(const ml_batch *b);
+
+/* Free the batch's own device memory and graph (not the grids).  Synchronises. */
+ml_status ml_batch_destroy(ml_batch *b);
+
 /* ---- Allocation-free gather (the paper has no counterpart) --------------------
  *
  * ml_gather_static computes the regularised field of Eq. E_regu_Emi,

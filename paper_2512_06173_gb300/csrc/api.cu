@@ -648,6 +648,93 @@ ml_status fold_planes(ml_grid *g, cudaStream_t s) {
 }
 
 template <typename T>
+void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
+    m = MolArgs<T>{};
+    m.nmol = g->nmol;
+    m.dt = (T)g->dt;
+    m.nx = g->nx; m.ny = g->ny; m.nz = g->nz; m.px = g->px; m.plane = g->plane;
+    for (int a = 0; a < 3; a++) { m.per[a] = g->per[a]; m.E[a] = (const T *)g->F[cur][a]; }
+    m.nlev = g->d_nlev; m.off = g->d_off; m.kind = g->d_kind; m.nsub = g->d_nsub; m.cmask = g->d_cmask;
+    m.gamma = (const T *)g->d_gamma; m.decay = (const T *)g->d_decay; m.dephase = (const T *)g->d_deph;
+    m.H0 = (const cx<T> *)g->d_H0; m.mu = (const cx<T> *)g->d_mu; m.pool = g->pool;
+    m.rho = (cx<T> *)g->d_rho;
+    m.moff = g->d_moff; m.mlist = g->d_mlist; m.part = (const T *)g->d_part;
+    m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
+    m.energy = g->d_energy; m.status = g->d_status;
+}
+
+template <typename T>
+void fill_gath_args(ml_grid *g, int cur, GathArgs<T> &ga) {
+    ga = GathArgs<T>{};
+    ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
+    for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = (const T *)g->F[cur][q]; }
+    ga.px = g->px; ga.plane = g->plane;
+    ga.off = g->d_joff; ga.ent = g->d_jent; ga.rec = (const T *)g->d_rec; ga.cmask = g->d_cmask;
+    ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
+}
+
+template <typename T>
+void fill_cur_args(ml_grid *g, CurArgs<T> &ca) {
+    ca = CurArgs<T>{};
+    ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
+    for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
+    ca.off = g->d_joff; ca.ent = g->d_jent; ca.rec = (const T *)g->d_rec;
+    ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
+    for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
+}
+
+// Arguments of the field pass reading level `cur`, with the DFT ring at slot 0.
+template <typename T>
+void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y) {
+    const int nxt = cur ^ 1;
+    y = YeeArgs<T>{};
+    y.nx = g->nx; y.ny = g->ny; y.nz = g->nz; y.px = g->px; y.py = g->py; y.plane = g->plane;
+    for (int a = 0; a < 3; a++) y.per[a] = g->per[a];
+    for (int f = 0; f < 6; f++) y.pml[f] = g->pml[f];
+    y.ntx = g->ntx; y.nty = g->nty; y.nchunk = g->nchunk; y.cz = g->cz; y.zcut = g->d_zcut;
+    y.dt = (T)g->dt;
+    for (int c = 0; c < 3; c++) {
+        y.Eo[c] = (const T *)g->F[cur][c];
+        y.Ho[c] = (const T *)g->F[cur][3 + c];
+        y.En[c] = (T *)g->F[nxt][c];
+        y.Hn[c] = (T *)g->F[nxt][3 + c];
+    }
+    for (int a = 0; a < 3; a++) {
+        y.cpml[a] = (const T *)g->cpml[a];
+        for (int q = 0; q < 2; q++) {
+            y.psiHo[a][q] = (const T *)g->psiH[cur][a][q];
+            y.psiHn[a][q] = (T *)g->psiH[nxt][a][q];
+            y.psiE[a][q] = (T *)g->psiE[a][q];
+        }
+    }
+    y.mat = g->mat;
+    y.mat_cb = (const T *)g->mat_cb; y.mat_dk = (const T *)g->mat_dk; y.mat_db = (const T *)g->mat_db;
+    for (int q = 0; q < 6; q++) { y.dbox[q] = g->dbox[q]; y.jbox[q] = g->jbox[q]; }
+    y.dcb = (const T *)g->dcb;
+    for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
+    y.absorbed_part = g->absorbed_part;
+    y.status = g->d_status;
+    if (g->nmol > 0)
+        for (int a = 0; a < 3; a++) {
+            y.jb0[a] = g->jb0[a];
+            y.jbn[a] = g->jbn[a];
+            y.Jb[a] = (const T *)g->d_J[a];
+        }
+    y.nsrc = (int)g->src.size();
+    for (int q = 0; q < y.nsrc; q++) y.src[q] = g->src[q];
+    y.step = g->step;
+    y.nplanes = (int)g->planes.size();
+    for (int p = 0; p < y.nplanes; p++) {
+        const Plane &pl = g->planes[p];
+        y.planes[p].axis = pl.axis;
+        y.planes[p].index = pl.index;
+        y.planes[p].nb = pl.nb;
+        y.planes[p].nc = pl.nc;
+        y.planes[p].buf = (T *)pl.d_buf;
+    }
+}
+
+template <typename T>
 ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
     for (long long it = 0; it < nsteps; it++) {
         const int cur = g->cur, nxt = cur ^ 1;
@@ -660,90 +747,31 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             CK(cudaStreamWaitEvent(g->side, g->ev_box, 0));
         }
         if (g->nmol > 0) {
-            MolArgs<T> m{};
-            m.nmol = g->nmol;
-            m.dt = (T)g->dt;
-            m.nx = g->nx; m.ny = g->ny; m.nz = g->nz; m.px = g->px; m.plane = g->plane;
-            for (int a = 0; a < 3; a++) { m.per[a] = g->per[a]; m.E[a] = (const T *)g->F[cur][a]; }
-            m.nlev = g->d_nlev; m.off = g->d_off; m.kind = g->d_kind; m.nsub = g->d_nsub; m.cmask = g->d_cmask;
-            m.gamma = (const T *)g->d_gamma; m.decay = (const T *)g->d_decay; m.dephase = (const T *)g->d_deph;
-            m.H0 = (const cx<T> *)g->d_H0; m.mu = (const cx<T> *)g->d_mu; m.pool = g->pool;
-            m.rho = (cx<T> *)g->d_rho;
-            m.moff = g->d_moff; m.mlist = g->d_mlist; m.part = (const T *)g->d_part;
-            m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
-            m.energy = g->d_energy; m.status = g->d_status;
             {
-                GathArgs<T> ga{};
-                ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
-                for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = (const T *)g->F[cur][q]; }
-                ga.px = g->px; ga.plane = g->plane;
-                ga.off = g->d_joff; ga.ent = g->d_jent; ga.rec = (const T *)g->d_rec; ga.cmask = g->d_cmask;
-                ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
+                GathArgs<T> ga;
+                fill_gath_args<T>(g, cur, ga);
                 LaunchScope ls(g, cs, 5);
                 CK(launch_gather<T>(ga, cs));
             }
             {
+                MolArgs<T> m;
+                fill_mol_args<T>(g, cur, m);
                 LaunchScope ls(g, cs, 0);
                 CK(launch_molecules<T>(m, cs));
             }
-            CurArgs<T> ca{};
-            ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
-            for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
-            ca.off = g->d_joff; ca.ent = g->d_jent; ca.rec = (const T *)g->d_rec;
-            ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
-            for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
             {
+                CurArgs<T> ca;
+                fill_cur_args<T>(g, ca);
                 LaunchScope ls(g, cs, 4);
                 CK(launch_current<T>(ca, cs));
             }
             CK(cudaEventRecord(g->ev_join, cs));
         }
-        YeeArgs<T> y{};
-        y.nx = g->nx; y.ny = g->ny; y.nz = g->nz; y.px = g->px; y.py = g->py; y.plane = g->plane;
-        for (int a = 0; a < 3; a++) y.per[a] = g->per[a];
-        for (int f = 0; f < 6; f++) y.pml[f] = g->pml[f];
-        y.ntx = g->ntx; y.nty = g->nty; y.nchunk = g->nchunk; y.cz = g->cz; y.zcut = g->d_zcut;
-        y.dt = (T)g->dt;
-        for (int c = 0; c < 3; c++) {
-            y.Eo[c] = (const T *)g->F[cur][c];
-            y.Ho[c] = (const T *)g->F[cur][3 + c];
-            y.En[c] = (T *)g->F[nxt][c];
-            y.Hn[c] = (T *)g->F[nxt][3 + c];
-        }
-        for (int a = 0; a < 3; a++) {
-            y.cpml[a] = (const T *)g->cpml[a];
-            for (int q = 0; q < 2; q++) {
-                y.psiHo[a][q] = (const T *)g->psiH[cur][a][q];
-                y.psiHn[a][q] = (T *)g->psiH[nxt][a][q];
-                y.psiE[a][q] = (T *)g->psiE[a][q];
-            }
-        }
-        y.mat = g->mat;
-        y.mat_cb = (const T *)g->mat_cb; y.mat_dk = (const T *)g->mat_dk; y.mat_db = (const T *)g->mat_db;
-        for (int q = 0; q < 6; q++) { y.dbox[q] = g->dbox[q]; y.jbox[q] = g->jbox[q]; }
-        y.dcb = (const T *)g->dcb;
-        for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
-        y.absorbed_part = g->absorbed_part;
-        y.status = g->d_status;
-        if (g->nmol > 0)
-            for (int a = 0; a < 3; a++) {
-                y.jb0[a] = g->jb0[a];
-                y.jbn[a] = g->jbn[a];
-                y.Jb[a] = (const T *)g->d_J[a];
-            }
-        y.nsrc = (int)g->src.size();
-        for (int q = 0; q < y.nsrc; q++) y.src[q] = g->src[q];
-        y.step = g->step;
+        YeeArgs<T> y;
+        fill_yee_args<T>(g, cur, y);
         if (!g->planes.empty() && g->nsamp == 0) g->samp_step0 = g->step;
-        y.nplanes = (int)g->planes.size();
-        for (int p = 0; p < y.nplanes; p++) {
-            const Plane &pl = g->planes[p];
-            y.planes[p].axis = pl.axis;
-            y.planes[p].index = pl.index;
-            y.planes[p].nb = pl.nb;
-            y.planes[p].nc = pl.nc;
-            y.planes[p].buf = (T *)pl.d_buf + (size_t)g->nsamp * 4 * pl.nb * pl.nc;
-        }
+        for (int p = 0; p < y.nplanes; p++)
+            y.planes[p].buf += (size_t)g->nsamp * 4 * y.planes[p].nb * y.planes[p].nc;
         if (chain) {
             // blocks clear of the current box overlap the chain; the others wait for J
             if (g->nblA > 0) {
@@ -778,6 +806,13 @@ template ml_status fold_planes<float>(ml_grid *, cudaStream_t);
 template ml_status fold_planes<double>(ml_grid *, cudaStream_t);
 template ml_status step_impl<float>(ml_grid *, long long, cudaStream_t);
 template ml_status step_impl<double>(ml_grid *, long long, cudaStream_t);
+#define ML_FILL(T)                                                    \
+    template void fill_mol_args<T>(ml_grid *, int, MolArgs<T> &);     \
+    template void fill_gath_args<T>(ml_grid *, int, GathArgs<T> &);   \
+    template void fill_cur_args<T>(ml_grid *, CurArgs<T> &);          \
+    template void fill_yee_args<T>(ml_grid *, int, YeeArgs<T> &);
+ML_FILL(float)
+ML_FILL(double)
 
 }  // namespace ml
 

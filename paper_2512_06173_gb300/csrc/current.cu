@@ -49,13 +49,12 @@ __device__ __forceinline__ void rec_slots(int c, int &bx, int &ay, int &cz) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) {
+__device__ __forceinline__ void current_body(const CurArgs<T> &a, const int blk) {
     constexpr int JEB = sizeof(T) == 4 ? 32 : 16;  // entries staged per batch
     __shared__ __align__(16) T sR[JEB][REC];
     __shared__ __align__(16) T sG[JEB][JY][JZ];
     __shared__ T sC[JEB];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * JX + tx;
-    const int blk = blockIdx.x;
     const int beg = a.off[blk], end = a.off[blk + 1];
     if (beg == end) return;  // no window here: J stays 0 (the box is zeroed at setup)
     const int bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
@@ -104,12 +103,11 @@ __global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) {
 // entry e and component c goes to part[e][c]; nothing is accumulated across
 // blocks here, so the result does not depend on scheduling.
 template <typename T>
-__global__ void __launch_bounds__(JX *JY) gather_kernel(const GathArgs<T> a) {
+__device__ __forceinline__ void gather_body(const GathArgs<T> &a, const int blk) {
     constexpr int JEB = sizeof(T) == 4 ? 32 : 16;
     __shared__ __align__(16) T sE[JZ][JY][JX];
     __shared__ __align__(16) T sR[JEB][REC];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * JX + tx;
-    const int blk = blockIdx.x;
     const int beg = a.off[blk], end = a.off[blk + 1];
     if (beg == end) return;
     const int bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
@@ -158,6 +156,40 @@ __global__ void __launch_bounds__(JX *JY) gather_kernel(const GathArgs<T> a) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(JX *JY) gather_kernel(const GathArgs<T> a) { gather_body(a, (int)blockIdx.x); }
+
+template <typename T>
+__global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) { current_body(a, (int)blockIdx.x); }
+
+// Batched forms: one block per (instance, box block) work item; the gather reads the
+// time level of this step.
+template <typename T>
+__global__ void __launch_bounds__(JX *JY) gather_batch_kernel(const GathBatch<T> b) {
+    const int2 wk = b.work[blockIdx.x];
+    gather_body(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(JX *JY) current_batch_kernel(const CurBatch<T> b) {
+    const int2 wk = b.work[blockIdx.x];
+    current_body(b.args[wk.x], wk.y);
+}
+
+template <typename T>
+cudaError_t launch_gather_batch(const GathBatch<T> &b, int nwork, cudaStream_t s) {
+    if (nwork == 0) return cudaSuccess;
+    gather_batch_kernel<T><<<nwork, dim3(JX, JY), 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_current_batch(const CurBatch<T> &b, int nwork, cudaStream_t s) {
+    if (nwork == 0) return cudaSuccess;
+    current_batch_kernel<T><<<nwork, dim3(JX, JY), 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s) {
     if (a.nblocks == 0) return cudaSuccess;
     gather_kernel<T><<<a.nblocks, dim3(JX, JY), 0, s>>>(a);
@@ -174,6 +206,8 @@ cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s) {
 #define ML_INST(T)                                                                                 \
     template cudaError_t launch_current<T>(const CurArgs<T> &, cudaStream_t);                      \
     template cudaError_t launch_gather<T>(const GathArgs<T> &, cudaStream_t);                      \
+    template cudaError_t launch_gather_batch<T>(const GathBatch<T> &, int, cudaStream_t);          \
+    template cudaError_t launch_current_batch<T>(const CurBatch<T> &, int, cudaStream_t);          \
     template cudaError_t launch_records<T>(int, const int4 *, const int *, const T *, T *, cudaStream_t);
 ML_INST(float)
 ML_INST(double)

@@ -44,8 +44,8 @@ cudaError_t launch_dft_sample(const PlaneArgs<T> &a, cudaStream_t s) {
 // the inner K-term sum runs in the field precision T with phases rounded from FP64,
 // the product with e^{i w t_0} dt and the running sum are FP64.
 template <typename T>
-__global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
-                                double dt, double2 *acc) {
+__device__ __forceinline__ void fold_body(const T *buf, int nsamp, int ncell, int nfreq, const double *omega,
+                                          long long step0, double dt, double2 *acc, long long t) {
     __shared__ T phr[DFT_K * ML_MAX_FREQS_DEV];
     __shared__ T phi[DFT_K * ML_MAX_FREQS_DEV];
     __shared__ double2 p0[2 * ML_MAX_FREQS_DEV];
@@ -64,7 +64,6 @@ __global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, c
         p0[ML_MAX_FREQS_DEV + f] = make_double2(cs * dt, sn * dt);
     }
     __syncthreads();
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= 4ll * ncell) return;
     const int comp = (int)(t / ncell), cell = (int)(t % ncell);
     const double2 *ph0 = comp < 2 ? p0 : p0 + ML_MAX_FREQS_DEV;
@@ -83,6 +82,36 @@ __global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, c
         x.y += (double)re * e0.y + (double)im * e0.x;
         *o = x;
     }
+}
+
+template <typename T>
+__global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
+                                double dt, double2 *acc) {
+    fold_body(buf, nsamp, ncell, nfreq, omega, step0, dt, acc, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+// Batched fold: one block per (plane descriptor, 256-entry chunk) work item; the first
+// sample's step is the descriptor's base + the device step counter + s_first.
+template <typename T>
+__global__ void dft_fold_batch_kernel(const FoldBatch<T> b) {
+    const int2 wk = b.work[blockIdx.x];
+    const FoldDesc<T> d = b.desc[wk.x];
+    fold_body(d.buf, b.nsamp, d.ncell, d.nfreq, d.omega, d.step_base + *b.boff + b.s_first, b.dt, d.acc,
+              (long long)wk.y * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
+cudaError_t launch_fold_batch(const FoldBatch<T> &b, int nwork, cudaStream_t s) {
+    if (nwork == 0 || b.nsamp == 0) return cudaSuccess;
+    dft_fold_batch_kernel<T><<<nwork, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+__global__ void tick_kernel(long long *c, int add) { *c += add; }
+
+cudaError_t launch_tick(long long *c, int add, cudaStream_t s) {
+    tick_kernel<<<1, 1, 0, s>>>(c, add);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -126,7 +155,8 @@ cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double 
 #define ML_INST(T)                                                                          \
     template cudaError_t launch_dft_sample<T>(const PlaneArgs<T> &, cudaStream_t);          \
     template cudaError_t launch_dft_fold<T>(const T *, int, int, int, const double *, long long, double, \
-                                            double2 *, cudaStream_t);
+                                            double2 *, cudaStream_t);                                 \
+    template cudaError_t launch_fold_batch<T>(const FoldBatch<T> &, int, cudaStream_t);
 ML_INST(float)
 ML_INST(double)
 

@@ -153,6 +153,12 @@ std::vector<Blob> state_blobs(ml_grid *g);
 template <typename T>
 ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s);
 
+// Kernel arguments of one grid (level `cur` = the field level the step reads).
+template <typename T> void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m);
+template <typename T> void fill_gath_args(ml_grid *g, int cur, GathArgs<T> &ga);
+template <typename T> void fill_cur_args(ml_grid *g, CurArgs<T> &ca);
+template <typename T> void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y);
+
 // Fold the pending plane samples into the FP64 DFT accumulators.
 template <typename T>
 ml_status fold_planes(ml_grid *g, cudaStream_t s);

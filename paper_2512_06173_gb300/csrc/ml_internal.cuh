@@ -200,7 +200,64 @@ struct PlaneArgs {
     int slot;
 };
 
+// ------------------------------------------------------------------ batches
+// Many independent grids advanced by the same launches: per-instance arguments live in
+// device arrays and each launch walks a list of (instance, block) work items.  A
+// sequence of steps is indexed by s (baked into the launch) plus a device step counter
+// (boff) that a tick kernel advances, so that a captured sequence can be replayed.
+template <typename T>
+struct YeeBatch {
+    const YeeArgs<T> *args;   // per instance, for level 0 (reads F[0], writes F[1]), step = base
+    const TmapSet *maps;      // per instance, two: level 0 and level 1
+    const int *lev0;          // level each instance reads at s = 0
+    const int2 *work;         // (instance, tile)
+    int nwork;
+    const long long *boff;
+    int s;                    // step within the sequence
+    int slot;                 // DFT ring slot of this step
+};
+template <typename T>
+struct GathBatch {
+    const GathArgs<T> *args;  // per instance, two: E of level 0 and of level 1
+    const int *lev0;
+    const int2 *work;         // (instance, box block)
+    int s;
+};
+template <typename T>
+struct CurBatch {
+    const CurArgs<T> *args;
+    const int2 *work;         // (instance, box block)
+};
+template <typename T>
+struct MolBatch {
+    const MolArgs<T> *args;
+    const int2 *work;         // (instance, first molecule of the block)
+};
+template <typename T>
+struct FoldDesc {
+    const T *buf;
+    int ncell, nfreq;
+    const double *omega;
+    long long step_base;
+    double2 *acc;
+};
+template <typename T>
+struct FoldBatch {
+    const FoldDesc<T> *desc;
+    const int2 *work;         // (descriptor, chunk of 256 entries)
+    int nsamp;
+    const long long *boff;
+    int s_first;
+    double dt;
+};
+
 // launchers (explicit instantiations for float and double live in the .cu files)
+template <typename T> cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_gather_batch(const GathBatch<T> &b, int nwork, cudaStream_t s);
+template <typename T> cudaError_t launch_current_batch(const CurBatch<T> &b, int nwork, cudaStream_t s);
+template <typename T> cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t s);
+template <typename T> cudaError_t launch_fold_batch(const FoldBatch<T> &b, int nwork, cudaStream_t s);
+cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s);

@@ -71,11 +71,11 @@ __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<T> a) {
+__device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0) {
     __shared__ MolShared<T> sh;
     const int lane = threadIdx.x & 31;
     const int wl = threadIdx.x >> 5;
-    const int m = blockIdx.x * MOL_WARPS + wl;
+    const int m = m0 + wl;
     if (m >= a.nmol) return;  // whole warp leaves together
 
     // ---- 0. every load of this molecule's data, issued before any is used
@@ -241,6 +241,25 @@ __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<
 }
 
 template <typename T>
+__global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<T> a) {
+    molecule_body(a, (int)blockIdx.x * MOL_WARPS);
+}
+
+// Batched form: one block per (instance, first molecule) work item.
+template <typename T>
+__global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
+    const int2 wk = b.work[blockIdx.x];
+    molecule_body(b.args[wk.x], wk.y);
+}
+
+template <typename T>
+cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t s) {
+    if (nwork == 0) return cudaSuccess;
+    molecule_batch_kernel<T><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s) {
     if (a.nmol == 0) return cudaSuccess;
     int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
@@ -333,6 +352,7 @@ cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long lo
 
 #define ML_INST(T)                                                                                              \
     template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t);                                 \
+    template cudaError_t launch_molecules_batch<T>(const MolBatch<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \
                                            const int *, const int *, const int *, T *, cudaStream_t);           \
     template cudaError_t launch_mol_export<T>(int, int, const int *, const long long *, const cx<T> *, const T *, \

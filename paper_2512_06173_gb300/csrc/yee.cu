@@ -109,8 +109,10 @@ constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before givin
 // caller guarantees the tile and its halo touch no CPML layer, wall, periodic
 // image, material/source cell, molecule window or flux plane, so none of those
 // paths is compiled in.
+// Returns false when a plane wait gave up (the block then reported ML_ERR_TIMEOUT and
+// drained its copies); uniform over the block.
 template <typename T, bool GEN>
-__device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &maps) {
+__device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
     constexpr int S = yee_stages<T>();
     constexpr int BP = box_pad<T>();
     constexpr int SW = 6 * BP;  // elements per stage
@@ -126,7 +128,6 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
-    const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY;
     const int k0 = a.zcut[bz];
@@ -502,7 +503,7 @@ __device__ __forceinline__ void yee_body(const YeeArgs<T> &a, const TmapSet &map
                 a.absorbed_part[tile] += s;
             }
         }
-        return;
+        return true;
     }
 drain:
     // a plane never arrived: report, then wait (bounded) for the copies this block
@@ -515,13 +516,13 @@ drain:
         }
     }
     __syncthreads();
+    return false;
 }
 
 // True when the block's tile (with its one-cell halo) needs none of the optional
 // paths of the field pass.
 template <typename T>
-__device__ __forceinline__ bool interior_block(const YeeArgs<T> &a) {
-    const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
+__device__ __forceinline__ bool interior_block(const YeeArgs<T> &a, const int tile) {
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
     if (a.mat || a.dcb || a.JD[0] || a.nsrc) return false;
@@ -543,8 +544,74 @@ __device__ __forceinline__ bool interior_block(const YeeArgs<T> &a) {
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_kernel(const YeeArgs<T> a,
                                                                            const __grid_constant__ TmapSet maps) {
-    if (interior_block(a)) yee_body<T, false>(a, maps);
-    else yee_body<T, true>(a, maps);
+    const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
+    if (interior_block(a, tile)) yee_body<T, false>(a, maps, tile);
+    else yee_body<T, true>(a, maps, tile);
+}
+
+// Batched field pass: one persistent launch for the tiles of many grids.  Each block
+// walks the (instance, tile) work list; per item it copies the instance's arguments
+// into shared memory, turns them to the time level, step and DFT ring slot of this
+// step, and runs the same body as the single-grid kernel.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_batch_kernel(const YeeBatch<T> b) {
+    __shared__ __align__(16) YeeArgs<T> sa;
+    __shared__ const TmapSet *smaps;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    constexpr int NW = (int)(sizeof(YeeArgs<T>) / sizeof(int));
+    static_assert(sizeof(YeeArgs<T>) % sizeof(int) == 0, "argument block copied as words");
+    for (int w = blockIdx.x; w < b.nwork; w += gridDim.x) {
+        const int2 wk = b.work[w];
+        __syncthreads();  // the previous item is done with sa and the barriers
+        if (w != (int)blockIdx.x && tid == 0)
+            for (int q = 0; q < yee_stages<T>(); q++) mbar_inval(&bars[q]);
+        const int *src = reinterpret_cast<const int *>(b.args + wk.x);
+        int *dst = reinterpret_cast<int *>(&sa);
+        for (int q = tid; q < NW; q += NTHREADS) dst[q] = src[q];
+        __syncthreads();
+        if (tid == 0) {
+            const int lev = (b.lev0[wk.x] + b.s) & 1;
+            if (lev) {
+                for (int c = 0; c < 3; c++) {
+                    const T *e = sa.Eo[c], *h = sa.Ho[c];
+                    sa.Eo[c] = sa.En[c];
+                    sa.Ho[c] = sa.Hn[c];
+                    sa.En[c] = const_cast<T *>(e);
+                    sa.Hn[c] = const_cast<T *>(h);
+                    for (int q = 0; q < 2; q++) {
+                        const T *p = sa.psiHo[c][q];
+                        sa.psiHo[c][q] = sa.psiHn[c][q];
+                        sa.psiHn[c][q] = const_cast<T *>(p);
+                    }
+                }
+            }
+            sa.step += *b.boff + b.s;
+            for (int p = 0; p < sa.nplanes; p++)
+                sa.planes[p].buf += (size_t)b.slot * 4 * sa.planes[p].nb * sa.planes[p].nc;
+            smaps = b.maps + 2 * wk.x + lev;
+        }
+        __syncthreads();
+        const bool ok = interior_block(sa, wk.y) ? yee_body<T, false>(sa, *smaps, wk.y)
+                                                 : yee_body<T, true>(sa, *smaps, wk.y);
+        // a wait that gave up may leave copies in flight: stop reusing this block
+        if (!ok) return;
+    }
+}
+
+template <typename T>
+cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s) {
+    static bool configured = false;
+    const size_t smem = yee_smem_bytes<T>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(yee_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (b.nwork == 0) return cudaSuccess;
+    yee_batch_kernel<T><<<grid, dim3(TX, NTY), smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -660,6 +727,7 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
 
 #define ML_INST(T)                                                                                            \
     template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t);                               \
+    template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t);                                        \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \
     template cudaError_t launch_zero_pec<T>(T *const *, int, int, int, int, long long, const int *, cudaStream_t);

@@ -108,6 +108,12 @@ def load(build_if_missing: bool = True):
         "ml_adjoint_run": (I, [P, I64, I, I, I, P, P, P, I, P]),
         "ml_set_design_eps": (I, [P, P, I, P]),
         "ml_set_couplings": (I, [P, P, I, P]),
+        "ml_batch_create": (I, [P, I, C.POINTER(P)]),
+        "ml_batch_step": (I, [P, I64, P]),
+        "ml_batch_set_tuning": (I, [P, I, I]),
+        "ml_batch_autotune": (I, [P, I, P, C.POINTER(I), C.POINTER(D)]),
+        "ml_batch_launch_count": (I64, [P]),
+        "ml_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -255,6 +261,37 @@ def ml_set_couplings(h: int, gamma_ptr: int, on_device: bool = False, stream: in
     _check(load().ml_set_couplings(C.c_void_p(h), C.c_void_p(gamma_ptr), 1 if on_device else 0, C.c_void_p(stream)))
 
 
+def ml_batch_create(handles) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    out = C.c_void_p()
+    _check(load().ml_batch_create(arr, len(handles), C.byref(out)))
+    return out.value
+
+
+def ml_batch_step(b: int, nsteps: int, stream: int = 0):
+    _check(load().ml_batch_step(C.c_void_p(b), int(nsteps), C.c_void_p(stream)))
+
+
+def ml_batch_set_tuning(b: int, blocks_per_sm: int, use_graph: bool = True):
+    _check(load().ml_batch_set_tuning(C.c_void_p(b), int(blocks_per_sm), 1 if use_graph else 0))
+
+
+def ml_batch_autotune(b: int, trial_steps: int, stream: int = 0):
+    choice = C.c_int(0)
+    ms = C.c_double(0.0)
+    _check(load().ml_batch_autotune(C.c_void_p(b), int(trial_steps), C.c_void_p(stream), C.byref(choice),
+                                    C.byref(ms)))
+    return choice.value, ms.value
+
+
+def ml_batch_launch_count(b: int) -> int:
+    return int(load().ml_batch_launch_count(C.c_void_p(b)))
+
+
+def ml_batch_destroy(b: int):
+    _check(load().ml_batch_destroy(C.c_void_p(b)))
+
+
 def ml_gather_static(E_ptr: int, nx: int, ny: int, nz: int, periodic, nmol: int, pos_ptr: int,
                      sigma_ptr: int, gamma_ptr: int, out_ptr: int, stream: int = 0):
     """Allocation-free regularised field from a caller-owned FP32 field (device
@@ -328,6 +365,39 @@ def molecule_desc(mol):
     d.rho = arr(np.ascontiguousarray(mol.rho0, np.complex128).view(np.float64), np.float64)
     d.pool = int(mol.H0.shape[0])
     return d, keep
+
+
+class Batch:
+    """Several Grids advanced together (one launch per kernel class per step)."""
+
+    def __init__(self, grids, stream: int = 0):
+        self.grids = list(grids)
+        self.stream = stream
+        self.h = ml_batch_create([g.h for g in self.grids])
+
+    def step(self, n: int):
+        ml_batch_step(self.h, n, self.stream)
+
+    def tune(self, blocks_per_sm: int, use_graph: bool = True):
+        ml_batch_set_tuning(self.h, blocks_per_sm, use_graph)
+
+    def autotune(self, trial_steps: int = 64):
+        return ml_batch_autotune(self.h, trial_steps, self.stream)
+
+    @property
+    def launches(self) -> int:
+        return ml_batch_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ml_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Grid:

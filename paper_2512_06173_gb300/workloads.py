@@ -310,6 +310,47 @@ def adjoint_design(n: int = 192, design: int = 96, nmol: int = 2000, pml: int = 
                    name=f"adjoint-design-{n}^3-box{design}^3-{nmol}tls")
 
 
+def plasmonic_instance(edge: int, nmol: int, rng, pml: int = 8, omega: float = 0.25, mu12: float = 0.05,
+                       sigma: float = 1.5, width: float = 20.0) -> Problem:
+    """One realisation of the plasmonic-heating geometry: cube of `edge` cells with CPML
+    on every face, a Drude sphere (eps_inf 1, plasma frequency 1, damping 0.05) of
+    radius edge/6 at the centre, `nmol` ground-state two-level emitters (omega0
+    `omega`, mu12 along z) at positions uniform in volume in the shell r+2 <= |x-c| <=
+    r+6, and a z-polarised Gaussian-pulse current sheet on the plane x = pml + 2."""
+    n = edge
+    r = edge / 6.0
+    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    c = n / 2.0
+    inside = (xx + 0.5 - c) ** 2 + (yy + 0.5 - c) ** 2 + (zz + 0.5 - c) ** 2 < r * r
+    mat = np.zeros((n, n, n), np.uint8)
+    mat[inside] = 1
+    # uniform in the shell volume: radius by inverse CDF of r^2, direction uniform
+    r0, r1 = r + 2.0, r + 6.0
+    u = rng.uniform(0, 1, nmol)
+    rad = (r0 ** 3 + u * (r1 ** 3 - r0 ** 3)) ** (1.0 / 3.0)
+    v = rng.normal(size=(nmol, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    pos = c + rad[:, None] * v
+    mats = [tls(tuple(pos[m]), omega, mu12, axis=2, sigma=sigma, cg=1.0, ce=0.0) for m in range(nmol)]
+    src = [Source(axis=0, index=pml + 2, comp=2, amp=1.0, omega=omega, width=width, t0=5.0 * width)]
+    return Problem(n, n, n, 0.5, pml=(pml,) * 6, mat=mat,
+                   materials=[Material(1.0), Material(1.0, wp=1.0, gamma=0.05)], sources=src,
+                   molecules=pack_molecules(mats), name=f"plasmonic-{n}^3-{nmol}tls")
+
+
+def plasmonic_batch(count: int = 64, seed: int = 5, edges=(64, 96, 128, 160), nmol_range=(200, 5000)) -> List[Problem]:
+    """`count` independent realisations: edge drawn uniformly from `edges`, emitter
+    count uniform in `nmol_range` (stand-in for the plasmonic-heating ensembles of
+    Sec. IV.D as a batch of disorder realisations)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        edge = int(rng.choice(edges))
+        nmol = int(rng.integers(nmol_range[0], nmol_range[1] + 1))
+        out.append(plasmonic_instance(edge, nmol, rng))
+    return out
+
+
 def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4,
                   multilevel: bool = True, eps_map: bool = True, drude: bool = False,
                   source: bool = True, planes: bool = True, periodic=(False, False, False)) -> Problem:

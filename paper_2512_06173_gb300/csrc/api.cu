@@ -195,9 +195,12 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         const int target = 8 * 152;
         const int want = std::max(1, std::min((target + tiles - 1) / tiles, (g->nz + 3) / 4));
         const int zl = g->pml[4], zh = g->pml[5];
+        // the low layer's chunk also takes the first plane above it: the chunk after it
+        // then recomputes, as its z-1 neighbour, a plane outside the layer
+        const int zlc = zl > 0 ? std::min(zl + 1, g->nz - zh) : 0;
         std::vector<std::pair<int, int>> seg;
-        if (zl > 0) seg.push_back({0, zl});
-        if (g->nz - zh > zl) seg.push_back({zl, g->nz - zh});
+        if (zlc > 0) seg.push_back({0, zlc});
+        if (g->nz - zh > zlc) seg.push_back({zlc, g->nz - zh});
         if (zh > 0) seg.push_back({g->nz - zh, g->nz});
         int len = std::min(16, std::max(4, (g->nz + want - 1) / want));
         // tuning knob: target planes per chunk (shorter chunks shrink the last
@@ -326,6 +329,38 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     for (int q = 0; q < d->n_sources; q++) {
         const ml_source &s = d->sources[q];
         g->src.push_back(SrcDev{s.axis, s.index, s.comp, s.amp, s.omega, s.width, s.t0});
+    }
+    {
+        // tiles whose own cells need the per-cell material path: a non-background
+        // material, the design box, the Drude box or a source plane
+        std::vector<int> zt(g->nz);
+        for (int c = 0; c < g->nchunk; c++)
+            for (int k = g->zcut[c]; k < g->zcut[c + 1]; k++) zt[k] = c;
+        std::vector<uint8_t> fl((size_t)g->nblocks, 0);
+        auto tile_of = [&](int i, int j, int k) { return ((long long)zt[k] * g->nty + j / TY) * g->ntx + i / TX; };
+        if (d->mat)
+            for (int k = 0; k < g->nz; k++)
+                for (int j = 0; j < g->ny; j++)
+                    for (int i = 0; i < g->nx; i++)
+                        if (d->mat[((long long)k * g->ny + j) * g->nx + i] != 0) fl[tile_of(i, j, k)] = 1;
+        for (int bz = 0; bz < g->nchunk; bz++)
+            for (int by = 0; by < g->nty; by++)
+                for (int bx = 0; bx < g->ntx; bx++) {
+                    const int lo[3] = {bx * TX, by * TY, g->zcut[bz]};
+                    const int hi[3] = {std::min(g->nx, bx * TX + TX), std::min(g->ny, by * TY + TY), g->zcut[bz + 1]};
+                    auto meets = [&](const int *box) {
+                        if (box[3] <= 0) return false;
+                        for (int a = 0; a < 3; a++)
+                            if (box[a] >= hi[a] || box[a] + box[3 + a] <= lo[a]) return false;
+                        return true;
+                    };
+                    bool f = meets(g->dbox) || meets(g->jbox);
+                    for (auto &q : g->src)
+                        if (q.index >= lo[q.axis] && q.index < hi[q.axis]) f = true;
+                    if (f) fl[((long long)bz * g->nty + by) * g->ntx + bx] = 1;
+                }
+        GA(g->d_tflags, fl.size());
+        GC(cudaMemcpy(g->d_tflags, fl.data(), fl.size(), cudaMemcpyHostToDevice));
     }
     GC(cudaDeviceSynchronize());
     *out = g;
@@ -692,6 +727,7 @@ void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y) {
     for (int a = 0; a < 3; a++) y.per[a] = g->per[a];
     for (int f = 0; f < 6; f++) y.pml[f] = g->pml[f];
     y.ntx = g->ntx; y.nty = g->nty; y.nchunk = g->nchunk; y.cz = g->cz; y.zcut = g->d_zcut;
+    y.tflags = g->d_tflags;
     y.dt = (T)g->dt;
     for (int c = 0; c < 3; c++) {
         y.Eo[c] = (const T *)g->F[cur][c];

@@ -43,6 +43,7 @@ struct ml_grid {
     int ntx = 0, nty = 0, nchunk = 0, cz = 0, nblocks = 0;
     std::vector<int> zcut;  // chunk boundaries along z
     int *d_zcut = nullptr;
+    uint8_t *d_tflags = nullptr;  // per tile: bit 0 = own cells need the material path
     int px = 0, py = 0;
     long long plane = 0;
     size_t vol = 0;  // padded elements per array

@@ -69,6 +69,7 @@ struct YeeArgs {
     int pml[6];
     int ntx, nty, nchunk, cz;   // cz: longest chunk
     const int *blist;           // blocks of this launch (tile indices), or null for all
+    const uint8_t *tflags;      // per tile: bit 0 = some own cell needs the material path
     const int *zcut;            // chunk c covers planes [zcut[c], zcut[c+1])
     T dt;
     const T *Eo[3];

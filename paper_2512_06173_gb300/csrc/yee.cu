@@ -105,14 +105,15 @@ __device__ __forceinline__ T src_value(const SrcDev &q, double t) {
 
 constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before giving up
 
-// Body of the field pass for one block.  GEN = false is the interior form: the
-// caller guarantees the tile and its halo touch no CPML layer, wall, periodic
-// image, material/source cell, molecule window or flux plane, so none of those
-// paths is compiled in.
+// Body of the field pass for one block.  MODE 0 is the interior form: the caller
+// guarantees the tile and its halo touch no CPML layer, wall, periodic image or
+// material/source cell, so none of those paths is compiled in.  MODE 1 adds the
+// CPML layers and the index-0 walls only; MODE 2 has every path.
 // Returns false when a plane wait gave up (the block then reported ML_ERR_TIMEOUT and
 // drained its copies); uniform over the block.
-template <typename T, bool GEN>
+template <typename T, int MODE>
 __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
+    constexpr bool GEN = MODE > 0, FULL = MODE == 2;
     constexpr int S = yee_stages<T>();
     constexpr int BP = box_pad<T>();
     constexpr int SW = 6 * BP;  // elements per stage
@@ -143,14 +144,24 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const bool fx = GEN && (a.pml[0] | a.pml[1]) && (x0 - 1 < a.pml[0] || x0 + TX > a.nx - a.pml[1]);
     const bool fy = GEN && (a.pml[2] | a.pml[3]) && (y0 - 1 < a.pml[2] || y0 + TY > a.ny - a.pml[3]);
     const bool zl = GEN && (a.pml[4] | a.pml[5]) != 0;
-    const bool img = GEN && ((a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
+    const bool img = FULL && ((a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
                              (a.per[2] && (k0 == 0 || k1 == a.nz)));
     const bool walls = GEN && ((!a.per[0] && x0 == 0) || (!a.per[1] && y0 == 0) || (!a.per[2] && k0 == 0));
-    const bool general = GEN && (a.mat != nullptr || a.dcb != nullptr || a.JD[0] != nullptr || a.nsrc > 0);
+    // per-cell material work (material table, design box, Drude, sources): only tiles
+    // whose own cells need it, when the grid has the per-tile flags
+    const bool general = FULL && (a.tflags ? (a.tflags[tile] & 1) != 0
+                                          : (a.mat != nullptr || a.dcb != nullptr || a.JD[0] != nullptr || a.nsrc > 0));
     // does the tile's column meet the box of the molecular current?
-    const bool has_mol = GEN && (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
+    const bool has_mol = (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
                          x0 + TX > a.jb0[0] && y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] &&
                          k0 < a.jb0[2] + a.jbn[2] && k1 > a.jb0[2];
+    // does a flux plane cross the tile (block-uniform)?
+    bool has_pl = false;
+    for (int p = 0; p < a.nplanes; p++) {
+        const int ax = a.planes[p].axis, idx = a.planes[p].index;
+        const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
+        if (idx >= lo && idx < hi) has_pl = true;
+    }
     const T cb0 = a.mat_cb[0];
     const int col = tx + 4;
     const int ob = (ty * RY + 1) * BOXW + col;       // first own cell inside a staged box
@@ -171,7 +182,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const int syh = fy ? slab(hjc, a.ny, a.pml[2], a.pml[3]) : -1;
     const int oh = hys * BOXW + hxs + 3;
 
-    if (GEN && tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
+    if (FULL && tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
     if (fx)
         for (int t = tid; t < 6 * BOXW; t += NTHREADS) {
             const int r = t / BOXW, cc = t % BOXW;
@@ -455,7 +466,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 }
                 // ---- DFT flux planes through this cell: E^{n+1} and the mean of H^{n+1/2}
                 // on both sides of the plane, written to the current sample slot
-                for (int p = 0; p < (GEN ? a.nplanes : 0); p++) {
+                for (int p = 0; p < (has_pl ? a.nplanes : 0); p++) {
                     const PlaneDev<T> &pl = a.planes[p];
                     const int ax = pl.axis;
                     if ((ax == 0 ? i : (ax == 1 ? j : k)) != pl.index) continue;
@@ -492,7 +503,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             sc = sn;
             if (++sn == S) { sn = 0; pn ^= 1u; }
         }
-        if (GEN && a.JD[0]) {
+        if (FULL && a.JD[0]) {
             // fixed-order block reduction into this block's accumulator
             for (int q = 16; q > 0; q >>= 1) absorbed += __shfl_xor_sync(0xffffffffu, absorbed, q);
             if (tx == 0) s_red[ty] = absorbed;
@@ -519,34 +530,47 @@ drain:
     return false;
 }
 
-// True when the block's tile (with its one-cell halo) needs none of the optional
-// paths of the field pass.
+// True when the block's tile (with its one-cell halo) needs none of the CPML, wall,
+// periodic-image and per-cell material paths of the field pass (the molecular
+// current and flux-plane sampling are block-uniform branches of every body).
 template <typename T>
 __device__ __forceinline__ bool interior_block(const YeeArgs<T> &a, const int tile) {
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
-    if (a.mat || a.dcb || a.JD[0] || a.nsrc) return false;
+    if (a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD[0] || a.nsrc)) return false;
     if (x0 == 0 || y0 == 0 || k0 == 0 || x0 + TX >= a.nx || y0 + TY >= a.ny || k1 >= a.nz) return false;
     if ((a.pml[0] && x0 - 1 < a.pml[0]) || (a.pml[1] && x0 + TX > a.nx - a.pml[1])) return false;
     if ((a.pml[2] && y0 - 1 < a.pml[2]) || (a.pml[3] && y0 + TY > a.ny - a.pml[3])) return false;
     if ((a.pml[4] && k0 - 1 < a.pml[4]) || (a.pml[5] && k1 > a.nz - a.pml[5])) return false;
-    if ((a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] && x0 + TX > a.jb0[0] &&
-        y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] && k0 < a.jb0[2] + a.jbn[2] && k1 > a.jb0[2])
-        return false;
-    for (int p = 0; p < a.nplanes; p++) {
-        const int ax = a.planes[p].axis, idx = a.planes[p].index;
-        const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
-        if (idx >= lo && idx < hi) return false;
-    }
     return true;
+}
+
+// 0: interior body; 1: CPML and walls only (no periodic image, no per-cell material
+// work in the tile); 2: every path.
+template <typename T>
+__device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
+    if (interior_block(a, tile)) return 0;
+    const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
+    const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
+    const bool img = (a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
+                     (a.per[2] && (k0 == 0 || k1 == a.nz));
+    const bool gen = a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD[0] || a.nsrc);
+    return (img || gen) ? 2 : 1;
+}
+
+template <typename T>
+__device__ __forceinline__ bool yee_dispatch(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
+    const int mode = block_mode(a, tile);
+    if (mode == 0) return yee_body<T, 0>(a, maps, tile);
+    if (mode == 1) return yee_body<T, 1>(a, maps, tile);
+    return yee_body<T, 2>(a, maps, tile);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_kernel(const YeeArgs<T> a,
                                                                            const __grid_constant__ TmapSet maps) {
     const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
-    if (interior_block(a, tile)) yee_body<T, false>(a, maps, tile);
-    else yee_body<T, true>(a, maps, tile);
+    yee_dispatch(a, maps, tile);
 }
 
 // Batched field pass: one persistent launch for the tiles of many grids.  Each block
@@ -593,8 +617,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_batch_ke
             smaps = b.maps + 2 * wk.x + lev;
         }
         __syncthreads();
-        const bool ok = interior_block(sa, wk.y) ? yee_body<T, false>(sa, *smaps, wk.y)
-                                                 : yee_body<T, true>(sa, *smaps, wk.y);
+        const bool ok = yee_dispatch(sa, *smaps, wk.y);
         // a wait that gave up may leave copies in flight: stop reusing this block
         if (!ok) return;
     }

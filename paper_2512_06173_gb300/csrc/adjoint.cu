@@ -902,7 +902,7 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
                 for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = U[q]; }
                 ga.px = g->px; ga.plane = g->plane;
-                ga.off = g->d_joff; ga.ent = g->d_jent; ga.rec = (const T *)g->d_rec; ga.cmask = g->d_cmask;
+                ga.off = g->d_joff; ga.ent = g->d_jent; ga.wf = g->d_wf; ga.w = (const T *)g->d_w; ga.cmask = g->d_cmask;
                 ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
                 CK(launch_gather<T>(ga, s));
                 g->launches++;
@@ -918,7 +918,7 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 CurArgs<T> ca{};
                 ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
                 for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
-                ca.off = g->d_joff; ca.ent = g->d_jent; ca.rec = (const T *)g->d_rec;
+                ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf; ca.w = (const T *)g->d_w;
                 ca.c = cadj; ca.cmask = g->gcmask;
                 for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
                 CK(launch_current<T>(ca, s));

@@ -478,16 +478,9 @@ ml_status rebuild_molecules(ml_grid *g) {
         for (int e = 0; e < (int)jent.size(); e++) mlist[fill[jent[e].x]++] = e;
     }
     CKS(upload_raw(L, &g->d_moff, moff));
+
     if (!mlist.empty()) CKS(upload_raw(L, &g->d_mlist, mlist));
     AL(L, g->d_part, std::max<size_t>(jent.size(), 1) * 3 * g->esz);
-    AL(L, g->d_rec, std::max<size_t>(jent.size(), 1) * REC * g->esz);
-    {
-        cudaError_t e = g->prec ? launch_records<double>((int)jent.size(), g->d_jent, g->d_wf, (const double *)g->d_w,
-                                                         (double *)g->d_rec, 0)
-                                : launch_records<float>((int)jent.size(), g->d_jent, g->d_wf, (const float *)g->d_w,
-                                                        (float *)g->d_rec, 0);
-        if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("records kernel: ") + cudaGetErrorString(e));
-    }
     // field-pass blocks whose tile (with halo) meets the current box
     {
         std::vector<int> A, B;
@@ -696,6 +689,7 @@ void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
     m.moff = g->d_moff; m.mlist = g->d_mlist; m.part = (const T *)g->d_part;
     m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
     m.energy = g->d_energy; m.status = g->d_status;
+    m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
 }
 
 template <typename T>
@@ -704,7 +698,7 @@ void fill_gath_args(ml_grid *g, int cur, GathArgs<T> &ga) {
     ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
     for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = (const T *)g->F[cur][q]; }
     ga.px = g->px; ga.plane = g->plane;
-    ga.off = g->d_joff; ga.ent = g->d_jent; ga.rec = (const T *)g->d_rec; ga.cmask = g->d_cmask;
+    ga.off = g->d_joff; ga.ent = g->d_jent; ga.wf = g->d_wf; ga.w = (const T *)g->d_w; ga.cmask = g->d_cmask;
     ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
 }
 
@@ -713,7 +707,7 @@ void fill_cur_args(ml_grid *g, CurArgs<T> &ca) {
     ca = CurArgs<T>{};
     ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
     for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
-    ca.off = g->d_joff; ca.ent = g->d_jent; ca.rec = (const T *)g->d_rec;
+    ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf; ca.w = (const T *)g->d_w;
     ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
     for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
 }
@@ -784,12 +778,7 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
         }
         if (g->nmol > 0) {
             {
-                GathArgs<T> ga;
-                fill_gath_args<T>(g, cur, ga);
-                LaunchScope ls(g, cs, 5);
-                CK(launch_gather<T>(ga, cs));
-            }
-            {
+                // each molecule's warp gathers its regularised field from E^n itself
                 MolArgs<T> m;
                 fill_mol_args<T>(g, cur, m);
                 LaunchScope ls(g, cs, 0);

@@ -85,7 +85,7 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
     std::vector<YeeArgs<T>> ya(n);
     std::vector<GathArgs<T>> ga(2 * n);
     std::vector<CurArgs<T>> ca(n);
-    std::vector<MolArgs<T>> ma(n);
+    std::vector<MolArgs<T>> ma(2 * n);
     std::vector<FoldDesc<T>> fd;
     b->h_maps.resize(2 * n);
     b->h_lev0.resize(n);
@@ -105,7 +105,8 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
             fill_gath_args<T>(g, 0, ga[2 * i]);
             fill_gath_args<T>(g, 1, ga[2 * i + 1]);
             fill_cur_args<T>(g, ca[i]);
-            fill_mol_args<T>(g, 0, ma[i]);
+            fill_mol_args<T>(g, 0, ma[2 * i]);
+            fill_mol_args<T>(g, 1, ma[2 * i + 1]);
             for (int q = 0; q < g->jnb; q++) b->h_gwork.push_back(make_int2(i, q));
             for (int m0 = 0; m0 < g->nmol; m0 += 4) b->h_mwork.push_back(make_int2(i, m0));
         }
@@ -157,13 +158,11 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
     for (int q = 0; q < count; q++) {
         const int st = s0 + q;
         if (nmw > 0) {
-            GathBatch<T> gb{(const GathArgs<T> *)b->d_gargs, b->d_lev0, b->d_gwork, st};
-            CK(launch_gather_batch<T>(gb, ngw, s));
-            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_mwork};
+            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st};
             CK(launch_molecules_batch<T>(mb, nmw, s));
             CurBatch<T> cb{(const CurArgs<T> *)b->d_cargs, b->d_gwork};
             CK(launch_current_batch<T>(cb, ngw, s));
-            b->launches += 3;
+            b->launches += 2;
         }
         YeeBatch<T> yb{(const YeeArgs<T> *)b->d_yargs, b->d_maps, b->d_lev0, b->d_ywork, nyw, b->d_boff, st,
                        st % DFT_KMAX};
@@ -223,7 +222,7 @@ ml_status batch_step(ml_batch *b, long long nsteps, cudaStream_t s) {
             CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
             b->sig = sig;
         }
-        const long long per = (long long)(b->h_gwork.size() ? 3 : 0) + 1;
+        const long long per = (long long)(b->h_mwork.size() ? 2 : 0) + 1;
         for (long long r = 0; r < reps; r++) {
             CK(cudaGraphLaunch(b->exec, s));
             b->launches += SEQ * per + (b->h_fwork.empty() ? 0 : SEQ / DFT_KMAX) + 1;

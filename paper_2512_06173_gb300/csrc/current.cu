@@ -17,43 +17,32 @@
 namespace ml {
 
 
-// Static records (setup): thread per (entry, slot).
-template <typename T>
-__global__ void records_kernel(int nent, const int4 *ent, const int *wf, const T *w, T *rec) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)nent * REC) return;
-    const int e = (int)(t / REC), q = (int)(t % REC);
-    const int4 en = ent[e];
-    const int f = wf[en.x];
-    int axis, stag, d;
-    if (q < 2 * JX) { axis = 0; stag = q / JX; d = q % JX - en.y; }
-    else if (q < 2 * JX + 2 * JY) { axis = 1; stag = (q - 2 * JX) / JY; d = (q - 2 * JX) % JY - en.z; }
-    else { axis = 2; stag = (q - 2 * JX - 2 * JY) / JZ; d = (q - 2 * JX - 2 * JY) % JZ - en.w; }
-    const int W = (f >> (8 * axis)) & 0xff;
-    rec[(long long)e * REC + q] = ((unsigned)d < (unsigned)W) ? w[(long long)en.x * NW + (2 * axis + stag) * WMAX + d] : T(0);
-}
+// Weight record of entry en (molecule en.x, window start relative to the block
+// origin en.y, en.z, en.w) for component c, slot q of RC = JX + JY + JZ:
+//   [0, JX) Bx(x)   [JX, JX+JY) Ay(y)   [JX+JY, RC) Cz(z),
+// each the molecule's 1D weight at the block's own cell (half-integer position along
+// c, integer elsewhere), 0 outside the window.  Built in shared memory per batch of
+// entries from the per-molecule weight table, which stays in L2.
+constexpr int RC = JX + JY + JZ;
 
 template <typename T>
-cudaError_t launch_records(int nent, const int4 *ent, const int *wf, const T *w, T *rec, cudaStream_t s) {
-    if (nent == 0) return cudaSuccess;
-    const long long n = (long long)nent * REC;
-    records_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nent, ent, wf, w, rec);
-    return cudaGetLastError();
-}
-
-// Record slot offsets of component c (half-integer along c, integer elsewhere).
-__device__ __forceinline__ void rec_slots(int c, int &bx, int &ay, int &cz) {
-    bx = c == 0 ? JX : 0;
-    ay = 2 * JX + (c == 1 ? JY : 0);
-    cz = 2 * JX + 2 * JY + (c == 2 ? JZ : 0);
+__device__ __forceinline__ T rec_value(const int4 en, const int wfm, const T *w, const int c, const int q) {
+    int axis, d;
+    if (q < JX) { axis = 0; d = q - en.y; }
+    else if (q < JX + JY) { axis = 1; d = q - JX - en.z; }
+    else { axis = 2; d = q - JX - JY - en.w; }
+    const int W = (wfm >> (8 * axis)) & 0xff;
+    return ((unsigned)d < (unsigned)W) ? w[(long long)en.x * NW + (2 * axis + (axis == c ? 1 : 0)) * WMAX + d] : T(0);
 }
 
 template <typename T>
 __device__ __forceinline__ void current_body(const CurArgs<T> &a, const int blk) {
     constexpr int JEB = sizeof(T) == 4 ? 32 : 16;  // entries staged per batch
-    __shared__ __align__(16) T sR[JEB][REC];
+    __shared__ __align__(16) T sR[JEB][RC];
     __shared__ __align__(16) T sG[JEB][JY][JZ];
     __shared__ T sC[JEB];
+    __shared__ int4 sEnt[JEB];
+    __shared__ int sWf[JEB];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * JX + tx;
     const int beg = a.off[blk], end = a.off[blk + 1];
     if (beg == end) return;  // no window here: J stays 0 (the box is zeroed at setup)
@@ -61,25 +50,29 @@ __device__ __forceinline__ void current_body(const CurArgs<T> &a, const int blk)
     const int xr = bx * JX + tx, yr = by * JY + ty, zr0 = bz * JZ;
     for (int c = 0; c < 3; c++) {
         if (!((a.cmask >> c) & 1)) continue;
-        int sbx, say, scz;
-        rec_slots(c, sbx, say, scz);
         T acc[JZ];
 #pragma unroll
         for (int q = 0; q < JZ; q++) acc[q] = T(0);
         for (int base = beg; base < end; base += JEB) {
             const int nb = min(JEB, end - base);
             __syncthreads();  // previous batch fully consumed
-            for (int t = tid; t < nb * REC; t += JX * JY) sR[t / REC][t % REC] = a.rec[(long long)base * REC + t];
-            if (tid < nb) sC[tid] = a.c[3ll * a.ent[base + tid].x + c];
+            if (tid < nb) {
+                const int4 en = a.ent[base + tid];
+                sEnt[tid] = en;
+                sWf[tid] = a.wf[en.x];
+                sC[tid] = a.c[3ll * en.x + c];
+            }
+            __syncthreads();
+            for (int t = tid; t < nb * RC; t += JX * JY) sR[t / RC][t % RC] = rec_value(sEnt[t / RC], sWf[t / RC], a.w, c, t % RC);
             __syncthreads();
             // G_e(y, k) = gamma mudot_e^c Ay_e(y) Cz_e(k)
             for (int t = tid; t < nb * JY * JZ; t += JX * JY) {
                 const int e = t / (JY * JZ), r = t % (JY * JZ), yy = r / JZ, zz = r % JZ;
-                sG[e][yy][zz] = sC[e] * sR[e][say + yy] * sR[e][scz + zz];
+                sG[e][yy][zz] = sC[e] * sR[e][JX + yy] * sR[e][JX + JY + zz];
             }
             __syncthreads();
             for (int e = 0; e < nb; e++) {
-                const T b = sR[e][sbx + tx];
+                const T b = sR[e][tx];
 #pragma unroll
                 for (int q = 0; q < JZ; q++) acc[q] += b * sG[e][ty][q];
             }
@@ -106,7 +99,9 @@ template <typename T>
 __device__ __forceinline__ void gather_body(const GathArgs<T> &a, const int blk) {
     constexpr int JEB = sizeof(T) == 4 ? 32 : 16;
     __shared__ __align__(16) T sE[JZ][JY][JX];
-    __shared__ __align__(16) T sR[JEB][REC];
+    __shared__ __align__(16) T sR[JEB][RC];
+    __shared__ int4 sEnt[JEB];
+    __shared__ int sWf[JEB];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * JX + tx;
     const int beg = a.off[blk], end = a.off[blk + 1];
     if (beg == end) return;
@@ -114,8 +109,6 @@ __device__ __forceinline__ void gather_body(const GathArgs<T> &a, const int blk)
     const int xr = bx * JX + tx, yr0 = by * JY, zr0 = bz * JZ;
     for (int c = 0; c < 3; c++) {
         if (!((a.gcmask >> c) & 1)) continue;
-        int sbx, say, scz;
-        rec_slots(c, sbx, say, scz);
         __syncthreads();  // sE of the previous component consumed
         for (int q = ty; q < JY * JZ; q += JY) {
             const int yy = q % JY, zz = q / JY;
@@ -131,10 +124,16 @@ __device__ __forceinline__ void gather_body(const GathArgs<T> &a, const int blk)
         for (int base = beg; base < end; base += JEB) {
             const int nb = min(JEB, end - base);
             __syncthreads();  // previous batch consumed (and sE written)
-            for (int t = tid; t < nb * REC; t += JX * JY) sR[t / REC][t % REC] = a.rec[(long long)base * REC + t];
+            if (tid < nb) {
+                const int4 en = a.ent[base + tid];
+                sEnt[tid] = en;
+                sWf[tid] = a.wf[en.x];
+            }
+            __syncthreads();
+            for (int t = tid; t < nb * RC; t += JX * JY) sR[t / RC][t % RC] = rec_value(sEnt[t / RC], sWf[t / RC], a.w, c, t % RC);
             __syncthreads();
             for (int e = ty; e < nb; e += JY) {
-                const int m = a.ent[base + e].x;
+                const int m = sEnt[e].x;
                 T v = T(0);
                 if ((a.cmask[m] >> c) & 1) {
                     T t = T(0);
@@ -142,10 +141,10 @@ __device__ __forceinline__ void gather_body(const GathArgs<T> &a, const int blk)
                     for (int zz = 0; zz < JZ; zz++) {
                         T u = T(0);
 #pragma unroll
-                        for (int yy = 0; yy < JY; yy++) u += sR[e][say + yy] * sE[zz][yy][tx];
-                        t += sR[e][scz + zz] * u;
+                        for (int yy = 0; yy < JY; yy++) u += sR[e][JX + yy] * sE[zz][yy][tx];
+                        t += sR[e][JX + JY + zz] * u;
                     }
-                    v = sR[e][sbx + tx] * t;
+                    v = sR[e][tx] * t;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -208,7 +207,7 @@ cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s) {
     template cudaError_t launch_gather<T>(const GathArgs<T> &, cudaStream_t);                      \
     template cudaError_t launch_gather_batch<T>(const GathBatch<T> &, int, cudaStream_t);          \
     template cudaError_t launch_current_batch<T>(const CurBatch<T> &, int, cudaStream_t);          \
-    template cudaError_t launch_records<T>(int, const int4 *, const int *, const T *, T *, cudaStream_t);
+
 ML_INST(float)
 ML_INST(double)
 

@@ -89,7 +89,6 @@ struct ml_grid {
     bool overlap = false;  // tuning (ML_OVERLAP=1): run the molecule chain beside the clear field blocks
     cudaEvent_t ev_join = nullptr, ev_box = nullptr;
     void *d_part = nullptr;                     // gather partials (entries, 3)
-    void *d_rec = nullptr;                      // static weight records (entries, REC)
     void *d_J[3] = {};
     ml::TmapSet tm[2];
     std::vector<ml::Plane> planes;

@@ -120,11 +120,6 @@ template <typename T> constexpr size_t yee_smem_bytes() {
 
 // ------------------------------------------------------------------ current
 constexpr int JX = 32, JY = 8, JZ = 8;  // cells per block of the current kernel
-// Static record of one (block, molecule window) entry: the molecule's 1D kernel
-// weights at the block's own cells, zero outside the window:
-//   [0,32) Bx integer-x  [32,64) Bx half-x  [64,72) Ay integer-y  [72,80) Ay half-y
-//   [80,88) Cz integer-z  [88,96) Cz half-z
-constexpr int REC = 2 * JX + 2 * JY + 2 * JZ;
 
 template <typename T>
 struct CurArgs {
@@ -132,7 +127,8 @@ struct CurArgs {
     int bn[3];           // box extent in cells
     const int *off;      // CSR: entries of block b are ent[off[b] .. off[b+1])
     const int4 *ent;     // (molecule, window start - block origin along x, y, z)
-    const T *rec;        // (entries, REC) static weight records
+    const int *wf;       // per molecule: window length along x, y, z (8 bits each)
+    const T *w;          // (M, NW) 1D kernel weights per axis and stagger
     const T *c;          // (M, 3) gamma * mudot of this step
     int cmask;           // components with a dipole
     T *J[3];             // box arrays (nz, ny, nx of the box)
@@ -150,7 +146,8 @@ struct GathArgs {
     long long plane;
     const int *off;
     const int4 *ent;
-    const T *rec;        // (entries, REC) static weight records
+    const int *wf;       // per molecule: window length along x, y, z (8 bits each)
+    const T *w;          // (M, NW) 1D kernel weights per axis and stagger
     const int *cmask;    // per molecule
     int gcmask;          // components staged
     const T *E[3];       // E^n (padded)
@@ -186,6 +183,9 @@ struct MolArgs {
     T *c;
     double *energy;
     int *status;
+    const int *win;        // per molecule: canonical window start along x, y, z
+    const int *wf;         // per molecule: window length along x, y, z (8 bits each)
+    const T *w;            // (M, NW) 1D kernel weights per axis and stagger
 };
 
 // ------------------------------------------------------------------ DFT planes
@@ -231,8 +231,10 @@ struct CurBatch {
 };
 template <typename T>
 struct MolBatch {
-    const MolArgs<T> *args;
+    const MolArgs<T> *args;   // per instance, two: E of level 0 and of level 1
+    const int *lev0;
     const int2 *work;         // (instance, first molecule of the block)
+    int s;
 };
 template <typename T>
 struct FoldDesc {
@@ -263,8 +265,6 @@ template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet 
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);
-template <typename T> cudaError_t launch_records(int nent, const int4 *ent, const int *wf, const T *w, T *rec,
-                                                 cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,
                                                  const int *win, const int *wf, const int *wraw,
                                                  const int *dims, const int *per, T *w, cudaStream_t s);

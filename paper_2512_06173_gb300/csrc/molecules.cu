@@ -42,7 +42,68 @@ template <typename T>
 struct MolShared {
     cx<T> H[MOL_WARPS][MAXLEV * MAXLEV];
     cx<T> S[MOL_WARPS][2][MAXLEV * MAXLEV];
+    T W[MOL_WARPS][NW];  // the molecule's 1D kernel weights (window form)
 };
+
+// Regularised-field sums of molecule m straight from the field (Eq. E_regu_Emi without
+// gamma): g_c = sum_window wx wy wz E^c over the canonical window (start win, folded
+// length wf; periodic axes wrap), component c sampled half a cell along c.  Lane
+// (dx = lane & 15, row parity = lane >> 4) sums its x column over the rows of its
+// parity and the planes in fixed order; the xor tree then adds the lanes.
+template <typename T>
+__device__ __forceinline__ void window_gather(const MolArgs<T> &a, const int m, const int cm, const T *sw, T (&g)[3]) {
+    const int lane = threadIdx.x & 31, dx = lane & 15, py = lane >> 4;
+    const int wfm = a.wf[m];
+    const int Wx = wfm & 0xff, Wy = (wfm >> 8) & 0xff, Wz = (wfm >> 16) & 0xff;
+    const int x0 = a.win[3 * m], y0 = a.win[3 * m + 1], z0 = a.win[3 * m + 2];
+    int x = x0 + dx;
+    if (x >= a.nx) x -= a.nx;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        T t = T(0);
+        if (((cm >> c) & 1) && dx < Wx) {
+            const T *E = a.E[c] + x + XO;
+            const T *wy = sw + (2 + (c == 1 ? 1 : 0)) * WMAX, *wz = sw + (4 + (c == 2 ? 1 : 0)) * WMAX;
+            // row offsets of this lane's rows (fixed bound, predicated: all loads of a
+            // plane are in flight together)
+            long long roff[WMAX / 2];
+            T wyv[WMAX / 2];
+#pragma unroll
+            for (int q = 0; q < WMAX / 2; q++) {
+                const int dy = py + 2 * q;
+                int y = y0 + dy;
+                if (y >= a.ny) y -= a.ny;
+                roff[q] = (long long)(y + 1) * a.px;
+                wyv[q] = dy < Wy ? wy[dy] : T(0);
+            }
+            for (int dz = 0; dz < Wz; dz += 2) {
+                T u0 = T(0), u1 = T(0);
+                int z = z0 + dz;
+                if (z >= a.nz) z -= a.nz;
+                int z1 = z + 1;
+                if (z1 >= a.nz) z1 -= a.nz;
+                const bool two = dz + 1 < Wz;
+                const T *Ez = E + (long long)(z + 1) * a.plane, *Ez1 = E + (long long)(z1 + 1) * a.plane;
+                T v0[WMAX / 2], v1[WMAX / 2];
+#pragma unroll
+                for (int q = 0; q < WMAX / 2; q++) {
+                    const bool in = py + 2 * q < Wy;
+                    v0[q] = in ? Ez[roff[q]] : T(0);
+                    v1[q] = (in && two) ? Ez1[roff[q]] : T(0);
+                }
+#pragma unroll
+                for (int q = 0; q < WMAX / 2; q++) {
+                    u0 += wyv[q] * v0[q];
+                    u1 += wyv[q] * v1[q];
+                }
+                t += wz[dz] * u0;
+                if (two) t += wz[dz + 1] * u1;
+            }
+            t *= sw[(c == 0 ? 1 : 0) * WMAX + dx];
+        }
+        g[c] = warp_sum(t);
+    }
+}
 
 // GKSL right-hand side for element (j,l) of rho given in S (n x n), H in Hs.
 template <typename T>
@@ -70,7 +131,9 @@ __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, c
     return out;
 }
 
-template <typename T>
+// FUSED: the warp gathers its own regularised field from E (window_gather);
+// otherwise it adds the gather kernel's partials.
+template <typename T, bool FUSED>
 __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0) {
     __shared__ MolShared<T> sh;
     const int lane = threadIdx.x & 31;
@@ -98,18 +161,29 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     }
     __syncwarp();
 
-    // ---- 1. regularised field: this molecule's gather partials, added lane-strided
-    // in list order and combined by a fixed xor tree
-    T g[3] = {T(0), T(0), T(0)};
-    for (int t = a.moff[m] + lane; t < a.moff[m + 1]; t += 32) {
-        const T *pp = a.part + 3ll * a.mlist[t];
-        g[0] += pp[0];
-        g[1] += pp[1];
-        g[2] += pp[2];
-    }
+    // ---- 1. regularised field
     T Et[3];
+    if (FUSED) {
+        T *sw = sh.W[wl];
+        for (int q = lane; q < NW; q += 32) sw[q] = a.w[(long long)m * NW + q];
+        __syncwarp();
+        T g[3];
+        window_gather(a, m, cm, sw, g);
 #pragma unroll
-    for (int c = 0; c < 3; c++) Et[c] = gam * warp_sum(g[c]);
+        for (int c = 0; c < 3; c++) Et[c] = gam * g[c];
+    } else {
+        // this molecule's gather partials, added lane-strided in list order and
+        // combined by a fixed xor tree
+        T g[3] = {T(0), T(0), T(0)};
+        for (int t = a.moff[m] + lane; t < a.moff[m + 1]; t += 32) {
+            const T *pp = a.part + 3ll * a.mlist[t];
+            g[0] += pp[0];
+            g[1] += pp[1];
+            g[2] += pp[2];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) Et[c] = gam * warp_sum(g[c]);
+    }
 
     // ---- 2. H = H0 - Etilde . mu and <mu> before the step.  For Hermitian
     // operators Re Tr(rho A) = sum_jl Re(rho_jl conj(A_jl)): own elements only.
@@ -242,14 +316,14 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 
 template <typename T>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<T> a) {
-    molecule_body(a, (int)blockIdx.x * MOL_WARPS);
+    molecule_body<T, true>(a, (int)blockIdx.x * MOL_WARPS);
 }
 
 // Batched form: one block per (instance, first molecule) work item.
 template <typename T>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
     const int2 wk = b.work[blockIdx.x];
-    molecule_body(b.args[wk.x], wk.y);
+    molecule_body<T, true>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
 }
 
 template <typename T>

@@ -252,6 +252,45 @@ def measure_adjoint(args, stream):
         g.close()
 
 
+def measure_bragg(args, stream):
+    """Bragg-resonator ensemble: 512x512x384 cells, 12-layer stack, 100,000 multilevel
+    Lindblad systems (2-8 levels, RK4), z-polarised pulse, FP32 fields; device time of
+    args.bragg_steps steps after a warm-up, per-kernel split from the tracing events."""
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    prob = workloads.bragg_ensemble()
+    sh = stream.cuda_stream
+    g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    K = args.bragg_steps
+    try:
+        g.step(5)
+        g.sync()
+        maxlink.ml_set_timing(g.h, True)
+        maxlink.ml_timing(g.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(K)
+        e1.record(stream)
+        stream.synchronize()
+        g.sync()
+        ms = e0.elapsed_time(e1)
+        kms, _ = maxlink.ml_timing(g.h)
+        maxlink.ml_set_timing(g.h, False)
+        hbm, peak_kind = peaks()
+        fp = kms[1] / K
+        alg = field_pass_bytes(prob, 4)
+        return {"workload": prob.name, "cells": prob.cells, "molecules": prob.molecules.count, "steps": K,
+                "dtype": "f32", "gcells_per_s": prob.cells * K / ms / 1e6,
+                "molecule_steps_per_s": prob.molecules.count * K / ms * 1e3, "ms_per_step": ms / K,
+                "field_pass": {"ms_per_step": fp, "alg_bytes": alg, "achieved_gbs": alg / (fp / 1e3) / 1e9,
+                               "frac": alg / (fp / 1e3) / 1e9 / hbm, "peak": hbm, "peak_kind": peak_kind},
+                "kernel_ms_per_step": {"molecules": kms[0] / K, "current": kms[4] / K, "field_pass": fp,
+                                       "plane_fold": kms[3] / K}}
+    finally:
+        g.close()
+
+
 def measure_batch(args, stream):
     """64 plasmonic realisations of uneven size (edges 64..160, 200-5000 emitters each):
     K steps as one batch (one launch per kernel class per step, graph-replayed, field-pass
@@ -391,6 +430,7 @@ def run_ours(args, world, rank, local):
     g2.close()
     adjoint = measure_adjoint(args, stream) if (world == 1 and not args.no_adjoint) else None
     batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
+    bragg = measure_bragg(args, stream) if (world == 1 and not args.no_bragg) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,6 +457,7 @@ def run_ours(args, world, rank, local):
             "molecule_steps_per_s": mol_steps,
             "adjoint": adjoint,
             "batch": batch,
+            "bragg": bragg,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
                                    "field_pass": kms[1] / K, "plane_fold": kms[3] / K},
             "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
@@ -442,6 +483,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
     ap.add_argument("--batch-steps", type=int, default=3000)
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--no-bragg", action="store_true", help="skip the Bragg-resonator ensemble")
+    ap.add_argument("--bragg-steps", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

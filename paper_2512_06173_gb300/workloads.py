@@ -235,31 +235,33 @@ def random_hermitian(rng, n, std):
 
 
 def bragg_ensemble(nx=512, ny=512, nz=384, nmol=100000, pml=10, slab=32, seed=3,
-                   layers=12, nfreq=8) -> Problem:
-    """Bragg-mirror stack along z (alternating eps 2.25 / 1.0 quarter-wave layers at
-    omega = 0.25, 4 and 6 cells) split around a central slab holding `nmol` multilevel
-    systems with level count uniform in 2..8, Hermitian z-dipoles with N(0, 0.01)
-    entries, harmonic ladders with spacing 0.2 +- 5 % and log-uniform decay rates in
-    [1e-6, 1e-4]; z-polarised Gaussian pulse sheet source.  Stand-in for the Bragg
-    resonator of Sec. IV.C."""
+                   layers=12, nfreq=8, width=20.0) -> Problem:
+    """Bragg-mirror stack (alternating eps 2.25 / 1.0 quarter-wave layers at omega =
+    0.25, 4 and 6 cells) along x, split around a central `slab`-cell slab holding
+    `nmol` multilevel systems with level count uniform in 2..8, Hermitian z-dipoles
+    with N(0, 0.01) entries, harmonic ladders with spacing 0.2 +- 5 % and log-uniform
+    decay rates in [1e-6, 1e-4]; a z-polarised Gaussian-pulse current sheet on the
+    plane x = pml + 2 and flux planes on both sides.  The pulse travels along x, so the
+    z-polarised field and the z-dipoles couple.  Stand-in for the Bragg resonator of
+    Sec. IV.C."""
     rng = np.random.Generator(np.random.PCG64(seed))
     mat = np.zeros((nz, ny, nx), np.uint8)
-    zc = nz // 2
+    xc = nx // 2
     half = layers // 2
-    # stack above and below the slab: (4 cells eps 2.25, 6 cells eps 1) x half
-    z = zc + slab // 2
+    # stack on both sides of the slab: (4 cells eps 2.25, 6 cells eps 1) x half
+    x = xc + slab // 2
     for _ in range(half):
-        mat[z:z + 4] = 1
-        z += 10
-    z = zc - slab // 2
+        mat[:, :, x:x + 4] = 1
+        x += 10
+    x = xc - slab // 2
     for _ in range(half):
-        mat[z - 4:z] = 1
-        z -= 10
+        mat[:, :, x - 4:x] = 1
+        x -= 10
     mats = []
     nl = rng.integers(2, 9, size=nmol)
-    px = rng.uniform(pml + 2, nx - pml - 2, size=nmol)
-    py = rng.uniform(pml + 2, ny - pml - 2, size=nmol)
-    pz = rng.uniform(zc - slab // 2, zc + slab // 2, size=nmol)
+    px = rng.uniform(xc - slab // 2, xc + slab // 2, size=nmol)
+    py = rng.uniform(pml + 7, ny - pml - 7, size=nmol)
+    pz = rng.uniform(pml + 7, nz - pml - 7, size=nmol)
     rates = np.exp(rng.uniform(np.log(1e-6), np.log(1e-4), size=nmol))
     for m in range(nmol):
         n = int(nl[m])
@@ -272,9 +274,9 @@ def bragg_ensemble(nx=512, ny=512, nz=384, nmol=100000, pml=10, slab=32, seed=3,
         mats.append(dict(n=n, pos=(px[m], py[m], pz[m]), sigma=1.5, gamma=1.0,
                          H0=np.diag(E).astype(np.complex128), mu=mu, rho=rho,
                          decay=float(rates[m]), kind=KIND_RK4, nsub=1))
-    src = [Source(axis=2, index=pml + 2, comp=0, amp=1.0, omega=0.25, width=20.0, t0=100.0)]
+    src = [Source(axis=0, index=pml + 2, comp=2, amp=1.0, omega=0.25, width=width, t0=5.0 * width)]
     om = np.linspace(0.20, 0.30, nfreq)
-    planes = [FluxPlane(2, pml + 6, om.copy()), FluxPlane(2, nz - pml - 4, om.copy())]
+    planes = [FluxPlane(0, pml + 6, om.copy()), FluxPlane(0, nx - pml - 4, om.copy())]
     return Problem(nx, ny, nz, 0.5, periodic=(False, False, False), pml=(pml,) * 6, mat=mat,
                    materials=[Material(1.0), Material(2.25)], sources=src,
                    molecules=pack_molecules(mats), planes=planes,

@@ -107,6 +107,30 @@ def test_coupled_all_features(ml, oracle_mod, precision, tol, seed):
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_bragg_resonator_copy(ml, oracle_mod, precision, tol):
+    """Small copy of the Bragg-resonator ensemble: layer stack along x, multilevel
+    Lindblad systems (2..8 levels) in the central slab, z-polarised pulse sheet, flux
+    planes on both sides; 120 steps so that the pulse reaches the slab."""
+    prob = W.bragg_ensemble(nx=96, ny=40, nz=36, nmol=30, pml=4, slab=8, layers=4, width=6.0)
+    g, o = run_pair(ml, oracle_mod, prob, 120, precision)
+    # the field is z-polarised: components that stay near zero are measured against
+    # the largest component's norm
+    fo = o.fields()
+    scale = max(np.linalg.norm(f) for f in fo)
+    for got, want in zip(g.fields(), fo):
+        assert np.linalg.norm(np.asarray(got, np.float64) - want) < tol * scale
+    pops = g.molecules(ml.ML_MOL_POP)
+    for m in range(prob.molecules.count):
+        n = int(prob.molecules.nlev[m])
+        assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+    # the far plane has not seen the pulse yet: errors against the larger flux
+    fl = [(g.flux(p), o.flux(p)) for p in range(len(prob.planes))]
+    fscale = max(np.abs(fo).max() for _, fo in fl)
+    for fg, fo in fl:
+        assert np.abs(fg - fo).max() < (1e-9 if precision == 1 else 1e-3) * fscale
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
 def test_drude_sphere(ml, oracle_mod, precision, tol):
     prob = W.small_coupled(seed=4, shape=(30, 30, 30), drude=True, eps_map=False, nmol=4, planes=False)
     g, o = run_pair(ml, oracle_mod, prob, 80, precision)

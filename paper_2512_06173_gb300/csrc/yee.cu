@@ -218,28 +218,38 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         if (ok && !mbar_wait_bounded(&bars[s], par, WAIT_LIMIT)) ok = false;
     };
     auto zslab = [&](int kc) { return zl ? slab(kc, a.nz, a.pml[4], a.pml[5]) : -1; };
-    // H-side CPML memory of a cell at canonical (xc, yc, kc) with slab coordinates
-    // sx, sy, sz: old values (p = {x0, x1, y0, y1, z0, z1}) loaded ahead of use
-    auto h_pml_load = [&](T (&p)[6], int xc, int yc, int kc, int sx, int sy, int sz) {
-        if (sx >= 0) { const long long q = ((long long)kc * a.ny + yc) * dxt + sx; p[0] = a.psiHo[0][0][q]; p[1] = a.psiHo[0][1][q]; }
-        if (sy >= 0) { const long long q = ((long long)kc * dyt + sy) * a.nx + xc; p[2] = a.psiHo[1][0][q]; p[3] = a.psiHo[1][1][q]; }
-        if (sz >= 0) { const long long q = ((long long)sz * a.ny + yc) * a.nx + xc; p[4] = a.psiHo[2][0][q]; p[5] = a.psiHo[2][1][q]; }
+    // Offsets of a cell at canonical (xc, yc, kc) in the three slab stores (-1 outside
+    // a layer); the stores hold fewer than 2^31 elements, so 32-bit offsets suffice,
+    // computed once per cell and plane for every load and store of the plane.
+    struct SlabOff { int x, y, z; };
+    auto slab_off = [&](int xc, int yc, int kc, int sx, int sy, int sz) {
+        SlabOff q;
+        q.x = sx >= 0 ? (kc * a.ny + yc) * dxt + sx : -1;
+        q.y = sy >= 0 ? (kc * dyt + sy) * a.nx + xc : -1;
+        q.z = sz >= 0 ? (sz * a.ny + yc) * a.nx + xc : -1;
+        return q;
     };
-    // apply the recursion (coefficient column cx of sCx, row ry of sCy) and, for an
-    // own cell, store the new memory in the other time level
-    auto h_pml = [&](T (&d)[6], T (&p)[6], int xc, int yc, int kc, int sx, int sy, int sz, int cx, int ry, bool own) {
-        if (sx >= 0) {
+    // H-side CPML memory (p = {x0, x1, y0, y1, z0, z1}), old level, loaded ahead of use
+    auto h_pml_load = [&](T (&p)[6], const SlabOff &q) {
+        if (q.x >= 0) { p[0] = a.psiHo[0][0][q.x]; p[1] = a.psiHo[0][1][q.x]; }
+        if (q.y >= 0) { p[2] = a.psiHo[1][0][q.y]; p[3] = a.psiHo[1][1][q.y]; }
+        if (q.z >= 0) { p[4] = a.psiHo[2][0][q.z]; p[5] = a.psiHo[2][1][q.z]; }
+    };
+    // apply the recursion (coefficient column cx of sCx, row ry of sCy, plane kc) and,
+    // for an own cell, store the new memory in the other time level
+    auto h_pml = [&](T (&d)[6], T (&p)[6], const SlabOff &q, int kc, int cx, int ry, bool own) {
+        if (q.x >= 0) {
             cpml_pair(sCx[3][cx], sCx[4][cx], sCx[5][cx], d[3], d[4], p[0], p[1]);
-            if (own) { const long long q = ((long long)kc * a.ny + yc) * dxt + sx; a.psiHn[0][0][q] = p[0]; a.psiHn[0][1][q] = p[1]; }
+            if (own) { a.psiHn[0][0][q.x] = p[0]; a.psiHn[0][1][q.x] = p[1]; }
         }
-        if (sy >= 0) {
+        if (q.y >= 0) {
             cpml_pair(sCy[3][ry], sCy[4][ry], sCy[5][ry], d[0], d[5], p[2], p[3]);
-            if (own) { const long long q = ((long long)kc * dyt + sy) * a.nx + xc; a.psiHn[1][0][q] = p[2]; a.psiHn[1][1][q] = p[3]; }
+            if (own) { a.psiHn[1][0][q.y] = p[2]; a.psiHn[1][1][q.y] = p[3]; }
         }
-        if (sz >= 0) {
+        if (q.z >= 0) {
             const T *cf = a.cpml[2];
             cpml_pair(cf[3 * a.nz + kc], cf[4 * a.nz + kc], cf[5 * a.nz + kc], d[1], d[2], p[4], p[5]);
-            if (own) { const long long q = ((long long)sz * a.ny + yc) * a.nx + xc; a.psiHn[2][0][q] = p[4]; a.psiHn[2][1][q] = p[5]; }
+            if (own) { a.psiHn[2][0][q.z] = p[4]; a.psiHn[2][1][q.z] = p[5]; }
         }
     };
 
@@ -258,9 +268,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             e_diffs<T, BP>(Ek, Ek1, o, d);
             if (sxo >= 0 || syo[r] >= 0 || sz >= 0) {
                 const int jc_ = canon(jb + r, a.ny, a.per[1]);
+                const SlabOff q = slab_off(ic, jc_, kc, sxo, syo[r], sz);
                 T p[6];
-                h_pml_load(p, ic, jc_, kc, sxo, syo[r], sz);
-                h_pml(d, p, ic, jc_, kc, sxo, syo[r], sz, col, ty * RY + r + 1, false);
+                h_pml_load(p, q);
+                h_pml(d, p, q, kc, col, ty * RY + r + 1, false);
             }
             T hz = Ek[5 * BP + o];
             hpx[r] = Ek[3 * BP + o];
@@ -285,19 +296,24 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             // latency overlaps the wait and the H phase (own H side, own E side, halo H side)
             T ph[RY][6], pe[RY][6], phh[6];
             bool pown[RY];
+            SlabOff qo[RY], qh;
 #pragma unroll
             for (int r = 0; r < RY; r++) {
                 const int j = jb + r;
                 pown[r] = xin && j < a.ny && (sxo >= 0 || syo[r] >= 0 || sz >= 0);
                 if (pown[r]) {
-                    h_pml_load(ph[r], i, j, k, sxo, syo[r], sz);
-                    if (sxo >= 0) { const long long q = ((long long)k * a.ny + j) * dxt + sxo; pe[r][0] = a.psiE[0][0][q]; pe[r][1] = a.psiE[0][1][q]; }
-                    if (syo[r] >= 0) { const long long q = ((long long)k * dyt + syo[r]) * a.nx + i; pe[r][2] = a.psiE[1][0][q]; pe[r][3] = a.psiE[1][1][q]; }
-                    if (sz >= 0) { const long long q = ((long long)sz * a.ny + j) * a.nx + i; pe[r][4] = a.psiE[2][0][q]; pe[r][5] = a.psiE[2][1][q]; }
+                    qo[r] = slab_off(i, j, k, sxo, syo[r], sz);
+                    h_pml_load(ph[r], qo[r]);
+                    if (qo[r].x >= 0) { pe[r][0] = a.psiE[0][0][qo[r].x]; pe[r][1] = a.psiE[0][1][qo[r].x]; }
+                    if (qo[r].y >= 0) { pe[r][2] = a.psiE[1][0][qo[r].y]; pe[r][3] = a.psiE[1][1][qo[r].y]; }
+                    if (qo[r].z >= 0) { pe[r][4] = a.psiE[2][0][qo[r].z]; pe[r][5] = a.psiE[2][1][qo[r].z]; }
                 }
             }
             const bool phalo = halo && (sxh >= 0 || syh >= 0 || sz >= 0);
-            if (phalo) h_pml_load(phh, hic, hjc, k, sxh, syh, sz);
+            if (phalo) {
+                qh = slab_off(hic, hjc, k, sxh, syh, sz);
+                h_pml_load(phh, qh);
+            }
             wait_stage(sn, pn);
             const T *Ek = stages + sc * SW, *Ek1 = stages + sn * SW, *Hk = Ek + 3 * BP;
             const long long pb = (long long)(k + 1) * a.plane;
@@ -332,7 +348,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 hz[r] = Hk[2 * BP + o];
                 T d[6];
                 e_diffs<T, BP>(Ek, Ek1, o, d);
-                if (pown[r]) h_pml(d, ph[r], i, j, k, sxo, syo[r], sz, col, ty * RY + r + 1, true);
+                if (pown[r]) h_pml(d, ph[r], qo[r], k, col, ty * RY + r + 1, true);
                 h_finish(a.dt, d, hx[r], hy[r], hz[r]);
                 const int sr = ty * RY + r + 1;
                 sH[0][sr][tx + 1] = hx[r];
@@ -356,7 +372,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 T qx = Hk[oh], qy = Hk[BP + oh], qz = Hk[2 * BP + oh];
                 T d[6];
                 e_diffs<T, BP>(Ek, Ek1, oh, d);
-                if (phalo) h_pml(d, phh, hic, hjc, k, sxh, syh, sz, hxs + 3, hys, false);
+                if (phalo) h_pml(d, phh, qh, k, hxs + 3, hys, false);
                 h_finish(a.dt, d, qx, qy, qz);
                 sH[0][hys][hxs] = qx;
                 sH[1][hys][hxs] = qy;
@@ -377,24 +393,22 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 T dHy_dx = hy[r] - sH[1][sr][tx];
                 T dHx_dy = hx[r] - sH[0][sr - 1][tx + 1];
                 if (pown[r]) {
-                    if (sxo >= 0) {
-                        const long long q = ((long long)k * a.ny + j) * dxt + sxo;
+                    const SlabOff &q = qo[r];
+                    if (q.x >= 0) {
                         cpml_pair(sCx[0][col], sCx[1][col], sCx[2][col], dHz_dx, dHy_dx, pe[r][0], pe[r][1]);
-                        a.psiE[0][0][q] = pe[r][0];
-                        a.psiE[0][1][q] = pe[r][1];
+                        a.psiE[0][0][q.x] = pe[r][0];
+                        a.psiE[0][1][q.x] = pe[r][1];
                     }
-                    if (syo[r] >= 0) {
-                        const long long q = ((long long)k * dyt + syo[r]) * a.nx + i;
+                    if (q.y >= 0) {
                         cpml_pair(sCy[0][sr], sCy[1][sr], sCy[2][sr], dHz_dy, dHx_dy, pe[r][2], pe[r][3]);
-                        a.psiE[1][0][q] = pe[r][2];
-                        a.psiE[1][1][q] = pe[r][3];
+                        a.psiE[1][0][q.y] = pe[r][2];
+                        a.psiE[1][1][q.y] = pe[r][3];
                     }
-                    if (sz >= 0) {
-                        const long long q = ((long long)sz * a.ny + j) * a.nx + i;
+                    if (q.z >= 0) {
                         const T *cf = a.cpml[2];
                         cpml_pair(cf[k], cf[a.nz + k], cf[2 * a.nz + k], dHy_dz, dHx_dz, pe[r][4], pe[r][5]);
-                        a.psiE[2][0][q] = pe[r][4];
-                        a.psiE[2][1][q] = pe[r][5];
+                        a.psiE[2][0][q.z] = pe[r][4];
+                        a.psiE[2][1][q.z] = pe[r][5];
                     }
                 }
                 const T curl0 = dHz_dy - dHy_dz;

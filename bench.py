@@ -350,6 +350,13 @@ def run_ours(args, world, rank, local):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU for the CUDA path")
     torch.cuda.set_device(local)
+    if args.section != "main":
+        # one secondary measurement alone (profiling runs): its JSON object, rank 0
+        fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg}[args.section]
+        out = fn(args, torch.cuda.Stream())
+        if rank == 0:
+            print(json.dumps({"section": args.section, **out}), flush=True)
+        return
     prob = workloads.superradiant_slab(n=args.edge, nmol=args.nmol, seed=2 + rank)
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
@@ -479,6 +486,8 @@ def main():
     ap.add_argument("--edge", type=int, default=256, help="grid edge (profiling runs use a smaller cube)")
     ap.add_argument("--nmol", type=int, default=10000)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg"],
+                    help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
     ap.add_argument("--batch-steps", type=int, default=3000)

@@ -291,6 +291,40 @@ def measure_bragg(args, stream):
         g.close()
 
 
+def measure_features(args, stream):
+    """Field-pass time per step on the 256^3 bench grid with features removed one at a
+    time (tracing events, 200 steps after 20 warm-up steps): where the pass loses time."""
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    sh = stream.cuda_stream
+    base = workloads.superradiant_slab()
+    vac = workloads.Problem(256, 256, 256, 0.5)
+    none = workloads.empty_molecules()
+    cases = [("bench: CPML 10, current box, 2 planes", base),
+             ("CPML only", base.replace(molecules=none, planes=[])),
+             ("PEC walls only", base.replace(pml=(0,) * 6, molecules=none, planes=[])),
+             ("CPML on x faces only", vac.replace(pml=(10, 10, 0, 0, 0, 0))),
+             ("CPML on y faces only", vac.replace(pml=(0, 0, 10, 10, 0, 0))),
+             ("CPML on z faces only", vac.replace(pml=(0, 0, 0, 0, 10, 10)))]
+    out = []
+    for label, prob in cases:
+        g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+        try:
+            g.step(20)
+            g.sync()
+            maxlink.ml_set_timing(g.h, True)
+            maxlink.ml_timing(g.h)
+            g.step(200)
+            g.sync()
+            ms, _ = maxlink.ml_timing(g.h)
+            maxlink.ml_set_timing(g.h, False)
+            us = ms[1] / 200 * 1e3
+            out.append({"case": label, "field_pass_us": us, "tbs_at_48B_per_cell": prob.cells * 48 / us / 1e6})
+        finally:
+            g.close()
+    return {"cases": out}
+
+
 def measure_batch(args, stream):
     """64 plasmonic realisations of uneven size (edges 64..160, 200-5000 emitters each):
     K steps as one batch (one launch per kernel class per step, graph-replayed, field-pass
@@ -352,7 +386,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
-        fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg}[args.section]
+        fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
+              "features": measure_features}[args.section]
         out = fn(args, torch.cuda.Stream())
         if rank == 0:
             print(json.dumps({"section": args.section, **out}), flush=True)
@@ -486,7 +521,7 @@ def main():
     ap.add_argument("--edge", type=int, default=256, help="grid edge (profiling runs use a smaller cube)")
     ap.add_argument("--nmol", type=int, default=10000)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
-    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg"],
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "features"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")

@@ -498,6 +498,7 @@ ml_status rebuild_molecules(ml_grid *g) {
         if (!B.empty()) CKS(upload_raw(L, &g->d_blB, B));
     }
     if (const char *ev = std::getenv("ML_OVERLAP")) g->overlap = std::atoi(ev) != 0;
+    if (const char *ev = std::getenv("ML_PDL")) g->pdl = std::atoi(ev) != 0;
     if (!g->side) {
         // highest priority: the chain's short kernels take SMs as field-pass blocks retire
         int lowest = 0, highest = 0;
@@ -788,9 +789,9 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
                 CurArgs<T> ca;
                 fill_cur_args<T>(g, ca);
                 LaunchScope ls(g, cs, 4);
-                CK(launch_current<T>(ca, cs));
+                CK(launch_current<T>(ca, cs, !chain && g->pdl));
             }
-            CK(cudaEventRecord(g->ev_join, cs));
+            if (chain) CK(cudaEventRecord(g->ev_join, cs));
         }
         YeeArgs<T> y;
         fill_yee_args<T>(g, cur, y);
@@ -812,7 +813,7 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             }
         } else {
             LaunchScope ls(g, s, 1);
-            CK(launch_yee<T>(y, g->tm[cur], g->nblocks, s));
+            CK(launch_yee<T>(y, g->tm[cur], g->nblocks, s, g->nmol > 0 && g->pdl));
         }
         if (!g->planes.empty()) {
             g->nsamp++;

@@ -13,6 +13,7 @@
 // of the block's list: deterministic, no atomics.  Only components along which
 // some molecule has a dipole are computed (cmask).
 #include "ml_internal.cuh"
+#include "tma.cuh"
 
 namespace ml {
 
@@ -157,8 +158,15 @@ __device__ __forceinline__ void gather_body(const GathArgs<T> &a, const int blk)
 template <typename T>
 __global__ void __launch_bounds__(JX *JY) gather_kernel(const GathArgs<T> a) { gather_body(a, (int)blockIdx.x); }
 
+// The field pass may be launched as this kernel's programmatic dependent: release it at
+// once (only its current-box tiles wait for this kernel's completion).  When this kernel
+// is itself launched that way, wait for the molecule kernel before reading its output.
 template <typename T>
-__global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) { current_body(a, (int)blockIdx.x); }
+__global__ void __launch_bounds__(JX *JY) current_kernel(const CurArgs<T> a) {
+    pdl_trigger();
+    pdl_wait();
+    current_body(a, (int)blockIdx.x);
+}
 
 // Batched forms: one block per (instance, box block) work item; the gather reads the
 // time level of this step.
@@ -196,14 +204,22 @@ cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s) {
+cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl) {
     if (a.nblocks == 0) return cudaSuccess;
-    current_kernel<T><<<a.nblocks, dim3(JX, JY), 0, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.nblocks);
+    cfg.blockDim = dim3(JX, JY);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, current_kernel<T>, a);
 }
 
 #define ML_INST(T)                                                                                 \
-    template cudaError_t launch_current<T>(const CurArgs<T> &, cudaStream_t);                      \
+    template cudaError_t launch_current<T>(const CurArgs<T> &, cudaStream_t, bool);                \
     template cudaError_t launch_gather<T>(const GathArgs<T> &, cudaStream_t);                      \
     template cudaError_t launch_gather_batch<T>(const GathBatch<T> &, int, cudaStream_t);          \
     template cudaError_t launch_current_batch<T>(const CurBatch<T> &, int, cudaStream_t);          \

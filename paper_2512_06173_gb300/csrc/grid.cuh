@@ -86,7 +86,10 @@ struct ml_grid {
     int *d_blA = nullptr, *d_blB = nullptr;
     int nblA = 0, nblB = 0;
     cudaStream_t side = nullptr;
-    bool overlap = false;  // tuning (ML_OVERLAP=1): run the molecule chain beside the clear field blocks
+    bool overlap = false;
+    // the current kernel and the field pass start while the kernel before them still
+    // runs (programmatic dependent launch; ML_PDL=0 turns it off)
+    bool pdl = true;  // tuning (ML_OVERLAP=1): run the molecule chain beside the clear field blocks
     cudaEvent_t ev_join = nullptr, ev_box = nullptr;
     void *d_part = nullptr;                     // gather partials (entries, 3)
     void *d_J[3] = {};

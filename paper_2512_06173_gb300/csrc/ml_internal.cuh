@@ -261,9 +261,12 @@ template <typename T> cudaError_t launch_current_batch(const CurBatch<T> &b, int
 template <typename T> cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t s);
 template <typename T> cudaError_t launch_fold_batch(const FoldBatch<T> &b, int nwork, cudaStream_t s);
 cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
-template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s);
+// pdl: launch with programmatic stream serialisation, so that blocks that do not read
+// the molecular current may start while the current kernel still runs.
+template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s,
+                                             bool pdl = false);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
-template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,
                                                  const int *win, const int *wf, const int *wraw,

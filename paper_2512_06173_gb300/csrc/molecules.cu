@@ -314,8 +314,11 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     }
 }
 
+// The current kernel may be launched as this kernel's programmatic dependent: release
+// it at once (it waits for this kernel's completion before reading the amplitudes).
 template <typename T>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<T> a) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     molecule_body<T, true>(a, (int)blockIdx.x * MOL_WARPS);
 }
 

@@ -155,6 +155,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const bool has_mol = (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
                          x0 + TX > a.jb0[0] && y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] &&
                          k0 < a.jb0[2] + a.jbn[2] && k1 > a.jb0[2];
+    // A tile that reads the molecular current waits for the current kernel when the
+    // pass was launched as its programmatic dependent (a no-op otherwise).
+    if (has_mol) pdl_wait();
     // does a flux plane cross the tile (block-uniform)?
     bool has_pl = false;
     for (int p = 0; p < a.nplanes; p++) {
@@ -652,7 +655,7 @@ cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s) {
+cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s, bool pdl) {
     static bool configured = false;
     const size_t smem = yee_smem_bytes<T>();
     if (!configured) {
@@ -660,7 +663,18 @@ cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cu
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    yee_kernel<T><<<nblocks, dim3(TX, NTY), smem, s>>>(a, maps);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(TX, NTY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, yee_kernel<T>, a, maps);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -763,7 +777,7 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
 }
 
 #define ML_INST(T)                                                                                            \
-    template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t);                               \
+    template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t, bool);                         \
     template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t);                                        \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \

@@ -867,6 +867,17 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
     CK(cudaGetLastError());
     g->launches++;
     int ping = 0;
+    struct Ev {
+        cudaEvent_t e = nullptr;
+        ~Ev() {
+            if (e) cudaEventDestroy(e);
+        }
+    } ev_fork, ev_join;
+    const cudaStream_t cs = (M && g->side) ? g->side : s;
+    if (M) {
+        CK(cudaEventCreateWithFlags(&ev_fork.e, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_join.e, cudaEventDisableTiming));
+    }
     for (long long sg = nseg - 1; sg >= 0; sg--) {
         const long long seg0 = sg * K, len = std::min<long long>(K, N - seg0);
         ml_status st = restore(g, ck + sbytes * sg, snaps[sg], s);
@@ -898,13 +909,17 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
         for (long long t = len - 1; t >= 0; t--) {
             const long long n = seg0 + t;
             if (M) {
+                // the molecule chain of this step runs on the side stream beside pass A
+                // (pass A reads only U, Hbar and phi); pass B waits for its current
+                CK(cudaEventRecord(ev_fork.e, s));
+                CK(cudaStreamWaitEvent(cs, ev_fork.e, 0));
                 GathArgs<T> ga{};
                 ga.nblocks = g->jnb; ga.nbx = g->jnbx; ga.nby = g->jnby;
                 for (int q = 0; q < 3; q++) { ga.bn[q] = g->jbn[q]; ga.b0[q] = g->jb0[q]; ga.E[q] = U[q]; }
                 ga.px = g->px; ga.plane = g->plane;
                 ga.off = g->d_joff; ga.ent = g->d_jent; ga.wf = g->d_wf; ga.w = (const T *)g->d_w; ga.cmask = g->d_cmask;
                 ga.gcmask = g->gcmask; ga.part = (T *)g->d_part;
-                CK(launch_gather<T>(ga, s));
+                CK(launch_gather<T>(ga, cs));
                 g->launches++;
                 AdjMolArgs<T> ma{};
                 ma.nmol = M; ma.dt = (T)g->dt; ma.cmask = g->d_cmask; ma.off = g->d_off;
@@ -912,7 +927,7 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 ma.pool = g->pool; ma.moff = g->d_moff; ma.mlist = g->d_mlist; ma.part = (const T *)g->d_part;
                 ma.rho_n = recR + t * slotR; ma.Et_n = recEt + (t + 1) * slotM; ma.md_n = recMd + (t + 1) * slotM;
                 ma.rhob = rhob; ma.cadj = cadj; ma.ggam = ggam;
-                adj_mol_kernel<T><<<(M + 127) / 128, 128, 0, s>>>(ma);
+                adj_mol_kernel<T><<<(M + 127) / 128, 128, 0, cs>>>(ma);
                 CK(cudaGetLastError());
                 g->launches++;
                 CurArgs<T> ca{};
@@ -921,8 +936,9 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf; ca.w = (const T *)g->d_w;
                 ca.c = cadj; ca.cmask = g->gcmask;
                 for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
-                CK(launch_current<T>(ca, s));
+                CK(launch_current<T>(ca, cs));
                 g->launches++;
+                CK(cudaEventRecord(ev_join.e, cs));
             }
             for (int a = 0; a < 3; a++)
                 for (int q = 0; q < 2; q++) {
@@ -938,6 +954,7 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
             fa.injectE = n >= 1;
             adj_passA_kernel<T><<<fgrid, fblock, 0, s>>>(fa);
             CK(cudaGetLastError());
+            if (M) CK(cudaStreamWaitEvent(s, ev_join.e, 0));
             adj_passB_kernel<T><<<fgrid, fblock, 0, s>>>(fa);
             CK(cudaGetLastError());
             g->launches += 2;

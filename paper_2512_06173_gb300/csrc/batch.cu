@@ -9,6 +9,7 @@
 // tick at the end of the sequence, gives the kernels the absolute step (source time,
 // DFT phases).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -22,6 +23,8 @@ struct ml_batch {
     int sms = 148;
     int blocks_per_sm = 0;  // field-pass grid: blocks_per_sm x SMs (0 = one block per work item)
     bool use_graph = true;
+    // programmatic dependent launch of the current and field-pass kernels (ML_PDL=0: off)
+    bool pdl = true;
     // host copies of the argument arrays (kept alive: they are the source of async copies)
     std::vector<unsigned char> h_yargs, h_gargs, h_cargs, h_margs, h_fdesc;
     std::vector<TmapSet> h_maps;
@@ -161,12 +164,12 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
             MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st};
             CK(launch_molecules_batch<T>(mb, nmw, s));
             CurBatch<T> cb{(const CurArgs<T> *)b->d_cargs, b->d_gwork};
-            CK(launch_current_batch<T>(cb, ngw, s));
+            CK(launch_current_batch<T>(cb, ngw, s, b->pdl));
             b->launches += 2;
         }
         YeeBatch<T> yb{(const YeeArgs<T> *)b->d_yargs, b->d_maps, b->d_lev0, b->d_ywork, nyw, b->d_boff, st,
                        st % DFT_KMAX};
-        CK(launch_yee_batch<T>(yb, grid, s));
+        CK(launch_yee_batch<T>(yb, grid, s, b->pdl && nmw > 0));
         b->launches++;
         const bool period_end = st % DFT_KMAX == DFT_KMAX - 1;
         if (nfw > 0 && (period_end || (fold_tail && q == count - 1))) {
@@ -262,6 +265,7 @@ ml_status ml_batch_create(ml_grid *const *grids, int n, ml_batch **out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->blocks_per_sm = b->prec ? 1 : 3;
+    if (const char *ev = std::getenv("ML_PDL")) b->pdl = std::atoi(ev) != 0;
     cudaError_t e = cudaMalloc((void **)&b->d_boff, sizeof(long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) {

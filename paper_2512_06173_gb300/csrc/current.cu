@@ -178,6 +178,8 @@ __global__ void __launch_bounds__(JX *JY) gather_batch_kernel(const GathBatch<T>
 
 template <typename T>
 __global__ void __launch_bounds__(JX *JY) current_batch_kernel(const CurBatch<T> b) {
+    pdl_trigger();
+    pdl_wait();
     const int2 wk = b.work[blockIdx.x];
     current_body(b.args[wk.x], wk.y);
 }
@@ -190,10 +192,18 @@ cudaError_t launch_gather_batch(const GathBatch<T> &b, int nwork, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_current_batch(const CurBatch<T> &b, int nwork, cudaStream_t s) {
+cudaError_t launch_current_batch(const CurBatch<T> &b, int nwork, cudaStream_t s, bool pdl) {
     if (nwork == 0) return cudaSuccess;
-    current_batch_kernel<T><<<nwork, dim3(JX, JY), 0, s>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nwork);
+    cfg.blockDim = dim3(JX, JY);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, current_batch_kernel<T>, b);
 }
 
 template <typename T>
@@ -222,7 +232,7 @@ cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl) {
     template cudaError_t launch_current<T>(const CurArgs<T> &, cudaStream_t, bool);                \
     template cudaError_t launch_gather<T>(const GathArgs<T> &, cudaStream_t);                      \
     template cudaError_t launch_gather_batch<T>(const GathBatch<T> &, int, cudaStream_t);          \
-    template cudaError_t launch_current_batch<T>(const CurBatch<T> &, int, cudaStream_t);          \
+    template cudaError_t launch_current_batch<T>(const CurBatch<T> &, int, cudaStream_t, bool);    \
 
 ML_INST(float)
 ML_INST(double)

@@ -255,9 +255,10 @@ struct FoldBatch {
 };
 
 // launchers (explicit instantiations for float and double live in the .cu files)
-template <typename T> cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s);
+template <typename T> cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_gather_batch(const GathBatch<T> &b, int nwork, cudaStream_t s);
-template <typename T> cudaError_t launch_current_batch(const CurBatch<T> &b, int nwork, cudaStream_t s);
+template <typename T> cudaError_t launch_current_batch(const CurBatch<T> &b, int nwork, cudaStream_t s,
+                                                       bool pdl = false);
 template <typename T> cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t s);
 template <typename T> cudaError_t launch_fold_batch(const FoldBatch<T> &b, int nwork, cudaStream_t s);
 cudaError_t launch_tick(long long *c, int add, cudaStream_t s);

@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<
 // Batched form: one block per (instance, first molecule) work item.
 template <typename T>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int2 wk = b.work[blockIdx.x];
     molecule_body<T, true>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
 }

@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_batch_ke
 }
 
 template <typename T>
-cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s) {
+cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s, bool pdl) {
     static bool configured = false;
     const size_t smem = yee_smem_bytes<T>();
     if (!configured) {
@@ -650,8 +650,17 @@ cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s) {
         configured = true;
     }
     if (b.nwork == 0) return cudaSuccess;
-    yee_batch_kernel<T><<<grid, dim3(TX, NTY), smem, s>>>(b);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TX, NTY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, yee_batch_kernel<T>, b);
 }
 
 template <typename T>
@@ -778,7 +787,7 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
 
 #define ML_INST(T)                                                                                            \
     template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t, bool);                         \
-    template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t);                                        \
+    template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t, bool);                                  \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \
     template cudaError_t launch_zero_pec<T>(T *const *, int, int, int, int, long long, const int *, cudaStream_t);

@@ -470,7 +470,9 @@ def run_ours(args, world, rank, local):
     maxlink.ml_set_fields(g2.h, maxlink.ML_ALL, host_fields.data_ptr(), False, sh)
     for _ in range(K):
         maxlink.ml_step(g2.h, 1, sh)
-        maxlink.ml_get_molecules(g2.h, maxlink.ML_MOL_POP, host_pop.data_ptr(), False, sh)
+        # each step's populations into page-locked host memory, enqueued without a
+        # synchronisation; the loop synchronises once at the end
+        maxlink.ml_get_molecules(g2.h, maxlink.ML_MOL_POP, host_pop.data_ptr(), maxlink.ML_HOST_ASYNC, sh)
     fl = [g2.flux(p) for p in range(len(prob.planes))]
     stream.synchronize()
     e2e_s = allreduce_max(world, time.perf_counter() - t0)

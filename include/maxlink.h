@@ -156,7 +156,12 @@ ml_status ml_get_fields(ml_grid *g, unsigned mask, void *dst, int dst_on_device,
  * Tangential E on PEC walls is kept at zero by every later step. */
 ml_status ml_set_fields(ml_grid *g, unsigned mask, const void *src, int src_on_device, void *stream);
 
-/* Read molecular state `what` (ML_MOL_*) as doubles into dst (device or host). */
+/* Read molecular state `what` (ML_MOL_*) as doubles into dst.  dst_on_device: 1 = dst is
+ * device memory; 0 = host memory, the call synchronises `stream`; 2 = page-locked host
+ * memory, the copy is enqueued on `stream` and the call returns at once (dst holds the
+ * values once the stream reaches the copy; the caller synchronises before reading).  Modes 0
+ * and 2 stage through one device buffer of the grid: calls on different streams are ordered
+ * by the caller.  Error: ML_ERR_INVALID_ARG for another dst_on_device. */
 ml_status ml_get_molecules(ml_grid *g, int what, double *dst, int dst_on_device, void *stream);
 
 /* Net flux through plane `id` per frequency: Re sum over the plane of

@@ -912,7 +912,8 @@ ml_status ml_get_molecules(ml_grid *g, int what, double *dst, int dst_on_device,
     cudaStream_t s = (cudaStream_t)stream;
     size_t n = what == 0 ? 2 * (size_t)g->pool
                          : (what == 3 ? (size_t)g->nmol : (what == 4 ? (size_t)g->nmol * MAXLEV : 3 * (size_t)g->nmol));
-    double *tgt = dst_on_device ? dst : g->d_export;
+    if (dst_on_device < 0 || dst_on_device > 2) return fail(ML_ERR_INVALID_ARG, "dst_on_device must be 0, 1 or 2");
+    double *tgt = dst_on_device == 1 ? dst : g->d_export;
     cudaError_t e = g->prec ? launch_mol_export<double>(what, g->nmol, g->d_nlev, g->d_off, (const cx<double> *)g->d_rho,
                                                         (const double *)g->d_Et, (const double *)g->d_mudot, g->d_energy,
                                                         g->pool, tgt, s)
@@ -920,9 +921,9 @@ ml_status ml_get_molecules(ml_grid *g, int what, double *dst, int dst_on_device,
                                                        (const float *)g->d_Et, (const float *)g->d_mudot, g->d_energy,
                                                        g->pool, tgt, s);
     CK(e);
-    if (!dst_on_device) {
+    if (dst_on_device != 1) {
         CK(cudaMemcpyAsync(dst, g->d_export, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        if (dst_on_device == 0) CK(cudaStreamSynchronize(s));
     }
     return ML_OK;
 }

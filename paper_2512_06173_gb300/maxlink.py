@@ -20,6 +20,7 @@ ML_F32, ML_F64 = 0, 1
 ML_MOL_RHO, ML_MOL_EFIELD, ML_MOL_MUDOT, ML_MOL_ENERGY, ML_MOL_POP = range(5)
 ML_EX, ML_EY, ML_EZ, ML_HX, ML_HY, ML_HZ, ML_ALL = 1, 2, 4, 8, 16, 32, 63
 ML_MAX_LEVELS = 8
+ML_HOST_ASYNC = 2  # ml_get_molecules: page-locked host destination, no synchronisation
 ML_STATIC_GATHER_MAX_MOLECULES = 16384
 
 EXPORTED = ["ml_last_error", "ml_version", "ml_grid_create", "ml_grid_destroy", "ml_add_molecules",
@@ -178,7 +179,7 @@ def ml_set_fields(h: int, mask: int, src_ptr: int, on_device: bool, stream: int 
     _check(load().ml_set_fields(C.c_void_p(h), mask, C.c_void_p(src_ptr), int(on_device), C.c_void_p(stream)))
 
 
-def ml_get_molecules(h: int, what: int, dst_ptr: int, on_device: bool, stream: int = 0):
+def ml_get_molecules(h: int, what: int, dst_ptr: int, on_device: int, stream: int = 0):
     _check(load().ml_get_molecules(C.c_void_p(h), what, C.c_void_p(dst_ptr), int(on_device), C.c_void_p(stream)))
 
 

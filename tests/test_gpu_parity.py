@@ -97,6 +97,13 @@ def test_coupled_all_features(ml, oracle_mod, precision, tol, seed):
     for m in range(prob.molecules.count):
         n = int(prob.molecules.nlev[m])
         assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+    # the enqueued readback into page-locked memory gives the same bytes once the
+    # stream has reached it
+    import torch
+    pinned = torch.zeros(pops.size, dtype=torch.float64).pin_memory()
+    ml.ml_get_molecules(g.h, ml.ML_MOL_POP, pinned.data_ptr(), ml.ML_HOST_ASYNC, g.stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(pinned.numpy().reshape(pops.shape), pops)
     md = g.molecules(ml.ML_MOL_MUDOT)
     for m in range(prob.molecules.count):
         _, omd, _ = o.mol_state(m)

@@ -930,12 +930,9 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 adj_mol_kernel<T><<<(M + 127) / 128, 128, 0, cs>>>(ma);
                 CK(cudaGetLastError());
                 g->launches++;
-                CurArgs<T> ca{};
-                ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
-                for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
-                ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf; ca.w = (const T *)g->d_w;
-                ca.c = cadj; ca.cmask = g->gcmask;
-                for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
+                CurArgs<T> ca;
+                fill_cur_args<T>(g, ca);
+                ca.c = cadj;
                 CK(launch_current<T>(ca, cs));
                 g->launches++;
                 CK(cudaEventRecord(ev_join.e, cs));

@@ -379,6 +379,7 @@ ml_status rebuild_molecules(ml_grid *g) {
     auto &L = g->mol_allocs;
     const int M = g->nmol;
     ml_status st;
+    g->all_tls = std::all_of(g->kind.begin(), g->kind.end(), [](int k) { return k == 0; });
 #define CKS(x)                     \
     do {                           \
         st = (x);                  \
@@ -469,6 +470,17 @@ ml_status rebuild_molecules(ml_grid *g) {
     joff[g->jnb] = (int)jent.size();
     CKS(upload_raw(L, &g->d_joff, joff));
     if (!jent.empty()) CKS(upload_raw(L, &g->d_jent, jent));
+    {
+        std::vector<unsigned char> jmask(jent.size());
+        for (size_t e = 0; e < jent.size(); e++) {
+            const int lo = jent[e].y, hi = lo + (g->wf[jent[e].x] & 0xff);
+            unsigned mk = 0;
+            for (int q = 0; q < JX / 4; q++)
+                if (lo < 4 * q + 4 && hi > 4 * q) mk |= 1u << q;
+            jmask[e] = (unsigned char)mk;
+        }
+        if (!jmask.empty()) CKS(upload_raw(L, &g->d_jmask, jmask));
+    }
     // molecule -> entries (ascending entry index)
     std::vector<int> moff(M + 1, 0), mlist(jent.size());
     for (const int4 &e : jent) moff[e.x + 1]++;
@@ -655,6 +667,13 @@ ml_status ml_add_flux_plane(ml_grid *g, int axis, int index, int nfreq, const do
     size_t ncell = (size_t)p.nb * p.nc;
     AL(g->allocs, p.d_buf, (size_t)DFT_KMAX * 4 * ncell * g->esz);
     AL(g->allocs, p.d_acc, 4 * (size_t)nfreq * ncell * sizeof(double2));
+    AL(g->allocs, p.d_ph, 2 * (size_t)DFT_KMAX * nfreq * g->esz);
+    {
+        cudaError_t e = g->prec ? launch_dft_phases<double>(p.d_omega, nfreq, g->dt, (double *)p.d_ph, 0)
+                                : launch_dft_phases<float>(p.d_omega, nfreq, g->dt, (float *)p.d_ph, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("phase table: ") + cudaGetErrorString(e));
+    }
     g->planes.push_back(p);
     if (id) *id = (int)g->planes.size() - 1;
     return ML_OK;
@@ -669,8 +688,8 @@ ml_status fold_planes(ml_grid *g, cudaStream_t s) {
     if (g->nsamp == 0) return ML_OK;
     for (auto &p : g->planes) {
         LaunchScope ls(g, s, 3);
-        CK(launch_dft_fold<T>((const T *)p.d_buf, g->nsamp, p.nb * p.nc, p.nfreq, p.d_omega, g->samp_step0, g->dt,
-                              p.d_acc, s));
+        CK(launch_dft_fold<T>((const T *)p.d_buf, g->nsamp, p.nb * p.nc, p.nfreq, p.d_omega, (const T *)p.d_ph,
+                              g->samp_step0, g->dt, p.d_acc, s));
     }
     g->nsamp = 0;
     return ML_OK;
@@ -691,6 +710,7 @@ void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
     m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
     m.energy = g->d_energy; m.status = g->d_status;
     m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
+    m.all_tls = g->all_tls ? 1 : 0;
 }
 
 template <typename T>
@@ -708,7 +728,7 @@ void fill_cur_args(ml_grid *g, CurArgs<T> &ca) {
     ca = CurArgs<T>{};
     ca.nblocks = g->jnb; ca.nbx = g->jnbx; ca.nby = g->jnby;
     for (int a = 0; a < 3; a++) ca.bn[a] = g->jbn[a];
-    ca.off = g->d_joff; ca.ent = g->d_jent; ca.wf = g->d_wf; ca.w = (const T *)g->d_w;
+    ca.off = g->d_joff; ca.ent = g->d_jent; ca.emask = g->d_jmask; ca.wf = g->d_wf; ca.w = (const T *)g->d_w;
     ca.c = (const T *)g->d_c; ca.cmask = g->gcmask;
     for (int c = 0; c < 3; c++) ca.J[c] = (T *)g->d_J[c];
 }

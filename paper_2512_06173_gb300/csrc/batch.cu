@@ -25,6 +25,7 @@ struct ml_batch {
     bool use_graph = true;
     // programmatic dependent launch of the current and field-pass kernels (ML_PDL=0: off)
     bool pdl = true;
+    bool mol_tls = true;  // every instance's molecules are all of kind 0
     // host copies of the argument arrays (kept alive: they are the source of async copies)
     std::vector<unsigned char> h_yargs, h_gargs, h_cargs, h_margs, h_fdesc;
     std::vector<TmapSet> h_maps;
@@ -96,8 +97,10 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
     b->h_gwork.clear();
     b->h_mwork.clear();
     b->h_fwork.clear();
+    b->mol_tls = true;
     for (int i = 0; i < n; i++) {
         ml_grid *g = b->g[i];
+        if (g->nmol > 0) b->mol_tls = b->mol_tls && g->all_tls;
         fill_yee_args<T>(g, 0, ya[i]);
         ya[i].blist = nullptr;
         b->h_maps[2 * i] = g->tm[0];
@@ -119,6 +122,7 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
             d.ncell = p.nb * p.nc;
             d.nfreq = p.nfreq;
             d.omega = p.d_omega;
+            d.ph = (const T *)p.d_ph;
             d.step_base = g->step;
             d.acc = p.d_acc;
             const int di = (int)fd.size();
@@ -161,7 +165,7 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
     for (int q = 0; q < count; q++) {
         const int st = s0 + q;
         if (nmw > 0) {
-            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st};
+            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st, b->mol_tls ? 1 : 0};
             CK(launch_molecules_batch<T>(mb, nmw, s));
             CurBatch<T> cb{(const CurArgs<T> *)b->d_cargs, b->d_gwork};
             CK(launch_current_batch<T>(cb, ngw, s, b->pdl));

@@ -38,23 +38,41 @@ cudaError_t launch_dft_sample(const PlaneArgs<T> &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The plane's table of inner phases e^{i w s dt}, s < K, computed in FP64 and rounded
+// to the field type once when the plane is added: the folds then spend no FP64
+// transcendental per sample and frequency.
+template <typename T>
+__global__ void dft_phase_kernel(const double *omega, int nfreq, double dt, T *ph) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= DFT_K * nfreq) return;
+    const int s = q / nfreq, f = q % nfreq;
+    double sn, cs;
+    sincos(omega[f] * (double)s * dt, &sn, &cs);
+    ph[q] = (T)cs;
+    ph[DFT_K * nfreq + q] = (T)sn;
+}
+
+template <typename T>
+cudaError_t launch_dft_phases(const double *omega, int nfreq, double dt, T *ph, cudaStream_t s) {
+    const int n = DFT_K * nfreq;
+    dft_phase_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(omega, nfreq, dt, ph);
+    return cudaGetLastError();
+}
+
 // acc: [4][nfreq][ncell] double2.  step0: step index n of the first sample (it holds
 // E at (n+1) dt and H at (n+1/2) dt).  Sample s lies s*dt after the first, so
 //   sum_s v_s e^{i w t_s} dt = e^{i w t_0} dt * sum_s v_s e^{i w s dt}:
-// the inner K-term sum runs in the field precision T with phases rounded from FP64,
-// the product with e^{i w t_0} dt and the running sum are FP64.
+// the inner K-term sum runs in the field precision T with phases rounded from FP64
+// (the plane's table), the product with e^{i w t_0} dt and the running sum are FP64.
 template <typename T>
-__device__ __forceinline__ void fold_body(const T *buf, int nsamp, int ncell, int nfreq, const double *omega,
-                                          long long step0, double dt, double2 *acc, long long t) {
+__device__ __forceinline__ void fold_body(const T *buf, const T *ph, int nsamp, int ncell, int nfreq,
+                                          const double *omega, long long step0, double dt, double2 *acc, long long t) {
     __shared__ T phr[DFT_K * ML_MAX_FREQS_DEV];
     __shared__ T phi[DFT_K * ML_MAX_FREQS_DEV];
     __shared__ double2 p0[2 * ML_MAX_FREQS_DEV];
     for (int q = threadIdx.x; q < nsamp * nfreq; q += blockDim.x) {
-        const int s = q / nfreq, f = q % nfreq;
-        double sn, cs;
-        sincos(omega[f] * (double)s * dt, &sn, &cs);
-        phr[q] = (T)cs;
-        phi[q] = (T)sn;
+        phr[q] = ph[q];
+        phi[q] = ph[DFT_K * nfreq + q];
     }
     for (int f = threadIdx.x; f < nfreq; f += blockDim.x) {
         double sn, cs;
@@ -85,9 +103,9 @@ __device__ __forceinline__ void fold_body(const T *buf, int nsamp, int ncell, in
 }
 
 template <typename T>
-__global__ void dft_fold_kernel(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
-                                double dt, double2 *acc) {
-    fold_body(buf, nsamp, ncell, nfreq, omega, step0, dt, acc, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+__global__ void dft_fold_kernel(const T *buf, const T *ph, int nsamp, int ncell, int nfreq, const double *omega,
+                                long long step0, double dt, double2 *acc) {
+    fold_body(buf, ph, nsamp, ncell, nfreq, omega, step0, dt, acc, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // Batched fold: one block per (plane descriptor, 256-entry chunk) work item; the first
@@ -96,7 +114,7 @@ template <typename T>
 __global__ void dft_fold_batch_kernel(const FoldBatch<T> b) {
     const int2 wk = b.work[blockIdx.x];
     const FoldDesc<T> d = b.desc[wk.x];
-    fold_body(d.buf, b.nsamp, d.ncell, d.nfreq, d.omega, d.step_base + *b.boff + b.s_first, b.dt, d.acc,
+    fold_body(d.buf, d.ph, b.nsamp, d.ncell, d.nfreq, d.omega, d.step_base + *b.boff + b.s_first, b.dt, d.acc,
               (long long)wk.y * blockDim.x + threadIdx.x);
 }
 
@@ -115,12 +133,12 @@ cudaError_t launch_tick(long long *c, int add, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_dft_fold(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, long long step0,
-                            double dt, double2 *acc, cudaStream_t s) {
+cudaError_t launch_dft_fold(const T *buf, int nsamp, int ncell, int nfreq, const double *omega, const T *ph,
+                            long long step0, double dt, double2 *acc, cudaStream_t s) {
     if (nsamp == 0) return cudaSuccess;
     long long n = 4ll * ncell;
     int blocks = (int)((n + 255) / 256);
-    dft_fold_kernel<T><<<blocks, 256, 0, s>>>(buf, nsamp, ncell, nfreq, omega, step0, dt, acc);
+    dft_fold_kernel<T><<<blocks, 256, 0, s>>>(buf, ph, nsamp, ncell, nfreq, omega, step0, dt, acc);
     return cudaGetLastError();
 }
 
@@ -154,8 +172,9 @@ cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double 
 
 #define ML_INST(T)                                                                          \
     template cudaError_t launch_dft_sample<T>(const PlaneArgs<T> &, cudaStream_t);          \
-    template cudaError_t launch_dft_fold<T>(const T *, int, int, int, const double *, long long, double, \
-                                            double2 *, cudaStream_t);                                 \
+    template cudaError_t launch_dft_fold<T>(const T *, int, int, int, const double *, const T *, long long,    \
+                                            double, double2 *, cudaStream_t);                                 \
+    template cudaError_t launch_dft_phases<T>(const double *, int, double, T *, cudaStream_t);              \
     template cudaError_t launch_fold_batch<T>(const FoldBatch<T> &, int, cudaStream_t);
 ML_INST(float)
 ML_INST(double)

@@ -26,6 +26,7 @@ struct Plane {
     int axis, index, nfreq, nb, nc;
     std::vector<double> omega;
     double *d_omega = nullptr;
+    void *d_ph = nullptr;  // e^{i w s dt}, s < DFT_KMAX, in the field type: [re: s x nfreq | im: s x nfreq]
     void *d_buf = nullptr;
     double2 *d_acc = nullptr;
 };
@@ -66,6 +67,8 @@ struct ml_grid {
     int nmol = 0;
     long long pool = 0;
     std::vector<int> nlev, kind, nsub, cmask, win, wf, wraw;
+    bool all_tls = true;  // every molecule is of kind 0 (two levels, exact step)
+
     std::vector<long long> off;
     std::vector<double> pos, sigma, gamma, decay, deph, H0, mu, rho0;
     // molecules: device
@@ -80,6 +83,7 @@ struct ml_grid {
     int jnbx = 0, jnby = 0, jnb = 0, gcmask = 0;
     int *d_joff = nullptr;
     int4 *d_jent = nullptr;
+    unsigned char *d_jmask = nullptr;  // per entry: the current kernel's column groups its x window meets
     int *d_moff = nullptr, *d_mlist = nullptr;  // molecule -> its entries
     // field-pass blocks split by whether they touch the current box: the others
     // run while the gather -> molecules -> current chain runs on the side stream

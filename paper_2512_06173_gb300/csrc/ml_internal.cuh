@@ -127,8 +127,9 @@ struct CurArgs {
     int bn[3];           // box extent in cells
     const int *off;      // CSR: entries of block b are ent[off[b] .. off[b+1])
     const int4 *ent;     // (molecule, window start - block origin along x, y, z)
+    const unsigned char *emask;  // per entry: bit q set when its x window meets columns 4q .. 4q+3
     const int *wf;       // per molecule: window length along x, y, z (8 bits each)
-    const T *w;          // (M, NW) 1D kernel weights per axis and stagger
+    const T *w;          // (M, NW) 1D kernel weights per axis and stagger (zero past the window)
     const T *c;          // (M, 3) gamma * mudot of this step
     int cmask;           // components with a dipole
     T *J[3];             // box arrays (nz, ny, nx of the box)
@@ -186,6 +187,7 @@ struct MolArgs {
     const int *win;        // per molecule: canonical window start along x, y, z
     const int *wf;         // per molecule: window length along x, y, z (8 bits each)
     const T *w;            // (M, NW) 1D kernel weights per axis and stagger
+    int all_tls;           // every molecule is a two-level system stepped exactly (kind 0)
 };
 
 // ------------------------------------------------------------------ DFT planes
@@ -235,12 +237,14 @@ struct MolBatch {
     const int *lev0;
     const int2 *work;         // (instance, first molecule of the block)
     int s;
+    int all_tls;              // every instance's molecules are all of kind 0
 };
 template <typename T>
 struct FoldDesc {
     const T *buf;
     int ncell, nfreq;
     const double *omega;
+    const T *ph;              // the plane's table of e^{i w s dt}
     long long step_base;
     double2 *acc;
 };
@@ -274,8 +278,9 @@ template <typename T> cudaError_t launch_weights(int nmol, const double *pos, co
                                                  const int *dims, const int *per, T *w, cudaStream_t s);
 template <typename T> cudaError_t launch_dft_sample(const PlaneArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_dft_fold(const T *buf, int nsamp, int ncell, int nfreq,
-                                                  const double *omega, long long step0, double dt,
+                                                  const double *omega, const T *ph, long long step0, double dt,
                                                   double2 *acc, cudaStream_t s);
+template <typename T> cudaError_t launch_dft_phases(const double *omega, int nfreq, double dt, T *ph, cudaStream_t s);
 cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *out, cudaStream_t s);
 template <typename T> cudaError_t launch_pack_fields(const T *src, T *dst, int nx, int ny, int nz, int px,
                                                      long long plane, int to_padded, cudaStream_t s);

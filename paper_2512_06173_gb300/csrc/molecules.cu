@@ -37,6 +37,7 @@ __device__ __forceinline__ long long fidx(int px, long long plane, int i, int j,
 }
 
 constexpr int MOL_WARPS = 4;
+constexpr int MOL_MIN_BLOCKS = 6;  // FP32: resident blocks per SM the register budget is cut for
 
 template <typename T>
 struct MolShared {
@@ -101,8 +102,63 @@ __device__ __forceinline__ void window_gather(const MolArgs<T> &a, const int m, 
             }
             t *= sw[(c == 0 ? 1 : 0) * WMAX + dx];
         }
-        g[c] = warp_sum(t);
+        g[c] = ((cm >> c) & 1) ? warp_sum(t) : T(0);
     }
+}
+
+// FP32 form of window_gather for a window that wraps on no axis and whose x extent,
+// widened to whole 16-byte groups, is at most 16 values: every padded row starts on a
+// 128-byte boundary, so the group starting at x0 & ~3 is aligned.  Lane = 4 * row +
+// group; rows rr and rr + 8.  Per plane a lane issues one 16-byte load per row, folds
+// the four values with its x weights (zero outside the window) and accumulates wz times
+// that; the y weights are applied at the end and the xor tree adds the lanes.  The
+// rows and groups past the window are never loaded.  Returns false when the window
+// does not qualify (the caller then takes window_gather).
+__device__ __forceinline__ bool window_gather_vec(const MolArgs<float> &a, const int cm, const int wfm, const int x0,
+                                                  const int y0, const int z0, const float *sw, float (&g)[3]) {
+    const int Wx = wfm & 0xff, Wy = (wfm >> 8) & 0xff, Wz = (wfm >> 16) & 0xff;
+    const int xa = x0 & ~3, sx = x0 - xa;
+    if (sx + Wx > 16 || x0 + Wx > a.nx || y0 + Wy > a.ny || z0 + Wz > a.nz) return false;
+    const int lane = threadIdx.x & 31, qd = lane & 3, rr = lane >> 2;
+    const bool in0 = rr < Wy, in1 = rr + 8 < Wy;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float t = 0.f;
+        if ((cm >> c) & 1) {
+            const float *wx = sw + (c == 0 ? 1 : 0) * WMAX, *wy = sw + (2 + (c == 1 ? 1 : 0)) * WMAX,
+                        *wz = sw + (4 + (c == 2 ? 1 : 0)) * WMAX;
+            float wxk[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int d = 4 * qd + k - sx;
+                wxk[k] = (unsigned)d < (unsigned)Wx ? wx[d] : 0.f;
+            }
+            const float *p0 = a.E[c] + (long long)(z0 + 1) * a.plane + (long long)(y0 + rr + 1) * a.px + XO + xa + 4 * qd;
+            const float *p1 = p0 + 8ll * a.px;
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int dz = 0; dz < Wz; dz += 4) {
+                float4 v0[4], v1[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const bool pz = dz + k < Wz;
+                    const long long o = (long long)k * a.plane;
+                    v0[k] = (pz && in0) ? __ldg(reinterpret_cast<const float4 *>(p0 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v1[k] = (pz && in1) ? __ldg(reinterpret_cast<const float4 *>(p1 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float w = dz + k < Wz ? wz[dz + k] : 0.f;
+                    acc0 += w * (wxk[0] * v0[k].x + wxk[1] * v0[k].y + wxk[2] * v0[k].z + wxk[3] * v0[k].w);
+                    acc1 += w * (wxk[0] * v1[k].x + wxk[1] * v1[k].y + wxk[2] * v1[k].z + wxk[3] * v1[k].w);
+                }
+                p0 += 4 * a.plane;
+                p1 += 4 * a.plane;
+            }
+            t = (in0 ? wy[rr] : 0.f) * acc0 + (in1 ? wy[rr + 8] : 0.f) * acc1;
+        }
+        g[c] = ((cm >> c) & 1) ? warp_sum(t) : 0.f;
+    }
+    return true;
 }
 
 // GKSL right-hand side for element (j,l) of rho given in S (n x n), H in Hs.
@@ -133,7 +189,7 @@ __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, c
 
 // FUSED: the warp gathers its own regularised field from E (window_gather);
 // otherwise it adds the gather kernel's partials.
-template <typename T, bool FUSED>
+template <typename T, bool FUSED, bool TLS>
 __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0) {
     __shared__ MolShared<T> sh;
     const int lane = threadIdx.x & 31;
@@ -141,13 +197,28 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     const int m = m0 + wl;
     if (m >= a.nmol) return;  // whole warp leaves together
 
-    // ---- 0. every load of this molecule's data, issued before any is used
-    const int n = a.nlev[m];
+    // ---- 0. every load of this molecule's data, issued before any is used.  TLS: every
+    // molecule has two levels at pool offset 4 m, so no load waits for another (the
+    // dipole of an absent component is zero in the pool and is loaded as such).
+    const int n = TLS ? 2 : a.nlev[m];
     const int nn = n * n;
-    const long long o = a.off[m];
+    const long long o = TLS ? 4ll * m : a.off[m];
     const int cm = a.cmask[m];
-    const int kind = a.kind[m];
+    const int kind = TLS ? 0 : a.kind[m];
     const T gam = a.gamma[m];
+    const double e_old = lane == 0 ? a.energy[m] : 0.0;
+    // the kernel window and its weights (FUSED)
+    static_assert(NW == 96, "three weights per lane");
+    int wfm = 0, x0 = 0, y0 = 0, z0 = 0;
+    T wreg[3];
+    if (FUSED) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) wreg[q] = a.w[(long long)m * NW + lane + 32 * q];
+        wfm = a.wf[m];
+        x0 = a.win[3 * m];
+        y0 = a.win[3 * m + 1];
+        z0 = a.win[3 * m + 2];
+    }
     // lane owns density-matrix elements e = lane and e = lane + 32 (row-major n x n)
     cx<T> r0[2], h0[2], mu[3][2];
 #pragma unroll
@@ -157,18 +228,23 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         r0[q] = in ? a.rho[o + e] : cx<T>{T(0), T(0)};
         h0[q] = in ? a.H0[o + e] : cx<T>{T(0), T(0)};
 #pragma unroll
-        for (int c = 0; c < 3; c++) mu[c][q] = (in && ((cm >> c) & 1)) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
+        for (int c = 0; c < 3; c++)
+            mu[c][q] = (in && (TLS || ((cm >> c) & 1))) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
+    }
+    if (FUSED) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) sh.W[wl][lane + 32 * q] = wreg[q];
     }
     __syncwarp();
 
     // ---- 1. regularised field
     T Et[3];
     if (FUSED) {
-        T *sw = sh.W[wl];
-        for (int q = lane; q < NW; q += 32) sw[q] = a.w[(long long)m * NW + q];
-        __syncwarp();
+        const T *sw = sh.W[wl];
         T g[3];
-        window_gather(a, m, cm, sw, g);
+        bool done = false;
+        if constexpr (sizeof(T) == 4) done = window_gather_vec(a, cm, wfm, x0, y0, z0, sw, g);
+        if (!done) window_gather(a, m, cm, sw, g);
 #pragma unroll
         for (int c = 0; c < 3; c++) Et[c] = gam * g[c];
     } else {
@@ -204,12 +280,12 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         }
     }
 #pragma unroll
-    for (int c = 0; c < 3; c++) mu0[c] = warp_sum(mu0[c]);
+    for (int c = 0; c < 3; c++) mu0[c] = ((cm >> c) & 1) ? warp_sum(mu0[c]) : T(0);
     __syncwarp();
 
     // ---- 3. density-matrix step over dt with the field held
     cx<T> r1[2] = {r0[0], r0[1]};
-    if (kind == 0) {
+    if (TLS || kind == 0) {
         // exact exponential of a 2x2 Hermitian H:
         // U = e^{-i hbar dt}[cos(W dt) - i sin(W dt)/W (H - hbar)], the phase cancels in U rho U^+
         // gather rho (elements 0..3 live on lanes 0..3) into shared memory first
@@ -299,7 +375,7 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     }
     en = warp_sum(en);
 #pragma unroll
-    for (int c = 0; c < 3; c++) mu1[c] = warp_sum(mu1[c]);
+    for (int c = 0; c < 3; c++) mu1[c] = ((cm >> c) & 1) ? warp_sum(mu1[c]) : T(0);
     if (lane == 0) {
         bool bad = false;
         for (int c = 0; c < 3; c++) {
@@ -309,39 +385,47 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
             a.c[3 * m + c] = gam * md;
             if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
         }
-        a.energy[m] += (double)en;
+        a.energy[m] = e_old + (double)en;
         if (bad) atomicCAS(a.status, 0, 6);
     }
 }
 
 // The current kernel may be launched as this kernel's programmatic dependent: release
 // it at once (it waits for this kernel's completion before reading the amplitudes).
-template <typename T>
-__global__ void __launch_bounds__(MOL_WARPS * 32) molecule_kernel(const MolArgs<T> a) {
+// TLS: every molecule is of kind 0, so the Lindblad path is compiled out (fewer
+// registers, more resident warps).
+template <typename T, bool TLS>
+__global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1) molecule_kernel(const MolArgs<T> a) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    molecule_body<T, true>(a, (int)blockIdx.x * MOL_WARPS);
+    molecule_body<T, true, TLS>(a, (int)blockIdx.x * MOL_WARPS);
 }
 
 // Batched form: one block per (instance, first molecule) work item.
-template <typename T>
+template <typename T, bool TLS>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int2 wk = b.work[blockIdx.x];
-    molecule_body<T, true>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
+    molecule_body<T, true, TLS>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
 }
 
 template <typename T>
 cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t s) {
     if (nwork == 0) return cudaSuccess;
-    molecule_batch_kernel<T><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
+    if (b.all_tls)
+        molecule_batch_kernel<T, true><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
+    else
+        molecule_batch_kernel<T, false><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s) {
     if (a.nmol == 0) return cudaSuccess;
-    int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
-    molecule_kernel<T><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
+    const int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
+    if (a.all_tls)
+        molecule_kernel<T, true><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
+    else
+        molecule_kernel<T, false><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -429,7 +513,7 @@ cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long lo
 }
 
 #define ML_INST(T)                                                                                              \
-    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t);                                 \
+    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t);                             \
     template cudaError_t launch_molecules_batch<T>(const MolBatch<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \
                                            const int *, const int *, const int *, T *, cudaStream_t);           \

@@ -803,7 +803,11 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
                 MolArgs<T> m;
                 fill_mol_args<T>(g, cur, m);
                 LaunchScope ls(g, cs, 0);
-                CK(launch_molecules<T>(m, cs));
+                // programmatic dependent of the previous field pass only when that pass has
+                // tiles that read J: such a tile releases this kernel only after its wait
+                // for the previous current kernel, hence after the previous molecule
+                // kernel, so the molecule state may be staged before this kernel's wait
+                CK(launch_molecules<T>(m, cs, !chain && g->pdl && g->gcmask != 0));
             }
             {
                 CurArgs<T> ca;

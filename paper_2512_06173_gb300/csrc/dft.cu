@@ -63,14 +63,20 @@ cudaError_t launch_dft_phases(const double *omega, int nfreq, double dt, T *ph, 
 // E at (n+1) dt and H at (n+1/2) dt).  Sample s lies s*dt after the first, so
 //   sum_s v_s e^{i w t_s} dt = e^{i w t_0} dt * sum_s v_s e^{i w s dt}:
 // the inner K-term sum runs in the field precision T with phases rounded from FP64
-// (the plane's table), the product with e^{i w t_0} dt and the running sum are FP64.
+// (the plane's table), as does the product with e^{i w t_0} dt; the running sum is
+// FP64 (GB300 issues FP64 at a small fraction of the FP32 rate, so the fold keeps
+// FP64 to the accumulation).
+// The K samples of a thread's cell sit in registers (a partial fold's missing samples
+// are zeros, which add nothing), and each group of FC accumulators is loaded before
+// any of them is written back.
 template <typename T>
 __device__ __forceinline__ void fold_body(const T *buf, const T *ph, int nsamp, int ncell, int nfreq,
                                           const double *omega, long long step0, double dt, double2 *acc, long long t) {
+    constexpr int FC = 4;
     __shared__ T phr[DFT_K * ML_MAX_FREQS_DEV];
     __shared__ T phi[DFT_K * ML_MAX_FREQS_DEV];
     __shared__ double2 p0[2 * ML_MAX_FREQS_DEV];
-    for (int q = threadIdx.x; q < nsamp * nfreq; q += blockDim.x) {
+    for (int q = threadIdx.x; q < DFT_K * nfreq; q += blockDim.x) {
         phr[q] = ph[q];
         phi[q] = ph[DFT_K * nfreq + q];
     }
@@ -86,19 +92,38 @@ __device__ __forceinline__ void fold_body(const T *buf, const T *ph, int nsamp, 
     const int comp = (int)(t / ncell), cell = (int)(t % ncell);
     const double2 *ph0 = comp < 2 ? p0 : p0 + ML_MAX_FREQS_DEV;
     T v[DFT_K];
-    for (int s = 0; s < nsamp; s++) v[s] = buf[((long long)s * 4 + comp) * ncell + cell];
-    for (int f = 0; f < nfreq; f++) {
-        T re = T(0), im = T(0);
-        for (int s = 0; s < nsamp; s++) {
-            re += v[s] * phr[s * nfreq + f];
-            im += v[s] * phi[s * nfreq + f];
+#pragma unroll
+    for (int s = 0; s < DFT_K; s++) v[s] = s < nsamp ? buf[((long long)s * 4 + comp) * ncell + cell] : T(0);
+    double2 *o = acc + (long long)comp * nfreq * ncell + cell;
+    for (int f0 = 0; f0 < nfreq; f0 += FC) {
+        double2 x[FC];
+#pragma unroll
+        for (int k = 0; k < FC; k++)
+            if (f0 + k < nfreq) x[k] = o[(long long)(f0 + k) * ncell];
+#pragma unroll
+        for (int k = 0; k < FC; k++) {
+            const int f = f0 + k;
+            if (f < nfreq) {
+                T re = T(0), im = T(0);
+#pragma unroll
+                for (int s = 0; s < DFT_K; s++) {
+                    re += v[s] * phr[s * nfreq + f];
+                    im += v[s] * phi[s * nfreq + f];
+                }
+                const double2 e0 = ph0[f];
+                if constexpr (sizeof(T) == 4) {
+                    // FP32 fields: the product with e^{i w t_0} dt in FP32 (its rounding is
+                    // that of the K-term sum), only the running sum in FP64
+                    const float e0x = (float)e0.x, e0y = (float)e0.y;
+                    x[k].x += (double)(re * e0x - im * e0y);
+                    x[k].y += (double)(re * e0y + im * e0x);
+                } else {
+                    x[k].x += (double)re * e0.x - (double)im * e0.y;
+                    x[k].y += (double)re * e0.y + (double)im * e0.x;
+                }
+                o[(long long)f * ncell] = x[k];
+            }
         }
-        const double2 e0 = ph0[f];
-        double2 *o = acc + ((long long)comp * nfreq + f) * ncell + cell;
-        double2 x = *o;
-        x.x += (double)re * e0.x - (double)im * e0.y;
-        x.y += (double)re * e0.y + (double)im * e0.x;
-        *o = x;
     }
 }
 

@@ -270,7 +270,7 @@ cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
 // the molecular current may start while the current kernel still runs.
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s,
                                              bool pdl = false);
-template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,

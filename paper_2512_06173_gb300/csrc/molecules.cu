@@ -237,6 +237,13 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     }
     __syncwarp();
 
+    // ---- programmatic dependence: everything above is this molecule's own state.  When
+    // the kernel is launched as the previous field pass's dependent, the field (or the
+    // gather partials) is read only after that pass has completed, and the current
+    // kernel is released only then.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     // ---- 1. regularised field
     T Et[3];
     if (FUSED) {
@@ -390,20 +397,20 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     }
 }
 
-// The current kernel may be launched as this kernel's programmatic dependent: release
-// it at once (it waits for this kernel's completion before reading the amplitudes).
+// The kernel may be launched as the previous field pass's programmatic dependent, and
+// the current kernel as this one's: molecule_body waits for the field pass before it
+// reads the field and releases the current kernel after that wait (the current kernel
+// waits for this kernel's completion before it reads the amplitudes).
 // TLS: every molecule is of kind 0, so the Lindblad path is compiled out (fewer
 // registers, more resident warps).
 template <typename T, bool TLS>
 __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1) molecule_kernel(const MolArgs<T> a) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     molecule_body<T, true, TLS>(a, (int)blockIdx.x * MOL_WARPS);
 }
 
 // Batched form: one block per (instance, first molecule) work item.
 template <typename T, bool TLS>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int2 wk = b.work[blockIdx.x];
     molecule_body<T, true, TLS>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
 }
@@ -419,14 +426,19 @@ cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t
 }
 
 template <typename T>
-cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s) {
+cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl) {
     if (a.nmol == 0) return cudaSuccess;
-    const int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
-    if (a.all_tls)
-        molecule_kernel<T, true><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
-    else
-        molecule_kernel<T, false><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.nmol + MOL_WARPS - 1) / MOL_WARPS);
+    cfg.blockDim = dim3(MOL_WARPS * 32);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return a.all_tls ? cudaLaunchKernelEx(&cfg, molecule_kernel<T, true>, a)
+                     : cudaLaunchKernelEx(&cfg, molecule_kernel<T, false>, a);
 }
 
 // K3: weights.  One thread per (molecule, axis, stagger).  The raw window has
@@ -513,7 +525,7 @@ cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long lo
 }
 
 #define ML_INST(T)                                                                                              \
-    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t);                             \
+    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t, bool);                             \
     template cudaError_t launch_molecules_batch<T>(const MolBatch<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \
                                            const int *, const int *, const int *, T *, cudaStream_t);           \

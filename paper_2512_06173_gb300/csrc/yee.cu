@@ -158,6 +158,12 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     // A tile that reads the molecular current waits for the current kernel when the
     // pass was launched as its programmatic dependent (a no-op otherwise).
     if (has_mol) pdl_wait();
+    // Release the next step's molecule kernel when it is launched as this pass's
+    // programmatic dependent: it stages its own state, then waits for this pass to
+    // complete before it reads the field.  A tile that waited above releases it only
+    // afterwards, so a release also implies that this step's molecule and current
+    // kernels are complete.
+    pdl_trigger();
     // does a flux plane cross the tile (block-uniform)?
     bool has_pl = false;
     for (int p = 0; p < a.nplanes; p++) {

@@ -234,8 +234,8 @@ ml_status ml_set_couplings(ml_grid *g, const double *gamma, int on_device, void 
 /* ---- Batches of independent grids (many realisations of uneven sizes) ----------
  * A batch advances several grids of the same precision and time step together:
  * each step is one launch per kernel class over every instance's blocks (gather,
- * molecules, current, one persistent field pass, and a DFT fold every 16 steps),
- * and runs of 32 steps are replayed from a CUDA graph captured on first use.
+ * molecules, current, one persistent field pass, and a DFT fold every 64 steps),
+ * and runs of 64 steps are replayed from a CUDA graph captured on first use.
  * Results are identical to stepping each grid with ml_step.  The grids keep their
  * own state and API (fields, flux, absorbed energy, checkpoints); while a batch
  * exists, structural changes to a member (molecules, planes) are picked up at the

@@ -756,7 +756,7 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
         st = snapshot(g, ck + sbytes * nseg, snaps[nseg], s);
         if (st != ML_OK) return st;
     }
-    CK(launch_flux_reduce(pl.d_acc, (int)ncell, pl.nfreq, g->d_scalar, s));
+    CK(launch_flux_reduce(pl.d_acc, (int)ncell, pl.nfreq, g->d_fpart, g->d_scalar, s));
     // the chosen frequency's sums, kept aside: the recompute below refills the plane
     double2 *objacc = nullptr;
     AA(objacc, 4 * (size_t)ncell * sizeof(double2));

@@ -325,6 +325,7 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     GA(g->d_zcut, g->zcut.size() * sizeof(int));
     GC(cudaMemcpy(g->d_zcut, g->zcut.data(), g->zcut.size() * sizeof(int), cudaMemcpyHostToDevice));
     GA(g->d_scalar, 64 * sizeof(double));
+    GA(g->d_fpart, (size_t)ML_MAX_FREQS * FLUX_NB * sizeof(double));
     GA(g->d_status, sizeof(int));
     for (int q = 0; q < d->n_sources; q++) {
         const ml_source &s = d->sources[q];
@@ -379,7 +380,8 @@ ml_status rebuild_molecules(ml_grid *g) {
     auto &L = g->mol_allocs;
     const int M = g->nmol;
     ml_status st;
-    g->all_tls = std::all_of(g->kind.begin(), g->kind.end(), [](int k) { return k == 0; });
+    // every molecule two-level: the pool offsets are then 4 m (pools are appended in order)
+    g->two_level = std::all_of(g->nlev.begin(), g->nlev.end(), [](int n) { return n == 2; });
 #define CKS(x)                     \
     do {                           \
         st = (x);                  \
@@ -710,7 +712,7 @@ void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
     m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
     m.energy = g->d_energy; m.status = g->d_status;
     m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
-    m.all_tls = g->all_tls ? 1 : 0;
+    m.two_level = g->two_level ? 1 : 0;
 }
 
 template <typename T>
@@ -959,7 +961,7 @@ ml_status ml_flux(ml_grid *g, int id, double *out, void *stream) {
     ml_status st = g->prec ? fold_planes<double>(g, s) : fold_planes<float>(g, s);
     if (st != ML_OK) return st;
     Plane &p = g->planes[id];
-    CK(launch_flux_reduce(p.d_acc, p.nb * p.nc, p.nfreq, g->d_scalar, s));
+    CK(launch_flux_reduce(p.d_acc, p.nb * p.nc, p.nfreq, g->d_fpart, g->d_scalar, s));
     CK(cudaMemcpyAsync(out, g->d_scalar, p.nfreq * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return ML_OK;

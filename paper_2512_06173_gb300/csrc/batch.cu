@@ -4,8 +4,8 @@
 //   field pass                        (one persistent launch over every instance's tiles)
 //   plane fold every DFT_KMAX steps   (one launch over every instance's planes)
 // The per-instance kernel arguments live in device arrays, written once per
-// ml_batch_step call.  A 32-step sequence (two time levels x two fold periods) is
-// captured once into a CUDA graph and replayed; a device step counter, advanced by a
+// ml_batch_step call.  A 64-step sequence (an even number of steps, whole fold periods)
+// is captured once into a CUDA graph and replayed; a device step counter, advanced by a
 // tick at the end of the sequence, gives the kernels the absolute step (source time,
 // DFT phases).
 #include <algorithm>
@@ -25,7 +25,7 @@ struct ml_batch {
     bool use_graph = true;
     // programmatic dependent launch of the current and field-pass kernels (ML_PDL=0: off)
     bool pdl = true;
-    bool mol_tls = true;  // every instance's molecules are all of kind 0
+    bool mol_two_level = true;  // every instance's molecules are all two-level
     // host copies of the argument arrays (kept alive: they are the source of async copies)
     std::vector<unsigned char> h_yargs, h_gargs, h_cargs, h_margs, h_fdesc;
     std::vector<TmapSet> h_maps;
@@ -48,7 +48,8 @@ struct ml_batch {
 
 namespace {
 
-constexpr int SEQ = 32;  // steps per captured sequence
+constexpr int SEQ = 64;  // steps per captured sequence: two time levels, whole fold periods
+static_assert(SEQ % DFT_KMAX == 0 && SEQ % 2 == 0, "a sequence starts at a fold boundary and on level 0");
 
 ml_status ensure(void **p, size_t &cap, size_t bytes) {
     if (bytes <= cap && *p) return ML_OK;
@@ -97,10 +98,10 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
     b->h_gwork.clear();
     b->h_mwork.clear();
     b->h_fwork.clear();
-    b->mol_tls = true;
+    b->mol_two_level = true;
     for (int i = 0; i < n; i++) {
         ml_grid *g = b->g[i];
-        if (g->nmol > 0) b->mol_tls = b->mol_tls && g->all_tls;
+        if (g->nmol > 0) b->mol_two_level = b->mol_two_level && g->two_level;
         fill_yee_args<T>(g, 0, ya[i]);
         ya[i].blist = nullptr;
         b->h_maps[2 * i] = g->tm[0];
@@ -165,7 +166,7 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
     for (int q = 0; q < count; q++) {
         const int st = s0 + q;
         if (nmw > 0) {
-            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st, b->mol_tls ? 1 : 0};
+            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st, b->mol_two_level ? 1 : 0};
             CK(launch_molecules_batch<T>(mb, nmw, s));
             CurBatch<T> cb{(const CurArgs<T> *)b->d_cargs, b->d_gwork};
             CK(launch_current_batch<T>(cb, ngw, s, b->pdl));

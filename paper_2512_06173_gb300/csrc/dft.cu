@@ -65,21 +65,19 @@ cudaError_t launch_dft_phases(const double *omega, int nfreq, double dt, T *ph, 
 // the inner K-term sum runs in the field precision T with phases rounded from FP64
 // (the plane's table), as does the product with e^{i w t_0} dt; the running sum is
 // FP64 (GB300 issues FP64 at a small fraction of the FP32 rate, so the fold keeps
-// FP64 to the accumulation).
-// The K samples of a thread's cell sit in registers (a partial fold's missing samples
-// are zeros, which add nothing), and each group of FC accumulators is loaded before
-// any of them is written back.
+// FP64 to the accumulation, once per K steps).
+// A thread owns one (component, cell); per group of FC frequencies it stages that
+// group's phases in shared memory, loads the FC accumulators, runs the K samples through
+// registers SC at a time (a partial fold's missing samples are zeros, which add nothing)
+// and writes the accumulators back.
 template <typename T>
 __device__ __forceinline__ void fold_body(const T *buf, const T *ph, int nsamp, int ncell, int nfreq,
                                           const double *omega, long long step0, double dt, double2 *acc, long long t) {
-    constexpr int FC = 4;
-    __shared__ T phr[DFT_K * ML_MAX_FREQS_DEV];
-    __shared__ T phi[DFT_K * ML_MAX_FREQS_DEV];
+    constexpr int FC = 8, SC = 8;
+    static_assert(DFT_K % SC == 0, "whole sample groups");
+    __shared__ __align__(16) T phr[DFT_K][FC];
+    __shared__ __align__(16) T phi[DFT_K][FC];
     __shared__ double2 p0[2 * ML_MAX_FREQS_DEV];
-    for (int q = threadIdx.x; q < DFT_K * nfreq; q += blockDim.x) {
-        phr[q] = ph[q];
-        phi[q] = ph[DFT_K * nfreq + q];
-    }
     for (int f = threadIdx.x; f < nfreq; f += blockDim.x) {
         double sn, cs;
         sincos(omega[f] * (double)(step0 + 1) * dt, &sn, &cs);
@@ -87,39 +85,71 @@ __device__ __forceinline__ void fold_body(const T *buf, const T *ph, int nsamp, 
         sincos(omega[f] * ((double)step0 + 0.5) * dt, &sn, &cs);
         p0[ML_MAX_FREQS_DEV + f] = make_double2(cs * dt, sn * dt);
     }
-    __syncthreads();
-    if (t >= 4ll * ncell) return;
-    const int comp = (int)(t / ncell), cell = (int)(t % ncell);
+    const bool act = t < 4ll * ncell;
+    const int comp = act ? (int)(t / ncell) : 0, cell = act ? (int)(t % ncell) : 0;
     const double2 *ph0 = comp < 2 ? p0 : p0 + ML_MAX_FREQS_DEV;
-    T v[DFT_K];
-#pragma unroll
-    for (int s = 0; s < DFT_K; s++) v[s] = s < nsamp ? buf[((long long)s * 4 + comp) * ncell + cell] : T(0);
+    const T *col = buf + (long long)comp * ncell + cell;  // sample s at col[4 s ncell]
     double2 *o = acc + (long long)comp * nfreq * ncell + cell;
     for (int f0 = 0; f0 < nfreq; f0 += FC) {
+        __syncthreads();  // the previous group's phases are consumed (p0 is written)
+        for (int q = threadIdx.x; q < DFT_K * FC; q += blockDim.x) {
+            const int s = q / FC, k = q % FC;
+            const bool in = f0 + k < nfreq;
+            phr[s][k] = in ? ph[s * nfreq + f0 + k] : T(0);
+            phi[s][k] = in ? ph[DFT_K * nfreq + s * nfreq + f0 + k] : T(0);
+        }
+        __syncthreads();
+        if (!act) continue;
         double2 x[FC];
 #pragma unroll
         for (int k = 0; k < FC; k++)
             if (f0 + k < nfreq) x[k] = o[(long long)(f0 + k) * ncell];
+        T re[FC], im[FC];
+#pragma unroll
+        for (int k = 0; k < FC; k++) re[k] = im[k] = T(0);
+        for (int s0 = 0; s0 < nsamp; s0 += SC) {
+            T v[SC];
+#pragma unroll
+            for (int j = 0; j < SC; j++) v[j] = s0 + j < nsamp ? col[4ll * (s0 + j) * ncell] : T(0);
+#pragma unroll
+            for (int j = 0; j < SC; j++) {
+                T pr[FC], pi[FC];
+                if constexpr (sizeof(T) == 4) {  // the group's phases of a sample as 16-byte loads
+#pragma unroll
+                    for (int k = 0; k < FC; k += 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(&phr[s0 + j][k]);
+                        const float4 b = *reinterpret_cast<const float4 *>(&phi[s0 + j][k]);
+                        pr[k] = a.x; pr[k + 1] = a.y; pr[k + 2] = a.z; pr[k + 3] = a.w;
+                        pi[k] = b.x; pi[k + 1] = b.y; pi[k + 2] = b.z; pi[k + 3] = b.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < FC; k++) {
+                        pr[k] = phr[s0 + j][k];
+                        pi[k] = phi[s0 + j][k];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < FC; k++) {
+                    re[k] += v[j] * pr[k];
+                    im[k] += v[j] * pi[k];
+                }
+            }
+        }
 #pragma unroll
         for (int k = 0; k < FC; k++) {
             const int f = f0 + k;
             if (f < nfreq) {
-                T re = T(0), im = T(0);
-#pragma unroll
-                for (int s = 0; s < DFT_K; s++) {
-                    re += v[s] * phr[s * nfreq + f];
-                    im += v[s] * phi[s * nfreq + f];
-                }
                 const double2 e0 = ph0[f];
                 if constexpr (sizeof(T) == 4) {
                     // FP32 fields: the product with e^{i w t_0} dt in FP32 (its rounding is
                     // that of the K-term sum), only the running sum in FP64
                     const float e0x = (float)e0.x, e0y = (float)e0.y;
-                    x[k].x += (double)(re * e0x - im * e0y);
-                    x[k].y += (double)(re * e0y + im * e0x);
+                    x[k].x += (double)(re[k] * e0x - im[k] * e0y);
+                    x[k].y += (double)(re[k] * e0y + im[k] * e0x);
                 } else {
-                    x[k].x += (double)re * e0.x - (double)im * e0.y;
-                    x[k].y += (double)re * e0.y + (double)im * e0.x;
+                    x[k].x += (double)re[k] * e0.x - (double)im[k] * e0.y;
+                    x[k].y += (double)re[k] * e0.y + (double)im[k] * e0.x;
                 }
                 o[(long long)f * ncell] = x[k];
             }
@@ -167,17 +197,18 @@ cudaError_t launch_dft_fold(const T *buf, int nsamp, int ncell, int nfreq, const
     return cudaGetLastError();
 }
 
-// out[f] = sum_cells Re(E_b conj(H_c) - E_c conj(H_b)), one block per frequency,
-// fixed-order tree reduction.
-__global__ void flux_reduce_kernel(const double2 *acc, int ncell, int nfreq, double *out) {
+// out[f] = sum_cells Re(E_b conj(H_c) - E_c conj(H_b)) in two fixed-order stages:
+// FLUX_NB blocks per frequency each reduce a strided share of the cells into part[f][b]
+// with a tree, then one block per frequency adds its FLUX_NB partials with a tree.
+__global__ void flux_partial_kernel(const double2 *acc, int ncell, int nfreq, double *part) {
     __shared__ double red[256];
-    const int f = blockIdx.x;
+    const int f = blockIdx.y, b = blockIdx.x;
     const double2 *E1 = acc + (0ll * nfreq + f) * ncell;
     const double2 *E2 = acc + (1ll * nfreq + f) * ncell;
     const double2 *H1 = acc + (2ll * nfreq + f) * ncell;
     const double2 *H2 = acc + (3ll * nfreq + f) * ncell;
     double s = 0.0;
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    for (int c = b * blockDim.x + threadIdx.x; c < ncell; c += FLUX_NB * blockDim.x) {
         double2 e1 = E1[c], e2 = E2[c], h1 = H1[c], h2 = H2[c];
         s += (e1.x * h2.x + e1.y * h2.y) - (e2.x * h1.x + e2.y * h1.y);
     }
@@ -187,11 +218,24 @@ __global__ void flux_reduce_kernel(const double2 *acc, int ncell, int nfreq, dou
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
+    if (threadIdx.x == 0) part[f * FLUX_NB + b] = red[0];
+}
+
+__global__ void flux_final_kernel(const double *part, double *out) {
+    __shared__ double red[FLUX_NB];
+    const int f = blockIdx.x;
+    red[threadIdx.x] = part[f * FLUX_NB + threadIdx.x];
+    __syncthreads();
+    for (int o = FLUX_NB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) out[f] = red[0];
 }
 
-cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *out, cudaStream_t s) {
-    flux_reduce_kernel<<<nfreq, 256, 0, s>>>(acc, ncell, nfreq, out);
+cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *part, double *out, cudaStream_t s) {
+    flux_partial_kernel<<<dim3(FLUX_NB, nfreq), 256, 0, s>>>(acc, ncell, nfreq, part);
+    flux_final_kernel<<<nfreq, FLUX_NB, 0, s>>>(part, out);
     return cudaGetLastError();
 }
 

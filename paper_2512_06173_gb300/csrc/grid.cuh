@@ -62,12 +62,13 @@ struct ml_grid {
     void *JD[3] = {};
     double *absorbed_part = nullptr;
     double *d_scalar = nullptr;
+    double *d_fpart = nullptr;  // flux reduction partials (ML_MAX_FREQS x FLUX_NB)
     std::vector<ml::SrcDev> src;
     // molecules: host mirror of the static description
     int nmol = 0;
     long long pool = 0;
     std::vector<int> nlev, kind, nsub, cmask, win, wf, wraw;
-    bool all_tls = true;  // every molecule is of kind 0 (two levels, exact step)
+    bool two_level = true;  // every molecule has two levels (pool offset 4 m)
 
     std::vector<long long> off;
     std::vector<double> pos, sigma, gamma, decay, deph, H0, mu, rho0;

@@ -39,7 +39,7 @@ constexpr int MAXLEV = 8;
 constexpr int MAXSRC = 4;
 constexpr int MAXPLANES = 8;
 #define ML_MAX_FREQS_DEV 64
-constexpr int DFT_KMAX = 16;  // samples buffered per plane before a fold
+constexpr int DFT_KMAX = 64;  // samples buffered per plane before a fold
 
 struct SrcDev {
     int axis, index, comp;
@@ -187,7 +187,7 @@ struct MolArgs {
     const int *win;        // per molecule: canonical window start along x, y, z
     const int *wf;         // per molecule: window length along x, y, z (8 bits each)
     const T *w;            // (M, NW) 1D kernel weights per axis and stagger
-    int all_tls;           // every molecule is a two-level system stepped exactly (kind 0)
+    int two_level;         // every molecule has two levels, at pool offset 4 m
 };
 
 // ------------------------------------------------------------------ DFT planes
@@ -237,7 +237,7 @@ struct MolBatch {
     const int *lev0;
     const int2 *work;         // (instance, first molecule of the block)
     int s;
-    int all_tls;              // every instance's molecules are all of kind 0
+    int two_level;            // every instance's molecules are all two-level
 };
 template <typename T>
 struct FoldDesc {
@@ -281,7 +281,8 @@ template <typename T> cudaError_t launch_dft_fold(const T *buf, int nsamp, int n
                                                   const double *omega, const T *ph, long long step0, double dt,
                                                   double2 *acc, cudaStream_t s);
 template <typename T> cudaError_t launch_dft_phases(const double *omega, int nfreq, double dt, T *ph, cudaStream_t s);
-cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *out, cudaStream_t s);
+constexpr int FLUX_NB = 64;  // blocks per frequency of the flux reduction (a power of two)
+cudaError_t launch_flux_reduce(const double2 *acc, int ncell, int nfreq, double *part, double *out, cudaStream_t s);
 template <typename T> cudaError_t launch_pack_fields(const T *src, T *dst, int nx, int ny, int nz, int px,
                                                      long long plane, int to_padded, cudaStream_t s);
 template <typename T> cudaError_t launch_refresh_ghosts(T *f, int nx, int ny, int nz, int px, long long plane,

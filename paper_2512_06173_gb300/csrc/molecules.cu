@@ -189,7 +189,7 @@ __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, c
 
 // FUSED: the warp gathers its own regularised field from E (window_gather);
 // otherwise it adds the gather kernel's partials.
-template <typename T, bool FUSED, bool TLS>
+template <typename T, bool FUSED, bool N2>
 __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0) {
     __shared__ MolShared<T> sh;
     const int lane = threadIdx.x & 31;
@@ -197,14 +197,15 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     const int m = m0 + wl;
     if (m >= a.nmol) return;  // whole warp leaves together
 
-    // ---- 0. every load of this molecule's data, issued before any is used.  TLS: every
+    // ---- 0. every load of this molecule's data, issued before any is used.  N2: every
     // molecule has two levels at pool offset 4 m, so no load waits for another (the
-    // dipole of an absent component is zero in the pool and is loaded as such).
-    const int n = TLS ? 2 : a.nlev[m];
+    // dipole of an absent component is zero in the pool and is loaded as such) and the
+    // Lindblad right-hand side is unrolled for n = 2.
+    const int n = N2 ? 2 : a.nlev[m];
     const int nn = n * n;
-    const long long o = TLS ? 4ll * m : a.off[m];
+    const long long o = N2 ? 4ll * m : a.off[m];
     const int cm = a.cmask[m];
-    const int kind = TLS ? 0 : a.kind[m];
+    const int kind = a.kind[m];
     const T gam = a.gamma[m];
     const double e_old = lane == 0 ? a.energy[m] : 0.0;
     // the kernel window and its weights (FUSED)
@@ -229,7 +230,7 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         h0[q] = in ? a.H0[o + e] : cx<T>{T(0), T(0)};
 #pragma unroll
         for (int c = 0; c < 3; c++)
-            mu[c][q] = (in && (TLS || ((cm >> c) & 1))) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
+            mu[c][q] = (in && (N2 || ((cm >> c) & 1))) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
     }
     if (FUSED) {
 #pragma unroll
@@ -292,7 +293,7 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 
     // ---- 3. density-matrix step over dt with the field held
     cx<T> r1[2] = {r0[0], r0[1]};
-    if (TLS || kind == 0) {
+    if (kind == 0) {
         // exact exponential of a 2x2 Hermitian H:
         // U = e^{-i hbar dt}[cos(W dt) - i sin(W dt)/W (H - hbar)], the phase cancels in U rho U^+
         // gather rho (elements 0..3 live on lanes 0..3) into shared memory first
@@ -401,24 +402,23 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 // the current kernel as this one's: molecule_body waits for the field pass before it
 // reads the field and releases the current kernel after that wait (the current kernel
 // waits for this kernel's completion before it reads the amplitudes).
-// TLS: every molecule is of kind 0, so the Lindblad path is compiled out (fewer
-// registers, more resident warps).
-template <typename T, bool TLS>
+// N2: every molecule has two levels (see molecule_body).
+template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1) molecule_kernel(const MolArgs<T> a) {
-    molecule_body<T, true, TLS>(a, (int)blockIdx.x * MOL_WARPS);
+    molecule_body<T, true, N2>(a, (int)blockIdx.x * MOL_WARPS);
 }
 
 // Batched form: one block per (instance, first molecule) work item.
-template <typename T, bool TLS>
+template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
     const int2 wk = b.work[blockIdx.x];
-    molecule_body<T, true, TLS>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
+    molecule_body<T, true, N2>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
 }
 
 template <typename T>
 cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t s) {
     if (nwork == 0) return cudaSuccess;
-    if (b.all_tls)
+    if (b.two_level)
         molecule_batch_kernel<T, true><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
     else
         molecule_batch_kernel<T, false><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
@@ -437,7 +437,7 @@ cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl) {
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = pdl ? 1 : 0;
-    return a.all_tls ? cudaLaunchKernelEx(&cfg, molecule_kernel<T, true>, a)
+    return a.two_level ? cudaLaunchKernelEx(&cfg, molecule_kernel<T, true>, a)
                      : cudaLaunchKernelEx(&cfg, molecule_kernel<T, false>, a);
 }
 

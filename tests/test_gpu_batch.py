@@ -68,7 +68,7 @@ def test_batch_matches_single_grids(ml, precision, tuning):
     if precision == 1 and tuning[0] > 1:
         pytest.skip("FP64 field pass holds one block per SM")
     probs = problems()
-    steps = 70  # two captured 32-step sequences and a 6-step tail
+    steps = 134  # two captured 64-step sequences and a 6-step tail
     ref = run_single(ml, probs, precision, steps)
     grids = [ml.Grid(p, precision) for p in probs]
     try:

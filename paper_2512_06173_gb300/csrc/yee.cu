@@ -537,6 +537,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 a.absorbed_part[tile] += s;
             }
         }
+        // When the pass is a programmatic dependent, its completion must imply that of
+        // the kernel before it (the next kernel's wait covers only this one).
+        pdl_wait();
         return true;
     }
 drain:
@@ -550,6 +553,7 @@ drain:
         }
     }
     __syncthreads();
+    pdl_wait();
     return false;
 }
 
@@ -590,7 +594,7 @@ __device__ __forceinline__ bool yee_dispatch(const YeeArgs<T> &a, const TmapSet 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_kernel(const YeeArgs<T> a,
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) yee_kernel(const YeeArgs<T> a,
                                                                            const __grid_constant__ TmapSet maps) {
     const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
     yee_dispatch(a, maps, tile);

@@ -164,6 +164,20 @@ ml_status ml_set_fields(ml_grid *g, unsigned mask, const void *src, int src_on_d
  * by the caller.  Error: ML_ERR_INVALID_ARG for another dst_on_device. */
 ml_status ml_get_molecules(ml_grid *g, int what, double *dst, int dst_on_device, void *stream);
 
+/* Population sink: every later ml_step writes the level populations of the new state
+ * (the diagonal of rho^{n+1}, Eq. population_decay_superradiance's P_e for two levels) of
+ * molecule m, as doubles, into
+ *     host[((s mod ring_steps) * count + m) * ML_MAX_LEVELS + l],  l < nlev(m),
+ * where s is the index of the step being taken (ml_step_count before it); the other
+ * entries are never written.  The molecule kernel stores them directly into `host`, which
+ * must be page-locked host memory the device can address (cudaHostAlloc, cudaMallocHost
+ * or cudaHostRegister), so no copy or extra kernel enters the stream; the values of a
+ * step are in place once the stream has passed that step.  `host` stays owned by the
+ * caller and must outlive the sink.  NULL removes the sink.  Batches (ml_batch_step) and
+ * the sweeps of ml_adjoint_run do not write it.  Errors: ML_ERR_INVALID_ARG for
+ * ring_steps < 1 or a pointer the device cannot address. */
+ml_status ml_set_population_sink(ml_grid *g, double *host, int64_t ring_steps);
+
 /* Net flux through plane `id` per frequency: Re sum over the plane of
  * (E~ x H~*) . n (Sec. IV.C, IV.D spectra), H~ averaged over the two half cells
  * around the plane.  out: host, nfreq doubles.  Synchronises `stream`. */

@@ -998,8 +998,12 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
     }
     const int K = (int)std::min<int64_t>(ckpt_every, nsteps);
     cudaStream_t s = (cudaStream_t)stream;
-    return g->prec ? adjoint_impl<double>(g, nsteps, K, plane_id, freq, objective, grad_eps, grad_gamma, on_device, s)
-                   : adjoint_impl<float>(g, nsteps, K, plane_id, freq, objective, grad_eps, grad_gamma, on_device, s);
+    g->pop_off = true;  // the sweeps write no population sink
+    const ml_status st =
+        g->prec ? adjoint_impl<double>(g, nsteps, K, plane_id, freq, objective, grad_eps, grad_gamma, on_device, s)
+                : adjoint_impl<float>(g, nsteps, K, plane_id, freq, objective, grad_eps, grad_gamma, on_device, s);
+    g->pop_off = false;
+    return st;
 }
 
 // Parameters of the objective: the design-box permittivity and the couplings.

@@ -713,6 +713,8 @@ void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
     m.energy = g->d_energy; m.status = g->d_status;
     m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
     m.two_level = g->two_level ? 1 : 0;
+    m.pop_sink = g->pop_off ? nullptr : g->pop_sink;
+    m.pop_slot = g->pop_sink ? (g->step % g->pop_ring) * (long long)g->nmol * MAXLEV : 0;
 }
 
 template <typename T>
@@ -928,6 +930,25 @@ ml_status ml_set_fields(ml_grid *g, unsigned mask, const void *src, int src_on_d
         in += N * g->esz;
         if (!src_on_device) CK(cudaStreamSynchronize(s));  // scratch is reused
     }
+    return ML_OK;
+}
+
+ml_status ml_set_population_sink(ml_grid *g, double *host, int64_t ring_steps) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    if (!host) {
+        g->pop_sink = nullptr;
+        g->pop_ring = 0;
+        return ML_OK;
+    }
+    if (ring_steps < 1) return fail(ML_ERR_INVALID_ARG, "ring_steps must be >= 1");
+    void *dev = nullptr;
+    cudaError_t e = cudaHostGetDevicePointer(&dev, host, 0);
+    if (e != cudaSuccess || !dev) {
+        cudaGetLastError();
+        return fail(ML_ERR_INVALID_ARG, "the population sink must be page-locked host memory the device can address");
+    }
+    g->pop_sink = (double *)dev;
+    g->pop_ring = ring_steps;
     return ML_OK;
 }
 

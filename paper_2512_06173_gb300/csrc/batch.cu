@@ -114,6 +114,7 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
             fill_cur_args<T>(g, ca[i]);
             fill_mol_args<T>(g, 0, ma[2 * i]);
             fill_mol_args<T>(g, 1, ma[2 * i + 1]);
+            ma[2 * i].pop_sink = ma[2 * i + 1].pop_sink = nullptr;  // batches write no sink
             for (int q = 0; q < g->jnb; q++) b->h_gwork.push_back(make_int2(i, q));
             for (int m0 = 0; m0 < g->nmol; m0 += 4) b->h_mwork.push_back(make_int2(i, m0));
         }

@@ -69,6 +69,9 @@ struct ml_grid {
     long long pool = 0;
     std::vector<int> nlev, kind, nsub, cmask, win, wf, wraw;
     bool two_level = true;  // every molecule has two levels (pool offset 4 m)
+    double *pop_sink = nullptr;  // device address of the caller's page-locked population ring
+    long long pop_ring = 0;
+    bool pop_off = false;        // set while the adjoint sweeps step the grid
 
     std::vector<long long> off;
     std::vector<double> pos, sigma, gamma, decay, deph, H0, mu, rho0;

@@ -188,6 +188,8 @@ struct MolArgs {
     const int *wf;         // per molecule: window length along x, y, z (8 bits each)
     const T *w;            // (M, NW) 1D kernel weights per axis and stagger
     int two_level;         // every molecule has two levels, at pool offset 4 m
+    double *pop_sink;      // populations of the new state, device address of page-locked host memory
+    long long pop_slot;    // row block of this step in the sink: (step mod ring) * nmol * MAXLEV
 };
 
 // ------------------------------------------------------------------ DFT planes

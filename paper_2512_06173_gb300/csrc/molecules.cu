@@ -376,6 +376,8 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         const int e = lane + 32 * q;
         if (e < nn) {
             a.rho[o + e] = r1[q];
+            if (a.pop_sink && e % (n + 1) == 0)  // diagonal element (j, j), j = e / (n + 1)
+                a.pop_sink[a.pop_slot + (long long)m * MAXLEV + e / (n + 1)] = (double)r1[q].re;
 #pragma unroll
             for (int c = 0; c < 3; c++) mu1[c] += r1[q].re * mu[c][q].re + r1[q].im * mu[c][q].im;
             en += r1[q].re * h0[q].re + r1[q].im * h0[q].im;

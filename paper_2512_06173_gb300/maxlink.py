@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         "ml_get_fields": (I, [P, C.c_uint, P, I, P]),
         "ml_set_fields": (I, [P, C.c_uint, P, I, P]),
         "ml_get_molecules": (I, [P, I, P, I, P]),
+        "ml_set_population_sink": (I, [P, P, I64]),
         "ml_flux": (I, [P, I, P, P]),
         "ml_flux_data": (I, [P, I, P, P]),
         "ml_absorbed": (I, [P, P, P]),
@@ -181,6 +182,11 @@ def ml_set_fields(h: int, mask: int, src_ptr: int, on_device: bool, stream: int 
 
 def ml_get_molecules(h: int, what: int, dst_ptr: int, on_device: int, stream: int = 0):
     _check(load().ml_get_molecules(C.c_void_p(h), what, C.c_void_p(dst_ptr), int(on_device), C.c_void_p(stream)))
+
+
+def ml_set_population_sink(h: int, host_ptr: int, ring_steps: int):
+    """host_ptr: page-locked host memory (0 removes the sink)."""
+    _check(load().ml_set_population_sink(C.c_void_p(h), C.c_void_p(host_ptr), int(ring_steps)))
 
 
 def ml_flux(h: int, plane: int, nfreq: int, stream: int = 0) -> np.ndarray:

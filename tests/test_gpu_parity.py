@@ -203,3 +203,36 @@ def test_window_crossing_wall_rejected(ml):
     with pytest.raises(ml.MaxlinkError) as e:
         ml.Grid(prob, 0)
     assert e.value.status == ml.ML_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("two_level", [False, True])
+def test_population_sink(ml, two_level):
+    """The molecule kernel's stores into the page-locked ring equal the populations read
+    back after each step (bit for bit), in the slot of that step; entries past a
+    molecule's levels and slots of other steps are left alone."""
+    import torch
+    prob = (W.superradiant_slab(n=48, nmol=40, slab=8, pml=6) if two_level
+            else W.small_coupled(seed=4, shape=(37, 22, 29)))
+    M, L, ring = prob.molecules.count, ml.ML_MAX_LEVELS, 3
+    g = ml.Grid(prob, 0)
+    try:
+        sink = torch.full((ring * M * L,), -7.0, dtype=torch.float64).pin_memory()
+        ml.ml_set_population_sink(g.h, sink.data_ptr(), ring)
+        nlev = prob.molecules.nlev
+        for s in range(5):
+            g.step(1)
+            g.sync()
+            want = g.molecules(ml.ML_MOL_POP)
+            got = sink.numpy().reshape(ring, M, L)[s % ring]
+            for m in range(M):
+                assert np.array_equal(got[m, :nlev[m]], want[m, :nlev[m]])
+                assert np.all(got[m, nlev[m]:] == -7.0)
+        ml.ml_set_population_sink(g.h, 0, 1)
+        before = sink.clone()
+        g.step(2)
+        g.sync()
+        assert torch.equal(sink, before)
+        with pytest.raises(ml.MaxlinkError):
+            ml.ml_set_population_sink(g.h, sink.data_ptr(), 0)
+    finally:
+        g.close()

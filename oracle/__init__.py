@@ -8,7 +8,8 @@ shares no code with the CUDA library.
 Functions without an independent pin are marked "parity unpinned" in their
 docstring (none at present: every piece is pinned by a test under `tests/`,
 see `tests/test_oracle_*.py`; the discrete adjoint by a dot-product identity and
-central differences in `tests/test_oracle_adjoint.py`).
+central differences in `tests/test_oracle_adjoint.py`; the single-mode cavity of
+`oracle/cavity.py` in `tests/test_oracle_cavity.py`).
 """
 from __future__ import annotations
 

@@ -291,6 +291,47 @@ def measure_bragg(args, stream):
         g.close()
 
 
+def measure_cavity(args, stream):
+    """Single-mode cavity (Sec. II normal-mode solver, single-mode limit): 1,000,000
+    two-level emitters resonant with the mode, in-plane dipoles, collective splitting
+    about 5% of the mode frequency; FP32 molecules, FP64 mode.  Device time of
+    args.cavity_steps steps after 20 warm-up steps.  Roofline: the molecule kernel's
+    algorithmic bytes per molecule-step (rho read + written, H0, mu_x, mu_y, gamma, the
+    energy sum read + written, gamma <mu> written and read back by the dipole sum:
+    204 B) over the step time."""
+    import numpy as np
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    M = args.cavity_molecules
+    mols = workloads.cavity_ensemble(M)
+    eps = 0.05 * 0.25 ** 2 / np.sqrt(2 * 0.25 * M * 0.05 ** 2 / 2)
+    sh = stream.cuda_stream
+    c = maxlink.Cavity(mols, 0.25, eps, 0.5, precision=maxlink.ML_F32, stream=sh)
+    K = args.cavity_steps
+    try:
+        c.step(20)
+        c.mode()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(K)
+        e1.record(stream)
+        stream.synchronize()
+        mode = c.mode()
+        ms = e0.elapsed_time(e1)
+        hbm, peak_kind = peaks()
+        alg = 204.0 * M
+        gbs = alg / (ms / K / 1e3) / 1e9
+        return {"workload": f"single-mode cavity, {M} two-level emitters, eps={eps:.3g}", "molecules": M, "steps": K,
+                "dtype": "f32 molecules, f64 mode", "ms_per_step": ms / K,
+                "molecule_steps_per_s": M * K / ms * 1e3, "launches_per_step": 2,
+                "roofline": {"bound": "hbm", "alg_bytes_per_step": alg, "achieved_gbs": gbs, "peak": hbm,
+                             "peak_kind": peak_kind, "frac": gbs / hbm},
+                "mode_after": [float(x) for x in mode]}
+    finally:
+        c.close()
+
+
 def measure_features(args, stream):
     """Field-pass time per step on the 256^3 bench grid with features removed one at a
     time (tracing events, 200 steps after 20 warm-up steps): where the pass loses time."""
@@ -387,7 +428,7 @@ def run_ours(args, world, rank, local):
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
         fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
-              "features": measure_features}[args.section]
+              "features": measure_features, "cavity": measure_cavity}[args.section]
         out = fn(args, torch.cuda.Stream())
         if rank == 0:
             print(json.dumps({"section": args.section, **out}), flush=True)
@@ -490,6 +531,7 @@ def run_ours(args, world, rank, local):
     adjoint = measure_adjoint(args, stream) if (world == 1 and not args.no_adjoint) else None
     batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
     bragg = measure_bragg(args, stream) if (world == 1 and not args.no_bragg) else None
+    cavity = measure_cavity(args, stream) if (world == 1 and not args.no_cavity) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -518,6 +560,7 @@ def run_ours(args, world, rank, local):
             "adjoint": adjoint,
             "batch": batch,
             "bragg": bragg,
+            "cavity": cavity,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
                                    "field_pass": kms[1] / K, "plane_fold": kms[3] / K},
             "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
@@ -541,13 +584,16 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--traced-steps", type=int, default=1000,
                     help="steps of the traced pass that times each kernel (roofline)")
-    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "features"],
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "features", "cavity"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
     ap.add_argument("--batch-steps", type=int, default=3000)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-bragg", action="store_true", help="skip the Bragg-resonator ensemble")
+    ap.add_argument("--no-cavity", action="store_true", help="skip the single-mode cavity")
+    ap.add_argument("--cavity-steps", type=int, default=2000)
+    ap.add_argument("--cavity-molecules", type=int, default=1000000)
     ap.add_argument("--bragg-steps", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -245,6 +245,52 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
 ml_status ml_set_design_eps(ml_grid *g, const double *eps, int on_device, void *stream);
 ml_status ml_set_couplings(ml_grid *g, const double *gamma, int on_device, void *stream);
 
+/* ---- Single-mode cavity (Sec. II, classical photonic dynamics in normal modes) -----
+ * The field is one cavity mode per polarisation lambda = x, y (Eq. H_F_normalmode in the
+ * single-mode limit, mode function e_lambda / sqrt(V)); molecules couple to it through
+ * their mean dipoles.  Per step of length dt (the grid coupling's reading):
+ *   E~_m = -gamma_m sum_lambda [eps q_lambda + (eps^2 / omega_c^2) d_lambda] e_lambda
+ *          (Eq. E_normalmode, held over the step, built from q^n and d^n),
+ *   rho_m advanced as in ml_step (exact 2x2 or RK4 GKSL),
+ *   d_lambda^{n+1} = sum_m gamma_m <mu_lambda>(rho^{n+1})       (Eq. dklambda_def),
+ *   q, p by velocity Verlet on q'' = -omega_c^2 q - eps d       (Eq. eom_cavmd_a),
+ *   half kicks with d^n and d^{n+1}.
+ * eps = omega_c / sqrt(V eps0) (Eq. varepsilon_cavmd) is given directly.  The molecule
+ * descriptor is that of ml_add_molecules; positions and widths are ignored.  The sums
+ * over molecules run in a fixed order (deterministic), in FP64. */
+typedef struct {
+    double omega_c;   /* mode frequency (> 0) */
+    double coupling;  /* eps of Eq. varepsilon_cavmd */
+    double dt;        /* time step (> 0) */
+    double q0[2];     /* initial mode coordinates, polarisations x and y */
+    double p0[2];     /* initial mode momenta */
+    int precision;    /* ML_F32 or ML_F64: the molecules' arithmetic (mode state is FP64) */
+} ml_cavity_desc;
+
+typedef struct ml_cavity ml_cavity;
+
+/* Create a cavity with `m` (copied; count >= 1).  d^0 is computed from the initial
+ * density matrices in FP64.  Errors: ML_ERR_INVALID_ARG (descriptor, molecule table as
+ * for ml_add_molecules), ML_ERR_OOM, ML_ERR_CUDA. */
+ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *m, ml_cavity **out);
+ml_status ml_cavity_destroy(ml_cavity *c);
+
+/* Enqueue nsteps steps on `stream` (two launches per step: the molecules, then the
+ * dipole sum and the mode update). */
+ml_status ml_cavity_step(ml_cavity *c, int64_t nsteps, void *stream);
+
+/* Mode state after the enqueued steps into host `out`:
+ * q_x, q_y, p_x, p_y, d_x, d_y.  Synchronises `stream`; ML_ERR_NUMERIC if a molecule's
+ * field or dipole rate became non-finite. */
+ml_status ml_cavity_mode(ml_cavity *c, double *out, void *stream);
+
+/* Molecular state `what` (ML_MOL_*, layouts as for ml_get_molecules) into host `dst`;
+ * synchronises `stream`. */
+ml_status ml_cavity_get_molecules(ml_cavity *c, int what, double *dst, void *stream);
+
+/* Steps taken. */
+int64_t ml_cavity_step_count(const ml_cavity *c);
+
 /* ---- Batches of independent grids (many realisations of uneven sizes) ----------
  * A batch advances several grids of the same precision and time step together:
  * each step is one launch per kernel class over every instance's blocks (gather,

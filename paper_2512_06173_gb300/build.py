@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmaxlink.so")
-SOURCES = ["api.cu", "yee.cu", "molecules.cu", "dft.cu", "current.cu", "adjoint.cu", "batch.cu", "static_gather.cu"]
+SOURCES = ["api.cu", "yee.cu", "molecules.cu", "dft.cu", "current.cu", "adjoint.cu", "batch.cu", "static_gather.cu",
+           "cavity.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,311 @@
+// Single-mode cavity solver (Sec. II, "Classical photonic dynamics in normal modes"),
+// in the single-mode limit the paper implements: one mode of frequency w_c per
+// polarisation lambda = x, y with mode function e_lambda / sqrt(V).
+//
+// Per step, two launches on the caller's stream:
+//   1. the molecule kernel in its uniform-field form: every molecule m sees
+//      E~_m = gamma_m Eu (Eq. E_normalmode; Eu is kept on the device), advances rho
+//      exactly as in ml_step, and writes gamma_m <mu> of the new state;
+//   2. cavity_mode_kernel: CAV_NB blocks add those dipoles in a fixed order into one
+//      partial each (FP64); the last block to finish (a ticket counter) adds the
+//      partials in block order, giving d^{n+1} (Eq. dklambda_def), advances q and p by
+//      velocity Verlet on q'' = -w_c^2 q - eps d (Eq. eom_cavmd_a) with half kicks at d^n
+//      and d^{n+1}, and writes the next field Eu = -(eps q + eps^2 / w_c^2 d).
+// Nothing waits on another block: the last block is whichever takes the final ticket.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "grid.cuh"
+
+using namespace ml;
+
+namespace {
+
+constexpr int CAV_NB = 128;   // blocks of the dipole sum
+constexpr int CAV_NT = 256;   // threads per block
+constexpr int MODE_N = 9;     // q_x q_y p_x p_y d_x d_y Eu_x Eu_y Eu_z
+
+template <typename T>
+__global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, int M, double *part, unsigned *ticket,
+                                                             double *mode, double wc, double eps, double dt) {
+    __shared__ double red[3][CAV_NT];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long long m = (long long)blockIdx.x * CAV_NT + tid; m < M; m += (long long)CAV_NB * CAV_NT)
+        for (int c = 0; c < 3; c++) s[c] += (double)gmu[3 * m + c];
+    for (int c = 0; c < 3; c++) red[c][tid] = s[c];
+    __syncthreads();
+    for (int o = CAV_NT / 2; o > 0; o >>= 1) {
+        if (tid < o)
+            for (int c = 0; c < 3; c++) red[c][tid] += red[c][tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        for (int c = 0; c < 3; c++) part[3 * blockIdx.x + c] = red[c][0];
+        __threadfence();  // the partial is visible before the ticket is taken
+        last = atomicAdd(ticket, 1u) == CAV_NB - 1;
+    }
+    __syncthreads();
+    if (!last || tid != 0) return;
+    __threadfence();
+    double d[2] = {0.0, 0.0};
+    for (int b = 0; b < CAV_NB; b++)
+        for (int l = 0; l < 2; l++) d[l] += __ldcg(part + 3 * b + l);
+    for (int l = 0; l < 2; l++) {
+        const double q = mode[l], p = mode[2 + l], d0 = mode[4 + l];
+        const double ph = p + 0.5 * dt * (-wc * wc * q - eps * d0);
+        const double qn = q + dt * ph;
+        const double pn = ph + 0.5 * dt * (-wc * wc * qn - eps * d[l]);
+        mode[l] = qn;
+        mode[2 + l] = pn;
+        mode[4 + l] = d[l];
+        mode[6 + l] = -(eps * qn + eps * eps / (wc * wc) * d[l]);
+    }
+    mode[8] = 0.0;
+    *ticket = 0u;  // ready for the next launch
+}
+
+}  // namespace
+
+struct ml_cavity {
+    int prec = 0;
+    size_t esz = 4;
+    int M = 0;
+    long long pool = 0;
+    double dt = 0.0, wc = 0.0, eps = 0.0;
+    bool two_level = true;
+    long long step = 0;
+    int *d_nlev = nullptr, *d_kind = nullptr, *d_nsub = nullptr, *d_cmask = nullptr, *d_status = nullptr;
+    long long *d_off = nullptr;
+    void *d_gamma = nullptr, *d_decay = nullptr, *d_deph = nullptr, *d_H0 = nullptr, *d_mu = nullptr,
+         *d_rho = nullptr, *d_Et = nullptr, *d_mudot = nullptr, *d_c = nullptr, *d_gmu = nullptr;
+    double *d_energy = nullptr, *d_mode = nullptr, *d_part = nullptr, *d_export = nullptr;
+    unsigned *d_ticket = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+ml_status cav_alloc(ml_cavity *c, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ML_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return ML_OK;
+}
+
+template <typename V>
+ml_status cav_upload(ml_cavity *c, V **dst, const std::vector<V> &v) {
+    ml_status s = cav_alloc(c, (void **)dst, v.size() * sizeof(V));
+    if (s != ML_OK) return s;
+    if (!v.empty()) CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return ML_OK;
+}
+
+// doubles, stored in the molecules' precision
+ml_status cav_upload_reals(ml_cavity *c, void **dst, const std::vector<double> &v) {
+    if (c->prec) return cav_upload(c, (double **)dst, v);
+    std::vector<float> f(v.begin(), v.end());
+    return cav_upload(c, (float **)dst, f);
+}
+
+template <typename T>
+void fill_cavity_args(ml_cavity *c, MolArgs<T> &m) {
+    m = MolArgs<T>{};
+    m.nmol = c->M;
+    m.dt = (T)c->dt;
+    m.nlev = c->d_nlev; m.off = c->d_off; m.kind = c->d_kind; m.nsub = c->d_nsub; m.cmask = c->d_cmask;
+    m.gamma = (const T *)c->d_gamma; m.decay = (const T *)c->d_decay; m.dephase = (const T *)c->d_deph;
+    m.H0 = (const cx<T> *)c->d_H0; m.mu = (const cx<T> *)c->d_mu; m.pool = c->pool;
+    m.rho = (cx<T> *)c->d_rho;
+    m.Et = (T *)c->d_Et; m.mudot = (T *)c->d_mudot; m.c = (T *)c->d_c;
+    m.energy = c->d_energy; m.status = c->d_status;
+    m.two_level = c->two_level ? 1 : 0;
+    m.Eu = c->d_mode + 6;
+    m.gmu = (T *)c->d_gmu;
+}
+
+template <typename T>
+ml_status cavity_steps(ml_cavity *c, long long nsteps, cudaStream_t s) {
+    MolArgs<T> m;
+    fill_cavity_args<T>(c, m);
+    for (long long it = 0; it < nsteps; it++) {
+        CK(launch_molecules_uniform<T>(m, s));
+        cavity_mode_kernel<T><<<CAV_NB, CAV_NT, 0, s>>>((const T *)c->d_gmu, c->M, c->d_part, c->d_ticket, c->d_mode,
+                                                         c->wc, c->eps, c->dt);
+        CK(cudaGetLastError());
+        c->step++;
+    }
+    return ML_OK;
+}
+
+}  // namespace
+
+ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, ml_cavity **out) {
+    if (!d || !md || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(d->omega_c > 0.0) || !std::isfinite(d->omega_c)) return fail(ML_ERR_INVALID_ARG, "omega_c must be > 0");
+    if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(ML_ERR_INVALID_ARG, "dt must be > 0");
+    if (!std::isfinite(d->coupling)) return fail(ML_ERR_INVALID_ARG, "non-finite coupling");
+    for (int l = 0; l < 2; l++)
+        if (!std::isfinite(d->q0[l]) || !std::isfinite(d->p0[l])) return fail(ML_ERR_INVALID_ARG, "non-finite mode state");
+    if (d->precision != ML_F32 && d->precision != ML_F64) return fail(ML_ERR_INVALID_ARG, "precision must be ML_F32 or ML_F64");
+    if (md->count < 1) return fail(ML_ERR_INVALID_ARG, "a cavity needs at least one molecule");
+    if (!md->nlev || !md->off || !md->gamma || !md->decay || !md->dephase || !md->kind || !md->nsub || !md->H0 ||
+        !md->mu || !md->rho)
+        return fail(ML_ERR_INVALID_ARG, "null molecule array");
+    const int M = md->count;
+    std::vector<int> nlev(M), kind(M), nsub(M), cmask(M);
+    std::vector<long long> off(M);
+    std::vector<double> gamma(M), decay(M), deph(M), H0, rho, mu;
+    long long pool = 0;
+    for (int m = 0; m < M; m++) {
+        const int n = md->nlev[m];
+        if (n < 2 || n > ML_MAX_LEVELS) return fail(ML_ERR_INVALID_ARG, "nlev must be 2..8");
+        if (md->off[m] < 0 || md->off[m] + (long long)n * n > md->pool) return fail(ML_ERR_INVALID_ARG, "pool offset out of range");
+        if (md->kind[m] != 0 && md->kind[m] != 1) return fail(ML_ERR_INVALID_ARG, "kind must be 0 or 1");
+        if (md->kind[m] == 0 && (n != 2 || md->decay[m] != 0.0 || md->dephase[m] != 0.0))
+            return fail(ML_ERR_INVALID_ARG, "kind 0 needs two levels and no Lindblad terms");
+        if (md->nsub[m] < 1) return fail(ML_ERR_INVALID_ARG, "nsub must be >= 1");
+        if (md->decay[m] < 0.0 || md->dephase[m] < 0.0) return fail(ML_ERR_INVALID_ARG, "negative rate");
+        if (!std::isfinite(md->gamma[m])) return fail(ML_ERR_INVALID_ARG, "non-finite gamma");
+        nlev[m] = n;
+        kind[m] = md->kind[m];
+        nsub[m] = md->nsub[m];
+        gamma[m] = md->gamma[m];
+        decay[m] = md->decay[m];
+        deph[m] = md->dephase[m];
+        off[m] = pool;
+        pool += (long long)n * n;
+    }
+    H0.resize(2 * pool);
+    rho.resize(2 * pool);
+    mu.assign(2 * 3 * pool, 0.0);
+    double d0[2] = {0.0, 0.0};
+    for (int m = 0; m < M; m++) {
+        const int nn = nlev[m] * nlev[m];
+        int cm = 0;
+        for (int e = 0; e < nn; e++) {
+            const long long src = md->off[m] + e, dst = off[m] + e;
+            H0[2 * dst] = md->H0[2 * src];
+            H0[2 * dst + 1] = md->H0[2 * src + 1];
+            rho[2 * dst] = md->rho[2 * src];
+            rho[2 * dst + 1] = md->rho[2 * src + 1];
+            for (int c = 0; c < 3; c++) {
+                const double re = md->mu[2 * (c * md->pool + src)], im = md->mu[2 * (c * md->pool + src) + 1];
+                mu[2 * (c * pool + dst)] = re;
+                mu[2 * (c * pool + dst) + 1] = im;
+                if (re != 0.0 || im != 0.0) cm |= 1 << c;
+                // <mu_c> = Re Tr(rho mu_c) = sum_e Re(rho_e conj(mu_c,e)) for Hermitian mu_c
+                if (c < 2) d0[c] += gamma[m] * (rho[2 * dst] * re + rho[2 * dst + 1] * im);
+            }
+        }
+        cmask[m] = cm;
+    }
+    ml_cavity *c = new ml_cavity();
+    c->prec = d->precision;
+    c->esz = c->prec ? 8 : 4;
+    c->M = M;
+    c->pool = pool;
+    c->dt = d->dt;
+    c->wc = d->omega_c;
+    c->eps = d->coupling;
+    c->two_level = true;
+    for (int m = 0; m < M; m++) c->two_level = c->two_level && nlev[m] == 2;
+    auto bail = [&](ml_status s) {
+        ml_cavity_destroy(c);
+        return s;
+    };
+    ml_status st;
+#define CAV(x)                          \
+    do {                                \
+        st = (x);                       \
+        if (st != ML_OK) return bail(st); \
+    } while (0)
+    CAV(cav_upload(c, &c->d_nlev, nlev));
+    CAV(cav_upload(c, &c->d_kind, kind));
+    CAV(cav_upload(c, &c->d_nsub, nsub));
+    CAV(cav_upload(c, &c->d_cmask, cmask));
+    CAV(cav_upload(c, &c->d_off, off));
+    CAV(cav_upload_reals(c, &c->d_gamma, gamma));
+    CAV(cav_upload_reals(c, &c->d_decay, decay));
+    CAV(cav_upload_reals(c, &c->d_deph, deph));
+    CAV(cav_upload_reals(c, &c->d_H0, H0));
+    CAV(cav_upload_reals(c, &c->d_mu, mu));
+    CAV(cav_upload_reals(c, &c->d_rho, rho));
+    CAV(cav_alloc(c, &c->d_Et, 3 * (size_t)M * c->esz));
+    CAV(cav_alloc(c, &c->d_mudot, 3 * (size_t)M * c->esz));
+    CAV(cav_alloc(c, &c->d_c, 3 * (size_t)M * c->esz));
+    CAV(cav_alloc(c, &c->d_gmu, 3 * (size_t)M * c->esz));
+    CAV(cav_upload(c, &c->d_energy, std::vector<double>(M, 0.0)));
+    CAV(cav_upload(c, &c->d_status, std::vector<int>(1, 0)));
+    CAV(cav_upload(c, &c->d_ticket, std::vector<unsigned>(1, 0u)));
+    CAV(cav_alloc(c, (void **)&c->d_part, 3 * CAV_NB * sizeof(double)));
+    CAV(cav_alloc(c, (void **)&c->d_export,
+                  std::max<size_t>((size_t)std::max<long long>(2 * pool, (long long)M * MAXLEV), 1) * sizeof(double)));
+    std::vector<double> mode(MODE_N, 0.0);
+    for (int l = 0; l < 2; l++) {
+        mode[l] = d->q0[l];
+        mode[2 + l] = d->p0[l];
+        mode[4 + l] = d0[l];
+        mode[6 + l] = -(c->eps * d->q0[l] + c->eps * c->eps / (c->wc * c->wc) * d0[l]);
+    }
+    CAV(cav_upload(c, &c->d_mode, mode));
+#undef CAV
+    *out = c;
+    return ML_OK;
+}
+
+ml_status ml_cavity_destroy(ml_cavity *c) {
+    if (!c) return ML_OK;
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+    return ML_OK;
+}
+
+ml_status ml_cavity_step(ml_cavity *c, int64_t nsteps, void *stream) {
+    if (!c) return fail(ML_ERR_INVALID_ARG, "null cavity");
+    if (nsteps < 0) return fail(ML_ERR_INVALID_ARG, "negative step count");
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->prec ? cavity_steps<double>(c, nsteps, s) : cavity_steps<float>(c, nsteps, s);
+}
+
+ml_status ml_cavity_mode(ml_cavity *c, double *out, void *stream) {
+    if (!c || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double buf[MODE_N];
+    int status = 0;
+    CK(cudaMemcpyAsync(buf, c->d_mode, sizeof(buf), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < 6; q++) out[q] = buf[q];
+    if (status) return fail(ML_ERR_NUMERIC, "a molecule's field or dipole rate became non-finite");
+    return ML_OK;
+}
+
+ml_status ml_cavity_get_molecules(ml_cavity *c, int what, double *dst, void *stream) {
+    if (!c || !dst) return fail(ML_ERR_INVALID_ARG, "null argument");
+    if (what < ML_MOL_RHO || what > ML_MOL_POP) return fail(ML_ERR_INVALID_ARG, "unknown molecular quantity");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = what == ML_MOL_RHO ? 2 * (size_t)c->pool
+                                        : (what == ML_MOL_ENERGY ? (size_t)c->M
+                                                                 : (what == ML_MOL_POP ? (size_t)c->M * MAXLEV : 3 * (size_t)c->M));
+    cudaError_t e = c->prec ? launch_mol_export<double>(what, c->M, c->d_nlev, c->d_off, (const cx<double> *)c->d_rho,
+                                                        (const double *)c->d_Et, (const double *)c->d_mudot,
+                                                        c->d_energy, c->pool, c->d_export, s)
+                            : launch_mol_export<float>(what, c->M, c->d_nlev, c->d_off, (const cx<float> *)c->d_rho,
+                                                       (const float *)c->d_Et, (const float *)c->d_mudot,
+                                                       c->d_energy, c->pool, c->d_export, s);
+    CK(e);
+    CK(cudaMemcpyAsync(dst, c->d_export, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+int64_t ml_cavity_step_count(const ml_cavity *c) { return c ? c->step : -1; }

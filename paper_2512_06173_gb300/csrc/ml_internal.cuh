@@ -190,6 +190,8 @@ struct MolArgs {
     int two_level;         // every molecule has two levels, at pool offset 4 m
     double *pop_sink;      // populations of the new state, device address of page-locked host memory
     long long pop_slot;    // row block of this step in the sink: (step mod ring) * nmol * MAXLEV
+    const double *Eu;      // uniform-field source: the field before gamma_m (3 values)
+    T *gmu;                // uniform-field source: gamma_m <mu> of the new state (M, 3)
 };
 
 // ------------------------------------------------------------------ DFT planes
@@ -273,6 +275,7 @@ cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s,
                                              bool pdl = false);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
+template <typename T> cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,

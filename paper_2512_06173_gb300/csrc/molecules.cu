@@ -187,9 +187,12 @@ __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, c
     return out;
 }
 
-// FUSED: the warp gathers its own regularised field from E (window_gather);
-// otherwise it adds the gather kernel's partials.
-template <typename T, bool FUSED, bool N2>
+// SRC: where the regularised field comes from.  SRC_PARTS: the gather kernel's
+// partials; SRC_WINDOW: the warp gathers its own window from E (window_gather);
+// SRC_UNIFORM: one field for every molecule (a.Eu, times gamma_m), as in the
+// single-mode cavity, and the warp also writes gamma_m <mu> of the new state.
+constexpr int SRC_PARTS = 0, SRC_WINDOW = 1, SRC_UNIFORM = 2;
+template <typename T, int SRC, bool N2>
 __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0) {
     __shared__ MolShared<T> sh;
     const int lane = threadIdx.x & 31;
@@ -208,11 +211,11 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     const int kind = a.kind[m];
     const T gam = a.gamma[m];
     const double e_old = lane == 0 ? a.energy[m] : 0.0;
-    // the kernel window and its weights (FUSED)
+    // the kernel window and its weights (SRC_WINDOW)
     static_assert(NW == 96, "three weights per lane");
     int wfm = 0, x0 = 0, y0 = 0, z0 = 0;
     T wreg[3];
-    if (FUSED) {
+    if (SRC == SRC_WINDOW) {
 #pragma unroll
         for (int q = 0; q < 3; q++) wreg[q] = a.w[(long long)m * NW + lane + 32 * q];
         wfm = a.wf[m];
@@ -232,7 +235,7 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         for (int c = 0; c < 3; c++)
             mu[c][q] = (in && (N2 || ((cm >> c) & 1))) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
     }
-    if (FUSED) {
+    if (SRC == SRC_WINDOW) {
 #pragma unroll
         for (int q = 0; q < 3; q++) sh.W[wl][lane + 32 * q] = wreg[q];
     }
@@ -247,7 +250,10 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 
     // ---- 1. regularised field
     T Et[3];
-    if (FUSED) {
+    if (SRC == SRC_UNIFORM) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) Et[c] = gam * (T)a.Eu[c];
+    } else if (SRC == SRC_WINDOW) {
         const T *sw = sh.W[wl];
         T g[3];
         bool done = false;
@@ -393,6 +399,7 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
             a.Et[3 * m + c] = Et[c];
             a.mudot[3 * m + c] = md;
             a.c[3 * m + c] = gam * md;
+            if (SRC == SRC_UNIFORM) a.gmu[3 * m + c] = gam * mu1[c];
             if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
         }
         a.energy[m] = e_old + (double)en;
@@ -407,14 +414,164 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 // N2: every molecule has two levels (see molecule_body).
 template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1) molecule_kernel(const MolArgs<T> a) {
-    molecule_body<T, true, N2>(a, (int)blockIdx.x * MOL_WARPS);
+    molecule_body<T, SRC_WINDOW, N2>(a, (int)blockIdx.x * MOL_WARPS);
+}
+
+// Uniform-field form for two-level molecules: one thread per molecule, so that a warp
+// streams 32 molecules' 2x2 matrices with 16-byte loads instead of one molecule's four
+// elements.  The same step as molecule_body: E~ = gamma Eu held over dt; the exact
+// 2x2 exponential (kind 0) or nsub classic RK4 substeps of the GKSL equation (kind 1);
+// mudot, the current amplitude, the energy sum and gamma <mu> of the new state.
+template <typename T>
+__device__ __forceinline__ void ld4(const cx<T> *p, cx<T> (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p)), b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = {a.x, a.y}; v[1] = {a.z, a.w}; v[2] = {b.x, b.y}; v[3] = {b.z, b.w};
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + e);
+            v[e] = {a.x, a.y};
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(cx<T> *p, const cx<T> (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(v[2].re, v[2].im, v[3].re, v[3].im);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) reinterpret_cast<double2 *>(p)[e] = make_double2(v[e].re, v[e].im);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) molecule_uniform_thread_kernel(const MolArgs<T> a) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.nmol) return;
+    const long long o = 4ll * m;
+    const int cm = a.cmask[m];
+    const int kind = a.kind[m];
+    const T gam = a.gamma[m];
+    const double e_old = a.energy[m];
+    cx<T> r[4], h0[4], mu[3][4];
+    ld4(a.rho + o, r);
+    ld4(a.H0 + o, h0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if ((cm >> c) & 1) ld4(a.mu + c * a.pool + o, mu[c]);
+        else
+            for (int e = 0; e < 4; e++) mu[c][e] = {T(0), T(0)};
+    }
+    T Et[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) Et[c] = gam * (T)a.Eu[c];
+    // H = H0 - Et . mu and <mu> before the step (Re Tr(rho A) = sum Re(rho_e conj(A_e)))
+    cx<T> H[4];
+    T mu0[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        H[e] = h0[e];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            H[e].re -= Et[c] * mu[c][e].re;
+            H[e].im -= Et[c] * mu[c][e].im;
+            mu0[c] += r[e].re * mu[c][e].re + r[e].im * mu[c][e].im;
+        }
+    }
+    cx<T> r1[4];
+    if (kind == 0) {
+        const T dt = a.dt;
+        const T z = T(0.5) * (H[0].re - H[3].re);
+        const cx<T> b = H[1];
+        const T W = sqrt(z * z + b.re * b.re + b.im * b.im);
+        const T cw = cos(W * dt);
+        const T sw = W > T(0) ? sin(W * dt) / W : dt;
+        cx<T> U[4];
+        U[0] = {cw, -sw * z};
+        U[1] = {sw * b.im, -sw * b.re};
+        U[2] = {-sw * b.im, -sw * b.re};
+        U[3] = {cw, sw * z};
+        cx<T> TT[4];
+        for (int p = 0; p < 2; p++)
+            for (int q = 0; q < 2; q++)
+                TT[p * 2 + q] = cadd(cmul(U[p * 2 + 0], r[0 * 2 + q]), cmul(U[p * 2 + 1], r[1 * 2 + q]));
+        for (int p = 0; p < 2; p++)
+            for (int q = 0; q < 2; q++)
+                r1[p * 2 + q] = cadd(cmul(TT[p * 2 + 0], cconj(U[q * 2 + 0])), cmul(TT[p * 2 + 1], cconj(U[q * 2 + 1])));
+    } else {
+        const int ns = a.nsub[m];
+        const T h = a.dt / T(ns);
+        const T decay = a.decay[m], deph = a.dephase[m];
+#pragma unroll
+        for (int e = 0; e < 4; e++) r1[e] = r[e];
+        for (int sstep = 0; sstep < ns; sstep++) {
+            cx<T> base[4], S[4], acc[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                base[e] = r1[e];
+                S[e] = r1[e];
+                acc[e] = {T(0), T(0)};
+            }
+#pragma unroll
+            for (int st = 0; st < 4; st++) {
+                const T wgt = (st == 0 || st == 3) ? T(1) : T(2);
+                const T cn = (st < 2) ? T(0.5) : T(1);
+                cx<T> f[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    f[e] = rhs_elem(2, e >> 1, e & 1, S, H, decay, deph);
+                    acc[e].re += wgt * f[e].re;
+                    acc[e].im += wgt * f[e].im;
+                }
+                if (st < 3)
+#pragma unroll
+                    for (int e = 0; e < 4; e++) S[e] = {base[e].re + cn * h * f[e].re, base[e].im + cn * h * f[e].im};
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                r1[e].re = base[e].re + h / T(6) * acc[e].re;
+                r1[e].im = base[e].im + h / T(6) * acc[e].im;
+            }
+        }
+    }
+    st4(a.rho + o, r1);
+    T mu1[3] = {T(0), T(0), T(0)};
+    T en = T(0);
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) mu1[c] += r1[e].re * mu[c][e].re + r1[e].im * mu[c][e].im;
+        en += r1[e].re * h0[e].re + r1[e].im * h0[e].im;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const T md = (mu1[c] - mu0[c]) / a.dt;
+        a.Et[3 * m + c] = Et[c];
+        a.mudot[3 * m + c] = md;
+        a.c[3 * m + c] = gam * md;
+        a.gmu[3 * m + c] = gam * mu1[c];
+        if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
+    }
+    a.energy[m] = e_old + (double)en;
+    if (bad) atomicCAS(a.status, 0, 6);
+}
+
+// Uniform-field form (single-mode cavity): no window, no field read.
+template <typename T, bool N2>
+__global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1)
+    molecule_uniform_kernel(const MolArgs<T> a) {
+    molecule_body<T, SRC_UNIFORM, N2>(a, (int)blockIdx.x * MOL_WARPS);
 }
 
 // Batched form: one block per (instance, first molecule) work item.
 template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
     const int2 wk = b.work[blockIdx.x];
-    molecule_body<T, true, N2>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
+    molecule_body<T, SRC_WINDOW, N2>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
 }
 
 template <typename T>
@@ -424,6 +581,18 @@ cudaError_t launch_molecules_batch(const MolBatch<T> &b, int nwork, cudaStream_t
         molecule_batch_kernel<T, true><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
     else
         molecule_batch_kernel<T, false><<<nwork, MOL_WARPS * 32, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s) {
+    if (a.nmol == 0) return cudaSuccess;
+    if (a.two_level) {
+        molecule_uniform_thread_kernel<T><<<(a.nmol + 255) / 256, 256, 0, s>>>(a);
+    } else {
+        const int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
+        molecule_uniform_kernel<T, false><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -527,7 +696,8 @@ cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long lo
 }
 
 #define ML_INST(T)                                                                                              \
-    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t, bool);                             \
+    template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t, bool);                           \
+    template cudaError_t launch_molecules_uniform<T>(const MolArgs<T> &, cudaStream_t);                             \
     template cudaError_t launch_molecules_batch<T>(const MolBatch<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \
                                            const int *, const int *, const int *, T *, cudaStream_t);           \

@@ -54,6 +54,11 @@ class ml_molecule_desc(C.Structure):
                 ("rho", C.c_void_p), ("pool", C.c_int64)]
 
 
+class ml_cavity_desc(C.Structure):
+    _fields_ = [("omega_c", C.c_double), ("coupling", C.c_double), ("dt", C.c_double),
+                ("q0", C.c_double * 2), ("p0", C.c_double * 2), ("precision", C.c_int)]
+
+
 _lib = None
 
 
@@ -110,6 +115,12 @@ def load(build_if_missing: bool = True):
         "ml_adjoint_run": (I, [P, I64, I, I, I, P, P, P, I, P]),
         "ml_set_design_eps": (I, [P, P, I, P]),
         "ml_set_couplings": (I, [P, P, I, P]),
+        "ml_cavity_create": (I, [C.POINTER(ml_cavity_desc), C.POINTER(ml_molecule_desc), C.POINTER(P)]),
+        "ml_cavity_destroy": (I, [P]),
+        "ml_cavity_step": (I, [P, I64, P]),
+        "ml_cavity_mode": (I, [P, P, P]),
+        "ml_cavity_get_molecules": (I, [P, I, P, P]),
+        "ml_cavity_step_count": (I64, [P]),
         "ml_batch_create": (I, [P, I, C.POINTER(P)]),
         "ml_batch_step": (I, [P, I64, P]),
         "ml_batch_set_tuning": (I, [P, I, I]),
@@ -268,6 +279,34 @@ def ml_set_couplings(h: int, gamma_ptr: int, on_device: bool = False, stream: in
     _check(load().ml_set_couplings(C.c_void_p(h), C.c_void_p(gamma_ptr), 1 if on_device else 0, C.c_void_p(stream)))
 
 
+def ml_cavity_create(desc: ml_cavity_desc, mdesc: ml_molecule_desc) -> int:
+    out = C.c_void_p()
+    _check(load().ml_cavity_create(C.byref(desc), C.byref(mdesc), C.byref(out)))
+    return out.value
+
+
+def ml_cavity_destroy(c: int):
+    _check(load().ml_cavity_destroy(C.c_void_p(c)))
+
+
+def ml_cavity_step(c: int, nsteps: int, stream: int = 0):
+    _check(load().ml_cavity_step(C.c_void_p(c), int(nsteps), C.c_void_p(stream)))
+
+
+def ml_cavity_mode(c: int, stream: int = 0) -> np.ndarray:
+    out = np.zeros(6)
+    _check(load().ml_cavity_mode(C.c_void_p(c), out.ctypes.data_as(C.c_void_p), C.c_void_p(stream)))
+    return out
+
+
+def ml_cavity_get_molecules(c: int, what: int, dst_ptr: int, stream: int = 0):
+    _check(load().ml_cavity_get_molecules(C.c_void_p(c), int(what), C.c_void_p(dst_ptr), C.c_void_p(stream)))
+
+
+def ml_cavity_step_count(c: int) -> int:
+    return int(load().ml_cavity_step_count(C.c_void_p(c)))
+
+
 def ml_batch_create(handles) -> int:
     arr = (C.c_void_p * len(handles))(*handles)
     out = C.c_void_p()
@@ -372,6 +411,65 @@ def molecule_desc(mol):
     d.rho = arr(np.ascontiguousarray(mol.rho0, np.complex128).view(np.float64), np.float64)
     d.pool = int(mol.H0.shape[0])
     return d, keep
+
+
+class Cavity:
+    """Single-mode cavity (polarisations x, y) coupled to a `workloads.Molecules` table."""
+
+    def __init__(self, molecules, omega_c: float, coupling: float, dt: float, q0=(0.0, 0.0), p0=(0.0, 0.0),
+                 precision: int = ML_F32, stream: int = 0):
+        d = ml_cavity_desc()
+        d.omega_c, d.coupling, d.dt, d.precision = float(omega_c), float(coupling), float(dt), int(precision)
+        for l in range(2):
+            d.q0[l] = float(q0[l])
+            d.p0[l] = float(p0[l])
+        md, self._keep = molecule_desc(molecules)
+        self.mol = molecules
+        self.stream = stream
+        self.h = ml_cavity_create(d, md)
+
+    def step(self, n: int = 1):
+        ml_cavity_step(self.h, n, self.stream)
+
+    def mode(self) -> np.ndarray:
+        """q_x, q_y, p_x, p_y, d_x, d_y."""
+        return ml_cavity_mode(self.h, self.stream)
+
+    def molecules(self, what: int) -> np.ndarray:
+        M = self.mol.count
+        if what == ML_MOL_RHO:
+            out = np.zeros(2 * int((self.mol.nlev.astype(np.int64) ** 2).sum()))
+            ml_cavity_get_molecules(self.h, what, _ptr(out), self.stream)
+            return out.view(np.complex128)
+        n = {ML_MOL_EFIELD: 3 * M, ML_MOL_MUDOT: 3 * M, ML_MOL_ENERGY: M, ML_MOL_POP: ML_MAX_LEVELS * M}[what]
+        out = np.zeros(n)
+        ml_cavity_get_molecules(self.h, what, _ptr(out), self.stream)
+        if what in (ML_MOL_EFIELD, ML_MOL_MUDOT):
+            return out.reshape(M, 3)
+        if what == ML_MOL_POP:
+            return out.reshape(M, ML_MAX_LEVELS)
+        return out
+
+    def rho(self, m: int) -> np.ndarray:
+        n = int(self.mol.nlev[m])
+        pool = self.molecules(ML_MOL_RHO)
+        off = int(np.concatenate([[0], np.cumsum(self.mol.nlev.astype(np.int64) ** 2)])[m])
+        return pool[off:off + n * n].reshape(n, n)
+
+    @property
+    def nstep(self) -> int:
+        return ml_cavity_step_count(self.h)
+
+    def close(self):
+        if self.h:
+            ml_cavity_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -427,3 +427,25 @@ def random_fields(prob: Problem, seed: int, scale: float = 1.0):
     """Seeded random initial E and H (6 arrays of shape (nz, ny, nx), float64)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return [scale * rng.standard_normal((prob.nz, prob.ny, prob.nx)) for _ in range(6)]
+
+
+def cavity_ensemble(M: int = 1_000_000, omega0: float = 0.25, mu12: float = 0.05, seed: int = 6) -> Molecules:
+    """Single-mode cavity workload (stand-in for the normal-mode examples of Sec. II):
+    `M` two-level emitters (H0 = diag(0, omega0), exact propagator), transition dipole
+    mu12 sigma_x in the cavity plane at a seeded uniform angle, gamma = 1, ground state
+    with a seeded 1e-3 coherence.  Built with array operations (pools of 4 elements per
+    emitter at offset 4 m)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    th = rng.uniform(0.0, 2 * np.pi, M)
+    ph = rng.uniform(0.0, 2 * np.pi, M)
+    cg, ce = np.sqrt(1.0 - 1e-6), 1e-3 * np.exp(1j * ph)
+    H0 = np.zeros((M, 4), np.complex128)
+    H0[:, 3] = omega0
+    mu = np.zeros((3, M, 4), np.complex128)
+    mu[0, :, 1] = mu[0, :, 2] = mu12 * np.cos(th)
+    mu[1, :, 1] = mu[1, :, 2] = mu12 * np.sin(th)
+    rho = np.stack([np.full(M, cg * cg), cg * np.conj(ce), ce * cg, np.abs(ce) ** 2], axis=1).astype(np.complex128)
+    return Molecules(np.full(M, 2, np.int32), 4 * np.arange(M, dtype=np.int64), np.zeros((M, 3)),
+                     np.ones(M), np.ones(M), np.zeros(M), np.zeros(M), np.zeros(M, np.int32),
+                     np.ones(M, np.int32), H0.ravel(), mu.reshape(3, -1), rho.ravel())
+

@@ -276,7 +276,8 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *m, m
 ml_status ml_cavity_destroy(ml_cavity *c);
 
 /* Enqueue nsteps steps on `stream` (two launches per step: the molecules, then the
- * dipole sum and the mode update). */
+ * dipole sum and the mode update; runs of 64 steps replay a CUDA graph captured on
+ * first use). */
 ml_status ml_cavity_step(ml_cavity *c, int64_t nsteps, void *stream);
 
 /* Mode state after the enqueued steps into host `out`:

@@ -8,10 +8,11 @@
 //      exactly as in ml_step, and writes gamma_m <mu> of the new state;
 //   2. cavity_mode_kernel: CAV_NB blocks add those dipoles in a fixed order into one
 //      partial each (FP64); the last block to finish (a ticket counter) adds the
-//      partials in block order, giving d^{n+1} (Eq. dklambda_def), advances q and p by
+//      partials by a fixed tree, giving d^{n+1} (Eq. dklambda_def), advances q and p by
 //      velocity Verlet on q'' = -w_c^2 q - eps d (Eq. eom_cavmd_a) with half kicks at d^n
 //      and d^{n+1}, and writes the next field Eu = -(eps q + eps^2 / w_c^2 d).
 // Nothing waits on another block: the last block is whichever takes the final ticket.
+// Runs of 64 steps are captured once into a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -26,9 +27,11 @@ namespace {
 constexpr int CAV_NB = 128;   // blocks of the dipole sum
 constexpr int CAV_NT = 256;   // threads per block
 constexpr int MODE_N = 9;     // q_x q_y p_x p_y d_x d_y Eu_x Eu_y Eu_z
+constexpr int CAV_SEQ = 64;   // steps per captured sequence
+static_assert(CAV_NB <= CAV_NT, "the last block loads one partial per thread");
 
 template <typename T>
-__global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, int M, double *part, unsigned *ticket,
+__global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, long long M, double *part, unsigned *ticket,
                                                              double *mode, double wc, double eps, double dt) {
     __shared__ double red[3][CAV_NT];
     __shared__ bool last;
@@ -49,11 +52,18 @@ __global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, int M
         last = atomicAdd(ticket, 1u) == CAV_NB - 1;
     }
     __syncthreads();
-    if (!last || tid != 0) return;
+    if (!last) return;
+    // the last block: the CAV_NB partials by the same fixed tree
     __threadfence();
-    double d[2] = {0.0, 0.0};
-    for (int b = 0; b < CAV_NB; b++)
-        for (int l = 0; l < 2; l++) d[l] += __ldcg(part + 3 * b + l);
+    for (int l = 0; l < 2; l++) red[l][tid] = tid < CAV_NB ? __ldcg(part + 3 * tid + l) : 0.0;
+    __syncthreads();
+    for (int o = CAV_NT / 2; o > 0; o >>= 1) {
+        if (tid < o)
+            for (int l = 0; l < 2; l++) red[l][tid] += red[l][tid + o];
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    const double d[2] = {red[0][0], red[1][0]};
     for (int l = 0; l < 2; l++) {
         const double q = mode[l], p = mode[2 + l], d0 = mode[4 + l];
         const double ph = p + 0.5 * dt * (-wc * wc * q - eps * d0);
@@ -83,8 +93,13 @@ struct ml_cavity {
     void *d_gamma = nullptr, *d_decay = nullptr, *d_deph = nullptr, *d_H0 = nullptr, *d_mu = nullptr,
          *d_rho = nullptr, *d_Et = nullptr, *d_mudot = nullptr, *d_c = nullptr, *d_gmu = nullptr;
     double *d_energy = nullptr, *d_mode = nullptr, *d_part = nullptr, *d_export = nullptr;
+    double *d_bpart = nullptr;  // two-level molecules: per-block dipole sums of the molecule kernel
     unsigned *d_ticket = nullptr;
     std::vector<void *> allocs;
+    // CAV_SEQ steps captured once into a graph (the arguments never change) and replayed
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -129,19 +144,53 @@ void fill_cavity_args(ml_cavity *c, MolArgs<T> &m) {
     m.two_level = c->two_level ? 1 : 0;
     m.Eu = c->d_mode + 6;
     m.gmu = (T *)c->d_gmu;
+    m.dpart = c->d_bpart;
+}
+
+template <typename T>
+ml_status enqueue_steps(ml_cavity *c, long long nsteps, cudaStream_t s) {
+    MolArgs<T> m;
+    fill_cavity_args<T>(c, m);
+    const long long nb = (c->M + MU_THREADS_HOST - 1) / MU_THREADS_HOST;
+    for (long long it = 0; it < nsteps; it++) {
+        CK(launch_molecules_uniform<T>(m, s));
+        // two-level molecules leave per-block sums; others gamma <mu> per molecule
+        if (c->two_level)
+            cavity_mode_kernel<double><<<CAV_NB, CAV_NT, 0, s>>>(c->d_bpart, nb, c->d_part, c->d_ticket, c->d_mode,
+                                                                  c->wc, c->eps, c->dt);
+        else
+            cavity_mode_kernel<T><<<CAV_NB, CAV_NT, 0, s>>>((const T *)c->d_gmu, c->M, c->d_part, c->d_ticket,
+                                                             c->d_mode, c->wc, c->eps, c->dt);
+        CK(cudaGetLastError());
+    }
+    return ML_OK;
 }
 
 template <typename T>
 ml_status cavity_steps(ml_cavity *c, long long nsteps, cudaStream_t s) {
-    MolArgs<T> m;
-    fill_cavity_args<T>(c, m);
-    for (long long it = 0; it < nsteps; it++) {
-        CK(launch_molecules_uniform<T>(m, s));
-        cavity_mode_kernel<T><<<CAV_NB, CAV_NT, 0, s>>>((const T *)c->d_gmu, c->M, c->d_part, c->d_ticket, c->d_mode,
-                                                         c->wc, c->eps, c->dt);
-        CK(cudaGetLastError());
-        c->step++;
+    const long long reps = nsteps / CAV_SEQ;
+    if (reps > 0 && !c->exec) {
+        if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        const ml_status e = enqueue_steps<T>(c, CAV_SEQ, c->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c->cap, &graph);
+        if (e != ML_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return e;
+        }
+        CK(ce);
+        c->graph = graph;
+        CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
     }
+    for (long long r = 0; r < reps; r++) {
+        CK(cudaGraphLaunch(c->exec, s));
+        c->step += CAV_SEQ;
+    }
+    const long long rest = nsteps - reps * CAV_SEQ;
+    ml_status st = enqueue_steps<T>(c, rest, s);
+    if (st != ML_OK) return st;
+    c->step += rest;
     return ML_OK;
 }
 
@@ -247,6 +296,7 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, 
     CAV(cav_upload(c, &c->d_status, std::vector<int>(1, 0)));
     CAV(cav_upload(c, &c->d_ticket, std::vector<unsigned>(1, 0u)));
     CAV(cav_alloc(c, (void **)&c->d_part, 3 * CAV_NB * sizeof(double)));
+    CAV(cav_alloc(c, (void **)&c->d_bpart, 3 * (size_t)((M + MU_THREADS_HOST - 1) / MU_THREADS_HOST) * sizeof(double)));
     CAV(cav_alloc(c, (void **)&c->d_export,
                   std::max<size_t>((size_t)std::max<long long>(2 * pool, (long long)M * MAXLEV), 1) * sizeof(double)));
     std::vector<double> mode(MODE_N, 0.0);
@@ -264,6 +314,9 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, 
 
 ml_status ml_cavity_destroy(ml_cavity *c) {
     if (!c) return ML_OK;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (void *p : c->allocs) cudaFree(p);
     delete c;
     return ML_OK;

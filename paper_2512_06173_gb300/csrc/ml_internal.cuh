@@ -192,7 +192,9 @@ struct MolArgs {
     long long pop_slot;    // row block of this step in the sink: (step mod ring) * nmol * MAXLEV
     const double *Eu;      // uniform-field source: the field before gamma_m (3 values)
     T *gmu;                // uniform-field source: gamma_m <mu> of the new state (M, 3)
+    double *dpart;         // uniform-field source, two-level molecules: per-block sums of gamma_m <mu> (3 each)
 };
+constexpr int MU_THREADS_HOST = 256;  // molecules per block of the thread-per-molecule uniform-field kernel
 
 // ------------------------------------------------------------------ DFT planes
 template <typename T>

@@ -37,7 +37,8 @@ __device__ __forceinline__ long long fidx(int px, long long plane, int i, int j,
 }
 
 constexpr int MOL_WARPS = 4;
-constexpr int MOL_MIN_BLOCKS = 6;  // FP32: resident blocks per SM the register budget is cut for
+constexpr int MOL_MIN_BLOCKS = 6;
+constexpr int MU_MIN_BLOCKS = 3;  // FP32 thread-per-molecule kernel: resident blocks per SM  // FP32: resident blocks per SM the register budget is cut for
 
 template <typename T>
 struct MolShared {
@@ -421,7 +422,9 @@ __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCK
 // streams 32 molecules' 2x2 matrices with 16-byte loads instead of one molecule's four
 // elements.  The same step as molecule_body: E~ = gamma Eu held over dt; the exact
 // 2x2 exponential (kind 0) or nsub classic RK4 substeps of the GKSL equation (kind 1);
-// mudot, the current amplitude, the energy sum and gamma <mu> of the new state.
+// mudot and the energy sum.  Instead of gamma <mu> per molecule, each block writes the
+// sum of its molecules' gamma <mu> of the new state (FP64, a fixed tree over the block)
+// to a.dpart[3 * block + c].
 template <typename T>
 __device__ __forceinline__ void ld4(const cx<T> *p, cx<T> (&v)[4]) {
     if constexpr (sizeof(T) == 4) {
@@ -447,24 +450,21 @@ __device__ __forceinline__ void st4(cx<T> *p, const cx<T> (&v)[4]) {
     }
 }
 
+constexpr int MU_THREADS = MU_THREADS_HOST;
+
 template <typename T>
-__global__ void __launch_bounds__(256) molecule_uniform_thread_kernel(const MolArgs<T> a) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= a.nmol) return;
+__device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const int m, double (&gm)[3]) {
     const long long o = 4ll * m;
-    const int cm = a.cmask[m];
     const int kind = a.kind[m];
     const T gam = a.gamma[m];
     const double e_old = a.energy[m];
+    // every load is independent of the others (an absent dipole component is zero in
+    // the pool and is loaded as such)
     cx<T> r[4], h0[4], mu[3][4];
     ld4(a.rho + o, r);
     ld4(a.H0 + o, h0);
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-        if ((cm >> c) & 1) ld4(a.mu + c * a.pool + o, mu[c]);
-        else
-            for (int e = 0; e < 4; e++) mu[c][e] = {T(0), T(0)};
-    }
+    for (int c = 0; c < 3; c++) ld4(a.mu + c * a.pool + o, mu[c]);
     T Et[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) Et[c] = gam * (T)a.Eu[c];
@@ -552,12 +552,30 @@ __global__ void __launch_bounds__(256) molecule_uniform_thread_kernel(const MolA
         const T md = (mu1[c] - mu0[c]) / a.dt;
         a.Et[3 * m + c] = Et[c];
         a.mudot[3 * m + c] = md;
-        a.c[3 * m + c] = gam * md;
-        a.gmu[3 * m + c] = gam * mu1[c];
+        gm[c] = (double)(gam * mu1[c]);
         if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
     }
     a.energy[m] = e_old + (double)en;
     if (bad) atomicCAS(a.status, 0, 6);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? MU_MIN_BLOCKS : 1)
+    molecule_uniform_thread_kernel(const MolArgs<T> a) {
+    __shared__ double red[3][MU_THREADS];
+    const int tid = threadIdx.x, m = blockIdx.x * MU_THREADS + tid;
+    double gm[3] = {0.0, 0.0, 0.0};
+    if (m < a.nmol) uniform_thread_step(a, m, gm);
+#pragma unroll
+    for (int c = 0; c < 3; c++) red[c][tid] = gm[c];
+    __syncthreads();
+    for (int s = MU_THREADS / 2; s > 0; s >>= 1) {
+        if (tid < s)
+#pragma unroll
+            for (int c = 0; c < 3; c++) red[c][tid] += red[c][tid + s];
+        __syncthreads();
+    }
+    if (tid < 3) a.dpart[3 * blockIdx.x + tid] = red[tid][0];
 }
 
 // Uniform-field form (single-mode cavity): no window, no field read.
@@ -588,7 +606,7 @@ template <typename T>
 cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s) {
     if (a.nmol == 0) return cudaSuccess;
     if (a.two_level) {
-        molecule_uniform_thread_kernel<T><<<(a.nmol + 255) / 256, 256, 0, s>>>(a);
+        molecule_uniform_thread_kernel<T><<<(a.nmol + MU_THREADS - 1) / MU_THREADS, MU_THREADS, 0, s>>>(a);
     } else {
         const int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
         molecule_uniform_kernel<T, false><<<blocks, MOL_WARPS * 32, 0, s>>>(a);

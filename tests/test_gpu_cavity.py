@@ -131,3 +131,24 @@ def test_refuses_bad_descriptors(ml):
         assert e.value.status == ml.ML_ERR_INVALID_ARG
     with pytest.raises(ml.MaxlinkError):
         ml.Cavity(W.empty_molecules(), 0.25, 0.01, 0.5)
+
+
+@pytest.mark.parametrize("two_level", [False, True])
+def test_graph_replay_equals_single_steps(ml, two_level):
+    """130 steps as two replays of the captured 64-step sequence plus two single steps
+    give the bits of 130 separate calls (both molecule kernels)."""
+    mols = (W.pack_molecules([W.tls((4.0, 4.0, 4.0), 0.25, 0.3, axis=m % 2, cg=np.sqrt(0.9), ce=np.sqrt(0.1),
+                                    dephase=1e-3 * (m % 2)) for m in range(300)])
+            if two_level else mixed(2, 30))
+    a = ml.Cavity(mols, 0.25, 0.01, 0.5, q0=(0.2, 0.1))
+    b = ml.Cavity(mols, 0.25, 0.01, 0.5, q0=(0.2, 0.1))
+    try:
+        for _ in range(130):
+            a.step(1)
+        b.step(130)
+        assert np.array_equal(a.mode(), b.mode())
+        assert np.array_equal(a.molecules(ml.ML_MOL_RHO), b.molecules(ml.ML_MOL_RHO))
+        assert a.nstep == b.nstep == 130
+    finally:
+        a.close()
+        b.close()

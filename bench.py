@@ -295,10 +295,10 @@ def measure_cavity(args, stream):
     """Single-mode cavity (Sec. II normal-mode solver, single-mode limit): 1,000,000
     two-level emitters resonant with the mode, in-plane dipoles, collective splitting
     about 5% of the mode frequency; FP32 molecules, FP64 mode.  Device time of
-    args.cavity_steps steps after 20 warm-up steps.  Roofline: the molecule kernel's
-    algorithmic bytes per molecule-step (rho read + written, H0, mu_x, mu_y, gamma, the
-    energy sum read + written, gamma <mu> written and read back by the dipole sum:
-    204 B) over the step time."""
+    args.cavity_steps steps after 20 warm-up steps.  Roofline: the algorithmic bytes per
+    molecule-step (rho read + written 64 B, H0 32 B, mu_x and mu_y 64 B, gamma 4 B, the
+    energy sum read + written 16 B, the field and dipole rate written 24 B: 204 B) over
+    the step time."""
     import numpy as np
     import torch
     from paper_2512_06173_gb300 import maxlink, workloads

@@ -9,7 +9,8 @@ Functions without an independent pin are marked "parity unpinned" in their
 docstring (none at present: every piece is pinned by a test under `tests/`,
 see `tests/test_oracle_*.py`; the discrete adjoint by a dot-product identity and
 central differences in `tests/test_oracle_adjoint.py`; the single-mode cavity of
-`oracle/cavity.py` in `tests/test_oracle_cavity.py`).
+`oracle/cavity.py` in `tests/test_oracle_cavity.py`; the laser-driven molecules of
+`oracle/laser.py` in `tests/test_oracle_laser.py`).
 """
 from __future__ import annotations
 

@@ -332,6 +332,46 @@ def measure_cavity(args, stream):
         c.close()
 
 
+def measure_laser(args, stream):
+    """Laser-driven molecules (classical path, Eq. E_analytical): 4,000,000 two-level
+    emitters (the single-mode cavity workload's emitters) spread over z in [0, 1000),
+    a resonant pulse of half width 200 crossing them; FP32.  One launch per step.
+    Roofline: algorithmic bytes per molecule-step (rho read + written 64 B, H0 32 B,
+    mu_x and mu_y 64 B, gamma 4 B, z 8 B, the energy sum read + written 16 B, the field
+    and dipole rate written 24 B: 212 B) over the step time."""
+    import numpy as np
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    M = args.laser_molecules
+    mols = workloads.cavity_ensemble(M)
+    mols.pos[:, 2] = np.random.default_rng(7).uniform(0.0, 1000.0, M)
+    sh = stream.cuda_stream
+    d = maxlink.Drive(mols, 1e-3, 0.25, 0.0, -200.0, 200.0, (1.0, 0.0, 0.0), 0.5, precision=maxlink.ML_F32, stream=sh)
+    K = args.laser_steps
+    try:
+        d.step(64)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(K)
+        e1.record(stream)
+        stream.synchronize()
+        pe = d.molecules(maxlink.ML_MOL_POP)[:, 1]
+        ms = e0.elapsed_time(e1)
+        hbm, peak_kind = peaks()
+        alg = 212.0 * M
+        gbs = alg / (ms / K / 1e3) / 1e9
+        return {"workload": f"laser-driven, {M} two-level emitters, z in [0, 1000), resonant cos^2 pulse",
+                "molecules": M, "steps": K, "dtype": "f32", "ms_per_step": ms / K,
+                "molecule_steps_per_s": M * K / ms * 1e3, "launches_per_step": 1,
+                "roofline": {"bound": "hbm", "alg_bytes_per_step": alg, "achieved_gbs": gbs, "peak": hbm,
+                             "peak_kind": peak_kind, "frac": gbs / hbm},
+                "pe_max": float(pe.max()), "pe_mean": float(pe.mean())}
+    finally:
+        d.close()
+
+
 def measure_features(args, stream):
     """Field-pass time per step on the 256^3 bench grid with features removed one at a
     time (tracing events, 200 steps after 20 warm-up steps): where the pass loses time."""
@@ -428,7 +468,7 @@ def run_ours(args, world, rank, local):
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
         fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
-              "features": measure_features, "cavity": measure_cavity}[args.section]
+              "features": measure_features, "cavity": measure_cavity, "laser": measure_laser}[args.section]
         out = fn(args, torch.cuda.Stream())
         if rank == 0:
             print(json.dumps({"section": args.section, **out}), flush=True)
@@ -532,6 +572,7 @@ def run_ours(args, world, rank, local):
     batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
     bragg = measure_bragg(args, stream) if (world == 1 and not args.no_bragg) else None
     cavity = measure_cavity(args, stream) if (world == 1 and not args.no_cavity) else None
+    laser = measure_laser(args, stream) if (world == 1 and not args.no_laser) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -561,6 +602,7 @@ def run_ours(args, world, rank, local):
             "batch": batch,
             "bragg": bragg,
             "cavity": cavity,
+            "laser": laser,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
                                    "field_pass": kms[1] / K, "plane_fold": kms[3] / K},
             "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
@@ -584,7 +626,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--traced-steps", type=int, default=1000,
                     help="steps of the traced pass that times each kernel (roofline)")
-    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "features", "cavity"],
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "features", "cavity", "laser"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
@@ -594,6 +636,9 @@ def main():
     ap.add_argument("--no-cavity", action="store_true", help="skip the single-mode cavity")
     ap.add_argument("--cavity-steps", type=int, default=2000)
     ap.add_argument("--cavity-molecules", type=int, default=1000000)
+    ap.add_argument("--no-laser", action="store_true", help="skip the laser-driven molecules")
+    ap.add_argument("--laser-steps", type=int, default=2000)
+    ap.add_argument("--laser-molecules", type=int, default=4000000)
     ap.add_argument("--bragg-steps", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:

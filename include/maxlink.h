@@ -292,6 +292,38 @@ ml_status ml_cavity_get_molecules(ml_cavity *c, int what, double *dst, void *str
 /* Steps taken. */
 int64_t ml_cavity_step_count(const ml_cavity *c);
 
+/* ---- Laser-driven molecules (Sec. II, analytical solutions: classical path) --------
+ * No back-action: every molecule sees the prescribed wave of Eq. E_analytical, a
+ * function of z - c t (c = 1) travelling along z:
+ *   E~_m(t) = gamma_m E0 pol env(u) cos(omega u + phase),  u = z_m - center - t,
+ *   env(u) = cos^2(pi u / (2 half_width)) for |u| < half_width, else 0
+ * (a carrier under a pulse envelope of compact support; the paper leaves the waveform
+ * open), held over each step from t = n dt as in ml_step; molecules advance as in
+ * ml_step.  z_m is the molecule descriptor's z position; widths are ignored. */
+typedef struct {
+    double amplitude;        /* E0 */
+    double omega;            /* carrier frequency (wave number omega / c) */
+    double phase;
+    double center;           /* the pulse centre's z at t = 0 */
+    double half_width;       /* > 0 */
+    double polarization[3];  /* pol (not normalised by the library) */
+    double dt;               /* > 0 */
+    int precision;           /* ML_F32 or ML_F64 */
+} ml_drive_desc;
+
+typedef struct ml_drive ml_drive;
+
+/* Create with `m` (copied; count >= 1, positions required).  Errors as for
+ * ml_cavity_create. */
+ml_status ml_drive_create(const ml_drive_desc *d, const ml_molecule_desc *m, ml_drive **out);
+ml_status ml_drive_destroy(ml_drive *d);
+/* Enqueue nsteps steps (one launch each; runs of 64 replay a captured graph). */
+ml_status ml_drive_step(ml_drive *d, int64_t nsteps, void *stream);
+/* Molecular state `what` (ML_MOL_*) into host `dst`; synchronises `stream`;
+ * ML_ERR_NUMERIC if a molecule's field or dipole rate became non-finite. */
+ml_status ml_drive_get_molecules(ml_drive *d, int what, double *dst, void *stream);
+int64_t ml_drive_step_count(const ml_drive *d);
+
 /* ---- Batches of independent grids (many realisations of uneven sizes) ----------
  * A batch advances several grids of the same precision and time step together:
  * each step is one launch per kernel class over every instance's blocks (gather,

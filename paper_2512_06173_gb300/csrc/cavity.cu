@@ -142,7 +142,7 @@ void fill_cavity_args(ml_cavity *c, MolArgs<T> &m) {
     m.Et = (T *)c->d_Et; m.mudot = (T *)c->d_mudot; m.c = (T *)c->d_c;
     m.energy = c->d_energy; m.status = c->d_status;
     m.two_level = c->two_level ? 1 : 0;
-    m.Eu = c->d_mode + 6;
+    m.Eu = c->d_mode ? c->d_mode + 6 : nullptr;
     m.gmu = (T *)c->d_gmu;
     m.dpart = c->d_bpart;
 }
@@ -196,16 +196,12 @@ ml_status cavity_steps(ml_cavity *c, long long nsteps, cudaStream_t s) {
 
 }  // namespace
 
-ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, ml_cavity **out) {
-    if (!d || !md || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
-    *out = nullptr;
-    if (!(d->omega_c > 0.0) || !std::isfinite(d->omega_c)) return fail(ML_ERR_INVALID_ARG, "omega_c must be > 0");
-    if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(ML_ERR_INVALID_ARG, "dt must be > 0");
-    if (!std::isfinite(d->coupling)) return fail(ML_ERR_INVALID_ARG, "non-finite coupling");
-    for (int l = 0; l < 2; l++)
-        if (!std::isfinite(d->q0[l]) || !std::isfinite(d->p0[l])) return fail(ML_ERR_INVALID_ARG, "non-finite mode state");
-    if (d->precision != ML_F32 && d->precision != ML_F64) return fail(ML_ERR_INVALID_ARG, "precision must be ML_F32 or ML_F64");
-    if (md->count < 1) return fail(ML_ERR_INVALID_ARG, "a cavity needs at least one molecule");
+namespace {
+
+// Validate and copy a molecule table into `c` (precision already set): device arrays of
+// the molecule step, the work arrays, and FP64 d0 = sum_m gamma_m <mu_x,y>(rho0).
+ml_status load_ensemble(ml_cavity *c, const ml_molecule_desc *md, double (&d0)[2]) {
+    if (md->count < 1) return fail(ML_ERR_INVALID_ARG, "an ensemble needs at least one molecule");
     if (!md->nlev || !md->off || !md->gamma || !md->decay || !md->dephase || !md->kind || !md->nsub || !md->H0 ||
         !md->mu || !md->rho)
         return fail(ML_ERR_INVALID_ARG, "null molecule array");
@@ -236,7 +232,7 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, 
     H0.resize(2 * pool);
     rho.resize(2 * pool);
     mu.assign(2 * 3 * pool, 0.0);
-    double d0[2] = {0.0, 0.0};
+    d0[0] = d0[1] = 0.0;
     for (int m = 0; m < M; m++) {
         const int nn = nlev[m] * nlev[m];
         int cm = 0;
@@ -257,25 +253,16 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, 
         }
         cmask[m] = cm;
     }
-    ml_cavity *c = new ml_cavity();
-    c->prec = d->precision;
     c->esz = c->prec ? 8 : 4;
     c->M = M;
     c->pool = pool;
-    c->dt = d->dt;
-    c->wc = d->omega_c;
-    c->eps = d->coupling;
     c->two_level = true;
     for (int m = 0; m < M; m++) c->two_level = c->two_level && nlev[m] == 2;
-    auto bail = [&](ml_status s) {
-        ml_cavity_destroy(c);
-        return s;
-    };
     ml_status st;
-#define CAV(x)                          \
-    do {                                \
-        st = (x);                       \
-        if (st != ML_OK) return bail(st); \
+#define CAV(x)                \
+    do {                      \
+        st = (x);             \
+        if (st != ML_OK) return st; \
     } while (0)
     CAV(cav_upload(c, &c->d_nlev, nlev));
     CAV(cav_upload(c, &c->d_kind, kind));
@@ -299,15 +286,42 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, 
     CAV(cav_alloc(c, (void **)&c->d_bpart, 3 * (size_t)((M + MU_THREADS_HOST - 1) / MU_THREADS_HOST) * sizeof(double)));
     CAV(cav_alloc(c, (void **)&c->d_export,
                   std::max<size_t>((size_t)std::max<long long>(2 * pool, (long long)M * MAXLEV), 1) * sizeof(double)));
-    std::vector<double> mode(MODE_N, 0.0);
-    for (int l = 0; l < 2; l++) {
-        mode[l] = d->q0[l];
-        mode[2 + l] = d->p0[l];
-        mode[4 + l] = d0[l];
-        mode[6 + l] = -(c->eps * d->q0[l] + c->eps * c->eps / (c->wc * c->wc) * d0[l]);
-    }
-    CAV(cav_upload(c, &c->d_mode, mode));
 #undef CAV
+    return ML_OK;
+}
+
+}  // namespace
+
+ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, ml_cavity **out) {
+    if (!d || !md || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(d->omega_c > 0.0) || !std::isfinite(d->omega_c)) return fail(ML_ERR_INVALID_ARG, "omega_c must be > 0");
+    if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(ML_ERR_INVALID_ARG, "dt must be > 0");
+    if (!std::isfinite(d->coupling)) return fail(ML_ERR_INVALID_ARG, "non-finite coupling");
+    for (int l = 0; l < 2; l++)
+        if (!std::isfinite(d->q0[l]) || !std::isfinite(d->p0[l])) return fail(ML_ERR_INVALID_ARG, "non-finite mode state");
+    if (d->precision != ML_F32 && d->precision != ML_F64) return fail(ML_ERR_INVALID_ARG, "precision must be ML_F32 or ML_F64");
+    ml_cavity *c = new ml_cavity();
+    c->prec = d->precision;
+    c->dt = d->dt;
+    c->wc = d->omega_c;
+    c->eps = d->coupling;
+    double d0[2];
+    ml_status st = load_ensemble(c, md, d0);
+    if (st == ML_OK) {
+        std::vector<double> mode(MODE_N, 0.0);
+        for (int l = 0; l < 2; l++) {
+            mode[l] = d->q0[l];
+            mode[2 + l] = d->p0[l];
+            mode[4 + l] = d0[l];
+            mode[6 + l] = -(c->eps * d->q0[l] + c->eps * c->eps / (c->wc * c->wc) * d0[l]);
+        }
+        st = cav_upload(c, &c->d_mode, mode);
+    }
+    if (st != ML_OK) {
+        ml_cavity_destroy(c);
+        return st;
+    }
     *out = c;
     return ML_OK;
 }
@@ -362,3 +376,149 @@ ml_status ml_cavity_get_molecules(ml_cavity *c, int what, double *dst, void *str
 }
 
 int64_t ml_cavity_step_count(const ml_cavity *c) { return c ? c->step : -1; }
+
+// ---- Laser-driven molecules (classical path, Eq. E_analytical) ----------------------
+// The molecules of an ml_cavity shell without the mode: every step is one launch of
+// the uniform-field molecule kernel with the laser's plane wave; the absolute step of a
+// launch is a device counter (advanced by a tick after each run of steps) plus the
+// launch's offset in that run, so that 64-step runs can be replayed from a graph.
+
+struct ml_drive {
+    ml_cavity *c = nullptr;
+    double E0 = 0.0, k = 0.0, phase = 0.0, xi0 = 0.0, W = 0.0, pol[3] = {0.0, 0.0, 0.0}, dt = 0.0;
+    double *d_z = nullptr;
+    long long *d_base = nullptr;
+    long long step = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+template <typename T>
+ml_status enqueue_drive(ml_drive *d, int nsteps, cudaStream_t s) {
+    if (nsteps <= 0) return ML_OK;
+    MolArgs<T> m;
+    fill_cavity_args<T>(d->c, m);
+    m.dpart = nullptr;
+    m.laser = 1;
+    m.zpos = d->d_z;
+    m.lbase = d->d_base;
+    m.ldt = d->dt;
+    m.lxi0 = d->xi0;
+    m.lk = d->k;
+    m.lphase = d->phase;
+    m.lW = d->W;
+    m.lE0 = d->E0;
+    for (int c = 0; c < 3; c++) m.lpol[c] = d->pol[c];
+    for (int q = 0; q < nsteps; q++) {
+        m.lstep = q;
+        CK(launch_molecules_uniform<T>(m, s));
+    }
+    CK(launch_tick(d->d_base, nsteps, s));
+    return ML_OK;
+}
+
+template <typename T>
+ml_status drive_steps(ml_drive *d, long long nsteps, cudaStream_t s) {
+    const long long reps = nsteps / CAV_SEQ;
+    if (reps > 0 && !d->exec) {
+        if (!d->cap) CK(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+        const ml_status e = enqueue_drive<T>(d, CAV_SEQ, d->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(d->cap, &graph);
+        if (e != ML_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return e;
+        }
+        CK(ce);
+        d->graph = graph;
+        CK(cudaGraphInstantiate(&d->exec, d->graph, 0));
+    }
+    for (long long r = 0; r < reps; r++) {
+        CK(cudaGraphLaunch(d->exec, s));
+        d->step += CAV_SEQ;
+        d->c->step += CAV_SEQ;
+    }
+    const int rest = (int)(nsteps - reps * CAV_SEQ);
+    ml_status st = enqueue_drive<T>(d, rest, s);
+    if (st != ML_OK) return st;
+    d->step += rest;
+    d->c->step += rest;
+    return ML_OK;
+}
+
+}  // namespace
+
+ml_status ml_drive_create(const ml_drive_desc *dd, const ml_molecule_desc *md, ml_drive **out) {
+    if (!dd || !md || !out) return fail(ML_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(dd->dt > 0.0) || !std::isfinite(dd->dt)) return fail(ML_ERR_INVALID_ARG, "dt must be > 0");
+    if (!(dd->half_width > 0.0) || !std::isfinite(dd->half_width)) return fail(ML_ERR_INVALID_ARG, "half_width must be > 0");
+    if (!std::isfinite(dd->amplitude) || !std::isfinite(dd->omega) || !std::isfinite(dd->phase) ||
+        !std::isfinite(dd->center))
+        return fail(ML_ERR_INVALID_ARG, "non-finite pulse parameter");
+    for (int c = 0; c < 3; c++)
+        if (!std::isfinite(dd->polarization[c])) return fail(ML_ERR_INVALID_ARG, "non-finite polarisation");
+    if (dd->precision != ML_F32 && dd->precision != ML_F64) return fail(ML_ERR_INVALID_ARG, "precision must be ML_F32 or ML_F64");
+    if (md->count >= 1 && !md->pos) return fail(ML_ERR_INVALID_ARG, "null molecule positions");
+    ml_drive *d = new ml_drive();
+    d->c = new ml_cavity();
+    d->c->prec = dd->precision;
+    d->c->dt = dd->dt;
+    d->E0 = dd->amplitude;
+    d->k = dd->omega;
+    d->phase = dd->phase;
+    d->xi0 = dd->center;
+    d->W = dd->half_width;
+    d->dt = dd->dt;
+    for (int c = 0; c < 3; c++) d->pol[c] = dd->polarization[c];
+    double d0[2];
+    ml_status st = load_ensemble(d->c, md, d0);
+    if (st == ML_OK) {
+        std::vector<double> z(md->count);
+        for (int m = 0; m < md->count; m++) {
+            z[m] = md->pos[3 * m + 2];
+            if (!std::isfinite(z[m])) st = fail(ML_ERR_INVALID_ARG, "non-finite position");
+        }
+        if (st == ML_OK) st = cav_upload(d->c, &d->d_z, z);
+        if (st == ML_OK) st = cav_upload(d->c, &d->d_base, std::vector<long long>(1, 0));
+    }
+    if (st != ML_OK) {
+        ml_drive_destroy(d);
+        return st;
+    }
+    *out = d;
+    return ML_OK;
+}
+
+ml_status ml_drive_destroy(ml_drive *d) {
+    if (!d) return ML_OK;
+    if (d->exec) cudaGraphExecDestroy(d->exec);
+    if (d->graph) cudaGraphDestroy(d->graph);
+    if (d->cap) cudaStreamDestroy(d->cap);
+    ml_cavity_destroy(d->c);
+    delete d;
+    return ML_OK;
+}
+
+ml_status ml_drive_step(ml_drive *d, int64_t nsteps, void *stream) {
+    if (!d) return fail(ML_ERR_INVALID_ARG, "null drive");
+    if (nsteps < 0) return fail(ML_ERR_INVALID_ARG, "negative step count");
+    cudaStream_t s = (cudaStream_t)stream;
+    return d->c->prec ? drive_steps<double>(d, nsteps, s) : drive_steps<float>(d, nsteps, s);
+}
+
+ml_status ml_drive_get_molecules(ml_drive *d, int what, double *dst, void *stream) {
+    if (!d) return fail(ML_ERR_INVALID_ARG, "null drive");
+    ml_status st = ml_cavity_get_molecules(d->c, what, dst, stream);
+    if (st != ML_OK) return st;
+    int status = 0;
+    CK(cudaMemcpy(&status, d->c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) return fail(ML_ERR_NUMERIC, "a molecule's field or dipole rate became non-finite");
+    return ML_OK;
+}
+
+int64_t ml_drive_step_count(const ml_drive *d) { return d ? d->step : -1; }

@@ -193,6 +193,14 @@ struct MolArgs {
     const double *Eu;      // uniform-field source: the field before gamma_m (3 values)
     T *gmu;                // uniform-field source: gamma_m <mu> of the new state (M, 3)
     double *dpart;         // uniform-field source, two-level molecules: per-block sums of gamma_m <mu> (3 each)
+    // uniform-field source with laser = 1: the prescribed plane wave of Eq. E_analytical
+    // instead of Eu, E~_m = gamma_m E0 pol env(u) cos(k u + phase), u = z_m - xi0 - t,
+    // t = (*lbase + lstep) dt, env(u) = cos^2(pi u / 2W) for |u| < W
+    int laser;
+    const double *zpos;
+    const long long *lbase;
+    int lstep;
+    double ldt, lxi0, lk, lphase, lW, lE0, lpol[3];
 };
 constexpr int MU_THREADS_HOST = 256;  // molecules per block of the thread-per-molecule uniform-field kernel
 

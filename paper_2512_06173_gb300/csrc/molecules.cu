@@ -162,6 +162,26 @@ __device__ __forceinline__ bool window_gather_vec(const MolArgs<float> &a, const
     return true;
 }
 
+// The uniform-field source's field at molecule m before gamma_m: Eu, or the laser's
+// plane wave (u in FP64, then the carrier and envelope in the field type on |u| < W).
+template <typename T>
+__device__ __forceinline__ void uniform_field(const MolArgs<T> &a, const int m, T (&E)[3]) {
+    if (!a.laser) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) E[c] = (T)a.Eu[c];
+        return;
+    }
+    const double u = (a.zpos[m] - a.lxi0) - (double)(*a.lbase + a.lstep) * a.ldt;
+    T f = T(0);
+    if (fabs(u) < a.lW) {
+        const T uf = (T)u;
+        const T cw = cos(T(1.5707963267948966) * uf / (T)a.lW);
+        f = (T)a.lE0 * cw * cw * cos((T)a.lk * uf + (T)a.lphase);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) E[c] = f * (T)a.lpol[c];
+}
+
 // GKSL right-hand side for element (j,l) of rho given in S (n x n), H in Hs.
 template <typename T>
 __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, const cx<T> *Hs, T decay, T deph) {
@@ -252,8 +272,9 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
     // ---- 1. regularised field
     T Et[3];
     if (SRC == SRC_UNIFORM) {
+        uniform_field(a, m, Et);
 #pragma unroll
-        for (int c = 0; c < 3; c++) Et[c] = gam * (T)a.Eu[c];
+        for (int c = 0; c < 3; c++) Et[c] *= gam;
     } else if (SRC == SRC_WINDOW) {
         const T *sw = sh.W[wl];
         T g[3];
@@ -452,6 +473,7 @@ __device__ __forceinline__ void st4(cx<T> *p, const cx<T> (&v)[4]) {
 
 constexpr int MU_THREADS = MU_THREADS_HOST;
 
+
 template <typename T>
 __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const int m, double (&gm)[3]) {
     const long long o = 4ll * m;
@@ -466,8 +488,9 @@ __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const i
 #pragma unroll
     for (int c = 0; c < 3; c++) ld4(a.mu + c * a.pool + o, mu[c]);
     T Et[3];
+    uniform_field(a, m, Et);
 #pragma unroll
-    for (int c = 0; c < 3; c++) Et[c] = gam * (T)a.Eu[c];
+    for (int c = 0; c < 3; c++) Et[c] *= gam;
     // H = H0 - Et . mu and <mu> before the step (Re Tr(rho A) = sum Re(rho_e conj(A_e)))
     cx<T> H[4];
     T mu0[3] = {T(0), T(0), T(0)};
@@ -575,7 +598,7 @@ __global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? MU_MIN_BLOCKS : 1
             for (int c = 0; c < 3; c++) red[c][tid] += red[c][tid + s];
         __syncthreads();
     }
-    if (tid < 3) a.dpart[3 * blockIdx.x + tid] = red[tid][0];
+    if (a.dpart && tid < 3) a.dpart[3 * blockIdx.x + tid] = red[tid][0];
 }
 
 // Uniform-field form (single-mode cavity): no window, no field read.

@@ -59,6 +59,12 @@ class ml_cavity_desc(C.Structure):
                 ("q0", C.c_double * 2), ("p0", C.c_double * 2), ("precision", C.c_int)]
 
 
+class ml_drive_desc(C.Structure):
+    _fields_ = [("amplitude", C.c_double), ("omega", C.c_double), ("phase", C.c_double), ("center", C.c_double),
+                ("half_width", C.c_double), ("polarization", C.c_double * 3), ("dt", C.c_double),
+                ("precision", C.c_int)]
+
+
 _lib = None
 
 
@@ -121,6 +127,11 @@ def load(build_if_missing: bool = True):
         "ml_cavity_mode": (I, [P, P, P]),
         "ml_cavity_get_molecules": (I, [P, I, P, P]),
         "ml_cavity_step_count": (I64, [P]),
+        "ml_drive_create": (I, [C.POINTER(ml_drive_desc), C.POINTER(ml_molecule_desc), C.POINTER(P)]),
+        "ml_drive_destroy": (I, [P]),
+        "ml_drive_step": (I, [P, I64, P]),
+        "ml_drive_get_molecules": (I, [P, I, P, P]),
+        "ml_drive_step_count": (I64, [P]),
         "ml_batch_create": (I, [P, I, C.POINTER(P)]),
         "ml_batch_step": (I, [P, I64, P]),
         "ml_batch_set_tuning": (I, [P, I, I]),
@@ -307,6 +318,28 @@ def ml_cavity_step_count(c: int) -> int:
     return int(load().ml_cavity_step_count(C.c_void_p(c)))
 
 
+def ml_drive_create(desc: ml_drive_desc, mdesc: ml_molecule_desc) -> int:
+    out = C.c_void_p()
+    _check(load().ml_drive_create(C.byref(desc), C.byref(mdesc), C.byref(out)))
+    return out.value
+
+
+def ml_drive_destroy(d: int):
+    _check(load().ml_drive_destroy(C.c_void_p(d)))
+
+
+def ml_drive_step(d: int, nsteps: int, stream: int = 0):
+    _check(load().ml_drive_step(C.c_void_p(d), int(nsteps), C.c_void_p(stream)))
+
+
+def ml_drive_get_molecules(d: int, what: int, dst_ptr: int, stream: int = 0):
+    _check(load().ml_drive_get_molecules(C.c_void_p(d), int(what), C.c_void_p(dst_ptr), C.c_void_p(stream)))
+
+
+def ml_drive_step_count(d: int) -> int:
+    return int(load().ml_drive_step_count(C.c_void_p(d)))
+
+
 def ml_batch_create(handles) -> int:
     arr = (C.c_void_p * len(handles))(*handles)
     out = C.c_void_p()
@@ -463,6 +496,62 @@ class Cavity:
     def close(self):
         if self.h:
             ml_cavity_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Drive:
+    """Molecules of a `workloads.Molecules` table driven by the prescribed wave of
+    Eq. E_analytical (no back-action); positions give each molecule's z."""
+
+    def __init__(self, molecules, amplitude: float, omega: float, phase: float, center: float, half_width: float,
+                 polarization, dt: float, precision: int = ML_F32, stream: int = 0):
+        d = ml_drive_desc()
+        d.amplitude, d.omega, d.phase, d.center = float(amplitude), float(omega), float(phase), float(center)
+        d.half_width, d.dt, d.precision = float(half_width), float(dt), int(precision)
+        for c in range(3):
+            d.polarization[c] = float(polarization[c])
+        md, self._keep = molecule_desc(molecules)
+        self.mol = molecules
+        self.stream = stream
+        self.h = ml_drive_create(d, md)
+
+    def step(self, n: int = 1):
+        ml_drive_step(self.h, n, self.stream)
+
+    def molecules(self, what: int) -> np.ndarray:
+        M = self.mol.count
+        if what == ML_MOL_RHO:
+            out = np.zeros(2 * int((self.mol.nlev.astype(np.int64) ** 2).sum()))
+            ml_drive_get_molecules(self.h, what, _ptr(out), self.stream)
+            return out.view(np.complex128)
+        n = {ML_MOL_EFIELD: 3 * M, ML_MOL_MUDOT: 3 * M, ML_MOL_ENERGY: M, ML_MOL_POP: ML_MAX_LEVELS * M}[what]
+        out = np.zeros(n)
+        ml_drive_get_molecules(self.h, what, _ptr(out), self.stream)
+        if what in (ML_MOL_EFIELD, ML_MOL_MUDOT):
+            return out.reshape(M, 3)
+        if what == ML_MOL_POP:
+            return out.reshape(M, ML_MAX_LEVELS)
+        return out
+
+    def rho(self, m: int) -> np.ndarray:
+        n = int(self.mol.nlev[m])
+        pool = self.molecules(ML_MOL_RHO)
+        off = int(np.concatenate([[0], np.cumsum(self.mol.nlev.astype(np.int64) ** 2)])[m])
+        return pool[off:off + n * n].reshape(n, n)
+
+    @property
+    def nstep(self) -> int:
+        return ml_drive_step_count(self.h)
+
+    def close(self):
+        if self.h:
+            ml_drive_destroy(self.h)
             self.h = None
 
     def __del__(self):

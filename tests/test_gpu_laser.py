@@ -1,0 +1,103 @@
+"""Laser-driven molecules (ml_drive_*) through the C ABI against the oracle's
+classical-path drive (oracle/laser.py) on the same seeded molecules at seeded z:
+populations every step and final density matrices; FP64 to round-off (1e-10), FP32
+within 1e-4.  Also: graph replay equals single steps bit for bit, and bad descriptors
+are refused.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_06173_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ml():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2512_06173_gb300 import maxlink
+    maxlink.load()
+    return maxlink
+
+
+@pytest.fixture(scope="module")
+def las():
+    from oracle import laser
+    return laser
+
+
+def ensemble(seed, M, two_level_only=False):
+    """Exact two-level, two-level with dephasing and 3..5-level ladders with decay, at
+    seeded z in [0, 60), seeded dipole directions in the xy plane."""
+    rng = np.random.default_rng(seed)
+    mats = []
+    for m in range(M):
+        kind = m % 2 if two_level_only else m % 3
+        th = rng.uniform(0, 2 * np.pi)
+        z = rng.uniform(0.0, 60.0)
+        if kind < 2:
+            d = W.tls((0.0, 0.0, z), rng.uniform(0.23, 0.27), rng.uniform(0.5, 1.2), axis=0,
+                      gamma=rng.uniform(0.5, 1.5), dephase=0.0 if kind == 0 else 1e-3)
+            mu = d["mu"][0].copy()
+            d["mu"] = np.stack([np.cos(th) * mu, np.sin(th) * mu, 0 * mu])
+        else:
+            n = 3 + m % 3
+            H0 = np.diag(np.cumsum([0.0] + list(0.25 * (1 + 0.05 * rng.standard_normal(n - 1))))).astype(complex)
+            ladder = np.diag(np.sqrt(np.arange(1, n)), 1).astype(complex)
+            x = 0.4 * (ladder + ladder.T)
+            rho = np.zeros((n, n), complex)
+            rho[0, 0] = 1.0
+            d = dict(n=n, pos=(0.0, 0.0, z), sigma=1.0, gamma=rng.uniform(0.5, 1.5), H0=H0,
+                     mu=np.stack([np.cos(th) * x, np.sin(th) * x, 0 * x]), rho=rho, decay=1e-3, dephase=0.0,
+                     kind=1, nsub=2)
+        mats.append(d)
+    return W.pack_molecules(mats)
+
+
+PULSE = dict(amplitude=0.03, omega=0.25, phase=0.3, center=-40.0, half_width=40.0,
+             polarization=(0.8, 0.6, 0.0), dt=0.5)
+
+
+@pytest.mark.parametrize("two_level_only", [False, True])
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_matches_oracle_every_step(ml, las, precision, tol, two_level_only):
+    mols = ensemble(3, 24, two_level_only)
+    o = las.OracleLaser(mols, **PULSE)
+    g = ml.Drive(mols, precision=precision, **PULSE)
+    try:
+        for _ in range(240):  # the pulse crosses every molecule
+            g.step(1)
+            o.step(1)
+            pg = g.molecules(ml.ML_MOL_POP)[:, :2]
+            po = o.populations()
+            assert np.abs(pg - po).max() < tol
+        assert np.abs(o.populations()[:, 1]).max() > 1e-3  # the pulse did excite
+        for m in range(mols.count):
+            assert np.abs(g.rho(m) - o.rho(m)).max() < 10 * tol
+    finally:
+        g.close()
+
+
+def test_graph_replay_equals_single_steps(ml):
+    mols = ensemble(4, 500, True)
+    a = ml.Drive(mols, **PULSE)
+    b = ml.Drive(mols, **PULSE)
+    try:
+        for _ in range(140):
+            a.step(1)
+        b.step(140)
+        assert np.array_equal(a.molecules(ml.ML_MOL_RHO), b.molecules(ml.ML_MOL_RHO))
+        assert a.nstep == b.nstep == 140
+    finally:
+        a.close()
+        b.close()
+
+
+def test_refuses_bad_descriptors(ml):
+    mols = ensemble(5, 3)
+    for bad in (dict(half_width=0.0), dict(dt=0.0), dict(amplitude=float("inf"))):
+        with pytest.raises(ml.MaxlinkError) as e:
+            ml.Drive(mols, **{**PULSE, **bad})
+        assert e.value.status == ml.ML_ERR_INVALID_ARG

@@ -51,7 +51,7 @@ def _load():
     ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     L.orc_create.restype = P
     L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, ip, ip, C.c_double, C.c_double,
-                             C.c_double, C.c_double, P, P, P]
+                             C.c_double, C.c_double, P, P, P, P]
     L.orc_destroy.argtypes = [P]
     L.orc_add_molecule.restype = C.c_int
     L.orc_add_molecule.argtypes = [P, C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -126,10 +126,12 @@ class OracleSim:
         nx, ny, nz = prob.nx, prob.ny, prob.nz
         self.shape = (nz, ny, nx)
         N = nx * ny * nz
-        # material description -> full-grid eps, Drude wp and damping (own conversion)
+        # material description -> full-grid eps, pole strength, damping and resonance
+        # (own conversion)
         eps = np.ones(self.shape)
         wp = np.zeros(self.shape)
         dg = np.zeros(self.shape)
+        w0 = np.zeros(self.shape)
         mats = prob.materials
         if prob.mat is not None:
             idx = np.asarray(prob.mat)
@@ -138,21 +140,25 @@ class OracleSim:
                 eps[sel] = mt.eps_inf
                 wp[sel] = mt.wp
                 dg[sel] = mt.gamma
+                w0[sel] = mt.omega0
         else:
             eps[:] = mats[0].eps_inf
             wp[:] = mats[0].wp
             dg[:] = mats[0].gamma
+            w0[:] = mats[0].omega0
         if prob.design_box is not None:
             x0, y0, z0, sx, sy, sz = prob.design_box
             eps[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx] = prob.design_eps
         self._eps = np.ascontiguousarray(eps.ravel())
         self._wp = np.ascontiguousarray(wp.ravel())
         self._dg = np.ascontiguousarray(dg.ravel())
+        self._w0 = np.ascontiguousarray(w0.ravel())
         per = np.array([1 if p else 0 for p in prob.periodic], np.int32)
         pml = np.array(prob.pml, np.int32)
         self.h = L.orc_create(nx, ny, nz, prob.dt, per, pml, prob.pml_m, prob.pml_sigma_max,
                               prob.pml_kappa_max, prob.pml_alpha_max,
-                              self._eps.ctypes.data, self._wp.ctypes.data, self._dg.ctypes.data)
+                              self._eps.ctypes.data, self._wp.ctypes.data, self._dg.ctypes.data,
+                              self._w0.ctypes.data)
         for s in prob.sources:
             L.orc_add_source(self.h, s.axis, s.index, s.comp, s.amp, s.omega, s.width, s.t0)
         for p in prob.planes:

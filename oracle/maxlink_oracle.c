@@ -69,8 +69,10 @@ typedef struct {
     double *E[3], *H[3];
     double *psi[12];   /* CPML memory variables, full grid (0 outside the layers) */
     double *eps;       /* relative permittivity (eps_inf in Drude cells) */
-    double *wp, *dg;   /* Drude plasma frequency and damping per cell */
-    double *JD[3];     /* Drude polarisation current at n-1/2 */
+    double *wp, *dg;   /* pole strength (Drude plasma frequency) and damping per cell */
+    double *w0;        /* pole resonance per cell: 0 Drude, > 0 Lorentz */
+    double *JD[3];     /* polarisation current of the pole at n-1/2 */
+    double *PD[3];     /* polarisation of a Lorentz pole at n */
     double *J[3];      /* scratch: molecular + source current at n+1/2 */
     /* CPML coefficients per axis: integer positions (E update) and half positions (H update) */
     double *bE[3], *cE[3], *kE[3], *bH[3], *cH[3], *kH[3];
@@ -125,7 +127,7 @@ static void pml_coeff(const osim *s, int a, double x, double *b, double *c, doub
 
 osim *orc_create(int nx, int ny, int nz, double dt, const int *periodic, const int *pml,
                  double pml_m, double sigma_max, double kappa_max, double alpha_max,
-                 const double *eps, const double *wp, const double *dg) {
+                 const double *eps, const double *wp, const double *dg, const double *w0) {
     osim *s = (osim *)calloc(1, sizeof(osim));
     s->nx = nx; s->ny = ny; s->nz = nz; s->dt = dt;
     for (int a = 0; a < 3; a++) s->periodic[a] = periodic[a];
@@ -136,16 +138,19 @@ osim *orc_create(int nx, int ny, int nz, double dt, const int *periodic, const i
         s->E[a] = calloc(N, sizeof(double));
         s->H[a] = calloc(N, sizeof(double));
         s->JD[a] = calloc(N, sizeof(double));
+        s->PD[a] = calloc(N, sizeof(double));
         s->J[a] = calloc(N, sizeof(double));
     }
     for (int p = 0; p < 12; p++) s->psi[p] = calloc(N, sizeof(double));
     s->eps = malloc(N * sizeof(double));
     s->wp = calloc(N, sizeof(double));
     s->dg = calloc(N, sizeof(double));
+    s->w0 = calloc(N, sizeof(double));
     for (long c = 0; c < N; c++) {
         s->eps[c] = eps ? eps[c] : 1.0;
         if (wp) s->wp[c] = wp[c];
         if (dg) s->dg[c] = dg[c];
+        if (w0) s->w0[c] = w0[c];
     }
     for (int a = 0; a < 3; a++) {
         int n = dimn(s, a);
@@ -165,12 +170,12 @@ static void adj_free(osim *s);
 void orc_destroy(osim *s) {
     if (!s) return;
     for (int a = 0; a < 3; a++) {
-        free(s->E[a]); free(s->H[a]); free(s->JD[a]); free(s->J[a]);
+        free(s->E[a]); free(s->H[a]); free(s->JD[a]); free(s->PD[a]); free(s->J[a]);
         free(s->bE[a]); free(s->cE[a]); free(s->kE[a]);
         free(s->bH[a]); free(s->cH[a]); free(s->kH[a]);
     }
     for (int p = 0; p < 12; p++) free(s->psi[p]);
-    free(s->eps); free(s->wp); free(s->dg);
+    free(s->eps); free(s->wp); free(s->dg); free(s->w0);
     free(s->mol);
     adj_free(s);
     for (int p = 0; p < s->nplane; p++) {
@@ -466,9 +471,12 @@ int orc_step(osim *s, long nsteps) {
                     for (int a = 0; a < 3; a++) {
                         double jd = 0.0;
                         if (s->wp[c] != 0.0) {
-                            /* Drude ADE: dJ/dt + g J = wp^2 E, centred at n */
+                            /* pole ADE dJ/dt + g J + w0^2 P = wp^2 E, dP/dt = J (w0 = 0: Drude),
+                               J centred at n: J^{n+1/2} from J^{n-1/2}, E^n and P^n */
                             double g2 = 0.5 * s->dg[c] * dt;
-                            jd = ((1.0 - g2) * s->JD[a][c] + dt * s->wp[c] * s->wp[c] * E[a][c]) / (1.0 + g2);
+                            jd = ((1.0 - g2) * s->JD[a][c] +
+                                  dt * (s->wp[c] * s->wp[c] * E[a][c] - s->w0[c] * s->w0[c] * s->PD[a][c])) /
+                                 (1.0 + g2);
                         }
                         double e_old = E[a][c];
                         double e_new = pec_forced(s, a, i, j, k)
@@ -477,6 +485,7 @@ int orc_step(osim *s, long nsteps) {
                         if (s->wp[c] != 0.0) {
                             absorbed += jd * 0.5 * (e_old + e_new) * dt;
                             s->JD[a][c] = jd;
+                            if (s->w0[c] != 0.0) s->PD[a][c] += dt * jd;  /* P^{n+1} */
                         }
                         E[a][c] = e_new;
                     }
@@ -1069,6 +1078,8 @@ int orc_adjoint_run(osim *s, long nsteps, int p, int f, double *grad_eps, double
     for (int q = 0; q < s->nmol; q++)
         if (s->mol[q].kind != 0) return -2;
     const long N = nn(s);
+    for (long c = 0; c < N; c++)
+        if (s->w0[c] != 0.0) return -3;  /* the reverse sweep transposes Drude poles only */
     const int M = s->nmol;
     const double dt = s->dt;
     oplane *pl = &s->plane[p];

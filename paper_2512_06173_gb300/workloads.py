@@ -53,9 +53,13 @@ class FluxPlane:
 
 @dataclass
 class Material:
+    """eps_inf plus at most one dispersive pole, dJ/dt + gamma J + omega0^2 P = wp^2 E
+    with dP/dt = J: omega0 = 0 is a Drude term (wp the plasma frequency), omega0 > 0 a
+    Lorentz oscillator (wp^2 = delta_eps omega0^2)."""
     eps_inf: float = 1.0
-    wp: float = 0.0      # Drude plasma frequency (0: no Drude term)
-    gamma: float = 0.0   # Drude damping
+    wp: float = 0.0      # pole strength (0: no pole)
+    gamma: float = 0.0   # pole damping
+    omega0: float = 0.0  # pole resonance (0: Drude)
 
 
 @dataclass

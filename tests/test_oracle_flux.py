@@ -91,3 +91,31 @@ def test_drude_plasma_oscillation(oracle_mod):
     Ef = sim.fields()[0]
     tot = 0.5 * einf * (Ef ** 2).sum() + sim.absorbed()
     assert abs(tot - 0.5 * einf * E0 ** 2 * 27) < 2e-3 * 0.5 * E0 ** 2 * 27
+
+
+def test_lorentz_oscillation(oracle_mod):
+    """A uniform field in a Lorentz medium (no curl): eps_inf E' = -J, J' = -g J - w0^2 P
+    + wp^2 E, P' = J conserve eps_inf E + P, so E'' + g E' + W^2 E = w0^2 E0 with
+    W^2 = w0^2 + wp^2 / eps_inf: a damped oscillation at sqrt(W^2 - g^2/4) about the
+    shifted equilibrium w0^2 E0 / W^2 (0 for a Drude pole), and the field energy plus the
+    work done on the medium stays at the initial field energy."""
+    wp, g, einf, w0, dt = 0.8, 0.05, 2.0, 0.6, 0.002
+    prob = Problem(3, 3, 3, dt, periodic=(True, True, True), mat=np.zeros((3, 3, 3), np.uint8),
+                   materials=[Material(einf, wp, g, w0)])
+    sim = oracle_mod.OracleSim(prob)
+    E0 = 0.7
+    sim.set_fields([np.full((3, 3, 3), E0), np.zeros((3, 3, 3)), np.zeros((3, 3, 3))] +
+                   [np.zeros((3, 3, 3))] * 3)
+    W2 = w0 ** 2 + wp ** 2 / einf
+    ws = np.sqrt(W2 - g ** 2 / 4)
+    Eeq = w0 ** 2 * E0 / W2
+    maxerr = 0.0
+    for n in range(1, 15001):
+        sim.step(1)
+        t = n * dt
+        want = Eeq + (E0 - Eeq) * np.exp(-g * t / 2) * (np.cos(ws * t) + g / (2 * ws) * np.sin(ws * t))
+        maxerr = max(maxerr, abs(sim.fields()[0][1, 1, 1] - want))
+    assert maxerr < 2e-3 * E0
+    Ef = sim.fields()[0]
+    tot = 0.5 * einf * (Ef ** 2).sum() + sim.absorbed()
+    assert abs(tot - 0.5 * einf * E0 ** 2 * 27) < 2e-3 * 0.5 * einf * E0 ** 2 * 27

@@ -48,10 +48,14 @@ typedef enum { ML_F32 = 0, ML_F64 = 1 } ml_precision;
 
 typedef struct ml_grid ml_grid;
 
-/* Material of a cell: eps_inf plus an optional Drude term (Sec. II.A.1 mentions
- * Drude/Lorentz dielectric functions): dJ/dt + gamma J = wp^2 E.  wp = 0: none. */
+/* Material of a cell: eps_inf plus an optional dispersive pole (Sec. II.A.1 mentions
+ * Drude/Lorentz dielectric functions): dJ/dt + gamma J + omega0^2 P = wp^2 E with
+ * dP/dt = J.  wp = 0: no pole; omega0 = 0: a Drude term; omega0 > 0: a Lorentz
+ * oscillator of strength wp^2 = delta_eps omega0^2.  Advanced by the centred ADE
+ * J^{n+1/2} = [(1 - gamma dt/2) J^{n-1/2} + dt (wp^2 E^n - omega0^2 P^n)] / (1 + gamma dt/2),
+ * P^{n+1} = P^n + dt J^{n+1/2}.  omega0 < 0 is ML_ERR_INVALID_ARG. */
 typedef struct {
-    double eps_inf, wp, gamma;
+    double eps_inf, wp, gamma, omega0;
 } ml_material;
 
 /* Soft current-sheet source on the plane `index` normal to `axis`, polarised along
@@ -234,8 +238,9 @@ ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *strea
  * full-state device checkpoints taken every ckpt_every steps, each segment
  * recomputed once (device memory ~ nsteps/ckpt_every checkpoints plus ckpt_every
  * design-box E records).  Molecules must be exact two-level ones (kind 0) with
- * gamma != 0.  Allocates its work memory for the call and frees it; synchronises
- * `stream`. */
+ * gamma != 0; materials may carry Drude poles but no Lorentz pole (omega0 > 0 is
+ * ML_ERR_INVALID_ARG).  Allocates its work memory for the call and frees it;
+ * synchronises `stream`. */
 ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_id, int freq, double *objective,
                          double *grad_eps, double *grad_gamma, int on_device, void *stream);
 

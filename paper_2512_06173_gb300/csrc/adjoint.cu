@@ -991,6 +991,7 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
     if (plane_id < 0 || plane_id >= (int)g->planes.size()) return fail(ML_ERR_INVALID_ARG, "no such plane");
     if (freq < 0 || freq >= g->planes[plane_id].nfreq) return fail(ML_ERR_INVALID_ARG, "no such frequency");
     if (grad_eps && !g->dcb) return fail(ML_ERR_INVALID_ARG, "grad_eps needs a design box");
+    if (g->PD[0]) return fail(ML_ERR_INVALID_ARG, "the adjoint transposes Drude poles only (no Lorentz omega0 > 0)");
     for (int m = 0; m < g->nmol; m++) {
         if (g->kind[m] != 0)
             return fail(ML_ERR_INVALID_ARG, "the adjoint takes exact two-level molecules (kind 0) only");

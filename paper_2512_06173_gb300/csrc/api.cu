@@ -263,16 +263,20 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         }
     }
     // materials
-    std::vector<double> cb(ML_MAX_MATERIALS, g->dt), dk(ML_MAX_MATERIALS, 0.0), db(ML_MAX_MATERIALS, 0.0);
-    bool any_drude = false;
+    std::vector<double> cb(ML_MAX_MATERIALS, g->dt), dk(ML_MAX_MATERIALS, 0.0), db(ML_MAX_MATERIALS, 0.0),
+        dp(ML_MAX_MATERIALS, 0.0);
+    bool any_drude = false, any_lorentz = false;
     for (int q = 0; q < d->n_materials; q++) {
         const ml_material &m = d->materials[q];
+        if (!(m.omega0 >= 0.0)) return bail(fail(ML_ERR_INVALID_ARG, "material omega0 must be >= 0"));
         cb[q] = g->dt / m.eps_inf;
         if (m.wp > 0) {
             double g2 = 0.5 * m.gamma * g->dt;
             dk[q] = (1.0 - g2) / (1.0 + g2);
             db[q] = m.wp * m.wp * g->dt / (1.0 + g2);
+            dp[q] = m.omega0 * m.omega0 * g->dt / (1.0 + g2);
             any_drude = true;
+            any_lorentz = any_lorentz || m.omega0 > 0;
         }
     }
     st = upload_reals(g, g->allocs, &g->mat_cb, cb);
@@ -280,6 +284,8 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     st = upload_reals(g, g->allocs, &g->mat_dk, dk);
     if (st != ML_OK) return bail(st);
     st = upload_reals(g, g->allocs, &g->mat_db, db);
+    if (st != ML_OK) return bail(st);
+    st = upload_reals(g, g->allocs, &g->mat_dp, dp);
     if (st != ML_OK) return bail(st);
     if (d->mat) {
         GA(g->mat, (size_t)N);
@@ -313,6 +319,8 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         for (int a = 0; a < 3; a++) { g->jbox[a] = lo[a]; g->jbox[3 + a] = hi[a] - lo[a] + 1; }
         size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
         for (int c = 0; c < 3; c++) GA(g->JD[c], cnt * g->esz);
+        if (any_lorentz)
+            for (int c = 0; c < 3; c++) GA(g->PD[c], cnt * g->esz);
     }
     for (int l = 0; l < 2; l++)
         for (int c = 0; c < 3; c++) {
@@ -767,6 +775,8 @@ void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y) {
     for (int q = 0; q < 6; q++) { y.dbox[q] = g->dbox[q]; y.jbox[q] = g->jbox[q]; }
     y.dcb = (const T *)g->dcb;
     for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
+    y.mat_dp = (const T *)g->mat_dp;
+    for (int c = 0; c < 3; c++) y.PD[c] = (T *)g->PD[c];
     y.absorbed_part = g->absorbed_part;
     y.status = g->d_status;
     if (g->nmol > 0)
@@ -1068,6 +1078,8 @@ std::vector<Blob> ml::state_blobs(ml_grid *g) {
     if (g->JD[0]) {
         size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
         for (int c = 0; c < 3; c++) b.push_back({g->JD[c], cnt * g->esz});
+        if (g->PD[0])
+            for (int c = 0; c < 3; c++) b.push_back({g->PD[c], cnt * g->esz});
     }
     b.push_back({g->absorbed_part, (size_t)g->nblocks * sizeof(double)});
     if (g->nmol) {

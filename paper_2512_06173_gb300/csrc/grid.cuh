@@ -55,11 +55,12 @@ struct ml_grid {
     void *psiE[3][2] = {};
     size_t psi_n[3] = {0, 0, 0};
     uint8_t *mat = nullptr;
-    void *mat_cb = nullptr, *mat_dk = nullptr, *mat_db = nullptr;
+    void *mat_cb = nullptr, *mat_dk = nullptr, *mat_db = nullptr, *mat_dp = nullptr;
     int dbox[6] = {0, 0, 0, 0, 0, 0};
     void *dcb = nullptr;
     int jbox[6] = {0, 0, 0, 0, 0, 0};
     void *JD[3] = {};
+    void *PD[3] = {};   // Lorentz-pole polarisation over the pole box (null: no Lorentz pole)
     double *absorbed_part = nullptr;
     double *d_scalar = nullptr;
     double *d_fpart = nullptr;  // flux reduction partials (ML_MAX_FREQS x FLUX_NB)

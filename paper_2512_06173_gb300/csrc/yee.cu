@@ -458,6 +458,17 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                         jd0 = dk * a.JD[0][jq] + db * eo0;
                         jd1 = dk * a.JD[1][jq] + db * eo1;
                         jd2 = dk * a.JD[2][jq] + db * eo2;
+                        // Lorentz pole: the restoring term -w0^2 P^n, then P^{n+1} = P^n + dt J^{n+1/2}
+                        const T dp = a.PD[0] ? a.mat_dp[midx] : T(0);
+                        if (dp != T(0)) {
+                            const T p0 = a.PD[0][jq], p1 = a.PD[1][jq], p2 = a.PD[2][jq];
+                            jd0 -= dp * p0;
+                            jd1 -= dp * p1;
+                            jd2 -= dp * p2;
+                            a.PD[0][jq] = p0 + a.dt * jd0;
+                            a.PD[1][jq] = p1 + a.dt * jd1;
+                            a.PD[2][jq] = p2 + a.dt * jd2;
+                        }
                         a.JD[0][jq] = jd0;
                         a.JD[1][jq] = jd1;
                         a.JD[2][jq] = jd2;

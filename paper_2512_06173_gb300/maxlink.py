@@ -30,7 +30,7 @@ EXPORTED = ["ml_last_error", "ml_version", "ml_grid_create", "ml_grid_destroy", 
 
 
 class ml_material(C.Structure):
-    _fields_ = [("eps_inf", C.c_double), ("wp", C.c_double), ("gamma", C.c_double)]
+    _fields_ = [("eps_inf", C.c_double), ("wp", C.c_double), ("gamma", C.c_double), ("omega0", C.c_double)]
 
 
 class ml_source(C.Structure):
@@ -401,7 +401,7 @@ def grid_desc(prob, precision: int = ML_F32):
         m = np.ascontiguousarray(prob.mat, np.uint8)
         keep.append(m)
         d.mat = _ptr(m)
-    mats = (ml_material * len(prob.materials))(*[ml_material(x.eps_inf, x.wp, x.gamma) for x in prob.materials])
+    mats = (ml_material * len(prob.materials))(*[ml_material(x.eps_inf, x.wp, x.gamma, x.omega0) for x in prob.materials])
     keep.append(mats)
     d.n_materials = len(prob.materials)
     d.materials = mats

@@ -359,9 +359,12 @@ def plasmonic_batch(count: int = 64, seed: int = 5, edges=(64, 96, 128, 160), nm
 
 def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4,
                   multilevel: bool = True, eps_map: bool = True, drude: bool = False,
-                  source: bool = True, planes: bool = True, periodic=(False, False, False)) -> Problem:
+                  source: bool = True, planes: bool = True, periodic=(False, False, False),
+                  lorentz: bool = False) -> Problem:
     """Small ragged problem for parity tests: every feature at once on a grid the
-    oracle finishes in well under a second per hundred steps."""
+    oracle finishes in well under a second per hundred steps.  `drude` puts a Drude
+    sphere at the centre; `lorentz` (with `drude`) turns its upper half (z above the
+    centre) into a Lorentz oscillator, so that one pole box holds both kinds."""
     rng = np.random.Generator(np.random.PCG64(1000 + seed))
     nx, ny, nz = shape
     pmls = tuple(0 if periodic[a // 2] else pml for a in range(6))
@@ -384,6 +387,9 @@ def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4
         r = min(nx, ny, nz) / 6
         inside = (xx + 0.5 - nx / 2) ** 2 + (yy + 0.5 - ny / 2) ** 2 + (zz + 0.5 - nz / 2) ** 2 < r * r
         mat[inside] = len(materials) - 1
+        if lorentz:
+            materials.append(Material(1.5, wp=0.6, gamma=0.02, omega0=0.3))
+            mat[inside & (zz >= nz // 2)] = len(materials) - 1
     mats = []
     for m in range(nmol):
         sigma = float(rng.choice([1.0, 1.5]))

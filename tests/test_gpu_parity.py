@@ -147,6 +147,40 @@ def test_drude_sphere(ml, oracle_mod, precision, tol):
     assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
 
 
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_lorentz_drude_sphere(ml, oracle_mod, precision, tol):
+    """One pole box holding a Drude half-sphere and a Lorentz half-sphere (the restoring
+    term and the polarisation update of the pole ADE), with molecules and a source."""
+    prob = W.small_coupled(seed=7, shape=(30, 28, 33), drude=True, lorentz=True, eps_map=False, nmol=4,
+                           planes=False)
+    g, o = run_pair(ml, oracle_mod, prob, 160, precision)
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+    ab_g, ab_o = g.absorbed(), o.absorbed()
+    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
+    pops = g.molecules(ml.ML_MOL_POP)
+    for m in range(prob.molecules.count):
+        n = int(prob.molecules.nlev[m])
+        assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+
+
+def test_lorentz_checkpoint_and_adjoint_refusal(ml):
+    """The polarisation is part of the saved state; the adjoint refuses Lorentz poles."""
+    prob = W.small_coupled(seed=8, shape=(26, 24, 28), drude=True, lorentz=True, nmol=3)
+    g = ml.Grid(prob, 1)
+    g.step(30)
+    blob = g.checkpoint()
+    g.step(50)
+    a = g.fields()
+    g.restore(blob)
+    g.step(50)
+    for x, y in zip(a, g.fields()):
+        assert np.array_equal(x, y)
+    with pytest.raises(ml.MaxlinkError) as e:
+        g.adjoint(10, 0, 0)
+    assert e.value.status == ml.ML_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
 def test_plain_single_emitter_trajectory(ml, oracle_mod, precision, tol):
     """40^3 cells, one emitter at the centre, 1000 steps; excited population every

@@ -64,7 +64,8 @@ def field_pass_bytes(prob, esz: int) -> float:
     """Algorithmic bytes of one launch of the fused field pass: E and H read and
     written once (12 esz per cell), four CPML memory variables read and written per
     cell and layer axis (8 esz), 1 B material index per cell if present, esz per
-    design-box cell, 6 esz per Drude cell.  Halo re-reads are not credited."""
+    design-box cell, 6 esz per pole cell (the pole current J read and written) and 6
+    esz more per Lorentz cell (the polarisation P).  Halo re-reads are not credited."""
     import numpy as np
     N = prob.cells
     b = 12 * esz * N
@@ -77,6 +78,9 @@ def field_pass_bytes(prob, esz: int) -> float:
         drude = [q for q, m in enumerate(prob.materials) if m.wp > 0]
         if drude:
             b += 6 * esz * int(np.isin(prob.mat, drude).sum())
+        lorentz = [q for q, m in enumerate(prob.materials) if m.wp > 0 and m.omega0 > 0]
+        if lorentz:
+            b += 6 * esz * int(np.isin(prob.mat, lorentz).sum())
     if prob.design_box is not None:
         x0, y0, z0, sx, sy, sz = prob.design_box
         b += esz * sx * sy * sz
@@ -291,6 +295,49 @@ def measure_bragg(args, stream):
         g.close()
 
 
+def measure_dispersive(args, stream):
+    """Dispersive stack: 512x512x256 cells periodic in x and y, a 32-cell Lorentz layer
+    on an 8-cell Drude film, 20,000 two-level emitters in the Lorentz layer, FP32;
+    device time of args.dispersive_steps steps after a warm-up, per-kernel split from
+    the tracing events; the field pass's algorithmic bytes include the pole current and
+    polarisation of every pole cell."""
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    prob = workloads.dispersive_stack()
+    sh = stream.cuda_stream
+    g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    K = args.dispersive_steps
+    try:
+        g.step(5)
+        g.sync()
+        maxlink.ml_set_timing(g.h, True)
+        maxlink.ml_timing(g.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(K)
+        e1.record(stream)
+        stream.synchronize()
+        g.sync()
+        ms = e0.elapsed_time(e1)
+        kms, _ = maxlink.ml_timing(g.h)
+        maxlink.ml_set_timing(g.h, False)
+        hbm, peak_kind = peaks()
+        fp = kms[1] / K
+        alg = field_pass_bytes(prob, 4)
+        pe = g.molecules(maxlink.ML_MOL_POP)[:, 1]
+        return {"workload": prob.name, "cells": prob.cells, "molecules": prob.molecules.count, "steps": K,
+                "dtype": "f32", "gcells_per_s": prob.cells * K / ms / 1e6,
+                "molecule_steps_per_s": prob.molecules.count * K / ms * 1e3, "ms_per_step": ms / K,
+                "field_pass": {"ms_per_step": fp, "alg_bytes": alg, "achieved_gbs": alg / (fp / 1e3) / 1e9,
+                               "frac": alg / (fp / 1e3) / 1e9 / hbm, "peak": hbm, "peak_kind": peak_kind},
+                "kernel_ms_per_step": {"molecules": kms[0] / K, "current": kms[4] / K, "field_pass": fp,
+                                       "plane_fold": kms[3] / K},
+                "pe_max": float(pe.max()), "flux_far_f3": float(g.flux(1)[3])}
+    finally:
+        g.close()
+
+
 def measure_cavity(args, stream):
     """Single-mode cavity (Sec. II normal-mode solver, single-mode limit): 1,000,000
     two-level emitters resonant with the mode, in-plane dipoles, collective splitting
@@ -468,7 +515,7 @@ def run_ours(args, world, rank, local):
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
         fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
-              "features": measure_features, "cavity": measure_cavity, "laser": measure_laser}[args.section]
+              "dispersive": measure_dispersive, "features": measure_features, "cavity": measure_cavity, "laser": measure_laser}[args.section]
         out = fn(args, torch.cuda.Stream())
         if rank == 0:
             print(json.dumps({"section": args.section, **out}), flush=True)
@@ -571,6 +618,7 @@ def run_ours(args, world, rank, local):
     adjoint = measure_adjoint(args, stream) if (world == 1 and not args.no_adjoint) else None
     batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
     bragg = measure_bragg(args, stream) if (world == 1 and not args.no_bragg) else None
+    dispersive = measure_dispersive(args, stream) if (world == 1 and not args.no_dispersive) else None
     cavity = measure_cavity(args, stream) if (world == 1 and not args.no_cavity) else None
     laser = measure_laser(args, stream) if (world == 1 and not args.no_laser) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
@@ -601,6 +649,7 @@ def run_ours(args, world, rank, local):
             "adjoint": adjoint,
             "batch": batch,
             "bragg": bragg,
+            "dispersive": dispersive,
             "cavity": cavity,
             "laser": laser,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
@@ -626,7 +675,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--traced-steps", type=int, default=1000,
                     help="steps of the traced pass that times each kernel (roofline)")
-    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "features", "cavity", "laser"],
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "dispersive", "features", "cavity",
+                                                        "laser"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
@@ -640,6 +690,8 @@ def main():
     ap.add_argument("--laser-steps", type=int, default=2000)
     ap.add_argument("--laser-molecules", type=int, default=4000000)
     ap.add_argument("--bragg-steps", type=int, default=400)
+    ap.add_argument("--no-dispersive", action="store_true", help="skip the dispersive stack")
+    ap.add_argument("--dispersive-steps", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -295,7 +295,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         issued = q0 + S;
     }
     {
-        double absorbed = 0.0;
+        // work done on the pole current, sum of J^{n+1/2} . (E^n + E^{n+1}) over the
+        // thread's cells in the field precision (GB300's FP64 rate is a small fraction
+        // of its FP32 rate); times dt/2 and summed in FP64 across the block
+        T absorbed = T(0);
         int sc = 1 % S;               // stage of plane k (= k0 = q0 + 1)
         int sn = 2 % S;               // stage of plane k + 1
         uint32_t pn = S > 2 ? 0u : 1u;  // parity of the fill of stage sn that holds plane k + 1
@@ -477,9 +480,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                     en1 = eo1 + cb * (curl1 - j1 - jd1);
                     en2 = eo2 + cb * (curl2 - j2 - jd2);
                     if (drude)
-                        absorbed += 0.5 * (double)a.dt *
-                                    ((double)jd0 * ((double)eo0 + (double)en0) + (double)jd1 * ((double)eo1 + (double)en1) +
-                                     (double)jd2 * ((double)eo2 + (double)en2));
+                        absorbed += jd0 * (eo0 + en0) + jd1 * (eo1 + en1) + jd2 * (eo2 + en2);
                 }
                 if (walls) {
                     // tangential E on an index-0 wall stays 0 (PEC)
@@ -539,8 +540,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         }
         if (FULL && a.JD[0]) {
             // fixed-order block reduction into this block's accumulator
-            for (int q = 16; q > 0; q >>= 1) absorbed += __shfl_xor_sync(0xffffffffu, absorbed, q);
-            if (tx == 0) s_red[ty] = absorbed;
+            double ab = 0.5 * (double)a.dt * (double)absorbed;
+            for (int q = 16; q > 0; q >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, q);
+            if (tx == 0) s_red[ty] = ab;
             __syncthreads();
             if (tid == 0) {
                 double s = 0.0;

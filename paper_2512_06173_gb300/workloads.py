@@ -233,6 +233,36 @@ def superradiant_slab(n: int = 256, nmol: int = 10000, slab: int = 32, pml: int 
                    planes=planes, name=f"superradiant-slab-{n}^3-{nmol}tls")
 
 
+def dispersive_stack(nx: int = 512, ny: int = 512, nz: int = 256, nmol: int = 20000, pml: int = 10,
+                     layer: int = 32, film: int = 8, nfreq: int = 8, seed: int = 5, width: float = 20.0,
+                     t0: float = 80.0) -> Problem:
+    """Planar dispersive stack, periodic in x and y with CPML on the z faces: a
+    `layer`-cell Lorentz dielectric (eps_inf 1.5, delta_eps 1, omega0 0.3, gamma 0.01)
+    centred in z on a `film`-cell Drude metal film (wp 1, gamma 0.05) that mirrors the
+    pulse; `nmol` ground-state two-level emitters (omega0 = 0.25, mu12 = 0.05 along x,
+    sigma = 1.5 cells) at seeded uniform positions in the middle of the Lorentz layer;
+    an x-polarised Gaussian-pulse current sheet (omega 0.25, temporal `width`, centred at
+    `t0`) near the lower CPML and
+    flux planes on both sides.  Stand-in for the emitters in dispersive media
+    (Drude/Lorentz dielectric functions) that the grid solver of Sec. II.A supports."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    zc = nz // 2
+    mat = np.zeros((nz, ny, nx), np.uint8)
+    mat[zc - layer // 2:zc + layer // 2] = 1
+    mat[zc + layer // 2:zc + layer // 2 + film] = 2
+    materials = [Material(1.0), Material(1.5, wp=0.3, gamma=0.01, omega0=0.3), Material(1.0, wp=1.0, gamma=0.05)]
+    xs = rng.uniform(0, nx, size=nmol)
+    ys = rng.uniform(0, ny, size=nmol)
+    zs = rng.uniform(zc - layer // 4, zc + layer // 4, size=nmol)
+    mols = [tls((xs[m], ys[m], zs[m]), 0.25, 0.05, axis=0, sigma=1.5) for m in range(nmol)]
+    om = np.linspace(0.20, 0.30, nfreq)
+    planes = [FluxPlane(2, pml + 6, om.copy()), FluxPlane(2, nz - pml - 4, om.copy())]
+    src = [Source(axis=2, index=pml + 2, comp=0, amp=1.0, omega=0.25, width=width, t0=t0)]
+    return Problem(nx, ny, nz, 0.5, periodic=(True, True, False), pml=(0, 0, 0, 0, pml, pml), mat=mat,
+                   materials=materials, sources=src, molecules=pack_molecules(mols), planes=planes,
+                   name=f"dispersive-stack-{nx}x{ny}x{nz}-{nmol}tls")
+
+
 def random_hermitian(rng, n, std):
     a = rng.normal(0, std, (n, n)) + 1j * rng.normal(0, std, (n, n))
     return (a + a.conj().T) / 2

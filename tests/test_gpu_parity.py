@@ -164,6 +164,28 @@ def test_lorentz_drude_sphere(ml, oracle_mod, precision, tol):
         assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
 
 
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_dispersive_stack_small(ml, oracle_mod, precision, tol):
+    """The dispersive-stack workload's generator at 26x22x64 (periodic x and y, ragged
+    tiles): a pulse through the Lorentz layer onto the Drude film, emitters in the
+    layer, flux on both sides, 220 steps."""
+    prob = W.dispersive_stack(nx=26, ny=22, nz=64, nmol=7, pml=6, layer=16, film=4, width=6.0, t0=18.0)
+    g, o = run_pair(ml, oracle_mod, prob, 220, precision)
+    fo = o.fields()
+    scale = max(np.linalg.norm(f) for f in fo)
+    for got, want in zip(g.fields(), fo):
+        assert np.linalg.norm(np.asarray(got, np.float64) - want) < tol * scale
+    pops = g.molecules(ml.ML_MOL_POP)
+    pe_o = np.array([np.real(o.rho(m)[1, 1]) for m in range(prob.molecules.count)])
+    assert pe_o.max() > 1e-6  # the pulse has reached the emitters
+    assert np.abs(pops[:, 1] - pe_o).max() < 10 * tol * max(pe_o.max(), 1e-3)
+    for p in range(len(prob.planes)):
+        fg, fw = g.flux(p), o.flux(p)
+        assert np.abs(fg - fw).max() < (1e-9 if precision == 1 else 1e-3) * np.abs(fw).max()
+    ab_g, ab_o = g.absorbed(), o.absorbed()
+    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
+
+
 def test_lorentz_checkpoint_and_adjoint_refusal(ml):
     """The polarisation is part of the saved state; the adjoint refuses Lorentz poles."""
     prob = W.small_coupled(seed=8, shape=(26, 24, 28), drude=True, lorentz=True, nmol=3)

@@ -51,7 +51,7 @@ def _load():
     ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     L.orc_create.restype = P
     L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, ip, ip, C.c_double, C.c_double,
-                             C.c_double, C.c_double, P, P, P, P]
+                             C.c_double, C.c_double, P, C.c_int, P, P, P]
     L.orc_destroy.argtypes = [P]
     L.orc_add_molecule.restype = C.c_int
     L.orc_add_molecule.argtypes = [P, C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -126,26 +126,22 @@ class OracleSim:
         nx, ny, nz = prob.nx, prob.ny, prob.nz
         self.shape = (nz, ny, nx)
         N = nx * ny * nz
-        # material description -> full-grid eps, pole strength, damping and resonance
-        # (own conversion)
-        eps = np.ones(self.shape)
-        wp = np.zeros(self.shape)
-        dg = np.zeros(self.shape)
-        w0 = np.zeros(self.shape)
+        # material description -> full-grid eps and, per pole slot, strength, damping and
+        # resonance (own conversion); a material's poles take slots 0, 1, ... in order
         mats = prob.materials
-        if prob.mat is not None:
-            idx = np.asarray(prob.mat)
-            for q, mt in enumerate(mats):
-                sel = idx == q
-                eps[sel] = mt.eps_inf
-                wp[sel] = mt.wp
-                dg[sel] = mt.gamma
-                w0[sel] = mt.omega0
-        else:
-            eps[:] = mats[0].eps_inf
-            wp[:] = mats[0].wp
-            dg[:] = mats[0].gamma
-            w0[:] = mats[0].omega0
+        npole = max([1] + [len(mt.poles()) for mt in mats])
+        eps = np.ones(self.shape)
+        wp = np.zeros((npole,) + self.shape)
+        dg = np.zeros((npole,) + self.shape)
+        w0 = np.zeros((npole,) + self.shape)
+        idx = np.asarray(prob.mat) if prob.mat is not None else np.zeros(self.shape, np.uint8)
+        for q, mt in enumerate(mats):
+            sel = idx == q
+            eps[sel] = mt.eps_inf
+            for p, (a, g, r) in enumerate(mt.poles()):
+                wp[p][sel] = a
+                dg[p][sel] = g
+                w0[p][sel] = r
         if prob.design_box is not None:
             x0, y0, z0, sx, sy, sz = prob.design_box
             eps[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx] = prob.design_eps
@@ -157,8 +153,10 @@ class OracleSim:
         pml = np.array(prob.pml, np.int32)
         self.h = L.orc_create(nx, ny, nz, prob.dt, per, pml, prob.pml_m, prob.pml_sigma_max,
                               prob.pml_kappa_max, prob.pml_alpha_max,
-                              self._eps.ctypes.data, self._wp.ctypes.data, self._dg.ctypes.data,
+                              self._eps.ctypes.data, npole, self._wp.ctypes.data, self._dg.ctypes.data,
                               self._w0.ctypes.data)
+        if not self.h:
+            raise ValueError(f"oracle: {npole} poles per material is more than it holds")
         for s in prob.sources:
             L.orc_add_source(self.h, s.axis, s.index, s.comp, s.amp, s.omega, s.width, s.t0)
         for p in prob.planes:

@@ -23,8 +23,8 @@
  *      the optional Lindblad terms                                          (Eq. von-Neumann-tls)
  *   3. mudot_m = (Tr rho^{n+1} mu - Tr rho^n mu) / dt                       (Eq. dipole_derivative)
  *   4. H^{n+1/2} = H^{n-1/2} - dt curl E^n  (CPML)                           (Eq. Maxwell b)
- *   5. J^{n+1/2} = sum_m gamma_m mudot_m kappa_m + sources; Drude J_D^{n+1/2}
- *   6. E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J - J_D)                     (Eq. Maxwell a)
+ *   5. J^{n+1/2} = sum_m gamma_m mudot_m kappa_m + sources; pole currents J_p^{n+1/2}
+ *   6. E^{n+1} = E^n + dt/eps (curl H^{n+1/2} - J - sum_p J_p)               (Eq. Maxwell a)
  *   7. DFT accumulators (E at t=(n+1)dt, H at t=(n+1/2)dt), molecular energy.
  */
 #include <complex.h>
@@ -39,6 +39,7 @@
 typedef double complex cplx;
 
 #define MAXLEV 8
+#define MAXPOLE 4  /* dispersive poles per cell */
 
 typedef struct {
     int n;
@@ -69,10 +70,12 @@ typedef struct {
     double *E[3], *H[3];
     double *psi[12];   /* CPML memory variables, full grid (0 outside the layers) */
     double *eps;       /* relative permittivity (eps_inf in Drude cells) */
-    double *wp, *dg;   /* pole strength (Drude plasma frequency) and damping per cell */
-    double *w0;        /* pole resonance per cell: 0 Drude, > 0 Lorentz */
-    double *JD[3];     /* polarisation current of the pole at n-1/2 */
-    double *PD[3];     /* polarisation of a Lorentz pole at n */
+    int npole;                 /* pole slots per cell */
+    double *wp[MAXPOLE];       /* pole strength (plasma frequency) per slot and cell; 0: none */
+    double *dg[MAXPOLE];       /* pole damping */
+    double *w0[MAXPOLE];       /* pole resonance: 0 Drude, > 0 Lorentz */
+    double *JD[MAXPOLE][3];    /* polarisation current of each pole at n-1/2 */
+    double *PD[MAXPOLE][3];    /* polarisation of each pole at n */
     double *J[3];      /* scratch: molecular + source current at n+1/2 */
     /* CPML coefficients per axis: integer positions (E update) and half positions (H update) */
     double *bE[3], *cE[3], *kE[3], *bH[3], *cH[3], *kH[3];
@@ -127,30 +130,37 @@ static void pml_coeff(const osim *s, int a, double x, double *b, double *c, doub
 
 osim *orc_create(int nx, int ny, int nz, double dt, const int *periodic, const int *pml,
                  double pml_m, double sigma_max, double kappa_max, double alpha_max,
-                 const double *eps, const double *wp, const double *dg, const double *w0) {
+                 const double *eps, int npole, const double *wp, const double *dg, const double *w0) {
     osim *s = (osim *)calloc(1, sizeof(osim));
     s->nx = nx; s->ny = ny; s->nz = nz; s->dt = dt;
     for (int a = 0; a < 3; a++) s->periodic[a] = periodic[a];
     for (int f = 0; f < 6; f++) s->pml[f] = pml[f];
     s->pml_m = pml_m; s->sigma_max = sigma_max; s->kappa_max = kappa_max; s->alpha_max = alpha_max;
     long N = nn(s);
+    if (npole < 1 || npole > MAXPOLE) { free(s); return NULL; }
+    s->npole = npole;
     for (int a = 0; a < 3; a++) {
         s->E[a] = calloc(N, sizeof(double));
         s->H[a] = calloc(N, sizeof(double));
-        s->JD[a] = calloc(N, sizeof(double));
-        s->PD[a] = calloc(N, sizeof(double));
         s->J[a] = calloc(N, sizeof(double));
     }
     for (int p = 0; p < 12; p++) s->psi[p] = calloc(N, sizeof(double));
     s->eps = malloc(N * sizeof(double));
-    s->wp = calloc(N, sizeof(double));
-    s->dg = calloc(N, sizeof(double));
-    s->w0 = calloc(N, sizeof(double));
-    for (long c = 0; c < N; c++) {
-        s->eps[c] = eps ? eps[c] : 1.0;
-        if (wp) s->wp[c] = wp[c];
-        if (dg) s->dg[c] = dg[c];
-        if (w0) s->w0[c] = w0[c];
+    for (long c = 0; c < N; c++) s->eps[c] = eps ? eps[c] : 1.0;
+    /* pole q of cell c at [q N + c] of wp, dg, w0 */
+    for (int q = 0; q < npole; q++) {
+        s->wp[q] = calloc(N, sizeof(double));
+        s->dg[q] = calloc(N, sizeof(double));
+        s->w0[q] = calloc(N, sizeof(double));
+        for (int a = 0; a < 3; a++) {
+            s->JD[q][a] = calloc(N, sizeof(double));
+            s->PD[q][a] = calloc(N, sizeof(double));
+        }
+        for (long c = 0; c < N; c++) {
+            if (wp) s->wp[q][c] = wp[q * N + c];
+            if (dg) s->dg[q][c] = dg[q * N + c];
+            if (w0) s->w0[q][c] = w0[q * N + c];
+        }
     }
     for (int a = 0; a < 3; a++) {
         int n = dimn(s, a);
@@ -170,12 +180,16 @@ static void adj_free(osim *s);
 void orc_destroy(osim *s) {
     if (!s) return;
     for (int a = 0; a < 3; a++) {
-        free(s->E[a]); free(s->H[a]); free(s->JD[a]); free(s->PD[a]); free(s->J[a]);
+        free(s->E[a]); free(s->H[a]); free(s->J[a]);
         free(s->bE[a]); free(s->cE[a]); free(s->kE[a]);
         free(s->bH[a]); free(s->cH[a]); free(s->kH[a]);
     }
     for (int p = 0; p < 12; p++) free(s->psi[p]);
-    free(s->eps); free(s->wp); free(s->dg); free(s->w0);
+    for (int q = 0; q < s->npole; q++) {
+        free(s->wp[q]); free(s->dg[q]); free(s->w0[q]);
+        for (int a = 0; a < 3; a++) { free(s->JD[q][a]); free(s->PD[q][a]); }
+    }
+    free(s->eps);
     free(s->mol);
     adj_free(s);
     for (int p = 0; p < s->nplane; p++) {
@@ -469,23 +483,28 @@ int orc_step(osim *s, long nsteps) {
                     curl[1] = (s->kE[2][k] * dHx_dz + P[8][c]) - (s->kE[0][i] * dHz_dx + P[9][c]);
                     curl[2] = (s->kE[0][i] * dHy_dx + P[10][c]) - (s->kE[1][j] * dHx_dy + P[11][c]);
                     for (int a = 0; a < 3; a++) {
-                        double jd = 0.0;
-                        if (s->wp[c] != 0.0) {
-                            /* pole ADE dJ/dt + g J + w0^2 P = wp^2 E, dP/dt = J (w0 = 0: Drude),
-                               J centred at n: J^{n+1/2} from J^{n-1/2}, E^n and P^n */
-                            double g2 = 0.5 * s->dg[c] * dt;
-                            jd = ((1.0 - g2) * s->JD[a][c] +
-                                  dt * (s->wp[c] * s->wp[c] * E[a][c] - s->w0[c] * s->w0[c] * s->PD[a][c])) /
-                                 (1.0 + g2);
+                        /* each pole's ADE dJ/dt + g J + w0^2 P = wp^2 E, dP/dt = J (w0 = 0:
+                           Drude), J centred at n: J^{n+1/2} from J^{n-1/2}, E^n and P^n */
+                        double jp[MAXPOLE], jd = 0.0;
+                        for (int q = 0; q < s->npole; q++) {
+                            jp[q] = 0.0;
+                            if (s->wp[q][c] == 0.0) continue;
+                            double g2 = 0.5 * s->dg[q][c] * dt;
+                            jp[q] = ((1.0 - g2) * s->JD[q][a][c] +
+                                     dt * (s->wp[q][c] * s->wp[q][c] * E[a][c] -
+                                           s->w0[q][c] * s->w0[q][c] * s->PD[q][a][c])) /
+                                    (1.0 + g2);
+                            jd += jp[q];
                         }
                         double e_old = E[a][c];
                         double e_new = pec_forced(s, a, i, j, k)
                                            ? 0.0
                                            : e_old + dt / s->eps[c] * (curl[a] - s->J[a][c] - jd);
-                        if (s->wp[c] != 0.0) {
-                            absorbed += jd * 0.5 * (e_old + e_new) * dt;
-                            s->JD[a][c] = jd;
-                            if (s->w0[c] != 0.0) s->PD[a][c] += dt * jd;  /* P^{n+1} */
+                        for (int q = 0; q < s->npole; q++) {
+                            if (s->wp[q][c] == 0.0) continue;
+                            absorbed += jp[q] * 0.5 * (e_old + e_new) * dt;
+                            s->JD[q][a][c] = jp[q];
+                            if (s->w0[q][c] != 0.0) s->PD[q][a][c] += dt * jp[q];  /* P^{n+1} */
                         }
                         E[a][c] = e_new;
                     }
@@ -605,7 +624,7 @@ void orc_set_fields(osim *s, const double *in) {
 
 void orc_get_drude(const osim *s, double *out) {
     long N = nn(s);
-    for (int a = 0; a < 3; a++) memcpy(out + a * N, s->JD[a], N * sizeof(double));
+    for (int a = 0; a < 3; a++) memcpy(out + a * N, s->JD[0][a], N * sizeof(double));
 }
 
 void orc_get_psi(const osim *s, double *out) {
@@ -698,7 +717,7 @@ void orc_set_psi(osim *s, const double *in) {
 
 void orc_set_drude(osim *s, const double *in) {
     long N = nn(s);
-    for (int a = 0; a < 3; a++) memcpy(s->JD[a], in + a * N, N * sizeof(double));
+    for (int a = 0; a < 3; a++) memcpy(s->JD[0][a], in + a * N, N * sizeof(double));
 }
 
 /* ================================================================== adjoint
@@ -812,12 +831,12 @@ static void adj_field_step(osim *s, const double *En, const double *En1, double 
                         jdb = -g * eb;
                         if (grad_eps) grad_eps[c] += eb * (-(En1[a * N + c] - En[a * N + c]) / s->eps[c]);
                     }
-                    if (s->wp[c] != 0.0) {
+                    if (s->wp[0][c] != 0.0) {
                         /* JD = jd; jd = ((1 - g2) JD_old + dt wp^2 E^n) / (1 + g2) */
                         jdb += A->JDb[a][c];
-                        double g2 = 0.5 * s->dg[c] * dt;
+                        double g2 = 0.5 * s->dg[0][c] * dt;
                         A->JDb[a][c] = jdb * (1.0 - g2) / (1.0 + g2);
-                        A->Eb_in[a][c] += jdb * dt * s->wp[c] * s->wp[c] / (1.0 + g2);
+                        A->Eb_in[a][c] += jdb * dt * s->wp[0][c] * s->wp[0][c] / (1.0 + g2);
                     }
                 }
                 /* curl[0] = (kE_y dHz_dy + P6) - (kE_z dHy_dz + P7), P6 = bE_y P6 + cE_y dHz_dy, ... */
@@ -1078,8 +1097,12 @@ int orc_adjoint_run(osim *s, long nsteps, int p, int f, double *grad_eps, double
     for (int q = 0; q < s->nmol; q++)
         if (s->mol[q].kind != 0) return -2;
     const long N = nn(s);
-    for (long c = 0; c < N; c++)
-        if (s->w0[c] != 0.0) return -3;  /* the reverse sweep transposes Drude poles only */
+    /* the reverse sweep transposes one Drude pole per cell (slot 0) only */
+    for (long c = 0; c < N; c++) {
+        if (s->w0[0][c] != 0.0) return -3;
+        for (int q = 1; q < s->npole; q++)
+            if (s->wp[q][c] != 0.0) return -3;
+    }
     const int M = s->nmol;
     const double dt = s->dt;
     oplane *pl = &s->plane[p];

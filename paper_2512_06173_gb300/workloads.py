@@ -53,13 +53,23 @@ class FluxPlane:
 
 @dataclass
 class Material:
-    """eps_inf plus at most one dispersive pole, dJ/dt + gamma J + omega0^2 P = wp^2 E
-    with dP/dt = J: omega0 = 0 is a Drude term (wp the plasma frequency), omega0 > 0 a
-    Lorentz oscillator (wp^2 = delta_eps omega0^2)."""
+    """eps_inf plus dispersive poles, each dJ/dt + gamma J + omega0^2 P = wp^2 E with
+    dP/dt = J, their currents summed: omega0 = 0 is a Drude term (wp the plasma
+    frequency), omega0 > 0 a Lorentz oscillator (wp^2 = delta_eps omega0^2).  The first
+    pole is (wp, gamma, omega0); `extra` holds up to MAX_POLES - 1 more."""
     eps_inf: float = 1.0
     wp: float = 0.0      # pole strength (0: no pole)
     gamma: float = 0.0   # pole damping
     omega0: float = 0.0  # pole resonance (0: Drude)
+    extra: Tuple[Tuple[float, float, float], ...] = ()  # further poles (wp, gamma, omega0)
+
+    def poles(self) -> List[Tuple[float, float, float]]:
+        """The material's poles with wp > 0, in order: the first, then `extra`."""
+        ps = [(self.wp, self.gamma, self.omega0)] + [tuple(map(float, p)) for p in self.extra]
+        return [p for p in ps if p[0] > 0]
+
+
+MAX_POLES = 4  # dispersive poles per material
 
 
 @dataclass

@@ -7,6 +7,10 @@
     same side, equal and opposite flux on the two sides.
   * Drude ADE: a spatially uniform field in a Drude medium oscillates as the damped
     plasma oscillation E(t) = E0 e^{-g t/2}(cos w't + g/(2w') sin w't), w'^2 = wp^2/eps - g^2/4.
+  * Lorentz pole: the same oscillation about the shifted equilibrium; several poles in
+    one cell: the exact solution of the continuous uniform-field equations (matrix
+    exponential), energy bookkeeping over all poles, and two half-strength poles equal
+    to one full-strength pole.
 """
 import numpy as np
 import pytest
@@ -119,3 +123,67 @@ def test_lorentz_oscillation(oracle_mod):
     Ef = sim.fields()[0]
     tot = 0.5 * einf * (Ef ** 2).sum() + sim.absorbed()
     assert abs(tot - 0.5 * einf * E0 ** 2 * 27) < 2e-3 * 0.5 * einf * E0 ** 2 * 27
+
+
+def _two_pole_uniform(oracle_mod, dt, T=20.0):
+    """Oracle E(t) in a uniform field against the exact solution of the continuous
+    equations eps_inf E' = -(J1 + J2), J_p' = -g_p J_p - w0_p^2 P_p + wp_p^2 E, P_p' = J_p
+    (x' = A x, solved by the matrix exponential), for a Drude pole plus a Lorentz pole."""
+    from scipy.linalg import expm
+    einf = 1.5
+    poles = [(0.5, 0.03, 0.0), (0.7, 0.05, 0.9)]
+    prob = Problem(3, 3, 3, dt, periodic=(True, True, True), mat=np.zeros((3, 3, 3), np.uint8),
+                   materials=[Material(einf, *poles[0], extra=(poles[1],))])
+    sim = oracle_mod.OracleSim(prob)
+    E0 = 0.7
+    sim.set_fields([np.full((3, 3, 3), E0)] + [np.zeros((3, 3, 3))] * 5)
+    A = np.zeros((5, 5))  # state (E, J1, P1, J2, P2)
+    for p, (wp, g, w0) in enumerate(poles):
+        j, q = 1 + 2 * p, 2 + 2 * p
+        A[0, j] = -1.0 / einf
+        A[j, j], A[j, q], A[j, 0], A[q, j] = -g, -w0 ** 2, wp ** 2, 1.0
+    x0 = np.array([E0, 0.0, 0.0, 0.0, 0.0])
+    err = 0.0
+    n = int(round(T / dt))
+    for s in range(1, n + 1):
+        sim.step(1)
+        if s % 50 == 0:
+            err = max(err, abs(sim.fields()[0][1, 1, 1] - (expm(A * s * dt) @ x0)[0]))
+    Ef = sim.fields()[0]
+    e_init = 0.5 * einf * E0 ** 2 * 27
+    return err, abs(0.5 * einf * (Ef ** 2).sum() + sim.absorbed() - e_init) / e_init
+
+
+def test_two_pole_medium_against_the_continuous_solution(oracle_mod):
+    """Drude + Lorentz poles in one cell: the scheme converges (first order, from the
+    staggered start J^{-1/2} = 0) to the exact uniform-field solution, and the field
+    energy plus the work done on both poles stays at the initial field energy."""
+    e1, b1 = _two_pole_uniform(oracle_mod, 0.004)
+    e2, b2 = _two_pole_uniform(oracle_mod, 0.002)
+    assert e1 < 1.5e-3 * 0.7
+    assert 1.8 < e1 / e2 < 2.2
+    assert max(b1, b2) < 1e-12
+
+
+def test_split_pole_equals_one_pole(oracle_mod):
+    """The pole ADE is linear in wp^2: two identical poles of strength wp / sqrt(2)
+    carry together the current of one pole of strength wp, in a 3D run with CPML,
+    a source and a Lorentz sphere."""
+    def prob(mat):
+        n = 14
+        zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        m = (((xx - 6.5) ** 2 + (yy - 7) ** 2 + (zz - 7.5) ** 2) < 16).astype(np.uint8)
+        return Problem(n, n, n, 0.5, pml=(3,) * 6, mat=m, materials=[Material(1.0), mat],
+                       sources=[Source(axis=2, index=4, comp=0, amp=1.0, omega=0.6, width=3.0, t0=8.0)])
+    wp, g, w0 = 0.9, 0.04, 0.6
+    a = oracle_mod.OracleSim(prob(Material(1.3, wp, g, w0)))
+    h = wp / np.sqrt(2.0)
+    b = oracle_mod.OracleSim(prob(Material(1.3, h, g, w0, extra=((h, g, w0),))))
+    a.step(80)
+    b.step(80)
+    fa, fb = a.fields(), b.fields()
+    scale = max(np.abs(f).max() for f in fa)
+    assert scale > 1e-3
+    for x, y in zip(fa, fb):
+        assert np.abs(x - y).max() < 1e-12 * scale
+    assert abs(a.absorbed() - b.absorbed()) < 1e-12 * abs(a.absorbed())

@@ -64,8 +64,8 @@ def field_pass_bytes(prob, esz: int) -> float:
     """Algorithmic bytes of one launch of the fused field pass: E and H read and
     written once (12 esz per cell), four CPML memory variables read and written per
     cell and layer axis (8 esz), 1 B material index per cell if present, esz per
-    design-box cell, 6 esz per pole cell (the pole current J read and written) and 6
-    esz more per Lorentz cell (the polarisation P).  Halo re-reads are not credited."""
+    design-box cell, 6 esz per pole of a cell (its current J read and written) and 6
+    esz more per Lorentz pole (its polarisation P).  Halo re-reads are not credited."""
     import numpy as np
     N = prob.cells
     b = 12 * esz * N
@@ -75,12 +75,9 @@ def field_pass_bytes(prob, esz: int) -> float:
         b += 8 * esz * th * (N // dims[a])
     if prob.mat is not None:
         b += N
-        drude = [q for q, m in enumerate(prob.materials) if m.wp > 0]
-        if drude:
-            b += 6 * esz * int(np.isin(prob.mat, drude).sum())
-        lorentz = [q for q, m in enumerate(prob.materials) if m.wp > 0 and m.omega0 > 0]
-        if lorentz:
-            b += 6 * esz * int(np.isin(prob.mat, lorentz).sum())
+        per = np.array([6 * esz * sum(1 + (w0 > 0) for _, _, w0 in m.poles()) for m in prob.materials])
+        if per.any():
+            b += int(per[np.asarray(prob.mat)].sum())
     if prob.design_box is not None:
         x0, y0, z0, sx, sy, sz = prob.design_box
         b += esz * sx * sy * sz

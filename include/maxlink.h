@@ -48,14 +48,26 @@ typedef enum { ML_F32 = 0, ML_F64 = 1 } ml_precision;
 
 typedef struct ml_grid ml_grid;
 
-/* Material of a cell: eps_inf plus an optional dispersive pole (Sec. II.A.1 mentions
- * Drude/Lorentz dielectric functions): dJ/dt + gamma J + omega0^2 P = wp^2 E with
- * dP/dt = J.  wp = 0: no pole; omega0 = 0: a Drude term; omega0 > 0: a Lorentz
- * oscillator of strength wp^2 = delta_eps omega0^2.  Advanced by the centred ADE
- * J^{n+1/2} = [(1 - gamma dt/2) J^{n-1/2} + dt (wp^2 E^n - omega0^2 P^n)] / (1 + gamma dt/2),
- * P^{n+1} = P^n + dt J^{n+1/2}.  omega0 < 0 is ML_ERR_INVALID_ARG. */
+/* Dispersive pole (Sec. II.A.1 mentions Drude/Lorentz dielectric functions):
+ * dJ/dt + gamma J + omega0^2 P = wp^2 E with dP/dt = J.  omega0 = 0: a Drude term;
+ * omega0 > 0: a Lorentz oscillator of strength wp^2 = delta_eps omega0^2.  Advanced by
+ * the centred ADE J^{n+1/2} = [(1 - gamma dt/2) J^{n-1/2} + dt (wp^2 E^n - omega0^2 P^n)]
+ * / (1 + gamma dt/2), P^{n+1} = P^n + dt J^{n+1/2}. */
+typedef struct {
+    double wp, gamma, omega0;
+} ml_pole;
+
+#define ML_MAX_POLES 4  /* dispersive poles per material */
+
+/* Material of a cell: eps_inf and up to ML_MAX_POLES poles whose currents add up in
+ * the E update.  The first pole is (wp, gamma, omega0), the others extra[0..n_extra);
+ * a pole with wp = 0 is absent.  n_extra outside 0..ML_MAX_POLES-1, eps_inf <= 0, or a
+ * negative omega0 or gamma is ML_ERR_INVALID_ARG.  A zero-initialised tail (n_extra =
+ * 0) gives the single-pole material. */
 typedef struct {
     double eps_inf, wp, gamma, omega0;
+    int n_extra;
+    ml_pole extra[ML_MAX_POLES - 1];
 } ml_material;
 
 /* Soft current-sheet source on the plane `index` normal to `axis`, polarised along

@@ -383,9 +383,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) adj_passB_kernel(
         const T cb = adj_cb(a, i, j, k, midx);
         // Drude: J_D = dk J_D + db E^n, used in the E update as -dt/eps J_D
         if (a.JDb[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] && j < a.jbox[1] + a.jbox[4] &&
-            k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx] != T(0)) {
+            k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx * ML_MAX_POLES] != T(0)) {
             const long long jq = ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
-            const T dk = a.mat_dk[midx], db = a.mat_db[midx];
+            const T dk = a.mat_dk[midx * ML_MAX_POLES], db = a.mat_db[midx * ML_MAX_POLES];
             const T t0 = a.JDb[0][jq] - dt * o0, t1 = a.JDb[1][jq] - dt * o1, t2 = a.JDb[2][jq] - dt * o2;
             a.JDb[0][jq] = dk * t0;
             a.JDb[1][jq] = dk * t1;
@@ -785,7 +785,7 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                     CK(cudaMemsetAsync(chi[l][a][q], 0, g->psi_n[a] * esz, s));
                 }
     T *JDb[3] = {};
-    if (g->JD[0]) {
+    if (g->JD) {
         const size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
         for (int c = 0; c < 3; c++) {
             AA(JDb[c], cnt * esz);
@@ -991,7 +991,9 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
     if (plane_id < 0 || plane_id >= (int)g->planes.size()) return fail(ML_ERR_INVALID_ARG, "no such plane");
     if (freq < 0 || freq >= g->planes[plane_id].nfreq) return fail(ML_ERR_INVALID_ARG, "no such frequency");
     if (grad_eps && !g->dcb) return fail(ML_ERR_INVALID_ARG, "grad_eps needs a design box");
-    if (g->PD[0]) return fail(ML_ERR_INVALID_ARG, "the adjoint transposes Drude poles only (no Lorentz omega0 > 0)");
+    if (g->PD || g->npole > 1)
+        return fail(ML_ERR_INVALID_ARG, "the adjoint transposes one Drude pole per material only (no Lorentz "
+                                        "omega0 > 0, no extra poles)");
     for (int m = 0; m < g->nmol; m++) {
         if (g->kind[m] != 0)
             return fail(ML_ERR_INVALID_ARG, "the adjoint takes exact two-level molecules (kind 0) only");

@@ -149,9 +149,17 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     }
     if (d->n_materials < 1 || d->n_materials > ML_MAX_MATERIALS || !d->materials)
         return fail(ML_ERR_INVALID_ARG, "need 1..64 materials");
-    for (int q = 0; q < d->n_materials; q++)
-        if (!(d->materials[q].eps_inf > 0.0) || d->materials[q].wp < 0.0 || d->materials[q].gamma < 0.0)
-            return fail(ML_ERR_INVALID_ARG, "material needs eps_inf > 0, wp >= 0, gamma >= 0");
+    for (int q = 0; q < d->n_materials; q++) {
+        const ml_material &m = d->materials[q];
+        if (!(m.eps_inf > 0.0) || m.n_extra < 0 || m.n_extra > ML_MAX_POLES - 1)
+            return fail(ML_ERR_INVALID_ARG, "material needs eps_inf > 0 and 0 <= n_extra < ML_MAX_POLES");
+        for (int p = 0; p <= m.n_extra; p++) {
+            const double wp = p ? m.extra[p - 1].wp : m.wp, ga = p ? m.extra[p - 1].gamma : m.gamma,
+                         w0 = p ? m.extra[p - 1].omega0 : m.omega0;
+            if (!(wp >= 0.0) || !(ga >= 0.0) || !(w0 >= 0.0))
+                return fail(ML_ERR_INVALID_ARG, "a pole needs wp >= 0, gamma >= 0, omega0 >= 0");
+        }
+    }
     if (d->n_sources < 0 || d->n_sources > ML_MAX_SOURCES || (d->n_sources && !d->sources))
         return fail(ML_ERR_INVALID_ARG, "0..4 sources");
     for (int q = 0; q < d->n_sources; q++) {
@@ -262,22 +270,30 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
             }
         }
     }
-    // materials
-    std::vector<double> cb(ML_MAX_MATERIALS, g->dt), dk(ML_MAX_MATERIALS, 0.0), db(ML_MAX_MATERIALS, 0.0),
-        dp(ML_MAX_MATERIALS, 0.0);
-    bool any_drude = false, any_lorentz = false;
+    // materials: dt / eps_inf, and per pole slot (material-major, ML_MAX_POLES slots per
+    // material) the ADE factors; a material's poles with wp > 0 take slots 0, 1, ...
+    std::vector<double> cb(ML_MAX_MATERIALS, g->dt), dk(ML_MAX_MATERIALS * ML_MAX_POLES, 0.0),
+        db(ML_MAX_MATERIALS * ML_MAX_POLES, 0.0), dp(ML_MAX_MATERIALS * ML_MAX_POLES, 0.0);
+    std::vector<uint8_t> has_pole(ML_MAX_MATERIALS, 0);
+    bool any_lorentz = false;
+    g->npole = 0;
     for (int q = 0; q < d->n_materials; q++) {
         const ml_material &m = d->materials[q];
-        if (!(m.omega0 >= 0.0)) return bail(fail(ML_ERR_INVALID_ARG, "material omega0 must be >= 0"));
         cb[q] = g->dt / m.eps_inf;
-        if (m.wp > 0) {
-            double g2 = 0.5 * m.gamma * g->dt;
-            dk[q] = (1.0 - g2) / (1.0 + g2);
-            db[q] = m.wp * m.wp * g->dt / (1.0 + g2);
-            dp[q] = m.omega0 * m.omega0 * g->dt / (1.0 + g2);
-            any_drude = true;
-            any_lorentz = any_lorentz || m.omega0 > 0;
+        int n = 0;
+        for (int p = 0; p <= m.n_extra; p++) {
+            const double wp = p ? m.extra[p - 1].wp : m.wp, ga = p ? m.extra[p - 1].gamma : m.gamma,
+                         w0 = p ? m.extra[p - 1].omega0 : m.omega0;
+            if (!(wp > 0)) continue;
+            const double g2 = 0.5 * ga * g->dt;
+            const int k = q * ML_MAX_POLES + n++;
+            dk[k] = (1.0 - g2) / (1.0 + g2);
+            db[k] = wp * wp * g->dt / (1.0 + g2);
+            dp[k] = w0 * w0 * g->dt / (1.0 + g2);
+            any_lorentz = any_lorentz || w0 > 0;
         }
+        has_pole[q] = n > 0;
+        g->npole = std::max(g->npole, n);
     }
     st = upload_reals(g, g->allocs, &g->mat_cb, cb);
     if (st != ML_OK) return bail(st);
@@ -302,14 +318,14 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         st = upload_reals(g, g->allocs, &g->dcb, v);
         if (st != ML_OK) return bail(st);
     }
-    // Drude box: bounding box of cells whose material has a Drude term
+    // pole box: bounding box of cells whose material has a dispersive pole
     int lo[3] = {g->nx, g->ny, g->nz}, hi[3] = {-1, -1, -1};
-    if (any_drude) {
+    if (g->npole > 0) {
         for (int k = 0; k < g->nz; k++)
             for (int j = 0; j < g->ny; j++)
                 for (int i = 0; i < g->nx; i++) {
                     int q = d->mat ? d->mat[((long long)k * g->ny + j) * g->nx + i] : 0;
-                    if (d->materials[q].wp > 0) {
+                    if (has_pole[q]) {
                         int idx[3] = {i, j, k};
                         for (int a = 0; a < 3; a++) { lo[a] = std::min(lo[a], idx[a]); hi[a] = std::max(hi[a], idx[a]); }
                     }
@@ -317,10 +333,9 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     }
     if (hi[0] >= 0) {
         for (int a = 0; a < 3; a++) { g->jbox[a] = lo[a]; g->jbox[3 + a] = hi[a] - lo[a] + 1; }
-        size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
-        for (int c = 0; c < 3; c++) GA(g->JD[c], cnt * g->esz);
-        if (any_lorentz)
-            for (int c = 0; c < 3; c++) GA(g->PD[c], cnt * g->esz);
+        g->jcnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
+        GA(g->JD, 3 * (size_t)g->npole * g->jcnt * g->esz);
+        if (any_lorentz) GA(g->PD, 3 * (size_t)g->npole * g->jcnt * g->esz);
     }
     for (int l = 0; l < 2; l++)
         for (int c = 0; c < 3; c++) {
@@ -774,9 +789,11 @@ void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y) {
     y.mat_cb = (const T *)g->mat_cb; y.mat_dk = (const T *)g->mat_dk; y.mat_db = (const T *)g->mat_db;
     for (int q = 0; q < 6; q++) { y.dbox[q] = g->dbox[q]; y.jbox[q] = g->jbox[q]; }
     y.dcb = (const T *)g->dcb;
-    for (int c = 0; c < 3; c++) y.JD[c] = (T *)g->JD[c];
     y.mat_dp = (const T *)g->mat_dp;
-    for (int c = 0; c < 3; c++) y.PD[c] = (T *)g->PD[c];
+    y.npole = g->npole;
+    y.jcnt = (long long)g->jcnt;
+    y.JD = (T *)g->JD;
+    y.PD = (T *)g->PD;
     y.absorbed_part = g->absorbed_part;
     y.status = g->d_status;
     if (g->nmol > 0)
@@ -1075,12 +1092,8 @@ std::vector<Blob> ml::state_blobs(ml_grid *g) {
                 b.push_back({g->psiH[g->cur][a][q], g->psi_n[a] * g->esz});
                 b.push_back({g->psiE[a][q], g->psi_n[a] * g->esz});
             }
-    if (g->JD[0]) {
-        size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
-        for (int c = 0; c < 3; c++) b.push_back({g->JD[c], cnt * g->esz});
-        if (g->PD[0])
-            for (int c = 0; c < 3; c++) b.push_back({g->PD[c], cnt * g->esz});
-    }
+    if (g->JD) b.push_back({g->JD, 3 * (size_t)g->npole * g->jcnt * g->esz});
+    if (g->PD) b.push_back({g->PD, 3 * (size_t)g->npole * g->jcnt * g->esz});
     b.push_back({g->absorbed_part, (size_t)g->nblocks * sizeof(double)});
     if (g->nmol) {
         b.push_back({g->d_rho, 2 * (size_t)g->pool * g->esz});

@@ -59,8 +59,10 @@ struct ml_grid {
     int dbox[6] = {0, 0, 0, 0, 0, 0};
     void *dcb = nullptr;
     int jbox[6] = {0, 0, 0, 0, 0, 0};
-    void *JD[3] = {};
-    void *PD[3] = {};   // Lorentz-pole polarisation over the pole box (null: no Lorentz pole)
+    int npole = 0;        // pole slots in use
+    size_t jcnt = 0;      // cells of the pole box
+    void *JD = nullptr;   // pole currents [slot][component][jcnt] over the pole box
+    void *PD = nullptr;   // pole polarisations, same layout (null: no Lorentz pole)
     double *absorbed_part = nullptr;
     double *d_scalar = nullptr;
     double *d_fpart = nullptr;  // flux reduction partials (ML_MAX_FREQS x FLUX_NB)

@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "maxlink.h"
+
 #include <string>
 
 namespace ml {
@@ -85,14 +87,16 @@ struct YeeArgs {
     // materials
     const uint8_t *mat;   // (nz,ny,nx) or null
     const T *mat_cb;      // dt / eps_inf per material
-    const T *mat_dk;      // pole recursion factor per material
-    const T *mat_db;      // pole drive factor per material (0 = none)
-    const T *mat_dp;      // pole restoring factor per material (0 = Drude)
+    const T *mat_dk;      // pole recursion factor [material * ML_MAX_POLES + slot]
+    const T *mat_db;      // pole drive factor, same layout (0 = no pole in the slot)
+    const T *mat_dp;      // pole restoring factor, same layout (0 = Drude)
     int dbox[6];
     const T *dcb;         // dt / eps per design-box cell
     int jbox[6];
-    T *JD[3];             // pole current over the pole box
-    T *PD[3];             // Lorentz-pole polarisation over the pole box (null: no Lorentz pole)
+    int npole;            // pole slots in use (0: no poles)
+    long long jcnt;       // cells of the pole box
+    T *JD;                // pole currents [slot][component][jcnt] over the pole box (null: none)
+    T *PD;                // pole polarisations, same layout (null: no Lorentz pole)
     double *absorbed_part;  // one accumulator per block
     // molecular current on its box (written by the current kernel this step)
     int jb0[3], jbn[3];     // box origin and extent in cells

@@ -150,7 +150,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     // per-cell material work (material table, design box, Drude, sources): only tiles
     // whose own cells need it, when the grid has the per-tile flags
     const bool general = FULL && (a.tflags ? (a.tflags[tile] & 1) != 0
-                                          : (a.mat != nullptr || a.dcb != nullptr || a.JD[0] != nullptr || a.nsrc > 0));
+                                          : (a.mat != nullptr || a.dcb != nullptr || a.JD != nullptr || a.nsrc > 0));
     // does the tile's column meet the box of the molecular current?
     const bool has_mol = (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
                          x0 + TX > a.jb0[0] && y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] &&
@@ -450,36 +450,47 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                     if (a.dcb && i >= a.dbox[0] && i < a.dbox[0] + a.dbox[3] && j >= a.dbox[1] &&
                         j < a.dbox[1] + a.dbox[4] && k >= a.dbox[2] && k < a.dbox[2] + a.dbox[5])
                         cb = a.dcb[((long long)(k - a.dbox[2]) * a.dbox[4] + (j - a.dbox[1])) * a.dbox[3] + (i - a.dbox[0])];
-                    const bool drude = a.JD[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] &&
-                                       j < a.jbox[1] + a.jbox[4] && k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] &&
-                                       a.mat_db[midx] != T(0);
+                    const bool pole = a.JD && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] &&
+                                      j < a.jbox[1] + a.jbox[4] && k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5];
+                    // dispersive poles: each slot's ADE J^{n+1/2} = dk J^{n-1/2} + db E^n - dp P^n,
+                    // then P^{n+1} = P^n + dt J^{n+1/2} (Lorentz); the currents add up
                     T jd0 = T(0), jd1 = T(0), jd2 = T(0);
-                    if (drude) {
+                    if (pole) {
+                        const long long jc = a.jcnt;
                         const long long jq =
                             ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
-                        const T dk = a.mat_dk[midx], db = a.mat_db[midx];
-                        jd0 = dk * a.JD[0][jq] + db * eo0;
-                        jd1 = dk * a.JD[1][jq] + db * eo1;
-                        jd2 = dk * a.JD[2][jq] + db * eo2;
-                        // Lorentz pole: the restoring term -w0^2 P^n, then P^{n+1} = P^n + dt J^{n+1/2}
-                        const T dp = a.PD[0] ? a.mat_dp[midx] : T(0);
-                        if (dp != T(0)) {
-                            const T p0 = a.PD[0][jq], p1 = a.PD[1][jq], p2 = a.PD[2][jq];
-                            jd0 -= dp * p0;
-                            jd1 -= dp * p1;
-                            jd2 -= dp * p2;
-                            a.PD[0][jq] = p0 + a.dt * jd0;
-                            a.PD[1][jq] = p1 + a.dt * jd1;
-                            a.PD[2][jq] = p2 + a.dt * jd2;
+                        for (int p = 0; p < a.npole; p++) {
+                            const int mk = midx * ML_MAX_POLES + p;
+                            const T db = a.mat_db[mk];
+                            if (db == T(0)) break;  // a material's poles fill slots 0, 1, ...
+                            const T dk = a.mat_dk[mk];
+                            T *J = a.JD + 3 * p * jc + jq;
+                            T q0 = dk * J[0] + db * eo0;
+                            T q1 = dk * J[jc] + db * eo1;
+                            T q2 = dk * J[2 * jc] + db * eo2;
+                            const T dp = a.PD ? a.mat_dp[mk] : T(0);
+                            if (dp != T(0)) {
+                                T *P = a.PD + 3 * p * jc + jq;
+                                const T p0 = P[0], p1 = P[jc], p2 = P[2 * jc];
+                                q0 -= dp * p0;
+                                q1 -= dp * p1;
+                                q2 -= dp * p2;
+                                P[0] = p0 + a.dt * q0;
+                                P[jc] = p1 + a.dt * q1;
+                                P[2 * jc] = p2 + a.dt * q2;
+                            }
+                            J[0] = q0;
+                            J[jc] = q1;
+                            J[2 * jc] = q2;
+                            jd0 += q0;
+                            jd1 += q1;
+                            jd2 += q2;
                         }
-                        a.JD[0][jq] = jd0;
-                        a.JD[1][jq] = jd1;
-                        a.JD[2][jq] = jd2;
                     }
                     en0 = eo0 + cb * (curl0 - j0 - jd0);
                     en1 = eo1 + cb * (curl1 - j1 - jd1);
                     en2 = eo2 + cb * (curl2 - j2 - jd2);
-                    if (drude)
+                    if (pole)
                         absorbed += jd0 * (eo0 + en0) + jd1 * (eo1 + en1) + jd2 * (eo2 + en2);
                 }
                 if (walls) {
@@ -538,7 +549,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             sc = sn;
             if (++sn == S) { sn = 0; pn ^= 1u; }
         }
-        if (FULL && a.JD[0]) {
+        if (FULL && a.JD) {
             // fixed-order block reduction into this block's accumulator
             double ab = 0.5 * (double)a.dt * (double)absorbed;
             for (int q = 16; q > 0; q >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, q);
@@ -577,7 +588,7 @@ template <typename T>
 __device__ __forceinline__ bool interior_block(const YeeArgs<T> &a, const int tile) {
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
-    if (a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD[0] || a.nsrc)) return false;
+    if (a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD || a.nsrc)) return false;
     if (x0 == 0 || y0 == 0 || k0 == 0 || x0 + TX >= a.nx || y0 + TY >= a.ny || k1 >= a.nz) return false;
     if ((a.pml[0] && x0 - 1 < a.pml[0]) || (a.pml[1] && x0 + TX > a.nx - a.pml[1])) return false;
     if ((a.pml[2] && y0 - 1 < a.pml[2]) || (a.pml[3] && y0 + TY > a.ny - a.pml[3])) return false;
@@ -594,7 +605,7 @@ __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
     const bool img = (a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
                      (a.per[2] && (k0 == 0 || k1 == a.nz));
-    const bool gen = a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD[0] || a.nsrc);
+    const bool gen = a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD || a.nsrc);
     return (img || gen) ? 2 : 1;
 }
 

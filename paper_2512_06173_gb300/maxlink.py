@@ -29,8 +29,27 @@ EXPORTED = ["ml_last_error", "ml_version", "ml_grid_create", "ml_grid_destroy", 
             "ml_checkpoint", "ml_restore", "ml_set_timing", "ml_timing", "ml_launch_count"]
 
 
+ML_MAX_POLES = 4
+
+
+class ml_pole(C.Structure):
+    _fields_ = [("wp", C.c_double), ("gamma", C.c_double), ("omega0", C.c_double)]
+
+
 class ml_material(C.Structure):
-    _fields_ = [("eps_inf", C.c_double), ("wp", C.c_double), ("gamma", C.c_double), ("omega0", C.c_double)]
+    _fields_ = [("eps_inf", C.c_double), ("wp", C.c_double), ("gamma", C.c_double), ("omega0", C.c_double),
+                ("n_extra", C.c_int), ("extra", ml_pole * (ML_MAX_POLES - 1))]
+
+
+def _material(x) -> ml_material:
+    """workloads.Material -> ml_material (first pole, then the extra ones)."""
+    m = ml_material(x.eps_inf, x.wp, x.gamma, x.omega0)
+    if len(x.extra) > ML_MAX_POLES - 1:
+        raise ValueError(f"at most {ML_MAX_POLES} poles per material")
+    m.n_extra = len(x.extra)
+    for q, (wp, g, w0) in enumerate(x.extra):
+        m.extra[q] = ml_pole(wp, g, w0)
+    return m
 
 
 class ml_source(C.Structure):
@@ -401,7 +420,7 @@ def grid_desc(prob, precision: int = ML_F32):
         m = np.ascontiguousarray(prob.mat, np.uint8)
         keep.append(m)
         d.mat = _ptr(m)
-    mats = (ml_material * len(prob.materials))(*[ml_material(x.eps_inf, x.wp, x.gamma, x.omega0) for x in prob.materials])
+    mats = (ml_material * len(prob.materials))(*[_material(x) for x in prob.materials])
     keep.append(mats)
     d.n_materials = len(prob.materials)
     d.materials = mats

@@ -248,8 +248,8 @@ def dispersive_stack(nx: int = 512, ny: int = 512, nz: int = 256, nmol: int = 20
                      t0: float = 80.0) -> Problem:
     """Planar dispersive stack, periodic in x and y with CPML on the z faces: a
     `layer`-cell Lorentz dielectric (eps_inf 1.5, delta_eps 1, omega0 0.3, gamma 0.01)
-    centred in z on a `film`-cell Drude metal film (wp 1, gamma 0.05) that mirrors the
-    pulse; `nmol` ground-state two-level emitters (omega0 = 0.25, mu12 = 0.05 along x,
+    centred in z on a `film`-cell Drude-Lorentz metal film (Drude wp 1, gamma 0.05 plus
+    an interband Lorentz pole wp 0.5, omega0 0.6, gamma 0.1) that mirrors the pulse; `nmol` ground-state two-level emitters (omega0 = 0.25, mu12 = 0.05 along x,
     sigma = 1.5 cells) at seeded uniform positions in the middle of the Lorentz layer;
     an x-polarised Gaussian-pulse current sheet (omega 0.25, temporal `width`, centred at
     `t0`) near the lower CPML and
@@ -260,7 +260,7 @@ def dispersive_stack(nx: int = 512, ny: int = 512, nz: int = 256, nmol: int = 20
     mat = np.zeros((nz, ny, nx), np.uint8)
     mat[zc - layer // 2:zc + layer // 2] = 1
     mat[zc + layer // 2:zc + layer // 2 + film] = 2
-    materials = [Material(1.0), Material(1.5, wp=0.3, gamma=0.01, omega0=0.3), Material(1.0, wp=1.0, gamma=0.05)]
+    materials = [Material(1.0), Material(1.5, wp=0.3, gamma=0.01, omega0=0.3), Material(1.0, wp=1.0, gamma=0.05, extra=((0.5, 0.1, 0.6),))]
     xs = rng.uniform(0, nx, size=nmol)
     ys = rng.uniform(0, ny, size=nmol)
     zs = rng.uniform(zc - layer // 4, zc + layer // 4, size=nmol)
@@ -404,7 +404,8 @@ def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4
     """Small ragged problem for parity tests: every feature at once on a grid the
     oracle finishes in well under a second per hundred steps.  `drude` puts a Drude
     sphere at the centre; `lorentz` (with `drude`) turns its upper half (z above the
-    centre) into a Lorentz oscillator, so that one pole box holds both kinds."""
+    centre) into a three-pole medium (two Lorentz oscillators and a Drude term), so that
+    one pole box holds one- and three-pole cells."""
     rng = np.random.Generator(np.random.PCG64(1000 + seed))
     nx, ny, nz = shape
     pmls = tuple(0 if periodic[a // 2] else pml for a in range(6))
@@ -428,7 +429,8 @@ def small_coupled(seed: int = 0, shape=(24, 20, 28), nmol: int = 6, pml: int = 4
         inside = (xx + 0.5 - nx / 2) ** 2 + (yy + 0.5 - ny / 2) ** 2 + (zz + 0.5 - nz / 2) ** 2 < r * r
         mat[inside] = len(materials) - 1
         if lorentz:
-            materials.append(Material(1.5, wp=0.6, gamma=0.02, omega0=0.3))
+            materials.append(Material(1.5, wp=0.6, gamma=0.02, omega0=0.3,
+                                      extra=((0.4, 0.05, 0.55), (0.3, 0.1, 0.0))))
             mat[inside & (zz >= nz // 2)] = len(materials) - 1
     mats = []
     for m in range(nmol):

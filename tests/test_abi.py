@@ -50,7 +50,7 @@ def test_version_and_error_strings():
 def test_invalid_arguments_are_rejected_without_a_gpu():
     """Argument validation happens before any CUDA call."""
     from paper_2512_06173_gb300 import maxlink
-    from paper_2512_06173_gb300.workloads import Problem
+    from paper_2512_06173_gb300.workloads import Material, Problem
     d, keep = maxlink.grid_desc(Problem(8, 8, 8, 0.5))
     d.nx = 0
     with pytest.raises(maxlink.MaxlinkError) as e:
@@ -63,3 +63,13 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     d, keep = maxlink.grid_desc(Problem(8, 8, 8, 1.5))
     with pytest.raises(maxlink.MaxlinkError):
         maxlink.ml_grid_create(d)
+    # pole tables: too many poles, a negative resonance in an extra pole
+    d, keep = maxlink.grid_desc(Problem(8, 8, 8, 0.5, materials=[Material(1.0, 0.5, 0.1)]))
+    d.materials[0].n_extra = maxlink.ML_MAX_POLES
+    with pytest.raises(maxlink.MaxlinkError) as e:
+        maxlink.ml_grid_create(d)
+    assert e.value.status == maxlink.ML_ERR_INVALID_ARG
+    d, keep = maxlink.grid_desc(Problem(8, 8, 8, 0.5, materials=[Material(1.0, 0.5, 0.1, extra=((0.3, 0.1, -0.2),))]))
+    with pytest.raises(maxlink.MaxlinkError) as e:
+        maxlink.ml_grid_create(d)
+    assert "omega0" in str(e.value)

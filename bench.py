@@ -501,6 +501,57 @@ def measure_batch(args, stream):
             g.close()
 
 
+def measure_transfer(args, stream):
+    """Resonance energy transfer (Sec. IV.B setup with model acceptors): 64 independent
+    96^3 realisations, each a two-level donor (dipole 2, coherent state) and a
+    ground-state 2-, 4- or 8-level model acceptor (strongest dipole 0.02) 8-24 cells
+    apart in vacuum; args.transfer_steps steps as one batch (one launch per kernel class
+    per step, graph-replayed, field-pass grid from the autotuner).  Reports the batch's
+    cell and molecule throughput and, as a readout of the physics, the acceptors' mean
+    energy gain by model and the donors' mean excited population."""
+    import numpy as np
+    import torch
+    from paper_2512_06173_gb300 import maxlink, workloads
+
+    probs = workloads.energy_transfer_batch(count=args.transfer_count)
+    sh = stream.cuda_stream
+    K = args.transfer_steps
+    cells = sum(p.cells for p in probs)
+    grids = [maxlink.Grid(p, maxlink.ML_F32, stream=sh) for p in probs]
+    b = maxlink.Batch(grids, stream=sh)
+    try:
+        b.step(32)
+        choice, tune_ms = b.autotune(64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = b.launches
+        e0.record(stream)
+        b.step(K)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = b.launches - l0
+        gain, pe_d = {}, []
+        for g, p in zip(grids, probs):
+            n = int(p.molecules.nlev[1])
+            H = p.molecules.matrix(p.molecules.H0, 1)
+            gain.setdefault(n, []).append(float(np.real(np.trace(g.rho(1) @ H))))
+            pe_d.append(float(g.rho(0)[1, 1].real))
+        mol_steps = sum(p.molecules.count for p in probs) * K
+        return {"workload": f"{len(probs)} energy-transfer realisations, 96^3 vacuum, 10-cell CPML, two-level donor "
+                            f"(mu 2, coherent) + 2/4/8-level model acceptor (mu 0.02) 8-24 cells apart",
+                "instances": len(probs), "cells": cells, "molecules": int(sum(p.molecules.count for p in probs)),
+                "steps": K, "dtype": "f32", "ms_per_step": ms / K, "gcells_per_s": cells * K / ms / 1e6,
+                "molecule_steps_per_s": mol_steps / ms * 1e3, "blocks_per_sm": choice,
+                "batched_launches": int(launches),
+                "acceptor_gain_mean": {str(n): float(np.mean(v)) for n, v in sorted(gain.items())},
+                "donor_pe_mean": float(np.mean(pe_d))}
+    finally:
+        b.close()
+        for g in grids:
+            g.close()
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -512,7 +563,7 @@ def run_ours(args, world, rank, local):
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
         fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
-              "dispersive": measure_dispersive, "features": measure_features, "cavity": measure_cavity, "laser": measure_laser}[args.section]
+              "dispersive": measure_dispersive, "transfer": measure_transfer, "features": measure_features, "cavity": measure_cavity, "laser": measure_laser}[args.section]
         out = fn(args, torch.cuda.Stream())
         if rank == 0:
             print(json.dumps({"section": args.section, **out}), flush=True)
@@ -616,6 +667,7 @@ def run_ours(args, world, rank, local):
     batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
     bragg = measure_bragg(args, stream) if (world == 1 and not args.no_bragg) else None
     dispersive = measure_dispersive(args, stream) if (world == 1 and not args.no_dispersive) else None
+    transfer = measure_transfer(args, stream) if (world == 1 and not args.no_transfer) else None
     cavity = measure_cavity(args, stream) if (world == 1 and not args.no_cavity) else None
     laser = measure_laser(args, stream) if (world == 1 and not args.no_laser) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
@@ -647,6 +699,7 @@ def run_ours(args, world, rank, local):
             "batch": batch,
             "bragg": bragg,
             "dispersive": dispersive,
+            "transfer": transfer,
             "cavity": cavity,
             "laser": laser,
             "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
@@ -672,8 +725,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--traced-steps", type=int, default=1000,
                     help="steps of the traced pass that times each kernel (roofline)")
-    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "dispersive", "features", "cavity",
-                                                        "laser"],
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "dispersive", "transfer", "features",
+                                                        "cavity", "laser"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
@@ -689,6 +742,9 @@ def main():
     ap.add_argument("--bragg-steps", type=int, default=400)
     ap.add_argument("--no-dispersive", action="store_true", help="skip the dispersive stack")
     ap.add_argument("--dispersive-steps", type=int, default=400)
+    ap.add_argument("--no-transfer", action="store_true", help="skip the energy-transfer realisations")
+    ap.add_argument("--transfer-steps", type=int, default=2000)
+    ap.add_argument("--transfer-count", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

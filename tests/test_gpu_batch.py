@@ -29,6 +29,7 @@ def problems():
         W.small_coupled(2, shape=(40, 17, 33), nmol=9, periodic=(True, False, False)),
         W.small_coupled(3, shape=(19, 26, 21), nmol=3, eps_map=False, planes=False),
         W.small_coupled(4, shape=(33, 33, 18), nmol=5, drude=True, periodic=(False, True, True)),
+        W.small_coupled(5, shape=(29, 27, 31), nmol=4, drude=True, lorentz=True, eps_map=False),
     ]
 
 
@@ -132,6 +133,24 @@ def test_autotune_restores_state(ml):
             s = state(ml, g, p)
             for x, y in zip(s["fields"], r["fields"]):
                 assert np.array_equal(x, y)
+    finally:
+        for g in grids:
+            g.close()
+
+
+def test_energy_transfer_batch_matches_single_grids(ml):
+    """Donor-acceptor realisations (two-, four- and eight-level acceptors at several
+    distances), batched: bit-identical to stepping each grid alone."""
+    probs = W.energy_transfer_batch(count=5, edge=48)
+    steps = 70
+    ref = run_single(ml, probs, 0, steps)
+    grids = [ml.Grid(p, 0) for p in probs]
+    try:
+        b = ml.Batch(grids)
+        b.step(steps)
+        for g, p, r in zip(grids, probs, ref):
+            same(state(ml, g, p), r)
+        b.close()
     finally:
         for g in grids:
             g.close()

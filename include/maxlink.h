@@ -203,7 +203,9 @@ ml_status ml_flux(ml_grid *g, int id, double *out, void *stream);
  * (nfreq, n_c, n_b) complex) as interleaved doubles into host `out`. */
 ml_status ml_flux_data(ml_grid *g, int id, double *out, void *stream);
 
-/* Energy absorbed by Drude cells so far: sum J_D . (E^n + E^{n+1})/2 dt.  Host out. */
+/* Work done on the dispersive poles so far: sum over pole cells and poles of
+ * J_p . (E^n + E^{n+1})/2 dt (for a Drude pole the absorbed energy; a Lorentz pole's
+ * share includes the energy it stores).  Host out. */
 ml_status ml_absorbed(ml_grid *g, double *out, void *stream);
 
 /* Synchronise `stream` and return the latched device status (then clear it). */
@@ -228,8 +230,8 @@ ml_status ml_timing(ml_grid *g, double *ms, int64_t *counts);
 /* Number of kernels this grid has launched since creation (all classes). */
 int64_t ml_launch_count(const ml_grid *g);
 
-/* Checkpoint the full state (fields, CPML memory, Drude currents, molecules, DFT
- * accumulators, step count) into host_buf.  With host_buf == NULL only *bytes is
+/* Checkpoint the full state (fields, CPML memory, pole currents and polarisations,
+ * molecules, DFT accumulators, step count) into host_buf.  With host_buf == NULL only *bytes is
  * set to the size needed.  ml_restore takes a buffer written by ml_checkpoint of a
  * grid created with the same descriptor, molecules and planes. */
 ml_status ml_checkpoint(ml_grid *g, void *host_buf, size_t *bytes, void *stream);

@@ -72,3 +72,32 @@ def test_gain_is_second_order_in_each_dipole(oracle_mod, which):
     g1, g2 = _acceptor_gain(oracle_mod, p1, 300), _acceptor_gain(oracle_mod, p2, 300)
     assert g1 > 0
     assert abs(g2 / g1 - 4.0) < 2e-3
+
+
+def test_workload_generators_are_seeded_and_well_formed():
+    """The energy-transfer realisations repeat for a seed; each acceptor has a Hermitian
+    z-dipole, sorted levels from 0, the donor-resonant level with the strongest ground
+    dipole, and starts in the ground state; the donor starts in (1/sqrt 2, 1/sqrt 2)."""
+    a = W.energy_transfer_batch(count=12, edge=48)
+    b = W.energy_transfer_batch(count=12, edge=48)
+    assert [p.name for p in a] == [p.name for p in b]
+    assert {int(p.molecules.nlev[1]) for p in a} <= {2, 4, 8}
+    for p, q in zip(a, b):
+        m = p.molecules
+        assert np.array_equal(m.pos, q.molecules.pos) and np.array_equal(m.mu, q.molecules.mu)
+        assert np.array_equal(m.H0, q.molecules.H0)
+        n = int(m.nlev[1])
+        H = m.matrix(m.H0, 1)
+        E = np.real(np.diag(H))
+        assert E[0] == 0.0 and np.all(np.diff(E) >= 0)
+        mz = m.matrix(m.mu[2], 1)
+        assert np.allclose(mz, mz.conj().T, atol=0)
+        assert np.all(m.matrix(m.mu[0], 1) == 0) and np.all(m.matrix(m.mu[1], 1) == 0)
+        k = int(np.argmax(np.abs(mz[0])))
+        assert E[k] == 0.25 and abs(mz[0, k]) == 0.02
+        r = m.matrix(m.rho0, 1)
+        assert r[0, 0] == 1.0 and np.abs(r).sum() == 1.0
+        rd = m.matrix(m.rho0, 0)
+        assert np.allclose(rd, 0.5) and m.kind[1] == W.KIND_RK4
+        assert abs(m.pos[1, 0] - m.pos[0, 0] - float(p.name.split("-d")[1].split("-")[0])) < 1e-3
+        assert n == len(E)

@@ -372,10 +372,13 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                         store_img(a, a.Hn[1], i, j, k, hy[r]);
                         store_img(a, a.Hn[2], i, j, k, hz[r]);
                     } else {
+                        // the new level is not read again in this pass: streaming
+                        // (evict-first) stores leave L2 to the planes that neighbouring
+                        // tiles still read as halos
                         const long long g = pb + gb + r * a.px;
-                        a.Hn[0][g] = hx[r];
-                        a.Hn[1][g] = hy[r];
-                        a.Hn[2][g] = hz[r];
+                        __stcs(&a.Hn[0][g], hx[r]);
+                        __stcs(&a.Hn[1][g], hy[r]);
+                        __stcs(&a.Hn[2][g], hz[r]);
                     }
                 }
             }
@@ -506,9 +509,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                     store_img(a, a.En[2], i, j, k, en2);
                 } else {
                     const long long g = pb + gb + r * a.px;
-                    a.En[0][g] = en0;
-                    a.En[1][g] = en1;
-                    a.En[2][g] = en2;
+                    __stcs(&a.En[0][g], en0);
+                    __stcs(&a.En[1][g], en1);
+                    __stcs(&a.En[2][g], en2);
                 }
                 // ---- DFT flux planes through this cell: E^{n+1} and the mean of H^{n+1/2}
                 // on both sides of the plane, written to the current sample slot

@@ -454,8 +454,10 @@ def measure_batch(args, stream):
     """64 plasmonic realisations of uneven size (edges 64..160, 200-5000 emitters each):
     K steps as one batch (one launch per kernel class per step, graph-replayed, field-pass
     grid from the autotuner) against the same K steps with ml_step on each grid in turn
-    (the plain one-instance-per-launch method).  Both start from the same state; the
-    per-instance absorbed energies must agree exactly."""
+    (the plain one-instance-per-launch method).  Both start from the same state.  The
+    plain grids use the automatic short z chunks, the batched ones 16-plane chunks: the
+    fields do not depend on the chunking, the per-instance absorbed energies agree to
+    rounding (the per-block partial sums are grouped differently)."""
     import numpy as np
     import torch
     from paper_2512_06173_gb300 import maxlink, workloads
@@ -464,7 +466,9 @@ def measure_batch(args, stream):
     sh = stream.cuda_stream
     K = args.batch_steps
     cells = sum(p.cells for p in probs)
-    plain = [maxlink.Grid(p, maxlink.ML_F32, stream=sh) for p in probs]
+    # each method in its own best decomposition: a grid stepped alone needs the short
+    # automatic z chunks to fill the GPU, batched grids take the long ones
+    plain = [maxlink.Grid(p.replace(zchunk=0), maxlink.ML_F32, stream=sh) for p in probs]
     grids = [maxlink.Grid(p, maxlink.ML_F32, stream=sh) for p in probs]
     b = maxlink.Batch(grids, stream=sh)
     try:
@@ -493,7 +497,7 @@ def measure_batch(args, stream):
                 "plain_gcells": cells * K / plain_ms / 1e6, "batched_gcells": cells * K / batch_ms / 1e6,
                 "speedup": plain_ms / batch_ms, "blocks_per_sm": choice, "autotune_trial_ms": tune_ms,
                 "batched_launches": int(launches),
-                "absorbed_max_abs_diff": float(np.max(np.abs(ab_p - ab_b))),
+                "absorbed_max_rel_diff": float(np.max(np.abs(ab_p - ab_b) / np.maximum(np.abs(ab_p), 1e-300))),
                 "absorbed_sum": float(ab_b.sum())}
     finally:
         b.close()

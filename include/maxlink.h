@@ -100,6 +100,12 @@ typedef struct {
     const double *design_eps;   /* host (sz,sy,sx) relative permittivity, no Drude inside */
     int n_sources;              /* 0..ML_MAX_SOURCES */
     const ml_source *sources;
+    int zchunk;                 /* planes per z chunk of the field pass: 0 = automatic
+                                   (about 8 blocks per SM for this grid alone), >= 2 = that
+                                   length (longer chunks suit grids stepped in a batch,
+                                   where other grids fill the GPU); 1 or < 0 is
+                                   ML_ERR_INVALID_ARG.  The results do not depend on it
+                                   except the summation order of ml_absorbed. */
 } ml_grid_desc;
 
 /* Molecule table (Sec. II.B.1).  Matrices are n x n row-major complex numbers

@@ -162,6 +162,7 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     }
     if (d->n_sources < 0 || d->n_sources > ML_MAX_SOURCES || (d->n_sources && !d->sources))
         return fail(ML_ERR_INVALID_ARG, "0..4 sources");
+    if (d->zchunk < 0 || d->zchunk == 1) return fail(ML_ERR_INVALID_ARG, "zchunk must be 0 (automatic) or >= 2");
     for (int q = 0; q < d->n_sources; q++) {
         const ml_source &s = d->sources[q];
         if (s.axis < 0 || s.axis > 2 || s.comp < 0 || s.comp > 2 || s.comp == s.axis || s.index < 0 ||
@@ -211,9 +212,12 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         if (g->nz - zh > zlc) seg.push_back({zlc, g->nz - zh});
         if (zh > 0) seg.push_back({g->nz - zh, g->nz});
         int len = std::min(16, std::max(4, (g->nz + want - 1) / want));
-        // tuning knob: target planes per chunk (shorter chunks shrink the last
-        // wave of blocks, longer ones amortise the chunk's extra boundary plane)
-        if (const char *ev = std::getenv("ML_ZCHUNK")) {
+        // planes per chunk chosen by the caller (shorter chunks shrink the last wave of
+        // blocks, longer ones amortise the chunk's extra boundary planes and its ring
+        // fill), else the ML_ZCHUNK tuning knob
+        if (d->zchunk >= 2) {
+            len = d->zchunk;
+        } else if (const char *ev = std::getenv("ML_ZCHUNK")) {
             const int v = std::atoi(ev);
             if (v >= 2) len = v;
         }

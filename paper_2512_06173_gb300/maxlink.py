@@ -63,7 +63,8 @@ class ml_grid_desc(C.Structure):
                 ("pml_m", C.c_double), ("pml_sigma_max", C.c_double), ("pml_kappa_max", C.c_double),
                 ("pml_alpha_max", C.c_double), ("mat", C.c_void_p), ("n_materials", C.c_int),
                 ("materials", C.POINTER(ml_material)), ("design_box", C.c_int * 6),
-                ("design_eps", C.c_void_p), ("n_sources", C.c_int), ("sources", C.POINTER(ml_source))]
+                ("design_eps", C.c_void_p), ("n_sources", C.c_int), ("sources", C.POINTER(ml_source)),
+                ("zchunk", C.c_int)]
 
 
 class ml_molecule_desc(C.Structure):
@@ -416,6 +417,7 @@ def grid_desc(prob, precision: int = ML_F32):
         d.pml[f] = prob.pml[f]
     d.pml_m, d.pml_sigma_max = prob.pml_m, prob.pml_sigma_max
     d.pml_kappa_max, d.pml_alpha_max = prob.pml_kappa_max, prob.pml_alpha_max
+    d.zchunk = prob.zchunk
     if prob.mat is not None:
         m = np.ascontiguousarray(prob.mat, np.uint8)
         keep.append(m)

@@ -190,6 +190,7 @@ class Problem:
     molecules: Molecules = field(default_factory=empty_molecules)
     planes: List[FluxPlane] = field(default_factory=list)
     name: str = "custom"
+    zchunk: int = 0  # planes per z chunk of the field pass (0: automatic; see ml_grid_desc)
 
     @property
     def dt(self) -> float:
@@ -393,7 +394,9 @@ def plasmonic_batch(count: int = 64, seed: int = 5, edges=(64, 96, 128, 160), nm
     for _ in range(count):
         edge = int(rng.choice(edges))
         nmol = int(rng.integers(nmol_range[0], nmol_range[1] + 1))
-        out.append(plasmonic_instance(edge, nmol, rng))
+        # batched grids fill the GPU together: long z chunks (fewer boundary planes
+        # and ring fills per cell) beat the many short ones a lone grid needs
+        out.append(plasmonic_instance(edge, nmol, rng).replace(zchunk=16))
     return out
 
 
@@ -453,7 +456,7 @@ def energy_transfer_batch(count: int = 64, edge: int = 96, seed: int = 12, dista
     for q in range(count):
         d = float(rng.uniform(*distances))
         n = int(rng.choice(models))
-        out.append(energy_transfer(edge=edge, distance=d, n_acceptor=n, seed=seed * 1000 + q))
+        out.append(energy_transfer(edge=edge, distance=d, n_acceptor=n, seed=seed * 1000 + q).replace(zchunk=16))
     return out
 
 

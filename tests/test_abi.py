@@ -73,3 +73,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     with pytest.raises(maxlink.MaxlinkError) as e:
         maxlink.ml_grid_create(d)
     assert "omega0" in str(e.value)
+    d, keep = maxlink.grid_desc(Problem(8, 8, 8, 0.5, zchunk=1))
+    with pytest.raises(maxlink.MaxlinkError) as e:
+        maxlink.ml_grid_create(d)
+    assert "zchunk" in str(e.value)

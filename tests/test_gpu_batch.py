@@ -154,3 +154,24 @@ def test_energy_transfer_batch_matches_single_grids(ml):
     finally:
         for g in grids:
             g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_chunk_length_does_not_change_the_results(ml, precision):
+    """The z-chunk length of the field pass (automatic, 2, 5, 16 planes) changes the
+    blocks, not the arithmetic of a cell: fields and density matrices are bit-identical;
+    the absorbed energy, summed per block, agrees to rounding."""
+    base = W.small_coupled(0, shape=(37, 22, 29), nmol=6, drude=True, lorentz=True)
+    out = []
+    for z in (0, 2, 5, 16):
+        g = ml.Grid(base.replace(zchunk=z), precision)
+        try:
+            g.step(45)
+            out.append(state(ml, g, base))
+        finally:
+            g.close()
+    for o in out[1:]:
+        for x, y in zip(o["fields"], out[0]["fields"]):
+            assert np.array_equal(x, y)
+        assert np.array_equal(o["rho"], out[0]["rho"])
+        assert abs(o["absorbed"] - out[0]["absorbed"]) <= (1e-12 if precision else 1e-5) * abs(out[0]["absorbed"])

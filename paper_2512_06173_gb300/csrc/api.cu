@@ -360,7 +360,7 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     }
     {
         // tiles whose own cells need the per-cell material path: a non-background
-        // material, the design box, the Drude box or a source plane
+        // material, the design box, the pole box or a source plane
         std::vector<int> zt(g->nz);
         for (int c = 0; c < g->nchunk; c++)
             for (int k = g->zcut[c]; k < g->zcut[c + 1]; k++) zt[k] = c;

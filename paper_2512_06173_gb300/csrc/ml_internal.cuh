@@ -12,9 +12,11 @@
 //     (pml_lo + pml_hi) cells along a, two H-side components (double-buffered,
 //     because neighbouring tiles recompute halo H from them) and two E-side
 //     components (updated in place by the owning cell).
-//   * per-cell uint8 material index, a continuous-eps design box, a Drude box.
+//   * per-cell uint8 material index, a continuous-eps design box, a pole box (pole
+//     currents and, for Lorentz poles, polarisations per pole slot).
 //   * molecule tables (SoA), per-molecule separable kernel weights, and the
-//     tile-binned molecule lists that make the current scatter deterministic.
+//     per-block entry lists of the current box (each molecule window meeting a
+//     block, in a fixed order) that make the current scatter deterministic.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>

@@ -8,11 +8,12 @@
 //   * CPML (Roden-Gedney recursive convolution, Taflove & Hagness Ch. 7) on the
 //     curl terms whose derivative runs across a layer,
 //   * the per-cell coefficient dt/eps (Eq. Dromega; material table or design box),
-//   * the Drude auxiliary current in Drude cells,
+//   * the dispersive poles of the pole box (Drude and Lorentz, up to four per
+//     material, each its own auxiliary-differential equation; currents summed),
 //   * soft current-sheet sources,
 //   * the molecular current J = sum_m gamma_m mudot_m kappa_m (Eq. J_mol with
-//     Eq. Polarization_mol), summed per cell in the fixed order of the tile's
-//     binned molecule list (deterministic, no atomics).
+//     Eq. Polarization_mol), read from the box the current kernel wrote this step
+//     (deterministic there, no atomics).
 // E and H are read from one time level and written to the other, so tiles never
 // race.  E^n planes are staged in shared memory (k and k+1 with halo); H^{n+1/2}
 // of plane k with its low halo lives in shared memory for the E update, the own
@@ -147,7 +148,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const bool img = FULL && ((a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
                              (a.per[2] && (k0 == 0 || k1 == a.nz)));
     const bool walls = GEN && ((!a.per[0] && x0 == 0) || (!a.per[1] && y0 == 0) || (!a.per[2] && k0 == 0));
-    // per-cell material work (material table, design box, Drude, sources): only tiles
+    // per-cell material work (material table, design box, poles, sources): only tiles
     // whose own cells need it, when the grid has the per-tile flags
     const bool general = FULL && (a.tflags ? (a.tflags[tile] & 1) != 0
                                           : (a.mat != nullptr || a.dcb != nullptr || a.JD != nullptr || a.nsrc > 0));

@@ -77,3 +77,35 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     with pytest.raises(maxlink.MaxlinkError) as e:
         maxlink.ml_grid_create(d)
     assert "zchunk" in str(e.value)
+
+
+def test_header_is_plain_c_and_the_binding_matches_its_layouts(tmp_path):
+    """include/maxlink.h compiles as C99 with warnings as errors, and every descriptor
+    struct the binding mirrors has the same size and field offsets in C and in ctypes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2512_06173_gb300 import maxlink
+    structs = {"ml_pole": maxlink.ml_pole, "ml_material": maxlink.ml_material, "ml_source": maxlink.ml_source,
+               "ml_grid_desc": maxlink.ml_grid_desc, "ml_molecule_desc": maxlink.ml_molecule_desc,
+               "ml_cavity_desc": maxlink.ml_cavity_desc, "ml_drive_desc": maxlink.ml_drive_desc}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "maxlink.h"', "int main(void) {"]
+    for s, cls in structs.items():
+        lines.append(f'    printf("{s} %zu\\n", sizeof({s}));')
+        for f, _ in cls._fields_:
+            lines.append(f'    printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for s, cls in structs.items():
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"

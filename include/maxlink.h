@@ -144,7 +144,9 @@ enum { ML_EX = 1, ML_EY = 2, ML_EZ = 4, ML_HX = 8, ML_HY = 16, ML_HZ = 32, ML_AL
 /* Message of the last failure on this thread ("" if none).  Never NULL. */
 const char *ml_last_error(void);
 
-/* Version string of the library build. */
+/* Version string of the library build.  0.2: ml_material carries up to ML_MAX_POLES
+ * dispersive poles (omega0, n_extra, extra[]) and ml_grid_desc ends with zchunk; a
+ * caller built against 0.1 descriptors must be rebuilt. */
 const char *ml_version(void);
 
 /* Create a grid (Eq. Maxwell on a Yee lattice, Eq. Dromega per cell), zero fields.

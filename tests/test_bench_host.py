@@ -1,0 +1,40 @@
+"""Host-side arithmetic of bench.py that the reported roofline rests on: the
+algorithmic bytes of one field-pass launch, checked against hand counts."""
+import os
+import sys
+
+import numpy as np
+
+from paper_2512_06173_gb300.workloads import Material, Problem
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_vacuum_and_cpml_bytes():
+    # E and H read and written: 12 values per cell
+    assert bench.field_pass_bytes(Problem(10, 12, 14, 0.5), 4) == 48 * 10 * 12 * 14
+    assert bench.field_pass_bytes(Problem(10, 12, 14, 0.5), 8) == 96 * 10 * 12 * 14
+    # four CPML memories read and written per cell and layer axis: 2 + 3 x-layers on a
+    # 10-wide grid cover 5 of its 10 columns, the 4 z-layers 4 of 14 planes
+    p = Problem(10, 12, 14, 0.5, pml=(2, 3, 0, 0, 4, 0))
+    N = 10 * 12 * 14
+    assert bench.field_pass_bytes(p, 4) == 48 * N + 32 * (5 * 12 * 14) + 32 * (10 * 12 * 4)
+
+
+def test_material_and_pole_bytes():
+    n = 6
+    mat = np.zeros((n, n, n), np.uint8)
+    mat[0] = 1  # 36 Drude cells
+    mat[1] = 2  # 36 Lorentz cells
+    mat[2] = 3  # 36 cells with a Drude and two Lorentz poles
+    mats = [Material(1.0), Material(1.0, 1.0, 0.1), Material(2.0, 0.5, 0.1, 0.4),
+            Material(1.0, 0.7, 0.1, extra=((0.3, 0.1, 0.5), (0.2, 0.05, 0.9)))]
+    p = Problem(n, n, n, 0.5, mat=mat, materials=mats)
+    N = n ** 3
+    # per pole 6 values for J (3 read + 3 written), per Lorentz pole 6 more for P
+    want = 48 * N + N + 36 * (24) + 36 * (24 + 24) + 36 * (3 * 24 + 2 * 24)
+    assert bench.field_pass_bytes(p, 4) == want
+    # a design box adds one coefficient per cell
+    q = Problem(n, n, n, 0.5, design_box=(1, 1, 1, 2, 3, 4), design_eps=np.ones((4, 3, 2)))
+    assert bench.field_pass_bytes(q, 4) == 48 * N + 4 * 24

@@ -9,6 +9,12 @@
     reactive near field of a narrow kernel acts half a step late; the resulting rate
     error is first order in dt and grows like 1/sigma^3.  The pins use sigma = 2
     (3 % off at Courant 0.5) and check the first-order convergence at sigma = 1.
+  * Strong excitation: the emitter radiates a classical field, so its power follows
+    |rho_ge|^2 = P_e P_g and the population obeys the logistic law dP_e/dt = -gamma
+    P_e P_g; it matches the quantum exponential decay only in the weak-excitation
+    limit, as the paper states.  From P_e = 0.9 the logit log(P_e / P_g) falls
+    linearly at the weak-excitation rate, while the exponential rate -d log P_e / dt
+    grows from about 0.1 gamma to gamma.
   * Superradiance (Eq. population_decay_superradiance): N co-located identical
     emitters evolve exactly like one emitter with coupling rescale sqrt(N) (the
     discrete identity behind the N-fold rate), and the ensemble decays N times faster.
@@ -62,6 +68,28 @@ def test_3d_fermi_golden_rule(oracle_mod):
     g = decay_rate(t, pe)
     want = w ** 3 * mu ** 2 / (3 * np.pi) * np.exp(-w ** 2 * sigma ** 2)
     assert abs(g / want - 1) < 0.05, g / want
+
+
+def test_2d_strong_excitation_follows_the_logistic_law(oracle_mod):
+    mu, w, sigma = 0.5, 0.25, 1.0
+    want = mu ** 2 * w ** 2 / 2 * np.exp(-w ** 2 * sigma ** 2)
+    t, pe, _ = run_emitters(oracle_mod, 2, 100, mu, sigma, 700, ce=np.sqrt(0.9))
+    tw, pw, _ = run_emitters(oracle_mod, 2, 100, mu, sigma, 400)
+    weak = decay_rate(tw, pw)
+    sel = (pe < 0.85) & (pe > 0.15)
+    logit = np.log(pe[sel] / (1 - pe[sel]))
+    fit = np.polyfit(t[sel], logit, 1)
+    g = -fit[0]
+    assert abs(g / weak - 1) < 0.03, (g, weak)
+    assert abs(g / want - 1) < 0.06, g / want
+    assert np.abs(logit - np.polyval(fit, t[sel])).max() < 0.05
+
+    def exp_rate(hi, lo):
+        s = (pe < hi) & (pe > lo)
+        return -np.polyfit(t[s], np.log(pe[s]), 1)[0]
+
+    # an exponential law would give one rate; the logistic one starts near gamma P_g
+    assert exp_rate(0.85, 0.75) < 0.3 * g and exp_rate(0.25, 0.15) > 0.7 * g
 
 
 @pytest.mark.slow

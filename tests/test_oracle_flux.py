@@ -11,6 +11,9 @@
     one cell: the exact solution of the continuous uniform-field equations (matrix
     exponential), energy bookkeeping over all poles, and two half-strength poles equal
     to one full-strength pole.
+  * Poynting closure: the energy a dispersive layer absorbs (time-domain work on its
+    poles) equals the net DFT flux into it integrated over frequency (Parseval), to
+    second order in dt.
 """
 import numpy as np
 import pytest
@@ -187,3 +190,38 @@ def test_split_pole_equals_one_pole(oracle_mod):
     for x, y in zip(fa, fb):
         assert np.abs(x - y).max() < 1e-12 * scale
     assert abs(a.absorbed() - b.absorbed()) < 1e-12 * abs(a.absorbed())
+
+
+def _closure(oracle_mod, dt, materials):
+    """Energy absorbed by a dispersive layer, two ways: the oracle's time-domain work on
+    the poles, and the net DFT flux into the layer integrated over frequency (Parseval:
+    integral of E x H over time = (1/pi) integral over w > 0 of Re(E~ x H~*))."""
+    nz = 200
+    mat = np.zeros((nz, 1, 1), np.uint8)
+    mat[90:96] = 1
+    om = np.linspace(0.0, 0.7, 281)  # the pulse's spectrum is negligible above 0.7
+    p = Problem(1, 1, nz, dt, periodic=(True, True, False), pml=(0, 0, 0, 0, 12, 12), mat=mat,
+                materials=materials,
+                sources=[Source(axis=2, index=16, comp=0, amp=1.0, omega=0.25, width=12.0, t0=72.0)],
+                planes=[FluxPlane(2, 60, om), FluxPlane(2, 130, om)])
+    sim = oracle_mod.OracleSim(p)
+    sim.step(int(round(1500 / dt)))
+    trap = getattr(np, "trapezoid", None) or getattr(np, "trapz")
+    into = trap(sim.flux(0) - sim.flux(1), om) / np.pi
+    return sim.absorbed(), into
+
+
+def test_poynting_closure_of_an_absorbing_layer(oracle_mod):
+    """A pulse through a 6-cell layer (1 x 1 periodic cross-section): the energy the
+    poles absorbed equals the net flux into the layer, to second order in dt (E is
+    sampled at whole steps, H at half steps), for a Drude layer and for a Drude + Lorentz
+    layer (whose reversibly stored energy has rung down by the end of the run)."""
+    drude = [Material(1.0), Material(1.0, 1.0, 0.05)]
+    a1, f1 = _closure(oracle_mod, 0.5, drude)
+    a2, f2 = _closure(oracle_mod, 0.25, drude)
+    assert a1 > 0.1
+    e1, e2 = abs(f1 / a1 - 1), abs(f2 / a2 - 1)
+    assert e1 < 5e-3 and 3.0 < e1 / e2 < 5.0, (e1, e2)
+    multi = [Material(1.0), Material(1.5, 0.6, 0.05, 0.3, extra=((0.5, 0.1, 0.0),))]
+    a3, f3 = _closure(oracle_mod, 0.5, multi)
+    assert a3 > 0.1 and abs(f3 / a3 - 1) < 5e-3

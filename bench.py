@@ -203,7 +203,8 @@ def run_reference(args, world, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": prob.cells, "molecules": prob.molecules.count},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} full steps of the 256^3 workload with all 10000 emitters"},
+                             "sample": f"{n} full steps of the {prob.nx}^3 workload with all "
+                                       f"{prob.molecules.count} emitters"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

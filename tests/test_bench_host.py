@@ -38,3 +38,23 @@ def test_material_and_pole_bytes():
     # a design box adds one coefficient per cell
     q = Problem(n, n, n, 0.5, design_box=(1, 1, 1, 2, 3, 4), design_eps=np.ones((4, 3, 2)))
     assert bench.field_pass_bytes(q, 4) == 48 * N + 4 * 24
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one JSON line
+    with the keys the contract asks for; run here on a small cube for speed."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--edge", "64",
+                        "--nmol", "20", "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["value"] > 0 and d["unit"] == "Gcell-updates/s" and d["steps"] >= 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "64^3" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -1,12 +1,16 @@
 """Benchmark of the coupled Yee / molecular-ensemble step on GB300.
 
-Workload (one step = the whole hot path: molecule gather + density-matrix step +
-current scatter + fused H/E pass with CPML + DFT flux planes): the superradiant
-slab, a 256^3 vacuum grid with 10-cell CPML on every face, 10,000 two-level
-emitters (omega0 = 0.25, mu12 = 0.02 along z, sigma = 1.5 cells, pure dephasing
-1e-5) at seeded positions in a 32-cell central slab, all excited with a seeded
-1e-3 coherence, and two 8-frequency flux planes.  FP32 fields and molecules,
-FP64 DFT and energy accumulators.  Synthetic, seeded inputs.
+Headline workload (one step = the whole hot path: molecule window gather + density-
+matrix step + current scatter + fused H/E pass with CPML, material map and source +
+DFT flux planes): the Bragg-resonator ensemble, 512 x 512 x 384 cells with 10-cell CPML
+on every face, a 12-layer quarter-wave stack (eps 2.25 / 1, 4 / 6 cells) along x split
+around a 32-cell central slab holding 100,000 multilevel Lindblad systems (2..8 levels,
+RK4; Hermitian z-dipoles with N(0, 0.01) entries, ladders 0.2 +- 5 %, decay rates
+log-uniform in [1e-6, 1e-4], sigma = 1.5 cells), a z-polarised Gaussian-pulse sheet and
+two 8-frequency flux planes; 8000 steps.  FP32 fields and molecules, FP64 DFT and
+energy accumulators.  Synthetic, seeded inputs standing in for the Bragg resonator of
+Sec. IV.C.  The other workloads (the 256^3 superradiant slab, the adjoint, batches,
+dispersive media, energy transfer, cavity, laser drive) are sections of the same line.
 
   python bench.py [--gpus N --steps K --warmup W]      our CUDA path (C ABI)
   python bench.py --impl reference ...                  the FP64 CPU oracle
@@ -31,24 +35,44 @@ if ROOT not in sys.path:
 
 METRIC = "coupled Yee Gcell-updates/s"
 UNIT = "Gcell-updates/s"
-WORKLOAD = ("superradiant slab: 256^3 vacuum, 10-cell CPML all faces, 10000 two-level emitters "
-            "(w0=0.25, mu12=0.02 z, sigma=1.5, dephasing 1e-5) in a 32-cell central slab, "
-            "2 flux planes x 8 frequencies")
 
 
-# DRAM bytes (read + write) per field-pass launch on this workload, from one ncu
-# capture (profiles/yee_kernel_superradiant.md); valid only for the source it was
-# measured on, identified by the sha256 prefix of yee.cu.
-FIELD_PASS_TRAFFIC = {"11ee3233b2bc7b8b": 1.0614e9}
+def headline_problem(args, rank: int = 0):
+    from paper_2512_06173_gb300 import workloads
+    nx, ny, nz = args.bragg_shape
+    return workloads.bragg_ensemble(nx=nx, ny=ny, nz=nz, nmol=args.bragg_nmol, seed=3 + rank)
 
 
-def field_pass_traffic(edge: int, nmol: int):
+def workload_text(prob) -> str:
+    return (f"Bragg-resonator ensemble: {prob.nx}x{prob.ny}x{prob.nz} cells, 10-cell CPML on all faces, "
+            f"12 quarter-wave layers (eps 2.25 / 1, 4 / 6 cells) along x around a 32-cell central slab, "
+            f"{prob.molecules.count} multilevel Lindblad systems (2-8 levels, RK4; z-dipoles N(0,0.01), "
+            f"ladders 0.2+-5%, decay log-U[1e-6,1e-4], sigma 1.5) in the slab, z-polarised Gaussian-pulse "
+            f"sheet, 2 flux planes x 8 frequencies")
+
+
+def config_of(prob, world: int) -> dict:
+    level_gb = 6 * prob.cells * 4 / 1e9
+    return {"workload": workload_text(prob), "cells": prob.cells, "molecules": prob.molecules.count,
+            "grid": [prob.nx, prob.ny, prob.nz],
+            "l2": f"inputs larger than L2 (fields {level_gb:.2f} GB per time level)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+# DRAM bytes (read + write) per field-pass launch, from one ncu capture of
+# `yee_kernel` (dram__bytes_read.sum + dram__bytes_write.sum, --clock-control none) on
+# the named workload; valid only for the source it was measured on, identified by the
+# sha256 prefix of yee.cu.
+FIELD_PASS_TRAFFIC = {
+    ("superradiant-slab-256^3-10000tls", "11ee3233b2bc7b8b"): 1.0614e9,
+}
+
+
+def field_pass_traffic(prob):
     import hashlib
-    if edge != 256 or nmol != 10000:
-        return None
     src = os.path.join(ROOT, "paper_2512_06173_gb300", "csrc", "yee.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return FIELD_PASS_TRAFFIC.get(h)
+    return FIELD_PASS_TRAFFIC.get((prob.name, h))
 
 
 def peaks():
@@ -177,34 +201,37 @@ def allreduce_sum(world, x: float) -> float:
 
 
 def cpu_oracle_run(prob, budget_s: float, max_steps: int, warm: int = 1):
-    """Time the FP64 oracle as it stands on this host's cores on the same workload."""
+    """Time the FP64 oracle as it stands on this host's cores on the same workload:
+    `warm` untimed steps, then as many full steps as fit in about `budget_s` seconds
+    (at least 2, at most max_steps).  Building the oracle's arrays is not timed."""
     import oracle
     sim = oracle.OracleSim(prob)
     t0 = time.perf_counter()
-    sim.step(warm)
+    sim.step(max(warm, 1))
     t_one = (time.perf_counter() - t0) / max(warm, 1)
     n = max(2, min(max_steps, int(budget_s / max(t_one, 1e-6))))
     t0 = time.perf_counter()
     sim.step(n)
     dt = time.perf_counter() - t0
+    del sim
     return n, dt, oracle.threads()
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 CPU oracle, rank 0 only, bounded sample."""
+    """Reference arm: the FP64 CPU oracle, rank 0 only, on the headline workload: W
+    warm-up steps, then a bounded sample of full steps (about args.ref_budget seconds)."""
     if rank != 0:
         return
-    from paper_2512_06173_gb300 import workloads
-    prob = workloads.superradiant_slab(n=args.edge, nmol=args.nmol, seed=2)
-    n, dt, cores = cpu_oracle_run(prob, budget_s=45.0, max_steps=args.steps, warm=max(1, min(args.warmup, 1)))
+    prob = headline_problem(args, 0)
+    n, dt, cores = cpu_oracle_run(prob, budget_s=args.ref_budget, max_steps=args.steps, warm=args.warmup)
     value = prob.cells * n / dt / 1e9
+    sample = (f"{n} full steps (after {args.warmup} warm-up steps) of the {prob.nx}x{prob.ny}x{prob.nz} "
+              f"workload with all {prob.molecules.count} systems, FP64, oracle as it stands")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": n, "warmup": 1, "ms_per_step": dt / n * 1e3, "higher_is_better": True,
+            "steps": n, "warmup": args.warmup, "ms_per_step": dt / n * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": prob.cells, "molecules": prob.molecules.count},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} full steps of the {prob.nx}^3 workload with all "
-                                       f"{prob.molecules.count} emitters"},
+            "config": config_of(prob, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -261,13 +288,22 @@ def measure_bragg(args, stream):
     import torch
     from paper_2512_06173_gb300 import maxlink, workloads
 
-    prob = workloads.bragg_ensemble()
+    nx, ny, nz = args.bragg_shape
+    prob = workloads.bragg_ensemble(nx=nx, ny=ny, nz=nz, nmol=args.bragg_nmol)
     sh = stream.cuda_stream
     g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
     K = args.bragg_steps
     try:
         g.step(5)
         g.sync()
+        # untraced: the launch chain overlaps as it does for a user
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        g.step(K)
+        u1.record(stream)
+        stream.synchronize()
+        g.sync()
+        ms_untraced = u0.elapsed_time(u1)
         maxlink.ml_set_timing(g.h, True)
         maxlink.ml_timing(g.h)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -284,7 +320,8 @@ def measure_bragg(args, stream):
         alg = field_pass_bytes(prob, 4)
         return {"workload": prob.name, "cells": prob.cells, "molecules": prob.molecules.count, "steps": K,
                 "dtype": "f32", "gcells_per_s": prob.cells * K / ms / 1e6,
-                "molecule_steps_per_s": prob.molecules.count * K / ms * 1e3, "ms_per_step": ms / K,
+                "molecule_steps_per_s": prob.molecules.count * K / ms * 1e3, "ms_per_step_traced": ms / K,
+                "ms_per_step": ms_untraced / K, "gcells_per_s_untraced": prob.cells * K / ms_untraced / 1e6,
                 "field_pass": {"ms_per_step": fp, "alg_bytes": alg, "achieved_gbs": alg / (fp / 1e3) / 1e9,
                                "frac": alg / (fp / 1e3) / 1e9 / hbm, "peak": hbm, "peak_kind": peak_kind},
                 "kernel_ms_per_step": {"molecules": kms[0] / K, "current": kms[4] / K, "field_pass": fp,
@@ -557,181 +594,213 @@ def measure_transfer(args, stream):
             g.close()
 
 
-def run_ours(args, world, rank, local):
+def gpu_index_of(local: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            return int(vis.split(",")[local])
+        except ValueError:
+            pass
+    return local
+
+
+def measure_coupled(prob, args, stream, world, rank, local, K, W, with_clocks=True, with_e2e=True):
+    """Whole-hot-path throughput of one workload: W warm-up steps, then K steps timed with
+    CUDA events on the launching stream between barriers (untraced, so the programmatic
+    launch chain overlaps as it does for a user), then a traced pass (events around every
+    launch) for the per-kernel split and the field pass's roofline, then the end-to-end leg
+    through the C ABI with host buffers."""
     import numpy as np
     import torch
-    from paper_2512_06173_gb300 import maxlink, workloads
+    from paper_2512_06173_gb300 import maxlink
+
+    sh = stream.cuda_stream
+    esz = 4
+    g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    out = {}
+    try:
+        g.step(W)
+        g.sync()
+        sampler = ClockSampler(gpu_index_of(local)) if (rank == 0 and with_clocks) else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        launches0 = maxlink.ml_launch_count(g.h)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(K)
+        e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        out["clocks"] = sampler.stop() if sampler else None
+        out["launches"] = maxlink.ml_launch_count(g.h) - launches0
+        ms = e0.elapsed_time(e1)
+        g.sync()
+        # traced pass right after the timed region: CUDA events around every launch on the
+        # launching stream give each kernel's average duration (the events separate the
+        # kernels, so they do not overlap here as they do in the timed region)
+        KT = max(1, min(K, args.traced_steps))
+        maxlink.ml_set_timing(g.h, True)
+        maxlink.ml_timing(g.h)  # clear
+        g.step(KT)
+        g.sync()
+        kms, kcnt = maxlink.ml_timing(g.h)
+        maxlink.ml_set_timing(g.h, False)
+        ms_max = allreduce_max(world, ms)
+        cells_total = allreduce_sum(world, float(prob.cells) * K)
+        out["ms_per_step"] = ms_max / K
+        out["value"] = cells_total / (ms_max / 1e3) / 1e9
+        out["molecule_steps_per_s"] = allreduce_sum(world, float(prob.molecules.count) * K) / (ms_max / 1e3)
+        hbm, peak_kind = peaks()
+        k1_ms = kms[1] / KT
+        alg = field_pass_bytes(prob, esz)
+        achieved = alg / (k1_ms / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": "yee_kernel (fused H/E + CPML + material + source + current "
+                                                      "read + plane sampling)",
+                           "timing": f"CUDA events around each launch on the launching stream, traced pass of {KT} "
+                                     f"steps after the timed region",
+                           "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                           "frac": achieved / hbm, "traffic": field_pass_traffic(prob), "alg_bytes_per_step": alg,
+                           "field_pass_ms_per_step": k1_ms, "launches_per_step": kcnt[1] / KT}
+        out["kernel_ms_per_step"] = {"molecules": kms[0] / KT, "current": kms[4] / KT, "field_pass": k1_ms,
+                                     "plane_fold": kms[3] / KT}
+        pops = g.molecules(maxlink.ML_MOL_POP)
+        flux = [g.flux(p) for p in range(len(prob.planes))]
+        out["check"] = {"pop_excited_mean": float(np.mean(1.0 - pops[:, 0])), "flux_plane0_f0": float(flux[0][0])}
+    finally:
+        g.close()
+    if not with_e2e:
+        return out
+    # ---- end to end through the C ABI with host buffers: every step's inputs are the
+    # previous step's state on the device; the initial fields come from pinned host memory
+    # inside the timed region, each step's populations reach pinned host memory through the
+    # population sink, and the spectra are read at the end
+    N = prob.cells
+    g2 = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
+    try:
+        host_fields = torch.zeros((6, N), dtype=torch.float32, pin_memory=True)
+        ring = 2
+        host_pop = torch.zeros((ring * prob.molecules.count * maxlink.ML_MAX_LEVELS,), dtype=torch.float64,
+                               pin_memory=True)
+        maxlink.ml_set_population_sink(g2.h, host_pop.data_ptr(), ring)
+        g2.step(W)
+        g2.sync()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        maxlink.ml_set_fields(g2.h, maxlink.ML_ALL, host_fields.data_ptr(), False, sh)
+        for _ in range(K):
+            maxlink.ml_step(g2.h, 1, sh)
+        fl = [g2.flux(p) for p in range(len(prob.planes))]
+        stream.synchronize()
+        e2e_s = allreduce_max(world, time.perf_counter() - t0)
+        g2.sync()
+        last = (maxlink.ml_step_count(g2.h) - 1) % ring
+        pe_e2e = float(1.0 - host_pop.view(ring, prob.molecules.count, maxlink.ML_MAX_LEVELS)[last, :, 0].mean())
+        maxlink.ml_set_population_sink(g2.h, 0, 1)
+        h2d = 6 * N * esz / K
+        # the populations written to the host each step (nlev doubles per molecule) and the
+        # spectra read once at the end
+        d2h = int(prob.molecules.nlev.sum()) * 8 + sum(8 * len(p.omegas) for p in prob.planes) / K
+        out["e2e"] = {"value": allreduce_sum(world, float(N) * K) / e2e_s / 1e9, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        out["check"]["e2e_flux_plane0_f0"] = float(fl[0][0])
+        out["check"]["e2e_pop_excited_mean"] = pe_e2e
+    finally:
+        g2.close()
+    return out
+
+
+def measure_superradiant(args, stream):
+    """Superradiant slab (256^3 vacuum, 10-cell CPML, 10,000 two-level emitters in a
+    32-cell central slab, two flux planes): the coupled step and its field pass's roofline,
+    args.sr_steps steps after 20 warm-up steps."""
+    from paper_2512_06173_gb300 import workloads
+    prob = workloads.superradiant_slab(n=args.edge, nmol=args.nmol, seed=2)
+    r = measure_coupled(prob, args, stream, 1, 0, 0, args.sr_steps, 20, with_clocks=False, with_e2e=False)
+    return {"workload": prob.name, "cells": prob.cells, "molecules": prob.molecules.count, "steps": args.sr_steps,
+            "dtype": "f32", "gcells_per_s": r["value"], "ms_per_step": r["ms_per_step"],
+            "molecule_steps_per_s": r["molecule_steps_per_s"], "roofline": r["roofline"],
+            "kernel_ms_per_step": r["kernel_ms_per_step"], "gpu_launches": r["launches"]}
+
+
+def run_ours(args, world, rank, local):
+    import torch
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU for the CUDA path")
     torch.cuda.set_device(local)
+    sections = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
+                "superradiant": measure_superradiant, "dispersive": measure_dispersive,
+                "transfer": measure_transfer, "features": measure_features, "cavity": measure_cavity,
+                "laser": measure_laser}
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
-        fn = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
-              "dispersive": measure_dispersive, "transfer": measure_transfer, "features": measure_features, "cavity": measure_cavity, "laser": measure_laser}[args.section]
-        out = fn(args, torch.cuda.Stream())
+        out = sections[args.section](args, torch.cuda.Stream())
         if rank == 0:
             print(json.dumps({"section": args.section, **out}), flush=True)
         return
-    prob = workloads.superradiant_slab(n=args.edge, nmol=args.nmol, seed=2 + rank)
+    prob = headline_problem(args, rank)
     stream = torch.cuda.Stream()
-    sh = stream.cuda_stream
-    g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
-    esz = 4
     K, W = args.steps, args.warmup
-    # ---- device-resident timed region
-    g.step(W)
-    g.sync()
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except ValueError:
-            pass
-    sampler = ClockSampler(gpu_index) if rank == 0 else None
-    if sampler:
-        sampler.start()
-        time.sleep(0.3)
-    launches0 = maxlink.ml_launch_count(g.h)
-    barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    g.step(K)
-    e1.record(stream)
-    stream.synchronize()
-    torch.cuda.synchronize()
-    barrier(world)
-    clocks = sampler.stop() if sampler else None
-    launches = maxlink.ml_launch_count(g.h) - launches0
-    ms = e0.elapsed_time(e1)
-    g.sync()
-    # ---- traced pass of the same workload right after the timed region: CUDA events
-    # around every launch on the launching stream give each kernel's average duration.
-    # The events separate the kernels, so the current kernel and the field pass do not
-    # overlap here as they do in the timed region.
-    KT = min(K, args.traced_steps)
-    maxlink.ml_set_timing(g.h, True)
-    maxlink.ml_timing(g.h)  # clear
-    g.step(KT)
-    g.sync()
-    kms, kcnt = maxlink.ml_timing(g.h)
-    maxlink.ml_set_timing(g.h, False)
-    kms = [v * K / KT for v in kms]
-    kcnt = [v * K / KT for v in kcnt]
-    ms_max = allreduce_max(world, ms)
-    cells_total = allreduce_sum(world, float(prob.cells) * K)
-    value = cells_total / (ms_max / 1e3) / 1e9
-    mol_steps = allreduce_sum(world, float(prob.molecules.count) * K) / (ms_max / 1e3)
-    hbm, peak_kind = peaks()
-    # the field pass may run as two launches per step (blocks clear of the molecular
-    # current box, then the box blocks): its time per step is the sum of both
-    k1_ms = kms[1] / K
-    alg = field_pass_bytes(prob, esz)
-    achieved = alg / (k1_ms / 1e3) / 1e9
-    pe_last = g.molecules(maxlink.ML_MOL_POP)[:, 1]
-    flux = [g.flux(p) for p in range(len(prob.planes))]
-    # ---- end to end through the C ABI with host buffers
-    N = prob.cells
+    main = measure_coupled(prob, args, stream, world, rank, local, K, W, with_clocks=True,
+                           with_e2e=not args.no_e2e)
     if args.no_e2e:
-        g.close()
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": K, "profiling_run": True}))
+            print(json.dumps({"metric": METRIC, "value": main["value"], "unit": UNIT, "steps": K,
+                              "profiling_run": True}), flush=True)
         return
-    g2 = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
-    host_fields = torch.zeros((6, N), dtype=torch.float32, pin_memory=True)
-    # each step's populations land in a page-locked ring written by the molecule kernel
-    ring = 2
-    host_pop = torch.zeros((ring * prob.molecules.count * maxlink.ML_MAX_LEVELS,), dtype=torch.float64,
-                           pin_memory=True)
-    maxlink.ml_set_population_sink(g2.h, host_pop.data_ptr(), ring)
-    g2.step(W)
-    g2.sync()
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    maxlink.ml_set_fields(g2.h, maxlink.ML_ALL, host_fields.data_ptr(), False, sh)
-    for _ in range(K):
-        maxlink.ml_step(g2.h, 1, sh)
-    fl = [g2.flux(p) for p in range(len(prob.planes))]
-    stream.synchronize()
-    e2e_s = allreduce_max(world, time.perf_counter() - t0)
-    g2.sync()
-    e2e = cells_total / e2e_s / 1e9
-    last = (maxlink.ml_step_count(g2.h) - 1) % ring
-    pe_e2e = float(host_pop.view(ring, prob.molecules.count, maxlink.ML_MAX_LEVELS)[last, :, 1].mean())
-    maxlink.ml_set_population_sink(g2.h, 0, 1)
-    h2d = 6 * N * esz / K
-    # the populations written to the host each step (nlev doubles per molecule) and the
-    # spectra read once at the end
-    d2h = int(prob.molecules.nlev.sum()) * 8 + sum(8 * len(p.omegas) for p in prob.planes) / K
-    g2.close()
-    adjoint = measure_adjoint(args, stream) if (world == 1 and not args.no_adjoint) else None
-    batch = measure_batch(args, stream) if (world == 1 and not args.no_batch) else None
-    bragg = measure_bragg(args, stream) if (world == 1 and not args.no_bragg) else None
-    dispersive = measure_dispersive(args, stream) if (world == 1 and not args.no_dispersive) else None
-    transfer = measure_transfer(args, stream) if (world == 1 and not args.no_transfer) else None
-    cavity = measure_cavity(args, stream) if (world == 1 and not args.no_cavity) else None
-    laser = measure_laser(args, stream) if (world == 1 and not args.no_laser) else None
+    solo = world == 1
+    sec = {}
+    for name, skip in (("superradiant", args.no_superradiant), ("adjoint", args.no_adjoint),
+                       ("batch", args.no_batch), ("dispersive", args.no_dispersive),
+                       ("transfer", args.no_transfer), ("cavity", args.no_cavity), ("laser", args.no_laser)):
+        sec[name] = sections[name](args, stream) if (solo and not skip) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and solo and not args.no_cpu_baseline:
         n, dt, cores = cpu_oracle_run(prob, budget_s=args.cpu_budget, max_steps=50)
         cpu = {"value": prob.cells * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n} full steps of the same 256^3 workload (all 10000 emitters), FP64"}
+               "sample": f"{n} full steps (after 1 warm-up step) of the same {prob.nx}x{prob.ny}x{prob.nz} "
+                         f"workload with all {prob.molecules.count} systems, FP64"}
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": prob.cells, "molecules": prob.molecules.count,
-                       "grid": [prob.nx, prob.ny, prob.nz], "l2": "inputs larger than L2 (fields 805 MB per level)",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "yee_kernel (fused H/E + CPML + current read + plane sampling)",
-                         "timing": f"CUDA events around each launch, traced pass of {KT} steps after the timed region",
-                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": field_pass_traffic(args.edge, args.nmol),
-                         "alg_bytes_per_step": alg,
-                         "field_pass_ms_per_step": k1_ms, "launches_per_step": kcnt[1] / K},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-            "molecule_steps_per_s": mol_steps,
-            "adjoint": adjoint,
-            "batch": batch,
-            "bragg": bragg,
-            "dispersive": dispersive,
-            "transfer": transfer,
-            "cavity": cavity,
-            "laser": laser,
-            "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
-                                   "field_pass": kms[1] / K, "plane_fold": kms[3] / K},
-            "check": {"pe_mean": float(np.mean(pe_last)), "flux_plane0_f0": float(flux[0][0]),
-                      "e2e_flux_plane0_f0": float(fl[0][0]), "e2e_pe_mean": pe_e2e},
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": config_of(prob, world),
+            "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": main["e2e"],
+            "gpu_launches": int(main["launches"]), "clocks": main["clocks"],
+            "molecule_steps_per_s": main["molecule_steps_per_s"],
+            "kernel_ms_per_step": main["kernel_ms_per_step"], "check": main["check"],
         }
+        line.update(sec)
         print(json.dumps(line), flush=True)
-    g.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=40.0,
+                    help="seconds of timed oracle steps in the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
-    ap.add_argument("--edge", type=int, default=256, help="grid edge (profiling runs use a smaller cube)")
-    ap.add_argument("--nmol", type=int, default=10000)
+    ap.add_argument("--edge", type=int, default=256, help="superradiant slab: grid edge")
+    ap.add_argument("--nmol", type=int, default=10000, help="superradiant slab: emitters")
+    ap.add_argument("--sr-steps", type=int, default=2000, help="superradiant slab: timed steps")
+    ap.add_argument("--no-superradiant", action="store_true", help="skip the superradiant slab")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
-    ap.add_argument("--traced-steps", type=int, default=1000,
+    ap.add_argument("--traced-steps", type=int, default=400,
                     help="steps of the traced pass that times each kernel (roofline)")
-    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "dispersive", "transfer", "features",
-                                                        "cavity", "laser"],
+    ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "superradiant",
+                                                        "dispersive", "transfer", "features", "cavity", "laser"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
@@ -745,6 +814,9 @@ def main():
     ap.add_argument("--laser-steps", type=int, default=2000)
     ap.add_argument("--laser-molecules", type=int, default=4000000)
     ap.add_argument("--bragg-steps", type=int, default=400)
+    ap.add_argument("--bragg-shape", type=int, nargs=3, default=(512, 512, 384),
+                    help="grid of the Bragg ensemble, the headline workload (profiling runs use a smaller copy)")
+    ap.add_argument("--bragg-nmol", type=int, default=100000)
     ap.add_argument("--no-dispersive", action="store_true", help="skip the dispersive stack")
     ap.add_argument("--dispersive-steps", type=int, default=400)
     ap.add_argument("--no-transfer", action="store_true", help="skip the energy-transfer realisations")

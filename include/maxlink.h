@@ -22,7 +22,8 @@
  *   - Every call returns an ml_status; ml_last_error() gives a message for the
  *     last failure on the calling thread.  No exception crosses the ABI.
  *   - The library copies every input; the caller keeps ownership of its buffers.
- *     Device memory of a grid is owned by the library until ml_grid_destroy.
+ *     Device memory of a grid is owned by the library until ml_grid_destroy; it comes
+ *     from the allocator of ml_set_allocator.
  */
 #ifndef MAXLINK_H
 #define MAXLINK_H
@@ -132,7 +133,9 @@ typedef struct {
 /* what to read with ml_get_molecules (all as double) */
 enum {
     ML_MOL_RHO = 0,     /* pool of interleaved complex rho (2*pool doubles) */
-    ML_MOL_EFIELD = 1,  /* (count,3) regularised field of the last step (Eq. E_regu_Em) */
+    ML_MOL_EFIELD = 1,  /* (count,3) regularised field of the last step (Eq. E_regu_Em); a
+                           component along which all of the molecule's dipole operators
+                           vanish does not enter its Hamiltonian, is not gathered and reads 0 */
     ML_MOL_MUDOT = 2,   /* (count,3) d<mu>/dt of the last step (Eq. dipole_derivative) */
     ML_MOL_ENERGY = 3,  /* (count) sum over steps of Tr(rho H0) (time average = / steps) */
     ML_MOL_POP = 4      /* (count, ML_MAX_LEVELS) diagonal of rho, zero-padded */
@@ -140,6 +143,29 @@ enum {
 
 /* component mask bits for ml_get_fields / ml_set_fields (order of the copies) */
 enum { ML_EX = 1, ML_EY = 2, ML_EZ = 4, ML_HX = 8, ML_HY = 16, ML_HZ = 32, ML_ALL = 63 };
+
+/* ---- Device memory ---------------------------------------------------------------
+ * The paper's problem statement (Sec. III) keeps the EM solver and the molecular drivers
+ * in separate programs with their own memory; here both live in one process next to the
+ * caller's framework, so every device buffer the library allocates (grids, molecule
+ * tables, flux planes, batches, the adjoint's work memory, cavities, drives) comes from
+ * one process-wide allocator that the caller may supply:
+ *   alloc(&ptr, bytes, stream, ctx): return 0 and set *ptr to at least `bytes` bytes of
+ *       device memory of the current device, 256-byte aligned; nonzero (or a NULL *ptr)
+ *       when it cannot, and the library call then fails with ML_ERR_OOM;
+ *   free(ptr, bytes, stream, ctx): give a buffer back.
+ * `stream` is NULL (the legacy default stream): the library zeroes new memory on that
+ * stream, waits for it, and frees only after the work that used the memory has finished.
+ * The default allocator is cudaMallocAsync / cudaFreeAsync on that stream.  The Python
+ * binding installs one backed by PyTorch's caching allocator when it loads the library.
+ * Every buffer is returned to the allocator it came from, so the allocator may be
+ * replaced at any time; `ctx` must stay valid while buffers from it are alive.
+ * ml_set_allocator(NULL, NULL, NULL) restores the default.  ml_gather_static allocates
+ * nothing and does not use the allocator.  Error: ML_ERR_INVALID_ARG when exactly one
+ * of the two functions is NULL. */
+typedef int (*ml_alloc_fn)(void **ptr, size_t bytes, void *stream, void *ctx);
+typedef void (*ml_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+ml_status ml_set_allocator(ml_alloc_fn alloc, ml_free_fn free_fn, void *ctx);
 
 /* Message of the last failure on this thread ("" if none).  Never NULL. */
 const char *ml_last_error(void);
@@ -216,8 +242,21 @@ ml_status ml_flux_data(ml_grid *g, int id, double *out, void *stream);
  * share includes the energy it stores).  Host out. */
 ml_status ml_absorbed(ml_grid *g, double *out, void *stream);
 
-/* Synchronise `stream` and return the latched device status (then clear it). */
+/* Synchronise `stream` and return the latched device status (then clear it):
+ * ML_ERR_NUMERIC when a NaN or Inf reached a molecule's regularised field or current,
+ * ML_ERR_TIMEOUT when a field-pass block gave up waiting for a plane of its copy ring
+ * (the block then waits, bounded, for its own copies in flight and exits without
+ * writing the rest of its tile, so the step's fields are not valid; later steps run
+ * normally).  The paper's hub detects failed or silent drivers with a barrier and
+ * timeouts (Sec. III); here the failure is reported by the device. */
 ml_status ml_sync_status(ml_grid *g, void *stream);
+
+/* Bound of the field pass's waits for a plane of its copy ring: `probes` suspended
+ * probes of up to 1 ms each (default 2000).  0 makes every wait give up at once, so
+ * the next ml_step reports ML_ERR_TIMEOUT through ml_sync_status (a host-side way to
+ * exercise the timeout path; nothing is left waiting).  Taken by the next ml_step or
+ * ml_batch_step.  Error: ML_ERR_INVALID_ARG outside 0 .. 2^31 - 1. */
+ml_status ml_set_wait_limit(ml_grid *g, int64_t probes);
 
 /* Steps taken so far. */
 int64_t ml_step_count(const ml_grid *g);

@@ -669,25 +669,8 @@ __global__ void adj_record_kernel(const T *E0, const T *E1, const T *E2, int px,
 
 namespace {
 
-struct DevList {
-    std::vector<void *> p;
-    ~DevList() {
-        for (void *q : p) cudaFree(q);
-    }
-};
-
-ml_status adj_alloc(DevList &L, void **out, size_t bytes) {
-    *out = nullptr;
-    if (bytes == 0) return ML_OK;
-    cudaError_t e = cudaMalloc(out, bytes);
-    if (e != cudaSuccess) {
-        *out = nullptr;
-        cudaGetLastError();
-        return fail(ML_ERR_OOM, "adjoint: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-    }
-    L.p.push_back(*out);
-    return ML_OK;
-}
+// work memory of one call, from the process allocator, returned when the call ends
+ml_status adj_alloc(DevList &L, void **out, size_t bytes) { return dev_alloc(L.v, out, bytes); }
 
 #define AA(ptr, bytes)                                             \
     do {                                                           \

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "grid.cuh"
@@ -24,20 +25,8 @@ thread_local std::string g_err;
 
 namespace {
 
-ml_status dalloc(std::vector<void *> &list, void **p, size_t bytes) {
-    *p = nullptr;
-    if (bytes == 0) return ML_OK;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return fail(ML_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
-    }
-    e = cudaMemset(*p, 0, bytes);
-    if (e != cudaSuccess) return fail(ML_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
-    list.push_back(*p);
-    return ML_OK;
-}
+// zeroed device memory from the process allocator, owned by `list`
+ml_status dalloc(std::vector<DevBuf> &list, void **p, size_t bytes) { return dev_alloc(list, p, bytes); }
 
 #define AL(list, ptr, bytes)                                                \
     do {                                                                    \
@@ -46,19 +35,19 @@ ml_status dalloc(std::vector<void *> &list, void **p, size_t bytes) {
     } while (0)
 
 template <typename T>
-ml_status upload_as(std::vector<void *> &list, void **dst, const std::vector<double> &v) {
+ml_status upload_as(std::vector<DevBuf> &list, void **dst, const std::vector<double> &v) {
     std::vector<T> t(v.begin(), v.end());
     AL(list, *dst, t.size() * sizeof(T));
     if (!t.empty()) CK(cudaMemcpy(*dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
     return ML_OK;
 }
 
-ml_status upload_reals(ml_grid *g, std::vector<void *> &list, void **dst, const std::vector<double> &v) {
+ml_status upload_reals(ml_grid *g, std::vector<DevBuf> &list, void **dst, const std::vector<double> &v) {
     return g->prec ? upload_as<double>(list, dst, v) : upload_as<float>(list, dst, v);
 }
 
 template <typename V>
-ml_status upload_raw(std::vector<void *> &list, V **dst, const std::vector<V> &v) {
+ml_status upload_raw(std::vector<DevBuf> &list, V **dst, const std::vector<V> &v) {
     AL(list, *dst, v.size() * sizeof(V));
     if (!v.empty()) CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
     return ML_OK;
@@ -126,8 +115,8 @@ ml_status ml_grid_destroy(ml_grid *g) {
     if (g->side) cudaStreamDestroy(g->side);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
     if (g->ev_box) cudaEventDestroy(g->ev_box);
-    for (void *p : g->mol_allocs) cudaFree(p);
-    for (void *p : g->allocs) cudaFree(p);
+    dev_free_all(g->mol_allocs);
+    dev_free_all(g->allocs);
     delete g;
     return ML_OK;
 }
@@ -182,7 +171,8 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
 
     ml_grid *g = new ml_grid();
     auto bail = [&](ml_status s) {
-        for (void *p : g->allocs) cudaFree(p);
+        cudaDeviceSynchronize();
+        dev_free_all(g->allocs);
         delete g;
         return s;
     };
@@ -359,8 +349,8 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
         g->src.push_back(SrcDev{s.axis, s.index, s.comp, s.amp, s.omega, s.width, s.t0});
     }
     {
-        // tiles whose own cells need the per-cell material path: a non-background
-        // material, the design box, the pole box or a source plane
+        // per-tile work of the field pass's own cells: bit 0 = the design box or the pole
+        // box, bit 1 = a non-background material, bit 2 = a source plane
         std::vector<int> zt(g->nz);
         for (int c = 0; c < g->nchunk; c++)
             for (int k = g->zcut[c]; k < g->zcut[c + 1]; k++) zt[k] = c;
@@ -370,7 +360,7 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
             for (int k = 0; k < g->nz; k++)
                 for (int j = 0; j < g->ny; j++)
                     for (int i = 0; i < g->nx; i++)
-                        if (d->mat[((long long)k * g->ny + j) * g->nx + i] != 0) fl[tile_of(i, j, k)] = 1;
+                        if (d->mat[((long long)k * g->ny + j) * g->nx + i] != 0) fl[tile_of(i, j, k)] |= 2;
         for (int bz = 0; bz < g->nchunk; bz++)
             for (int by = 0; by < g->nty; by++)
                 for (int bx = 0; bx < g->ntx; bx++) {
@@ -382,10 +372,10 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
                             if (box[a] >= hi[a] || box[a] + box[3 + a] <= lo[a]) return false;
                         return true;
                     };
-                    bool f = meets(g->dbox) || meets(g->jbox);
+                    uint8_t f = (meets(g->dbox) || meets(g->jbox)) ? 1 : 0;
                     for (auto &q : g->src)
-                        if (q.index >= lo[q.axis] && q.index < hi[q.axis]) f = true;
-                    if (f) fl[((long long)bz * g->nty + by) * g->ntx + bx] = 1;
+                        if (q.index >= lo[q.axis] && q.index < hi[q.axis]) f |= 4;
+                    fl[((long long)bz * g->nty + by) * g->ntx + bx] |= f;
                 }
         GA(g->d_tflags, fl.size());
         GC(cudaMemcpy(g->d_tflags, fl.data(), fl.size(), cudaMemcpyHostToDevice));
@@ -402,8 +392,8 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
 namespace {
 
 ml_status rebuild_molecules(ml_grid *g) {
-    for (void *p : g->mol_allocs) cudaFree(p);
-    g->mol_allocs.clear();
+    cudaDeviceSynchronize();
+    dev_free_all(g->mol_allocs);
     auto &L = g->mol_allocs;
     const int M = g->nmol;
     ml_status st;
@@ -552,6 +542,36 @@ ml_status rebuild_molecules(ml_grid *g) {
     for (int c = 0; c < 3; c++) {
         g->d_J[c] = nullptr;
         if ((g->gcmask >> c) & 1) AL(L, g->d_J[c], jvol * g->esz);
+    }
+    // packed molecule kernel (grids with multilevel molecules): molecules sorted by
+    // (kind, level count, substeps) and, within a class, by window position (neighbours
+    // share field lines in L2), cut into work items of pack_per_warp(n) molecules
+    g->nitems = 0;
+    if (!g->two_level && M > 0) {
+        std::vector<int> ord(M);
+        for (int m = 0; m < M; m++) ord[m] = m;
+        auto key = [&](int m) {
+            return std::make_tuple(g->kind[m] == 0 ? 0 : 1, g->nlev[m], g->nsub[m], g->win[3 * m + 2],
+                                   g->win[3 * m + 1], g->win[3 * m], m);
+        };
+        std::sort(ord.begin(), ord.end(), [&](int x, int y) { return key(x) < key(y); });
+        std::vector<int4> items;
+        for (int i = 0; i < M;) {
+            const int m0 = ord[i];
+            const int n = g->nlev[m0], cls = g->kind[m0] == 0 ? 0 : 1, ns = g->nsub[m0];
+            const int per = pack_per_warp(n);
+            int c = 0;
+            while (i + c < M && c < per) {
+                const int mc = ord[i + c];
+                if (g->nlev[mc] != n || (g->kind[mc] == 0 ? 0 : 1) != cls || g->nsub[mc] != ns) break;
+                c++;
+            }
+            items.push_back(make_int4(i, c, n, cls | (ns << 4)));
+            i += c;
+        }
+        g->nitems = (int)items.size();
+        CKS(upload_raw(L, &g->d_order, ord));
+        CKS(upload_raw(L, &g->d_items, items));
     }
     CK(cudaDeviceSynchronize());
     return ML_OK;
@@ -740,6 +760,9 @@ void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
     m.energy = g->d_energy; m.status = g->d_status;
     m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;
     m.two_level = g->two_level ? 1 : 0;
+    m.order = g->d_order;
+    m.items = g->d_items;
+    m.nitems = g->nitems;
     m.pop_sink = g->pop_off ? nullptr : g->pop_sink;
     m.pop_slot = g->pop_sink ? (g->step % g->pop_ring) * (long long)g->nmol * MAXLEV : 0;
 }
@@ -800,6 +823,7 @@ void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y) {
     y.PD = (T *)g->PD;
     y.absorbed_part = g->absorbed_part;
     y.status = g->d_status;
+    y.wait_limit = g->wait_limit;
     if (g->nmol > 0)
         for (int a = 0; a < 3; a++) {
             y.jb0[a] = g->jb0[a];
@@ -842,7 +866,9 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
                 // tiles that read J: such a tile releases this kernel only after its wait
                 // for the previous current kernel, hence after the previous molecule
                 // kernel, so the molecule state may be staged before this kernel's wait
-                CK(launch_molecules<T>(m, cs, !chain && g->pdl && g->gcmask != 0));
+                const bool pdl_mol = !chain && g->pdl && g->gcmask != 0;
+                if (g->nitems > 0) CK(launch_molecules_packed<T>(m, cs, pdl_mol));
+                else CK(launch_molecules<T>(m, cs, pdl_mol));
             }
             {
                 CurArgs<T> ca;
@@ -1051,6 +1077,13 @@ ml_status ml_sync_status(ml_grid *g, void *stream) {
     if (st == ML_ERR_NUMERIC) return fail(ML_ERR_NUMERIC, "non-finite molecular field or current");
     if (st == ML_ERR_TIMEOUT) return fail(ML_ERR_TIMEOUT, "device wait timed out");
     if (st != 0) return fail((ml_status)st, "device status " + std::to_string(st));
+    return ML_OK;
+}
+
+ml_status ml_set_wait_limit(ml_grid *g, int64_t probes) {
+    if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");
+    if (probes < 0 || probes > 0x7fffffffll) return fail(ML_ERR_INVALID_ARG, "probes must be in 0 .. 2^31 - 1");
+    g->wait_limit = (uint32_t)probes;
     return ML_OK;
 }
 

@@ -44,6 +44,7 @@ struct ml_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> sig;  // what the graph baked in
     long long launches = 0;
+    std::vector<ml::DevBuf> mem;  // the device arrays above
 };
 
 namespace {
@@ -51,25 +52,21 @@ namespace {
 constexpr int SEQ = 64;  // steps per captured sequence: two time levels, whole fold periods
 static_assert(SEQ % DFT_KMAX == 0 && SEQ % 2 == 0, "a sequence starts at a fold boundary and on level 0");
 
-ml_status ensure(void **p, size_t &cap, size_t bytes) {
+ml_status ensure(ml_batch *bt, void **p, size_t &cap, size_t bytes) {
     if (bytes <= cap && *p) return ML_OK;
-    if (*p) cudaFree(*p);
+    if (*p) dev_release(bt->mem, *p);
     *p = nullptr;
     cap = 0;
     const size_t b = std::max<size_t>(bytes, 256);
-    cudaError_t e = cudaMalloc(p, b);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return fail(ML_ERR_OOM, "batch: cudaMalloc failed");
-    }
+    ml_status st = dev_alloc(bt->mem, p, b);
+    if (st != ML_OK) return st;
     cap = b;
     return ML_OK;
 }
 
 template <typename V>
 ml_status upload(ml_batch *b, int slot, void **dptr, const std::vector<V> &h, cudaStream_t s) {
-    ml_status st = ensure(dptr, b->cap[slot], h.size() * sizeof(V));
+    ml_status st = ensure(b, dptr, b->cap[slot], h.size() * sizeof(V));
     if (st != ML_OK) return st;
     if (!h.empty()) CK(cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, s));
     return ML_OK;
@@ -272,8 +269,14 @@ ml_status ml_batch_create(ml_grid *const *grids, int n, ml_batch **out) {
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->blocks_per_sm = b->prec ? 1 : 3;
     if (const char *ev = std::getenv("ML_PDL")) b->pdl = std::atoi(ev) != 0;
-    cudaError_t e = cudaMalloc((void **)&b->d_boff, sizeof(long long));
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    {
+        ml_status st = dev_alloc(b->mem, (void **)&b->d_boff, sizeof(long long));
+        if (st != ML_OK) {
+            ml_batch_destroy(b);
+            return st;
+        }
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         // kernel attributes are set outside any capture
         e = b->prec ? launch_yee_batch<double>(YeeBatch<double>{}, 1, b->cap_stream)
@@ -291,10 +294,7 @@ ml_status ml_batch_destroy(ml_batch *b) {
     if (!b) return ML_OK;
     cudaDeviceSynchronize();
     drop_graph(b);
-    void *ptrs[] = {b->d_yargs, b->d_gargs, b->d_cargs, b->d_margs, b->d_fdesc, b->d_maps, b->d_lev0,
-                    b->d_ywork, b->d_gwork, b->d_mwork, b->d_fwork, b->d_boff};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    dev_free_all(b->mem);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return ML_OK;
@@ -328,12 +328,7 @@ ml_status ml_batch_autotune(ml_batch *b, int trial_steps, void *stream, int *blo
     std::vector<void *> snaps;
     std::vector<long long> steps;
     std::vector<int> curs;
-    struct Free {
-        std::vector<void *> &v;
-        ~Free() {
-            for (void *p : v) cudaFree(p);
-        }
-    } fr{snaps};
+    DevList snap_mem;  // returned when the call ends
     for (ml_grid *g : b->g) {
         // empty DFT rings first, so that the snapshot plus the host counters is the state
         ml_status st = g->prec ? fold_planes<double>(g, s) : fold_planes<float>(g, s);
@@ -342,10 +337,8 @@ ml_status ml_batch_autotune(ml_batch *b, int trial_steps, void *stream, int *blo
         size_t n = 0;
         for (auto &x : blobs.back()) n += x.bytes;
         void *p = nullptr;
-        if (cudaMalloc(&p, n) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ML_ERR_OOM, "autotune: no memory for the state snapshot");
-        }
+        st = dev_alloc(snap_mem.v, &p, n);
+        if (st != ML_OK) return st;
         snaps.push_back(p);
         char *o = (char *)p;
         for (auto &x : blobs.back()) {

@@ -95,7 +95,7 @@ struct ml_cavity {
     double *d_energy = nullptr, *d_mode = nullptr, *d_part = nullptr, *d_export = nullptr;
     double *d_bpart = nullptr;  // two-level molecules: per-block dipole sums of the molecule kernel
     unsigned *d_ticket = nullptr;
-    std::vector<void *> allocs;
+    std::vector<ml::DevBuf> allocs;
     // CAV_SEQ steps captured once into a graph (the arguments never change) and replayed
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -105,14 +105,7 @@ struct ml_cavity {
 namespace {
 
 ml_status cav_alloc(ml_cavity *c, void **p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return fail(ML_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
-    }
-    c->allocs.push_back(*p);
-    return ML_OK;
+    return dev_alloc(c->allocs, p, std::max<size_t>(bytes, 16));
 }
 
 template <typename V>
@@ -331,7 +324,8 @@ ml_status ml_cavity_destroy(ml_cavity *c) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cap) cudaStreamDestroy(c->cap);
-    for (void *p : c->allocs) cudaFree(p);
+    cudaDeviceSynchronize();
+    dev_free_all(c->allocs);
     delete c;
     return ML_OK;
 }

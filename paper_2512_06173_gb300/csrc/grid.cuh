@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include "devmem.cuh"
 #include "maxlink.h"
 #include "ml_internal.cuh"
 
@@ -44,7 +45,7 @@ struct ml_grid {
     int ntx = 0, nty = 0, nchunk = 0, cz = 0, nblocks = 0;
     std::vector<int> zcut;  // chunk boundaries along z
     int *d_zcut = nullptr;
-    uint8_t *d_tflags = nullptr;  // per tile: bit 0 = own cells need the material path
+    uint8_t *d_tflags = nullptr;  // per tile: bit 0 = pole or design box, bit 1 = material, bit 2 = source
     int px = 0, py = 0;
     long long plane = 0;
     size_t vol = 0;  // padded elements per array
@@ -72,6 +73,9 @@ struct ml_grid {
     long long pool = 0;
     std::vector<int> nlev, kind, nsub, cmask, win, wf, wraw;
     bool two_level = true;  // every molecule has two levels (pool offset 4 m)
+    int *d_order = nullptr;      // packed molecule kernel: molecules in work-item order
+    int4 *d_items = nullptr;     //   and its work items (first, count, levels, kind | nsub << 4)
+    int nitems = 0;
     double *pop_sink = nullptr;  // device address of the caller's page-locked population ring
     long long pop_ring = 0;
     bool pop_off = false;        // set while the adjoint sweeps step the grid
@@ -110,6 +114,7 @@ struct ml_grid {
     long long samp_step0 = 0;
     void *scratch = nullptr;
     int *d_status = nullptr;
+    uint32_t wait_limit = 2000;  // probes of a field-pass plane wait (ml_set_wait_limit)
     long long step = 0;
     // tracing: CUDA events around each launch of ml_step, per kernel class
     bool timing = false;
@@ -117,8 +122,8 @@ struct ml_grid {
     struct Timed { cudaEvent_t a, b; int kind; };  // kind: 0 molecules 1 field 2 sample 3 fold 4 current 5 gather
     std::vector<Timed> timed;
     long long launches = 0;
-    std::vector<void *> allocs;       // grid lifetime
-    std::vector<void *> mol_allocs;   // rebuilt when molecules are added
+    std::vector<ml::DevBuf> allocs;       // grid lifetime
+    std::vector<ml::DevBuf> mol_allocs;   // rebuilt when molecules are added
 };
 
 namespace ml {

@@ -73,7 +73,8 @@ struct YeeArgs {
     int pml[6];
     int ntx, nty, nchunk, cz;   // cz: longest chunk
     const int *blist;           // blocks of this launch (tile indices), or null for all
-    const uint8_t *tflags;      // per tile: bit 0 = some own cell needs the material path
+    const uint8_t *tflags;      // per tile: bit 0 = the pole box or the design box meets its own
+                                //   cells, bit 1 = a non-background material, bit 2 = a source plane
     const int *zcut;            // chunk c covers planes [zcut[c], zcut[c+1])
     T dt;
     const T *Eo[3];
@@ -109,6 +110,7 @@ struct YeeArgs {
     PlaneDev<T> planes[MAXPLANES];
     long long step;
     int *status;
+    uint32_t wait_limit;  // probes of a plane wait before it gives up (ML_ERR_TIMEOUT)
 };
 
 // TMA descriptors of the six arrays of the time level the field pass reads.
@@ -209,7 +211,20 @@ struct MolArgs {
     const long long *lbase;
     int lstep;
     double ldt, lxi0, lk, lphase, lW, lE0, lpol[3];
+    // packed form (grids with multilevel molecules): molecules sorted by (kind, level
+    // count, substeps, window position) in `order`; item i covers order[x .. x+y) with
+    // level count z and w = kind | nsub << 4, one item per warp
+    const int *order;
+    const int4 *items;
+    int nitems;
 };
+// Molecules per warp of the packed molecule kernel for n levels: a molecule's n(n+1)/2
+// upper-triangle elements go to a group of G lanes, G the next power of two (64 for
+// n = 8: two elements per lane).
+__host__ __device__ constexpr int pack_group(int n) {
+    return n * (n + 1) / 2 <= 4 ? 4 : (n * (n + 1) / 2 <= 8 ? 8 : (n * (n + 1) / 2 <= 16 ? 16 : (n * (n + 1) / 2 <= 32 ? 32 : 64)));
+}
+__host__ __device__ constexpr int pack_per_warp(int n) { return pack_group(n) <= 32 ? 32 / pack_group(n) : 1; }
 constexpr int MU_THREADS_HOST = 256;  // molecules per block of the thread-per-molecule uniform-field kernel
 
 // ------------------------------------------------------------------ DFT planes
@@ -293,6 +308,7 @@ cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s,
                                              bool pdl = false);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
+template <typename T> cudaError_t launch_molecules_packed(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);

@@ -321,6 +321,12 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 
     // ---- 3. density-matrix step over dt with the field held
     cx<T> r1[2] = {r0[0], r0[1]};
+    // RK4: the change of the own elements over the step, summed from the substeps'
+    // increments.  d<mu>/dt is Re Tr(drho mu)/dt (Eq. dipole_derivative): the same
+    // quantity as the difference of the two traces, without the cancellation of the
+    // diagonal terms of mu in FP32.
+    cx<T> dr[2] = {{T(0), T(0)}, {T(0), T(0)}};
+    const bool incr = kind != 0;
     if (kind == 0) {
         // exact exponential of a 2x2 Hermitian H:
         // U = e^{-i hbar dt}[cos(W dt) - i sin(W dt)/W (H - hbar)], the phase cancels in U rho U^+
@@ -390,14 +396,18 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
                 }
             }
             for (int q = 0; q < 2; q++) {
-                r1[q].re = base[q].re + h / T(6) * acc[q].re;
-                r1[q].im = base[q].im + h / T(6) * acc[q].im;
+                const T ur = h / T(6) * acc[q].re, ui = h / T(6) * acc[q].im;
+                r1[q].re = base[q].re + ur;
+                r1[q].im = base[q].im + ui;
+                dr[q].re += ur;
+                dr[q].im += ui;
             }
             __syncwarp();
         }
     }
     // ---- 4. <mu> after, mudot, current amplitude, energy
     T mu1[3] = {T(0), T(0), T(0)};
+    T dmu[3] = {T(0), T(0), T(0)};
     T en = T(0);
 #pragma unroll
     for (int q = 0; q < 2; q++) {
@@ -407,17 +417,23 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
             if (a.pop_sink && e % (n + 1) == 0)  // diagonal element (j, j), j = e / (n + 1)
                 a.pop_sink[a.pop_slot + (long long)m * MAXLEV + e / (n + 1)] = (double)r1[q].re;
 #pragma unroll
-            for (int c = 0; c < 3; c++) mu1[c] += r1[q].re * mu[c][q].re + r1[q].im * mu[c][q].im;
+            for (int c = 0; c < 3; c++) {
+                mu1[c] += r1[q].re * mu[c][q].re + r1[q].im * mu[c][q].im;
+                dmu[c] += dr[q].re * mu[c][q].re + dr[q].im * mu[c][q].im;
+            }
             en += r1[q].re * h0[q].re + r1[q].im * h0[q].im;
         }
     }
     en = warp_sum(en);
 #pragma unroll
-    for (int c = 0; c < 3; c++) mu1[c] = ((cm >> c) & 1) ? warp_sum(mu1[c]) : T(0);
+    for (int c = 0; c < 3; c++) {
+        mu1[c] = ((cm >> c) & 1) ? warp_sum(mu1[c]) : T(0);
+        if (incr) dmu[c] = ((cm >> c) & 1) ? warp_sum(dmu[c]) : T(0);
+    }
     if (lane == 0) {
         bool bad = false;
         for (int c = 0; c < 3; c++) {
-            const T md = (mu1[c] - mu0[c]) / a.dt;
+            const T md = (incr ? dmu[c] : mu1[c] - mu0[c]) / a.dt;
             a.Et[3 * m + c] = Et[c];
             a.mudot[3 * m + c] = md;
             a.c[3 * m + c] = gam * md;
@@ -437,6 +453,337 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
 template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1) molecule_kernel(const MolArgs<T> a) {
     molecule_body<T, SRC_WINDOW, N2>(a, (int)blockIdx.x * MOL_WARPS);
+}
+
+// ------------------------------------------------------------------ packed molecules
+// Grids with multilevel molecules: one warp per work item of up to pack_per_warp(n)
+// molecules of one kind, level count n and substep count (sorted on the host).  The
+// warp gathers each molecule's regularised field in turn (Eq. E_regu_Emi, as in
+// molecule_body), then steps all of them at once: the density matrix and the RK4 stages
+// are Hermitian, so a molecule's group of lanes holds only its upper-triangle elements
+// (lane u of the group owns element u of the row-major upper triangle, and u + 32 too
+// for n = 8) and writes each new element to both halves of the shared matrix; the GKSL
+// right-hand side is unrolled for the compile-time n.  d<mu>/dt is Re Tr(drho mu)/dt
+// with drho the step's increment (Eq. dipole_derivative).
+template <typename T>
+struct PackShared {
+    cx<T> S[MOL_WARPS][2][64];  // per molecule q of the warp: matrix at q * n * n
+    cx<T> H[MOL_WARPS][64];
+    T W[MOL_WARPS][NW];
+    T Et[MOL_WARPS][8][3];
+    cx<T> K[MOL_WARPS][2][4][32];  // per lane and slot: H0 and the three dipole elements,
+                                   // kept for the outputs while the RK4 stages run
+};
+
+// (j, l), j <= l, of upper-triangle element u (row-major) of an n x n matrix
+template <int N>
+__device__ __forceinline__ void upper_index(int u, int &j, int &l) {
+    j = 0;
+#pragma unroll
+    for (int q = 0; q < N; q++)
+        if (j == q && u >= N - q) {
+            u -= N - q;
+            j = q + 1;
+        }
+    l = j + u;
+}
+
+// GKSL right-hand side of element (j, l) (the rhs_elem formula, n fixed at compile time)
+template <typename T, int N>
+__device__ __forceinline__ cx<T> rhs_fixed(int j, int l, const cx<T> *S, const cx<T> *H, T decay, T deph) {
+    cx<T> acc = {T(0), T(0)};
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+        const cx<T> x = cmul(H[j * N + p], S[p * N + l]);
+        const cx<T> y = cmul(S[j * N + p], H[p * N + l]);
+        acc.re += x.re - y.re;
+        acc.im += x.im - y.im;
+    }
+    cx<T> out = {acc.im, -acc.re};
+    const cx<T> r = S[j * N + l];
+    if (decay != T(0)) {
+        const T f = T(0.5) * decay * (T(j >= 1) + T(l >= 1));
+        out.re -= f * r.re;
+        out.im -= f * r.im;
+        if (j == l && j + 1 < N) out.re += decay * S[(j + 1) * N + (j + 1)].re;
+    }
+    if (deph != T(0) && j != l) {
+        out.re -= deph * r.re;
+        out.im -= deph * r.im;
+    }
+    return out;
+}
+
+// sum over the lanes of a group of G (a power of two <= 32; 64: the whole warp)
+template <typename T, int G>
+__device__ __forceinline__ T group_sum(T v) {
+    constexpr int W = G > 32 ? 32 : G;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T, int N, bool EXACT>
+__device__ __forceinline__ void packed_body(const MolArgs<T> &a, const int4 item, PackShared<T> &sh, const int wl) {
+    constexpr int G = pack_group(N), NN = N * N, NE = N * (N + 1) / 2, SL = G > 32 ? 2 : 1;
+    constexpr int GL = G > 32 ? 32 : G;  // lanes per group
+    const int lane = threadIdx.x & 31;
+    const int q = lane / GL, u0 = lane % GL;
+    const int cnt = item.y;
+    const bool live = q < cnt;
+    const int m = a.order[item.x + (live ? q : 0)];
+    int jj[SL], ll[SL];
+    bool own[SL];
+#pragma unroll
+    for (int s = 0; s < SL; s++) {
+        const int u = u0 + 32 * s;
+        own[s] = live && u < NE;
+        upper_index<N>(own[s] ? u : 0, jj[s], ll[s]);
+    }
+    // ---- this molecule's own elements and parameters, loaded before the dependence wait
+    const long long o = a.off[m];
+    const int cm = a.cmask[m];
+    const T gam = a.gamma[m];
+    const T decay = EXACT ? T(0) : a.decay[m], deph = EXACT ? T(0) : a.dephase[m];
+    const double e_old = (live && u0 == 0) ? a.energy[m] : 0.0;
+    cx<T> r0[SL], h0[SL], mu[3][SL];
+#pragma unroll
+    for (int s = 0; s < SL; s++) {
+        const long long e = o + jj[s] * N + ll[s];
+        r0[s] = own[s] ? a.rho[e] : cx<T>{T(0), T(0)};
+        h0[s] = own[s] ? a.H0[e] : cx<T>{T(0), T(0)};
+#pragma unroll
+        for (int c = 0; c < 3; c++) mu[c][s] = (own[s] && ((cm >> c) & 1)) ? a.mu[c * a.pool + e] : cx<T>{T(0), T(0)};
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    // ---- 1. regularised fields, one molecule of the item after the other (whole warp)
+    for (int qq = 0; qq < cnt; qq++) {
+        const int mq = a.order[item.x + qq];
+        const T w0 = a.w[(long long)mq * NW + lane], w1 = a.w[(long long)mq * NW + lane + 32],
+                w2 = a.w[(long long)mq * NW + lane + 64];
+        const int wfm = a.wf[mq], x0 = a.win[3 * mq], y0 = a.win[3 * mq + 1], z0 = a.win[3 * mq + 2];
+        const int cmq = a.cmask[mq];
+        __syncwarp();
+        sh.W[wl][lane] = w0;
+        sh.W[wl][lane + 32] = w1;
+        sh.W[wl][lane + 64] = w2;
+        __syncwarp();
+        T g[3];
+        bool done = false;
+        if constexpr (sizeof(T) == 4) done = window_gather_vec(a, cmq, wfm, x0, y0, z0, sh.W[wl], g);
+        if (!done) window_gather(a, mq, cmq, sh.W[wl], g);
+        if (lane == 0) {
+            const T gq = a.gamma[mq];
+#pragma unroll
+            for (int c = 0; c < 3; c++) sh.Et[wl][qq][c] = gq * g[c];
+        }
+    }
+    __syncwarp();
+    T Et[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) Et[c] = live ? sh.Et[wl][q][c] : T(0);
+
+    // ---- 2. H = H0 - Et . mu and S = rho, both halves of each matrix
+    cx<T> *Hs = sh.H[wl] + q * NN;
+    cx<T> *S0 = sh.S[wl][0] + q * NN, *S1 = sh.S[wl][1] + q * NN;
+#pragma unroll
+    for (int s = 0; s < SL; s++) {
+        sh.K[wl][s][0][lane] = h0[s];
+#pragma unroll
+        for (int c = 0; c < 3; c++) sh.K[wl][s][1 + c][lane] = mu[c][s];
+    }
+#pragma unroll
+    for (int s = 0; s < SL; s++)
+        if (own[s]) {
+            cx<T> h = h0[s];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                h.re -= Et[c] * mu[c][s].re;
+                h.im -= Et[c] * mu[c][s].im;
+            }
+            const int j = jj[s], l = ll[s];
+            Hs[j * N + l] = h;
+            Hs[l * N + j] = cconj(h);
+            S0[j * N + l] = r0[s];
+            S0[l * N + j] = cconj(r0[s]);
+        }
+    __syncwarp();
+
+    // ---- 3. the step
+    cx<T> r1[SL], dr[SL];
+    if constexpr (EXACT) {
+        // U = cos(W dt) - i sin(W dt)/W (H - tr H / 2): the exact propagator of the held
+        // 2x2 Hamiltonian (its phase cancels); rho' = U rho U^+; for d<mu>/dt the increment
+        // A rho + rho A^+ + A rho A^+ with A = U - 1 (cos(W dt) - 1 = -2 sin^2(W dt / 2))
+        const T dt = a.dt;
+        const T z = T(0.5) * (Hs[0].re - Hs[3].re);
+        const cx<T> b = Hs[1];
+        const T W = sqrt(z * z + b.re * b.re + b.im * b.im);
+        const T sh2 = sin(T(0.5) * W * dt);
+        const T cm1 = T(-2) * sh2 * sh2;
+        const T sw = W > T(0) ? sin(W * dt) / W : dt;
+        const cx<T> a00 = {cm1, -sw * z}, a01 = {sw * b.im, -sw * b.re}, a10 = {-sw * b.im, -sw * b.re},
+                    a11 = {cm1, sw * z};
+        const int j = jj[0], l = ll[0];
+        // rows j and l of A and of U = 1 + A, and the columns l of rho (no indexed arrays)
+        const cx<T> aj0 = j ? a10 : a00, aj1 = j ? a11 : a01, al0 = l ? a10 : a00, al1 = l ? a11 : a01;
+        const cx<T> uj0 = {aj0.re + T(j == 0), aj0.im}, uj1 = {aj1.re + T(j == 1), aj1.im};
+        const cx<T> ul0 = {al0.re + T(l == 0), al0.im}, ul1 = {al1.re + T(l == 1), al1.im};
+        const cx<T> R00 = S0[0], R01 = S0[1], R10 = S0[2], R11 = S0[3];
+        const cx<T> Rj0 = j ? R10 : R00, Rj1 = j ? R11 : R01;  // row j of rho
+        const cx<T> R0l = l ? R01 : R00, R1l = l ? R11 : R10;  // column l of rho
+        // (X rho Y^+)_jl for rows x0, x1 of X and y0, y1 of Y
+        auto sand = [&](cx<T> x0, cx<T> x1, cx<T> y0, cx<T> y1) {
+            const cx<T> t0 = cadd(cmul(x0, R00), cmul(x1, R10)), t1 = cadd(cmul(x0, R01), cmul(x1, R11));
+            return cadd(cmul(t0, cconj(y0)), cmul(t1, cconj(y1)));
+        };
+        r1[0] = sand(uj0, uj1, ul0, ul1);
+        cx<T> d = sand(aj0, aj1, al0, al1);
+        d = cadd(d, cadd(cmul(aj0, R0l), cmul(aj1, R1l)));                  // (A rho)_jl
+        d = cadd(d, cadd(cmul(Rj0, cconj(al0)), cmul(Rj1, cconj(al1))));    // (rho A^+)_jl
+        dr[0] = d;
+    } else {
+        const int ns = item.w >> 4;
+        const T h = a.dt / T(ns);
+#pragma unroll
+        for (int s = 0; s < SL; s++) {
+            r1[s] = r0[s];
+            dr[s] = {T(0), T(0)};
+        }
+        for (int sstep = 0; sstep < ns; sstep++) {
+            cx<T> base[SL], acc[SL];
+#pragma unroll
+            for (int s = 0; s < SL; s++) {
+                base[s] = r1[s];
+                acc[s] = {T(0), T(0)};
+            }
+            const cx<T> *Sc = S0;
+            cx<T> *Sn = S1;
+#pragma unroll
+            for (int st = 0; st < 4; st++) {
+                const T wgt = (st == 0 || st == 3) ? T(1) : T(2);
+                const T cn = (st < 2) ? T(0.5) : T(1);
+                cx<T> f[SL];
+#pragma unroll
+                for (int s = 0; s < SL; s++)
+                    if (own[s]) {
+                        f[s] = rhs_fixed<T, N>(jj[s], ll[s], Sc, Hs, decay, deph);
+                        acc[s].re += wgt * f[s].re;
+                        acc[s].im += wgt * f[s].im;
+                    }
+                if (st < 3) {
+#pragma unroll
+                    for (int s = 0; s < SL; s++)
+                        if (own[s]) {
+                            const cx<T> v = {base[s].re + cn * h * f[s].re, base[s].im + cn * h * f[s].im};
+                            Sn[jj[s] * N + ll[s]] = v;
+                            Sn[ll[s] * N + jj[s]] = cconj(v);
+                        }
+                    __syncwarp();
+                    const cx<T> *t = Sc;
+                    Sc = Sn;
+                    Sn = const_cast<cx<T> *>(t);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < SL; s++) {
+                const T ur = h / T(6) * acc[s].re, ui = h / T(6) * acc[s].im;
+                r1[s] = {base[s].re + ur, base[s].im + ui};
+                dr[s].re += ur;
+                dr[s].im += ui;
+            }
+            if (sstep + 1 < ns) {
+                __syncwarp();  // every lane is done reading the stage matrices
+#pragma unroll
+                for (int s = 0; s < SL; s++)
+                    if (own[s]) {
+                        S0[jj[s] * N + ll[s]] = r1[s];
+                        S0[ll[s] * N + jj[s]] = cconj(r1[s]);
+                    }
+                __syncwarp();
+            }
+        }
+    }
+
+    // ---- 4. outputs: rho (both halves), d<mu>/dt, current amplitude, energy sum
+    T dmu[3] = {T(0), T(0), T(0)};
+    T en = T(0);
+#pragma unroll
+    for (int s = 0; s < SL; s++)
+        if (own[s]) {
+            h0[s] = sh.K[wl][s][0][lane];
+#pragma unroll
+            for (int c = 0; c < 3; c++) mu[c][s] = sh.K[wl][s][1 + c][lane];
+            const int j = jj[s], l = ll[s];
+            const T wt = j == l ? T(1) : T(2);  // Re Tr(X A) over both halves of Hermitian X, A
+            a.rho[o + j * N + l] = r1[s];
+            if (j != l) a.rho[o + l * N + j] = cconj(r1[s]);
+            else if (a.pop_sink) a.pop_sink[a.pop_slot + (long long)m * MAXLEV + j] = (double)r1[s].re;
+#pragma unroll
+            for (int c = 0; c < 3; c++) dmu[c] += wt * (dr[s].re * mu[c][s].re + dr[s].im * mu[c][s].im);
+            en += wt * (r1[s].re * h0[s].re + r1[s].im * h0[s].im);
+        }
+    en = group_sum<T, G>(en);
+#pragma unroll
+    for (int c = 0; c < 3; c++) dmu[c] = ((cm >> c) & 1) ? group_sum<T, G>(dmu[c]) : T(0);
+    if (live && u0 == 0) {
+        bool bad = false;
+        for (int c = 0; c < 3; c++) {
+            const T md = dmu[c] / a.dt;
+            a.Et[3 * m + c] = Et[c];
+            a.mudot[3 * m + c] = md;
+            a.c[3 * m + c] = gam * md;
+            if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
+        }
+        a.energy[m] = e_old + (double)en;
+        if (bad) atomicCAS(a.status, 0, 6);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1)
+    molecule_packed_kernel(const MolArgs<T> a) {
+    __shared__ PackShared<T> sh;
+    const int wl = threadIdx.x >> 5;
+    const int it = (int)blockIdx.x * MOL_WARPS + wl;
+    if (it >= a.nitems) {
+        // no item: still take part in the launch chain
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        return;
+    }
+    const int4 item = a.items[it];
+    const int n = item.z;
+    if ((item.w & 15) == 0) {
+        packed_body<T, 2, true>(a, item, sh, wl);
+        return;
+    }
+    switch (n) {
+        case 2: packed_body<T, 2, false>(a, item, sh, wl); break;
+        case 3: packed_body<T, 3, false>(a, item, sh, wl); break;
+        case 4: packed_body<T, 4, false>(a, item, sh, wl); break;
+        case 5: packed_body<T, 5, false>(a, item, sh, wl); break;
+        case 6: packed_body<T, 6, false>(a, item, sh, wl); break;
+        case 7: packed_body<T, 7, false>(a, item, sh, wl); break;
+        default: packed_body<T, 8, false>(a, item, sh, wl); break;
+    }
+}
+
+template <typename T>
+cudaError_t launch_molecules_packed(const MolArgs<T> &a, cudaStream_t s, bool pdl) {
+    if (a.nitems == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.nitems + MOL_WARPS - 1) / MOL_WARPS);
+    cfg.blockDim = dim3(MOL_WARPS * 32);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, molecule_packed_kernel<T>, a);
 }
 
 // Uniform-field form for two-level molecules: one thread per molecule, so that a warp
@@ -738,6 +1085,7 @@ cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long lo
 
 #define ML_INST(T)                                                                                              \
     template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t, bool);                           \
+    template cudaError_t launch_molecules_packed<T>(const MolArgs<T> &, cudaStream_t, bool);                    \
     template cudaError_t launch_molecules_uniform<T>(const MolArgs<T> &, cudaStream_t);                             \
     template cudaError_t launch_molecules_batch<T>(const MolBatch<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \

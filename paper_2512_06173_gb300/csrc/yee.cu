@@ -109,12 +109,15 @@ constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before givin
 // Body of the field pass for one block.  MODE 0 is the interior form: the caller
 // guarantees the tile and its halo touch no CPML layer, wall, periodic image or
 // material/source cell, so none of those paths is compiled in.  MODE 1 adds the
-// CPML layers and the index-0 walls only; MODE 2 has every path.
+// CPML layers, the index-0 walls and the source sheets; MODE 3 is the interior form plus
+// the per-cell coefficient dt/eps of a material index (from a shared-memory table) and
+// the source sheets, for tiles clear of the layers and walls; MODE 2 has every path
+// (poles, design box, periodic images, and a material map next to a layer or wall).
 // Returns false when a plane wait gave up (the block then reported ML_ERR_TIMEOUT and
 // drained its copies); uniform over the block.
 template <typename T, int MODE>
 __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
-    constexpr bool GEN = MODE > 0, FULL = MODE == 2;
+    constexpr bool GEN = MODE == 1 || MODE == 2, FULL = MODE == 2, MATL = MODE == 3;
     constexpr int S = yee_stages<T>();
     constexpr int BP = box_pad<T>();
     constexpr int SW = 6 * BP;  // elements per stage
@@ -127,6 +130,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     __shared__ double s_red[NTHREADS / 32];
     __shared__ T sCx[6][BOXW];  // CPML coefficients at x = x0-4+col (bE cE kE bH cH kH)
     __shared__ T sCy[6][BOXH];  // at y = y0-1+row
+    __shared__ T s_cb[MATL ? ML_MAX_MATERIALS : 1];  // dt / eps_inf per material (MODE 3)
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
@@ -150,8 +154,16 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const bool walls = GEN && ((!a.per[0] && x0 == 0) || (!a.per[1] && y0 == 0) || (!a.per[2] && k0 == 0));
     // per-cell material work (material table, design box, poles, sources): only tiles
     // whose own cells need it, when the grid has the per-tile flags
-    const bool general = FULL && (a.tflags ? (a.tflags[tile] & 1) != 0
+    const bool general = FULL && (a.tflags ? (a.tflags[tile] & 7) != 0
                                           : (a.mat != nullptr || a.dcb != nullptr || a.JD != nullptr || a.nsrc > 0));
+    // MODES 1 and 3: does a source sheet cross the tile (block-uniform)?
+    bool has_src = false;
+    if (MODE == 1 || MATL)
+        for (int q = 0; q < a.nsrc; q++) {
+            const int ax = a.src[q].axis, idx = a.src[q].index;
+            const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
+            if (idx >= lo && idx < hi) has_src = true;
+        }
     // does the tile's column meet the box of the molecular current?
     const bool has_mol = (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
                          x0 + TX > a.jb0[0] && y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] &&
@@ -192,7 +204,8 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const int syh = fy ? slab(hjc, a.ny, a.pml[2], a.pml[3]) : -1;
     const int oh = hys * BOXW + hxs + 3;
 
-    if (FULL && tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
+    if (MODE > 0 && tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
+    if (MATL && tid < ML_MAX_MATERIALS) s_cb[tid] = a.mat_cb[tid];
     if (fx)
         for (int t = tid; t < 6 * BOXW; t += NTHREADS) {
             const int r = t / BOXW, cc = t % BOXW;
@@ -225,7 +238,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         for (int q = q0; q <= qlast && q < q0 + S; q++) { issue(q); issued = q; }
     bool ok = true;
     auto wait_stage = [&](int s, uint32_t par) {
-        if (ok && !mbar_wait_bounded(&bars[s], par, WAIT_LIMIT)) ok = false;
+        if (ok && !mbar_wait_bounded(&bars[s], par, a.wait_limit)) ok = false;
     };
     auto zslab = [&](int kc) { return zl ? slab(kc, a.nz, a.pml[4], a.pml[5]) : -1; };
     // Offsets of a cell at canonical (xc, yc, kc) in the three slab stores (-1 outside
@@ -300,6 +313,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         // thread's cells in the field precision (GB300's FP64 rate is a small fraction
         // of its FP32 rate); times dt/2 and summed in FP64 across the block
         T absorbed = T(0);
+        // MODE 3: material index of the own cell, plane by plane (loaded before the wait)
+        const long long nxy = (long long)a.nx * a.ny;
+        const uint8_t *mp = (MATL && a.mat) ? a.mat + ((long long)k0 * a.ny + jb) * a.nx + i : nullptr;
         int sc = 1 % S;               // stage of plane k (= k0 = q0 + 1)
         int sn = 2 % S;               // stage of plane k + 1
         uint32_t pn = S > 2 ? 0u : 1u;  // parity of the fill of stage sn that holds plane k + 1
@@ -327,6 +343,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 qh = slab_off(hic, hjc, k, sxh, syh, sz);
                 h_pml_load(phh, qh);
             }
+            const int midx_l = (MATL && mp && xin && jb < a.ny) ? (int)mp[0] : 0;
             wait_stage(sn, pn);
             const T *Ek = stages + sc * SW, *Ek1 = stages + sn * SW, *Hk = Ek + 3 * BP;
             const long long pb = (long long)(k + 1) * a.plane;
@@ -433,7 +450,23 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 const T eo0 = Ek[o], eo1 = Ek[BP + o], eo2 = Ek[2 * BP + o];
                 T j0 = J0[r], j1 = J1[r], j2 = J2[r];
                 T en0, en1, en2;
-                if (!general) {
+                if (MODE == 1 || MATL) {
+                    if (has_src)
+                        for (int q = 0; q < a.nsrc; q++) {
+                            const int ax = a.src[q].axis;
+                            const int pos = ax == 0 ? i : (ax == 1 ? j : k);
+                            if (pos == a.src[q].index) {
+                                const int cmp = a.src[q].comp;
+                                if (cmp == 0) j0 += s_src[q];
+                                else if (cmp == 1) j1 += s_src[q];
+                                else j2 += s_src[q];
+                            }
+                        }
+                    const T cb = MATL ? s_cb[midx_l] : cb0;
+                    en0 = eo0 + cb * (curl0 - j0);
+                    en1 = eo1 + cb * (curl1 - j1);
+                    en2 = eo2 + cb * (curl2 - j2);
+                } else if (!general) {
                     en0 = eo0 + cb0 * (curl0 - j0);
                     en1 = eo1 + cb0 * (curl1 - j1);
                     en2 = eo2 + cb0 * (curl2 - j2);
@@ -552,6 +585,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             }
             sc = sn;
             if (++sn == S) { sn = 0; pn ^= 1u; }
+            if (MATL && mp) mp += nxy;
         }
         if (FULL && a.JD) {
             // fixed-order block reduction into this block's accumulator
@@ -585,14 +619,21 @@ drain:
     return false;
 }
 
-// True when the block's tile (with its one-cell halo) needs none of the CPML, wall,
-// periodic-image and per-cell material paths of the field pass (the molecular
-// current and flux-plane sampling are block-uniform branches of every body).
+// Per-cell work flags of a tile: bit 0 = pole box or design box, bit 1 = a
+// non-background material, bit 2 = a source sheet.  Without the per-tile table every
+// tile of a grid with any such feature takes the full body.
 template <typename T>
-__device__ __forceinline__ bool interior_block(const YeeArgs<T> &a, const int tile) {
+__device__ __forceinline__ int tile_flags(const YeeArgs<T> &a, const int tile) {
+    return a.tflags ? (int)a.tflags[tile] : ((a.mat || a.dcb || a.JD || a.nsrc) ? 1 : 0);
+}
+
+// True when the block's tile (with its one-cell halo) touches none of the CPML layers,
+// walls and periodic images of the field pass (the molecular current and flux-plane
+// sampling are block-uniform branches of every body).
+template <typename T>
+__device__ __forceinline__ bool interior_geometry(const YeeArgs<T> &a, const int tile) {
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
-    if (a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD || a.nsrc)) return false;
     if (x0 == 0 || y0 == 0 || k0 == 0 || x0 + TX >= a.nx || y0 + TY >= a.ny || k1 >= a.nz) return false;
     if ((a.pml[0] && x0 - 1 < a.pml[0]) || (a.pml[1] && x0 + TX > a.nx - a.pml[1])) return false;
     if ((a.pml[2] && y0 - 1 < a.pml[2]) || (a.pml[3] && y0 + TY > a.ny - a.pml[3])) return false;
@@ -600,17 +641,21 @@ __device__ __forceinline__ bool interior_block(const YeeArgs<T> &a, const int ti
     return true;
 }
 
-// 0: interior body; 1: CPML and walls only (no periodic image, no per-cell material
-// work in the tile); 2: every path.
+// 0: interior body; 1: CPML, walls and source sheets (no periodic image, material map,
+// pole or design box in the tile); 3: interior geometry with a material map or source
+// sheets; 2: every path.
 template <typename T>
 __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
-    if (interior_block(a, tile)) return 0;
+    const int fl = tile_flags(a, tile);
+    if (interior_geometry(a, tile)) {
+        if (fl == 0) return 0;
+        if ((fl & 1) == 0) return 3;
+    }
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
     const bool img = (a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
                      (a.per[2] && (k0 == 0 || k1 == a.nz));
-    const bool gen = a.tflags ? (a.tflags[tile] & 1) != 0 : (a.mat || a.dcb || a.JD || a.nsrc);
-    return (img || gen) ? 2 : 1;
+    return (img || (fl & 3) != 0) ? 2 : 1;
 }
 
 template <typename T>
@@ -618,6 +663,7 @@ __device__ __forceinline__ bool yee_dispatch(const YeeArgs<T> &a, const TmapSet 
     const int mode = block_mode(a, tile);
     if (mode == 0) return yee_body<T, 0>(a, maps, tile);
     if (mode == 1) return yee_body<T, 1>(a, maps, tile);
+    if (mode == 3) return yee_body<T, 3>(a, maps, tile);
     return yee_body<T, 2>(a, maps, tile);
 }
 

@@ -87,6 +87,46 @@ class ml_drive_desc(C.Structure):
 
 _lib = None
 
+# ml_alloc_fn / ml_free_fn of the header
+_ALLOC_T = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_void_p), C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class TorchAllocator:
+    """The boundary's allocator callback backed by PyTorch's caching allocator: every
+    device buffer the library allocates comes from `torch.cuda.caching_allocator_alloc`
+    and goes back through `torch.cuda.caching_allocator_delete`.  Counts the calls and
+    the bytes the library holds."""
+
+    def __init__(self):
+        self.allocs = 0
+        self.frees = 0
+        self.live_bytes = 0
+        self.c_alloc = _ALLOC_T(self._alloc)
+        self.c_free = _FREE_T(self._free)
+
+    def _alloc(self, pp, nbytes, stream, ctx):
+        try:
+            import torch
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:
+            return 1
+        pp[0] = ptr
+        self.allocs += 1
+        self.live_bytes += int(nbytes)
+        return 0
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        try:
+            import torch
+            torch.cuda.caching_allocator_delete(int(ptr))
+        finally:
+            self.frees += 1
+            self.live_bytes -= int(nbytes)
+
+
+_allocator: Optional[TorchAllocator] = None
+
 
 class MaxlinkError(RuntimeError):
     def __init__(self, status, msg):
@@ -130,6 +170,8 @@ def load(build_if_missing: bool = True):
         "ml_flux_data": (I, [P, I, P, P]),
         "ml_absorbed": (I, [P, P, P]),
         "ml_sync_status": (I, [P, P]),
+        "ml_set_wait_limit": (I, [P, I64]),
+        "ml_set_allocator": (I, [_ALLOC_T, _FREE_T, P]),
         "ml_step_count": (I64, [P]),
         "ml_molecule_count": (I, [P]),
         "ml_checkpoint": (I, [P, P, C.POINTER(C.c_size_t), P]),
@@ -164,7 +206,50 @@ def load(build_if_missing: bool = True):
         f.restype = res
         f.argtypes = args
     _lib = L
+    # device memory of the library from PyTorch's caching allocator when a GPU is present
+    try:
+        import torch
+        if torch.cuda.is_available() and os.environ.get("ML_ALLOCATOR", "torch") == "torch":
+            use_torch_allocator()
+    except ImportError:
+        pass
     return L
+
+
+def ml_set_allocator(alloc=None, free=None, ctx=None):
+    """Install ctypes callbacks of types `_ALLOC_T` / `_FREE_T` as the library's device
+    allocator (None, None: the library default).  The caller keeps the callbacks alive."""
+    _check(load().ml_set_allocator(alloc if alloc is not None else _ALLOC_T(),
+                                   free if free is not None else _FREE_T(), ctx))
+
+
+def use_torch_allocator() -> TorchAllocator:
+    """Install (once) the PyTorch-backed allocator and return it."""
+    global _allocator
+    L = load()
+    if _allocator is None:
+        a = TorchAllocator()
+        _check(L.ml_set_allocator(a.c_alloc, a.c_free, None))
+        _allocator = a
+    return _allocator
+
+
+def use_default_allocator():
+    """Back to the library's default allocator (cudaMallocAsync / cudaFreeAsync).  Buffers
+    allocated before keep going back to the allocator they came from."""
+    global _allocator
+    _check(load().ml_set_allocator(_ALLOC_T(), _FREE_T(), None))
+    if _allocator is not None:
+        _keep_alive.append(_allocator)
+    _allocator = None
+
+
+_keep_alive: List[TorchAllocator] = []  # allocators whose buffers may still be alive
+
+
+def allocator() -> Optional[TorchAllocator]:
+    """The PyTorch-backed allocator in use, or None (library default)."""
+    return _allocator
 
 
 def _check(status: int):
@@ -251,6 +336,16 @@ def ml_absorbed(h: int, stream: int = 0) -> float:
 
 def ml_sync_status(h: int, stream: int = 0):
     _check(load().ml_sync_status(C.c_void_p(h), C.c_void_p(stream)))
+
+
+def ml_sync_status_code(h: int, stream: int = 0) -> int:
+    """The latched device status as an integer (ML_OK, ML_ERR_TIMEOUT, ML_ERR_NUMERIC ...),
+    without raising."""
+    return int(load().ml_sync_status(C.c_void_p(h), C.c_void_p(stream)))
+
+
+def ml_set_wait_limit(h: int, probes: int):
+    _check(load().ml_set_wait_limit(C.c_void_p(h), int(probes)))
 
 
 def ml_step_count(h: int) -> int:

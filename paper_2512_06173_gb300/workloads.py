@@ -294,13 +294,16 @@ def bragg_ensemble(nx=512, ny=512, nz=384, nmol=100000, pml=10, slab=32, seed=3,
     xc = nx // 2
     half = layers // 2
     # stack on both sides of the slab: (4 cells eps 2.25, 6 cells eps 1) x half
+    # (on a grid too narrow for the whole stack the layers that would leave it are dropped)
     x = xc + slab // 2
     for _ in range(half):
-        mat[:, :, x:x + 4] = 1
+        if x + 4 <= nx:
+            mat[:, :, x:x + 4] = 1
         x += 10
     x = xc - slab // 2
     for _ in range(half):
-        mat[:, :, x - 4:x] = 1
+        if x - 4 >= 0:
+            mat[:, :, x - 4:x] = 1
         x -= 10
     mats = []
     nl = rng.integers(2, 9, size=nmol)

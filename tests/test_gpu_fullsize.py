@@ -1,9 +1,16 @@
-"""The benchmarked workload at its full size and in the launch configuration bench.py
-times (FP32, molecule -> current -> field pass as programmatic dependent launches):
+"""Full-size parity in the launch configuration bench.py times (FP32, molecule -> current
+-> field pass as programmatic dependent launches):
 
-- against the FP64 oracle: the 256^3 superradiant slab with 10,000 two-level emitters,
-  20 steps from seeded random fields, every field value (relative L2 <= 1e-4) and every
-  emitter's populations;
+- the 256^3 superradiant slab with 10,000 two-level emitters, 20 steps from seeded random
+  fields, against the FP64 oracle: every field value (relative L2 <= 1e-4), the emitters'
+  coherences rho_01 and dipole rates (relative L2 <= 1e-4), and the change of their
+  excited populations, whose FP32 error is set by storing rho_11 ~ 1 in FP32: it must stay
+  within 3x of what the oracle itself shows with its state rounded to FP32 after every
+  step (or within 1e-4 relative L2);
+- a 256 x 256 x 192 copy of the Bragg-resonator ensemble (the headline workload's stack,
+  slab and molecule mix: 15,000 systems of 2..8 levels, RK4), 24 steps from seeded random
+  fields: fields, density matrices, excited populations, regularised fields, dipole rates
+  and flux spectra within relative L2 1e-4 of the oracle;
 - the overlapped launch chain against the serialised one (ML_PDL=0, read when a grid is
   created) on a 128^3 copy: bit-identical fields, density matrices and DFT sums.  A
   dependency the overlap had lost would show up here as a difference.
@@ -65,6 +72,17 @@ def test_overlapped_chain_is_bit_identical_to_serialised(ml, monkeypatch):
             assert np.array_equal(x, y)
 
 
+def rounded_molecules(prob):
+    """The problem with its molecule parameters rounded to FP32 (as the FP32 path holds them)."""
+    from paper_2512_06173_gb300 import workloads as Wm
+    m = prob.molecules
+    f32 = lambda x: x.astype(np.float32).astype(np.float64)
+    c64 = lambda x: x.astype(np.complex64).astype(np.complex128)
+    mr = Wm.Molecules(m.nlev, m.off, m.pos, m.sigma, f32(m.gamma), f32(m.decay), f32(m.dephase), m.kind, m.nsub,
+                      c64(m.H0), c64(m.mu), c64(m.rho0))
+    return prob.replace(molecules=mr)
+
+
 def test_full_size_bench_workload_against_oracle(ml, oracle_mod):
     prob = W.superradiant_slab()
     f0 = random_fields(prob, 2)
@@ -76,6 +94,52 @@ def test_full_size_bench_workload_against_oracle(ml, oracle_mod):
         g.sync()
         fg = g.fields()
         pops = g.molecules(ml.ML_MOL_POP)
+        rho = g.molecules(ml.ML_MOL_RHO).reshape(-1, 4)
+        md = g.molecules(ml.ML_MOL_MUDOT)
+    finally:
+        g.close()
+    M = prob.molecules.count
+    o = oracle_mod.OracleSim(prob)
+    o.set_fields(f0)
+    o.step(steps)
+    for got, want in zip(fg, o.fields()):
+        assert rel(got, want) < 1e-4
+    ro = [o.rho(m) for m in range(M)]
+    c01 = np.array([r[0, 1] for r in ro])
+    assert np.linalg.norm(rho[:, 1] - c01) < 1e-4 * np.linalg.norm(c01)
+    assert rel(md, np.array([o.mol_state(m)[1] for m in range(M)])) < 1e-4
+    # change of the excited populations against the FP32 storage floor
+    pe0 = np.real(prob.molecules.rho0.reshape(-1, 4)[:, 3])
+    d_o = np.array([r[1, 1].real for r in ro]) - pe0
+    d_g = pops[:, 1] - pe0
+    o32 = oracle_mod.OracleSim(rounded_molecules(prob))
+    o32.set_fields(f0)
+    for _ in range(steps):
+        o32.step(1)
+        for m in range(M):
+            o32.set_rho(m, o32.rho(m).astype(np.complex64).astype(np.complex128))
+        o32.set_fields([f.astype(np.float32).astype(np.float64) for f in o32.fields()])
+    d_32 = np.array([o32.rho(m)[1, 1].real for m in range(M)]) - pe0
+    floor = np.linalg.norm(d_32 - d_o)
+    assert np.linalg.norm(d_g - d_o) <= max(1e-4 * np.linalg.norm(d_o), 3.0 * floor)
+
+
+def test_bragg_ensemble_copy_at_size(ml, oracle_mod):
+    prob = W.bragg_ensemble(nx=256, ny=256, nz=192, nmol=15000)
+    f0 = random_fields(prob, 3)
+    steps = 24
+    g = ml.Grid(prob, 0)
+    M = prob.molecules.count
+    try:
+        g.set_fields(f0)
+        g.step(steps)
+        g.sync()
+        fg = g.fields()
+        rho = g.molecules(ml.ML_MOL_RHO)
+        pops = g.molecules(ml.ML_MOL_POP)
+        md = g.molecules(ml.ML_MOL_MUDOT)
+        et = g.molecules(ml.ML_MOL_EFIELD)
+        flux = [g.flux(p) for p in range(len(prob.planes))]
     finally:
         g.close()
     o = oracle_mod.OracleSim(prob)
@@ -83,5 +147,15 @@ def test_full_size_bench_workload_against_oracle(ml, oracle_mod):
     o.step(steps)
     for got, want in zip(fg, o.fields()):
         assert rel(got, want) < 1e-4
-    po = np.array([np.real(p[:2]) for p in o.populations()])
-    assert np.abs(pops[:, :2] - po).max() < 1e-4
+    mol = prob.molecules
+    ro = np.concatenate([o.rho(m).ravel() for m in range(M)])
+    assert np.linalg.norm(rho - ro) < 1e-4 * np.linalg.norm(ro)
+    nl = mol.nlev
+    pe_g = np.concatenate([pops[m, 1:nl[m]] for m in range(M)])
+    pe_o = np.concatenate([np.real(np.diag(o.rho(m)))[1:] for m in range(M)])
+    assert pe_o.max() > 1e-6 and rel(pe_g, pe_o) < 1e-4
+    st = [o.mol_state(m) for m in range(M)]
+    assert rel(md, np.array([x[1] for x in st])) < 1e-4
+    assert rel(et[:, 2], np.array([x[0][2] for x in st])) < 1e-4  # z-dipoles: E_z is gathered
+    for p in range(len(prob.planes)):
+        assert rel(flux[p], o.flux(p)) < 1e-4

@@ -3,7 +3,9 @@ seeded inputs, element by element.
 
 Tolerances: FP64 GPU runs agree with the oracle to round-off (relative L2 <= 1e-10;
 the summation order of the molecular current and the kernel sums differ); FP32
-runs agree within relative L2 <= 1e-4 for fields and populations.
+runs agree within relative L2 <= 1e-4 for fields, density matrices, excited-level
+populations, dipole rates d<mu>/dt, regularised fields, energy sums and flux spectra
+(measured FP32 errors are 1e-8 .. 1e-5).
 """
 import numpy as np
 import pytest
@@ -31,6 +33,19 @@ def rel(a, b):
     b = np.asarray(b, np.float64).ravel()
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def crel(a, b):
+    a = np.asarray(a, np.complex128).ravel()
+    b = np.asarray(b, np.complex128).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def excited(pops, prob):
+    """Populations of the excited levels (1 .. n-1) of every molecule, concatenated."""
+    nl = prob.molecules.nlev
+    return np.concatenate([pops[m, 1:int(nl[m])] for m in range(prob.molecules.count)])
 
 
 def run_pair(ml, oracle_mod, prob, steps, precision, fields=None, molecules=True):
@@ -78,8 +93,8 @@ def test_thin_periodic_layer(ml, oracle_mod, precision, tol):
     g, o = run_pair(ml, oracle_mod, prob, 120, precision)
     for got, want in zip(g.fields(), o.fields()):
         assert rel(got, want) < tol
-    for m in range(2):
-        assert np.abs(g.rho(m) - o.rho(m)).max() < tol * 10
+    assert crel(np.concatenate([g.rho(m).ravel() for m in range(2)]),
+                np.concatenate([o.rho(m).ravel() for m in range(2)])) < tol
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
@@ -91,12 +106,11 @@ def test_coupled_all_features(ml, oracle_mod, precision, tol, seed):
     g, o = run_pair(ml, oracle_mod, prob, 60, precision)
     for got, want in zip(g.fields(), o.fields()):
         assert rel(got, want) < tol
-    for m in range(prob.molecules.count):
-        assert np.abs(g.rho(m) - o.rho(m)).max() < 10 * tol
+    M = prob.molecules.count
+    assert crel(np.concatenate([g.rho(m).ravel() for m in range(M)]),
+                np.concatenate([o.rho(m).ravel() for m in range(M)])) < tol
     pops = g.molecules(ml.ML_MOL_POP)
-    for m in range(prob.molecules.count):
-        n = int(prob.molecules.nlev[m])
-        assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+    assert rel(excited(pops, prob), np.concatenate([np.real(np.diag(o.rho(m)))[1:] for m in range(M)])) < tol
     # the enqueued readback into page-locked memory gives the same bytes once the
     # stream has reached it
     import torch
@@ -105,12 +119,10 @@ def test_coupled_all_features(ml, oracle_mod, precision, tol, seed):
     torch.cuda.synchronize()
     assert np.array_equal(pinned.numpy().reshape(pops.shape), pops)
     md = g.molecules(ml.ML_MOL_MUDOT)
-    for m in range(prob.molecules.count):
-        _, omd, _ = o.mol_state(m)
-        assert np.abs(md[m] - omd).max() <= 10 * tol * max(1.0, np.abs(omd).max())
+    assert rel(md, np.array([o.mol_state(m)[1] for m in range(M)])) < tol
     for p in range(len(prob.planes)):
         fg, fo = g.flux(p), o.flux(p)
-        assert rel(fg, fo) < (1e-9 if precision == 1 else 1e-3)
+        assert rel(fg, fo) < (1e-9 if precision == 1 else tol)
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
@@ -126,15 +138,15 @@ def test_bragg_resonator_copy(ml, oracle_mod, precision, tol):
     scale = max(np.linalg.norm(f) for f in fo)
     for got, want in zip(g.fields(), fo):
         assert np.linalg.norm(np.asarray(got, np.float64) - want) < tol * scale
+    M = prob.molecules.count
     pops = g.molecules(ml.ML_MOL_POP)
-    for m in range(prob.molecules.count):
-        n = int(prob.molecules.nlev[m])
-        assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+    assert rel(excited(pops, prob), np.concatenate([np.real(np.diag(o.rho(m)))[1:] for m in range(M)])) < tol
+    assert rel(g.molecules(ml.ML_MOL_MUDOT), np.array([o.mol_state(m)[1] for m in range(M)])) < tol
     # the far plane has not seen the pulse yet: errors against the larger flux
     fl = [(g.flux(p), o.flux(p)) for p in range(len(prob.planes))]
     fscale = max(np.abs(fo).max() for _, fo in fl)
     for fg, fo in fl:
-        assert np.abs(fg - fo).max() < (1e-9 if precision == 1 else 1e-3) * fscale
+        assert np.abs(fg - fo).max() < (1e-9 if precision == 1 else tol) * fscale
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
@@ -144,7 +156,7 @@ def test_drude_sphere(ml, oracle_mod, precision, tol):
     for got, want in zip(g.fields(), o.fields()):
         assert rel(got, want) < tol
     ab_g, ab_o = g.absorbed(), o.absorbed()
-    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
+    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else tol) * abs(ab_o)
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
@@ -157,11 +169,10 @@ def test_lorentz_drude_sphere(ml, oracle_mod, precision, tol):
     for got, want in zip(g.fields(), o.fields()):
         assert rel(got, want) < tol
     ab_g, ab_o = g.absorbed(), o.absorbed()
-    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
+    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else tol) * abs(ab_o)
+    M = prob.molecules.count
     pops = g.molecules(ml.ML_MOL_POP)
-    for m in range(prob.molecules.count):
-        n = int(prob.molecules.nlev[m])
-        assert np.abs(pops[m, :n] - np.real(np.diag(o.rho(m)))).max() < 10 * tol
+    assert rel(excited(pops, prob), np.concatenate([np.real(np.diag(o.rho(m)))[1:] for m in range(M)])) < tol
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
@@ -178,12 +189,12 @@ def test_dispersive_stack_small(ml, oracle_mod, precision, tol):
     pops = g.molecules(ml.ML_MOL_POP)
     pe_o = np.array([np.real(o.rho(m)[1, 1]) for m in range(prob.molecules.count)])
     assert pe_o.max() > 1e-6  # the pulse has reached the emitters
-    assert np.abs(pops[:, 1] - pe_o).max() < 10 * tol * max(pe_o.max(), 1e-3)
+    assert rel(pops[:, 1], pe_o) < tol
     for p in range(len(prob.planes)):
         fg, fw = g.flux(p), o.flux(p)
-        assert np.abs(fg - fw).max() < (1e-9 if precision == 1 else 1e-3) * np.abs(fw).max()
+        assert np.abs(fg - fw).max() < (1e-9 if precision == 1 else tol) * np.abs(fw).max()
     ab_g, ab_o = g.absorbed(), o.absorbed()
-    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else 1e-3) * abs(ab_o)
+    assert abs(ab_g - ab_o) <= (1e-9 if precision == 1 else tol) * abs(ab_o)
 
 
 def test_lorentz_checkpoint_and_adjoint_refusal(ml):
@@ -219,7 +230,7 @@ def test_plain_single_emitter_trajectory(ml, oracle_mod, precision, tol):
     assert rel(pe_g, pe_o) < tol
     ez_g = g.fields(ml.ML_EZ)[0][:, 20, 20]
     ez_o = o.fields()[2][:, 20, 20]
-    assert rel(ez_g, ez_o) < (tol if precision == 1 else 1e-3)
+    assert rel(ez_g, ez_o) < tol
 
 
 def test_checkpoint_roundtrip(ml):
@@ -292,3 +303,46 @@ def test_population_sink(ml, two_level):
             ml.ml_set_population_sink(g.h, sink.data_ptr(), 0)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+@pytest.mark.parametrize("seed", [0, 3])
+def test_molecule_field_and_energy(ml, oracle_mod, precision, tol, seed):
+    """The regularised field of the last step (Eq. E_regu_Emi, ML_MOL_EFIELD) and the
+    FP64 running sum of Tr(rho H0) over the steps (ML_MOL_ENERGY) of every molecule,
+    two-level and multilevel, against the oracle's."""
+    prob = W.small_coupled(seed=seed, shape=(37, 22, 29))
+    g, o = run_pair(ml, oracle_mod, prob, 60, precision)
+    mol = prob.molecules
+    M = mol.count
+    st = [o.mol_state(m) for m in range(M)]
+    et_o = np.array([s[0] for s in st])
+    en_o = np.array([s[2] for s in st])
+    # the components along which a molecule has a dipole (the others do not enter its
+    # Hamiltonian and are not gathered: they read 0)
+    cm = np.array([[np.any(mol.matrix(mol.mu[c], m) != 0) for c in range(3)] for m in range(M)])
+    et_g = g.molecules(ml.ML_MOL_EFIELD)
+    assert np.abs(et_o[cm]).max() > 0 and np.all(et_g[~cm] == 0)
+    assert rel(et_g[cm], et_o[cm]) < tol
+    assert rel(g.molecules(ml.ML_MOL_ENERGY), en_o) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+@pytest.mark.parametrize("case", ["material", "source"])
+def test_material_and_source_bodies(ml, oracle_mod, precision, tol, case):
+    """Grids large enough for tiles clear of every layer and wall: a layer stack across
+    interior tiles (the material body of the field pass: dt/eps from the material table)
+    and a source sheet crossing interior tiles and CPML tiles (the interior-geometry and
+    CPML bodies with a source), with molecules, against the oracle."""
+    if case == "material":
+        prob = W.bragg_ensemble(nx=136, ny=40, nz=44, nmol=12, pml=4, slab=8, layers=6, width=6.0)
+    else:
+        prob = W.small_coupled(seed=3, shape=(70, 30, 40), eps_map=False, nmol=6)
+    g, o = run_pair(ml, oracle_mod, prob, 120, precision)
+    fo = o.fields()
+    scale = max(np.linalg.norm(f) for f in fo)
+    for got, want in zip(g.fields(), fo):
+        assert np.linalg.norm(np.asarray(got, np.float64) - want) < tol * scale
+    M = prob.molecules.count
+    ro = [o.rho(m) for m in range(M)]
+    assert crel(np.concatenate([g.rho(m).ravel() for m in range(M)]), np.concatenate([r.ravel() for r in ro])) < tol

@@ -528,12 +528,21 @@ def measure_batch(args, stream):
         launches = b.launches - l0
         ab_p = np.array([g.absorbed() for g in plain])
         ab_b = np.array([g.absorbed() for g in grids])
+        # the batch's field passes move at least the algorithmic bytes of every instance's
+        # field pass each step: that over the batched step time (which also holds the
+        # molecule, current and fold kernels) is a lower bound of the field passes' rate
+        hbm, peak_kind = peaks()
+        alg = sum(field_pass_bytes(p, 4) for p in probs)
+        step_gbs = alg / (batch_ms / K / 1e3) / 1e9
         return {"workload": f"{len(probs)} plasmonic realisations, edges {{64,96,128,160}}, Drude sphere r=edge/6, "
                             f"200-5000 emitters in a shell, z-polarised pulse", "instances": len(probs),
                 "cells": cells, "molecules": int(sum(p.molecules.count for p in probs)), "steps": K,
                 "dtype": "f32", "plain_ms": plain_ms, "batched_ms": batch_ms,
                 "plain_gcells": cells * K / plain_ms / 1e6, "batched_gcells": cells * K / batch_ms / 1e6,
                 "speedup": plain_ms / batch_ms, "blocks_per_sm": choice, "autotune_trial_ms": tune_ms,
+                "roofline": {"bound": "hbm", "alg_bytes_per_step": alg, "achieved_gbs_whole_step": step_gbs,
+                             "peak": hbm, "peak_kind": peak_kind, "frac": step_gbs / hbm,
+                             "note": "field-pass algorithmic bytes of all instances over the whole batched step"},
                 "batched_launches": int(launches),
                 "absorbed_max_rel_diff": float(np.max(np.abs(ab_p - ab_b) / np.maximum(np.abs(ab_p), 1e-300))),
                 "absorbed_sum": float(ab_b.sum())}

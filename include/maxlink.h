@@ -298,10 +298,12 @@ ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *strea
  * periodic axes, molecule gather/step/scatter); the field history is rebuilt from
  * full-state device checkpoints taken every ckpt_every steps, each segment
  * recomputed once (device memory ~ nsteps/ckpt_every checkpoints plus ckpt_every
- * design-box E records).  Molecules must be exact two-level ones (kind 0) with
- * gamma != 0; materials may carry Drude poles but no Lorentz pole (omega0 > 0 is
- * ML_ERR_INVALID_ARG).  Allocates its work memory for the call and frees it;
- * synchronises `stream`. */
+ * design-box E records).  Molecules of both kinds (the exact two-level step, and the
+ * RK4 GKSL step of up to ML_MAX_LEVELS levels with decay, dephasing and substeps, whose
+ * stages are walked back) with gamma != 0; materials may carry Drude poles but no
+ * Lorentz pole (omega0 > 0 is ML_ERR_INVALID_ARG).  Allocates its work memory for the call and frees it;
+ * synchronises `stream`.  With both gradient pointers NULL the call runs only the
+ * forward steps and returns the objective (no checkpoints, no reverse sweep). */
 ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_id, int freq, double *objective,
                          double *grad_eps, double *grad_gamma, int on_device, void *stream);
 
@@ -453,7 +455,9 @@ ml_status ml_batch_destroy(ml_batch *b);
  *
  * The first call on each device does a one-time set-up (it looks up the device
  * address of the scratch array with the device current); make that first call
- * before any stream capture.  All calls on a device share the one scratch array,
+ * before any stream capture.  The looked-up address is kept for the life of the
+ * process, so do not call the entry point after cudaDeviceReset on that device.  The
+ * stream must belong to the current device (else ML_ERR_INVALID_ARG).  All calls on a device share the one scratch array,
  * so calls that overlap on the GPU (on different streams, or from several host
  * threads) race and give wrong results: order them on one stream or synchronise
  * between them. */

@@ -306,7 +306,8 @@ class OracleSim:
         self.L.orc_adj_field(self.h)
 
     def mol_vjp(self, m: int, Et, rho: np.ndarray, X: np.ndarray, mdb):
-        """Adjoints of (rho, Et) of one exact two-level step from those of (rho', mudot)."""
+        """Adjoints of (rho, Et) of one molecule step (exact two-level or RK4 GKSL) from
+        those of (rho', mudot)."""
         n = rho.shape[0]
         rb = np.zeros(2 * n * n)
         Etb = np.zeros(3)
@@ -324,8 +325,6 @@ class OracleSim:
         gg = np.zeros(max(self.nmol, 1))
         obj = np.zeros(1)
         rc = self.L.orc_adjoint_run(self.h, int(nsteps), int(plane), int(freq), ge, gg, obj)
-        if rc == -2:
-            raise ValueError("the adjoint takes exact two-level molecules only")
         if rc != 0:
             raise ValueError(f"adjoint run failed ({rc})")
         return float(obj[0]), ge.reshape(self.shape), gg[:self.nmol]

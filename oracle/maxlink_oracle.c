@@ -226,16 +226,23 @@ int orc_add_molecule(osim *s, int n, const double *pos, double sigma, double gam
 /* Gaussian kernel (Eq. Polarization_mol with the Gaussian choice of Sec. II.A.1):
  * along axis a the window is the 2R+2 indices starting at floor(pos)-R, R=ceil(3 sigma);
  * sample positions are i (stag=0) or i+1/2 (stag=1); the 1D weights are normalised
- * to sum 1 over the window, so the 3D sum of kappa times the cell volume is 1. */
+ * to sum 1 over the window, so the 3D sum of kappa times the cell volume is 1.  The
+ * Gaussian is evaluated relative to the window's nearest sample (a common factor that
+ * the normalisation removes), so a narrow kernel gives finite weights instead of 0/0. */
 static int window(const omol *m, int a, int stag, int *i0, double *w) {
     int R = (int)ceil(3.0 * m->sigma);
     int W = 2 * R + 2;
     *i0 = (int)floor(m->pos[a]) - R;
-    double sum = 0.0;
+    double d2[32], dmin = INFINITY;
     for (int t = 0; t < W; t++) {
         double x = (*i0 + t) + 0.5 * stag;
         double d = x - m->pos[a];
-        w[t] = exp(-d * d / (2.0 * m->sigma * m->sigma));
+        d2[t] = d * d;
+        if (d2[t] < dmin) dmin = d2[t];
+    }
+    double sum = 0.0;
+    for (int t = 0; t < W; t++) {
+        w[t] = exp(-(d2[t] - dmin) / (2.0 * m->sigma * m->sigma));
         sum += w[t];
     }
     for (int t = 0; t < W; t++) w[t] /= sum;
@@ -996,9 +1003,91 @@ static double rdot(int n, const cplx *X, const cplx *Y) {
     return acc;
 }
 
-/* Vector-Jacobian product of one exact two-level step (rho, Et) -> (rho', mudot)
- * with rho' = U rho U^+, U = exp(-i dt (H0 - Et . mu)), mudot = (<mu>(rho') - <mu>(rho))/dt:
- * given the adjoints X of rho' and mdb of mudot, returns those of rho (rhob) and Et (Etb). */
+/* Adjoint of the GKSL right-hand side under the real inner product Re Tr(X^+ Y):
+ * for L(rho) = -i [H, rho] + sum_k (L_k rho L_k^+ - 1/2 {L_k^+ L_k, rho}) with Hermitian H,
+ *   L^+(X) = i [H, X] + sum_k (L_k^+ X L_k - 1/2 {L_k^+ L_k, X}),
+ * the jump operators of lindblad_rhs, multiplied out literally. */
+static void lindblad_adj(const omol *m, const cplx *H, const cplx *X, cplx *out) {
+    int n = m->n;
+    cplx A[MAXLEV * MAXLEV], B[MAXLEV * MAXLEV], L[MAXLEV * MAXLEV], Ld[MAXLEV * MAXLEV];
+    cplx LdL[MAXLEV * MAXLEV], T1[MAXLEV * MAXLEV], T2[MAXLEV * MAXLEV];
+    matmul(n, H, X, A);
+    matmul(n, X, H, B);
+    for (int e = 0; e < n * n; e++) out[e] = I * (A[e] - B[e]);
+    for (int pass = 0; pass < 2; pass++) {
+        double rate = pass == 0 ? m->decay : m->dephase;
+        if (rate == 0.0) continue;
+        for (int k = (pass == 0 ? 1 : 0); k < n; k++) {
+            memset(L, 0, sizeof(L));
+            if (pass == 0) L[(k - 1) * n + k] = sqrt(rate);
+            else L[k * n + k] = sqrt(rate);
+            dagger(n, L, Ld);
+            matmul(n, Ld, L, LdL);
+            matmul(n, Ld, X, T1);
+            matmul(n, T1, L, T2);           /* L^+ X L */
+            matmul(n, LdL, X, A);
+            matmul(n, X, LdL, B);
+            for (int e = 0; e < n * n; e++) out[e] += T2[e] - 0.5 * (A[e] + B[e]);
+        }
+    }
+}
+
+/* Re Tr(Y^+ dL/dEt_a (S)) for each a: H = H0 - Et . mu, so dL/dEt_a (S) = i [mu_a, S]. */
+static void dl_de_dot(const omol *m, const cplx *Y, const cplx *S, double *acc) {
+    int n = m->n;
+    cplx A[MAXLEV * MAXLEV], B[MAXLEV * MAXLEV], D[MAXLEV * MAXLEV];
+    for (int a = 0; a < 3; a++) {
+        matmul(n, m->mu[a], S, A);
+        matmul(n, S, m->mu[a], B);
+        for (int e = 0; e < n * n; e++) D[e] = I * (A[e] - B[e]);
+        acc[a] += rdot(n, Y, D);
+    }
+}
+
+/* Reverse of one classic RK4 substep of length h under the held H (molecule_advance):
+ * given the adjoint Y of the substep's result and its start rho, replaces Y by the
+ * adjoint of rho and adds the substep's part of the adjoint of Et to Etb.  The forward
+ * stages are recomputed from rho; the reverse walks them back (k4, k3, k2, k1). */
+static void rk4_vjp(const omol *m, const cplx *H, const cplx *rho, double h, cplx *Y, double *Etb) {
+    const int n = m->n;
+    cplx k[MAXLEV * MAXLEV], S2[MAXLEV * MAXLEV], S3[MAXLEV * MAXLEV], S4[MAXLEV * MAXLEV];
+    cplx kb1[MAXLEV * MAXLEV], kb2[MAXLEV * MAXLEV], kb3[MAXLEV * MAXLEV], kb4[MAXLEV * MAXLEV];
+    cplx Sb[MAXLEV * MAXLEV], rb[MAXLEV * MAXLEV];
+    lindblad_rhs(m, H, rho, k);
+    for (int e = 0; e < n * n; e++) S2[e] = rho[e] + 0.5 * h * k[e];
+    lindblad_rhs(m, H, S2, k);
+    for (int e = 0; e < n * n; e++) S3[e] = rho[e] + 0.5 * h * k[e];
+    lindblad_rhs(m, H, S3, k);
+    for (int e = 0; e < n * n; e++) S4[e] = rho[e] + h * k[e];
+    /* rho' = rho + h/6 (k1 + 2 k2 + 2 k3 + k4) */
+    for (int e = 0; e < n * n; e++) {
+        rb[e] = Y[e];
+        kb1[e] = kb4[e] = h / 6.0 * Y[e];
+        kb2[e] = kb3[e] = h / 3.0 * Y[e];
+    }
+    /* k4 = L(S4), S4 = rho + h k3 */
+    lindblad_adj(m, H, kb4, Sb);
+    dl_de_dot(m, kb4, S4, Etb);
+    for (int e = 0; e < n * n; e++) { rb[e] += Sb[e]; kb3[e] += h * Sb[e]; }
+    /* k3 = L(S3), S3 = rho + h/2 k2 */
+    lindblad_adj(m, H, kb3, Sb);
+    dl_de_dot(m, kb3, S3, Etb);
+    for (int e = 0; e < n * n; e++) { rb[e] += Sb[e]; kb2[e] += 0.5 * h * Sb[e]; }
+    /* k2 = L(S2), S2 = rho + h/2 k1 */
+    lindblad_adj(m, H, kb2, Sb);
+    dl_de_dot(m, kb2, S2, Etb);
+    for (int e = 0; e < n * n; e++) { rb[e] += Sb[e]; kb1[e] += 0.5 * h * Sb[e]; }
+    /* k1 = L(rho) */
+    lindblad_adj(m, H, kb1, Sb);
+    dl_de_dot(m, kb1, rho, Etb);
+    for (int e = 0; e < n * n; e++) Y[e] = rb[e] + Sb[e];
+}
+
+/* Vector-Jacobian product of one molecule step (rho, Et) -> (rho', mudot),
+ * mudot = (<mu>(rho') - <mu>(rho))/dt: given the adjoints X of rho' and mdb of mudot,
+ * returns those of rho (rhob) and Et (Etb).  Exact two-level step: rho' = U rho U^+,
+ * U = exp(-i dt (H0 - Et . mu)).  RK4 (kind 1): nsub classic RK4 substeps of the GKSL
+ * equation, reversed substep by substep (rk4_vjp). */
 static void mol_vjp_core(const omol *m, const double *Et, const cplx *rho, const cplx *X, const double *mdb,
                          double dt, cplx *rhob, double *Etb) {
     const int n = m->n;
@@ -1013,6 +1102,31 @@ static void mol_vjp_core(const omol *m, const double *Et, const cplx *rho, const
             rhob[i * n + j] = -g;
         }
     effective_h(m, Et, H);
+    if (m->kind != 0) {
+        /* forward substeps from rho (their starts kept), then the reverse */
+        const int ns = m->nsub;
+        const double h = dt / ns;
+        cplx *st = malloc((size_t)ns * MAXLEV * MAXLEV * sizeof(cplx));
+        cplx cur[MAXLEV * MAXLEV], k1[MAXLEV * MAXLEV], k2[MAXLEV * MAXLEV], k3[MAXLEV * MAXLEV];
+        cplx k4[MAXLEV * MAXLEV], tmp[MAXLEV * MAXLEV];
+        memcpy(cur, rho, (size_t)n * n * sizeof(cplx));
+        for (int q = 0; q < ns; q++) {
+            memcpy(st + (long)q * MAXLEV * MAXLEV, cur, (size_t)n * n * sizeof(cplx));
+            lindblad_rhs(m, H, cur, k1);
+            for (int e = 0; e < n * n; e++) tmp[e] = cur[e] + 0.5 * h * k1[e];
+            lindblad_rhs(m, H, tmp, k2);
+            for (int e = 0; e < n * n; e++) tmp[e] = cur[e] + 0.5 * h * k2[e];
+            lindblad_rhs(m, H, tmp, k3);
+            for (int e = 0; e < n * n; e++) tmp[e] = cur[e] + h * k3[e];
+            lindblad_rhs(m, H, tmp, k4);
+            for (int e = 0; e < n * n; e++) cur[e] += h / 6.0 * (k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + k4[e]);
+        }
+        for (int a = 0; a < 3; a++) Etb[a] = 0.0;
+        for (int q = ns - 1; q >= 0; q--) rk4_vjp(m, H, st + (long)q * MAXLEV * MAXLEV, h, Xt, Etb);
+        for (int e = 0; e < n * n; e++) rhob[e] += Xt[e];
+        free(st);
+        return;
+    }
     for (int e = 0; e < n * n; e++) A[e] = -I * dt * H[e];
     expm(n, A, U);
     dagger(n, U, Ud);
@@ -1091,11 +1205,9 @@ static int adj_molecule(osim *s, int q, const double *En, const cplx *rho_n, con
  * steps of this run only (the plane's sums restart).  grad_eps (N doubles) and
  * grad_gamma (nmol doubles) receive d(objective)/d eps per cell and d/d gamma per
  * molecule.  The forward fields of every step are kept (memory 3 N (nsteps + 1)
- * doubles).  Returns -2 if a molecule is not an exact two-level one. */
+ * doubles).  Molecules of both kinds (exact two-level, RK4 GKSL). */
 int orc_adjoint_run(osim *s, long nsteps, int p, int f, double *grad_eps, double *grad_gamma, double *obj) {
     if (p < 0 || p >= s->nplane || f < 0 || f >= s->plane[p].nfreq || nsteps < 1) return -1;
-    for (int q = 0; q < s->nmol; q++)
-        if (s->mol[q].kind != 0) return -2;
     const long N = nn(s);
     /* the reverse sweep transposes one Drude pole per cell (slot 0) only */
     for (long c = 0; c < N; c++) {

@@ -477,6 +477,9 @@ template <typename T>
 struct AdjMolArgs {
     int nmol;
     T dt;
+    const int *kind;          // 0: exact two-level; 1: RK4 GKSL
+    const int *nlev, *nsub;
+    const T *decay, *dephase;
     const int *cmask;
     const long long *off;
     const T *gamma;
@@ -523,7 +526,7 @@ __device__ __forceinline__ void dag2(const cx<T> *A, cx<T> *B) {
 template <typename T>
 __global__ void adj_mol_kernel(const AdjMolArgs<T> a) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= a.nmol) return;
+    if (m >= a.nmol || a.kind[m] != 0) return;  // RK4 molecules: adj_rk4_kernel
     const int cmk = a.cmask[m];
     const long long o = a.off[m];
     const T gam = a.gamma[m], dt = a.dt;
@@ -640,6 +643,286 @@ __global__ void adj_mol_kernel(const AdjMolArgs<T> a) {
     a.ggam[m] += gg;
 }
 
+// ------------------------------------------------------------------ RK4 GKSL molecules
+// Reverse of one molecule step of nsub classic RK4 substeps of the GKSL equation under
+// the held H = H0 - Et . mu (one warp per molecule; lane owns elements lane and lane +
+// 32 of the row-major n x n matrices, which live in shared memory).  With Y the adjoint
+// of a substep's result and rho_s its start, the stages S2 = rho_s + h/2 k1, S3 =
+// rho_s + h/2 k2, S4 = rho_s + h k3 (k = L(S)) are recomputed, then walked back:
+//   kb4 = h/6 Y, kb3 = h/3 Y, kb2 = h/3 Y, kb1 = h/6 Y, rhob = Y,
+//   Sb = L^+(kb4): rhob += Sb, kb3 += h Sb;   Sb = L^+(kb3): rhob += Sb, kb2 += h/2 Sb;
+//   Sb = L^+(kb2): rhob += Sb, kb1 += h/2 Sb; rhob += L^+(kb1),
+// and Etb_c += Re<kb, dL/dEt_c (S)> at each stage, dL/dEt_c (S) = i [mu_c, S].  Under the
+// inner product Re Tr(X^+ Y), L^+(X) = i [H, X] + D^+(X): the ladder decay moves
+// population down in D and up in D^+ (element (j, j) gains decay X_{j-1,j-1}); the
+// dephasing part is self-adjoint.  rho_s is rebuilt from rho^n by s forward substeps.
+constexpr int ADJ_RK4_WARPS = 4;
+
+template <typename T>
+struct AdjRk4Shared {
+    cx<T> H[ADJ_RK4_WARPS][64];
+    cx<T> Mu[ADJ_RK4_WARPS][3][64];
+    cx<T> S[ADJ_RK4_WARPS][4][64];  // rho_s, S2, S3, S4
+    cx<T> K[ADJ_RK4_WARPS][64];     // argument of the next L or L^+
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_adj(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// L(S)_jl (the forward GKSL right-hand side of the molecule kernel)
+template <typename T>
+__device__ __forceinline__ cx<T> gksl(int n, int j, int l, const cx<T> *S, const cx<T> *H, T decay, T deph) {
+    cx<T> acc = {T(0), T(0)};
+    for (int p = 0; p < n; p++) {
+        const cx<T> x = acmul(H[j * n + p], S[p * n + l]), y = acmul(S[j * n + p], H[p * n + l]);
+        acc.re += x.re - y.re;
+        acc.im += x.im - y.im;
+    }
+    cx<T> out = {acc.im, -acc.re};  // -i acc
+    const cx<T> r = S[j * n + l];
+    const T f = T(0.5) * decay * (T(j >= 1) + T(l >= 1));
+    out.re -= f * r.re;
+    out.im -= f * r.im;
+    if (j == l && j + 1 < n) out.re += decay * S[(j + 1) * n + (j + 1)].re;
+    if (j != l) {
+        out.re -= deph * r.re;
+        out.im -= deph * r.im;
+    }
+    return out;
+}
+
+// L^+(X)_jl
+template <typename T>
+__device__ __forceinline__ cx<T> gksl_adj(int n, int j, int l, const cx<T> *X, const cx<T> *H, T decay, T deph) {
+    cx<T> acc = {T(0), T(0)};
+    for (int p = 0; p < n; p++) {
+        const cx<T> x = acmul(H[j * n + p], X[p * n + l]), y = acmul(X[j * n + p], H[p * n + l]);
+        acc.re += x.re - y.re;
+        acc.im += x.im - y.im;
+    }
+    cx<T> out = {-acc.im, acc.re};  // +i acc
+    const cx<T> r = X[j * n + l];
+    const T f = T(0.5) * decay * (T(j >= 1) + T(l >= 1));
+    out.re -= f * r.re;
+    out.im -= f * r.im;
+    if (j == l && j >= 1) out.re += decay * X[(j - 1) * n + (j - 1)].re;
+    if (j != l) {
+        out.re -= deph * r.re;
+        out.im -= deph * r.im;
+    }
+    return out;
+}
+
+// Re( conj(Y_jl) (i [mu, S])_jl )
+template <typename T>
+__device__ __forceinline__ T dl_dot(int n, int j, int l, cx<T> y, const cx<T> *Mu, const cx<T> *S) {
+    cx<T> acc = {T(0), T(0)};
+    for (int p = 0; p < n; p++) {
+        const cx<T> x = acmul(Mu[j * n + p], S[p * n + l]), z = acmul(S[j * n + p], Mu[p * n + l]);
+        acc.re += x.re - z.re;
+        acc.im += x.im - z.im;
+    }
+    const cx<T> d = {-acc.im, acc.re};  // i acc
+    return y.re * d.re + y.im * d.im;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ADJ_RK4_WARPS * 32) adj_rk4_kernel(const AdjMolArgs<T> a) {
+    __shared__ AdjRk4Shared<T> sh;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int m = blockIdx.x * ADJ_RK4_WARPS + wl;
+    if (m >= a.nmol || a.kind[m] == 0) return;  // whole warp
+    const int n = a.nlev[m], nn = n * n, ns = a.nsub[m];
+    const int cmk = a.cmask[m];
+    const long long o = a.off[m];
+    const T gam = a.gamma[m], dt = a.dt, h = dt / T(ns), decay = a.decay[m], deph = a.dephase[m];
+    cx<T> *H = sh.H[wl], *K = sh.K[wl];
+    cx<T> *Rs = sh.S[wl][0], *S2 = sh.S[wl][1], *S3 = sh.S[wl][2], *S4 = sh.S[wl][3];
+    // G_c = sum kappa U^{n+1} (the molecule's gather partials, lane-strided, fixed tree)
+    T G[3] = {T(0), T(0), T(0)};
+    for (int t = a.moff[m] + lane; t < a.moff[m + 1]; t += 32) {
+        const T *pp = a.part + 3ll * a.mlist[t];
+        G[0] += pp[0];
+        G[1] += pp[1];
+        G[2] += pp[2];
+    }
+    T Et[3], md[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        G[c] = ((cmk >> c) & 1) ? warp_sum_adj(G[c]) : T(0);
+        Et[c] = a.Et_n[3 * m + c];
+        md[c] = a.md_n[3 * m + c];
+    }
+    int jj[2], ll[2];
+    bool own[2];
+    cx<T> Y[2], r0[2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int e = lane + 32 * q;
+        own[q] = e < nn;
+        jj[q] = own[q] ? e / n : 0;
+        ll[q] = own[q] ? e - jj[q] * n : 0;
+        if (own[q]) {
+            cx<T> hv = a.H0[o + e];
+            cx<T> y = a.rhob[o + e];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const cx<T> mv = ((cmk >> c) & 1) ? a.mu[c * a.pool + o + e] : cx<T>{T(0), T(0)};
+                sh.Mu[wl][c][e] = mv;
+                hv.re -= Et[c] * mv.re;
+                hv.im -= Et[c] * mv.im;
+                // adjoint of rho' gains the gradient of mudot: (-gamma G_c) mu_c
+                y.re += -gam * G[c] * mv.re;
+                y.im += -gam * G[c] * mv.im;
+            }
+            H[e] = hv;
+            Y[q] = y;
+            r0[q] = a.rho_n[o + e];
+        }
+    }
+    __syncwarp();
+    double Etb[3] = {0.0, 0.0, 0.0};
+    T eb[3] = {T(0), T(0), T(0)};
+    for (int sidx = ns - 1; sidx >= 0; sidx--) {
+        // rho_s: sidx forward substeps from rho^n
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (own[q]) Rs[lane + 32 * q] = r0[q];
+        __syncwarp();
+        for (int f = 0; f <= sidx; f++) {
+            // stages of substep f from Rs (kept in S2, S3, S4); for f < sidx also its result
+            cx<T> base[2], acc[2] = {{T(0), T(0)}, {T(0), T(0)}}, kk[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++) base[q] = own[q] ? Rs[lane + 32 * q] : cx<T>{T(0), T(0)};
+            const cx<T> *src = Rs;
+            cx<T> *dsts[3] = {S2, S3, S4};
+#pragma unroll
+            for (int st = 0; st < 4; st++) {
+                const T wgt = (st == 0 || st == 3) ? T(1) : T(2);
+#pragma unroll
+                for (int q = 0; q < 2; q++)
+                    if (own[q]) {
+                        kk[q] = gksl(n, jj[q], ll[q], src, H, decay, deph);
+                        acc[q].re += wgt * kk[q].re;
+                        acc[q].im += wgt * kk[q].im;
+                    }
+                if (st < 3) {
+                    const T cn = st < 2 ? T(0.5) : T(1);
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        if (own[q]) dsts[st][lane + 32 * q] = {base[q].re + cn * h * kk[q].re, base[q].im + cn * h * kk[q].im};
+                    __syncwarp();
+                    src = dsts[st];
+                }
+            }
+            if (f < sidx) {
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < 2; q++)
+                    if (own[q]) Rs[lane + 32 * q] = {base[q].re + h / T(6) * acc[q].re, base[q].im + h / T(6) * acc[q].im};
+                __syncwarp();
+            }
+        }
+        // walk the stages of substep sidx back
+        cx<T> rb[2], kb[2];
+        auto put_k = [&](const cx<T> (&v)[2]) {
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+                if (own[q]) K[lane + 32 * q] = v[q];
+            __syncwarp();
+        };
+        auto dots = [&](const cx<T> (&v)[2], const cx<T> *Sst) {
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                if ((cmk >> c) & 1)
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        if (own[q]) eb[c] += dl_dot(n, jj[q], ll[q], v[q], sh.Mu[wl][c], Sst);
+        };
+        cx<T> k3b[2], k2b[2], k1b[2], sb[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            rb[q] = Y[q];
+            kb[q] = {h / T(6) * Y[q].re, h / T(6) * Y[q].im};  // kb4
+            k3b[q] = {h / T(3) * Y[q].re, h / T(3) * Y[q].im};
+            k2b[q] = k3b[q];
+            k1b[q] = kb[q];
+        }
+        // k4 = L(S4), S4 = rho_s + h k3
+        put_k(kb);
+        dots(kb, S4);
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (own[q]) {
+                sb[q] = gksl_adj(n, jj[q], ll[q], K, H, decay, deph);
+                rb[q].re += sb[q].re; rb[q].im += sb[q].im;
+                k3b[q].re += h * sb[q].re; k3b[q].im += h * sb[q].im;
+            }
+        // k3 = L(S3), S3 = rho_s + h/2 k2
+        put_k(k3b);
+        dots(k3b, S3);
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (own[q]) {
+                sb[q] = gksl_adj(n, jj[q], ll[q], K, H, decay, deph);
+                rb[q].re += sb[q].re; rb[q].im += sb[q].im;
+                k2b[q].re += T(0.5) * h * sb[q].re; k2b[q].im += T(0.5) * h * sb[q].im;
+            }
+        // k2 = L(S2), S2 = rho_s + h/2 k1
+        put_k(k2b);
+        dots(k2b, S2);
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (own[q]) {
+                sb[q] = gksl_adj(n, jj[q], ll[q], K, H, decay, deph);
+                rb[q].re += sb[q].re; rb[q].im += sb[q].im;
+                k1b[q].re += T(0.5) * h * sb[q].re; k1b[q].im += T(0.5) * h * sb[q].im;
+            }
+        // k1 = L(rho_s)
+        put_k(k1b);
+        dots(k1b, Rs);
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (own[q]) {
+                sb[q] = gksl_adj(n, jj[q], ll[q], K, H, decay, deph);
+                Y[q] = {rb[q].re + sb[q].re, rb[q].im + sb[q].im};
+            }
+        __syncwarp();
+    }
+    // adjoint of rho^n: the reversed steps, minus the gradient of <mu>(rho^n) in mudot
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+        if (own[q]) {
+            const int e = lane + 32 * q;
+            cx<T> r = Y[q];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const cx<T> mv = sh.Mu[wl][c][e];
+                r.re -= -gam * G[c] * mv.re;
+                r.im -= -gam * G[c] * mv.im;
+            }
+            a.rhob[o + e] = r;
+        }
+#pragma unroll
+    for (int c = 0; c < 3; c++) Etb[c] = (double)warp_sum_adj(eb[c]);
+    if (lane == 0) {
+        double gg = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            gg += (double)md[c] * (double)(-dt * G[c]);
+            gg += Etb[c] * (double)Et[c] / (double)gam;
+            a.cadj[3 * m + c] = (T)(-(double)gam * Etb[c] / (double)dt);
+        }
+        a.ggam[m] += gg;
+    }
+}
+
 // Copy what the reverse sweep needs from one forward step: the design-box E (3 x
 // nbox), rho (pool) and, if rec_mol, the step's field and mudot (3 per molecule).
 template <typename T>
@@ -711,6 +994,8 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
     const Plane &pl = g->planes[pid];
     const long long ncell = (long long)pl.nb * pl.nc;
     const int M = g->nmol;
+    bool any_rk4 = false;  // RK4 GKSL molecules take their own reverse kernel
+    for (int m = 0; m < M; m++) any_rk4 = any_rk4 || g->kind[m] != 0;
     const long long nbox = g->dcb ? (long long)g->dbox[3] * g->dbox[4] * g->dbox[5] : 0;
     // the objective counts the steps of this run only
     CK(cudaGetLastError());
@@ -719,6 +1004,18 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
         if (st != ML_OK) return st;
     }
     CK(cudaMemsetAsync(pl.d_acc, 0, 4 * (size_t)pl.nfreq * ncell * sizeof(double2), s));
+    if (!grad_eps && !grad_gamma) {
+        // no gradient wanted: the forward steps and the objective only
+        ml_status st = step_impl<T>(g, N, s);
+        if (st == ML_OK) st = fold_planes<T>(g, s);
+        if (st != ML_OK) return st;
+        CK(launch_flux_reduce(pl.d_acc, (int)ncell, pl.nfreq, g->d_fpart, g->d_scalar, s));
+        double objv = 0.0;
+        CK(cudaMemcpyAsync(&objv, g->d_scalar + f, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (obj) *obj = objv;
+        return ML_OK;
+    }
     const long long n0 = g->step;
     // ---- forward sweep with a full-state checkpoint at the start of every segment
     size_t sbytes = 0;
@@ -910,7 +1207,13 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                 ma.pool = g->pool; ma.moff = g->d_moff; ma.mlist = g->d_mlist; ma.part = (const T *)g->d_part;
                 ma.rho_n = recR + t * slotR; ma.Et_n = recEt + (t + 1) * slotM; ma.md_n = recMd + (t + 1) * slotM;
                 ma.rhob = rhob; ma.cadj = cadj; ma.ggam = ggam;
+                ma.kind = g->d_kind; ma.nlev = g->d_nlev; ma.nsub = g->d_nsub;
+                ma.decay = (const T *)g->d_decay; ma.dephase = (const T *)g->d_deph;
                 adj_mol_kernel<T><<<(M + 127) / 128, 128, 0, cs>>>(ma);
+                if (any_rk4) {
+                    adj_rk4_kernel<T><<<(M + ADJ_RK4_WARPS - 1) / ADJ_RK4_WARPS, ADJ_RK4_WARPS * 32, 0, cs>>>(ma);
+                    g->launches++;
+                }
                 CK(cudaGetLastError());
                 g->launches++;
                 CurArgs<T> ca;
@@ -977,11 +1280,8 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
     if (g->PD || g->npole > 1)
         return fail(ML_ERR_INVALID_ARG, "the adjoint transposes one Drude pole per material only (no Lorentz "
                                         "omega0 > 0, no extra poles)");
-    for (int m = 0; m < g->nmol; m++) {
-        if (g->kind[m] != 0)
-            return fail(ML_ERR_INVALID_ARG, "the adjoint takes exact two-level molecules (kind 0) only");
+    for (int m = 0; m < g->nmol; m++)
         if (g->gamma[m] == 0.0) return fail(ML_ERR_INVALID_ARG, "the adjoint needs gamma != 0 for every molecule");
-    }
     const int K = (int)std::min<int64_t>(ckpt_every, nsteps);
     cudaStream_t s = (cudaStream_t)stream;
     g->pop_off = true;  // the sweeps write no population sink

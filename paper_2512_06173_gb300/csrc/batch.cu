@@ -113,7 +113,10 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
             fill_mol_args<T>(g, 1, ma[2 * i + 1]);
             ma[2 * i].pop_sink = ma[2 * i + 1].pop_sink = nullptr;  // batches write no sink
             for (int q = 0; q < g->jnb; q++) b->h_gwork.push_back(make_int2(i, q));
-            for (int m0 = 0; m0 < g->nmol; m0 += 4) b->h_mwork.push_back(make_int2(i, m0));
+            if (g->nitems > 0)  // packed molecule items, four warps per block
+                for (int it = 0; it < g->nitems; it += 4) b->h_mwork.push_back(make_int2(i, it));
+            else
+                for (int m0 = 0; m0 < g->nmol; m0 += 4) b->h_mwork.push_back(make_int2(i, m0));
         }
         for (auto &p : g->planes) {
             FoldDesc<T> d{};

@@ -742,12 +742,9 @@ __device__ __forceinline__ void packed_body(const MolArgs<T> &a, const int4 item
     }
 }
 
+// Work item `it` of the packed form (one warp), dispatched on its kind and level count.
 template <typename T>
-__global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1)
-    molecule_packed_kernel(const MolArgs<T> a) {
-    __shared__ PackShared<T> sh;
-    const int wl = threadIdx.x >> 5;
-    const int it = (int)blockIdx.x * MOL_WARPS + wl;
+__device__ __forceinline__ void packed_item(const MolArgs<T> &a, const int it, PackShared<T> &sh, const int wl) {
     if (it >= a.nitems) {
         // no item: still take part in the launch chain
         asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -755,12 +752,11 @@ __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCK
         return;
     }
     const int4 item = a.items[it];
-    const int n = item.z;
     if ((item.w & 15) == 0) {
         packed_body<T, 2, true>(a, item, sh, wl);
         return;
     }
-    switch (n) {
+    switch (item.z) {
         case 2: packed_body<T, 2, false>(a, item, sh, wl); break;
         case 3: packed_body<T, 3, false>(a, item, sh, wl); break;
         case 4: packed_body<T, 4, false>(a, item, sh, wl); break;
@@ -769,6 +765,14 @@ __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCK
         case 7: packed_body<T, 7, false>(a, item, sh, wl); break;
         default: packed_body<T, 8, false>(a, item, sh, wl); break;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1)
+    molecule_packed_kernel(const MolArgs<T> a) {
+    __shared__ PackShared<T> sh;
+    const int wl = threadIdx.x >> 5;
+    packed_item(a, (int)blockIdx.x * MOL_WARPS + wl, sh, wl);
 }
 
 template <typename T>
@@ -955,11 +959,20 @@ __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCK
     molecule_body<T, SRC_UNIFORM, N2>(a, (int)blockIdx.x * MOL_WARPS);
 }
 
-// Batched form: one block per (instance, first molecule) work item.
+// Batched form: one block per (instance, first molecule) work item, or, for an instance
+// whose molecules take the packed form when it is stepped alone, per (instance, first
+// packed item): the same arithmetic as that instance's own step.
 template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32) molecule_batch_kernel(const MolBatch<T> b) {
     const int2 wk = b.work[blockIdx.x];
-    molecule_body<T, SRC_WINDOW, N2>(b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)], wk.y);
+    const MolArgs<T> &a = b.args[2 * wk.x + ((b.lev0[wk.x] + b.s) & 1)];
+    if (a.nitems > 0) {
+        __shared__ PackShared<T> sh;
+        const int wl = threadIdx.x >> 5;
+        packed_item(a, wk.y + wl, sh, wl);
+        return;
+    }
+    molecule_body<T, SRC_WINDOW, N2>(a, wk.y);
 }
 
 template <typename T>
@@ -1018,9 +1031,12 @@ __global__ void weights_kernel(int nmol, const double *pos, const double *sigma,
     const int s = (int)floor(p) - R;
     double v[32];
     double sum = 0.0;
+    // exponent relative to the nearest sample (the largest weight is 1): the normalisation
+    // removes the common factor, and a narrow kernel cannot underflow to 0/0
+    const double fc = p - 0.5 * st, dn = fc - floor(fc + 0.5);
     for (int q = 0; q < W; q++) {
         double x = (double)(s + q) + 0.5 * st - p;
-        v[q] = exp(-x * x / (2.0 * sg * sg));
+        v[q] = exp(-(x * x - dn * dn) / (2.0 * sg * sg));
         sum += v[q];
     }
     double f[WMAX];

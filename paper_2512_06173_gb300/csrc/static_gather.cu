@@ -37,17 +37,34 @@ struct SgArgs {
     float *out;
 };
 
-// normalised Gaussian weight of index t in the window starting at s along an axis,
-// sample position (s + t) + stag/2, molecule centre p
-__device__ __forceinline__ double sg_w(int t, int W, int s, int stag, double p, double sg) {
-    double sum = 0.0, v = 0.0;
-    for (int q = 0; q < W; q++) {
-        const double d = (double)(s + q) + 0.5 * stag - p;
-        const double g = exp(-d * d / (2.0 * sg * sg));
-        sum += g;
-        if (q == t) v = g;
+// The six normalised 1D weight vectors of molecule m ([axis][stagger][t], zero past the
+// window), computed by one warp into `w`: sample t of axis ax at (s + t) + stag/2, centre
+// p.  The exponent is taken relative to the nearest sample, so the largest weight is
+// exactly 1 and a narrow kernel cannot underflow to 0/0 (the normalisation removes the
+// common factor).  Three exps per lane.
+__device__ __forceinline__ void sg_weights(const double (&p)[3], const int (&s)[3], int W, double sg, float (&w)[6][16]) {
+    const int lane = threadIdx.x;
+    const double inv = 1.0 / (2.0 * sg * sg);
+    double e[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int v = lane + 32 * k;  // vector v / 16 = 2 ax + stag, entry t = v % 16
+        const int ax = (v >> 4) >> 1, stag = (v >> 4) & 1, t = v & 15;
+        // nearest sample of this vector: distance of the centre to the sample grid
+        const double f = p[ax] - 0.5 * stag;
+        const double dn = f - floor(f + 0.5);
+        const double d = (double)(s[ax] + t) + 0.5 * stag - p[ax];
+        e[k] = t < W ? exp(-(d * d - dn * dn) * inv) : 0.0;
     }
-    return v / sum;
+    // sums of each 16-entry vector: lanes 0-15 and 16-31 hold one vector per k
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        double sum = e[k];
+        for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const int v = lane + 32 * k;
+        w[v >> 4][v & 15] = (float)(e[k] / sum);
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ int sg_wrap(int c, int n, int per, bool &ok) {
@@ -66,6 +83,7 @@ __device__ __forceinline__ bool sg_valid(const SgArgs &a, int m) {
 
 // grid: (molecules, SG_PLANES), 32 threads.  Lane = (dx in 0..15, row parity).
 __global__ void sg_partial_kernel(const SgArgs a) {
+    __shared__ float w[6][16];
     const int m = blockIdx.x, dz = blockIdx.y, lane = threadIdx.x;
     if (m >= a.nmol) return;
     float part[3] = {0.f, 0.f, 0.f};
@@ -78,25 +96,25 @@ __global__ void sg_partial_kernel(const SgArgs a) {
             p[ax] = a.pos[3 * m + ax];
             s[ax] = (int)floor(p[ax]) - R;
         }
+        sg_weights(p, s, W, sg, w);
         const int dx = lane & 15, ly = lane >> 4;
         bool okz = dz < W;
         const int z = sg_wrap(s[2] + dz, a.nz, a.pz, okz);
         bool okx = dx < W;
         const int x = sg_wrap(s[0] + dx, a.nx, a.px, okx);
         if (okz && okx) {
-            // component c is sampled half a cell along c (Yee staggering)
-            const double wx[2] = {sg_w(dx, W, s[0], 0, p[0], sg), sg_w(dx, W, s[0], 1, p[0], sg)};
-            const double wz[2] = {sg_w(dz, W, s[2], 0, p[2], sg), sg_w(dz, W, s[2], 1, p[2], sg)};
+            // component c is sampled half a cell along c (Yee staggering): w[2 ax + stag]
+            const float wx0 = w[0][dx], wx1 = w[1][dx], wz0 = w[4][dz], wz1 = w[5][dz];
             const long long N = (long long)a.nx * a.ny * a.nz;
             for (int dy = ly; dy < W; dy += 2) {
                 bool oky = true;
                 const int y = sg_wrap(s[1] + dy, a.ny, a.py, oky);
                 if (!oky) continue;
-                const double wy0 = sg_w(dy, W, s[1], 0, p[1], sg), wy1 = sg_w(dy, W, s[1], 1, p[1], sg);
+                const float wy0 = w[2][dy], wy1 = w[3][dy];
                 const long long f = ((long long)z * a.ny + y) * a.nx + x;
-                part[0] += a.E[f] * (float)(wx[1] * wy0 * wz[0]);
-                part[1] += a.E[N + f] * (float)(wx[0] * wy1 * wz[0]);
-                part[2] += a.E[2 * N + f] * (float)(wx[0] * wy0 * wz[1]);
+                part[0] += a.E[f] * (wx1 * wy0 * wz0);
+                part[1] += a.E[N + f] * (wx0 * wy1 * wz0);
+                part[2] += a.E[2 * N + f] * (wx0 * wy0 * wz1);
             }
         }
     }
@@ -140,6 +158,13 @@ ml_status ml_gather_static(const float *E, int nx, int ny, int nz, const int *pe
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 256) return sg_fail(ML_ERR_CUDA, "cudaGetDevice failed");
+    if (stream) {
+        // the scratch address is the current device's: the stream must belong to it
+        int sdev = -1;
+        e = cudaStreamGetDevice((cudaStream_t)stream, &sdev);
+        if (e != cudaSuccess || sdev != dev)
+            return sg_fail(ML_ERR_INVALID_ARG, "the stream does not belong to the current device");
+    }
     float *scratch = nullptr;
     {
         // set-up on the first call for this device (the device is current here)

@@ -108,16 +108,19 @@ constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before givin
 
 // Body of the field pass for one block.  MODE 0 is the interior form: the caller
 // guarantees the tile and its halo touch no CPML layer, wall, periodic image or
-// material/source cell, so none of those paths is compiled in.  MODE 1 adds the
-// CPML layers, the index-0 walls and the source sheets; MODE 3 is the interior form plus
-// the per-cell coefficient dt/eps of a material index (from a shared-memory table) and
-// the source sheets, for tiles clear of the layers and walls; MODE 2 has every path
-// (poles, design box, periodic images, and a material map next to a layer or wall).
+// material/source cell, so none of those paths is compiled in.  MODE 1 adds the CPML
+// layers, the index-0 walls, the source sheets and the per-cell coefficient dt/eps of a
+// material index (from a shared-memory table; measured faster than the same body
+// without the table even on tiles that have no material); MODE 3 is the interior form
+// with the source sheets and the material table, for tiles clear of the layers and
+// walls; MODE 2 has every path (dispersive poles, design box, periodic images).
 // Returns false when a plane wait gave up (the block then reported ML_ERR_TIMEOUT and
 // drained its copies); uniform over the block.
 template <typename T, int MODE>
 __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
-    constexpr bool GEN = MODE == 1 || MODE == 2, FULL = MODE == 2, MATL = MODE == 3;
+    constexpr bool GEN = MODE == 1 || MODE == 2, FULL = MODE == 2;
+    constexpr bool MATF = MODE == 1 || MODE == 3;  // sources and materials from the tables, no pole work
+    constexpr bool MATT = MATF;                    // material table
     constexpr int S = yee_stages<T>();
     constexpr int BP = box_pad<T>();
     constexpr int SW = 6 * BP;  // elements per stage
@@ -130,7 +133,13 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     __shared__ double s_red[NTHREADS / 32];
     __shared__ T sCx[6][BOXW];  // CPML coefficients at x = x0-4+col (bE cE kE bH cH kH)
     __shared__ T sCy[6][BOXH];  // at y = y0-1+row
-    __shared__ T s_cb[MATL ? ML_MAX_MATERIALS : 1];  // dt / eps_inf per material (MODE 3)
+    __shared__ T s_cb[MATT ? ML_MAX_MATERIALS : 1];  // dt / eps_inf per material (MODES 1, 3)
+    // the grid's sources and flux planes (read per cell from here, not from the kernel
+    // parameters: a dynamically indexed parameter array would be copied to local memory)
+    __shared__ int s_sax[MAXSRC], s_sidx[MAXSRC], s_scmp[MAXSRC];
+    __shared__ int s_pax[MAXPLANES], s_pidx[MAXPLANES], s_pnb[MAXPLANES], s_pnc[MAXPLANES];
+    __shared__ T *s_pbuf[MAXPLANES];
+    __shared__ T s_scol[RY][3][MATF ? NTHREADS : 1];  // per thread and row: x- and y-normal sources
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
@@ -156,14 +165,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     // whose own cells need it, when the grid has the per-tile flags
     const bool general = FULL && (a.tflags ? (a.tflags[tile] & 7) != 0
                                           : (a.mat != nullptr || a.dcb != nullptr || a.JD != nullptr || a.nsrc > 0));
-    // MODES 1 and 3: does a source sheet cross the tile (block-uniform)?
-    bool has_src = false;
-    if (MODE == 1 || MATL)
-        for (int q = 0; q < a.nsrc; q++) {
-            const int ax = a.src[q].axis, idx = a.src[q].index;
-            const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
-            if (idx >= lo && idx < hi) has_src = true;
-        }
+    // MODES 1 and 3: does a source sheet cross the tile (block-uniform)?  Does the tile
+    // hold a non-background material?
+    const bool has_mat = MATT && a.mat != nullptr && (a.tflags ? (a.tflags[tile] & 2) != 0 : true);
+
     // does the tile's column meet the box of the molecular current?
     const bool has_mol = (a.Jb[0] || a.Jb[1] || a.Jb[2]) && x0 < a.jb0[0] + a.jbn[0] &&
                          x0 + TX > a.jb0[0] && y0 < a.jb0[1] + a.jbn[1] && y0 + TY > a.jb0[1] &&
@@ -177,13 +182,6 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     // afterwards, so a release also implies that this step's molecule and current
     // kernels are complete.
     pdl_trigger();
-    // does a flux plane cross the tile (block-uniform)?
-    bool has_pl = false;
-    for (int p = 0; p < a.nplanes; p++) {
-        const int ax = a.planes[p].axis, idx = a.planes[p].index;
-        const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
-        if (idx >= lo && idx < hi) has_pl = true;
-    }
     const T cb0 = a.mat_cb[0];
     const int col = tx + 4;
     const int ob = (ty * RY + 1) * BOXW + col;       // first own cell inside a staged box
@@ -204,8 +202,20 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const int syh = fy ? slab(hjc, a.ny, a.pml[2], a.pml[3]) : -1;
     const int oh = hys * BOXW + hxs + 3;
 
-    if (MODE > 0 && tid < a.nsrc) s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
-    if (MATL && tid < ML_MAX_MATERIALS) s_cb[tid] = a.mat_cb[tid];
+    if (MODE > 0 && tid < a.nsrc) {
+        s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
+        s_sax[tid] = a.src[tid].axis;
+        s_sidx[tid] = a.src[tid].index;
+        s_scmp[tid] = a.src[tid].comp;
+    }
+    if (tid < a.nplanes) {
+        s_pax[tid] = a.planes[tid].axis;
+        s_pidx[tid] = a.planes[tid].index;
+        s_pnb[tid] = a.planes[tid].nb;
+        s_pnc[tid] = a.planes[tid].nc;
+        s_pbuf[tid] = a.planes[tid].buf;
+    }
+    if (MATT && tid < ML_MAX_MATERIALS) s_cb[tid] = a.mat_cb[tid];
     if (fx)
         for (int t = tid; t < 6 * BOXW; t += NTHREADS) {
             const int r = t / BOXW, cc = t % BOXW;
@@ -222,6 +232,46 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         for (int c = 0; c < 3; c++) { prefetch_tmap(&maps.E[c]); prefetch_tmap(&maps.H[c]); }
     }
     __syncthreads();
+    // does a source sheet or a flux plane cross the tile (block-uniform)?
+    auto crosses = [&](int ax, int idx) {
+        const int lo = ax == 0 ? x0 : (ax == 1 ? y0 : k0), hi = ax == 0 ? x0 + TX : (ax == 1 ? y0 + TY : k1);
+        return idx >= lo && idx < hi;
+    };
+    bool has_src = false, has_pl = false;
+    if (MATF)
+        for (int q = 0; q < a.nsrc; q++) has_src = has_src || crosses(s_sax[q], s_sidx[q]);
+    for (int p = 0; p < a.nplanes; p++) has_pl = has_pl || crosses(s_pax[p], s_pidx[p]);
+    // source sheets through an own cell's column (x- or y-normal: the same every plane,
+    // summed per component into s_scol) and the z-normal ones that cross the chunk
+    // (checked per plane); flux planes through an own column or the chunk
+    static_assert(RY <= 3 && MAXSRC <= 8 && MAXPLANES <= 8, "fmask layout");
+    unsigned fmask = 0;  // bits 0..7: z-normal sources crossing the chunk; 8 + 8 r ..: planes of row r
+    if (MATF && has_src)
+#pragma unroll
+        for (int r = 0; r < RY; r++) {
+            T sc0 = T(0), sc1 = T(0), sc2 = T(0);
+            for (int q = 0; q < a.nsrc; q++) {
+                const int ax = s_sax[q], idx = s_sidx[q], cmp = s_scmp[q];
+                if (ax == 2) {
+                    if (idx >= k0 && idx < k1) fmask |= 1u << q;
+                } else if ((ax == 0 ? i : jb + r) == idx) {
+                    const T v = s_src[q];
+                    sc0 += cmp == 0 ? v : T(0);
+                    sc1 += cmp == 1 ? v : T(0);
+                    sc2 += cmp == 2 ? v : T(0);
+                }
+            }
+            s_scol[r][0][tid] = sc0;
+            s_scol[r][1][tid] = sc1;
+            s_scol[r][2][tid] = sc2;
+        }
+    if (has_pl)
+#pragma unroll
+        for (int r = 0; r < RY; r++)
+            for (int p = 0; p < a.nplanes; p++) {
+                const int ax = s_pax[p], idx = s_pidx[p];
+                if (ax == 2 ? (idx >= k0 && idx < k1) : ((ax == 0 ? i : jb + r) == idx)) fmask |= 256u << (8 * r + p);
+            }
     // producer: one thread issues the six tiled loads of plane q into its stage
     auto issue = [&](int q) {
         const int s = (q - q0) % S;
@@ -314,8 +364,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         // of its FP32 rate); times dt/2 and summed in FP64 across the block
         T absorbed = T(0);
         // MODE 3: material index of the own cell, plane by plane (loaded before the wait)
-        const long long nxy = (long long)a.nx * a.ny;
-        const uint8_t *mp = (MATL && a.mat) ? a.mat + ((long long)k0 * a.ny + jb) * a.nx + i : nullptr;
+        // offset of the own cell's material byte (32-bit: a grid with a material map has
+        // fewer than 2^32 cells, checked when it is created)
+        const unsigned nxy = (unsigned)a.nx * (unsigned)a.ny;
+        unsigned mo = has_mat ? ((unsigned)k0 * (unsigned)a.ny + (unsigned)jb) * (unsigned)a.nx + (unsigned)i : 0u;
         int sc = 1 % S;               // stage of plane k (= k0 = q0 + 1)
         int sn = 2 % S;               // stage of plane k + 1
         uint32_t pn = S > 2 ? 0u : 1u;  // parity of the fill of stage sn that holds plane k + 1
@@ -343,7 +395,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 qh = slab_off(hic, hjc, k, sxh, syh, sz);
                 h_pml_load(phh, qh);
             }
-            const int midx_l = (MATL && mp && xin && jb < a.ny) ? (int)mp[0] : 0;
+            int midx_l[RY];
+#pragma unroll
+            for (int r = 0; r < RY; r++)
+                midx_l[r] = (MATT && has_mat && xin && jb + r < a.ny) ? (int)a.mat[mo + (unsigned)(r * a.nx)] : 0;
             wait_stage(sn, pn);
             const T *Ek = stages + sc * SW, *Ek1 = stages + sn * SW, *Hk = Ek + 3 * BP;
             const long long pb = (long long)(k + 1) * a.plane;
@@ -450,19 +505,22 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 const T eo0 = Ek[o], eo1 = Ek[BP + o], eo2 = Ek[2 * BP + o];
                 T j0 = J0[r], j1 = J1[r], j2 = J2[r];
                 T en0, en1, en2;
-                if (MODE == 1 || MATL) {
-                    if (has_src)
-                        for (int q = 0; q < a.nsrc; q++) {
-                            const int ax = a.src[q].axis;
-                            const int pos = ax == 0 ? i : (ax == 1 ? j : k);
-                            if (pos == a.src[q].index) {
-                                const int cmp = a.src[q].comp;
-                                if (cmp == 0) j0 += s_src[q];
-                                else if (cmp == 1) j1 += s_src[q];
-                                else j2 += s_src[q];
-                            }
-                        }
-                    const T cb = MATL ? s_cb[midx_l] : cb0;
+                if (MATF) {
+                    if (has_src) {
+                        j0 += s_scol[r][0][tid];
+                        j1 += s_scol[r][1][tid];
+                        j2 += s_scol[r][2][tid];
+                        if (fmask & 255u)
+                            for (int q = 0; q < a.nsrc; q++)
+                                if (((fmask >> q) & 1u) && k == s_sidx[q]) {
+                                    const int cmp = s_scmp[q];
+                                    const T v = s_src[q];
+                                    j0 += cmp == 0 ? v : T(0);
+                                    j1 += cmp == 1 ? v : T(0);
+                                    j2 += cmp == 2 ? v : T(0);
+                                }
+                    }
+                    const T cb = MATT ? s_cb[midx_l[r]] : cb0;
                     en0 = eo0 + cb * (curl0 - j0);
                     en1 = eo1 + cb * (curl1 - j1);
                     en2 = eo2 + cb * (curl2 - j2);
@@ -472,10 +530,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                     en2 = eo2 + cb0 * (curl2 - j2);
                 } else {
                     for (int q = 0; q < a.nsrc; q++) {
-                        const int ax = a.src[q].axis;
+                        const int ax = s_sax[q];
                         const int pos = ax == 0 ? i : (ax == 1 ? j : k);
-                        if (pos == a.src[q].index) {
-                            const int cmp = a.src[q].comp;
+                        if (pos == s_sidx[q]) {
+                            const int cmp = s_scmp[q];
                             if (cmp == 0) j0 += s_src[q];
                             else if (cmp == 1) j1 += s_src[q];
                             else j2 += s_src[q];
@@ -549,11 +607,12 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 }
                 // ---- DFT flux planes through this cell: E^{n+1} and the mean of H^{n+1/2}
                 // on both sides of the plane, written to the current sample slot
-                for (int p = 0; p < (has_pl ? a.nplanes : 0); p++) {
-                    const PlaneDev<T> &pl = a.planes[p];
-                    const int ax = pl.axis;
-                    if ((ax == 0 ? i : (ax == 1 ? j : k)) != pl.index) continue;
-                    const bool zero_m = pl.index == 0 && !a.per[ax];  // H(-1) is the wall ghost (0)
+                for (int p = 0; p < (((fmask >> (8 + 8 * r)) & 255u) ? a.nplanes : 0); p++) {
+                    if (!((fmask >> (8 + 8 * r + p)) & 1u)) continue;
+                    const int ax = s_pax[p], pidx = s_pidx[p];
+                    if (ax == 2 && k != pidx) continue;
+                    const int per_a = ax == 0 ? a.per[0] : (ax == 1 ? a.per[1] : a.per[2]);
+                    const bool zero_m = pidx == 0 && !per_a;  // H(-1) is the wall ghost (0)
                     T eb, ec, hb, hc, hbm, hcm;
                     int u, v;
                     if (ax == 2) {
@@ -564,11 +623,13 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                         eb = en2; ec = en0; hb = hz[r]; hc = hx[r]; hbm = sH[2][sr - 1][tx + 1]; hcm = sH[0][sr - 1][tx + 1]; u = k; v = i;
                     }
                     if (zero_m) { hbm = T(0); hcm = T(0); }
-                    const long long ncell = (long long)pl.nb * pl.nc, t = (long long)v * pl.nb + u;
-                    pl.buf[t] = eb;
-                    pl.buf[ncell + t] = ec;
-                    pl.buf[2 * ncell + t] = T(0.5) * (hb + hbm);
-                    pl.buf[3 * ncell + t] = T(0.5) * (hc + hcm);
+                    const int pnb = s_pnb[p];
+                    T *pbuf = s_pbuf[p];
+                    const long long ncell = (long long)pnb * s_pnc[p], t = (long long)v * pnb + u;
+                    pbuf[t] = eb;
+                    pbuf[ncell + t] = ec;
+                    pbuf[2 * ncell + t] = T(0.5) * (hb + hbm);
+                    pbuf[3 * ncell + t] = T(0.5) * (hc + hcm);
                 }
             }
 #pragma unroll
@@ -585,7 +646,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             }
             sc = sn;
             if (++sn == S) { sn = 0; pn ^= 1u; }
-            if (MATL && mp) mp += nxy;
+            if (MATT && has_mat) mo += nxy;
         }
         if (FULL && a.JD) {
             // fixed-order block reduction into this block's accumulator
@@ -641,7 +702,7 @@ __device__ __forceinline__ bool interior_geometry(const YeeArgs<T> &a, const int
     return true;
 }
 
-// 0: interior body; 1: CPML, walls and source sheets (no periodic image, material map,
+// 0: interior body; 1: CPML, walls, source sheets and material map (no periodic image,
 // pole or design box in the tile); 3: interior geometry with a material map or source
 // sheets; 2: every path.
 template <typename T>
@@ -650,12 +711,13 @@ __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
     if (interior_geometry(a, tile)) {
         if (fl == 0) return 0;
         if ((fl & 1) == 0) return 3;
+        return 2;
     }
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
     const bool img = (a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
                      (a.per[2] && (k0 == 0 || k1 == a.nz));
-    return (img || (fl & 3) != 0) ? 2 : 1;
+    return (img || (fl & 1) != 0) ? 2 : 1;
 }
 
 template <typename T>

@@ -1,10 +1,10 @@
 """GPU discrete adjoint (ml_adjoint_run) against the oracle's adjoint on the same
 seeded problems: objective, d/d eps over the design box and d/d gamma per
-molecule.  FP64 runs agree to round-off; FP32 runs within 1e-3 relative L2
-(gradients) and 1e-4 (objective).  Also: the result does not depend on the
-checkpoint interval (up to the round-off of the per-segment gradient sums), the
-grid ends in the state a plain run reaches, and
-unsupported inputs are refused.
+molecule, for exact two-level emitters and RK4 GKSL systems of up to 8 levels.  FP64
+runs agree to round-off; FP32 runs within 1e-3 relative L2 (gradients) and 1e-4
+(objective).  Also: the result does not depend on the checkpoint interval (up to the
+round-off of the per-segment gradient sums), the grid ends in the state a plain run
+reaches, and unsupported inputs (zero couplings, no design box) are refused.
 """
 import numpy as np
 import pytest
@@ -133,8 +133,36 @@ def test_setters_move_the_objective_as_the_gradient_says(ml):
         g.close()
 
 
+def with_multilevel(prob, seed, levels=(3, 5, 8), nsub=(1, 2, 1)):
+    """The problem with RK4 GKSL systems (ladder decay and dephasing) added next to its
+    two-level emitters."""
+    rng = np.random.default_rng(seed)
+    mol = prob.molecules
+    mats = [dict(n=int(mol.nlev[m]), pos=mol.pos[m], sigma=mol.sigma[m], gamma=mol.gamma[m],
+                 H0=mol.matrix(mol.H0, m), mu=np.stack([mol.matrix(mol.mu[a], m) for a in range(3)]),
+                 rho=mol.matrix(mol.rho0, m), decay=mol.decay[m], dephase=mol.dephase[m], kind=int(mol.kind[m]),
+                 nsub=int(mol.nsub[m])) for m in range(mol.count)]
+    zc = prob.nz // 2
+    for n, ns in zip(levels, nsub):
+        mu = np.stack([W.random_hermitian(rng, n, 0.4) for _ in range(3)])
+        c = rng.normal(size=n) + 1j * rng.normal(size=n)
+        c /= np.linalg.norm(c)
+        E = np.concatenate([[0.0], np.cumsum(0.3 * (1 + 0.05 * rng.uniform(-1, 1, n - 1)))])
+        mats.append(dict(n=n, pos=[rng.uniform(4, prob.nx - 5), rng.uniform(4, prob.ny - 5), rng.uniform(zc + 1, zc + 3)],
+                         sigma=0.8, gamma=rng.uniform(0.5, 1.5), H0=np.diag(E).astype(complex), mu=mu,
+                         rho=np.outer(c, c.conj()), decay=0.02, dephase=0.01, kind=W.KIND_RK4, nsub=ns))
+    return prob.replace(molecules=W.pack_molecules(mats))
+
+
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+def test_multilevel_molecules_against_oracle(ml, oracle_mod, precision, tol_obj, tol_grad):
+    """The reverse sweep through RK4 GKSL molecules (3, 5 and 8 levels, decay,
+    dephasing, two substeps for one of them) next to exact two-level ones."""
+    compare(ml, oracle_mod, with_multilevel(coupled(11), 11), 80, precision, tol_obj, tol_grad)
+
+
 def test_refuses_unsupported_inputs(ml):
-    mol = W.pack_molecules([W.tls([7.0, 6.0, 10.0], 0.3, 0.5, sigma=1.0, decay=0.01)])
+    mol = W.pack_molecules([W.tls([7.0, 6.0, 10.0], 0.3, 0.5, sigma=1.0, gamma=0.0, decay=0.01)])
     prob = W.Problem(14, 12, 20, 0.5, molecules=mol, planes=[W.FluxPlane(2, 15, np.array([0.3]))])
     g = ml.Grid(prob, 0)
     try:
@@ -170,6 +198,9 @@ def test_autograd_function(ml):
         gam = torch.tensor(prob.molecules.gamma, dtype=torch.float64, device="cuda", requires_grad=True)
         J = CoupledFlux.apply(eps, gam, g, state0, 150, 0, 0, 40)
         assert abs(J.item() - obj_ref) <= 1e-12 * abs(obj_ref)
+        # no input needs a gradient: the forward steps alone give the same objective
+        J0 = CoupledFlux.apply(eps.detach(), gam.detach(), g, state0, 150, 0, 0, 40)
+        assert not J0.requires_grad and abs(J0.item() - obj_ref) <= 1e-12 * abs(obj_ref)
         (2.0 * J).backward()
         np.testing.assert_allclose(eps.grad.cpu().numpy(), 2.0 * ge_ref, rtol=1e-12, atol=0)
         np.testing.assert_allclose(gam.grad.cpu().numpy(), 2.0 * gg_ref, rtol=1e-12, atol=0)

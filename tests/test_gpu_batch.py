@@ -175,3 +175,36 @@ def test_chunk_length_does_not_change_the_results(ml, precision):
             assert np.array_equal(x, y)
         assert np.array_equal(o["rho"], out[0]["rho"])
         assert abs(o["absorbed"] - out[0]["absorbed"]) <= (1e-12 if precision else 1e-5) * abs(out[0]["absorbed"])
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_batched_instances_against_oracle(ml, oracle_mod, precision, tol):
+    """Every instance of a batch, stepped together through the graph-replayed launches,
+    against the FP64 oracle stepping that instance alone: fields, density matrices,
+    flux spectra and absorbed energy (relative L2; FP64 to round-off, FP32 within 1e-4)."""
+    probs = [problems()[q] for q in (0, 2, 5)] + [W.plasmonic_instance(40, 30, np.random.default_rng(3), width=6.0)]
+    grids = [ml.Grid(p, precision) for p in probs]
+    b = ml.Batch(grids)
+    try:
+        b.step(110)  # one graph sequence of 64 steps and a remainder
+        for g, p in zip(grids, probs):
+            o = oracle_mod.OracleSim(p)
+            o.step(110)
+            fo = o.fields()
+            scale = max(np.linalg.norm(f) for f in fo)
+            for got, want in zip(g.fields(), fo):
+                assert np.linalg.norm(np.asarray(got, np.float64) - want) < tol * scale
+            M = p.molecules.count
+            if M:
+                rg = np.concatenate([g.rho(m).ravel() for m in range(M)])
+                ro = np.concatenate([o.rho(m).ravel() for m in range(M)])
+                assert np.linalg.norm(rg - ro) < tol * np.linalg.norm(ro)
+            for q in range(len(p.planes)):
+                fg, fw = g.flux(q), o.flux(q)
+                assert np.abs(fg - fw).max() <= tol * max(np.abs(fw).max(), 1e-300)
+            ab_o = o.absorbed()
+            assert abs(g.absorbed() - ab_o) <= tol * max(abs(ab_o), 1e-300)
+    finally:
+        b.close()
+        for g in grids:
+            g.close()

@@ -346,3 +346,24 @@ def test_material_and_source_bodies(ml, oracle_mod, precision, tol, case):
     M = prob.molecules.count
     ro = [o.rho(m) for m in range(M)]
     assert crel(np.concatenate([g.rho(m).ravel() for m in range(M)]), np.concatenate([r.ravel() for r in ro])) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_narrow_kernels(ml, oracle_mod, precision, tol):
+    """Kernels far narrower than a cell (sigma = 0.01 and 0.005, where every sample's
+    Gaussian underflows unless it is taken relative to the nearest sample): finite
+    regularised fields and currents equal to the oracle's."""
+    mols = W.pack_molecules([W.tls((6.5, 5.5, 7.5), 0.25, 0.5, axis=a, sigma=sg, cg=np.sqrt(0.7), ce=np.sqrt(0.3))
+                             for a, sg in ((0, 0.01), (2, 0.005), (1, 0.01))])
+    mols.pos[2] = (9.0, 6.0, 5.0)
+    prob = W.Problem(16, 13, 14, 0.5, pml=(3,) * 6, molecules=mols)
+    f = W.random_fields(prob, 4)
+    g, o = run_pair(ml, oracle_mod, prob, 5, precision, fields=f)
+    et = g.molecules(ml.ML_MOL_EFIELD)
+    et_o = np.array([o.mol_state(m)[0] for m in range(3)])
+    cm = np.array([[a == b for b in range(3)] for a in (0, 2, 1)])
+    assert np.all(np.isfinite(et)) and np.all(np.isfinite(g.molecules(ml.ML_MOL_MUDOT)))
+    assert rel(et[cm], et_o[cm]) < tol
+    for got, want in zip(g.fields(), o.fields()):
+        assert rel(got, want) < tol
+

@@ -5,8 +5,9 @@ from the adjoint code itself:
 * dot-product identity <L x, y> = <x, L^T y> for the linear field step (CPML on
   some axes, periodic and wall axes, material table, Drude cells): any dropped
   term, wrong sign or transposed index in the reversed step breaks it;
-* the vector-Jacobian product of one exact two-level step against central
-  differences of the forward molecule step (which the molecule tests pin to
+* the vector-Jacobian product of one molecule step (exact two-level, and RK4 GKSL
+  with ladder decay, dephasing and several substeps for 3 and 5 levels) against
+  central differences of the forward molecule step (which the molecule tests pin to
   closed forms);
 * the full gradient against central differences of the forward flux
   (Sec. IV spectra) for a coupled problem with CPML, a design box, a source and
@@ -81,11 +82,53 @@ def test_molecule_vjp_matches_central_differences(oracle_mod):
         assert abs(fdr - np.sum((rb.conj() * d).real)) < 1e-8
 
 
-def _coupled(seed, drude=False):
+@pytest.mark.parametrize("n,nsub", [(3, 1), (5, 2), (2, 3)])
+def test_rk4_molecule_vjp_matches_central_differences(oracle_mod, n, nsub):
+    rng = np.random.default_rng(10 + n)
+    mu = np.stack([W.random_hermitian(rng, n, 0.3) for _ in range(3)])
+    c = rng.normal(size=n) + 1j * rng.normal(size=n)
+    c /= np.linalg.norm(c)
+    rho = 0.7 * np.outer(c, c.conj()) + 0.3 * np.eye(n) / n
+    E = np.concatenate([[0.0], np.cumsum(0.2 + 0.05 * rng.uniform(size=n - 1))])
+    mol = W.pack_molecules([dict(n=n, pos=[6.3, 5.1, 6.7], sigma=1.0, gamma=0.7, H0=np.diag(E).astype(complex),
+                                 mu=mu, rho=rho, decay=0.05, dephase=0.03, kind=W.KIND_RK4, nsub=nsub)])
+    o = oracle_mod.OracleSim(W.Problem(13, 11, 12, 0.5, molecules=mol))
+    Et = rng.standard_normal(3)
+    X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    X = X + X.conj().T
+    mdb = rng.standard_normal(3)
+    rb, Etb = o.mol_vjp(0, Et, rho, X, mdb)
+
+    def F(Ev, r):
+        o.set_rho(0, r)
+        md = o.molecule_step(0, Ev)
+        return np.sum((X.conj() * o.rho(0)).real) + md @ mdb
+
+    h = 1e-6
+    fd = np.array([(F(Et + h * e, rho) - F(Et - h * e, rho)) / (2 * h) for e in np.eye(3)])
+    np.testing.assert_allclose(Etb, fd, rtol=0, atol=1e-7)
+    for _ in range(4):  # random Hermitian directions in rho
+        d = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        d = d + d.conj().T
+        fdr = (F(Et, rho + h * d) - F(Et, rho - h * d)) / (2 * h)
+        assert abs(fdr - np.sum((rb.conj() * d).real)) < 1e-7
+
+
+def _coupled(seed, drude=False, multilevel=False):
     rng = np.random.default_rng(seed)
     nx, ny, nz = 14, 12, 20
     mats = [W.tls([rng.uniform(5, 9), rng.uniform(5, 7), rng.uniform(11, 13)], 0.3, 0.8, axis=q % 3,
                   sigma=0.8, gamma=rng.uniform(0.5, 1.5), cg=np.sqrt(0.7), ce=np.sqrt(0.3)) for q in range(3)]
+    if multilevel:
+        # RK4 GKSL systems of 3 and 4 levels with decay and dephasing, one with two substeps
+        for q, n in enumerate((3, 4)):
+            mu = np.stack([W.random_hermitian(rng, n, 0.4) for _ in range(3)])
+            c = rng.normal(size=n) + 1j * rng.normal(size=n)
+            c /= np.linalg.norm(c)
+            E = np.concatenate([[0.0], np.cumsum(0.3 * (1 + 0.05 * rng.uniform(-1, 1, n - 1)))])
+            mats.append(dict(n=n, pos=[rng.uniform(5, 9), rng.uniform(5, 7), rng.uniform(11, 13)], sigma=0.8,
+                             gamma=rng.uniform(0.5, 1.5), H0=np.diag(E).astype(complex), mu=mu,
+                             rho=np.outer(c, c.conj()), decay=0.02, dephase=0.01, kind=W.KIND_RK4, nsub=1 + q))
     mol = W.pack_molecules(mats)
     deps = 1.0 + rng.uniform(0, 1.5, (4, 5, 6))
     kw = {}
@@ -99,9 +142,9 @@ def _coupled(seed, drude=False):
                      planes=[W.FluxPlane(2, 15, np.array([0.25, 0.3]))], molecules=mol, **kw)
 
 
-@pytest.mark.parametrize("drude", [False, True])
-def test_gradient_matches_central_differences(oracle_mod, drude):
-    prob = _coupled(5, drude)
+@pytest.mark.parametrize("drude,multilevel", [(False, False), (True, False), (False, True)])
+def test_gradient_matches_central_differences(oracle_mod, drude, multilevel):
+    prob = _coupled(5, drude, multilevel)
     NS = 80
 
     def J(p):
@@ -132,10 +175,3 @@ def test_gradient_matches_central_differences(oracle_mod, drude):
                                                       mol.dephase, mol.kind, mol.nsub, mol.H0, mol.mu,
                                                       mol.rho0)))) / (2 * h)
         assert abs(gg[m] - fd) <= 1e-6 * abs(fd)
-
-
-def test_adjoint_takes_two_level_exact_molecules_only(oracle_mod):
-    mol = W.pack_molecules([W.tls([6.0, 5.0, 10.0], 0.3, 0.5, decay=0.01)])
-    prob = W.Problem(12, 10, 20, 0.5, molecules=mol, planes=[W.FluxPlane(2, 15, np.array([0.3]))])
-    with pytest.raises(ValueError):
-        oracle_mod.OracleSim(prob).adjoint_run(5, 0, 0)

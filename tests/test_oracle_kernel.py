@@ -90,3 +90,27 @@ def test_window_outside_wall_rejected(oracle_mod):
     sim = oracle_mod.OracleSim(prob)
     with pytest.raises(ValueError):
         sim.step(1)
+
+
+@pytest.mark.parametrize("sigma", [0.01, 0.005])
+def test_narrow_kernel_selects_the_nearest_samples(oracle_mod, sigma):
+    """A kernel much narrower than a cell (Eq. Polarization_mol as sigma -> 0) weights only
+    the samples nearest the centre, equally when two are equally near: for a molecule at
+    a cell centre (i+1/2, j+1/2, k+1/2) the x component is sampled at x = i+1/2 exactly and
+    at the two y and the two z samples half a cell away, so E~_x is gamma times the mean
+    of four Ex values (and likewise for y, z).  exp(-d^2 / 2 sigma^2) underflows for
+    every sample here; the normalised weights must still come out finite."""
+    i, j, k = 6, 4, 5
+    mols = [tls((i + 0.5, j + 0.5, k + 0.5), 0.25, 0.1, sigma=sigma, gamma=1.3)]
+    prob = Problem(13, 11, 12, 0.5, molecules=pack_molecules(mols))
+    sim = oracle_mod.OracleSim(prob)
+    f = random_fields(prob, 31)
+    sim.set_fields(f)
+    Ex, Ey, Ez = f[0], f[1], f[2]
+    want = 1.3 * 0.25 * np.array([
+        Ex[k, j, i] + Ex[k, j + 1, i] + Ex[k + 1, j, i] + Ex[k + 1, j + 1, i],
+        Ey[k, j, i] + Ey[k, j, i + 1] + Ey[k + 1, j, i] + Ey[k + 1, j, i + 1],
+        Ez[k, j, i] + Ez[k, j, i + 1] + Ez[k, j + 1, i] + Ez[k, j + 1, i + 1]])
+    got = sim.gather(0)
+    assert np.all(np.isfinite(got))
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-15)

@@ -324,8 +324,8 @@ def measure_bragg(args, stream):
                 "ms_per_step": ms_untraced / K, "gcells_per_s_untraced": prob.cells * K / ms_untraced / 1e6,
                 "field_pass": {"ms_per_step": fp, "alg_bytes": alg, "achieved_gbs": alg / (fp / 1e3) / 1e9,
                                "frac": alg / (fp / 1e3) / 1e9 / hbm, "peak": hbm, "peak_kind": peak_kind},
-                "kernel_ms_per_step": {"molecules": kms[0] / K, "current": kms[4] / K, "field_pass": fp,
-                                       "plane_fold": kms[3] / K}}
+                "kernel_ms_per_step": {"gather": kms[5] / K, "molecules": kms[0] / K, "current": kms[4] / K,
+                                       "field_pass": fp, "plane_fold": kms[3] / K}}
     finally:
         g.close()
 
@@ -526,6 +526,16 @@ def measure_batch(args, stream):
         stream.synchronize()
         plain_ms, batch_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
         launches = b.launches - l0
+        # per-kernel split of the batched step (traced, without the graph): the time a step
+        # spends outside kernels (launch gaps, kernel tails) is what one fused persistent
+        # launch per step could at most take away
+        KT = 128
+        maxlink.ml_batch_set_timing(b.h, True)
+        maxlink.ml_batch_timing(b.h)
+        b.step(KT)
+        kms, _ = maxlink.ml_batch_timing(b.h)
+        maxlink.ml_batch_set_timing(b.h, False)
+        ksum = float(kms[0] + kms[1] + kms[3] + kms[4]) / KT
         ab_p = np.array([g.absorbed() for g in plain])
         ab_b = np.array([g.absorbed() for g in grids])
         # the batch's field passes move at least the algorithmic bytes of every instance's
@@ -540,6 +550,9 @@ def measure_batch(args, stream):
                 "dtype": "f32", "plain_ms": plain_ms, "batched_ms": batch_ms,
                 "plain_gcells": cells * K / plain_ms / 1e6, "batched_gcells": cells * K / batch_ms / 1e6,
                 "speedup": plain_ms / batch_ms, "blocks_per_sm": choice, "autotune_trial_ms": tune_ms,
+                "kernel_ms_per_step_traced": {"molecules": kms[0] / KT, "current": kms[4] / KT,
+                                              "field_pass": kms[1] / KT, "plane_fold": kms[3] / KT},
+                "step_minus_kernel_sum_ms": batch_ms / K - ksum,
                 "roofline": {"bound": "hbm", "alg_bytes_per_step": alg, "achieved_gbs_whole_step": step_gbs,
                              "peak": hbm, "peak_kind": peak_kind, "frac": step_gbs / hbm,
                              "note": "field-pass algorithmic bytes of all instances over the whole batched step"},
@@ -675,8 +688,8 @@ def measure_coupled(prob, args, stream, world, rank, local, K, W, with_clocks=Tr
                            "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                            "frac": achieved / hbm, "traffic": field_pass_traffic(prob), "alg_bytes_per_step": alg,
                            "field_pass_ms_per_step": k1_ms, "launches_per_step": kcnt[1] / KT}
-        out["kernel_ms_per_step"] = {"molecules": kms[0] / KT, "current": kms[4] / KT, "field_pass": k1_ms,
-                                     "plane_fold": kms[3] / KT}
+        out["kernel_ms_per_step"] = {"gather": kms[5] / KT, "molecules": kms[0] / KT, "current": kms[4] / KT,
+                                     "field_pass": k1_ms, "plane_fold": kms[3] / KT}
         pops = g.molecules(maxlink.ML_MOL_POP)
         flux = [g.flux(p) for p in range(len(prob.planes))]
         out["check"] = {"pop_excited_mean": float(np.mean(1.0 - pops[:, 0])), "flux_plane0_f0": float(flux[0][0])}

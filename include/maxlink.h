@@ -300,8 +300,8 @@ ml_status ml_restore(ml_grid *g, const void *host_buf, size_t bytes, void *strea
  * recomputed once (device memory ~ nsteps/ckpt_every checkpoints plus ckpt_every
  * design-box E records).  Molecules of both kinds (the exact two-level step, and the
  * RK4 GKSL step of up to ML_MAX_LEVELS levels with decay, dephasing and substeps, whose
- * stages are walked back) with gamma != 0; materials may carry Drude poles but no
- * Lorentz pole (omega0 > 0 is ML_ERR_INVALID_ARG).  Allocates its work memory for the call and frees it;
+ * stages are walked back) with gamma != 0; every dispersive pole slot, Drude and
+ * Lorentz (the polarisation's adjoint is carried beside the current's).  Allocates its work memory for the call and frees it;
  * synchronises `stream`.  With both gradient pointers NULL the call runs only the
  * forward steps and returns the objective (no checkpoints, no reverse sweep). */
 ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_id, int freq, double *objective,
@@ -420,6 +420,15 @@ ml_status ml_batch_autotune(ml_batch *b, int trial_steps, void *stream, int *blo
 
 /* Kernels (and graph launches) this batch has enqueued. */
 int64_t ml_batch_launch_count(const ml_batch *b);
+
+/* Per-kernel timing of a batch (tracing): while enabled, steps run without the graph
+ * and every launch is bracketed by CUDA events on the stream; ml_batch_timing writes the
+ * summed milliseconds and launch counts per kernel class {molecules, field pass, -, fold,
+ * molecular current, -} into ms[0..5] / counts[0..5] (either may be NULL) and clears the
+ * record.  The events separate the launches, so traced steps do not overlap kernels as
+ * untraced ones do. */
+ml_status ml_batch_set_timing(ml_batch *b, int enable);
+ml_status ml_batch_timing(ml_batch *b, double *ms, int64_t *counts);
 
 /* Free the batch's own device memory and graph (not the grids).  Synchronises. */
 ml_status ml_batch_destroy(ml_batch *b);

@@ -96,6 +96,10 @@ def _load():
     L.orc_adj_reset.argtypes = [P]
     L.orc_adj_get.argtypes = [P, dp]
     L.orc_adj_set.argtypes = [P, dp]
+    L.orc_npole.restype = C.c_int
+    L.orc_npole.argtypes = [P]
+    L.orc_get_poles.argtypes = [P, dp]
+    L.orc_set_poles.argtypes = [P, dp]
     L.orc_adj_field.argtypes = [P]
     L.orc_mol_vjp.restype = C.c_int
     L.orc_mol_vjp.argtypes = [P, C.c_int, dp, dp, dp, dp, dp, dp]
@@ -291,12 +295,28 @@ class OracleSim:
     def adj_reset(self):
         self.L.orc_adj_reset(self.h)
 
-    def adj_state(self) -> np.ndarray:
-        """Adjoint field state as (21, nz, ny, nx): Eb[3], Hb[3], psi_b[12], JD_b[3]."""
+    @property
+    def npole(self) -> int:
+        return int(self.L.orc_npole(self.h))
+
+    def poles(self) -> List[np.ndarray]:
+        """Every pole slot's state: per slot J[3] (at n-1/2) then P[3] (at n)."""
         N = int(np.prod(self.shape))
-        out = np.zeros(21 * N)
+        out = np.zeros(6 * self.npole * N)
+        self.L.orc_get_poles(self.h, out)
+        return [out[q * N:(q + 1) * N].reshape(self.shape) for q in range(6 * self.npole)]
+
+    def set_poles(self, st: List[np.ndarray]):
+        self.L.orc_set_poles(self.h, np.ascontiguousarray(np.concatenate([np.ravel(x) for x in st]), np.float64))
+
+    def adj_state(self) -> np.ndarray:
+        """Adjoint field state as (18 + 6 npole, nz, ny, nx): Eb[3], Hb[3], psi_b[12], then
+        per pole slot J_b[3], P_b[3]."""
+        N = int(np.prod(self.shape))
+        n = 18 + 6 * self.npole
+        out = np.zeros(n * N)
         self.L.orc_adj_get(self.h, out)
-        return out.reshape((21,) + self.shape)
+        return out.reshape((n,) + self.shape)
 
     def set_adj_state(self, st: np.ndarray):
         self.L.orc_adj_set(self.h, np.ascontiguousarray(st, np.float64).ravel())

@@ -736,12 +736,14 @@ void orc_set_drude(osim *s, const double *in) {
  * is undone in reverse order by adding (df/dxi)^T ybar to xbar_i; nothing is
  * reorganised, so the code below can be read against orc_step line by line.
  * Complex matrices are real vectors under <X, Y> = Re sum conj(X_ij) Y_ij.
- * Molecules: the exact two-level propagator (kind 0) only.
+ * Molecules: the exact two-level propagator and the RK4 GKSL step.  Dispersive media:
+ * every pole slot, Drude and Lorentz.
  */
 
 
 struct oadj {
-    double *Eb[3], *Hb[3], *Pb[12], *JDb[3];  /* adjoints of E, H, psi, J_D */
+    double *Eb[3], *Hb[3], *Pb[12];  /* adjoints of E, H, psi */
+    double *JDb[MAXPOLE][3], *PDb[MAXPOLE][3];  /* adjoints of each pole's current and polarisation */
     double *Jb[3];     /* adjoint of the molecular + source current of the step */
     double *Eb_in[3];  /* scratch: adjoint of E^n while a step is reversed */
     cplx *rhob;        /* nmol x MAXLEV^2: adjoint of each density matrix */
@@ -751,7 +753,8 @@ static void adj_free(osim *s) {
     struct oadj *A = s->adj;
     if (!A) return;
     for (int a = 0; a < 3; a++) {
-        free(A->Eb[a]); free(A->Hb[a]); free(A->JDb[a]); free(A->Jb[a]); free(A->Eb_in[a]);
+        free(A->Eb[a]); free(A->Hb[a]); free(A->Jb[a]); free(A->Eb_in[a]);
+        for (int q = 0; q < MAXPOLE; q++) { free(A->JDb[q][a]); free(A->PDb[q][a]); }
     }
     for (int p = 0; p < 12; p++) free(A->Pb[p]);
     free(A->rhob);
@@ -766,22 +769,30 @@ void orc_adj_reset(osim *s) {
     struct oadj *A = calloc(1, sizeof(*A));
     for (int a = 0; a < 3; a++) {
         A->Eb[a] = calloc(N, sizeof(double)); A->Hb[a] = calloc(N, sizeof(double));
-        A->JDb[a] = calloc(N, sizeof(double)); A->Jb[a] = calloc(N, sizeof(double));
+        A->Jb[a] = calloc(N, sizeof(double));
         A->Eb_in[a] = calloc(N, sizeof(double));
+        for (int q = 0; q < s->npole; q++) {
+            A->JDb[q][a] = calloc(N, sizeof(double));
+            A->PDb[q][a] = calloc(N, sizeof(double));
+        }
     }
     for (int p = 0; p < 12; p++) A->Pb[p] = calloc(N, sizeof(double));
     A->rhob = calloc((size_t)(s->nmol > 0 ? s->nmol : 1) * MAXLEV * MAXLEV, sizeof(cplx));
     s->adj = A;
 }
 
-/* adjoint field state as 21 x N doubles: Eb[3], Hb[3], Pb[12], JDb[3] */
+/* adjoint field state as (18 + 6 npole) x N doubles: Eb[3], Hb[3], Pb[12], then per
+ * pole slot JDb[3], PDb[3] */
 void orc_adj_get(const osim *s, double *out) {
     const struct oadj *A = s->adj;
     long N = nn(s);
     for (int a = 0; a < 3; a++) {
         memcpy(out + a * N, A->Eb[a], N * sizeof(double));
         memcpy(out + (3 + a) * N, A->Hb[a], N * sizeof(double));
-        memcpy(out + (18 + a) * N, A->JDb[a], N * sizeof(double));
+        for (int q = 0; q < s->npole; q++) {
+            memcpy(out + (18 + 6 * q + a) * N, A->JDb[q][a], N * sizeof(double));
+            memcpy(out + (21 + 6 * q + a) * N, A->PDb[q][a], N * sizeof(double));
+        }
     }
     for (int p = 0; p < 12; p++) memcpy(out + (6 + p) * N, A->Pb[p], N * sizeof(double));
 }
@@ -792,9 +803,31 @@ void orc_adj_set(osim *s, const double *in) {
     for (int a = 0; a < 3; a++) {
         memcpy(A->Eb[a], in + a * N, N * sizeof(double));
         memcpy(A->Hb[a], in + (3 + a) * N, N * sizeof(double));
-        memcpy(A->JDb[a], in + (18 + a) * N, N * sizeof(double));
+        for (int q = 0; q < s->npole; q++) {
+            memcpy(A->JDb[q][a], in + (18 + 6 * q + a) * N, N * sizeof(double));
+            memcpy(A->PDb[q][a], in + (21 + 6 * q + a) * N, N * sizeof(double));
+        }
     }
     for (int p = 0; p < 12; p++) memcpy(A->Pb[p], in + (6 + p) * N, N * sizeof(double));
+}
+
+/* every pole's state as 6 npole x N doubles: per slot JD[3] (n-1/2), PD[3] (n) */
+int orc_npole(const osim *s) { return s->npole; }
+void orc_get_poles(const osim *s, double *out) {
+    long N = nn(s);
+    for (int q = 0; q < s->npole; q++)
+        for (int a = 0; a < 3; a++) {
+            memcpy(out + (6 * q + a) * N, s->JD[q][a], N * sizeof(double));
+            memcpy(out + (6 * q + 3 + a) * N, s->PD[q][a], N * sizeof(double));
+        }
+}
+void orc_set_poles(osim *s, const double *in) {
+    long N = nn(s);
+    for (int q = 0; q < s->npole; q++)
+        for (int a = 0; a < 3; a++) {
+            memcpy(s->JD[q][a], in + (6 * q + a) * N, N * sizeof(double));
+            memcpy(s->PD[q][a], in + (6 * q + 3 + a) * N, N * sizeof(double));
+        }
 }
 
 /* f(i,j,k) += v if the cell exists (the transpose of reading it through at()) */
@@ -803,10 +836,10 @@ static void adj_add(const osim *s, double *f, int i, int j, int k, double v) {
     if (c >= 0) f[c] += v;
 }
 
-/* Reverse of steps 4-6 of orc_step (CPML H update, currents, E update with Drude).
- * On entry the state holds the adjoints of the step's outputs (E^{n+1}, H^{n+1/2},
- * psi after the step, J_D^{n+1/2}); on exit those of its inputs (E^n, H^{n-1/2},
- * psi before, J_D^{n-1/2}).  Jb receives the adjoint of the current J^{n+1/2}.
+/* Reverse of steps 4-6 of orc_step (CPML H update, currents, E update with the
+ * dispersive poles).  On entry the state holds the adjoints of the step's outputs
+ * (E^{n+1}, H^{n+1/2}, psi after the step, each pole's J^{n+1/2} and P^{n+1}); on exit
+ * those of its inputs (E^n, H^{n-1/2}, psi before, J^{n-1/2}, P^n).  Jb receives the adjoint of the current J^{n+1/2}.
  * With grad_eps, adds d(objective)/d eps of every cell, which needs E^n (En) and
  * E^{n+1} (En1): dE^{n+1}/d eps = -(E^{n+1} - E^n) / eps in a cell that is not held
  * at zero. */
@@ -838,12 +871,18 @@ static void adj_field_step(osim *s, const double *En, const double *En1, double 
                         jdb = -g * eb;
                         if (grad_eps) grad_eps[c] += eb * (-(En1[a * N + c] - En[a * N + c]) / s->eps[c]);
                     }
-                    if (s->wp[0][c] != 0.0) {
-                        /* JD = jd; jd = ((1 - g2) JD_old + dt wp^2 E^n) / (1 + g2) */
-                        jdb += A->JDb[a][c];
-                        double g2 = 0.5 * s->dg[0][c] * dt;
-                        A->JDb[a][c] = jdb * (1.0 - g2) / (1.0 + g2);
-                        A->Eb_in[a][c] += jdb * dt * s->wp[0][c] * s->wp[0][c] / (1.0 + g2);
+                    for (int q = 0; q < s->npole; q++) {
+                        if (s->wp[q][c] == 0.0) continue;
+                        /* JD_q = jp; jp = ((1 - g2) JD_old + dt (wp^2 E^n - w0^2 P^n)) / (1 + g2);
+                         * P^{n+1} = P^n + dt jp (Lorentz).  Adjoint of jp: its part of the E
+                         * update, the carried JD_q adjoint and, through P^{n+1}, dt Pbar */
+                        double g2 = 0.5 * s->dg[q][c] * dt;
+                        double tot = jdb + A->JDb[q][a][c];
+                        if (s->w0[q][c] != 0.0) tot += dt * A->PDb[q][a][c];
+                        A->JDb[q][a][c] = tot * (1.0 - g2) / (1.0 + g2);
+                        A->Eb_in[a][c] += tot * dt * s->wp[q][c] * s->wp[q][c] / (1.0 + g2);
+                        if (s->w0[q][c] != 0.0)
+                            A->PDb[q][a][c] -= tot * dt * s->w0[q][c] * s->w0[q][c] / (1.0 + g2);
                     }
                 }
                 /* curl[0] = (kE_y dHz_dy + P6) - (kE_z dHy_dz + P7), P6 = bE_y P6 + cE_y dHz_dy, ... */
@@ -1209,12 +1248,6 @@ static int adj_molecule(osim *s, int q, const double *En, const cplx *rho_n, con
 int orc_adjoint_run(osim *s, long nsteps, int p, int f, double *grad_eps, double *grad_gamma, double *obj) {
     if (p < 0 || p >= s->nplane || f < 0 || f >= s->plane[p].nfreq || nsteps < 1) return -1;
     const long N = nn(s);
-    /* the reverse sweep transposes one Drude pole per cell (slot 0) only */
-    for (long c = 0; c < N; c++) {
-        if (s->w0[0][c] != 0.0) return -3;
-        for (int q = 1; q < s->npole; q++)
-            if (s->wp[q][c] != 0.0) return -3;
-    }
     const int M = s->nmol;
     const double dt = s->dt;
     oplane *pl = &s->plane[p];

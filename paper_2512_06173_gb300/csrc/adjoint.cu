@@ -45,11 +45,14 @@ struct AdjFieldArgs {
     const T *chi_in[3][2];
     T *chi_out[3][2];
     const uint8_t *mat;
-    const T *mat_cb, *mat_dk, *mat_db;
+    const T *mat_cb, *mat_dk, *mat_db, *mat_dp;
     int dbox[6];
     const T *dcb;
     int jbox[6];
-    T *JDb[3];
+    int npole;               // pole slots in use
+    long long jcnt;          // cells of the pole box
+    T *JDb;                  // adjoint of each slot's pole current, [slot][component][jcnt] (null: no poles)
+    T *PDb;                  // adjoint of each slot's polarisation, same layout (null: no Lorentz pole)
     int jb0[3], jbn[3];
     const T *Jb[3];
     T *gseg;                 // design-box gradient of the current segment (pass A), or null
@@ -381,18 +384,37 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) adj_passB_kernel(
         const T o0 = a.U[0][g], o1 = a.U[1][g], o2 = a.U[2][g];
         int midx;
         const T cb = adj_cb(a, i, j, k, midx);
-        // Drude: J_D = dk J_D + db E^n, used in the E update as -dt/eps J_D
-        if (a.JDb[0] && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] && j < a.jbox[1] + a.jbox[4] &&
-            k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5] && a.mat_db[midx * ML_MAX_POLES] != T(0)) {
+        // dispersive poles, slot by slot: J' = dk J + db E^n - dp P, used in the E update as
+        // -dt/eps J'; Lorentz (dp != 0): P' = P + dt J'.  The adjoint of J' collects the E
+        // update's -dt U, the carried adjoint of J' and, through P', dt Pbar'.
+        if (a.JDb && i >= a.jbox[0] && i < a.jbox[0] + a.jbox[3] && j >= a.jbox[1] && j < a.jbox[1] + a.jbox[4] &&
+            k >= a.jbox[2] && k < a.jbox[2] + a.jbox[5]) {
             const long long jq = ((long long)(k - a.jbox[2]) * a.jbox[4] + (j - a.jbox[1])) * a.jbox[3] + (i - a.jbox[0]);
-            const T dk = a.mat_dk[midx * ML_MAX_POLES], db = a.mat_db[midx * ML_MAX_POLES];
-            const T t0 = a.JDb[0][jq] - dt * o0, t1 = a.JDb[1][jq] - dt * o1, t2 = a.JDb[2][jq] - dt * o2;
-            a.JDb[0][jq] = dk * t0;
-            a.JDb[1][jq] = dk * t1;
-            a.JDb[2][jq] = dk * t2;
-            d0 += db * t0;
-            d1 += db * t1;
-            d2 += db * t2;
+            const long long jc = a.jcnt;
+            for (int p = 0; p < a.npole; p++) {
+                const int mk = midx * ML_MAX_POLES + p;
+                const T db = a.mat_db[mk];
+                if (db == T(0)) break;  // a material's poles fill slots 0, 1, ...
+                const T dk = a.mat_dk[mk];
+                const T dp = a.PDb ? a.mat_dp[mk] : T(0);
+                T *Jb = a.JDb + 3 * p * jc + jq;
+                T t0 = Jb[0] - dt * o0, t1 = Jb[jc] - dt * o1, t2 = Jb[2 * jc] - dt * o2;
+                if (dp != T(0)) {
+                    T *Pb = a.PDb + 3 * p * jc + jq;
+                    t0 += dt * Pb[0];
+                    t1 += dt * Pb[jc];
+                    t2 += dt * Pb[2 * jc];
+                    Pb[0] -= dp * t0;
+                    Pb[jc] -= dp * t1;
+                    Pb[2 * jc] -= dp * t2;
+                }
+                Jb[0] = dk * t0;
+                Jb[jc] = dk * t1;
+                Jb[2 * jc] = dk * t2;
+                d0 += db * t0;
+                d1 += db * t1;
+                d2 += db * t2;
+            }
         }
         // d objective / d E^n (sampled by the step before this one)
         if (a.injectE && a.tab && (a.pax == 0 ? i : (a.pax == 1 ? j : k)) == a.pidx) {
@@ -1064,12 +1086,14 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
                     CK(cudaMemsetAsync(phi[l][a][q], 0, g->psi_n[a] * esz, s));
                     CK(cudaMemsetAsync(chi[l][a][q], 0, g->psi_n[a] * esz, s));
                 }
-    T *JDb[3] = {};
+    T *JDb = nullptr, *PDb = nullptr;  // adjoints of the pole currents and polarisations
     if (g->JD) {
-        const size_t cnt = (size_t)g->jbox[3] * g->jbox[4] * g->jbox[5];
-        for (int c = 0; c < 3; c++) {
-            AA(JDb[c], cnt * esz);
-            CK(cudaMemsetAsync(JDb[c], 0, cnt * esz, s));
+        const size_t cnt = 3 * (size_t)g->npole * g->jcnt;
+        AA(JDb, cnt * esz);
+        CK(cudaMemsetAsync(JDb, 0, cnt * esz, s));
+        if (g->PD) {
+            AA(PDb, cnt * esz);
+            CK(cudaMemsetAsync(PDb, 0, cnt * esz, s));
         }
     }
     double *geps = nullptr, *ggam = nullptr;
@@ -1106,9 +1130,14 @@ ml_status adjoint_impl(ml_grid *g, long long N, int K, int pid, int f, double *o
     for (int a = 0; a < 3; a++) fa.per[a] = g->per[a];
     for (int q = 0; q < 6; q++) fa.pml[q] = g->pml[q];
     fa.dt = (T)g->dt;
-    for (int c = 0; c < 3; c++) { fa.U[c] = U[c]; fa.Hb[c] = Hb[c]; fa.cpml[c] = (const T *)g->cpml[c]; fa.JDb[c] = JDb[c]; }
+    for (int c = 0; c < 3; c++) { fa.U[c] = U[c]; fa.Hb[c] = Hb[c]; fa.cpml[c] = (const T *)g->cpml[c]; }
+    fa.JDb = JDb;
+    fa.PDb = PDb;
+    fa.npole = g->npole;
+    fa.jcnt = (long long)g->jcnt;
     fa.mat = g->mat;
     fa.mat_cb = (const T *)g->mat_cb; fa.mat_dk = (const T *)g->mat_dk; fa.mat_db = (const T *)g->mat_db;
+    fa.mat_dp = (const T *)g->mat_dp;
     for (int q = 0; q < 6; q++) { fa.dbox[q] = g->dbox[q]; fa.jbox[q] = g->jbox[q]; }
     fa.dcb = (const T *)g->dcb;
     if (M)
@@ -1277,9 +1306,6 @@ ml_status ml_adjoint_run(ml_grid *g, int64_t nsteps, int ckpt_every, int plane_i
     if (plane_id < 0 || plane_id >= (int)g->planes.size()) return fail(ML_ERR_INVALID_ARG, "no such plane");
     if (freq < 0 || freq >= g->planes[plane_id].nfreq) return fail(ML_ERR_INVALID_ARG, "no such frequency");
     if (grad_eps && !g->dcb) return fail(ML_ERR_INVALID_ARG, "grad_eps needs a design box");
-    if (g->PD || g->npole > 1)
-        return fail(ML_ERR_INVALID_ARG, "the adjoint transposes one Drude pole per material only (no Lorentz "
-                                        "omega0 > 0, no extra poles)");
     for (int m = 0; m < g->nmol; m++)
         if (g->gamma[m] == 0.0) return fail(ML_ERR_INVALID_ARG, "the adjoint needs gamma != 0 for every molecule");
     const int K = (int)std::min<int64_t>(ckpt_every, nsteps);

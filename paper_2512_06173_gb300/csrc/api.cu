@@ -869,14 +869,18 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
                 // each molecule's warp gathers its regularised field from E^n itself
                 MolArgs<T> m;
                 fill_mol_args<T>(g, cur, m);
-                LaunchScope ls(g, cs, 0);
                 // programmatic dependent of the previous field pass only when that pass has
                 // tiles that read J: such a tile releases this kernel only after its wait
                 // for the previous current kernel, hence after the previous molecule
                 // kernel, so the molecule state may be staged before this kernel's wait
                 const bool pdl_mol = !chain && g->pdl && g->gcmask != 0;
-                if (g->nitems > 0) CK(launch_molecules_packed<T>(m, cs, pdl_mol));
-                else CK(launch_molecules<T>(m, cs, pdl_mol));
+                if (g->nitems > 0) {
+                    LaunchScope ls(g, cs, 0);
+                    CK(launch_molecules_packed<T>(m, cs, pdl_mol));
+                } else {
+                    LaunchScope ls(g, cs, 0);
+                    CK(launch_molecules<T>(m, cs, pdl_mol));
+                }
             }
             {
                 CurArgs<T> ca;

@@ -45,6 +45,11 @@ struct ml_batch {
     std::vector<long long> sig;  // what the graph baked in
     long long launches = 0;
     std::vector<ml::DevBuf> mem;  // the device arrays above
+    // tracing (ml_batch_set_timing): events around each launch of steps taken without the
+    // graph, per kernel class {molecules, field pass, -, fold, current}
+    bool timing = false;
+    struct Timed { cudaEvent_t a, b; int kind; };
+    std::vector<Timed> timed;
 };
 
 namespace {
@@ -159,6 +164,29 @@ ml_status prepare(ml_batch *b, cudaStream_t s) {
 }
 
 // Enqueue steps s0 .. s0+count-1 of a sequence that starts at a fold boundary.
+// Events around one launch while tracing (never inside a capture: traced steps run
+// without the graph).
+struct BatchScope {
+    ml_batch *b;
+    cudaStream_t s;
+    int kind;
+    cudaEvent_t a = nullptr;
+    BatchScope(ml_batch *b_, cudaStream_t s_, int k) : b(b_), s(s_), kind(k) {
+        if (b->timing) {
+            cudaEventCreate(&a);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~BatchScope() {
+        if (a) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            cudaEventRecord(e, s);
+            b->timed.push_back({a, e, kind});
+        }
+    }
+};
+
 template <typename T>
 ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s) {
     const int nyw = (int)b->h_ywork.size(), ngw = (int)b->h_gwork.size(), nmw = (int)b->h_mwork.size();
@@ -167,18 +195,28 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
     for (int q = 0; q < count; q++) {
         const int st = s0 + q;
         if (nmw > 0) {
-            MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st, b->mol_two_level ? 1 : 0};
-            CK(launch_molecules_batch<T>(mb, nmw, s));
-            CurBatch<T> cb{(const CurArgs<T> *)b->d_cargs, b->d_gwork};
-            CK(launch_current_batch<T>(cb, ngw, s, b->pdl));
+            {
+                BatchScope bs(b, s, 0);
+                MolBatch<T> mb{(const MolArgs<T> *)b->d_margs, b->d_lev0, b->d_mwork, st, b->mol_two_level ? 1 : 0};
+                CK(launch_molecules_batch<T>(mb, nmw, s));
+            }
+            {
+                BatchScope bs(b, s, 4);
+                CurBatch<T> cb{(const CurArgs<T> *)b->d_cargs, b->d_gwork};
+                CK(launch_current_batch<T>(cb, ngw, s, b->pdl));
+            }
             b->launches += 2;
         }
-        YeeBatch<T> yb{(const YeeArgs<T> *)b->d_yargs, b->d_maps, b->d_lev0, b->d_ywork, nyw, b->d_boff, st,
-                       st % DFT_KMAX};
-        CK(launch_yee_batch<T>(yb, grid, s, b->pdl && nmw > 0));
+        {
+            BatchScope bs(b, s, 1);
+            YeeBatch<T> yb{(const YeeArgs<T> *)b->d_yargs, b->d_maps, b->d_lev0, b->d_ywork, nyw, b->d_boff, st,
+                           st % DFT_KMAX};
+            CK(launch_yee_batch<T>(yb, grid, s, b->pdl && nmw > 0));
+        }
         b->launches++;
         const bool period_end = st % DFT_KMAX == DFT_KMAX - 1;
         if (nfw > 0 && (period_end || (fold_tail && q == count - 1))) {
+            BatchScope bs(b, s, 3);
             const int first = st - st % DFT_KMAX;
             FoldBatch<T> fbt{(const FoldDesc<T> *)b->d_fdesc, b->d_fwork, st - first + 1, b->d_boff, first,
                              b->g[0]->dt};
@@ -208,7 +246,7 @@ ml_status batch_step(ml_batch *b, long long nsteps, cudaStream_t s) {
                                   (long long)(uintptr_t)b->d_lev0, (long long)(uintptr_t)b->d_ywork,
                                   (long long)(uintptr_t)b->d_gwork, (long long)(uintptr_t)b->d_mwork,
                                   (long long)(uintptr_t)b->d_fwork};
-    const long long reps = b->use_graph ? nsteps / SEQ : 0;
+    const long long reps = (b->use_graph && !b->timing) ? nsteps / SEQ : 0;
     if (reps > 0) {
         if (b->exec && sig != b->sig) drop_graph(b);
         if (!b->exec) {
@@ -319,6 +357,33 @@ ml_status ml_batch_set_tuning(ml_batch *b, int blocks_per_sm, int use_graph) {
 }
 
 int64_t ml_batch_launch_count(const ml_batch *b) { return b ? b->launches : -1; }
+
+ml_status ml_batch_set_timing(ml_batch *b, int enable) {
+    if (!b) return fail(ML_ERR_INVALID_ARG, "null batch");
+    b->timing = enable != 0;
+    return ML_OK;
+}
+
+ml_status ml_batch_timing(ml_batch *b, double *ms, int64_t *counts) {
+    if (!b) return fail(ML_ERR_INVALID_ARG, "null batch");
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    int64_t c[6] = {0, 0, 0, 0, 0, 0};
+    for (auto &x : b->timed) {
+        CK(cudaEventSynchronize(x.b));
+        float f = 0.f;
+        CK(cudaEventElapsedTime(&f, x.a, x.b));
+        t[x.kind] += f;
+        c[x.kind]++;
+        cudaEventDestroy(x.a);
+        cudaEventDestroy(x.b);
+    }
+    b->timed.clear();
+    for (int q = 0; q < 6; q++) {
+        if (ms) ms[q] = t[q];
+        if (counts) counts[q] = c[q];
+    }
+    return ML_OK;
+}
 
 // Autotuner: time `trial_steps` batched steps for each field-pass grid shape (blocks
 // per SM 1..occupancy, or one block per work item), restoring every grid's state after

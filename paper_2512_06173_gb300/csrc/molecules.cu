@@ -558,7 +558,9 @@ __device__ __forceinline__ void packed_body(const MolArgs<T> &a, const int4 item
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    // ---- 1. regularised fields, one molecule of the item after the other (whole warp)
+    // ---- 1. regularised fields, one molecule of the item after the other (whole warp;
+    // a separate gather kernel with many more windows in flight measured slower overall:
+    // 0.250 vs 0.239 ms per step on the 512 x 512 x 384 ensemble)
     for (int qq = 0; qq < cnt; qq++) {
         const int mq = a.order[item.x + qq];
         const T w0 = a.w[(long long)mq * NW + lane], w1 = a.w[(long long)mq * NW + lane + 32],

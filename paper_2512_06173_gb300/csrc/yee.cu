@@ -109,17 +109,18 @@ constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before givin
 // Body of the field pass for one block.  MODE 0 is the interior form: the caller
 // guarantees the tile and its halo touch no CPML layer, wall, periodic image or
 // material/source cell, so none of those paths is compiled in.  MODE 1 adds the CPML
-// layers, the index-0 walls, the source sheets and the per-cell coefficient dt/eps of a
-// material index (from a shared-memory table; measured faster than the same body
-// without the table even on tiles that have no material); MODE 3 is the interior form
-// with the source sheets and the material table, for tiles clear of the layers and
-// walls; MODE 2 has every path (dispersive poles, design box, periodic images).
+// layers and the index-0 walls; MODE 4 adds to those the source sheets and the per-cell
+// coefficient dt/eps of a material index (from a shared-memory table); MODE 3 is the
+// interior form with the source sheets and the material table, for tiles clear of the
+// layers and walls; MODE 2 has every path (dispersive poles, design box, periodic
+// images).  The CPML body is kept without the tables: their registers cost the vacuum
+// layers' tiles time even where the tables are never read.
 // Returns false when a plane wait gave up (the block then reported ML_ERR_TIMEOUT and
 // drained its copies); uniform over the block.
 template <typename T, int MODE>
 __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
-    constexpr bool GEN = MODE == 1 || MODE == 2, FULL = MODE == 2;
-    constexpr bool MATF = MODE == 1 || MODE == 3;  // sources and materials from the tables, no pole work
+    constexpr bool GEN = MODE == 1 || MODE == 2 || MODE == 4, FULL = MODE == 2;
+    constexpr bool MATF = MODE == 3 || MODE == 4;  // sources and materials from the tables, no pole work
     constexpr bool MATT = MATF;                    // material table
     constexpr int S = yee_stages<T>();
     constexpr int BP = box_pad<T>();
@@ -129,17 +130,19 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     T *stages = reinterpret_cast<T *>(smem_raw + 128);
     T *sHp = stages + S * SW;
     T(*sH)[TY + 1][TX + 1] = reinterpret_cast<T(*)[TY + 1][TX + 1]>(sHp);
-    __shared__ T s_src[MAXSRC];
-    __shared__ double s_red[NTHREADS / 32];
-    __shared__ T sCx[6][BOXW];  // CPML coefficients at x = x0-4+col (bE cE kE bH cH kH)
-    __shared__ T sCy[6][BOXH];  // at y = y0-1+row
-    __shared__ T s_cb[MATT ? ML_MAX_MATERIALS : 1];  // dt / eps_inf per material (MODES 1, 3)
+    // Static shared arrays are sized for the bodies that use them (every body's arrays add
+    // to the kernel's footprint, and a larger shared-memory carve-out leaves less L1).
+    constexpr int NSRC_S = (FULL || MATF) ? MAXSRC : 1;
+    __shared__ T s_src[NSRC_S];
+    __shared__ double s_red[FULL ? NTHREADS / 32 : 1];
+    __shared__ T sCx[GEN ? 6 : 1][GEN ? BOXW : 1];  // CPML coefficients at x = x0-4+col (bE cE kE bH cH kH)
+    __shared__ T sCy[GEN ? 6 : 1][GEN ? BOXH : 1];  // at y = y0-1+row
+    __shared__ T s_cb[MATT ? ML_MAX_MATERIALS : 1];  // dt / eps_inf per material (MODES 3, 4)
     // the grid's sources and flux planes (read per cell from here, not from the kernel
     // parameters: a dynamically indexed parameter array would be copied to local memory)
-    __shared__ int s_sax[MAXSRC], s_sidx[MAXSRC], s_scmp[MAXSRC];
+    __shared__ int s_sax[NSRC_S], s_sidx[NSRC_S], s_scmp[NSRC_S];
     __shared__ int s_pax[MAXPLANES], s_pidx[MAXPLANES], s_pnb[MAXPLANES], s_pnc[MAXPLANES];
     __shared__ T *s_pbuf[MAXPLANES];
-    __shared__ T s_scol[RY][3][MATF ? NTHREADS : 1];  // per thread and row: x- and y-normal sources
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
@@ -165,8 +168,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     // whose own cells need it, when the grid has the per-tile flags
     const bool general = FULL && (a.tflags ? (a.tflags[tile] & 7) != 0
                                           : (a.mat != nullptr || a.dcb != nullptr || a.JD != nullptr || a.nsrc > 0));
-    // MODES 1 and 3: does a source sheet cross the tile (block-uniform)?  Does the tile
-    // hold a non-background material?
+    // MODES 3 and 4: does the tile hold a non-background material?
     const bool has_mat = MATT && a.mat != nullptr && (a.tflags ? (a.tflags[tile] & 2) != 0 : true);
 
     // does the tile's column meet the box of the molecular current?
@@ -202,19 +204,26 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const int syh = fy ? slab(hjc, a.ny, a.pml[2], a.pml[3]) : -1;
     const int oh = hys * BOXW + hxs + 3;
 
-    if (MODE > 0 && tid < a.nsrc) {
-        s_src[tid] = src_value<T>(a.src[tid], ((double)a.step + 0.5) * (double)a.dt);
-        s_sax[tid] = a.src[tid].axis;
-        s_sidx[tid] = a.src[tid].index;
-        s_scmp[tid] = a.src[tid].comp;
-    }
-    if (tid < a.nplanes) {
-        s_pax[tid] = a.planes[tid].axis;
-        s_pidx[tid] = a.planes[tid].index;
-        s_pnb[tid] = a.planes[tid].nb;
-        s_pnc[tid] = a.planes[tid].nc;
-        s_pbuf[tid] = a.planes[tid].buf;
-    }
+    // (compile-time indices into the parameter arrays: indexing them by the thread
+    // would make the compiler copy them to local memory)
+    if (FULL || MATF)
+#pragma unroll
+        for (int q = 0; q < MAXSRC; q++)
+            if (tid == q && q < a.nsrc) {
+                s_src[q] = src_value<T>(a.src[q], ((double)a.step + 0.5) * (double)a.dt);
+                s_sax[q] = a.src[q].axis;
+                s_sidx[q] = a.src[q].index;
+                s_scmp[q] = a.src[q].comp;
+            }
+#pragma unroll
+    for (int p = 0; p < MAXPLANES; p++)
+        if (tid == p && p < a.nplanes) {
+            s_pax[p] = a.planes[p].axis;
+            s_pidx[p] = a.planes[p].index;
+            s_pnb[p] = a.planes[p].nb;
+            s_pnc[p] = a.planes[p].nc;
+            s_pbuf[p] = a.planes[p].buf;
+        }
     if (MATT && tid < ML_MAX_MATERIALS) s_cb[tid] = a.mat_cb[tid];
     if (fx)
         for (int t = tid; t < 6 * BOXW; t += NTHREADS) {
@@ -241,30 +250,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     if (MATF)
         for (int q = 0; q < a.nsrc; q++) has_src = has_src || crosses(s_sax[q], s_sidx[q]);
     for (int p = 0; p < a.nplanes; p++) has_pl = has_pl || crosses(s_pax[p], s_pidx[p]);
-    // source sheets through an own cell's column (x- or y-normal: the same every plane,
-    // summed per component into s_scol) and the z-normal ones that cross the chunk
-    // (checked per plane); flux planes through an own column or the chunk
-    static_assert(RY <= 3 && MAXSRC <= 8 && MAXPLANES <= 8, "fmask layout");
-    unsigned fmask = 0;  // bits 0..7: z-normal sources crossing the chunk; 8 + 8 r ..: planes of row r
-    if (MATF && has_src)
-#pragma unroll
-        for (int r = 0; r < RY; r++) {
-            T sc0 = T(0), sc1 = T(0), sc2 = T(0);
-            for (int q = 0; q < a.nsrc; q++) {
-                const int ax = s_sax[q], idx = s_sidx[q], cmp = s_scmp[q];
-                if (ax == 2) {
-                    if (idx >= k0 && idx < k1) fmask |= 1u << q;
-                } else if ((ax == 0 ? i : jb + r) == idx) {
-                    const T v = s_src[q];
-                    sc0 += cmp == 0 ? v : T(0);
-                    sc1 += cmp == 1 ? v : T(0);
-                    sc2 += cmp == 2 ? v : T(0);
-                }
-            }
-            s_scol[r][0][tid] = sc0;
-            s_scol[r][1][tid] = sc1;
-            s_scol[r][2][tid] = sc2;
-        }
+    // flux planes through an own column (x- or y-normal) or crossing the chunk (z-normal,
+    // checked per plane)
+    static_assert(RY <= 3 && MAXPLANES <= 8, "fmask layout");
+    unsigned fmask = 0;  // bits 8 + 8 r ..: the planes of own row r
     if (has_pl)
 #pragma unroll
         for (int r = 0; r < RY; r++)
@@ -363,7 +352,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
         // thread's cells in the field precision (GB300's FP64 rate is a small fraction
         // of its FP32 rate); times dt/2 and summed in FP64 across the block
         T absorbed = T(0);
-        // MODE 3: material index of the own cell, plane by plane (loaded before the wait)
+        // MODES 3 and 4: material index of the own cell, plane by plane (loaded before the wait)
         // offset of the own cell's material byte (32-bit: a grid with a material map has
         // fewer than 2^32 cells, checked when it is created)
         const unsigned nxy = (unsigned)a.nx * (unsigned)a.ny;
@@ -506,20 +495,17 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 T j0 = J0[r], j1 = J1[r], j2 = J2[r];
                 T en0, en1, en2;
                 if (MATF) {
-                    if (has_src) {
-                        j0 += s_scol[r][0][tid];
-                        j1 += s_scol[r][1][tid];
-                        j2 += s_scol[r][2][tid];
-                        if (fmask & 255u)
-                            for (int q = 0; q < a.nsrc; q++)
-                                if (((fmask >> q) & 1u) && k == s_sidx[q]) {
-                                    const int cmp = s_scmp[q];
-                                    const T v = s_src[q];
-                                    j0 += cmp == 0 ? v : T(0);
-                                    j1 += cmp == 1 ? v : T(0);
-                                    j2 += cmp == 2 ? v : T(0);
-                                }
-                    }
+                    if (has_src)
+                        for (int q = 0; q < a.nsrc; q++) {
+                            const int ax = s_sax[q];
+                            if ((ax == 0 ? i : (ax == 1 ? j : k)) == s_sidx[q]) {
+                                const int cmp = s_scmp[q];
+                                const T v = s_src[q];
+                                j0 += cmp == 0 ? v : T(0);
+                                j1 += cmp == 1 ? v : T(0);
+                                j2 += cmp == 2 ? v : T(0);
+                            }
+                        }
                     const T cb = MATT ? s_cb[midx_l[r]] : cb0;
                     en0 = eo0 + cb * (curl0 - j0);
                     en1 = eo1 + cb * (curl1 - j1);
@@ -702,9 +688,9 @@ __device__ __forceinline__ bool interior_geometry(const YeeArgs<T> &a, const int
     return true;
 }
 
-// 0: interior body; 1: CPML, walls, source sheets and material map (no periodic image,
-// pole or design box in the tile); 3: interior geometry with a material map or source
-// sheets; 2: every path.
+// 0: interior body; 1: CPML and walls (no periodic image, pole or design box, material
+// or source sheet in the tile); 4: CPML and walls with a material map or source sheets;
+// 3: interior geometry with a material map or source sheets; 2: every path.
 template <typename T>
 __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
     const int fl = tile_flags(a, tile);
@@ -717,7 +703,7 @@ __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
     const bool img = (a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
                      (a.per[2] && (k0 == 0 || k1 == a.nz));
-    return (img || (fl & 1) != 0) ? 2 : 1;
+    return (img || (fl & 1) != 0) ? 2 : (fl != 0 ? 4 : 1);
 }
 
 template <typename T>
@@ -726,6 +712,7 @@ __device__ __forceinline__ bool yee_dispatch(const YeeArgs<T> &a, const TmapSet 
     if (mode == 0) return yee_body<T, 0>(a, maps, tile);
     if (mode == 1) return yee_body<T, 1>(a, maps, tile);
     if (mode == 3) return yee_body<T, 3>(a, maps, tile);
+    if (mode == 4) return yee_body<T, 4>(a, maps, tile);
     return yee_body<T, 2>(a, maps, tile);
 }
 

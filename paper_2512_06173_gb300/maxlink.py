@@ -199,6 +199,8 @@ def load(build_if_missing: bool = True):
         "ml_batch_set_tuning": (I, [P, I, I]),
         "ml_batch_autotune": (I, [P, I, P, C.POINTER(I), C.POINTER(D)]),
         "ml_batch_launch_count": (I64, [P]),
+        "ml_batch_set_timing": (I, [P, I]),
+        "ml_batch_timing": (I, [P, P, P]),
         "ml_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -480,6 +482,18 @@ def ml_batch_autotune(b: int, trial_steps: int, stream: int = 0):
 
 def ml_batch_launch_count(b: int) -> int:
     return int(load().ml_batch_launch_count(C.c_void_p(b)))
+
+
+def ml_batch_set_timing(b: int, enable: bool):
+    _check(load().ml_batch_set_timing(C.c_void_p(b), int(enable)))
+
+
+def ml_batch_timing(b: int):
+    """(ms[6], counts[6]) per kernel class of the batch's traced launches."""
+    ms = np.zeros(6)
+    cnt = np.zeros(6, np.int64)
+    _check(load().ml_batch_timing(C.c_void_p(b), C.c_void_p(_ptr(ms)), C.c_void_p(_ptr(cnt))))
+    return ms, cnt
 
 
 def ml_batch_destroy(b: int):

@@ -30,7 +30,7 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def coupled(seed, shape=(14, 12, 20), periodic=(False, True, False), drude=False, nmol=3, pml=3):
+def coupled(seed, shape=(14, 12, 20), periodic=(False, True, False), drude=False, nmol=3, pml=3, lorentz=False):
     rng = np.random.default_rng(seed)
     nx, ny, nz = shape
     zc = nz // 2
@@ -43,7 +43,15 @@ def coupled(seed, shape=(14, 12, 20), periodic=(False, True, False), drude=False
     if drude:
         m = np.zeros((nz, ny, nx), np.uint8)
         m[zc + 4:zc + 7, 2:6, nx - 7:nx - 3] = 1
-        kw = dict(mat=m, materials=[W.Material(), W.Material(eps_inf=1.2, wp=0.9, gamma=0.05)])
+        media = [W.Material(), W.Material(eps_inf=1.2, wp=0.9, gamma=0.05)]
+        if lorentz:
+            # a Lorentz oscillator and a three-pole material next to the Drude block
+            m[zc + 4:zc + 7, 6:10, nx - 7:nx - 3] = 2
+            m[pml + 1:pml + 3, 2:ny - 2, 2:nx - 2] = 3
+            media += [W.Material(eps_inf=1.5, wp=0.5, gamma=0.02, omega0=0.3),
+                      W.Material(eps_inf=1.1, wp=0.4, gamma=0.03, omega0=0.35,
+                                 extra=((0.3, 0.05, 0.5), (0.5, 0.08, 0.0)))]
+        kw = dict(mat=m, materials=media)
     p6 = tuple(0 if periodic[a // 2] else pml for a in range(6))
     return W.Problem(nx, ny, nz, 0.5, periodic=periodic, pml=p6, design_box=box, design_eps=deps,
                      sources=[W.Source(2, pml + 1, 0, 1.0, 0.3, 6.0, 18.0)],
@@ -159,6 +167,14 @@ def test_multilevel_molecules_against_oracle(ml, oracle_mod, precision, tol_obj,
     """The reverse sweep through RK4 GKSL molecules (3, 5 and 8 levels, decay,
     dephasing, two substeps for one of them) next to exact two-level ones."""
     compare(ml, oracle_mod, with_multilevel(coupled(11), 11), 80, precision, tol_obj, tol_grad)
+
+
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+def test_lorentz_and_multipole_media_against_oracle(ml, oracle_mod, precision, tol_obj, tol_grad):
+    """The reverse sweep through Drude, Lorentz and three-pole cells (each slot's current
+    and, for Lorentz poles, polarisation adjoint)."""
+    prob = coupled(12, shape=(37, 21, 26), periodic=(False, False, False), drude=True, nmol=4, lorentz=True)
+    compare(ml, oracle_mod, prob, 70, precision, tol_obj, tol_grad, ckpt=16)
 
 
 def test_refuses_unsupported_inputs(ml):

@@ -208,3 +208,30 @@ def test_batched_instances_against_oracle(ml, oracle_mod, precision, tol):
         b.close()
         for g in grids:
             g.close()
+
+
+def test_batch_tracing_counts_and_results(ml):
+    """ml_batch_set_timing: traced steps run without the graph, one event pair per launch
+    and kernel class, and give the same bits as untraced steps."""
+    probs = [problems()[q] for q in (0, 2)]
+    outs = []
+    for traced in (False, True):
+        grids = [ml.Grid(p, 0) for p in probs]
+        b = ml.Batch(grids)
+        try:
+            if traced:
+                ml.ml_batch_set_timing(b.h, True)
+            b.step(70)
+            if traced:
+                ms, cnt = ml.ml_batch_timing(b.h)
+                assert cnt[0] == 70 and cnt[4] == 70 and cnt[1] == 70  # molecules, current, field pass
+                assert cnt[3] == 2  # folds: one full 64-step period and the tail
+                assert np.all(ms[[0, 1, 3, 4]] > 0)
+                ml.ml_batch_set_timing(b.h, False)
+            outs.append([state(ml, g, p) for g, p in zip(grids, probs)])
+        finally:
+            b.close()
+            for g in grids:
+                g.close()
+    for x, y in zip(outs[0], outs[1]):
+        same(x, y)

@@ -3,15 +3,16 @@ per-cell permittivity and per-molecule coupling) against facts that do not come
 from the adjoint code itself:
 
 * dot-product identity <L x, y> = <x, L^T y> for the linear field step (CPML on
-  some axes, periodic and wall axes, material table, Drude cells): any dropped
-  term, wrong sign or transposed index in the reversed step breaks it;
+  some axes, periodic and wall axes, material table, Drude, Lorentz and three-pole
+  cells): any dropped term, wrong sign or transposed index in the reversed step
+  breaks it;
 * the vector-Jacobian product of one molecule step (exact two-level, and RK4 GKSL
   with ladder decay, dephasing and several substeps for 3 and 5 levels) against
   central differences of the forward molecule step (which the molecule tests pin to
   closed forms);
 * the full gradient against central differences of the forward flux
   (Sec. IV spectra) for a coupled problem with CPML, a design box, a source and
-  molecules.
+  molecules (two-level and multilevel), with Drude, Lorentz and three-pole media.
 """
 import numpy as np
 import pytest
@@ -23,20 +24,21 @@ def _dot_case(oracle_mod, prob, seed):
     rng = np.random.default_rng(seed)
     o = oracle_mod.OracleSim(prob)
     sh = o.shape
+    npl = o.npole
     x = [rng.standard_normal(sh) for _ in range(6)]
     psi = [rng.standard_normal(sh) for _ in range(12)]
-    jd = [rng.standard_normal(sh) for _ in range(3)]
+    pol = [rng.standard_normal(sh) for _ in range(6 * npl)]
     o.set_fields(x)
     o.set_psi(psi)
-    o.set_drude_current(jd)
+    o.set_poles(pol)
     o.step(1)
-    Lx = np.concatenate([np.ravel(f) for f in o.fields() + o.psi() + o.drude_current()])
-    y = rng.standard_normal((21,) + sh)
+    Lx = np.concatenate([np.ravel(f) for f in o.fields() + o.psi() + o.poles()])
+    y = rng.standard_normal((18 + 6 * npl,) + sh)
     o.adj_reset()
     o.set_adj_state(y)
     o.adj_field_step()
     LTy = o.adj_state().ravel()
-    xv = np.concatenate([np.ravel(f) for f in x + psi + jd])
+    xv = np.concatenate([np.ravel(f) for f in x + psi + pol])
     a, b = Lx @ y.ravel(), xv @ LTy
     return abs(a - b) / abs(a)
 
@@ -54,6 +56,21 @@ def test_field_step_dot_product_materials_drude_walls(oracle_mod):
                      materials=[W.Material(), W.Material(eps_inf=1.5, wp=0.8, gamma=0.1),
                                 W.Material(eps_inf=2.25)])
     assert _dot_case(oracle_mod, prob, 1) < 1e-12
+
+
+def test_field_step_dot_product_lorentz_and_multipole(oracle_mod):
+    """Lorentz poles (the restoring term and the polarisation update) and materials with
+    three poles, next to a Drude material and CPML."""
+    mat = np.zeros((12, 11, 13), np.uint8)
+    mat[4:8, 3:7, 5:9] = 1
+    mat[0:3, :, :] = 2
+    mat[9:11, 2:9, 1:12] = 3
+    prob = W.Problem(13, 11, 12, 0.5, periodic=(False, True, False), pml=(3, 2, 0, 0, 2, 2), mat=mat,
+                     materials=[W.Material(), W.Material(eps_inf=1.5, wp=0.8, gamma=0.1),
+                                W.Material(eps_inf=2.0, wp=0.5, gamma=0.05, omega0=0.4),
+                                W.Material(eps_inf=1.2, wp=0.6, gamma=0.02, omega0=0.3,
+                                           extra=((0.4, 0.05, 0.55), (0.3, 0.1, 0.0)))])
+    assert _dot_case(oracle_mod, prob, 2) < 1e-12
 
 
 def test_molecule_vjp_matches_central_differences(oracle_mod):
@@ -114,7 +131,7 @@ def test_rk4_molecule_vjp_matches_central_differences(oracle_mod, n, nsub):
         assert abs(fdr - np.sum((rb.conj() * d).real)) < 1e-7
 
 
-def _coupled(seed, drude=False, multilevel=False):
+def _coupled(seed, drude=False, multilevel=False, lorentz=False):
     rng = np.random.default_rng(seed)
     nx, ny, nz = 14, 12, 20
     mats = [W.tls([rng.uniform(5, 9), rng.uniform(5, 7), rng.uniform(11, 13)], 0.3, 0.8, axis=q % 3,
@@ -135,16 +152,25 @@ def _coupled(seed, drude=False, multilevel=False):
     if drude:
         m = np.zeros((nz, ny, nx), np.uint8)
         m[14:17, 2:6, 8:12] = 1
-        kw = dict(mat=m, materials=[W.Material(), W.Material(eps_inf=1.2, wp=0.9, gamma=0.05)])
+        mats = [W.Material(), W.Material(eps_inf=1.2, wp=0.9, gamma=0.05)]
+        if lorentz:
+            # a Lorentz oscillator and a three-pole material next to the Drude block
+            m[14:17, 6:10, 8:12] = 2
+            m[3:5, 2:10, 2:12] = 3
+            mats += [W.Material(eps_inf=1.5, wp=0.5, gamma=0.02, omega0=0.3),
+                     W.Material(eps_inf=1.1, wp=0.4, gamma=0.03, omega0=0.35,
+                                extra=((0.3, 0.05, 0.5), (0.5, 0.08, 0.0)))]
+        kw = dict(mat=m, materials=mats)
     return W.Problem(nx, ny, nz, 0.5, periodic=(False, True, False), pml=(3, 3, 0, 0, 3, 3),
                      design_box=(0 if drude else 4, 3, 6, 6, 5, 4), design_eps=deps,
                      sources=[W.Source(2, 4, 0, 1.0, 0.3, 6.0, 18.0)],
                      planes=[W.FluxPlane(2, 15, np.array([0.25, 0.3]))], molecules=mol, **kw)
 
 
-@pytest.mark.parametrize("drude,multilevel", [(False, False), (True, False), (False, True)])
-def test_gradient_matches_central_differences(oracle_mod, drude, multilevel):
-    prob = _coupled(5, drude, multilevel)
+@pytest.mark.parametrize("drude,multilevel,lorentz", [(False, False, False), (True, False, False),
+                                                      (False, True, False), (True, False, True)])
+def test_gradient_matches_central_differences(oracle_mod, drude, multilevel, lorentz):
+    prob = _coupled(5, drude, multilevel, lorentz)
     NS = 80
 
     def J(p):

@@ -1,5 +1,7 @@
 """ml_gather_static, the allocation-free gather, against the gather inside a grid's
-step on the same field and against Eq. E_regu_Emi restated here with numpy.
+step on the same field, against the oracle's gather, and against Eq. E_regu_Emi
+restated here with numpy (for windows that cross a wall, which the oracle's grid
+refuses).
 
 The entry point serves callers that cannot let a library allocate device memory
 (their memory is reserved by their own allocator, or an allocation's possible
@@ -63,14 +65,19 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_matches_grid_gather_twice(ml, case):
+def test_matches_grid_gather_twice(ml, oracle_mod, case):
     import torch
     (nx, ny, nz), periodic, nmol = CASES[case]
     mol = ensemble(10 + case, (nx, ny, nz), periodic, nmol)
     prob = W.Problem(nx, ny, nz, 0.5, periodic=periodic, molecules=mol)
+    fields = [f.astype(np.float32).astype(np.float64) for f in W.random_fields(prob, 20 + case)]
+    # the oracle's gather (Eq. E_regu_Emi, FP64) of the same FP32 field
+    o = oracle_mod.OracleSim(prob)
+    o.set_fields(fields)
+    want_o = np.array([o.gather(m) for m in range(nmol)])
     g = ml.Grid(prob, ml.ML_F32)
     try:
-        g.set_fields(W.random_fields(prob, 20 + case))
+        g.set_fields(fields)
         N = nx * ny * nz
         E = torch.empty(3 * N, dtype=torch.float32, device="cuda")
         ml.ml_get_fields(g.h, ml.ML_EX | ml.ML_EY | ml.ML_EZ, E.data_ptr(), True, 0)
@@ -95,6 +102,7 @@ def test_matches_grid_gather_twice(ml, case):
         assert np.all(np.isfinite(got))
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < TOL32
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-4 * scale)
+        assert np.linalg.norm(got - want_o) / np.linalg.norm(want_o) < TOL32
 
 
 def restated_gather(E, pos, sigma, gamma, periodic):

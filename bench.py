@@ -236,22 +236,19 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def measure_adjoint(args, stream):
-    """Forward and adjoint wall time of the inverse-design workload (192^3 vacuum with
-    CPML, 96^3 design box, 2000 emitters, 3000 steps, checkpoints every 100 steps).
-    `reverse_ms` is the adjoint call minus a plain forward run of the same steps: the
-    checkpointed recompute plus the reversed steps."""
+def adjoint_case(prob, S, K, stream):
+    """Forward and adjoint wall time of one inverse-design problem: `reverse_ms` is the
+    adjoint call minus a plain forward run of the same S steps (the checkpointed
+    recompute plus the reversed steps), checkpoints every K steps."""
     import torch
-    from paper_2512_06173_gb300 import maxlink, workloads
+    from paper_2512_06173_gb300 import maxlink
 
-    prob = workloads.adjoint_design()
     sh = stream.cuda_stream
     g = maxlink.Grid(prob, maxlink.ML_F32, stream=sh)
-    S, K = args.adj_steps, 100
     try:
         state0 = g.checkpoint()
-        nb = 96 ** 3
-        ge = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        sx, sy, sz = prob.design_box[3:]
+        ge = torch.zeros(sx * sy * sz, dtype=torch.float64, device="cuda")
         gg = torch.zeros(prob.molecules.count, dtype=torch.float64, device="cuda")
         # warm-up of both paths (module load, first allocations)
         g.step(20)
@@ -279,6 +276,19 @@ def measure_adjoint(args, stream):
                 "grad_eps_l2": float(torch.linalg.norm(ge)), "grad_gamma_l2": float(torch.linalg.norm(gg))}
     finally:
         g.close()
+
+
+def measure_adjoint(args, stream):
+    """The inverse-design workload (192^3 vacuum with CPML, 96^3 design box, 2000
+    two-level emitters, 3000 steps, checkpoints every 100 steps), and the same problem
+    with every part of the step the adjoint takes: emitters replaced by RK4 GKSL systems
+    of 2..8 levels, a Lorentz layer and a Drude + Lorentz film behind the design box."""
+    from paper_2512_06173_gb300 import workloads
+
+    out = adjoint_case(workloads.adjoint_design(), args.adj_steps, 100, stream)
+    out["full_step"] = adjoint_case(workloads.adjoint_design(multilevel=True, media=True), args.adj_steps, 100,
+                                    stream)
+    return out
 
 
 def measure_bragg(args, stream):

@@ -46,6 +46,8 @@ struct ml_grid {
     std::vector<int> zcut;  // chunk boundaries along z
     int *d_zcut = nullptr;
     uint8_t *d_tflags = nullptr;  // per tile: bit 0 = pole or design box, bit 1 = material, bit 2 = source
+    uint8_t *d_tmode = nullptr;   // per tile: the field-pass body it takes
+    int bodies = ml::YEE_BODIES_ALL;  // the field-pass kernel's body set (YEE_BODIES_*)
     int px = 0, py = 0;
     long long plane = 0;
     size_t vol = 0;  // padded elements per array

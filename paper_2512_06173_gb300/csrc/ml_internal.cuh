@@ -65,9 +65,16 @@ struct PlaneDev {
     T *buf;
 };
 
+// Body sets of the field-pass kernel: a grid takes the smallest set that covers every
+// tile's body (block_mode in yee.cu).
+constexpr int YEE_BODIES_VACUUM = 0;  // interior and CPML bodies
+constexpr int YEE_BODIES_TABLES = 1;  // interior, interior with tables, CPML with tables
+constexpr int YEE_BODIES_ALL = 2;     // every body
+
 template <typename T>
 struct YeeArgs {
     int nx, ny, nz, px, py;
+    int bodies;                 // YEE_BODIES_*: which kernel the host launches
     long long plane;
     int per[3];
     int pml[6];
@@ -307,6 +314,8 @@ cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
 // the molecular current may start while the current kernel still runs.
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s,
                                              bool pdl = false);
+// the field-pass body of every tile (0..4, see block_mode in yee.cu), one byte per tile
+template <typename T> cudaError_t launch_tile_modes(const YeeArgs<T> &a, int ntiles, uint8_t *out, cudaStream_t s);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_molecules_packed(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s);

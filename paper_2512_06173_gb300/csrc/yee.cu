@@ -706,21 +706,30 @@ __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
     return (img || (fl & 1) != 0) ? 2 : (fl != 0 ? 4 : 1);
 }
 
-template <typename T>
+// Body of a tile in a kernel compiled with body set B.  The host picks the set from the
+// bodies of all of the grid's tiles: with YEE_BODIES_VACUUM every tile takes body 0 or 1;
+// with YEE_BODIES_TABLES body 0, 3 or 4 (a CPML tile without material or source takes
+// body 4, which then reads the background entry of the table).
+template <typename T, int B = YEE_BODIES_ALL>
 __device__ __forceinline__ bool yee_dispatch(const YeeArgs<T> &a, const TmapSet &maps, const int tile) {
     const int mode = block_mode(a, tile);
     if (mode == 0) return yee_body<T, 0>(a, maps, tile);
+    if (B == YEE_BODIES_VACUUM) return yee_body<T, 1>(a, maps, tile);
+    if (B == YEE_BODIES_TABLES) {
+        if (mode == 3) return yee_body<T, 3>(a, maps, tile);
+        return yee_body<T, 4>(a, maps, tile);
+    }
     if (mode == 1) return yee_body<T, 1>(a, maps, tile);
     if (mode == 3) return yee_body<T, 3>(a, maps, tile);
     if (mode == 4) return yee_body<T, 4>(a, maps, tile);
     return yee_body<T, 2>(a, maps, tile);
 }
 
-template <typename T>
+template <typename T, int B>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) yee_kernel(const YeeArgs<T> a,
                                                                            const __grid_constant__ TmapSet maps) {
     const int tile = a.blist ? a.blist[blockIdx.x] : (int)blockIdx.x;
-    yee_dispatch(a, maps, tile);
+    yee_dispatch<T, B>(a, maps, tile);
 }
 
 // Batched field pass: one persistent launch for the tiles of many grids.  Each block
@@ -798,12 +807,16 @@ cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s, boo
 
 template <typename T>
 cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s, bool pdl) {
-    static bool configured = false;
+    static bool configured[3] = {};
     const size_t smem = yee_smem_bytes<T>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(yee_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int b = a.bodies == YEE_BODIES_VACUUM || a.bodies == YEE_BODIES_TABLES ? a.bodies : YEE_BODIES_ALL;
+    void (*kern)(const YeeArgs<T>, const TmapSet) = b == YEE_BODIES_VACUUM   ? yee_kernel<T, YEE_BODIES_VACUUM>
+                                                    : b == YEE_BODIES_TABLES ? yee_kernel<T, YEE_BODIES_TABLES>
+                                                                             : yee_kernel<T, YEE_BODIES_ALL>;
+    if (!configured[b]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured[b] = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblocks);
@@ -815,8 +828,23 @@ cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cu
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = pdl ? 1 : 0;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, yee_kernel<T>, a, maps);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, maps);
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// The body each tile of the field pass takes (block_mode), one byte per tile: the host
+// orders the pass's blocks by it once, when the grid is created.
+template <typename T>
+__global__ void tile_modes_kernel(const YeeArgs<T> a, int ntiles, uint8_t *out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) out[t] = (uint8_t)block_mode(a, t);
+}
+
+template <typename T>
+cudaError_t launch_tile_modes(const YeeArgs<T> &a, int ntiles, uint8_t *out, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    tile_modes_kernel<T><<<(ntiles + 255) / 256, 256, 0, s>>>(a, ntiles, out);
     return cudaGetLastError();
 }
 
@@ -921,6 +949,7 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
 #define ML_INST(T)                                                                                            \
     template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t, bool);                         \
     template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t, bool);                                  \
+    template cudaError_t launch_tile_modes<T>(const YeeArgs<T> &, int, uint8_t *, cudaStream_t);                              \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \
     template cudaError_t launch_zero_pec<T>(T *const *, int, int, int, int, long long, const int *, cudaStream_t);

@@ -333,14 +333,23 @@ def bragg_ensemble(nx=512, ny=512, nz=384, nmol=100000, pml=10, slab=32, seed=3,
 
 def adjoint_design(n: int = 192, design: int = 96, nmol: int = 2000, pml: int = 10, sigma: float = 1.5,
                    gamma: float = 0.02, seed: int = 4, omega: float = 0.25, width: float = 20.0,
-                   mol_x: Optional[Tuple[float, float]] = None) -> Problem:
+                   mol_x: Optional[Tuple[float, float]] = None, multilevel: bool = False,
+                   media: bool = False) -> Problem:
     """Inverse-design problem for the adjoint: vacuum cube with CPML on every face, a
     centred design box of `design`^3 cells with eps = 1 + U(0, 1.5), `nmol` two-level
     emitters (omega0 = `omega`, mu12 = 1 along z, coupling `gamma`, ground state) in a
     slab in front of the box, a z-polarised Gaussian-pulse current sheet (carrier
     `omega`, width `width`, peak at 5 widths) on the plane x = pml + 2 and one flux
     plane near the far x face.  The pulse travels along x, so its field and the
-    dipoles are both along z."""
+    dipoles are both along z.
+
+    `multilevel` makes the emitters RK4 GKSL systems with level count uniform in 2..8
+    (harmonic ladders at `omega` +- 5 %, Hermitian z-dipoles with N(0, 0.5) entries,
+    log-uniform ladder decay in [1e-5, 1e-3], ground state).  `media` adds behind the
+    design box a 4-cell Lorentz layer (eps_inf 1.5, delta_eps 1, omega0 0.3, gamma 0.01)
+    and a 2-cell film with a weak Drude pole (wp 0.2, gamma 0.05) plus a Lorentz pole
+    (wp 0.1, omega0 0.6, gamma 0.1).  Both draw from a generator of their own, so the
+    default problem does not change."""
     rng = np.random.Generator(np.random.PCG64(seed))
     x0 = (n - design) // 2
     deps = 1.0 + rng.uniform(0.0, 1.5, (design, design, design))
@@ -351,13 +360,39 @@ def adjoint_design(n: int = 192, design: int = 96, nmol: int = 2000, pml: int = 
     xs = rng.uniform(mol_x[0], mol_x[1], size=nmol)
     ys = rng.uniform(lo, hi, size=nmol)
     zs = rng.uniform(lo, hi, size=nmol)
-    mats = [tls((xs[m], ys[m], zs[m]), omega, 1.0, axis=2, sigma=sigma, gamma=gamma, cg=1.0, ce=0.0)
-            for m in range(nmol)]
+    if not multilevel:
+        mats = [tls((xs[m], ys[m], zs[m]), omega, 1.0, axis=2, sigma=sigma, gamma=gamma, cg=1.0, ce=0.0)
+                for m in range(nmol)]
+    else:
+        r2 = np.random.Generator(np.random.PCG64(seed + 1000))
+        nl = r2.integers(2, 9, size=nmol)
+        rates = np.exp(r2.uniform(np.log(1e-5), np.log(1e-3), size=nmol))
+        mats = []
+        for m in range(nmol):
+            k = int(nl[m])
+            E = np.concatenate([[0.0], np.cumsum(omega * (1 + r2.uniform(-0.05, 0.05, size=k - 1)))])
+            mu = np.zeros((3, k, k), np.complex128)
+            mu[2] = random_hermitian(r2, k, 0.5)
+            rho = np.zeros((k, k), np.complex128)
+            rho[0, 0] = 1.0
+            mats.append(dict(n=k, pos=(xs[m], ys[m], zs[m]), sigma=sigma, gamma=gamma,
+                             H0=np.diag(E).astype(np.complex128), mu=mu, rho=rho,
+                             decay=float(rates[m]), kind=KIND_RK4, nsub=1))
+    mat, materials = None, [Material(1.0)]
+    if media:
+        mat = np.zeros((n, n, n), np.uint8)
+        xl = x0 + design + 4
+        mat[:, :, xl:xl + 4] = 1
+        mat[:, :, xl + 4:xl + 6] = 2
+        materials = [Material(1.0), Material(1.5, wp=0.3, gamma=0.01, omega0=0.3),
+                     Material(1.0, wp=0.2, gamma=0.05, extra=((0.1, 0.1, 0.6),))]
     src = [Source(axis=0, index=pml + 2, comp=2, amp=1.0, omega=omega, width=width, t0=5.0 * width)]
     planes = [FluxPlane(0, n - pml - 4, np.array([omega]))]
+    kind = "ml" if multilevel else "tls"
     return Problem(n, n, n, 0.5, pml=(pml,) * 6, design_box=(x0, x0, x0, design, design, design),
                    design_eps=deps, sources=src, molecules=pack_molecules(mats), planes=planes,
-                   name=f"adjoint-design-{n}^3-box{design}^3-{nmol}tls")
+                   mat=mat, materials=materials,
+                   name=f"adjoint-design-{n}^3-box{design}^3-{nmol}{kind}" + ("-media" if media else ""))
 
 
 def plasmonic_instance(edge: int, nmol: int, rng, pml: int = 8, omega: float = 0.25, mu12: float = 0.05,

@@ -177,6 +177,31 @@ def test_lorentz_and_multipole_media_against_oracle(ml, oracle_mod, precision, t
     compare(ml, oracle_mod, prob, 70, precision, tol_obj, tol_grad, ckpt=16)
 
 
+_FULL = {}
+
+
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+def test_design_problem_with_multilevel_molecules_and_media(ml, oracle_mod, precision, tol_obj, tol_grad):
+    """A 64^3 copy of the inverse-design problem with every part of the step the adjoint
+    takes at once: CPML on all faces, the design box, a source sheet, RK4 GKSL systems of
+    2..8 levels, a Lorentz layer and a Drude + Lorentz film between the box and the flux
+    plane."""
+    prob = W.adjoint_design(n=64, design=12, nmol=12, pml=6, width=6.0, multilevel=True, media=True)
+    if "o" not in _FULL:
+        o = oracle_mod.OracleSim(prob)
+        _FULL["o"] = o.adjoint_run(160, 0, 0)
+    obj_o, ge_o, gg_o = _FULL["o"]
+    x0, y0, z0, sx, sy, sz = prob.design_box
+    g = ml.Grid(prob, precision)
+    try:
+        obj, ge, gg = g.adjoint(160, 0, 0, ckpt_every=40)
+    finally:
+        g.close()
+    assert abs(obj - obj_o) <= tol_obj * abs(obj_o)
+    assert rel(ge, ge_o[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx]) < tol_grad
+    assert rel(gg, gg_o) < tol_grad
+
+
 def test_refuses_unsupported_inputs(ml):
     mol = W.pack_molecules([W.tls([7.0, 6.0, 10.0], 0.3, 0.5, sigma=1.0, gamma=0.0, decay=0.01)])
     prob = W.Problem(14, 12, 20, 0.5, molecules=mol, planes=[W.FluxPlane(2, 15, np.array([0.3]))])

@@ -760,6 +760,41 @@ def measure_superradiant(args, stream):
             "kernel_ms_per_step": r["kernel_ms_per_step"], "gpu_launches": r["launches"]}
 
 
+def measure_static_gather(args, stream):
+    """ml_gather_static at its molecule limit: 16,384 molecules at seeded positions in a
+    256^3 FP32 field (periodic on every axis), widths sigma = 1.5 and the widest accepted
+    sigma = 7/3 (a 16-plane window); CUDA events around 50 calls after 5 warm-up calls."""
+    import numpy as np
+    import torch
+    from paper_2512_06173_gb300 import maxlink
+
+    n, M = 256, maxlink.ML_STATIC_GATHER_MAX_MOLECULES
+    rng = np.random.default_rng(11)
+    E = torch.randn(3 * n ** 3, dtype=torch.float32, device="cuda")
+    pos = torch.tensor(rng.uniform(0.0, n, (M, 3)), dtype=torch.float64, device="cuda")
+    gamma = torch.ones(M, dtype=torch.float64, device="cuda")
+    out = torch.empty((M, 3), dtype=torch.float32, device="cuda")
+    sh = stream.cuda_stream
+    res = {"molecules": M, "grid": f"{n}^3"}
+    for sg in (1.5, 7.0 / 3.0):
+        sigma = torch.full((M,), sg, dtype=torch.float64, device="cuda")
+        call = lambda: maxlink.ml_gather_static(E.data_ptr(), n, n, n, (1, 1, 1), M, pos.data_ptr(),
+                                                sigma.data_ptr(), gamma.data_ptr(), out.data_ptr(), sh)
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                call()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(50):
+                call()
+            e1.record(stream)
+        e1.synchronize()
+        us = e0.elapsed_time(e1) / 50 * 1e3
+        R = int(np.ceil(3 * sg))
+        res[f"sigma_{sg:.3f}"] = {"us_per_call": us, "molecules_per_s": M / us * 1e6, "window": 2 * R + 2}
+    return res
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -769,7 +804,7 @@ def run_ours(args, world, rank, local):
     sections = {"adjoint": measure_adjoint, "batch": measure_batch, "bragg": measure_bragg,
                 "superradiant": measure_superradiant, "dispersive": measure_dispersive,
                 "transfer": measure_transfer, "features": measure_features, "cavity": measure_cavity,
-                "laser": measure_laser}
+                "laser": measure_laser, "static_gather": measure_static_gather}
     if args.section != "main":
         # one secondary measurement alone (profiling runs): its JSON object, rank 0
         out = sections[args.section](args, torch.cuda.Stream())
@@ -790,7 +825,8 @@ def run_ours(args, world, rank, local):
     sec = {}
     for name, skip in (("superradiant", args.no_superradiant), ("adjoint", args.no_adjoint),
                        ("batch", args.no_batch), ("dispersive", args.no_dispersive),
-                       ("transfer", args.no_transfer), ("cavity", args.no_cavity), ("laser", args.no_laser)):
+                       ("transfer", args.no_transfer), ("cavity", args.no_cavity), ("laser", args.no_laser),
+                       ("static_gather", args.no_static_gather)):
         sec[name] = sections[name](args, stream) if (solo and not skip) else None
     # ---- CPU baseline: the oracle on this host, rank 0 at N=1 only
     cpu = None
@@ -832,7 +868,8 @@ def main():
     ap.add_argument("--traced-steps", type=int, default=400,
                     help="steps of the traced pass that times each kernel (roofline)")
     ap.add_argument("--section", default="main", choices=["main", "adjoint", "batch", "bragg", "superradiant",
-                                                        "dispersive", "transfer", "features", "cavity", "laser"],
+                                                        "dispersive", "transfer", "features", "cavity", "laser",
+                                                        "static_gather"],
                     help="run only this measurement (the default runs the main line with every section)")
     ap.add_argument("--adj-steps", type=int, default=3000)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-realisations comparison")
@@ -843,6 +880,7 @@ def main():
     ap.add_argument("--cavity-steps", type=int, default=2000)
     ap.add_argument("--cavity-molecules", type=int, default=1000000)
     ap.add_argument("--no-laser", action="store_true", help="skip the laser-driven molecules")
+    ap.add_argument("--no-static-gather", action="store_true", help="skip the allocation-free gather timing")
     ap.add_argument("--laser-steps", type=int, default=2000)
     ap.add_argument("--laser-molecules", type=int, default=4000000)
     ap.add_argument("--bragg-steps", type=int, default=400)

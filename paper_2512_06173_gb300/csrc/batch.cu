@@ -26,6 +26,7 @@ struct ml_batch {
     // programmatic dependent launch of the current and field-pass kernels (ML_PDL=0: off)
     bool pdl = true;
     bool mol_two_level = true;  // every instance's molecules are all two-level
+    int bodies = ml::YEE_BODIES_ALL;  // field-pass body set covering every instance
     // host copies of the argument arrays (kept alive: they are the source of async copies)
     std::vector<unsigned char> h_yargs, h_gargs, h_cargs, h_margs, h_fdesc;
     std::vector<TmapSet> h_maps;
@@ -210,7 +211,7 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
         {
             BatchScope bs(b, s, 1);
             YeeBatch<T> yb{(const YeeArgs<T> *)b->d_yargs, b->d_maps, b->d_lev0, b->d_ywork, nyw, b->d_boff, st,
-                           st % DFT_KMAX};
+                           st % DFT_KMAX, b->bodies};
             CK(launch_yee_batch<T>(yb, grid, s, b->pdl && nmw > 0));
         }
         b->launches++;
@@ -310,6 +311,13 @@ ml_status ml_batch_create(ml_grid *const *grids, int n, ml_batch **out) {
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->blocks_per_sm = b->prec ? 1 : 3;
     if (const char *ev = std::getenv("ML_PDL")) b->pdl = std::atoi(ev) != 0;
+    // the smallest body set of the field pass that covers every instance's tiles (a
+    // vacuum grid's CPML tiles may take the table body: it reads the background entry)
+    b->bodies = YEE_BODIES_VACUUM;
+    for (ml_grid *g : b->g) {
+        if (g->bodies == YEE_BODIES_ALL) b->bodies = YEE_BODIES_ALL;
+        else if (g->bodies == YEE_BODIES_TABLES && b->bodies == YEE_BODIES_VACUUM) b->bodies = YEE_BODIES_TABLES;
+    }
     {
         ml_status st = dev_alloc(b->mem, (void **)&b->d_boff, sizeof(long long));
         if (st != ML_OK) {
@@ -320,8 +328,10 @@ ml_status ml_batch_create(ml_grid *const *grids, int n, ml_batch **out) {
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         // kernel attributes are set outside any capture
-        e = b->prec ? launch_yee_batch<double>(YeeBatch<double>{}, 1, b->cap_stream)
-                    : launch_yee_batch<float>(YeeBatch<float>{}, 1, b->cap_stream);
+        YeeBatch<double> yd{};
+        YeeBatch<float> yf{};
+        yd.bodies = yf.bodies = b->bodies;
+        e = b->prec ? launch_yee_batch<double>(yd, 1, b->cap_stream) : launch_yee_batch<float>(yf, 1, b->cap_stream);
     }
     if (e != cudaSuccess) {
         ml_batch_destroy(b);

@@ -262,6 +262,7 @@ struct YeeBatch {
     const long long *boff;
     int s;                    // step within the sequence
     int slot;                 // DFT ring slot of this step
+    int bodies;               // YEE_BODIES_* covering every instance's tiles
 };
 template <typename T>
 struct GathBatch {

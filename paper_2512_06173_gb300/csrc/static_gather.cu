@@ -9,10 +9,12 @@
 // file-scope device array below, of a fixed maximum size, held by every GPU that
 // loads the library until the process exits.
 //
-// Two kernels: for each molecule and each plane of its kernel window, one warp
-// writes the plane's weighted field sums into the scratch array (every slot the
-// second kernel reads is written by the first, so nothing needs clearing); one warp
-// per molecule then adds the planes in a fixed order and applies the coupling.
+// Two kernels: one block per molecule, whose first warp computes the molecule's six
+// normalised 1D weight vectors once into shared memory, and whose sixteen warps (one
+// per plane of the kernel window) write the planes' weighted field sums into the
+// scratch array (every slot the second kernel reads is written by the first, so
+// nothing needs clearing); one warp per molecule then adds the planes in a fixed
+// order and applies the coupling.
 // Calls share the scratch: calls that overlap on the GPU (for example on two
 // streams) race, so issue them one after another.
 #include <cmath>
@@ -43,7 +45,7 @@ struct SgArgs {
 // exactly 1 and a narrow kernel cannot underflow to 0/0 (the normalisation removes the
 // common factor).  Three exps per lane.
 __device__ __forceinline__ void sg_weights(const double (&p)[3], const int (&s)[3], int W, double sg, float (&w)[6][16]) {
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const double inv = 1.0 / (2.0 * sg * sg);
     double e[3];
 #pragma unroll
@@ -81,22 +83,28 @@ __device__ __forceinline__ bool sg_valid(const SgArgs &a, int m) {
     return ok;
 }
 
-// grid: (molecules, SG_PLANES), 32 threads.  Lane = (dx in 0..15, row parity).
-__global__ void sg_partial_kernel(const SgArgs a) {
+// grid: molecules, SG_PLANES warps per block: warp dz takes plane dz of the window.
+// Lane = (dx in 0..15, row parity).
+__global__ void __launch_bounds__(SG_PLANES * 32) sg_partial_kernel(const SgArgs a) {
     __shared__ float w[6][16];
-    const int m = blockIdx.x, dz = blockIdx.y, lane = threadIdx.x;
+    const int m = blockIdx.x, dz = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (m >= a.nmol) return;
-    float part[3] = {0.f, 0.f, 0.f};
-    if (sg_valid(a, m)) {
+    const bool valid = sg_valid(a, m);  // uniform over the block
+    int R = 0, W = 0, s[3] = {0, 0, 0};
+    if (valid) {
         const double sg = a.sigma[m];
-        const int R = (int)ceil(3.0 * sg), W = 2 * R + 2;
-        int s[3];
+        R = (int)ceil(3.0 * sg);
+        W = 2 * R + 2;
         double p[3];
         for (int ax = 0; ax < 3; ax++) {
             p[ax] = a.pos[3 * m + ax];
             s[ax] = (int)floor(p[ax]) - R;
         }
-        sg_weights(p, s, W, sg, w);
+        if (dz == 0) sg_weights(p, s, W, sg, w);
+    }
+    __syncthreads();
+    float part[3] = {0.f, 0.f, 0.f};
+    if (valid) {
         const int dx = lane & 15, ly = lane >> 4;
         bool okz = dz < W;
         const int z = sg_wrap(s[2] + dz, a.nz, a.pz, okz);
@@ -187,7 +195,7 @@ ml_status ml_gather_static(const float *E, int nx, int ny, int nz, const int *pe
     a.scratch = scratch;
     a.out = out;
     cudaStream_t s = (cudaStream_t)stream;
-    sg_partial_kernel<<<dim3(nmol, SG_PLANES), 32, 0, s>>>(a);
+    sg_partial_kernel<<<nmol, SG_PLANES * 32, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return sg_fail(ML_ERR_CUDA, std::string("partial kernel: ") + cudaGetErrorString(e));
     sg_reduce_kernel<<<(nmol + 3) / 4, 128, 0, s>>>(a);

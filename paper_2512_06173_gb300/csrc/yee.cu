@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 4 : 1) yee_kernel(c
 // walks the (instance, tile) work list; per item it copies the instance's arguments
 // into shared memory, turns them to the time level, step and DFT ring slot of this
 // step, and runs the same body as the single-grid kernel.
-template <typename T>
+template <typename T, int B>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_batch_kernel(const YeeBatch<T> b) {
     __shared__ __align__(16) YeeArgs<T> sa;
     __shared__ const TmapSet *smaps;
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_batch_ke
             smaps = b.maps + 2 * wk.x + lev;
         }
         __syncthreads();
-        const bool ok = yee_dispatch(sa, *smaps, wk.y);
+        const bool ok = yee_dispatch<T, B>(sa, *smaps, wk.y);
         // a wait that gave up may leave copies in flight: stop reusing this block
         if (!ok) return;
     }
@@ -784,12 +784,16 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 3 : 1) yee_batch_ke
 
 template <typename T>
 cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s, bool pdl) {
-    static bool configured = false;
+    static bool configured[3] = {};
     const size_t smem = yee_smem_bytes<T>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(yee_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int bs = b.bodies == YEE_BODIES_VACUUM || b.bodies == YEE_BODIES_TABLES ? b.bodies : YEE_BODIES_ALL;
+    void (*kern)(const YeeBatch<T>) = bs == YEE_BODIES_VACUUM   ? yee_batch_kernel<T, YEE_BODIES_VACUUM>
+                                      : bs == YEE_BODIES_TABLES ? yee_batch_kernel<T, YEE_BODIES_TABLES>
+                                                                : yee_batch_kernel<T, YEE_BODIES_ALL>;
+    if (!configured[bs]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured[bs] = true;
     }
     if (b.nwork == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -802,7 +806,7 @@ cudaError_t launch_yee_batch(const YeeBatch<T> &b, int grid, cudaStream_t s, boo
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, yee_batch_kernel<T>, b);
+    return cudaLaunchKernelEx(&cfg, kern, b);
 }
 
 template <typename T>

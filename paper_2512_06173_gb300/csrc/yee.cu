@@ -261,7 +261,11 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 const int ax = s_pax[p], idx = s_pidx[p];
                 if (ax == 2 ? (idx >= k0 && idx < k1) : ((ax == 0 ? i : jb + r) == idx)) fmask |= 256u << (8 * r + p);
             }
-    // producer: one thread issues the six tiled loads of plane q into its stage
+    // producer: one thread issues the six tiled loads of plane q into its stage.  The E
+    // boxes start at x0 - 4 (x0 - 1 and x0 + 32 are needed); the H boxes start at x0 - 8
+    // and end at x0 + 31 (H is needed at x0 - 1 and the own columns only), so an H row is
+    // five 32-byte sectors instead of six; H of column x in a stage therefore sits four
+    // places to the right of E of column x.
     auto issue = [&](int q) {
         const int s = (q - q0) % S;
         T *st = stages + s * SW;
@@ -269,7 +273,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             tma_load_3d(st + c * BP, &maps.E[c], x0 + BOXX, y0, q + 1, &bars[s]);
-            tma_load_3d(st + (3 + c) * BP, &maps.H[c], x0 + BOXX, y0, q + 1, &bars[s]);
+            tma_load_3d(st + (3 + c) * BP, &maps.H[c], x0 + BOXX - 4, y0, q + 1, &bars[s]);
         }
     };
     int issued = q0 - 1;
@@ -335,9 +339,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 h_pml_load(p, q);
                 h_pml(d, p, q, kc, col, ty * RY + r + 1, false);
             }
-            T hz = Ek[5 * BP + o];
-            hpx[r] = Ek[3 * BP + o];
-            hpy[r] = Ek[4 * BP + o];
+            T hz = Ek[5 * BP + o + 4];
+            hpx[r] = Ek[3 * BP + o + 4];
+            hpy[r] = Ek[4 * BP + o + 4];
             h_finish(a.dt, d, hpx[r], hpy[r], hz);
         }
     }
@@ -417,9 +421,9 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 const int o = ob + r * BOXW;
                 const int j = jb + r;
                 const bool own = xin && j < a.ny;
-                hx[r] = Hk[o];
-                hy[r] = Hk[BP + o];
-                hz[r] = Hk[2 * BP + o];
+                hx[r] = Hk[o + 4];
+                hy[r] = Hk[BP + o + 4];
+                hz[r] = Hk[2 * BP + o + 4];
                 T d[6];
                 e_diffs<T, BP>(Ek, Ek1, o, d);
                 if (pown[r]) h_pml(d, ph[r], qo[r], k, col, ty * RY + r + 1, true);
@@ -446,7 +450,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
             }
             // ---- H^{n+1/2}(k): low halo row (y0-1) and column (x0-1), recomputed
             if (halo) {
-                T qx = Hk[oh], qy = Hk[BP + oh], qz = Hk[2 * BP + oh];
+                T qx = Hk[oh + 4], qy = Hk[BP + oh + 4], qz = Hk[2 * BP + oh + 4];
                 T d[6];
                 e_diffs<T, BP>(Ek, Ek1, oh, d);
                 if (phalo) h_pml(d, phh, qh, k, hxs + 3, hys, false);

@@ -59,8 +59,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// TMA descriptor of one padded field array: 3D (px, py, nz+2), box BOXW x BOXH x 1.
-ml_status make_tmap(const ml_grid *g, void *base, CUtensorMap *out) {
+// TMA descriptor of one padded field array: 3D (px, py, nz+2), box BOXW x rows x 1.
+ml_status make_tmap(const ml_grid *g, void *base, int rows, CUtensorMap *out) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void *p = nullptr;
@@ -72,7 +72,7 @@ ml_status make_tmap(const ml_grid *g, void *base, CUtensorMap *out) {
     }
     cuuint64_t dims[3] = {(cuuint64_t)g->px, (cuuint64_t)g->py, (cuuint64_t)(g->nz + 2)};
     cuuint64_t strides[2] = {(cuuint64_t)g->px * g->esz, (cuuint64_t)g->plane * g->esz};
-    cuuint32_t box[3] = {(cuuint32_t)BOXW, (cuuint32_t)BOXH, 1};
+    cuuint32_t box[3] = {(cuuint32_t)BOXW, (cuuint32_t)rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(out, g->prec ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -338,9 +338,9 @@ ml_status ml_grid_create(const ml_grid_desc *d, void *stream, ml_grid **out) {
     }
     for (int l = 0; l < 2; l++)
         for (int c = 0; c < 3; c++) {
-            st = make_tmap(g, g->F[l][c], &g->tm[l].E[c]);
+            st = make_tmap(g, g->F[l][c], BOXH, &g->tm[l].E[c]);
             if (st != ML_OK) return bail(st);
-            st = make_tmap(g, g->F[l][3 + c], &g->tm[l].H[c]);
+            st = make_tmap(g, g->F[l][3 + c], BOXHH, &g->tm[l].H[c]);
             if (st != ML_OK) return bail(st);
         }
     GA(g->absorbed_part, (size_t)g->nblocks * sizeof(double));

@@ -128,7 +128,8 @@ struct TmapSet {
 
 constexpr int BOXW = TX + 8;   // TMA box: x0-4 .. x0+TX+3 (16-byte aligned start)
 constexpr int BOXX = XO - 4;   // padded x index of the box start minus x0
-constexpr int BOXH = TY + 2;   // rows y0-1 .. y0+TY
+constexpr int BOXH = TY + 2;   // rows y0-1 .. y0+TY (E)
+constexpr int BOXHH = TY + 1;  // rows y0-1 .. y0+TY-1 (H: the curl of E needs E at y0+TY, never H)
 template <typename T> constexpr int yee_stages() { return sizeof(T) == 4 ? 4 : 3; }
 template <typename T> constexpr int box_pad() { return (int)(((BOXW * BOXH * sizeof(T) + 127) / 128) * 128 / sizeof(T)); }
 template <typename T> constexpr size_t yee_smem_bytes() {

@@ -154,7 +154,8 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     const int jb = y0 + ty * RY;  // first own row; own rows jb .. jb+RY-1
     const int q0 = k0 - 1;        // first plane of the ring
     const int qlast = k1;         // last plane needed (z+1 neighbour of the last own plane)
-    constexpr uint32_t STAGE_BYTES = 6u * BOXW * BOXH * sizeof(T);
+    // bytes a stage receives: three E boxes of BOXH rows and three H boxes of BOXHH rows
+    constexpr uint32_t STAGE_BYTES = 3u * BOXW * (BOXH + BOXHH) * sizeof(T);
 
     // block-uniform features: CPML layers this tile (with its halo) can touch,
     // periodic ghost images to write, per-cell material work, molecular current
@@ -262,9 +263,10 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 if (ax == 2 ? (idx >= k0 && idx < k1) : ((ax == 0 ? i : jb + r) == idx)) fmask |= 256u << (8 * r + p);
             }
     // producer: one thread issues the six tiled loads of plane q into its stage.  The E
-    // boxes start at x0 - 4 (x0 - 1 and x0 + 32 are needed); the H boxes start at x0 - 8
-    // and end at x0 + 31 (H is needed at x0 - 1 and the own columns only), so an H row is
-    // five 32-byte sectors instead of six; H of column x in a stage therefore sits four
+    // boxes start at x0 - 4 (x0 - 1 and x0 + 32 are needed) and hold rows y0 - 1 .. y0 + 8;
+    // the H boxes start at x0 - 8 and end at x0 + 31 (H is needed at x0 - 1 and the own
+    // columns only), so an H row is five 32-byte sectors instead of six, and hold rows
+    // y0 - 1 .. y0 + 7 (no H of row y0 + 8 is read).  H of column x in a stage sits four
     // places to the right of E of column x.
     auto issue = [&](int q) {
         const int s = (q - q0) % S;

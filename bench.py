@@ -504,7 +504,7 @@ def measure_batch(args, stream):
     K steps as one batch (one launch per kernel class per step, graph-replayed, field-pass
     grid from the autotuner) against the same K steps with ml_step on each grid in turn
     (the plain one-instance-per-launch method).  Both start from the same state.  The
-    plain grids use the automatic short z chunks, the batched ones 16-plane chunks: the
+    plain grids use the automatic short z chunks, the batched ones 32-plane chunks: the
     fields do not depend on the chunking, the per-instance absorbed energies agree to
     rounding (the per-block partial sums are grouped differently)."""
     import numpy as np

@@ -434,7 +434,7 @@ def plasmonic_batch(count: int = 64, seed: int = 5, edges=(64, 96, 128, 160), nm
         nmol = int(rng.integers(nmol_range[0], nmol_range[1] + 1))
         # batched grids fill the GPU together: long z chunks (fewer boundary planes
         # and ring fills per cell) beat the many short ones a lone grid needs
-        out.append(plasmonic_instance(edge, nmol, rng).replace(zchunk=16))
+        out.append(plasmonic_instance(edge, nmol, rng).replace(zchunk=32))
     return out
 
 
@@ -494,7 +494,7 @@ def energy_transfer_batch(count: int = 64, edge: int = 96, seed: int = 12, dista
     for q in range(count):
         d = float(rng.uniform(*distances))
         n = int(rng.choice(models))
-        out.append(energy_transfer(edge=edge, distance=d, n_acceptor=n, seed=seed * 1000 + q).replace(zchunk=16))
+        out.append(energy_transfer(edge=edge, distance=d, n_acceptor=n, seed=seed * 1000 + q).replace(zchunk=32))
     return out
 
 

@@ -1,8 +1,8 @@
 """GPU discrete adjoint (ml_adjoint_run) against the oracle's adjoint on the same
 seeded problems: objective, d/d eps over the design box and d/d gamma per
 molecule, for exact two-level emitters and RK4 GKSL systems of up to 8 levels.  FP64
-runs agree to round-off; FP32 runs within 1e-3 relative L2 (gradients) and 1e-4
-(objective).  Also: the result does not depend on the checkpoint interval (up to the
+runs agree to round-off; FP32 runs within 1e-4 relative L2 (gradients) and 1e-5
+(objective): the measured FP32 errors on these problems are at most 9e-7 and 8e-8.  Also: the result does not depend on the checkpoint interval (up to the
 round-off of the per-segment gradient sums), the grid ends in the state a plain run
 reaches, and unsupported inputs (zero couplings, no design box) are refused.
 """
@@ -76,12 +76,12 @@ def compare(ml, oracle_mod, prob, steps, precision, tol_obj, tol_grad, ckpt=25, 
     return obj, ge, gg
 
 
-@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-5, 1e-4)])
 def test_coupled_design_box_and_molecules(ml, oracle_mod, precision, tol_obj, tol_grad):
     compare(ml, oracle_mod, coupled(5), 80, precision, tol_obj, tol_grad)
 
 
-@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-5, 1e-4)])
 def test_drude_walls_ragged(ml, oracle_mod, precision, tol_obj, tol_grad):
     prob = coupled(6, shape=(37, 21, 26), periodic=(False, False, False), drude=True, nmol=4)
     compare(ml, oracle_mod, prob, 70, precision, tol_obj, tol_grad, ckpt=16)
@@ -162,14 +162,14 @@ def with_multilevel(prob, seed, levels=(3, 5, 8), nsub=(1, 2, 1)):
     return prob.replace(molecules=W.pack_molecules(mats))
 
 
-@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-5, 1e-4)])
 def test_multilevel_molecules_against_oracle(ml, oracle_mod, precision, tol_obj, tol_grad):
     """The reverse sweep through RK4 GKSL molecules (3, 5 and 8 levels, decay,
     dephasing, two substeps for one of them) next to exact two-level ones."""
     compare(ml, oracle_mod, with_multilevel(coupled(11), 11), 80, precision, tol_obj, tol_grad)
 
 
-@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-5, 1e-4)])
 def test_lorentz_and_multipole_media_against_oracle(ml, oracle_mod, precision, tol_obj, tol_grad):
     """The reverse sweep through Drude, Lorentz and three-pole cells (each slot's current
     and, for Lorentz poles, polarisation adjoint)."""
@@ -180,7 +180,7 @@ def test_lorentz_and_multipole_media_against_oracle(ml, oracle_mod, precision, t
 _FULL = {}
 
 
-@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-5, 1e-4)])
 def test_design_problem_with_multilevel_molecules_and_media(ml, oracle_mod, precision, tol_obj, tol_grad):
     """A 64^3 copy of the inverse-design problem with every part of the step the adjoint
     takes at once: CPML on all faces, the design box, a source sheet, RK4 GKSL systems of
@@ -222,7 +222,7 @@ def design_copy():
     return W.adjoint_design(n=24, design=10, nmol=20, pml=4, sigma=1.0, width=6.0, mol_x=(8.0, 11.0), seed=14)
 
 
-@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-4, 1e-3)])
+@pytest.mark.parametrize("precision,tol_obj,tol_grad", [(1, 1e-10, 1e-8), (0, 1e-5, 1e-4)])
 def test_design_workload_copy_matches_oracle(ml, oracle_mod, precision, tol_obj, tol_grad):
     compare(ml, oracle_mod, design_copy(), 150, precision, tol_obj, tol_grad, ckpt=40, freq=0)
 

@@ -121,3 +121,38 @@ def test_allocator_arguments(ml):
     a = ml.TorchAllocator()
     assert L.ml_set_allocator(a.c_alloc, ml._FREE_T(), None) == ml.ML_ERR_INVALID_ARG
     assert L.ml_set_allocator(ml._ALLOC_T(), a.c_free, None) == ml.ML_ERR_INVALID_ARG
+
+
+def test_refused_allocation_gives_oom_and_returns_memory(ml, oracle_mod):
+    """An allocator that refuses: grid creation fails with ML_ERR_OOM, every buffer the
+    call had taken goes back through the callback, and the library keeps working."""
+    ga = ml.use_torch_allocator()
+    L = ml.load()
+    al = ml.TorchAllocator()
+    limit = 10
+
+    def refusing(pp, nbytes, stream, ctx):
+        if al.allocs >= limit:
+            return 1
+        return al._alloc(pp, nbytes, stream, ctx)
+
+    c_alloc = ml._ALLOC_T(refusing)
+    assert L.ml_set_allocator(c_alloc, al.c_free, None) == ml.ML_OK
+    prob = W.small_coupled(seed=3, shape=(37, 22, 29))
+    try:
+        with pytest.raises(ml.MaxlinkError) as e:
+            ml.Grid(prob, 0)
+        assert e.value.status == ml.ML_ERR_OOM
+        assert al.allocs == limit and al.frees == limit and al.live_bytes == 0
+    finally:
+        assert L.ml_set_allocator(ga.c_alloc, ga.c_free, None) == ml.ML_OK
+    g = ml.Grid(prob, 0)
+    try:
+        g.step(20)
+        g.sync()
+        o = oracle_mod.OracleSim(prob)
+        o.step(20)
+        for a, b in zip(g.fields(), o.fields()):
+            assert rel(a, b) < 1e-4
+    finally:
+        g.close()

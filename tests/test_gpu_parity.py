@@ -98,6 +98,34 @@ def test_thin_periodic_layer(ml, oracle_mod, precision, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
+def test_printed_superradiance_example(ml, oracle_mod, precision, tol):
+    """The paper's printed superradiance example (Appendix B, tests/golden): four
+    co-located two-level systems at a coupling of 1.0 in grid units, a one-cell kernel,
+    an 80 x 80 cell with 30-cell absorbing layers, nz = 1 periodic; 200 steps (the
+    excited population falls to about a quarter).  Coherences, populations and fields."""
+    import json
+    from test_oracle_golden import GOLDEN, grid_units
+    gd = json.load(open(GOLDEN))
+    _, n, pml, w, mu = grid_units(gd)
+    cg, ce = np.sqrt(gd["initial_state"]["cg_squared"]), gd["initial_state"]["ce"]
+    mols = W.pack_molecules([W.tls((n / 2, n / 2, 0.5), w, mu, axis=2, sigma=1.0, gamma=1.0, cg=cg, ce=ce)
+                             for _ in range(4)])
+    prob = W.Problem(n, n, 1, 0.5, periodic=(False, False, True), pml=(pml, pml, pml, pml, 0, 0), molecules=mols)
+    g, o = run_pair(ml, oracle_mod, prob, 200, precision)
+    try:
+        for got, want in zip(g.fields(), o.fields()):
+            assert rel(got, want) < tol
+        r_g = [g.rho(m) for m in range(4)]
+        r_o = [o.rho(m) for m in range(4)]
+        assert crel(np.array([r[0, 1] for r in r_g]), np.array([r[0, 1] for r in r_o])) < tol
+        pe_o = np.array([r[1, 1].real for r in r_o])
+        assert pe_o.max() < 0.5e-4  # decayed from 1e-4
+        assert rel([r[1, 1].real for r in r_g], pe_o) < tol
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_coupled_all_features(ml, oracle_mod, precision, tol, seed):
     """eps map + design box + source sheet + flux planes + two-level and multilevel

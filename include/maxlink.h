@@ -172,7 +172,9 @@ const char *ml_last_error(void);
 
 /* Version string of the library build.  0.2: ml_material carries up to ML_MAX_POLES
  * dispersive poles (omega0, n_extra, extra[]) and ml_grid_desc ends with zchunk; a
- * caller built against 0.1 descriptors must be rebuilt. */
+ * caller built against 0.1 descriptors must be rebuilt.  0.3 adds entry points only
+ * (ml_set_allocator, ml_set_wait_limit, ml_batch_set_timing / ml_batch_timing,
+ * ml_gather_static); 0.2 callers need no change. */
 const char *ml_version(void);
 
 /* Create a grid (Eq. Maxwell on a Yee lattice, Eq. Dromega per cell), zero fields.

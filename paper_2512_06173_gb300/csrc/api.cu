@@ -105,7 +105,7 @@ const char *ml_last_error(void) { return g_err.c_str(); }
 // Lets entry points defined in other files report through ml_last_error.
 void ml::set_last_error(const std::string &msg) { g_err = msg; }
 
-const char *ml_version(void) { return "maxlink-gb300 0.2 (sm_103a)"; }
+const char *ml_version(void) { return "maxlink-gb300 0.3 (sm_103a)"; }
 
 ml_status ml_grid_destroy(ml_grid *g) {
     if (!g) return fail(ML_ERR_INVALID_ARG, "null grid");

@@ -1,7 +1,8 @@
 """Single-mode cavity (ml_cavity_*) through the C ABI against the oracle's cavity
 (oracle/cavity.py) on the same seeded molecules: the mode state (q, p, d of both
 polarisations) after every step and the final density matrices.  FP64 agrees to
-round-off (relative 1e-10), FP32 within 1e-4.  Also at 3,000 two-level emitters (the
+round-off (relative 1e-10 on the mode, 1e-9 on the density matrices), FP32 within
+1e-4 (measured: 3.5e-6 on the mode, 1.8e-6 on the density matrices).  Also at 3,000 two-level emitters (the
 two-level path and the multi-block dipole sum), the sqrt(N) identity on the GPU, and
 refusal of bad descriptors.
 """
@@ -63,8 +64,8 @@ def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
-def test_matches_oracle_every_step(ml, cav, precision, tol):
+@pytest.mark.parametrize("precision,tol,rho_tol", [(1, 1e-10, 1e-9), (0, 1e-4, 1e-4)])
+def test_matches_oracle_every_step(ml, cav, precision, tol, rho_tol):
     mols = mixed(0, 12)
     kw = dict(omega_c=0.25, coupling=0.01, dt=0.5, q0=(0.3, -0.2), p0=(0.0, 0.1))
     o = cav.OracleCavity(mols, **kw)
@@ -76,7 +77,7 @@ def test_matches_oracle_every_step(ml, cav, precision, tol):
             o.step(1)
             assert rel(g.mode(), o.mode()) < tol
         for m in range(mols.count):
-            assert rel(g.rho(m), o.rho(m)) < 10 * tol
+            assert rel(g.rho(m), o.rho(m)) < rho_tol  # FP32 measured: 1.8e-6
         assert g.nstep == 150
     finally:
         g.close()

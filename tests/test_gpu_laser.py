@@ -1,7 +1,7 @@
 """Laser-driven molecules (ml_drive_*) through the C ABI against the oracle's
 classical-path drive (oracle/laser.py) on the same seeded molecules at seeded z:
-populations every step and final density matrices; FP64 to round-off (1e-10), FP32
-within 1e-4.  Also: graph replay equals single steps bit for bit, and bad descriptors
+populations every step and final density matrices; FP64 to round-off (1e-10 on the
+populations, 1e-9 on the density matrices), FP32 within 1e-4 (measured: 6e-6).  Also: graph replay equals single steps bit for bit, and bad descriptors
 are refused.
 """
 import numpy as np
@@ -61,8 +61,8 @@ PULSE = dict(amplitude=0.03, omega=0.25, phase=0.3, center=-40.0, half_width=40.
 
 
 @pytest.mark.parametrize("two_level_only", [False, True])
-@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
-def test_matches_oracle_every_step(ml, las, precision, tol, two_level_only):
+@pytest.mark.parametrize("precision,tol,rho_tol", [(1, 1e-10, 1e-9), (0, 1e-4, 1e-4)])
+def test_matches_oracle_every_step(ml, las, precision, tol, rho_tol, two_level_only):
     mols = ensemble(3, 24, two_level_only)
     o = las.OracleLaser(mols, **PULSE)
     g = ml.Drive(mols, precision=precision, **PULSE)
@@ -75,7 +75,7 @@ def test_matches_oracle_every_step(ml, las, precision, tol, two_level_only):
             assert np.abs(pg - po).max() < tol
         assert np.abs(o.populations()[:, 1]).max() > 1e-3  # the pulse did excite
         for m in range(mols.count):
-            assert np.abs(g.rho(m) - o.rho(m)).max() < 10 * tol
+            assert np.abs(g.rho(m) - o.rho(m)).max() < rho_tol  # FP32 measured: 5e-6
     finally:
         g.close()
 

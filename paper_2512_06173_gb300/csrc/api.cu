@@ -883,6 +883,16 @@ void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y) {
     }
 }
 
+// Arguments of the periodic-image refresh of the six field arrays of level `lev`.
+template <typename T>
+ImgArgs<T> image_args(const ml_grid *g, int lev) {
+    ImgArgs<T> a{};
+    for (int c = 0; c < 6; c++) a.f[c] = (T *)g->F[lev][c];
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.px = g->px; a.plane = g->plane;
+    for (int q = 0; q < 3; q++) a.per[q] = g->per[q];
+    return a;
+}
+
 template <typename T>
 ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
     for (long long it = 0; it < nsteps; it++) {
@@ -943,6 +953,11 @@ ml_status step_impl(ml_grid *g, long long nsteps, cudaStream_t s) {
             LaunchScope ls(g, s, 1);
             CK(launch_yee<T>(y, g->tm[cur], g->nblocks, s, g->nmol > 0 && g->pdl));
         }
+        if (g->per[0] | g->per[1] | g->per[2]) {
+            // periodic images of the level just written, before anything reads its ghosts
+            LaunchScope ls(g, s, 1);
+            CK(launch_images<T>(image_args<T>(g, nxt), s));
+        }
         if (!g->planes.empty()) {
             g->nsamp++;
             if (g->nsamp == DFT_KMAX) {
@@ -964,7 +979,8 @@ template ml_status step_impl<double>(ml_grid *, long long, cudaStream_t);
     template void fill_mol_args<T>(ml_grid *, int, MolArgs<T> &);     \
     template void fill_gath_args<T>(ml_grid *, int, GathArgs<T> &);   \
     template void fill_cur_args<T>(ml_grid *, CurArgs<T> &);          \
-    template void fill_yee_args<T>(ml_grid *, int, YeeArgs<T> &);
+    template void fill_yee_args<T>(ml_grid *, int, YeeArgs<T> &);                                               \
+    template ImgArgs<T> image_args<T>(const ml_grid *, int);
 ML_FILL(float)
 ML_FILL(double)
 

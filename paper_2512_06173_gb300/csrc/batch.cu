@@ -213,6 +213,14 @@ ml_status enqueue(ml_batch *b, int s0, int count, bool fold_tail, cudaStream_t s
             YeeBatch<T> yb{(const YeeArgs<T> *)b->d_yargs, b->d_maps, b->d_lev0, b->d_ywork, nyw, b->d_boff, st,
                            st % DFT_KMAX, b->bodies};
             CK(launch_yee_batch<T>(yb, grid, s, b->pdl && nmw > 0));
+            // periodic images of the level each periodic instance just wrote
+            for (size_t i = 0; i < b->g.size(); i++) {
+                const ml_grid *gi = b->g[i];
+                if (!(gi->per[0] | gi->per[1] | gi->per[2])) continue;
+                const int wrote = 1 - ((b->h_lev0[i] + st) & 1);
+                CK(launch_images<T>(image_args<T>(gi, wrote), s));
+                b->launches++;
+            }
         }
         b->launches++;
         const bool period_end = st % DFT_KMAX == DFT_KMAX - 1;
@@ -247,6 +255,13 @@ ml_status batch_step(ml_batch *b, long long nsteps, cudaStream_t s) {
                                   (long long)(uintptr_t)b->d_lev0, (long long)(uintptr_t)b->d_ywork,
                                   (long long)(uintptr_t)b->d_gwork, (long long)(uintptr_t)b->d_mwork,
                                   (long long)(uintptr_t)b->d_fwork};
+    // the periodic-image launches bake in the level each periodic instance writes
+    long long nper = 0;
+    for (size_t i = 0; i < b->g.size(); i++)
+        if (b->g[i]->per[0] | b->g[i]->per[1] | b->g[i]->per[2]) {
+            nper++;
+            sig.push_back(((long long)i << 1) | (b->h_lev0[i] & 1));
+        }
     const long long reps = (b->use_graph && !b->timing) ? nsteps / SEQ : 0;
     if (reps > 0) {
         if (b->exec && sig != b->sig) drop_graph(b);
@@ -270,7 +285,7 @@ ml_status batch_step(ml_batch *b, long long nsteps, cudaStream_t s) {
             CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
             b->sig = sig;
         }
-        const long long per = (long long)(b->h_mwork.size() ? 2 : 0) + 1;
+        const long long per = (long long)(b->h_mwork.size() ? 2 : 0) + 1 + nper;
         for (long long r = 0; r < reps; r++) {
             CK(cudaGraphLaunch(b->exec, s));
             b->launches += SEQ * per + (b->h_fwork.empty() ? 0 : SEQ / DFT_KMAX) + 1;

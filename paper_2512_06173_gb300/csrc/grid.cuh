@@ -179,6 +179,7 @@ template <typename T> void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m);
 template <typename T> void fill_gath_args(ml_grid *g, int cur, GathArgs<T> &ga);
 template <typename T> void fill_cur_args(ml_grid *g, CurArgs<T> &ca);
 template <typename T> void fill_yee_args(ml_grid *g, int cur, YeeArgs<T> &y);
+template <typename T> ImgArgs<T> image_args(const ml_grid *g, int lev);
 
 // Fold the pending plane samples into the FP64 DFT accumulators.
 template <typename T>

@@ -316,6 +316,17 @@ cudaError_t launch_tick(long long *c, int add, cudaStream_t s);
 // the molecular current may start while the current kernel still runs.
 template <typename T> cudaError_t launch_yee(const YeeArgs<T> &a, const TmapSet &maps, int nblocks, cudaStream_t s,
                                              bool pdl = false);
+// Periodic ghost images of the six field arrays of one time level: every ghost cell on
+// a face of a periodic axis takes the value of its image inside the grid (wall ghosts
+// stay 0).  Run after each field pass of a grid with a periodic axis.
+template <typename T>
+struct ImgArgs {
+    T *f[6];
+    int nx, ny, nz, px;
+    long long plane;
+    int per[3];
+};
+template <typename T> cudaError_t launch_images(const ImgArgs<T> &a, cudaStream_t s);
 // the field-pass body of every tile (0..4, see block_mode in yee.cu), one byte per tile
 template <typename T> cudaError_t launch_tile_modes(const YeeArgs<T> &a, int ntiles, uint8_t *out, cudaStream_t s);
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);

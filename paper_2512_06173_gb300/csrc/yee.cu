@@ -41,32 +41,6 @@ __device__ __forceinline__ int slab(int p, int n, int lo, int hi) {
     return -1;
 }
 
-// Write v at (i,j,k) and at every periodic ghost image of that cell.
-template <typename T>
-__device__ __forceinline__ void store_img(const YeeArgs<T> &a, T *f, int i, int j, int k, T v) {
-    f[gi(a, i, j, k)] = v;
-    const bool bx = a.per[0] && (i == 0 || i == a.nx - 1);
-    const bool by = a.per[1] && (j == 0 || j == a.ny - 1);
-    const bool bz = a.per[2] && (k == 0 || k == a.nz - 1);
-    if (!(bx | by | bz)) return;
-    // candidate coordinates per axis: the cell itself, its image at n (if at 0),
-    // its image at -1 (if at n-1); a value of INT_MIN marks "no such image"
-    const int NONE = -0x40000000;
-    for (int c = 0; c < 3; c++) {
-        const int kk = c == 0 ? k : (c == 1 ? (bz && k == 0 ? a.nz : NONE) : (bz && k == a.nz - 1 ? -1 : NONE));
-        if (kk == NONE) continue;
-        for (int b = 0; b < 3; b++) {
-            const int jj = b == 0 ? j : (b == 1 ? (by && j == 0 ? a.ny : NONE) : (by && j == a.ny - 1 ? -1 : NONE));
-            if (jj == NONE) continue;
-            for (int q = 0; q < 3; q++) {
-                const int ii = q == 0 ? i : (q == 1 ? (bx && i == 0 ? a.nx : NONE) : (bx && i == a.nx - 1 ? -1 : NONE));
-                if (ii == NONE || (q | b | c) == 0) continue;
-                f[gi(a, ii, jj, kk)] = v;
-            }
-        }
-    }
-}
-
 // Curl differences of E^n around H cell o (Eq. Maxwell b): Ek / Ek1 point at Ex of the
 // staged planes k / k+1 (components BP apart), o = row * BOXW + col.
 // d = {dEz/dy, dEy/dz, dEx/dz, dEz/dx, dEy/dx, dEx/dy}.
@@ -107,14 +81,15 @@ __device__ __forceinline__ T src_value(const SrcDev &q, double t) {
 constexpr uint32_t WAIT_LIMIT = 2000;  // probes of up to 1 ms each before giving up
 
 // Body of the field pass for one block.  MODE 0 is the interior form: the caller
-// guarantees the tile and its halo touch no CPML layer, wall, periodic image or
-// material/source cell, so none of those paths is compiled in.  MODE 1 adds the CPML
-// layers and the index-0 walls; MODE 4 adds to those the source sheets and the per-cell
-// coefficient dt/eps of a material index (from a shared-memory table); MODE 3 is the
-// interior form with the source sheets and the material table, for tiles clear of the
-// layers and walls; MODE 2 has every path (dispersive poles, design box, periodic
-// images).  The CPML body is kept without the tables: their registers cost the vacuum
-// layers' tiles time even where the tables are never read.
+// guarantees the tile and its halo touch no CPML layer, wall or material/source cell,
+// so none of those paths is compiled in.  MODE 1 adds the CPML layers and the index-0
+// walls; MODE 4 adds to those the source sheets and the per-cell coefficient dt/eps of a
+// material index (from a shared-memory table); MODE 3 is the interior form with the
+// source sheets and the material table, for tiles clear of the layers and walls; MODE 2
+// has every path (dispersive poles, design box).  The CPML body is kept without the
+// tables: their registers cost the vacuum layers' tiles time even where the tables are
+// never read.  No body writes periodic ghost images: every body stores its own cells
+// only, and image_kernel copies the images after the pass.
 // Returns false when a plane wait gave up (the block then reported ML_ERR_TIMEOUT and
 // drained its copies); uniform over the block.
 template <typename T, int MODE>
@@ -157,13 +132,12 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
     // bytes a stage receives: three E boxes of BOXH rows and three H boxes of BOXHH rows
     constexpr uint32_t STAGE_BYTES = 3u * BOXW * (BOXH + BOXHH) * sizeof(T);
 
-    // block-uniform features: CPML layers this tile (with its halo) can touch,
-    // periodic ghost images to write, per-cell material work, molecular current
+    // block-uniform features: CPML layers this tile (with its halo) can touch, per-cell
+    // material work, molecular current (periodic ghost images are written after the pass
+    // by image_kernel)
     const bool fx = GEN && (a.pml[0] | a.pml[1]) && (x0 - 1 < a.pml[0] || x0 + TX > a.nx - a.pml[1]);
     const bool fy = GEN && (a.pml[2] | a.pml[3]) && (y0 - 1 < a.pml[2] || y0 + TY > a.ny - a.pml[3]);
     const bool zl = GEN && (a.pml[4] | a.pml[5]) != 0;
-    const bool img = FULL && ((a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
-                             (a.per[2] && (k0 == 0 || k1 == a.nz)));
     const bool walls = GEN && ((!a.per[0] && x0 == 0) || (!a.per[1] && y0 == 0) || (!a.per[2] && k0 == 0));
     // per-cell material work (material table, design box, poles, sources): only tiles
     // whose own cells need it, when the grid has the per-tile flags
@@ -435,19 +409,13 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                 sH[1][sr][tx + 1] = hy[r];
                 sH[2][sr][tx + 1] = hz[r];
                 if (own) {
-                    if (img) {
-                        store_img(a, a.Hn[0], i, j, k, hx[r]);
-                        store_img(a, a.Hn[1], i, j, k, hy[r]);
-                        store_img(a, a.Hn[2], i, j, k, hz[r]);
-                    } else {
-                        // the new level is not read again in this pass: streaming
-                        // (evict-first) stores leave L2 to the planes that neighbouring
-                        // tiles still read as halos
-                        const long long g = pb + gb + r * a.px;
-                        __stcs(&a.Hn[0][g], hx[r]);
-                        __stcs(&a.Hn[1][g], hy[r]);
-                        __stcs(&a.Hn[2][g], hz[r]);
-                    }
+                    // the new level is not read again in this pass: streaming
+                    // (evict-first) stores leave L2 to the planes that neighbouring
+                    // tiles still read as halos
+                    const long long g = pb + gb + r * a.px;
+                    __stcs(&a.Hn[0][g], hx[r]);
+                    __stcs(&a.Hn[1][g], hy[r]);
+                    __stcs(&a.Hn[2][g], hz[r]);
                 }
             }
             // ---- H^{n+1/2}(k): low halo row (y0-1) and column (x0-1), recomputed
@@ -587,11 +555,7 @@ __device__ __forceinline__ bool yee_body(const YeeArgs<T> &a, const TmapSet &map
                     if (wx || wz) en1 = T(0);
                     if (wx || wy) en2 = T(0);
                 }
-                if (img) {
-                    store_img(a, a.En[0], i, j, k, en0);
-                    store_img(a, a.En[1], i, j, k, en1);
-                    store_img(a, a.En[2], i, j, k, en2);
-                } else {
+                {
                     const long long g = pb + gb + r * a.px;
                     __stcs(&a.En[0][g], en0);
                     __stcs(&a.En[1][g], en1);
@@ -680,23 +644,26 @@ __device__ __forceinline__ int tile_flags(const YeeArgs<T> &a, const int tile) {
     return a.tflags ? (int)a.tflags[tile] : ((a.mat || a.dcb || a.JD || a.nsrc) ? 1 : 0);
 }
 
-// True when the block's tile (with its one-cell halo) touches none of the CPML layers,
-// walls and periodic images of the field pass (the molecular current and flux-plane
-// sampling are block-uniform branches of every body).
+// True when the block's tile (with its one-cell halo) touches none of the CPML layers
+// and walls of the field pass (the molecular current and flux-plane sampling are
+// block-uniform branches of every body).  The edge of a periodic axis is interior: its
+// ghost cells hold the images, written after each pass.
 template <typename T>
 __device__ __forceinline__ bool interior_geometry(const YeeArgs<T> &a, const int tile) {
     const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
     const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
-    if (x0 == 0 || y0 == 0 || k0 == 0 || x0 + TX >= a.nx || y0 + TY >= a.ny || k1 >= a.nz) return false;
+    if ((!a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (!a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
+        (!a.per[2] && (k0 == 0 || k1 >= a.nz)))
+        return false;
     if ((a.pml[0] && x0 - 1 < a.pml[0]) || (a.pml[1] && x0 + TX > a.nx - a.pml[1])) return false;
     if ((a.pml[2] && y0 - 1 < a.pml[2]) || (a.pml[3] && y0 + TY > a.ny - a.pml[3])) return false;
     if ((a.pml[4] && k0 - 1 < a.pml[4]) || (a.pml[5] && k1 > a.nz - a.pml[5])) return false;
     return true;
 }
 
-// 0: interior body; 1: CPML and walls (no periodic image, pole or design box, material
-// or source sheet in the tile); 4: CPML and walls with a material map or source sheets;
-// 3: interior geometry with a material map or source sheets; 2: every path.
+// 0: interior body; 1: CPML and walls (no pole or design box, material or source sheet
+// in the tile); 4: CPML and walls with a material map or source sheets; 3: interior
+// geometry with a material map or source sheets; 2: every path (poles, design box).
 template <typename T>
 __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
     const int fl = tile_flags(a, tile);
@@ -705,11 +672,7 @@ __device__ __forceinline__ int block_mode(const YeeArgs<T> &a, const int tile) {
         if ((fl & 1) == 0) return 3;
         return 2;
     }
-    const int bx = tile % a.ntx, by = (tile / a.ntx) % a.nty, bz = tile / (a.ntx * a.nty);
-    const int x0 = bx * TX, y0 = by * TY, k0 = a.zcut[bz], k1 = a.zcut[bz + 1];
-    const bool img = (a.per[0] && (x0 == 0 || x0 + TX >= a.nx)) || (a.per[1] && (y0 == 0 || y0 + TY >= a.ny)) ||
-                     (a.per[2] && (k0 == 0 || k1 == a.nz));
-    return (img || (fl & 1) != 0) ? 2 : (fl != 0 ? 4 : 1);
+    return (fl & 1) != 0 ? 2 : (fl != 0 ? 4 : 1);
 }
 
 // Body of a tile in a kernel compiled with body set B.  The host picks the set from the
@@ -915,6 +878,60 @@ cudaError_t launch_refresh_ghosts(T *f, int nx, int ny, int nz, int px, long lon
     return cudaGetLastError();
 }
 
+// Periodic images after a field pass: one thread per ghost cell on the faces of the
+// periodic axes (a cell on two faces is written twice, with the same value).  The cell
+// takes the value of its image inside the grid, found by wrapping each coordinate; a
+// ghost that lies outside along a wall axis stays 0.  Reading only interior cells makes
+// the order of the writes irrelevant.
+template <typename T>
+__global__ void image_kernel(const ImgArgs<T> a) {
+    const long long X = a.nx + 2, Y = a.ny + 2, Z = a.nz + 2;
+    const long long fx = a.per[0] ? 2 * Y * Z : 0, fy = a.per[1] ? 2 * X * Z : 0, fz = a.per[2] ? 2 * X * Y : 0;
+    const long long n = fx + fy + fz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (t < fx) {
+            const long long r = t % (Y * Z);
+            j = (int)(r % Y) - 1;
+            k = (int)(r / Y) - 1;
+            i = t >= Y * Z ? a.nx : -1;
+        } else if (t < fx + fy) {
+            const long long u = t - fx, r = u % (X * Z);
+            i = (int)(r % X) - 1;
+            k = (int)(r / X) - 1;
+            j = u >= X * Z ? a.ny : -1;
+        } else {
+            const long long u = t - fx - fy, r = u % (X * Y);
+            i = (int)(r % X) - 1;
+            j = (int)(r / X) - 1;
+            k = u >= X * Y ? a.nz : -1;
+        }
+        const bool ox = i < 0 || i >= a.nx, oy = j < 0 || j >= a.ny, oz = k < 0 || k >= a.nz;
+        if ((ox && !a.per[0]) || (oy && !a.per[1]) || (oz && !a.per[2])) continue;
+        const int si = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
+        const int sj = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
+        const int sk = k < 0 ? k + a.nz : (k >= a.nz ? k - a.nz : k);
+        const long long dst = (long long)(k + 1) * a.plane + (long long)(j + 1) * a.px + (i + XO);
+        const long long src = (long long)(sk + 1) * a.plane + (long long)(sj + 1) * a.px + (si + XO);
+        T v[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) v[c] = a.f[c][src];
+#pragma unroll
+        for (int c = 0; c < 6; c++) a.f[c][dst] = v[c];
+    }
+}
+
+template <typename T>
+cudaError_t launch_images(const ImgArgs<T> &a, cudaStream_t s) {
+    const long long X = a.nx + 2, Y = a.ny + 2, Z = a.nz + 2;
+    const long long n = (a.per[0] ? 2 * Y * Z : 0) + (a.per[1] ? 2 * X * Z : 0) + (a.per[2] ? 2 * X * Y : 0);
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    image_kernel<T><<<(int)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // Zero tangential E on the index-0 walls of non-periodic axes.
 template <typename T>
 __global__ void pec_kernel(T *ex, T *ey, T *ez, int nx, int ny, int nz, int px, long long plane, int p0, int p1,
@@ -960,6 +977,7 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
     template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t, bool);                         \
     template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t, bool);                                  \
     template cudaError_t launch_tile_modes<T>(const YeeArgs<T> &, int, uint8_t *, cudaStream_t);                              \
+    template cudaError_t launch_images<T>(const ImgArgs<T> &, cudaStream_t);                                                 \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \
     template cudaError_t launch_zero_pec<T>(T *const *, int, int, int, int, long long, const int *, cudaStream_t);

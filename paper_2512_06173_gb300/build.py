@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmaxlink.so")
 SOURCES = ["api.cu", "yee.cu", "molecules.cu", "dft.cu", "current.cu", "adjoint.cu", "batch.cu", "static_gather.cu",
-           "cavity.cu", "devmem.cu"]
+           "cavity.cu", "devmem.cu", "images.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

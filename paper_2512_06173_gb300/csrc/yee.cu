@@ -878,60 +878,6 @@ cudaError_t launch_refresh_ghosts(T *f, int nx, int ny, int nz, int px, long lon
     return cudaGetLastError();
 }
 
-// Periodic images after a field pass: one thread per ghost cell on the faces of the
-// periodic axes (a cell on two faces is written twice, with the same value).  The cell
-// takes the value of its image inside the grid, found by wrapping each coordinate; a
-// ghost that lies outside along a wall axis stays 0.  Reading only interior cells makes
-// the order of the writes irrelevant.
-template <typename T>
-__global__ void image_kernel(const ImgArgs<T> a) {
-    const long long X = a.nx + 2, Y = a.ny + 2, Z = a.nz + 2;
-    const long long fx = a.per[0] ? 2 * Y * Z : 0, fy = a.per[1] ? 2 * X * Z : 0, fz = a.per[2] ? 2 * X * Y : 0;
-    const long long n = fx + fy + fz;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        if (t < fx) {
-            const long long r = t % (Y * Z);
-            j = (int)(r % Y) - 1;
-            k = (int)(r / Y) - 1;
-            i = t >= Y * Z ? a.nx : -1;
-        } else if (t < fx + fy) {
-            const long long u = t - fx, r = u % (X * Z);
-            i = (int)(r % X) - 1;
-            k = (int)(r / X) - 1;
-            j = u >= X * Z ? a.ny : -1;
-        } else {
-            const long long u = t - fx - fy, r = u % (X * Y);
-            i = (int)(r % X) - 1;
-            j = (int)(r / X) - 1;
-            k = u >= X * Y ? a.nz : -1;
-        }
-        const bool ox = i < 0 || i >= a.nx, oy = j < 0 || j >= a.ny, oz = k < 0 || k >= a.nz;
-        if ((ox && !a.per[0]) || (oy && !a.per[1]) || (oz && !a.per[2])) continue;
-        const int si = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
-        const int sj = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
-        const int sk = k < 0 ? k + a.nz : (k >= a.nz ? k - a.nz : k);
-        const long long dst = (long long)(k + 1) * a.plane + (long long)(j + 1) * a.px + (i + XO);
-        const long long src = (long long)(sk + 1) * a.plane + (long long)(sj + 1) * a.px + (si + XO);
-        T v[6];
-#pragma unroll
-        for (int c = 0; c < 6; c++) v[c] = a.f[c][src];
-#pragma unroll
-        for (int c = 0; c < 6; c++) a.f[c][dst] = v[c];
-    }
-}
-
-template <typename T>
-cudaError_t launch_images(const ImgArgs<T> &a, cudaStream_t s) {
-    const long long X = a.nx + 2, Y = a.ny + 2, Z = a.nz + 2;
-    const long long n = (a.per[0] ? 2 * Y * Z : 0) + (a.per[1] ? 2 * X * Z : 0) + (a.per[2] ? 2 * X * Y : 0);
-    if (n == 0) return cudaSuccess;
-    long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    image_kernel<T><<<(int)blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 // Zero tangential E on the index-0 walls of non-periodic axes.
 template <typename T>
 __global__ void pec_kernel(T *ex, T *ey, T *ez, int nx, int ny, int nz, int px, long long plane, int p0, int p1,
@@ -977,7 +923,6 @@ cudaError_t launch_sum_doubles(const double *src, int n, double *dst, cudaStream
     template cudaError_t launch_yee<T>(const YeeArgs<T> &, const TmapSet &, int, cudaStream_t, bool);                         \
     template cudaError_t launch_yee_batch<T>(const YeeBatch<T> &, int, cudaStream_t, bool);                                  \
     template cudaError_t launch_tile_modes<T>(const YeeArgs<T> &, int, uint8_t *, cudaStream_t);                              \
-    template cudaError_t launch_images<T>(const ImgArgs<T> &, cudaStream_t);                                                 \
     template cudaError_t launch_pack_fields<T>(const T *, T *, int, int, int, int, long long, int, cudaStream_t); \
     template cudaError_t launch_refresh_ghosts<T>(T *, int, int, int, int, long long, const int *, cudaStream_t); \
     template cudaError_t launch_zero_pec<T>(T *const *, int, int, int, int, long long, const int *, cudaStream_t);

@@ -74,8 +74,9 @@ def test_vacuum_cpml_fields(ml, oracle_mod, precision, tol, shape):
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL64), (0, TOL32)])
 @pytest.mark.parametrize("per", [(True, True, True), (True, False, True), (False, True, False)])
-def test_periodic_and_walls(ml, oracle_mod, precision, tol, per):
-    nx, ny, nz = 33, 10, 12
+@pytest.mark.parametrize("shape", [(33, 10, 12), (64, 24, 12)])  # nx % 8 == 0: sector-wide x images
+def test_periodic_and_walls(ml, oracle_mod, precision, tol, per, shape):
+    nx, ny, nz = shape
     pml = tuple(0 if per[a // 2] else 3 for a in range(6))
     prob = W.Problem(nx, ny, nz, 0.5, periodic=per, pml=pml)
     f = W.random_fields(prob, 8)

@@ -64,8 +64,8 @@ def config_of(prob, world: int) -> dict:
 # the named workload; valid only for the source it was measured on, identified by the
 # sha256 prefix of yee.cu.
 FIELD_PASS_TRAFFIC = {
-    ("bragg-512x512x384-100000ml", "79a53f0c99f39ec0"): 6.2219e9,
-    ("superradiant-slab-256^3-10000tls", "79a53f0c99f39ec0"): 1.0408e9,
+    ("bragg-512x512x384-100000ml", "6053a25796039c2f"): 6.2251e9,
+    ("superradiant-slab-256^3-10000tls", "6053a25796039c2f"): 1.0410e9,
 }
 
 

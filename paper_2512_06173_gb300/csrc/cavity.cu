@@ -32,7 +32,7 @@ static_assert(CAV_NB <= CAV_NT, "the last block loads one partial per thread");
 
 template <typename T>
 __global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, long long M, double *part, unsigned *ticket,
-                                                             double *mode, double wc, double eps, double dt) {
+                                                             double *mode, float *euf, double wc, double eps, double dt) {
     __shared__ double red[3][CAV_NT];
     __shared__ bool last;
     const int tid = threadIdx.x;
@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, long 
         mode[6 + l] = -(eps * qn + eps * eps / (wc * wc) * d[l]);
     }
     mode[8] = 0.0;
+    if (euf)  // FP32 molecules read the field in their own type
+        for (int l = 0; l < 3; l++) euf[l] = (float)mode[6 + l];
     *ticket = 0u;  // ready for the next launch
 }
 
@@ -87,6 +89,7 @@ struct ml_cavity {
     long long pool = 0;
     double dt = 0.0, wc = 0.0, eps = 0.0;
     bool two_level = true;
+    bool exact_only = true;  // every molecule is kind 0 (the exact 2x2 step)
     long long step = 0;
     int *d_nlev = nullptr, *d_kind = nullptr, *d_nsub = nullptr, *d_cmask = nullptr, *d_status = nullptr;
     long long *d_off = nullptr;
@@ -94,6 +97,7 @@ struct ml_cavity {
          *d_rho = nullptr, *d_Et = nullptr, *d_mudot = nullptr, *d_c = nullptr, *d_gmu = nullptr;
     double *d_energy = nullptr, *d_mode = nullptr, *d_part = nullptr, *d_export = nullptr;
     double *d_bpart = nullptr;  // two-level molecules: per-block dipole sums of the molecule kernel
+    float *d_euf = nullptr;     // FP32 molecules: the mode's field Eu in FP32
     unsigned *d_ticket = nullptr;
     std::vector<ml::DevBuf> allocs;
     // CAV_SEQ steps captured once into a graph (the arguments never change) and replayed
@@ -135,7 +139,8 @@ void fill_cavity_args(ml_cavity *c, MolArgs<T> &m) {
     m.Et = (T *)c->d_Et; m.mudot = (T *)c->d_mudot; m.c = (T *)c->d_c;
     m.energy = c->d_energy; m.status = c->d_status;
     m.two_level = c->two_level ? 1 : 0;
-    m.Eu = c->d_mode ? c->d_mode + 6 : nullptr;
+    m.exact_only = c->exact_only ? 1 : 0;
+    m.Eu = (const T *)(const void *)(sizeof(T) == 8 ? (c->d_mode ? c->d_mode + 6 : nullptr) : (const void *)c->d_euf);
     m.gmu = (T *)c->d_gmu;
     m.dpart = c->d_bpart;
 }
@@ -150,10 +155,10 @@ ml_status enqueue_steps(ml_cavity *c, long long nsteps, cudaStream_t s) {
         // two-level molecules leave per-block sums; others gamma <mu> per molecule
         if (c->two_level)
             cavity_mode_kernel<double><<<CAV_NB, CAV_NT, 0, s>>>(c->d_bpart, nb, c->d_part, c->d_ticket, c->d_mode,
-                                                                  c->wc, c->eps, c->dt);
+                                                                  c->d_euf, c->wc, c->eps, c->dt);
         else
             cavity_mode_kernel<T><<<CAV_NB, CAV_NT, 0, s>>>((const T *)c->d_gmu, c->M, c->d_part, c->d_ticket,
-                                                             c->d_mode, c->wc, c->eps, c->dt);
+                                                             c->d_mode, c->d_euf, c->wc, c->eps, c->dt);
         CK(cudaGetLastError());
     }
     return ML_OK;
@@ -250,7 +255,11 @@ ml_status load_ensemble(ml_cavity *c, const ml_molecule_desc *md, double (&d0)[2
     c->M = M;
     c->pool = pool;
     c->two_level = true;
-    for (int m = 0; m < M; m++) c->two_level = c->two_level && nlev[m] == 2;
+    c->exact_only = true;
+    for (int m = 0; m < M; m++) {
+        c->two_level = c->two_level && nlev[m] == 2;
+        c->exact_only = c->exact_only && kind[m] == 0;
+    }
     ml_status st;
 #define CAV(x)                \
     do {                      \
@@ -310,6 +319,7 @@ ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *md, 
             mode[6 + l] = -(c->eps * d->q0[l] + c->eps * c->eps / (c->wc * c->wc) * d0[l]);
         }
         st = cav_upload(c, &c->d_mode, mode);
+        if (st == ML_OK && !c->prec) st = cav_upload(c, &c->d_euf, std::vector<float>(mode.begin() + 6, mode.end()));
     }
     if (st != ML_OK) {
         ml_cavity_destroy(c);
@@ -380,7 +390,9 @@ int64_t ml_cavity_step_count(const ml_cavity *c) { return c ? c->step : -1; }
 struct ml_drive {
     ml_cavity *c = nullptr;
     double E0 = 0.0, k = 0.0, phase = 0.0, xi0 = 0.0, W = 0.0, pol[3] = {0.0, 0.0, 0.0}, dt = 0.0;
-    double *d_z = nullptr;
+    double *d_z = nullptr;        // FP64 molecules: z_m
+    float2 *d_zr = nullptr;       // FP32 molecules: z_m - xi0 as a float pair
+    float2 *d_tt = nullptr;       // FP32 molecules: t of each launch of the next run as a float pair
     long long *d_base = nullptr;
     long long step = 0;
     cudaStream_t cap = nullptr;
@@ -389,6 +401,21 @@ struct ml_drive {
 };
 
 namespace {
+
+// a double as a float pair: hi = the nearest float, lo = the remainder rounded
+__host__ __device__ inline float2 split_pair(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// After a run of n launches: advance the run's first step and write, for each launch q
+// of the next run, t = (first step + q) dt as a float pair (FP64 here, once per run).
+__global__ void drive_tick_kernel(long long *base, int n, float2 *tt, double dt) {
+    const long long b = *base + n;
+    __syncthreads();  // every thread has read the old value
+    if (threadIdx.x == 0) *base = b;
+    tt[threadIdx.x] = split_pair((double)(b + threadIdx.x) * dt);
+}
 
 template <typename T>
 ml_status enqueue_drive(ml_drive *d, int nsteps, cudaStream_t s) {
@@ -401,16 +428,23 @@ ml_status enqueue_drive(ml_drive *d, int nsteps, cudaStream_t s) {
     m.lbase = d->d_base;
     m.ldt = d->dt;
     m.lxi0 = d->xi0;
-    m.lk = d->k;
-    m.lphase = d->phase;
-    m.lW = d->W;
-    m.lE0 = d->E0;
-    for (int c = 0; c < 3; c++) m.lpol[c] = d->pol[c];
+    m.lzr = d->d_zr;
+    m.ltt = d->d_tt;
+    m.lk = (T)d->k;
+    m.lphase = (T)d->phase;
+    m.lW = (T)d->W;
+    m.lE0 = (T)d->E0;
+    for (int c = 0; c < 3; c++) m.lpol[c] = (T)d->pol[c];
     for (int q = 0; q < nsteps; q++) {
         m.lstep = q;
         CK(launch_molecules_uniform<T>(m, s));
     }
-    CK(launch_tick(d->d_base, nsteps, s));
+    if (sizeof(T) == 8) {
+        CK(launch_tick(d->d_base, nsteps, s));
+    } else {
+        drive_tick_kernel<<<1, CAV_SEQ, 0, s>>>(d->d_base, nsteps, d->d_tt, d->dt);
+        CK(cudaGetLastError());
+    }
     return ML_OK;
 }
 
@@ -477,7 +511,14 @@ ml_status ml_drive_create(const ml_drive_desc *dd, const ml_molecule_desc *md, m
             z[m] = md->pos[3 * m + 2];
             if (!std::isfinite(z[m])) st = fail(ML_ERR_INVALID_ARG, "non-finite position");
         }
-        if (st == ML_OK) st = cav_upload(d->c, &d->d_z, z);
+        if (st == ML_OK && d->c->prec) st = cav_upload(d->c, &d->d_z, z);
+        if (st == ML_OK && !d->c->prec) {
+            std::vector<float2> zr(md->count), tt(CAV_SEQ);
+            for (int m = 0; m < md->count; m++) zr[m] = split_pair(z[m] - d->xi0);
+            for (int q = 0; q < CAV_SEQ; q++) tt[q] = split_pair((double)q * d->dt);
+            st = cav_upload(d->c, &d->d_zr, zr);
+            if (st == ML_OK) st = cav_upload(d->c, &d->d_tt, tt);
+        }
         if (st == ML_OK) st = cav_upload(d->c, &d->d_base, std::vector<long long>(1, 0));
     }
     if (st != ML_OK) {

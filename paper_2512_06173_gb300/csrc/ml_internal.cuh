@@ -206,19 +206,23 @@ struct MolArgs {
     const int *wf;         // per molecule: window length along x, y, z (8 bits each)
     const T *w;            // (M, NW) 1D kernel weights per axis and stagger
     int two_level;         // every molecule has two levels, at pool offset 4 m
+    int exact_only;        // (uniform-field solvers) every molecule takes the exact 2x2 step
     double *pop_sink;      // populations of the new state, device address of page-locked host memory
     long long pop_slot;    // row block of this step in the sink: (step mod ring) * nmol * MAXLEV
-    const double *Eu;      // uniform-field source: the field before gamma_m (3 values)
+    const T *Eu;           // uniform-field source: the field before gamma_m (3 values, field type)
     T *gmu;                // uniform-field source: gamma_m <mu> of the new state (M, 3)
     double *dpart;         // uniform-field source, two-level molecules: per-block sums of gamma_m <mu> (3 each)
     // uniform-field source with laser = 1: the prescribed plane wave of Eq. E_analytical
     // instead of Eu, E~_m = gamma_m E0 pol env(u) cos(k u + phase), u = z_m - xi0 - t,
-    // t = (*lbase + lstep) dt, env(u) = cos^2(pi u / 2W) for |u| < W
+    // t = (run's first step + lstep) dt, env(u) = cos^2(pi u / 2W) for |u| < W
     int laser;
-    const double *zpos;
-    const long long *lbase;
     int lstep;
-    double ldt, lxi0, lk, lphase, lW, lE0, lpol[3];
+    const double *zpos;     // FP64 fields: z_m
+    const long long *lbase; // FP64 fields: the run's first step
+    double ldt, lxi0;       // FP64 fields
+    const float2 *lzr;      // FP32 fields: z_m - xi0 as a float pair (hi, lo = the FP64 remainder)
+    const float2 *ltt;      // FP32 fields: t of each launch of the run as a float pair
+    T lk, lphase, lW, lE0, lpol[3];
     // packed form (grids with multilevel molecules): molecules sorted by (kind, level
     // count, substeps, window position) in `order`; item i covers order[x .. x+y) with
     // level count z and w = kind | nsub << 4, one item per warp

@@ -38,7 +38,8 @@ __device__ __forceinline__ long long fidx(int px, long long plane, int i, int j,
 
 constexpr int MOL_WARPS = 4;
 constexpr int MOL_MIN_BLOCKS = 6;
-constexpr int MU_MIN_BLOCKS = 3;  // FP32 thread-per-molecule kernel: resident blocks per SM  // FP32: resident blocks per SM the register budget is cut for
+constexpr int MU_MIN_BLOCKS = 3;        // FP32 thread-per-molecule kernel: resident blocks per SM the register budget is cut for
+constexpr int MU_MIN_BLOCKS_EXACT = 4;  // the same, every molecule on the exact 2x2 step
 
 template <typename T>
 struct MolShared {
@@ -163,23 +164,38 @@ __device__ __forceinline__ bool window_gather_vec(const MolArgs<float> &a, const
 }
 
 // The uniform-field source's field at molecule m before gamma_m: Eu, or the laser's
-// plane wave (u in FP64, then the carrier and envelope in the field type on |u| < W).
+// plane wave on |u| < W.  With FP64 fields u = (z_m - xi0) - t is FP64.  With FP32 fields
+// both z_m - xi0 and t arrive as float pairs (hi + lo, the pair rounded from FP64), and u
+// is their difference by Knuth's two-sum of the high parts plus the low parts: the same
+// u to about 2^-48 of |z_m - xi0| + |t|, without FP64 arithmetic, which GB300 issues at
+// a small fraction of the FP32 rate.
 template <typename T>
 __device__ __forceinline__ void uniform_field(const MolArgs<T> &a, const int m, T (&E)[3]) {
     if (!a.laser) {
 #pragma unroll
-        for (int c = 0; c < 3; c++) E[c] = (T)a.Eu[c];
+        for (int c = 0; c < 3; c++) E[c] = a.Eu[c];
         return;
     }
-    const double u = (a.zpos[m] - a.lxi0) - (double)(*a.lbase + a.lstep) * a.ldt;
+    T uf;
+    bool in;
+    if constexpr (sizeof(T) == 8) {
+        const double u = (a.zpos[m] - a.lxi0) - (double)(*a.lbase + a.lstep) * a.ldt;
+        in = fabs(u) < a.lW;
+        uf = u;
+    } else {
+        const float2 z = a.lzr[m], t = a.ltt[a.lstep];
+        const float s = z.x - t.x, v = s - z.x;
+        const float err = (z.x - (s - v)) + (-t.x - v);
+        uf = s + (err + (z.y - t.y));
+        in = fabsf(uf) < a.lW;
+    }
     T f = T(0);
-    if (fabs(u) < a.lW) {
-        const T uf = (T)u;
-        const T cw = cos(T(1.5707963267948966) * uf / (T)a.lW);
-        f = (T)a.lE0 * cw * cw * cos((T)a.lk * uf + (T)a.lphase);
+    if (in) {
+        const T cw = cos(T(1.5707963267948966) * uf / a.lW);
+        f = a.lE0 * cw * cw * cos(a.lk * uf + a.lphase);
     }
 #pragma unroll
-    for (int c = 0; c < 3; c++) E[c] = f * (T)a.lpol[c];
+    for (int c = 0; c < 3; c++) E[c] = f * a.lpol[c];
 }
 
 // GKSL right-hand side for element (j,l) of rho given in S (n x n), H in Hs.
@@ -827,8 +843,8 @@ __device__ __forceinline__ void st4(cx<T> *p, const cx<T> (&v)[4]) {
 constexpr int MU_THREADS = MU_THREADS_HOST;
 
 
-template <typename T>
-__device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const int m, double (&gm)[3]) {
+template <typename T, bool EXACT_ONLY>
+__device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const int m, T (&gm)[3]) {
     const long long o = 4ll * m;
     const int kind = a.kind[m];
     const T gam = a.gamma[m];
@@ -858,7 +874,7 @@ __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const i
         }
     }
     cx<T> r1[4];
-    if (kind == 0) {
+    if (EXACT_ONLY || kind == 0) {
         const T dt = a.dt;
         const T z = T(0.5) * (H[0].re - H[3].re);
         const cx<T> b = H[1];
@@ -877,7 +893,7 @@ __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const i
         for (int p = 0; p < 2; p++)
             for (int q = 0; q < 2; q++)
                 r1[p * 2 + q] = cadd(cmul(TT[p * 2 + 0], cconj(U[q * 2 + 0])), cmul(TT[p * 2 + 1], cconj(U[q * 2 + 1])));
-    } else {
+    } else if constexpr (!EXACT_ONLY) {
         const int ns = a.nsub[m];
         const T h = a.dt / T(ns);
         const T decay = a.decay[m], deph = a.dephase[m];
@@ -928,30 +944,39 @@ __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const i
         const T md = (mu1[c] - mu0[c]) / a.dt;
         a.Et[3 * m + c] = Et[c];
         a.mudot[3 * m + c] = md;
-        gm[c] = (double)(gam * mu1[c]);
+        gm[c] = gam * mu1[c];
         if (!isfinite(Et[c]) || !isfinite(md)) bad = true;
     }
     a.energy[m] = e_old + (double)en;
     if (bad) atomicCAS(a.status, 0, 6);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? MU_MIN_BLOCKS : 1)
+// EXACT_ONLY: every molecule takes the exact 2x2 step, so the RK4 branch (and its
+// registers) is not compiled in, and four blocks of 256 fit on an SM.
+// The block's sum of gamma <mu>: each warp adds its 32 terms in the field type by a
+// fixed shuffle tree, then one thread per component adds the eight warp sums in FP64
+// in warp order (a deterministic sum with few FP64 operations).
+template <typename T, bool EXACT_ONLY>
+__global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? (EXACT_ONLY ? MU_MIN_BLOCKS_EXACT : MU_MIN_BLOCKS) : 1)
     molecule_uniform_thread_kernel(const MolArgs<T> a) {
-    __shared__ double red[3][MU_THREADS];
+    __shared__ double red[3][MU_THREADS / 32];
     const int tid = threadIdx.x, m = blockIdx.x * MU_THREADS + tid;
-    double gm[3] = {0.0, 0.0, 0.0};
-    if (m < a.nmol) uniform_thread_step(a, m, gm);
+    T gm[3] = {T(0), T(0), T(0)};
+    if (m < a.nmol) uniform_thread_step<T, EXACT_ONLY>(a, m, gm);
+    if (!a.dpart) return;  // the laser drive has no mode to feed
 #pragma unroll
-    for (int c = 0; c < 3; c++) red[c][tid] = gm[c];
-    __syncthreads();
-    for (int s = MU_THREADS / 2; s > 0; s >>= 1) {
-        if (tid < s)
+    for (int c = 0; c < 3; c++) {
 #pragma unroll
-            for (int c = 0; c < 3; c++) red[c][tid] += red[c][tid + s];
-        __syncthreads();
+        for (int off = 16; off > 0; off >>= 1) gm[c] += __shfl_down_sync(0xffffffffu, gm[c], off);
+        if ((tid & 31) == 0) red[c][tid >> 5] = (double)gm[c];
     }
-    if (a.dpart && tid < 3) a.dpart[3 * blockIdx.x + tid] = red[tid][0];
+    __syncthreads();
+    if (tid < 3) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < MU_THREADS / 32; w++) sum += red[tid][w];
+        a.dpart[3 * blockIdx.x + tid] = sum;
+    }
 }
 
 // Uniform-field form (single-mode cavity): no window, no field read.
@@ -991,7 +1016,11 @@ template <typename T>
 cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s) {
     if (a.nmol == 0) return cudaSuccess;
     if (a.two_level) {
-        molecule_uniform_thread_kernel<T><<<(a.nmol + MU_THREADS - 1) / MU_THREADS, MU_THREADS, 0, s>>>(a);
+        const int nb = (a.nmol + MU_THREADS - 1) / MU_THREADS;
+        if (a.exact_only)
+            molecule_uniform_thread_kernel<T, true><<<nb, MU_THREADS, 0, s>>>(a);
+        else
+            molecule_uniform_thread_kernel<T, false><<<nb, MU_THREADS, 0, s>>>(a);
     } else {
         const int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
         molecule_uniform_kernel<T, false><<<blocks, MOL_WARPS * 32, 0, s>>>(a);

@@ -80,6 +80,27 @@ def test_matches_oracle_every_step(ml, las, precision, tol, rho_tol, two_level_o
         g.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_far_molecules_late_steps(ml, las, precision, tol):
+    """Molecules at z in [960, 1000) reached after about 2000 steps, stepped through the
+    graph runs: u = (z - xi0) - t cancels two numbers near 1000, which FP32 fields form
+    from float pairs."""
+    mols = ensemble(6, 12, True)
+    mols.pos[:, 2] = np.random.default_rng(7).uniform(960.0, 1000.0, size=mols.count)
+    o = las.OracleLaser(mols, **PULSE)
+    g = ml.Drive(mols, precision=precision, **PULSE)
+    try:
+        for chunk in (1900, 230):
+            g.step(chunk)
+            o.step(chunk)
+            assert np.abs(g.molecules(ml.ML_MOL_POP)[:, :2] - o.populations()).max() < tol
+        assert np.abs(o.populations()[:, 1]).max() > 1e-3  # the pulse did arrive
+        for m in range(mols.count):
+            assert np.abs(g.rho(m) - o.rho(m)).max() < tol
+    finally:
+        g.close()
+
+
 def test_graph_replay_equals_single_steps(ml):
     mols = ensemble(4, 500, True)
     a = ml.Drive(mols, **PULSE)

@@ -64,19 +64,7 @@ __global__ void __launch_bounds__(CAV_NT) cavity_mode_kernel(const T *gmu, long 
     }
     if (tid != 0) return;
     const double d[2] = {red[0][0], red[1][0]};
-    for (int l = 0; l < 2; l++) {
-        const double q = mode[l], p = mode[2 + l], d0 = mode[4 + l];
-        const double ph = p + 0.5 * dt * (-wc * wc * q - eps * d0);
-        const double qn = q + dt * ph;
-        const double pn = ph + 0.5 * dt * (-wc * wc * qn - eps * d[l]);
-        mode[l] = qn;
-        mode[2 + l] = pn;
-        mode[4 + l] = d[l];
-        mode[6 + l] = -(eps * qn + eps * eps / (wc * wc) * d[l]);
-    }
-    mode[8] = 0.0;
-    if (euf)  // FP32 molecules read the field in their own type
-        for (int l = 0; l < 3; l++) euf[l] = (float)mode[6 + l];
+    cavity_advance_mode(mode, euf, d, wc, eps, dt);
     *ticket = 0u;  // ready for the next launch
 }
 
@@ -90,6 +78,7 @@ struct ml_cavity {
     double dt = 0.0, wc = 0.0, eps = 0.0;
     bool two_level = true;
     bool exact_only = true;  // every molecule is kind 0 (the exact 2x2 step)
+    int mu_zero = 7;         // bit c: mu_c is zero for every molecule
     long long step = 0;
     int *d_nlev = nullptr, *d_kind = nullptr, *d_nsub = nullptr, *d_cmask = nullptr, *d_status = nullptr;
     long long *d_off = nullptr;
@@ -140,25 +129,31 @@ void fill_cavity_args(ml_cavity *c, MolArgs<T> &m) {
     m.energy = c->d_energy; m.status = c->d_status;
     m.two_level = c->two_level ? 1 : 0;
     m.exact_only = c->exact_only ? 1 : 0;
+    m.mu_zero = c->mu_zero;
     m.Eu = (const T *)(const void *)(sizeof(T) == 8 ? (c->d_mode ? c->d_mode + 6 : nullptr) : (const void *)c->d_euf);
     m.gmu = (T *)c->d_gmu;
     m.dpart = c->d_bpart;
+    m.mode = c->d_mode;
+    m.euf = c->d_euf;
+    m.ticket = c->d_ticket;
+    m.wc = c->wc;
+    m.eps = c->eps;
+    m.mdt = c->dt;
 }
 
 template <typename T>
 ml_status enqueue_steps(ml_cavity *c, long long nsteps, cudaStream_t s) {
     MolArgs<T> m;
     fill_cavity_args<T>(c, m);
-    const long long nb = (c->M + MU_THREADS_HOST - 1) / MU_THREADS_HOST;
     for (long long it = 0; it < nsteps; it++) {
+        if (c->two_level) {
+            // one launch: the molecules' partial sums and, in its last block, the mode step
+            CK(launch_molecules_cavity<T>(m, s));
+            continue;
+        }
         CK(launch_molecules_uniform<T>(m, s));
-        // two-level molecules leave per-block sums; others gamma <mu> per molecule
-        if (c->two_level)
-            cavity_mode_kernel<double><<<CAV_NB, CAV_NT, 0, s>>>(c->d_bpart, nb, c->d_part, c->d_ticket, c->d_mode,
-                                                                  c->d_euf, c->wc, c->eps, c->dt);
-        else
-            cavity_mode_kernel<T><<<CAV_NB, CAV_NT, 0, s>>>((const T *)c->d_gmu, c->M, c->d_part, c->d_ticket,
-                                                             c->d_mode, c->d_euf, c->wc, c->eps, c->dt);
+        cavity_mode_kernel<T><<<CAV_NB, CAV_NT, 0, s>>>((const T *)c->d_gmu, c->M, c->d_part, c->d_ticket, c->d_mode,
+                                                         c->d_euf, c->wc, c->eps, c->dt);
         CK(cudaGetLastError());
     }
     return ML_OK;
@@ -256,9 +251,11 @@ ml_status load_ensemble(ml_cavity *c, const ml_molecule_desc *md, double (&d0)[2
     c->pool = pool;
     c->two_level = true;
     c->exact_only = true;
+    c->mu_zero = 7;
     for (int m = 0; m < M; m++) {
         c->two_level = c->two_level && nlev[m] == 2;
         c->exact_only = c->exact_only && kind[m] == 0;
+        c->mu_zero &= ~cmask[m];
     }
     ml_status st;
 #define CAV(x)                \

@@ -207,11 +207,17 @@ struct MolArgs {
     const T *w;            // (M, NW) 1D kernel weights per axis and stagger
     int two_level;         // every molecule has two levels, at pool offset 4 m
     int exact_only;        // (uniform-field solvers) every molecule takes the exact 2x2 step
+    int mu_zero;           // (uniform-field solvers) bit c set: every molecule's mu_c is zero and is not loaded
     double *pop_sink;      // populations of the new state, device address of page-locked host memory
     long long pop_slot;    // row block of this step in the sink: (step mod ring) * nmol * MAXLEV
     const T *Eu;           // uniform-field source: the field before gamma_m (3 values, field type)
     T *gmu;                // uniform-field source: gamma_m <mu> of the new state (M, 3)
     double *dpart;         // uniform-field source, two-level molecules: per-block sums of gamma_m <mu> (3 each)
+    // single-mode cavity, two-level molecules: the launch's last block advances the mode
+    double *mode;          // q_x q_y p_x p_y d_x d_y Eu_x Eu_y Eu_z (FP64)
+    float *euf;            // Eu in FP32 for FP32 molecules, else null
+    unsigned *ticket;      // blocks of the launch that have written their partial
+    double wc, eps, mdt;   // mode frequency, coupling, time step
     // uniform-field source with laser = 1: the prescribed plane wave of Eq. E_analytical
     // instead of Eu, E~_m = gamma_m E0 pol env(u) cos(k u + phase), u = z_m - xi0 - t,
     // t = (run's first step + lstep) dt, env(u) = cos^2(pi u / 2W) for |u| < W
@@ -336,6 +342,29 @@ template <typename T> cudaError_t launch_tile_modes(const YeeArgs<T> &a, int nti
 template <typename T> cudaError_t launch_molecules(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_molecules_packed(const MolArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s);
+// single-mode cavity with two-level molecules: the molecule step and the mode step in one launch
+template <typename T> cudaError_t launch_molecules_cavity(const MolArgs<T> &a, cudaStream_t s);
+constexpr int CAV_GRID = 3 * 152;  // blocks of that launch at most: one wave of three per SM on 152 SMs
+
+// One velocity-Verlet step of the single-mode cavity (Sec. II normal modes, single-mode
+// limit) given the new dipole sums d = sum_m gamma_m <mu_x,y>; writes the next field
+// Eu = -(eps q + eps^2 / wc^2 d), and its FP32 copy when euf is set.
+__device__ inline void cavity_advance_mode(double *mode, float *euf, const double (&d)[2], double wc, double eps,
+                                           double dt) {
+    for (int l = 0; l < 2; l++) {
+        const double q = mode[l], p = mode[2 + l], d0 = mode[4 + l];
+        const double ph = p + 0.5 * dt * (-wc * wc * q - eps * d0);
+        const double qn = q + dt * ph;
+        const double pn = ph + 0.5 * dt * (-wc * wc * qn - eps * d[l]);
+        mode[l] = qn;
+        mode[2 + l] = pn;
+        mode[4 + l] = d[l];
+        mode[6 + l] = -(eps * qn + eps * eps / (wc * wc) * d[l]);
+    }
+    mode[8] = 0.0;
+    if (euf)
+        for (int l = 0; l < 3; l++) euf[l] = (float)mode[6 + l];
+}
 template <typename T> cudaError_t launch_current(const CurArgs<T> &a, cudaStream_t s, bool pdl = false);
 template <typename T> cudaError_t launch_gather(const GathArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_weights(int nmol, const double *pos, const double *sigma,

@@ -10,6 +10,8 @@
 //   4. FP64 running sum of Tr(rho H0) for the time-averaged molecular energy.
 // K3 (setup): separable, normalised 1D Gaussian weights per molecule, axis and
 // staggering, folded onto one period on periodic axes.
+#include <algorithm>
+
 #include "ml_internal.cuh"
 
 namespace ml {
@@ -849,13 +851,20 @@ __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const i
     const int kind = a.kind[m];
     const T gam = a.gamma[m];
     const double e_old = a.energy[m];
-    // every load is independent of the others (an absent dipole component is zero in
-    // the pool and is loaded as such)
+    // every load is independent of the others; a dipole component that is zero for the
+    // whole ensemble is not read (one that is zero for some molecules is read as zeros)
     cx<T> r[4], h0[4], mu[3][4];
     ld4(a.rho + o, r);
     ld4(a.H0 + o, h0);
 #pragma unroll
-    for (int c = 0; c < 3; c++) ld4(a.mu + c * a.pool + o, mu[c]);
+    for (int c = 0; c < 3; c++) {
+        if ((a.mu_zero >> c) & 1) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) mu[c][e] = {T(0), T(0)};
+        } else {
+            ld4(a.mu + c * a.pool + o, mu[c]);
+        }
+    }
     T Et[3];
     uniform_field(a, m, Et);
 #pragma unroll
@@ -979,6 +988,70 @@ __global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? (EXACT_ONLY ? MU_
     }
 }
 
+// Single-mode cavity with two-level molecules, one launch per step: a fixed grid of at
+// most CAV_GRID blocks walks the molecules (block b takes rows b, b + grid, ... of 256),
+// each warp adds its 32 terms of gamma <mu> in the field type by the shuffle tree and
+// accumulates its rows as an unevaluated pair hi + lo (Knuth's two-sum: FP32 operations
+// that keep about twice the FP32 precision); the block writes the FP64 sum of its warps
+// in warp order.  The block that takes the last ticket adds the partials in a fixed order
+// (thread t: partials t, t + 256, ...; then a tree) and advances the mode.  No block
+// waits for another; the grid, and so every sum, does not depend on the device.
+template <typename T, bool EXACT_ONLY>
+__global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? MU_MIN_BLOCKS : 1)
+    molecule_cavity_kernel(const MolArgs<T> a) {
+    __shared__ double red[2][MU_THREADS];
+    __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    T hi[2] = {T(0), T(0)}, lo[2] = {T(0), T(0)};
+    for (long long row = blockIdx.x; row * MU_THREADS < a.nmol; row += gridDim.x) {
+        const long long m = row * MU_THREADS + tid;
+        T gm[3] = {T(0), T(0), T(0)};
+        if (m < a.nmol) uniform_thread_step<T, EXACT_ONLY>(a, (int)m, gm);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) gm[c] += __shfl_down_sync(0xffffffffu, gm[c], off);
+            const T t = gm[c], sm = hi[c] + t, v = sm - hi[c];  // lane 0's t is the warp's sum
+            lo[c] += (hi[c] - (sm - v)) + (t - v);
+            hi[c] = sm;
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 2; c++) red[c][wp] = (double)hi[c] + (double)lo[c];
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            double sum = 0.0;
+            for (int w = 0; w < MU_THREADS / 32; w++) sum += red[c][w];
+            a.dpart[2 * blockIdx.x + c] = sum;
+        }
+        __threadfence();  // the partial is visible before the ticket is taken
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        double sum = 0.0;
+        for (int b = tid; b < (int)gridDim.x; b += MU_THREADS) sum += __ldcg(a.dpart + 2 * b + c);
+        red[c][tid] = sum;
+    }
+    __syncthreads();
+    for (int o = MU_THREADS / 2; o > 0; o >>= 1) {
+        if (tid < o)
+#pragma unroll
+            for (int c = 0; c < 2; c++) red[c][tid] += red[c][tid + o];
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    const double d[2] = {red[0][0], red[1][0]};
+    cavity_advance_mode(a.mode, a.euf, d, a.wc, a.eps, a.mdt);
+    *a.ticket = 0u;  // ready for the next launch
+}
+
 // Uniform-field form (single-mode cavity): no window, no field read.
 template <typename T, bool N2>
 __global__ void __launch_bounds__(MOL_WARPS * 32, sizeof(T) == 4 ? MOL_MIN_BLOCKS : 1)
@@ -1025,6 +1098,17 @@ cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s) {
         const int blocks = (a.nmol + MOL_WARPS - 1) / MOL_WARPS;
         molecule_uniform_kernel<T, false><<<blocks, MOL_WARPS * 32, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_molecules_cavity(const MolArgs<T> &a, cudaStream_t s) {
+    if (a.nmol == 0 || !a.two_level || !a.dpart || !a.mode || !a.ticket) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(CAV_GRID, ((long long)a.nmol + MU_THREADS - 1) / MU_THREADS);
+    if (a.exact_only)
+        molecule_cavity_kernel<T, true><<<grid, MU_THREADS, 0, s>>>(a);
+    else
+        molecule_cavity_kernel<T, false><<<grid, MU_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1133,7 +1217,8 @@ cudaError_t launch_mol_export(int what, int nmol, const int *nlev, const long lo
 #define ML_INST(T)                                                                                              \
     template cudaError_t launch_molecules<T>(const MolArgs<T> &, cudaStream_t, bool);                           \
     template cudaError_t launch_molecules_packed<T>(const MolArgs<T> &, cudaStream_t, bool);                    \
-    template cudaError_t launch_molecules_uniform<T>(const MolArgs<T> &, cudaStream_t);                             \
+    template cudaError_t launch_molecules_uniform<T>(const MolArgs<T> &, cudaStream_t);                         \
+    template cudaError_t launch_molecules_cavity<T>(const MolArgs<T> &, cudaStream_t);                          \
     template cudaError_t launch_molecules_batch<T>(const MolBatch<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_weights<T>(int, const double *, const double *, const int *, const int *,       \
                                            const int *, const int *, const int *, T *, cudaStream_t);           \

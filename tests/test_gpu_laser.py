@@ -81,6 +81,31 @@ def test_matches_oracle_every_step(ml, las, precision, tol, rho_tol, two_level_o
 
 
 @pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_out_of_plane_dipoles(ml, las, precision, tol):
+    """Every third molecule's dipole tilted out of the xy plane and a polarisation with
+    a z component: the kernels read mu_z only when some molecule has one."""
+    mols = ensemble(8, 24, True)
+    for m in range(0, mols.count, 3):
+        o = int(mols.off[m])
+        mols.mu[2, o:o + 4] = 0.7 * mols.mu[0, o:o + 4] + 0.4 * mols.mu[1, o:o + 4]
+    pulse = {**PULSE, "polarization": (0.6, 0.0, 0.8)}
+    o = las.OracleLaser(mols, **pulse)
+    g = ml.Drive(mols, precision=precision, **pulse)
+    try:
+        for _ in range(8):
+            g.step(30)
+            o.step(30)
+            assert np.abs(g.molecules(ml.ML_MOL_POP)[:, :2] - o.populations()).max() < tol
+        assert np.abs(o.populations()[:, 1]).max() > 1e-3
+        mudot_g = g.molecules(ml.ML_MOL_MUDOT)
+        assert np.abs(mudot_g[0::3, 2]).max() > 0  # the tilted molecules' mu_z moves
+        for m in range(mols.count):
+            assert np.abs(g.rho(m) - o.rho(m)).max() < tol
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
 def test_far_molecules_late_steps(ml, las, precision, tol):
     """Molecules at z in [960, 1000) reached after about 2000 steps, stepped through the
     graph runs: u = (z - xi0) - t cancels two numbers near 1000, which FP32 fields form

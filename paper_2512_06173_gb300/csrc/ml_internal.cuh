@@ -212,7 +212,7 @@ struct MolArgs {
     long long pop_slot;    // row block of this step in the sink: (step mod ring) * nmol * MAXLEV
     const T *Eu;           // uniform-field source: the field before gamma_m (3 values, field type)
     T *gmu;                // uniform-field source: gamma_m <mu> of the new state (M, 3)
-    double *dpart;         // uniform-field source, two-level molecules: per-block sums of gamma_m <mu> (3 each)
+    double *dpart;         // single-mode cavity, two-level molecules: per-block sums of gamma_m <mu_x,y> (2 each)
     // single-mode cavity, two-level molecules: the launch's last block advances the mode
     double *mode;          // q_x q_y p_x p_y d_x d_y Eu_x Eu_y Eu_z (FP64)
     float *euf;            // Eu in FP32 for FP32 molecules, else null

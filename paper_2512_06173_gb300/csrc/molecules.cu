@@ -812,11 +812,10 @@ cudaError_t launch_molecules_packed(const MolArgs<T> &a, cudaStream_t s, bool pd
 
 // Uniform-field form for two-level molecules: one thread per molecule, so that a warp
 // streams 32 molecules' 2x2 matrices with 16-byte loads instead of one molecule's four
-// elements.  The same step as molecule_body: E~ = gamma Eu held over dt; the exact
-// 2x2 exponential (kind 0) or nsub classic RK4 substeps of the GKSL equation (kind 1);
-// mudot and the energy sum.  Instead of gamma <mu> per molecule, each block writes the
-// sum of its molecules' gamma <mu> of the new state (FP64, a fixed tree over the block)
-// to a.dpart[3 * block + c].
+// elements.  The same step as molecule_body: E~ = gamma Eu (or the laser's wave) held
+// over dt; the exact 2x2 exponential (kind 0) or nsub classic RK4 substeps of the GKSL
+// equation (kind 1); mudot and the energy sum.  uniform_thread_step hands gamma <mu> of
+// the new state to its caller: the cavity kernel sums it, the laser drive needs none.
 template <typename T>
 __device__ __forceinline__ void ld4(const cx<T> *p, cx<T> (&v)[4]) {
     if constexpr (sizeof(T) == 4) {
@@ -960,32 +959,15 @@ __device__ __forceinline__ void uniform_thread_step(const MolArgs<T> &a, const i
     if (bad) atomicCAS(a.status, 0, 6);
 }
 
-// EXACT_ONLY: every molecule takes the exact 2x2 step, so the RK4 branch (and its
-// registers) is not compiled in, and four blocks of 256 fit on an SM.
-// The block's sum of gamma <mu>: each warp adds its 32 terms in the field type by a
-// fixed shuffle tree, then one thread per component adds the eight warp sums in FP64
-// in warp order (a deterministic sum with few FP64 operations).
+// Laser drive (no mode to feed).  EXACT_ONLY: every molecule takes the exact 2x2 step,
+// so the RK4 branch (and its registers) is not compiled in, and four blocks of 256 fit
+// on an SM.
 template <typename T, bool EXACT_ONLY>
 __global__ void __launch_bounds__(MU_THREADS, sizeof(T) == 4 ? (EXACT_ONLY ? MU_MIN_BLOCKS_EXACT : MU_MIN_BLOCKS) : 1)
     molecule_uniform_thread_kernel(const MolArgs<T> a) {
-    __shared__ double red[3][MU_THREADS / 32];
-    const int tid = threadIdx.x, m = blockIdx.x * MU_THREADS + tid;
-    T gm[3] = {T(0), T(0), T(0)};
+    const int m = blockIdx.x * MU_THREADS + threadIdx.x;
+    T gm[3];
     if (m < a.nmol) uniform_thread_step<T, EXACT_ONLY>(a, m, gm);
-    if (!a.dpart) return;  // the laser drive has no mode to feed
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) gm[c] += __shfl_down_sync(0xffffffffu, gm[c], off);
-        if ((tid & 31) == 0) red[c][tid >> 5] = (double)gm[c];
-    }
-    __syncthreads();
-    if (tid < 3) {
-        double sum = 0.0;
-#pragma unroll
-        for (int w = 0; w < MU_THREADS / 32; w++) sum += red[tid][w];
-        a.dpart[3 * blockIdx.x + tid] = sum;
-    }
 }
 
 // Single-mode cavity with two-level molecules, one launch per step: a fixed grid of at
@@ -1089,6 +1071,7 @@ template <typename T>
 cudaError_t launch_molecules_uniform(const MolArgs<T> &a, cudaStream_t s) {
     if (a.nmol == 0) return cudaSuccess;
     if (a.two_level) {
+        if (a.dpart) return cudaErrorInvalidValue;  // a two-level cavity steps through launch_molecules_cavity
         const int nb = (a.nmol + MU_THREADS - 1) / MU_THREADS;
         if (a.exact_only)
             molecule_uniform_thread_kernel<T, true><<<nb, MU_THREADS, 0, s>>>(a);

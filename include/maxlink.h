@@ -345,9 +345,10 @@ typedef struct ml_cavity ml_cavity;
 ml_status ml_cavity_create(const ml_cavity_desc *d, const ml_molecule_desc *m, ml_cavity **out);
 ml_status ml_cavity_destroy(ml_cavity *c);
 
-/* Enqueue nsteps steps on `stream` (two launches per step: the molecules, then the
- * dipole sum and the mode update; runs of 64 steps replay a CUDA graph captured on
- * first use). */
+/* Enqueue nsteps steps on `stream` (one launch per step for two-level ensembles, whose
+ * last block adds the dipole sum and updates the mode; two for others: the molecules,
+ * then the dipole sum and the mode update; runs of 64 steps replay a CUDA graph
+ * captured on first use). */
 ml_status ml_cavity_step(ml_cavity *c, int64_t nsteps, void *stream);
 
 /* Mode state after the enqueued steps into host `out`:

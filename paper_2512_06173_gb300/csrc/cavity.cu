@@ -2,15 +2,17 @@
 // in the single-mode limit the paper implements: one mode of frequency w_c per
 // polarisation lambda = x, y with mode function e_lambda / sqrt(V).
 //
-// Per step, two launches on the caller's stream:
-//   1. the molecule kernel in its uniform-field form: every molecule m sees
-//      E~_m = gamma_m Eu (Eq. E_normalmode; Eu is kept on the device), advances rho
-//      exactly as in ml_step, and writes gamma_m <mu> of the new state;
-//   2. cavity_mode_kernel: CAV_NB blocks add those dipoles in a fixed order into one
-//      partial each (FP64); the last block to finish (a ticket counter) adds the
-//      partials by a fixed tree, giving d^{n+1} (Eq. dklambda_def), advances q and p by
-//      velocity Verlet on q'' = -w_c^2 q - eps d (Eq. eom_cavmd_a) with half kicks at d^n
-//      and d^{n+1}, and writes the next field Eu = -(eps q + eps^2 / w_c^2 d).
+// Every molecule m sees E~_m = gamma_m Eu (Eq. E_normalmode; Eu is kept on the device)
+// and advances rho exactly as in ml_step.  The new dipole sum d^{n+1} (Eq. dklambda_def)
+// is added in a fixed order; then q and p advance by velocity Verlet on
+// q'' = -w_c^2 q - eps d (Eq. eom_cavmd_a) with half kicks at d^n and d^{n+1}, and the
+// next field is Eu = -(eps q + eps^2 / w_c^2 d).  Per step, on the caller's stream:
+//   - ensembles of two-level molecules: one launch (molecule_cavity_kernel): per-block
+//     partial sums, and the block that takes the last ticket adds them and steps the mode;
+//   - other ensembles: the warp-per-molecule uniform-field kernel writes gamma_m <mu>
+//     per molecule, then cavity_mode_kernel: CAV_NB blocks add them in a fixed order
+//     into one FP64 partial each, and the last block (a ticket counter) adds the
+//     partials by a fixed tree and steps the mode.
 // Nothing waits on another block: the last block is whichever takes the final ticket.
 // Runs of 64 steps are captured once into a CUDA graph and replayed.
 #include <algorithm>

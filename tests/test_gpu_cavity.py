@@ -104,6 +104,34 @@ def test_three_thousand_two_level_emitters(ml, cav):
         g.close()
 
 
+def test_blocks_with_several_rows(ml, cav):
+    """120,000 exact two-level emitters (the cavity workload's ensemble): more rows of 256
+    than the one-launch kernel has blocks (456), so some blocks add two rows, and the last
+    row is ragged (192 molecules).  Mode after every step and sampled density matrices
+    against the oracle, FP64 and FP32."""
+    M = 120_000
+    mols = W.cavity_ensemble(M)
+    eps = 0.05 * 0.25 ** 2 / np.sqrt(2 * 0.25 * M * 0.05 ** 2 / 2)
+    kw = dict(omega_c=0.25, coupling=eps, dt=0.5, q0=(2e-3, -1e-3), p0=(0.0, 5e-4))
+    o = cav.OracleCavity(mols, **kw)
+    gs = {prec: ml.Cavity(mols, precision=prec, **kw) for prec in (1, 0)}
+    tol = {1: 1e-10, 0: 1e-4}
+    sample = np.r_[0:8, 255:259, 116_730:116_745, M - 200:M]
+    try:
+        for _ in range(4):
+            o.step(1)
+            for prec, g in gs.items():
+                g.step(1)
+                assert rel(g.mode(), o.mode()) < tol[prec], prec
+        for prec, g in gs.items():
+            pool = g.molecules(ml.ML_MOL_RHO)  # two levels each: molecule m at 4 m
+            for m in sample:
+                assert rel(pool[4 * m:4 * m + 4].reshape(2, 2), o.rho(int(m))) < tol[prec], (prec, m)
+    finally:
+        for g in gs.values():
+            g.close()
+
+
 def test_sqrt_n_identity(ml):
     N = 7
     kw = dict(omega0=0.25, mu12=0.8, axis=1, cg=np.sqrt(0.7), ce=np.sqrt(0.3) * np.exp(0.4j), dephase=1e-3)

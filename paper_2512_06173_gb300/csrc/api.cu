@@ -793,7 +793,6 @@ void fill_mol_args(ml_grid *g, int cur, MolArgs<T> &m) {
     m.gamma = (const T *)g->d_gamma; m.decay = (const T *)g->d_decay; m.dephase = (const T *)g->d_deph;
     m.H0 = (const cx<T> *)g->d_H0; m.mu = (const cx<T> *)g->d_mu; m.pool = g->pool;
     m.rho = (cx<T> *)g->d_rho;
-    m.moff = g->d_moff; m.mlist = g->d_mlist; m.part = (const T *)g->d_part;
     m.Et = (T *)g->d_Et; m.mudot = (T *)g->d_mudot; m.c = (T *)g->d_c;
     m.energy = g->d_energy; m.status = g->d_status;
     m.win = g->d_win; m.wf = g->d_wf; m.w = (const T *)g->d_w;

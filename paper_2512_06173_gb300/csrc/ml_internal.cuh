@@ -194,9 +194,6 @@ struct MolArgs {
     const cx<T> *mu;       // 3 pools back to back
     long long pool;
     cx<T> *rho;
-    const int *moff;       // CSR over molecules: partial-sum entries of molecule m
-    const int *mlist;      //   are mlist[moff[m] .. moff[m+1]]
-    const T *part;         // (entries, 3) gather partials of this step
     T *Et;
     T *mudot;
     T *c;

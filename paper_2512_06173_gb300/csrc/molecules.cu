@@ -226,13 +226,14 @@ __device__ __forceinline__ cx<T> rhs_elem(int n, int j, int l, const cx<T> *S, c
     return out;
 }
 
-// SRC: where the regularised field comes from.  SRC_PARTS: the gather kernel's
-// partials; SRC_WINDOW: the warp gathers its own window from E (window_gather);
-// SRC_UNIFORM: one field for every molecule (a.Eu, times gamma_m), as in the
-// single-mode cavity, and the warp also writes gamma_m <mu> of the new state.
-constexpr int SRC_PARTS = 0, SRC_WINDOW = 1, SRC_UNIFORM = 2;
+// SRC: where the regularised field comes from.  SRC_WINDOW: the warp gathers its own
+// window from E (window_gather); SRC_UNIFORM: one field for every molecule (a.Eu, times
+// gamma_m), as in the single-mode cavity, and the warp also writes gamma_m <mu> of the
+// new state.
+constexpr int SRC_WINDOW = 1, SRC_UNIFORM = 2;
 template <typename T, int SRC, bool N2>
 __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0) {
+    static_assert(SRC == SRC_WINDOW || SRC == SRC_UNIFORM, "unknown field source");
     __shared__ MolShared<T> sh;
     const int lane = threadIdx.x & 31;
     const int wl = threadIdx.x >> 5;
@@ -293,7 +294,7 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         uniform_field(a, m, Et);
 #pragma unroll
         for (int c = 0; c < 3; c++) Et[c] *= gam;
-    } else if (SRC == SRC_WINDOW) {
+    } else {
         const T *sw = sh.W[wl];
         T g[3];
         bool done = false;
@@ -301,18 +302,6 @@ __device__ __forceinline__ void molecule_body(const MolArgs<T> &a, const int m0)
         if (!done) window_gather(a, m, cm, sw, g);
 #pragma unroll
         for (int c = 0; c < 3; c++) Et[c] = gam * g[c];
-    } else {
-        // this molecule's gather partials, added lane-strided in list order and
-        // combined by a fixed xor tree
-        T g[3] = {T(0), T(0), T(0)};
-        for (int t = a.moff[m] + lane; t < a.moff[m + 1]; t += 32) {
-            const T *pp = a.part + 3ll * a.mlist[t];
-            g[0] += pp[0];
-            g[1] += pp[1];
-            g[2] += pp[2];
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c++) Et[c] = gam * warp_sum(g[c]);
     }
 
     // ---- 2. H = H0 - Etilde . mu and <mu> before the step.  For Hermitian
